@@ -1,0 +1,358 @@
+"""Benchmark of the lattice sweep (MLUPS and fraction of the HBM roofline).
+
+Workload: one four-control-point metaball settling in a walled 128x128x256
+D3Q19 lattice, BGK tau = 0.8, FP32 populations, 100 DEM sub-steps per LBM
+step (the single non-spherical particle run, synthetic shape, seeded).  A
+"step" is one whole LBM step through the C ABI: particle geometry and
+binning, node classification with refilling, the fused sweep, the force
+reduction and the DEM sub-cycle.
+
+Prints one JSON line.  value = lattice updates per second over all nodes of
+all ranks (MLUPS); e2e = the same metric with the per-step host->device
+particle upload and device->host force/state read through the public API;
+roofline = the sweep kernel's algorithmic bytes over its CUDA-event time;
+cpu_baseline = the FP64 CPU oracle timed on a bounded sample of the same
+workload on the host cores.  The populations (2 x 319 MB) exceed the 129 MB
+L2, so no flush is needed between steps.
+
+--impl reference times the oracle itself (on rank 0; other ranks exit).
+With torchrun and --gpus N > 1 every rank runs an independent replica on its
+own GPU (the sweep does not exchange data), timed between barriers, max over
+ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline per lattice sweep; drag rel. error vs FP64 oracle"
+UNIT = "MLUPS"
+BYTES_PER_FLUID_NODE = 2 * 19 * 4  # FP32 D3Q19: 19 loads + 19 stores
+BYTES_PER_NODE_FLAGS = 2           # uint16 flag per node
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_settling_metaball_128x128x256.txt")
+SWEEP_SOURCES = ["k_sweep.cuh", "k_flags.cuh", "lbm_internal.cuh", "launch_impl.cuh", "sweep_f32.cu"]
+
+
+def workload():
+    from paper_2206_11634_gb300 import workloads
+    return workloads.settling_metaball(tau=0.8)
+
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return float(json.load(open(p))["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def sweep_source_hash():
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2206_11634_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, when it was
+    taken on the current sweep source; else None."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    vals = {}
+    for line in open(PROFILE_SUMMARY):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != sweep_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.out.flush()
+        rows = []
+        for line in open(self.out.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float) -> float:
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_lattice(pkg, wl, stream):
+    kw = dict(periodic=wl["periodic"], lattice=19, storage=wl["storage"], n_sub=wl["n_sub"],
+              max_particles=len(wl["particles"]), tau=wl["tau"], gravity=wl["gravity"], force=wl["force"],
+              kn=wl["kn"], eta_n=wl["eta_n"], kt=wl["kt"], eta_t=wl["eta_t"], mu_s=wl["mu_s"], c_tol=wl["c_tol"])
+    lat = pkg.Lattice(wl["nx"], wl["ny"], wl["nz"], stream=stream, **kw)
+    parts = [pkg.make_particle(p["cp"], p["K"], p["x"], q=p["q"], v=p["v"], w=p["w"], Rs=p["Rs"],
+                               density=p["density"], fixed=p["fixed"]) for p in wl["particles"]]
+    lat.set_particles(parts)
+    return lat
+
+
+def oracle_sample(wl, steps: int):
+    """Time `steps` steps of the FP64 oracle on the full workload."""
+    import oracle
+    o = oracle.Oracle(wl["nx"], wl["ny"], wl["nz"], Q=19, periodic=tuple(wl["periodic"]), tau=wl["tau"],
+                      n_sub=wl["n_sub"], gravity=wl["gravity"], force=wl["force"], kn=wl["kn"], eta_n=wl["eta_n"],
+                      kt=wl["kt"], eta_t=wl["eta_t"], mu_s=wl["mu_s"], c_tol=wl["c_tol"])
+    o.set_particles([oracle.make_particle(p["cp"], p["K"], p["x"], q=p["q"], v=p["v"], w=p["w"], Rs=p["Rs"],
+                                          density=p["density"], fixed=p["fixed"]) for p in wl["particles"]])
+    o.step(1)  # first step pays the page-in of the arrays
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    n = wl["nx"] * wl["ny"] * wl["nz"]
+    return n * steps / dt / 1e6, dt
+
+
+def omp_threads() -> int:
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def run_reference(args):
+    world, rank, local, dist = dist_setup()
+    if rank != 0:
+        return 0
+    wl = workload()
+    import oracle
+    oracle.build()
+    steps = max(1, args.steps)
+    warm = max(0, args.warmup)
+    if warm:
+        oracle_sample(wl, warm)
+    mlups, dt = oracle_sample(wl, steps)
+    cores = omp_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": round(dt / steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "lattice": "D3Q19", "storage": "f64", "tau": wl["tau"],
+                       "n_sub": wl["n_sub"], "particles": len(wl["particles"])},
+            "cpu_baseline": {"value": round(mlups, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{steps} steps of the full {wl['nx']}x{wl['ny']}x{wl['nz']} workload"},
+            "e2e": {"value": round(mlups, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    world, rank, local, dist = dist_setup()
+    torch.cuda.set_device(local)
+    import paper_2206_11634_gb300 as pkg
+    from paper_2206_11634_gb300 import build as lib_build
+    if rank == 0 or not os.path.exists(pkg.LIB_PATH):
+        lib_build.build()
+    barrier(dist)
+    wl = workload()
+    nodes = wl["nx"] * wl["ny"] * wl["nz"]
+    stream = torch.cuda.Stream()
+    lat = make_lattice(pkg, wl, stream)
+
+    # warm-up
+    lat.step(max(3, args.warmup))
+    torch.cuda.synchronize()
+    fl = lat.flags()
+    n_fluid = int((fl == 0).sum().item())
+
+    # timed device region, per-kernel events recorded inside the library
+    lat.profile(True)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier(dist)
+        torch.cuda.synchronize()
+        start.record(stream)
+        lat.step(args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        barrier(dist)
+    ms_local = start.elapsed_time(stop)
+    prof = lat.profile_read()
+    lat.profile(False)
+    lat.check()
+    ms = max_over_ranks(dist, ms_local)
+    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+
+    # end-to-end through the public API with host buffers: per step upload
+    # the particle state, step, read back forces, torques and state
+    import numpy as np
+    np_ = len(wl["particles"])
+    state = (pkg.LbmParticle * np_)()
+    F = np.zeros((np_, 3))
+    T = np.zeros((np_, 3))
+    import ctypes as C
+    L = lat.L
+    L.lbm_get_forces(lat.h, None, None, state)
+    e2e_steps = max(1, args.steps // 4)
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rc = L.lbm_set_particles(lat.h, state, np_)
+        rc |= L.lbm_step(lat.h, 1)
+        rc |= L.lbm_get_forces(lat.h, F.ctypes.data_as(C.POINTER(C.c_double)),
+                               T.ctypes.data_as(C.POINTER(C.c_double)), state)
+        if rc:
+            raise RuntimeError(L.lbm_last_error(lat.h).decode())
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
+    barrier(dist)
+    e2e_value = world * nodes * e2e_steps / e2e_s / 1e6
+    h2d = C.sizeof(pkg.LbmParticle) * np_
+    d2h = 48 * np_ + C.sizeof(pkg.LbmParticle) * np_
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    sweep_ms, sweep_n = prof["k_sweep"]
+    sweep_avg_s = sweep_ms / max(1, sweep_n) * 1e-3
+    alg_bytes = BYTES_PER_FLUID_NODE * n_fluid + BYTES_PER_NODE_FLAGS * nodes
+    peak, peak_kind = measured_peak_gbs()
+    achieved = alg_bytes / sweep_avg_s / 1e9
+    traffic = profiled_traffic()
+    kernels = {k: {"avg_us": round(v[0] / max(1, v[1]) * 1e3, 3), "launches": v[1],
+                   "share": round(v[0] / max(1e-12, sum(x[0] for x in prof.values())), 4)} for k, v in prof.items()}
+
+    # CPU baseline: the oracle as it stands on this host, bounded sample
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cpu_steps = args.cpu_steps
+        mlups, dt = oracle_sample(wl, cpu_steps)
+        cpu = {"value": round(mlups, 4), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+               "sample": f"{cpu_steps} steps of the full {wl['nx']}x{wl['ny']}x{wl['nz']} workload, FP64, "
+                         f"{dt:.1f} s"}
+
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "lattice": "D3Q19", "storage": "f32", "tau": wl["tau"],
+                       "n_sub": wl["n_sub"], "particles": len(wl["particles"]), "nodes": nodes,
+                       "fluid_nodes": n_fluid, "l2": "no flush: populations 2x319 MB exceed the 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": f"{peak_kind} copy",
+                         "kernel": "k_sweep", "bytes_per_launch": alg_bytes,
+                         "avg_launch_us": round(sweep_avg_s * 1e6, 3)},
+            "kernels": kernels,
+            "gpu_launches": int(sum(v[1] for v in prof.values())),
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

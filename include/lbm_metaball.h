@@ -1,0 +1,195 @@
+/*
+ * lbm_metaball.h -- C ABI of the GB300 (sm_103a) lattice sweep of the coupled
+ * metaball-DEM / lattice-Boltzmann method of Zhang et al., arXiv 2206.11634.
+ *
+ * One handle holds one lattice (D3Q19, or the paper's D3Q15 of §2.2), its
+ * node flags and a set of metaball particles.  lbm_step() advances it by whole
+ * LBM steps, each of which runs on the GPU, in order:
+ *   1. node classification (§2.3.1, Eq. (26)): a node is solid when
+ *      M_j(x) = sum_i K_i/|x - x_i|^2 >= c0 for a particle j (Eq. (4)), owned
+ *      by the particle with the largest M_j (ties to the lower index);
+ *      nodes a particle uncovered since the last step are refilled (§2.3.3,
+ *      Eq. (30));
+ *   2. the fused stream/collide sweep (§2.2, Eqs. (14)-(18), BGK with Guo
+ *      forcing) with velocity-interpolated bounce-back on particle links
+ *      (§2.3.1, Eqs. (19)-(25), q from Eq. (27)), halfway bounce-back on box
+ *      walls and where VIBB lacks a second fluid node (§2.3.5 item 1), the
+ *      Galilean-invariant momentum exchange (§2.3.2, Eqs. (28)-(29)) and the
+ *      missing-force-point terms (§2.3.5 item 2, Eqs. (31)-(32));
+ *   3. a deterministic reduction of the per-link force and torque into one
+ *      FP64 total per particle;
+ *   4. n_sub DEM sub-steps (§2.3.4) with the hydrodynamic load frozen:
+ *      metaball-metaball and metaball-wall contacts (§2.1.3-2.1.4, Eqs.
+ *      (5)-(13)), the contact law of §2.1.1 (Eqs. (2)-(3)), velocity Verlet
+ *      and Euler's equations in the body frame (Eq. (1)), in FP64.
+ *
+ * Units are lattice units: dx = dt = C = 1, c_s^2 = 1/3.  Node (i,j,k) sits
+ * at position (i,j,k); a non-periodic face is a resting no-slip wall halfway
+ * between the last node and the next (at -1/2 and n-1/2).
+ *
+ * Memory and ownership.  The library allocates no device memory.  The caller
+ * asks lbm_workspace_size() for the size, allocates one device buffer (any
+ * allocator, 256-byte aligned), and passes it to lbm_init(); the handle
+ * borrows it until lbm_destroy().  The handle itself is a small host
+ * allocation.  All GPU work is issued on the caller's CUDA stream given to
+ * lbm_init() (NULL = legacy default stream).  Host buffers passed in are
+ * read or written during the call only.
+ *
+ * Errors.  Every function returns LBM_OK (0) or a negative lbm_status.
+ * lbm_last_error() gives a one-line message for the last failure on a handle.
+ * A function that fails leaves the handle usable unless the status is
+ * LBM_ERR_CUDA.  lbm_step() is asynchronous: device-side conditions
+ * (particle list overflow, non-finite or supersonic state) are reported by
+ * the next call that synchronises (lbm_get_forces, lbm_get_fields,
+ * lbm_get_populations, lbm_check).
+ */
+#ifndef LBM_METABALL_H
+#define LBM_METABALL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_MAX_CP 16          /* control points per particle */
+#define LBM_MAX_PER_BRICK 16   /* particles whose search boxes meet one 32x4x2 node brick */
+
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_ERR_BAD_ARG = -1,       /* invalid argument or configuration */
+    LBM_ERR_WS_TOO_SMALL = -2,  /* workspace smaller than lbm_workspace_size() */
+    LBM_ERR_CAPACITY = -3,      /* more particles than max_particles, or a brick list overflowed */
+    LBM_ERR_DIVERGED = -4,      /* non-finite populations or |u| > 0.5 seen by lbm_check() */
+    LBM_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
+    LBM_ERR_CUDA = -6           /* a CUDA call failed; the message names it */
+};
+
+enum lbm_storage {
+    LBM_STORE_F64 = 0,   /* populations stored and collided in FP64 */
+    LBM_STORE_F32 = 1,   /* stored and collided in FP32 */
+    LBM_STORE_F16 = 2,   /* stored as FP16 offsets (f_i/w_i - rho0), collided in FP32 */
+    LBM_STORE_BF16 = 3   /* stored as BF16 offsets (f_i/w_i - rho0), collided in FP32 */
+};
+
+/* Simulation parameters.  Zero-initialise, then set what is needed; the
+ * library's defaults are noted where 0 is not meaningful. */
+typedef struct lbm_config {
+    int32_t nx, ny, nz;        /* lattice nodes per axis, >= 2 */
+    int32_t lattice;           /* 19 (D3Q19) or 15 (D3Q15, §2.2) */
+    int32_t storage;           /* enum lbm_storage */
+    int32_t periodic[3];       /* 1 = periodic axis, 0 = halfway walls */
+    int32_t n_sub;             /* DEM sub-steps per LBM step (§2.3.4); 0 = particles never move */
+    int32_t vibb;              /* 1 = VIBB on particle links; 0 = halfway bounce-back on all of them */
+    int32_t missing_force;     /* 1 = add the missing-force-point terms of §2.3.5 item 2 */
+    int32_t max_particles;     /* capacity reserved in the workspace, >= 1 */
+    double tau;                /* BGK relaxation time, > 1/2 */
+    double rho0;               /* reference density (initial fluid, refill, Eq. (31)) */
+    double c0;                 /* surface value of M (Eq. (26)); 1 for the metaball of Eq. (4) */
+    double u0[3];              /* initial uniform fluid velocity */
+    double force[3];           /* body force density on the fluid (Guo forcing) */
+    double gravity[3];         /* gravity, applied to particles as (1 - rho0/rho_s) g (§3.1) */
+    double kn, eta_n;          /* normal spring and dashpot, Eq. (2) */
+    double kt, eta_t, mu_s;    /* tangential spring, dashpot and Coulomb coefficient, Eq. (3) */
+    double c_tol;              /* lower bound of M at the closest point, Eq. (5) */
+    double mass_spacing;       /* sample spacing of the mass-property integration (0 -> 0.5) */
+} lbm_config;
+
+/* One particle: shape, material and rigid-body state.  Control points are in
+ * the body frame relative to x; orientation q is a unit quaternion (w,x,y,z)
+ * mapping body to world; w is the angular velocity in the world frame.
+ * With mass <= 0 lbm_set_particles() computes mass, centroid and inertia by
+ * sampling {M >= c0} on a grid of spacing mass_spacing, then shifts the
+ * control points so that x is the centroid; otherwise mass and the body-frame
+ * inertia tensor (about x) are taken as given. */
+typedef struct lbm_particle {
+    int32_t n_cp;                 /* 1 .. LBM_MAX_CP */
+    int32_t fixed;                /* 1 = never moved by the DEM (its v and w still set u_w) */
+    double cp[LBM_MAX_CP][3];     /* control points x_i, body frame (Eq. (4)) */
+    double K[LBM_MAX_CP];         /* weights K_i >= 0 (Eq. (4)) */
+    double Rs;                    /* sphero radius of the contact skin (§2.1.3) */
+    double density;               /* rho_s */
+    double mass;
+    double inertia[9];            /* body-frame inertia tensor, row major */
+    double x[3];
+    double q[4];
+    double v[3];
+    double w[3];
+} lbm_particle;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Device bytes lbm_init() needs for this configuration.  Returns
+ * LBM_ERR_BAD_ARG for an invalid configuration. */
+int lbm_workspace_size(const lbm_config *cfg, size_t *bytes);
+
+/* Create a handle on the current CUDA device.  dev_ws: device buffer of at
+ * least lbm_workspace_size() bytes, 256-byte aligned, owned by the caller and
+ * borrowed until lbm_destroy().  cuda_stream: a cudaStream_t (NULL = default
+ * stream).  Initialises every node to f^eq(rho0, u0) with no particles. */
+int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_stream, lbm_handle **out);
+
+/* Replace the particle set (host array of n particles, 0 <= n <=
+ * max_particles).  Computes mass properties where mass <= 0, resets the
+ * contact history and copies the table to the device (stream ordered).  The
+ * node flags are recomputed at the start of the next lbm_step(). */
+int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n);
+
+/* Advance nsteps >= 0 LBM steps on the handle's stream (asynchronous). */
+int lbm_step(lbm_handle *h, int nsteps);
+
+/* Synchronise and copy out the hydrodynamic force and torque of the last
+ * step (F, T: host double[n][3], either may be NULL) and, if state_out is not
+ * NULL, the current particle states (host lbm_particle[n]). */
+int lbm_get_forces(lbm_handle *h, double *F, double *T, lbm_particle *state_out);
+
+/* Synchronise and write the macroscopic fields of the stored populations to
+ * caller device buffers (any may be NULL): dev_rho double[nz][ny][nx],
+ * dev_u double[3][nz][ny][nx] (u = (sum f e - F/2)/rho, the velocity of the
+ * last collision), dev_flags uint16[nz][ny][nx] (0 = fluid, j+1 = solid node
+ * owned by particle j).  Solid nodes report rho = 0, u = 0. */
+int lbm_get_fields(lbm_handle *h, void *dev_rho, void *dev_u, void *dev_flags);
+
+/* Test hooks: copy the stored (post-collision) populations from / to a
+ * caller device buffer double[Q][nz][ny][nx], converting from / to the
+ * storage format. */
+int lbm_set_populations(lbm_handle *h, const void *dev_f);
+int lbm_get_populations(lbm_handle *h, void *dev_f);
+
+/* Synchronise and report the device-side health: LBM_ERR_CAPACITY when a
+ * brick list overflowed, LBM_ERR_DIVERGED when populations are non-finite or
+ * some fluid node moves faster than 0.5 (checked over the whole lattice). */
+int lbm_check(lbm_handle *h);
+
+/* Counters of the last step: new fluid nodes refilled and particle links. */
+int lbm_get_counters(lbm_handle *h, int64_t *steps, int32_t *nrefill, int32_t *nlinks);
+
+/* Kernels launched per lbm_step() step (for launch accounting). */
+int lbm_kernels_per_step(const lbm_handle *h);
+
+/* Kernel timing.  With enable = 1, every later lbm_step() records a CUDA
+ * event pair around each of its kernels on the handle's stream (up to 65536
+ * launches per kernel; later ones are not recorded).  lbm_profile_read()
+ * synchronises and returns, for kernel k (0 bin, 1 flags, 2 sweep, 3 force
+ * reduce, 4 DEM), the summed device time in milliseconds and the number of
+ * launches recorded since profiling was enabled; enable = 0 stops recording
+ * and releases the events.  The events are created on the host side of the
+ * CUDA runtime (no device memory is allocated). */
+int lbm_profile(lbm_handle *h, int enable);
+int lbm_profile_read(lbm_handle *h, int kernel, double *total_ms, int64_t *launches);
+
+/* Change the stream later work is issued on. */
+int lbm_set_stream(lbm_handle *h, void *cuda_stream);
+
+/* Release the handle (not the workspace).  Synchronises its stream. */
+int lbm_destroy(lbm_handle *h);
+
+/* Message of the last failure on h (or of the last failed lbm_init when h is
+ * NULL); never NULL. */
+const char *lbm_last_error(const lbm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

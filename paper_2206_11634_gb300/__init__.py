@@ -1,0 +1,7 @@
+"""GB300-native (sm_103a) lattice sweep of the coupled metaball-DEM / LBM method
+(arXiv 2206.11634): node classification, fused stream/collide with
+velocity-interpolated bounce-back, refilling, momentum-exchange force
+reduction and the metaball DEM, behind the C ABI of include/lbm_metaball.h.
+"""
+from .lbm import (LIB_PATH, STORAGE, Lattice, LbmConfig, LbmError, LbmParticle, load_library,  # noqa: F401
+                  make_config, make_particle, particle_dict)

@@ -1,0 +1,253 @@
+// Node classification and local refilling (templated on storage and lattice).
+//
+// k_flags (one CTA per brick): sorts the brick's list, classifies its nodes
+// (§2.3.1: solid when M_j >= c0, Eq. (26), owner = largest M_j, ties to the
+// lower index), and refills the nodes the particles uncovered since the last
+// step (§2.3.3, Eq. (30)).  M is evaluated in FP32 against a certified
+// error band and re-evaluated in FP64 inside it, so the flags equal those of
+// an exact FP64 evaluation.
+#pragma once
+
+#include "lbm_internal.cuh"
+
+namespace lbmmb {
+
+__device__ __forceinline__ void quat_rot(const double q[4], const double v[3], double r[3]) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double R00 = 1 - 2 * (y * y + z * z), R01 = 2 * (x * y - w * z), R02 = 2 * (x * z + w * y);
+    const double R10 = 2 * (x * y + w * z), R11 = 1 - 2 * (x * x + z * z), R12 = 2 * (y * z - w * x);
+    const double R20 = 2 * (x * z - w * y), R21 = 2 * (y * z + w * x), R22 = 1 - 2 * (x * x + y * y);
+    r[0] = R00 * v[0] + R01 * v[1] + R02 * v[2];
+    r[1] = R10 * v[0] + R11 * v[1] + R12 * v[2];
+    r[2] = R20 * v[0] + R21 * v[1] + R22 * v[2];
+}
+
+template <typename C>
+__device__ __forceinline__ C feq_i(int ex, int ey, int ez, C w, C rho, C ux, C uy, C uz) {
+    const C eu = ex * ux + ey * uy + ez * uz;
+    const C uu = ux * ux + uy * uy + uz * uz;
+    return w * rho * (C(1) + C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu);
+}
+
+template <typename S, int Q>
+__global__ void __launch_bounds__(BRICK) k_flags(Params P) {
+    using L = Lat<Q>;
+    using Cd = Codec<S>;
+    using C = typename Cd::C;
+    constexpr bool kF64 = sizeof(C) == 8;
+    const int b = blockIdx.x;
+    const int tid = threadIdx.x;
+    __shared__ SmemParticles sp;
+    __shared__ int s_cnt;
+
+    int cnt = P.bcount[b];
+    if (cnt > MAXPB) cnt = MAXPB;
+    const bool need = cnt > 0 || P.occ_new[b] || P.occ_old[b];
+    if (!need) return;  // uniform: nothing solid here now, before, or in this buffer
+    if (tid == 0) {
+        // ascending particle order makes the list, and hence every sum over
+        // it, independent of the scatter's atomic order
+        int ids[MAXPB];
+        for (int s = 0; s < cnt; s++) ids[s] = P.blist[b * MAXPB + s];
+        for (int s = 1; s < cnt; s++) {
+            int v = ids[s], k = s - 1;
+            while (k >= 0 && ids[k] > v) { ids[k + 1] = ids[k]; k--; }
+            ids[k + 1] = v;
+        }
+        for (int s = 0; s < cnt; s++) P.blist[b * MAXPB + s] = ids[s];
+        P.bcount[b] = cnt;
+        s_cnt = cnt;
+    }
+    __syncthreads();
+    int bxi, byi, bzi;
+    brick_coords(P, b, bxi, byi, bzi);
+    const int bx0 = bxi * BX, by0 = byi * BY, bz0 = bzi * BZ;
+    if (cnt > 0) load_smem_particles(P, sp, b, bx0, by0, bz0);
+
+    const int lx = tid % BX, ly = (tid / BX) % BY, lz = tid / (BX * BY);
+    const int x = bx0 + lx, y = by0 + ly, z = bz0 + lz;
+    const bool active = x < P.nx && y < P.ny && z < P.nz;
+    const long long n = (long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z);
+
+    int own = -1;
+    if (active && cnt > 0) {
+        int ncand = 0;
+        int cand[MAXPB];
+        double m64[MAXPB];
+        float m32[MAXPB];
+        for (int s = 0; s < cnt; s++) {
+            bool unsure;
+            const float M = metaball32(P, sp, s, (float)lx, (float)ly, (float)lz, unsure);
+            bool inside;
+            double Md = (double)M;
+            if (kF64 || unsure) {
+                Md = metaball64(P, P.parts[sp.id[s]], (double)x, (double)y, (double)z);
+                inside = Md >= P.c0;
+            } else {
+                inside = M >= (float)P.c0;
+            }
+            if (inside) {
+                cand[ncand] = s;
+                m32[ncand] = M;
+                m64[ncand] = (kF64 || unsure) ? Md : -1.0;
+                ncand++;
+            }
+        }
+        if (ncand == 1) {
+            own = sp.id[cand[0]];
+        } else if (ncand > 1) {
+            // several particles cover the node: decide the largest M in FP64
+            double best = 0.0;
+            for (int c = 0; c < ncand; c++) {
+                const int s = cand[c];
+                double M = m64[c] >= 0.0 ? m64[c]
+                                         : metaball64(P, P.parts[sp.id[s]], (double)x, (double)y, (double)z);
+                (void)m32;
+                if (own < 0 || M > best) {
+                    own = sp.id[s];
+                    best = M;
+                }
+            }
+        }
+    }
+    const uint16_t fl = own >= 0 ? (uint16_t)(own + 1) : (uint16_t)0;
+    if (active) P.flag_new[n] = fl;
+    const int any_solid = __syncthreads_or(fl != 0);
+    if (tid == 0) P.occ_new[b] = (uint8_t)(any_solid != 0);
+
+    // Local refilling, §2.3.3.  Reading: f_i' at x_new is "known after
+    // streaming" when it streams in from x_new + e_i and that node was a fluid
+    // node of the previous step; then f_i = f_i'(x_new+e_i) + 6 w_i rho0
+    // e_i.u_w, else f_i = f^eq_i(rho0, u_new); u_w = u_new is the surface
+    // velocity at x_new of the particle that uncovered it.  The values become
+    // the node's post-collision populations.
+    if (active && fl == 0) {
+        const uint16_t old = P.flag_old[n];
+        if (old != 0) {
+            const DevParticle &pj = P.parts[old - 1];
+            double r[3] = {minimg_d(P, 0, (double)x - pj.x[0]), minimg_d(P, 1, (double)y - pj.x[1]),
+                           minimg_d(P, 2, (double)z - pj.x[2])};
+            const C ux = (C)(pj.v[0] + pj.w[1] * r[2] - pj.w[2] * r[1]);
+            const C uy = (C)(pj.v[1] + pj.w[2] * r[0] - pj.w[0] * r[2]);
+            const C uz = (C)(pj.v[2] + pj.w[0] * r[1] - pj.w[1] * r[0]);
+            const C rho0 = (C)P.rho0;
+            S *A = (S *)P.fA;
+            const long long N = P.N;
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+                int sx = x + ex, sy = y + ey, sz = z + ez;
+                bool in = true;
+                if (sx < 0 || sx >= P.nx) { if (P.per[0]) sx = (sx + P.nx) % P.nx; else in = false; }
+                if (sy < 0 || sy >= P.ny) { if (P.per[1]) sy = (sy + P.ny) % P.ny; else in = false; }
+                if (sz < 0 || sz >= P.nz) { if (P.per[2]) sz = (sz + P.nz) % P.nz; else in = false; }
+                const C w = (C)L::w(i);
+                C f;
+                const long long nb = (long long)sx + (long long)P.nx * ((long long)sy + (long long)P.ny * sz);
+                if (i != 0 && in && P.flag_old[nb] == 0) {
+                    const int io = L::opp(i);
+                    f = Cd::ld_plain(A + (long long)io * N + nb, w, rho0) +
+                        C(6) * w * rho0 * (ex * ux + ey * uy + ez * uz);
+                } else {
+                    f = feq_i<C>(ex, ey, ez, w, rho0, ux, uy, uz);
+                }
+                Cd::st(A + (long long)i * N + n, f, w, rho0);
+            }
+            atomicAdd(&P.counters[CNT_NREFILL], 1);
+        }
+    }
+}
+
+// Every node to f^eq(rho0, u0).
+template <typename S, int Q>
+__global__ void k_init(Params P, S *f) {
+    using L = Lat<Q>;
+    using C = typename Codec<S>::C;
+    const C rho0 = (C)P.rho0, ux = (C)P.u0[0], uy = (C)P.u0[1], uz = (C)P.u0[2];
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < P.N; n += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const C w = (C)L::w(i);
+            Codec<S>::st(f + (long long)i * P.N + n, feq_i<C>(L::e(i, 0), L::e(i, 1), L::e(i, 2), w, rho0, ux, uy, uz),
+                         w, rho0);
+        }
+    }
+}
+
+// Stored populations -> FP64 [Q][N] (and back).
+template <typename S, int Q>
+__global__ void k_get_pop(Params P, const S *f, double *out) {
+    using L = Lat<Q>;
+    using C = typename Codec<S>::C;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < P.N; n += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < Q; i++)
+            out[(long long)i * P.N + n] =
+                (double)Codec<S>::ld_plain(f + (long long)i * P.N + n, (C)L::w(i), (C)P.rho0);
+    }
+}
+template <typename S, int Q>
+__global__ void k_set_pop(Params P, S *f, const double *in) {
+    using L = Lat<Q>;
+    using C = typename Codec<S>::C;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < P.N; n += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < Q; i++)
+            Codec<S>::st(f + (long long)i * P.N + n, (C)in[(long long)i * P.N + n], (C)L::w(i), (C)P.rho0);
+    }
+}
+
+// Macroscopic fields of the stored populations: rho = sum f, u = (sum f e -
+// F/2)/rho (the velocity of the collision that produced them).
+template <typename S, int Q>
+__global__ void k_fields(Params P, const S *f, const uint16_t *flags, double *rho, double *u, uint16_t *fl_out) {
+    using L = Lat<Q>;
+    using C = typename Codec<S>::C;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < P.N; n += (long long)gridDim.x * blockDim.x) {
+        const uint16_t fl = flags[n];
+        if (fl_out) fl_out[n] = fl;
+        double r = 0, mx = 0, my = 0, mz = 0;
+        if (fl == 0) {
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                const double fi = (double)Codec<S>::ld_plain(f + (long long)i * P.N + n, (C)L::w(i), (C)P.rho0);
+                r += fi;
+                mx += fi * L::e(i, 0);
+                my += fi * L::e(i, 1);
+                mz += fi * L::e(i, 2);
+            }
+        }
+        if (rho) rho[n] = r;
+        if (u) {
+            const bool ok = fl == 0;
+            u[n] = ok ? (mx - 0.5 * P.F[0]) / r : 0.0;
+            u[P.N + n] = ok ? (my - 0.5 * P.F[1]) / r : 0.0;
+            u[2 * P.N + n] = ok ? (mz - 0.5 * P.F[2]) / r : 0.0;
+        }
+    }
+}
+
+// Health scan: non-finite populations or |u| > 0.5 at a fluid node.
+template <typename S, int Q>
+__global__ void k_check(Params P, const S *f, const uint16_t *flags) {
+    using L = Lat<Q>;
+    using C = typename Codec<S>::C;
+    bool bad = false;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < P.N; n += (long long)gridDim.x * blockDim.x) {
+        if (flags[n] != 0) continue;
+        float r = 0, mx = 0, my = 0, mz = 0;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const float fi = (float)Codec<S>::ld_plain(f + (long long)i * P.N + n, (C)L::w(i), (C)P.rho0);
+            r += fi;
+            mx += fi * L::e(i, 0);
+            my += fi * L::e(i, 1);
+            mz += fi * L::e(i, 2);
+        }
+        const float u2 = (mx * mx + my * my + mz * mz) / (r * r);
+        if (!(r > 0.f) || !isfinite(r) || !(u2 <= 0.25f)) bad = true;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&P.status[ST_ERR], ERRB_DIVERGED);
+}
+
+}  // namespace lbmmb

@@ -1,0 +1,456 @@
+// The fused lattice sweep (one CTA per 32x4x2 brick, one node per thread).
+//
+// For every fluid node x (flags of this step):
+//   pull    f_i(x, t+1) = f+_i(x - e_i, t) from the read array (§2.2, Eq. (14));
+//   walls   a source beyond a non-periodic face: halfway bounce-back
+//           f_i = f+_i'(x) (resting wall);
+//   links   a source inside particle j: the unknown by VIBB, Eqs. (19)-(25),
+//           with q from Eq. (27), or halfway bounce-back with the moving-wall
+//           term when x - d is not a fluid node (§2.3.5 item 1); the
+//           Galilean-invariant momentum exchange of Eqs. (28)-(29) goes to
+//           particle j;
+//   collide rho, u (Eq. (18) with the half-force shift), BGK toward f^eq
+//           (Eqs. (15)-(16)) plus Guo's forcing term; store to the write array.
+// For every solid node the missing force points of §2.3.5 item 2 (Eqs.
+// (31)-(32)) are added to the particles whose surface its links cross.
+//
+// Bricks with no particle in their list take the plain path: 19 coalesced
+// loads and 19 coalesced stores per node, no flag reads.  Per-link force and
+// torque terms are accumulated per listed particle, reduced across the CTA in
+// a fixed order (warp butterfly, then warps in order) and written as FP64
+// partials per (brick, particle); k_force_reduce sums them in brick order.
+#pragma once
+
+#include "k_flags.cuh"
+
+namespace lbmmb {
+
+template <typename C>
+__device__ __forceinline__ C warp_sum(C v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Listed slot of particle id (the list is short and ascending).
+__device__ __forceinline__ int slot_of(const SmemParticles &sp, int id) {
+    for (int s = 0; s < sp.n; s++)
+        if (sp.id[s] == id) return s;
+    return -1;
+}
+
+// Whether world node (x,y,z) + brick offset lies inside listed particle s,
+// decided exactly: FP32 outside the error band, FP64 inside it.  Mval gets a
+// value of M (FP32 or FP64) usable for q.
+template <bool kF64>
+__device__ __forceinline__ bool inside_exact(const Params &P, const SmemParticles &sp, int s, int lx, int ly, int lz,
+                                             int bx0, int by0, int bz0, double &Mval) {
+    if (!kF64) {
+        bool unsure;
+        const float M = metaball32(P, sp, s, (float)lx, (float)ly, (float)lz, unsure);
+        if (!unsure) {
+            Mval = M;
+            return M >= (float)P.c0;
+        }
+    }
+    const double M = metaball64(P, P.parts[sp.id[s]], (double)(bx0 + lx), (double)(by0 + ly), (double)(bz0 + lz));
+    Mval = M;
+    return M >= P.c0;
+}
+
+// M value for the link fraction (no exactness needed beyond the working
+// precision).
+template <bool kF64>
+__device__ __forceinline__ double m_value(const Params &P, const SmemParticles &sp, int s, int lx, int ly, int lz,
+                                          int bx0, int by0, int bz0) {
+    if (!kF64) {
+        bool unsure;
+        return (double)metaball32(P, sp, s, (float)lx, (float)ly, (float)lz, unsure);
+    }
+    return metaball64(P, P.parts[sp.id[s]], (double)(bx0 + lx), (double)(by0 + ly), (double)(bz0 + lz));
+}
+
+// Lever arm from particle s's centroid to the brick-local point p (minimum
+// image), in the working precision.
+template <typename C>
+__device__ __forceinline__ void lever(const Params &P, const SmemParticles &sp, int s, int bx0, int by0, int bz0,
+                                      C px, C py, C pz, C r[3]) {
+    if (sizeof(C) == 8) {
+        const DevParticle &p = P.parts[sp.id[s]];
+        r[0] = (C)minimg_d(P, 0, bx0 + (double)px - p.x[0]);
+        r[1] = (C)minimg_d(P, 1, by0 + (double)py - p.x[1]);
+        r[2] = (C)minimg_d(P, 2, bz0 + (double)pz - p.x[2]);
+        return;
+    }
+    C d[3] = {px - (C)sp.prel[s][0], py - (C)sp.prel[s][1], pz - (C)sp.prel[s][2]};
+    const int Ls[3] = {P.nx, P.ny, P.nz};
+    for (int a = 0; a < 3; a++) {
+        if (P.per[a]) {
+            const C L = (C)Ls[a];
+            if (d[a] > C(0.5) * L) d[a] -= L;
+            else if (d[a] < C(-0.5) * L) d[a] += L;
+        }
+        r[a] = d[a];
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ void particle_velocity(const Params &P, const SmemParticles &sp, int s, const C r[3],
+                                                  C uw[3]) {
+    C v[3], w[3];
+    if (sizeof(C) == 8) {
+        const DevParticle &p = P.parts[sp.id[s]];
+        for (int a = 0; a < 3; a++) { v[a] = (C)p.v[a]; w[a] = (C)p.w[a]; }
+    } else {
+        for (int a = 0; a < 3; a++) { v[a] = (C)sp.v[s][a]; w[a] = (C)sp.w[s][a]; }
+    }
+    uw[0] = v[0] + w[1] * r[2] - w[2] * r[1];
+    uw[1] = v[1] + w[2] * r[0] - w[0] * r[2];
+    uw[2] = v[2] + w[0] * r[1] - w[1] * r[0];
+}
+
+template <typename C>
+__device__ __forceinline__ void add_term(C (*acc)[6], int s, const C dP[3], const C r[3]) {
+    acc[s][0] += dP[0];
+    acc[s][1] += dP[1];
+    acc[s][2] += dP[2];
+    acc[s][3] += r[1] * dP[2] - r[2] * dP[1];
+    acc[s][4] += r[2] * dP[0] - r[0] * dP[2];
+    acc[s][5] += r[0] * dP[1] - r[1] * dP[0];
+}
+
+// The unknown population of one particle link (direction i arrives at x from
+// the solid node x + d, d = -e_i) and its momentum-exchange term.
+template <typename S, int Q>
+__device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, const SmemParticles &sp, int i, int x,
+                                                          int y, int z, int lx, int ly, int lz, int bx0, int by0,
+                                                          int bz0, long long ns_solid,
+                                                          const typename Codec<S>::C *fown,
+                                                          typename Codec<S>::C rho_f,
+                                                          const typename Codec<S>::C *u_f,
+                                                          typename Codec<S>::C (*acc)[6]) {
+    using L = Lat<Q>;
+    using Cd = Codec<S>;
+    using C = typename Cd::C;
+    constexpr bool kF64 = sizeof(C) == 8;
+    const int io = L::opp(i);
+    const int dx = L::e(io, 0), dy = L::e(io, 1), dz = L::e(io, 2);  // d, into the solid
+    const int j = (int)P.flag_new[ns_solid] - 1;
+    const int s = slot_of(sp, j);
+    const C w_io = (C)L::w(io);
+    const C rho0 = (C)P.rho0;
+    const S *A = (const S *)P.fA;
+    const long long N = P.N;
+    if (s < 0) {  // cannot happen for a consistent brick list; bounce back plainly
+        atomicOr(&P.status[ST_ERR], ERRB_BRICK_OVERFLOW);
+        return fown[io];
+    }
+    // q by Eq. (27), clamped to [0,1] (rounding can push it past the ends)
+    const double Mf = m_value<kF64>(P, sp, s, lx, ly, lz, bx0, by0, bz0);
+    const double Ms = m_value<kF64>(P, sp, s, lx + dx, ly + dy, lz + dz, bx0, by0, bz0);
+    C q = (C)((P.c0 - Mf) / (Ms - Mf));
+    q = q < C(0) ? C(0) : (q > C(1) ? C(1) : q);
+    C r[3], uw[3];
+    lever<C>(P, sp, s, bx0, by0, bz0, (C)lx + q * dx, (C)ly + q * dy, (C)lz + q * dz, r);
+    particle_velocity<C>(P, sp, s, r, uw);
+    const C eu_w = -(dx * uw[0] + dy * uw[1] + dz * uw[2]);  // e_i . u_w with e_i = -d
+    // second fluid node x_ff = x - d
+    int fx = x - dx, fy = y - dy, fz = z - dz;
+    bool ff_ok = true;
+    if (fx < 0 || fx >= P.nx) { if (P.per[0]) fx = (fx + P.nx) % P.nx; else ff_ok = false; }
+    if (fy < 0 || fy >= P.ny) { if (P.per[1]) fy = (fy + P.ny) % P.ny; else ff_ok = false; }
+    if (fz < 0 || fz >= P.nz) { if (P.per[2]) fz = (fz + P.nz) % P.nz; else ff_ok = false; }
+    const long long nff = (long long)fx + (long long)P.nx * ((long long)fy + (long long)P.ny * fz);
+    if (ff_ok) ff_ok = P.flag_new[nff] == 0;
+    C fin;
+    if (!P.vibb || !ff_ok) {
+        fin = fown[io] + C(6) * w_io * rho_f * eu_w;
+    } else {
+        C rho_ff = 0, m_ff[3] = {0, 0, 0}, fff_io = 0;
+#pragma unroll
+        for (int k = 0; k < Q; k++) {
+            const C fk = Cd::ld(A + (long long)k * N + nff, (C)L::w(k), rho0);
+            rho_ff += fk;
+            m_ff[0] += fk * L::e(k, 0);
+            m_ff[1] += fk * L::e(k, 1);
+            m_ff[2] += fk * L::e(k, 2);
+            if (k == io) fff_io = fk;
+        }
+        C u_ff[3];
+        for (int a = 0; a < 3; a++) u_ff[a] = (m_ff[a] - C(0.5) * (C)P.F[a]) / rho_ff;
+        const C feq_f = feq_i<C>(dx, dy, dz, w_io, rho_f, u_f[0], u_f[1], u_f[2]);
+        const C feq_ff = feq_i<C>(dx, dy, dz, w_io, rho_ff, u_ff[0], u_ff[1], u_ff[2]);
+        // Eq. (21): non-equilibrium part, interpolated (q <= 1/2) or
+        // extrapolated (q > 1/2) from x_f and x_ff
+        const C fneq_d = C(2) * q * (fown[io] - feq_f) + (C(1) - C(2) * q) * (fff_io - feq_ff);
+        C rho_d, us[3], uss[3], ud[3];
+        if (q <= C(0.5)) {  // Eqs. (22)-(23), first branches
+            rho_d = C(2) * q * rho_f + (C(1) - C(2) * q) * rho_ff;
+            for (int a = 0; a < 3; a++) us[a] = C(2) * q * u_f[a] + (C(1) - C(2) * q) * u_ff[a];
+        } else {            // second branches
+            rho_d = rho_f;
+            for (int a = 0; a < 3; a++) us[a] = (C(1) - q) / q * u_f[a] + (C(2) * q - C(1)) / q * uw[a];
+        }
+        for (int a = 0; a < 3; a++) uss[a] = (C(1) - q) / (C(1) + q) * u_ff[a] + C(2) * q / (C(1) + q) * uw[a];  // (24)
+        for (int a = 0; a < 3; a++) ud[a] = us[a] / C(3) + C(2) * uss[a] / C(3);                                 // (25)
+        const C fplus_d = feq_i<C>(dx, dy, dz, w_io, rho_d, ud[0], ud[1], ud[2]) + fneq_d;                       // (20)
+        fin = fplus_d + C(6) * w_io * rho_f * eu_w;                                                              // (19)
+    }
+    // Eq. (28): (e_i' - u_w) f+_i'(x,t) - (e_i - u_w) f_i(x,t+1), e_i' = d
+    C dP[3];
+    dP[0] = (C(dx) - uw[0]) * fown[io] - (C(-dx) - uw[0]) * fin;
+    dP[1] = (C(dy) - uw[1]) * fown[io] - (C(-dy) - uw[1]) * fin;
+    dP[2] = (C(dz) - uw[2]) * fown[io] - (C(-dz) - uw[2]) * fin;
+    add_term<C>(acc, s, dP, r);
+    return fin;
+}
+
+// Missing force points at a solid node (§2.3.5 item 2).  Reading: a link
+// y -> x_s = y + d crossing particle j's surface (M_j(y) < c0 <= M_j(x_s))
+// is seen by Eq. (28) when y is a fluid node and x_s is owned by j; every
+// other crossing link (y covered by another particle or beyond a wall, or
+// x_s inside j but owned by another particle) is a missing force point and
+// gets Eqs. (31)-(32) with f^eq(rho0, u_w).
+template <typename S, int Q>
+__device__ __noinline__ void solid_node(const Params &P, const SmemParticles &sp, int x, int y, int z, int lx, int ly,
+                                        int lz, int bx0, int by0, int bz0, int owner,
+                                        typename Codec<S>::C (*acc)[6]) {
+    using L = Lat<Q>;
+    using C = typename Codec<S>::C;
+    constexpr bool kF64 = sizeof(C) == 8;
+    const C rho0 = (C)P.rho0;
+    for (int s = 0; s < sp.n; s++) {
+        const int j = sp.id[s];
+        double Ms;
+        if (j == owner) {
+            Ms = m_value<kF64>(P, sp, s, lx, ly, lz, bx0, by0, bz0);
+        } else if (!inside_exact<kF64>(P, sp, s, lx, ly, lz, bx0, by0, bz0, Ms)) {
+            continue;
+        }
+        for (int i = 1; i < Q; i++) {
+            const int dx = L::e(i, 0), dy = L::e(i, 1), dz = L::e(i, 2);
+            int yx = x - dx, yy = y - dy, yz = z - dz;
+            bool in = true;
+            if (yx < 0 || yx >= P.nx) { if (P.per[0]) yx = (yx + P.nx) % P.nx; else in = false; }
+            if (yy < 0 || yy >= P.ny) { if (P.per[1]) yy = (yy + P.ny) % P.ny; else in = false; }
+            if (yz < 0 || yz >= P.nz) { if (P.per[2]) yz = (yz + P.nz) % P.nz; else in = false; }
+            if (in) {
+                const uint16_t fy = P.flag_new[(long long)yx + (long long)P.nx * ((long long)yy + (long long)P.ny * yz)];
+                if (fy == 0 && j == owner) continue;  // an ordinary link of j
+                if (fy == (uint16_t)(j + 1)) continue;  // interior of j
+            }
+            double My;
+            if (inside_exact<kF64>(P, sp, s, lx - dx, ly - dy, lz - dz, bx0, by0, bz0, My)) continue;
+            C q = (C)((P.c0 - My) / (Ms - My));
+            q = q < C(0) ? C(0) : (q > C(1) ? C(1) : q);
+            C r[3], uw[3];
+            lever<C>(P, sp, s, bx0, by0, bz0, (C)(lx - dx) + q * dx, (C)(ly - dy) + q * dy, (C)(lz - dz) + q * dz, r);
+            particle_velocity<C>(P, sp, s, r, uw);
+            const int io = L::opp(i);
+            const C fi = feq_i<C>(dx, dy, dz, (C)L::w(i), rho0, uw[0], uw[1], uw[2]);
+            const C fo = feq_i<C>(-dx, -dy, -dz, (C)L::w(io), rho0, uw[0], uw[1], uw[2]);
+            C dP[3];
+            dP[0] = (C(dx) - uw[0]) * fi - (C(-dx) - uw[0]) * fo;
+            dP[1] = (C(dy) - uw[1]) * fi - (C(-dy) - uw[1]) * fo;
+            dP[2] = (C(dz) - uw[2]) * fi - (C(-dz) - uw[2]) * fo;
+            add_term<C>(acc, s, dP, r);
+        }
+    }
+}
+
+// Collide one node and store it: moments (Eq. (18)) with the half-force
+// shift, BGK toward f^eq (Eqs. (15)-(16)) plus Guo's forcing term.
+template <typename S, int Q>
+__device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>::C (&fin)[Q], S *B, long long N,
+                                              long long n) {
+    using L = Lat<Q>;
+    using Cd = Codec<S>;
+    using C = typename Cd::C;
+    const C rho0 = (C)P.rho0;
+    C rho = 0, mx = 0, my = 0, mz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        rho += fin[i];
+        mx += fin[i] * L::e(i, 0);
+        my += fin[i] * L::e(i, 1);
+        mz += fin[i] * L::e(i, 2);
+    }
+    const C Fx = (C)P.F[0], Fy = (C)P.F[1], Fz = (C)P.F[2];
+    const C inv_rho = C(1) / rho;
+    const C ux = (mx + C(0.5) * Fx) * inv_rho, uy = (my + C(0.5) * Fy) * inv_rho, uz = (mz + C(0.5) * Fz) * inv_rho;
+    const C omega = (C)(1.0 / P.tau);
+    const C gfac = (C)(1.0 - 0.5 / P.tau);
+    const C uu = ux * ux + uy * uy + uz * uz;
+    const C uF = ux * Fx + uy * Fy + uz * Fz;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+        const C w = (C)L::w(i);
+        const C eu = ex * ux + ey * uy + ez * uz;
+        const C feq = w * rho * (C(1) + C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu);
+        const C eF = ex * Fx + ey * Fy + ez * Fz;
+        const C Si = gfac * w * (C(3) * (eF - uF) + C(9) * eu * eF);
+        Cd::st(B + (long long)i * N + n, fin[i] + omega * (feq - fin[i]) + Si, w, rho0);
+    }
+}
+
+// Neighbour coordinates of a node along each axis (index 0: -1, 1: 0, 2: +1),
+// wrapped on periodic axes, -1 beyond a wall.
+__device__ __forceinline__ void neighbour_coords(const Params &P, int x, int y, int z, int xs[3], int ys[3], int zs[3]) {
+    xs[1] = x; ys[1] = y; zs[1] = z;
+    xs[0] = x - 1; xs[2] = x + 1; ys[0] = y - 1; ys[2] = y + 1; zs[0] = z - 1; zs[2] = z + 1;
+    if (xs[0] < 0) xs[0] = P.per[0] ? P.nx - 1 : -1;
+    if (xs[2] >= P.nx) xs[2] = P.per[0] ? 0 : -1;
+    if (ys[0] < 0) ys[0] = P.per[1] ? P.ny - 1 : -1;
+    if (ys[2] >= P.ny) ys[2] = P.per[1] ? 0 : -1;
+    if (zs[0] < 0) zs[0] = P.per[2] ? P.nz - 1 : -1;
+    if (zs[2] >= P.nz) zs[2] = P.per[2] ? 0 : -1;
+}
+
+// A node of a brick no particle reaches: pull, halfway bounce-back at walls
+// (the node's own outgoing population), collide.  No flags are read.
+template <typename S, int Q>
+__device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z, long long n) {
+    using L = Lat<Q>;
+    using Cd = Codec<S>;
+    using C = typename Cd::C;
+    const S *A = (const S *)P.fA;
+    S *B = (S *)P.fB;
+    const long long N = P.N;
+    const C rho0 = (C)P.rho0;
+    int xs[3], ys[3], zs[3];
+    neighbour_coords(P, x, y, z, xs, ys, zs);
+    C fin[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
+        const long long src = ((sx | sy | sz) < 0)
+                                  ? (long long)L::opp(i) * N + n  // wall: f_i = f+_i'(x)
+                                  : (long long)i * N + (long long)sx + (long long)P.nx * ((long long)sy + (long long)P.ny * sz);
+        fin[i] = Cd::ld(A + src, (C)L::w(((sx | sy | sz) < 0) ? L::opp(i) : i), rho0);
+    }
+    collide_store<S, Q>(P, fin, B, N, n);
+}
+
+// Bricks some particle reaches: flags, particle links, missing force points
+// and the deterministic reduction of the per-particle terms.
+template <typename S, int Q>
+__device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, double (*red)[6], int *s_links, int b,
+                                        int bx0, int by0, int bz0, int cnt) {
+    using L = Lat<Q>;
+    using Cd = Codec<S>;
+    using C = typename Cd::C;
+    const int tid = threadIdx.x;
+    const int lx = tid % BX, ly = (tid / BX) % BY, lz = tid / (BX * BY);
+    const int x = bx0 + lx, y = by0 + ly, z = bz0 + lz;
+    const bool active = x < P.nx && y < P.ny && z < P.nz;
+    const long long N = P.N;
+    const long long n = (long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z);
+    const S *A = (const S *)P.fA;
+    S *B = (S *)P.fB;
+    const C rho0 = (C)P.rho0;
+
+    C acc[MAXPB][6];
+    for (int s = 0; s < cnt; s++)
+        for (int c = 0; c < 6; c++) acc[s][c] = 0;
+    int nlinks = 0;
+
+    if (active) {
+        const uint16_t fl = P.flag_new[n];
+        if (fl != 0) {
+            if (P.missing_force) solid_node<S, Q>(P, sp, x, y, z, lx, ly, lz, bx0, by0, bz0, fl - 1, acc);
+        } else {
+            int xs[3], ys[3], zs[3];
+            neighbour_coords(P, x, y, z, xs, ys, zs);
+            C fin[Q];
+            uint32_t wallmask = 0, linkmask = 0;
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
+                if ((sx | sy | sz) < 0) {
+                    wallmask |= 1u << i;
+                    fin[i] = 0;
+                } else {
+                    const long long src = (long long)sx + (long long)P.nx * ((long long)sy + (long long)P.ny * sz);
+                    fin[i] = Cd::ld(A + (long long)i * N + src, (C)L::w(i), rho0);
+                    if (P.flag_new[src] != 0) linkmask |= 1u << i;
+                }
+            }
+            if (wallmask | linkmask) {
+                C fown[Q];
+                C rho_f = 0, m_f[3] = {0, 0, 0};
+#pragma unroll
+                for (int k = 0; k < Q; k++) {
+                    fown[k] = Cd::ld(A + (long long)k * N + n, (C)L::w(k), rho0);
+                    rho_f += fown[k];
+                    m_f[0] += fown[k] * L::e(k, 0);
+                    m_f[1] += fown[k] * L::e(k, 1);
+                    m_f[2] += fown[k] * L::e(k, 2);
+                }
+                C u_f[3];
+                for (int a = 0; a < 3; a++) u_f[a] = (m_f[a] - C(0.5) * (C)P.F[a]) / rho_f;
+#pragma unroll
+                for (int i = 1; i < Q; i++) {
+                    if (wallmask & (1u << i)) {
+                        fin[i] = fown[L::opp(i)];
+                    } else if (linkmask & (1u << i)) {
+                        const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
+                        const long long src =
+                            (long long)sx + (long long)P.nx * ((long long)sy + (long long)P.ny * sz);
+                        fin[i] = particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, src, fown, rho_f,
+                                                     u_f, acc);
+                        nlinks++;
+                    }
+                }
+            }
+            collide_store<S, Q>(P, fin, B, N, n);
+        }
+    }
+
+    {
+        // deterministic CTA reduction of the per-particle terms
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int s = 0; s < cnt; s++) {
+            for (int c = 0; c < 6; c++) {
+                C v = acc[s][c];
+                v = warp_sum<C>(v);
+                if (lane == 0) red[warp][c] = (double)v;
+            }
+            __syncthreads();
+            if (tid < 6) {
+                double t = 0.0;
+                for (int w = 0; w < BRICK / 32; w++) t += red[w][tid];
+                P.partial[((long long)b * MAXPB + s) * 6 + tid] = t;
+            }
+            __syncthreads();
+        }
+        const int nl = __reduce_add_sync(0xffffffffu, (unsigned)nlinks);
+        if (lane == 0 && nl) atomicAdd(s_links, nl);
+        __syncthreads();
+        if (tid == 0 && *s_links) atomicAdd(&P.counters[CNT_NLINKS], *s_links);
+    }
+}
+
+template <typename S, int Q>
+__global__ void __launch_bounds__(BRICK, 3) k_sweep(Params P) {
+    __shared__ SmemParticles sp;
+    __shared__ double red[BRICK / 32][6];
+    __shared__ int s_links;
+    const int b = blockIdx.x;
+    const int tid = threadIdx.x;
+    int bxi, byi, bzi;
+    brick_coords(P, b, bxi, byi, bzi);
+    const int bx0 = bxi * BX, by0 = byi * BY, bz0 = bzi * BZ;
+    const int cnt = min(P.bcount[b], MAXPB);  // uniform over the CTA
+    if (cnt == 0) {
+        const int x = bx0 + tid % BX, y = by0 + (tid / BX) % BY, z = bz0 + tid / (BX * BY);
+        if (x < P.nx && y < P.ny && z < P.nz)
+            plain_node<S, Q>(P, x, y, z, (long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z));
+        return;
+    }
+    if (tid == 0) s_links = 0;
+    load_smem_particles(P, sp, b, bx0, by0, bz0);
+    near_brick<S, Q>(P, sp, red, &s_links, b, bx0, by0, bz0, cnt);
+}
+
+}  // namespace lbmmb

@@ -1,0 +1,58 @@
+// Launch wrappers of the storage-templated kernels; each sweep_<type>.cu
+// instantiates them for one storage type.
+#pragma once
+
+#include "k_sweep.cuh"
+
+namespace lbmmb {
+
+constexpr int kGridStrideBlocks = 152 * 8;
+
+template <typename S>
+void launch_init_t(const Params &P, void *f, cudaStream_t st) {
+    if (P.Q == 19) k_init<S, 19><<<kGridStrideBlocks, 256, 0, st>>>(P, (S *)f);
+    else k_init<S, 15><<<kGridStrideBlocks, 256, 0, st>>>(P, (S *)f);
+}
+template <typename S>
+void launch_flags_t(const Params &P, cudaStream_t st) {
+    if (P.Q == 19) k_flags<S, 19><<<P.nbricks, BRICK, 0, st>>>(P);
+    else k_flags<S, 15><<<P.nbricks, BRICK, 0, st>>>(P);
+}
+template <typename S>
+void launch_sweep_t(const Params &P, cudaStream_t st) {
+    if (P.Q == 19) k_sweep<S, 19><<<P.nbricks, BRICK, 0, st>>>(P);
+    else k_sweep<S, 15><<<P.nbricks, BRICK, 0, st>>>(P);
+}
+template <typename S>
+void launch_fields_t(const Params &P, const void *f, const uint16_t *flags, double *rho, double *u, uint16_t *fl,
+                     cudaStream_t st) {
+    if (P.Q == 19) k_fields<S, 19><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, flags, rho, u, fl);
+    else k_fields<S, 15><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, flags, rho, u, fl);
+}
+template <typename S>
+void launch_get_pop_t(const Params &P, const void *f, double *out, cudaStream_t st) {
+    if (P.Q == 19) k_get_pop<S, 19><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, out);
+    else k_get_pop<S, 15><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, out);
+}
+template <typename S>
+void launch_set_pop_t(const Params &P, void *f, const double *in, cudaStream_t st) {
+    if (P.Q == 19) k_set_pop<S, 19><<<kGridStrideBlocks, 256, 0, st>>>(P, (S *)f, in);
+    else k_set_pop<S, 15><<<kGridStrideBlocks, 256, 0, st>>>(P, (S *)f, in);
+}
+template <typename S>
+void launch_check_t(const Params &P, const void *f, const uint16_t *flags, cudaStream_t st) {
+    if (P.Q == 19) k_check<S, 19><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, flags);
+    else k_check<S, 15><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, flags);
+}
+
+#define LBMMB_INSTANTIATE(S)                                                                                     \
+    template void launch_init_t<S>(const Params &, void *, cudaStream_t);                                        \
+    template void launch_flags_t<S>(const Params &, cudaStream_t);                                               \
+    template void launch_sweep_t<S>(const Params &, cudaStream_t);                                               \
+    template void launch_fields_t<S>(const Params &, const void *, const uint16_t *, double *, double *,         \
+                                     uint16_t *, cudaStream_t);                                                  \
+    template void launch_get_pop_t<S>(const Params &, const void *, double *, cudaStream_t);                     \
+    template void launch_set_pop_t<S>(const Params &, void *, const double *, cudaStream_t);                     \
+    template void launch_check_t<S>(const Params &, const void *, const uint16_t *, cudaStream_t);
+
+}  // namespace lbmmb

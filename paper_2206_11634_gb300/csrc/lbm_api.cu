@@ -1,0 +1,618 @@
+// Host side of the C ABI (include/lbm_metaball.h): configuration checks,
+// workspace layout, particle set-up (mass properties), and the per-step
+// launch sequence.  No device memory is allocated here: every device array
+// lives in the caller's workspace.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+using namespace lbmmb;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t storage_bytes(int s) { return s == LBM_STORE_F64 ? 8 : (s == LBM_STORE_F32 ? 4 : 2); }
+
+// Byte offsets of every array in the workspace.
+struct Layout {
+    size_t f[2], flags[2], occ[2];
+    size_t bin;        // bcount[nbricks] followed by the per-step counters
+    size_t bin_bytes;
+    size_t blist, partial, parts, Fh, Th, Fc, Tc;
+    size_t pairF, pair_on, pair_xi, pair_xm, wall_on, wall_xi, wall_xcw;
+    size_t status;
+    size_t total;
+    long long N;
+    int nbx, nby, nbz, nbricks;
+};
+
+constexpr int kStepCounters = 4;  // nrefill, nlinks, 2 spare
+
+const char *check_config(const lbm_config *c) {
+    if (!c) return "config is NULL";
+    if (c->nx < 2 || c->ny < 2 || c->nz < 2) return "nx, ny, nz must be >= 2";
+    if ((long long)c->nx * c->ny * c->nz > (1LL << 40)) return "lattice too large";
+    if (c->lattice != 19 && c->lattice != 15) return "lattice must be 19 (D3Q19) or 15 (D3Q15)";
+    if (c->storage < LBM_STORE_F64 || c->storage > LBM_STORE_BF16) return "storage must be one of enum lbm_storage";
+    if (!(c->tau > 0.5) || !std::isfinite(c->tau)) return "tau must be > 1/2";
+    if (!(c->rho0 > 0.0)) return "rho0 must be > 0";
+    if (!(c->c0 > 0.0)) return "c0 must be > 0";
+    if (c->max_particles < 1 || c->max_particles > 65534) return "max_particles must be in 1..65534";
+    if (c->n_sub < 0) return "n_sub must be >= 0";
+    for (int a = 0; a < 3; a++)
+        if (c->periodic[a] != 0 && c->periodic[a] != 1) return "periodic[] must be 0 or 1";
+    if (c->mass_spacing < 0.0) return "mass_spacing must be >= 0";
+    return nullptr;
+}
+
+void make_layout(const lbm_config *c, Layout *L) {
+    const long long N = (long long)c->nx * c->ny * c->nz;
+    L->N = N;
+    L->nbx = (c->nx + BX - 1) / BX;
+    L->nby = (c->ny + BY - 1) / BY;
+    L->nbz = (c->nz + BZ - 1) / BZ;
+    L->nbricks = L->nbx * L->nby * L->nbz;
+    const size_t P = (size_t)c->max_particles, nb = (size_t)L->nbricks;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    const size_t fbytes = (size_t)c->lattice * (size_t)N * storage_bytes(c->storage);
+    L->f[0] = take(fbytes);
+    L->f[1] = take(fbytes);
+    L->flags[0] = take((size_t)N * 2);
+    L->flags[1] = take((size_t)N * 2);
+    L->occ[0] = take(nb);
+    L->occ[1] = take(nb);
+    L->bin_bytes = nb * 4 + kStepCounters * 4;
+    L->bin = take(L->bin_bytes);
+    L->blist = take(nb * MAXPB * 4);
+    L->partial = take(nb * MAXPB * 6 * 8);
+    L->parts = take(P * sizeof(DevParticle));
+    L->Fh = take(P * 24);
+    L->Th = take(P * 24);
+    L->Fc = take(P * 24);
+    L->Tc = take(P * 24);
+    L->pairF = take(P * P * 9 * 8);
+    L->pair_on = take(P * P * 4);
+    L->pair_xi = take(P * P * 24);
+    L->pair_xm = take(P * P * 24);
+    L->wall_on = take(P * NWALL * 4);
+    L->wall_xi = take(P * NWALL * 24);
+    L->wall_xcw = take(P * NWALL * 24);
+    L->status = take(ST_SLOTS * 4);
+    L->total = o;
+}
+
+thread_local char g_init_error[256] = "no error";
+
+}  // namespace
+
+constexpr int kProfKernels = 5;
+constexpr int kProfCap = 65536;
+
+struct lbm_handle {
+    lbm_config cfg;
+    // kernel timing (lbm_profile): event pairs per kernel, in launch order
+    bool prof;
+    std::vector<cudaEvent_t> ev[kProfKernels][2];
+    int64_t nrec[kProfKernels];
+    Layout L;
+    char *ws;
+    cudaStream_t stream;
+    int cur;    // populations consistent with flags[fcur] live in f[cur]
+    int fcur;
+    int np;
+    int64_t steps;
+    char err[256];
+};
+
+namespace {
+
+int fail(lbm_handle *h, int code, const char *fmt, ...) {
+    char *buf = h ? h->err : g_init_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_check(lbm_handle *h, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return LBM_OK;
+    return fail(h, LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+template <typename T>
+T *at(lbm_handle *h, size_t off) {
+    return reinterpret_cast<T *>(h->ws + off);
+}
+
+Params make_params(lbm_handle *h) {
+    const lbm_config &c = h->cfg;
+    Params P;
+    std::memset(&P, 0, sizeof(P));
+    P.nx = c.nx; P.ny = c.ny; P.nz = c.nz; P.Q = c.lattice;
+    for (int a = 0; a < 3; a++) P.per[a] = c.periodic[a];
+    P.N = h->L.N;
+    P.nbx = h->L.nbx; P.nby = h->L.nby; P.nbz = h->L.nbz; P.nbricks = h->L.nbricks;
+    P.np = h->np; P.n_sub = c.n_sub; P.vibb = c.vibb; P.missing_force = c.missing_force;
+    P.tau = c.tau; P.rho0 = c.rho0; P.c0 = c.c0;
+    for (int a = 0; a < 3; a++) { P.F[a] = c.force[a]; P.g[a] = c.gravity[a]; P.u0[a] = c.u0[a]; }
+    P.kn = c.kn; P.eta_n = c.eta_n; P.kt = c.kt; P.eta_t = c.eta_t; P.mu_s = c.mu_s; P.c_tol = c.c_tol;
+    P.fA = h->ws + h->L.f[h->cur];
+    P.fB = h->ws + h->L.f[1 - h->cur];
+    P.flag_new = at<uint16_t>(h, h->L.flags[1 - h->fcur]);
+    P.flag_old = at<uint16_t>(h, h->L.flags[h->fcur]);
+    P.occ_new = at<uint8_t>(h, h->L.occ[1 - h->fcur]);
+    P.occ_old = at<uint8_t>(h, h->L.occ[h->fcur]);
+    P.bcount = at<int>(h, h->L.bin);
+    P.blist = at<int>(h, h->L.blist);
+    P.partial = at<double>(h, h->L.partial);
+    P.parts = at<DevParticle>(h, h->L.parts);
+    P.Fh = at<double>(h, h->L.Fh);
+    P.Th = at<double>(h, h->L.Th);
+    P.Fc = at<double>(h, h->L.Fc);
+    P.Tc = at<double>(h, h->L.Tc);
+    P.pairF = at<double>(h, h->L.pairF);
+    P.pair_on = at<int>(h, h->L.pair_on);
+    P.pair_xi = at<double>(h, h->L.pair_xi);
+    P.pair_xm = at<double>(h, h->L.pair_xm);
+    P.wall_on = at<int>(h, h->L.wall_on);
+    P.wall_xi = at<double>(h, h->L.wall_xi);
+    P.wall_xcw = at<double>(h, h->L.wall_xcw);
+    P.status = at<int>(h, h->L.status);
+    P.counters = at<int>(h, h->L.bin + (size_t)h->L.nbricks * 4);
+    return P;
+}
+
+// Parameters of the read-only paths (fields, populations, check): the
+// current populations are f[cur], the current flags flags[fcur].
+Params current_params(lbm_handle *h) {
+    Params P = make_params(h);
+    P.fA = h->ws + h->L.f[h->cur];
+    P.flag_new = at<uint16_t>(h, h->L.flags[h->fcur]);
+    return P;
+}
+
+template <template <typename> class F, typename... A>
+void by_storage(int storage, A &&...args) {
+    switch (storage) {
+        case LBM_STORE_F64: F<double>::run(args...); break;
+        case LBM_STORE_F32: F<float>::run(args...); break;
+        case LBM_STORE_F16: F<__half>::run(args...); break;
+        default: F<__nv_bfloat16>::run(args...); break;
+    }
+}
+template <typename S> struct DoInit { static void run(const Params &P, void *f, cudaStream_t st) { launch_init_t<S>(P, f, st); } };
+template <typename S> struct DoFlags { static void run(const Params &P, cudaStream_t st) { launch_flags_t<S>(P, st); } };
+template <typename S> struct DoSweep { static void run(const Params &P, cudaStream_t st) { launch_sweep_t<S>(P, st); } };
+template <typename S> struct DoFields {
+    static void run(const Params &P, double *rho, double *u, uint16_t *fl, cudaStream_t st) {
+        launch_fields_t<S>(P, P.fA, P.flag_new, rho, u, fl, st);
+    }
+};
+template <typename S> struct DoGetPop { static void run(const Params &P, double *out, cudaStream_t st) { launch_get_pop_t<S>(P, P.fA, out, st); } };
+template <typename S> struct DoSetPop { static void run(const Params &P, const double *in, cudaStream_t st) { launch_set_pop_t<S>(P, P.fA, in, st); } };
+template <typename S> struct DoCheck { static void run(const Params &P, cudaStream_t st) { launch_check_t<S>(P, P.fA, P.flag_new, st); } };
+
+// ---------------------------------------------------------------------------
+// Host particle set-up.
+// ---------------------------------------------------------------------------
+void quat_matrix(const double q[4], double R[9]) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+bool invert3(const double A[9], double B[9]) {
+    const double c0 = A[4] * A[8] - A[5] * A[7];
+    const double c1 = A[5] * A[6] - A[3] * A[8];
+    const double c2 = A[3] * A[7] - A[4] * A[6];
+    const double det = A[0] * c0 + A[1] * c1 + A[2] * c2;
+    if (det == 0.0 || !std::isfinite(det)) return false;
+    const double id = 1.0 / det;
+    B[0] = c0 * id; B[1] = (A[2] * A[7] - A[1] * A[8]) * id; B[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    B[3] = c1 * id; B[4] = (A[0] * A[8] - A[2] * A[6]) * id; B[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    B[6] = c2 * id; B[7] = (A[1] * A[6] - A[0] * A[7]) * id; B[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    return true;
+}
+
+// Volume, centroid and inertia of {M >= c0} by counting cell-centre samples
+// of a grid of spacing hs (each cell adds its own hs^2/12 per axis to the
+// second moments), then the body frame is moved to the centroid.
+bool mass_properties(lbm_particle &p, double c0, double hs) {
+    double B = 0.0, Ks = 0.0;
+    for (int k = 0; k < p.n_cp; k++) {
+        for (int a = 0; a < 3; a++) B = std::fmax(B, std::fabs(p.cp[k][a]));
+        Ks += p.K[k];
+    }
+    B += std::sqrt(Ks / c0);
+    const int n = (int)std::ceil(B / hs);
+    double cnt = 0, s[3] = {0, 0, 0}, S[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = -n; k < n; k++)
+        for (int j = -n; j < n; j++)
+            for (int i = -n; i < n; i++) {
+                const double x = (i + 0.5) * hs, y = (j + 0.5) * hs, z = (k + 0.5) * hs;
+                double M = 0.0;
+                for (int c = 0; c < p.n_cp; c++) {
+                    const double dx = x - p.cp[c][0], dy = y - p.cp[c][1], dz = z - p.cp[c][2];
+                    M += p.K[c] / (dx * dx + dy * dy + dz * dz);
+                }
+                if (M >= c0) {
+                    cnt += 1.0;
+                    s[0] += x; s[1] += y; s[2] += z;
+                    S[0] += x * x; S[1] += y * y; S[2] += z * z;
+                    S[3] += x * y; S[4] += x * z; S[5] += y * z;
+                }
+            }
+    if (cnt == 0.0) return false;
+    const double V = cnt * hs * hs * hs;
+    const double c[3] = {s[0] / cnt, s[1] / cnt, s[2] / cnt};
+    const double cell = hs * hs / 12.0;
+    const double Cxx = S[0] / cnt - c[0] * c[0] + cell, Cyy = S[1] / cnt - c[1] * c[1] + cell,
+                 Czz = S[2] / cnt - c[2] * c[2] + cell;
+    const double Cxy = S[3] / cnt - c[0] * c[1], Cxz = S[4] / cnt - c[0] * c[2], Cyz = S[5] / cnt - c[1] * c[2];
+    const double m = p.density * V;
+    p.mass = m;
+    p.inertia[0] = m * (Cyy + Czz); p.inertia[1] = -m * Cxy;        p.inertia[2] = -m * Cxz;
+    p.inertia[3] = -m * Cxy;        p.inertia[4] = m * (Cxx + Czz); p.inertia[5] = -m * Cyz;
+    p.inertia[6] = -m * Cxz;        p.inertia[7] = -m * Cyz;        p.inertia[8] = m * (Cxx + Cyy);
+    double R[9];
+    quat_matrix(p.q, R);
+    for (int k = 0; k < p.n_cp; k++)
+        for (int a = 0; a < 3; a++) p.cp[k][a] -= c[a];
+    for (int a = 0; a < 3; a++) p.x[a] += R[3 * a] * c[0] + R[3 * a + 1] * c[1] + R[3 * a + 2] * c[2];
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_workspace_size(const lbm_config *cfg, size_t *bytes) {
+    if (const char *m = check_config(cfg)) return fail(nullptr, LBM_ERR_BAD_ARG, "%s", m);
+    if (!bytes) return fail(nullptr, LBM_ERR_BAD_ARG, "bytes is NULL");
+    Layout L;
+    make_layout(cfg, &L);
+    *bytes = L.total;
+    return LBM_OK;
+}
+
+int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_stream, lbm_handle **out) {
+    if (!out) return fail(nullptr, LBM_ERR_BAD_ARG, "out is NULL");
+    *out = nullptr;
+    if (const char *m = check_config(cfg)) return fail(nullptr, LBM_ERR_BAD_ARG, "%s", m);
+    Layout L;
+    make_layout(cfg, &L);
+    if (!dev_ws) return fail(nullptr, LBM_ERR_BAD_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(dev_ws) % kAlign) return fail(nullptr, LBM_ERR_BAD_ARG, "workspace not 256-byte aligned");
+    if (ws_bytes < L.total)
+        return fail(nullptr, LBM_ERR_WS_TOO_SMALL, "workspace of %zu bytes, %zu needed", ws_bytes, L.total);
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, dev_ws) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(nullptr, LBM_ERR_BAD_ARG, "workspace is not device memory");
+    }
+    lbm_handle *h = new (std::nothrow) lbm_handle();
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "out of host memory");
+    h->cfg = *cfg;
+    if (h->cfg.mass_spacing == 0.0) h->cfg.mass_spacing = 0.5;
+    h->L = L;
+    h->ws = static_cast<char *>(dev_ws);
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->cur = 0;
+    h->fcur = 0;
+    h->np = 0;
+    h->steps = 0;
+    h->prof = false;
+    for (int k = 0; k < kProfKernels; k++) h->nrec[k] = 0;
+    std::snprintf(h->err, sizeof(h->err), "no error");
+    // everything but the populations starts at zero: all nodes fluid, no
+    // bricks occupied, no contacts, no errors
+    const size_t zero_from = L.flags[0];
+    int rc = cuda_check(h, cudaMemsetAsync(h->ws + zero_from, 0, L.total - zero_from, h->stream), "cudaMemsetAsync");
+    if (rc == LBM_OK) {
+        Params P = make_params(h);
+        by_storage<DoInit>(h->cfg.storage, P, (void *)(h->ws + L.f[0]), h->stream);
+        by_storage<DoInit>(h->cfg.storage, P, (void *)(h->ws + L.f[1]), h->stream);
+        rc = cuda_check(h, cudaGetLastError(), "init kernel launch");
+    }
+    if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (rc != LBM_OK) {
+        std::snprintf(g_init_error, sizeof(g_init_error), "%s", h->err);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    if (n < 0 || (n > 0 && !host)) return fail(h, LBM_ERR_BAD_ARG, "bad particle array");
+    if (n > h->cfg.max_particles)
+        return fail(h, LBM_ERR_CAPACITY, "%d particles, capacity %d", n, h->cfg.max_particles);
+    std::vector<DevParticle> dev((size_t)(n > 0 ? n : 1));
+    for (int j = 0; j < n; j++) {
+        lbm_particle p = host[j];
+        if (p.n_cp < 1 || p.n_cp > LBM_MAX_CP) return fail(h, LBM_ERR_BAD_ARG, "particle %d: n_cp out of range", j);
+        const double qn = std::sqrt(p.q[0] * p.q[0] + p.q[1] * p.q[1] + p.q[2] * p.q[2] + p.q[3] * p.q[3]);
+        if (!(qn > 0.0)) return fail(h, LBM_ERR_BAD_ARG, "particle %d: zero quaternion", j);
+        for (int a = 0; a < 4; a++) p.q[a] /= qn;
+        for (int k = 0; k < p.n_cp; k++)
+            if (!(p.K[k] >= 0.0)) return fail(h, LBM_ERR_BAD_ARG, "particle %d: negative weight", j);
+        if (!(p.density > 0.0)) return fail(h, LBM_ERR_BAD_ARG, "particle %d: density must be > 0", j);
+        if (p.mass <= 0.0 && !mass_properties(p, h->cfg.c0, h->cfg.mass_spacing))
+            return fail(h, LBM_ERR_BAD_ARG, "particle %d: empty shape", j);
+        DevParticle &d = dev[j];
+        std::memset(&d, 0, sizeof(d));
+        for (int a = 0; a < 3; a++) { d.x[a] = p.x[a]; d.v[a] = p.v[a]; d.w[a] = p.w[a]; }
+        for (int a = 0; a < 4; a++) d.q[a] = p.q[a];
+        d.ncp = p.n_cp;
+        d.fixed = p.fixed != 0;
+        double Ks = 0.0, rmax = 0.0;
+        for (int k = 0; k < p.n_cp; k++) {
+            for (int a = 0; a < 3; a++) d.cpb[k][a] = p.cp[k][a];
+            d.K[k] = p.K[k];
+            Ks += p.K[k];
+            rmax = std::fmax(rmax, std::sqrt(p.cp[k][0] * p.cp[k][0] + p.cp[k][1] * p.cp[k][1] + p.cp[k][2] * p.cp[k][2]));
+        }
+        d.sumK = Ks;
+        d.brad = rmax + std::sqrt(Ks / h->cfg.c0) + p.Rs;
+        d.mass = p.mass;
+        d.density = p.density;
+        d.Rs = p.Rs;
+        for (int a = 0; a < 9; a++) d.I[a] = p.inertia[a];
+        if (!invert3(d.I, d.Iinv)) {
+            if (!d.fixed) return fail(h, LBM_ERR_BAD_ARG, "particle %d: singular inertia", j);
+            for (int a = 0; a < 9; a++) d.Iinv[a] = 0.0;
+        }
+        // world control points and search box (refreshed by every step)
+        double R[9];
+        quat_matrix(d.q, R);
+        for (int a = 0; a < 3; a++) { d.lo[a] = 1e300; d.hi[a] = -1e300; }
+        for (int k = 0; k < d.ncp; k++)
+            for (int a = 0; a < 3; a++) {
+                d.cpw[k][a] = d.x[a] + R[3 * a] * d.cpb[k][0] + R[3 * a + 1] * d.cpb[k][1] + R[3 * a + 2] * d.cpb[k][2];
+                d.lo[a] = std::fmin(d.lo[a], d.cpw[k][a]);
+                d.hi[a] = std::fmax(d.hi[a], d.cpw[k][a]);
+            }
+        for (int a = 0; a < 3; a++) { d.lo[a] -= std::sqrt(Ks / h->cfg.c0); d.hi[a] += std::sqrt(Ks / h->cfg.c0); }
+    }
+    int rc = LBM_OK;
+    if (n > 0)
+        rc = cuda_check(h, cudaMemcpyAsync(h->ws + h->L.parts, dev.data(), sizeof(DevParticle) * (size_t)n,
+                                           cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(particles)");
+    const size_t P = (size_t)h->cfg.max_particles;
+    if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.pair_on, 0, P * P * 4, h->stream), "cudaMemsetAsync");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.wall_on, 0, P * NWALL * 4, h->stream), "cudaMemsetAsync");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.Fh, 0, P * 24, h->stream), "cudaMemsetAsync");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.Th, 0, P * 24, h->stream), "cudaMemsetAsync");
+    // the staging vector dies with this call
+    if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (rc == LBM_OK) h->np = n;
+    return rc;
+}
+
+// Event pair around one kernel launch when profiling.
+struct ProfScope {
+    lbm_handle *h;
+    int k;
+    bool on;
+    ProfScope(lbm_handle *h_, int k_, bool launched) : h(h_), k(k_), on(h_->prof && launched && h_->nrec[k_] < kProfCap) {
+        if (!on) return;
+        const size_t i = (size_t)h->nrec[k];
+        if (h->ev[k][0].size() <= i) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) { on = false; return; }
+            h->ev[k][0].push_back(a);
+            h->ev[k][1].push_back(b);
+        }
+        cudaEventRecord(h->ev[k][0][i], h->stream);
+    }
+    ~ProfScope() {
+        if (!on) return;
+        cudaEventRecord(h->ev[k][1][(size_t)h->nrec[k]], h->stream);
+        h->nrec[k]++;
+    }
+};
+
+int lbm_step(lbm_handle *h, int nsteps) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    if (nsteps < 0) return fail(h, LBM_ERR_BAD_ARG, "nsteps < 0");
+    for (int t = 0; t < nsteps; t++) {
+        Params P = make_params(h);
+        // fresh brick lists and step counters
+        cudaError_t e = cudaMemsetAsync(h->ws + h->L.bin, 0, h->L.bin_bytes, h->stream);
+        if (e != cudaSuccess) return cuda_check(h, e, "cudaMemsetAsync(bricks)");
+        { ProfScope s(h, 0, P.np > 0); launch_bin(P, h->stream); }
+        { ProfScope s(h, 1, true); by_storage<DoFlags>(h->cfg.storage, P, h->stream); }
+        { ProfScope s(h, 2, true); by_storage<DoSweep>(h->cfg.storage, P, h->stream); }
+        { ProfScope s(h, 3, P.np > 0); launch_force_reduce(P, h->stream); }
+        { ProfScope s(h, 4, P.np > 0 && P.n_sub > 0); launch_dem(P, h->stream); }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_check(h, e, "kernel launch");
+        h->cur ^= 1;
+        h->fcur ^= 1;
+        h->steps++;
+    }
+    return LBM_OK;
+}
+
+int lbm_kernels_per_step(const lbm_handle *h) {
+    if (!h) return 0;
+    return h->np > 0 ? (h->cfg.n_sub > 0 ? 5 : 4) : 2;
+}
+
+static int read_status(lbm_handle *h, int *st) {
+    int rc = cuda_check(h, cudaMemcpyAsync(st, h->ws + h->L.status, ST_SLOTS * 4, cudaMemcpyDeviceToHost, h->stream),
+                        "cudaMemcpyAsync(status)");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return rc;
+}
+
+static int status_code(lbm_handle *h, const int *st) {
+    if (st[ST_ERR] & ERRB_BRICK_OVERFLOW)
+        return fail(h, LBM_ERR_CAPACITY, "more than %d particles met one brick; results are invalid", MAXPB);
+    if (st[ST_ERR] & ERRB_TIMEOUT) return fail(h, LBM_ERR_TIMEOUT, "a device wait gave up");
+    return LBM_OK;
+}
+
+int lbm_get_forces(lbm_handle *h, double *F, double *T, lbm_particle *state_out) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    int st[ST_SLOTS];
+    int rc = read_status(h, st);
+    if (rc != LBM_OK) return rc;
+    if ((rc = status_code(h, st)) != LBM_OK) return rc;
+    const size_t n = (size_t)h->np;
+    if (n == 0) return LBM_OK;
+    if (F) rc = cuda_check(h, cudaMemcpyAsync(F, h->ws + h->L.Fh, n * 24, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(F)");
+    if (rc == LBM_OK && T)
+        rc = cuda_check(h, cudaMemcpyAsync(T, h->ws + h->L.Th, n * 24, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(T)");
+    std::vector<DevParticle> dev;
+    if (rc == LBM_OK && state_out) {
+        dev.resize(n);
+        rc = cuda_check(h, cudaMemcpyAsync(dev.data(), h->ws + h->L.parts, n * sizeof(DevParticle),
+                                           cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(particles)");
+    }
+    if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (rc == LBM_OK && state_out) {
+        for (size_t j = 0; j < n; j++) {
+            const DevParticle &d = dev[j];
+            lbm_particle &p = state_out[j];
+            std::memset(&p, 0, sizeof(p));
+            p.n_cp = d.ncp;
+            p.fixed = d.fixed;
+            for (int k = 0; k < d.ncp; k++) {
+                for (int a = 0; a < 3; a++) p.cp[k][a] = d.cpb[k][a];
+                p.K[k] = d.K[k];
+            }
+            p.Rs = d.Rs; p.density = d.density; p.mass = d.mass;
+            for (int a = 0; a < 9; a++) p.inertia[a] = d.I[a];
+            for (int a = 0; a < 3; a++) { p.x[a] = d.x[a]; p.v[a] = d.v[a]; p.w[a] = d.w[a]; }
+            for (int a = 0; a < 4; a++) p.q[a] = d.q[a];
+        }
+    }
+    return rc;
+}
+
+int lbm_get_fields(lbm_handle *h, void *dev_rho, void *dev_u, void *dev_flags) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    Params P = current_params(h);
+    by_storage<DoFields>(h->cfg.storage, P, (double *)dev_rho, (double *)dev_u, (uint16_t *)dev_flags, h->stream);
+    int rc = cuda_check(h, cudaGetLastError(), "fields kernel launch");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return rc;
+}
+
+int lbm_set_populations(lbm_handle *h, const void *dev_f) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    if (!dev_f) return fail(h, LBM_ERR_BAD_ARG, "dev_f is NULL");
+    Params P = current_params(h);
+    by_storage<DoSetPop>(h->cfg.storage, P, (const double *)dev_f, h->stream);
+    int rc = cuda_check(h, cudaGetLastError(), "set_populations kernel launch");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return rc;
+}
+
+int lbm_get_populations(lbm_handle *h, void *dev_f) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    if (!dev_f) return fail(h, LBM_ERR_BAD_ARG, "dev_f is NULL");
+    Params P = current_params(h);
+    by_storage<DoGetPop>(h->cfg.storage, P, (double *)dev_f, h->stream);
+    int rc = cuda_check(h, cudaGetLastError(), "get_populations kernel launch");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return rc;
+}
+
+int lbm_check(lbm_handle *h) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    Params P = current_params(h);
+    by_storage<DoCheck>(h->cfg.storage, P, h->stream);
+    int rc = cuda_check(h, cudaGetLastError(), "check kernel launch");
+    if (rc != LBM_OK) return rc;
+    int st[ST_SLOTS];
+    if ((rc = read_status(h, st)) != LBM_OK) return rc;
+    if ((rc = status_code(h, st)) != LBM_OK) return rc;
+    if (st[ST_ERR] & ERRB_DIVERGED)
+        return fail(h, LBM_ERR_DIVERGED, "non-finite populations or |u| > 0.5 at a fluid node");
+    return LBM_OK;
+}
+
+int lbm_get_counters(lbm_handle *h, int64_t *steps, int32_t *nrefill, int32_t *nlinks) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    int c[kStepCounters];
+    int rc = cuda_check(h, cudaMemcpyAsync(c, h->ws + h->L.bin + (size_t)h->L.nbricks * 4, sizeof(c),
+                                           cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(counters)");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (rc != LBM_OK) return rc;
+    if (steps) *steps = h->steps;
+    if (nrefill) *nrefill = c[0];
+    if (nlinks) *nlinks = c[1];
+    return LBM_OK;
+}
+
+static void release_profile(lbm_handle *h) {
+    for (int k = 0; k < kProfKernels; k++) {
+        for (int a = 0; a < 2; a++) {
+            for (cudaEvent_t e : h->ev[k][a]) cudaEventDestroy(e);
+            h->ev[k][a].clear();
+        }
+        h->nrec[k] = 0;
+    }
+}
+
+int lbm_profile(lbm_handle *h, int enable) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    cudaStreamSynchronize(h->stream);
+    release_profile(h);
+    h->prof = enable != 0;
+    return LBM_OK;
+}
+
+int lbm_profile_read(lbm_handle *h, int kernel, double *total_ms, int64_t *launches) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    if (kernel < 0 || kernel >= kProfKernels) return fail(h, LBM_ERR_BAD_ARG, "kernel index out of range");
+    int rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (rc != LBM_OK) return rc;
+    double sum = 0.0;
+    for (int64_t i = 0; i < h->nrec[kernel]; i++) {
+        float ms = 0.f;
+        rc = cuda_check(h, cudaEventElapsedTime(&ms, h->ev[kernel][0][(size_t)i], h->ev[kernel][1][(size_t)i]),
+                        "cudaEventElapsedTime");
+        if (rc != LBM_OK) return rc;
+        sum += ms;
+    }
+    if (total_ms) *total_ms = sum;
+    if (launches) *launches = h->nrec[kernel];
+    return LBM_OK;
+}
+
+int lbm_set_stream(lbm_handle *h, void *cuda_stream) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle *h) {
+    if (!h) return LBM_OK;
+    cudaStreamSynchronize(h->stream);
+    release_profile(h);
+    delete h;
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_handle *h) { return h ? h->err : g_init_error; }
+
+}  // extern "C"

@@ -1,0 +1,328 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.
+
+Tolerances (element by element, stated per test):
+- node flags: bit-exact (inputs rejected when a node lies within 1e-9
+  relative of a surface);
+- one step, FP64 storage: populations within 1e-13 absolute (values ~0.1;
+  only the rounding order differs), force/torque within 1e-11 of the
+  force scale;
+- one step, FP32 storage: populations within 2e-6 absolute -- the collision
+  of ~0.1-sized values in FP32 rounds at ~1e-8 per operation, and the link
+  fraction q of Eq. (27) is computed from FP32 metaball values (relative error
+  <= 2^-13, which moves a VIBB population by at most ~1e-6); forces within
+  2e-6 per boundary link plus 1e-5 relative;
+- FP16 / BF16 offset storage: the stored offset s = f/w - rho0 is rounded to
+  11 / 8 significant bits, so a population carries an absolute error of at
+  most w |s| 2^-11 (resp. 2^-8) on top of the FP32 error: 2e-5 / 1.5e-4.
+"""
+import numpy as np
+import pytest
+
+from tests import _helpers as H
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2206_11634_gb300 import build as b
+    b.build()
+    import paper_2206_11634_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def W():
+    from paper_2206_11634_gb300 import workloads
+    return workloads
+
+
+POP_TOL = {"f64": 1e-13, "f32": 2e-6, "f16": 2e-5, "bf16": 1.5e-4}
+
+
+def _sync_populations(gpu, orc, rng, amp=1e-2):
+    """Random populations into the GPU (in its storage format), read back as
+    FP64, injected identically into the oracle."""
+    f = rng.uniform(1 - amp, 1 + amp, (gpu.Q,) + gpu.shape) * orc.w[:, None, None, None]
+    gpu.set_populations(torch.from_numpy(f).cuda())
+    back = gpu.populations().cpu().numpy()
+    orc.set_populations(back)
+    return back
+
+
+def _compare_step(pkg, oracle_mod, wl, storage, Q=19, rng_seed=0, steps=1, amp=1e-2, check_forces=True):
+    rng = np.random.default_rng(rng_seed)
+    wl = H.with_margin(oracle_mod, wl)
+    gpu = H.make_gpu(pkg, wl, Q=Q, storage=storage)
+    orc = H.make_oracle(oracle_mod, wl, Q=Q)
+    gpu.set_particles(H.gpu_particles(pkg, wl))
+    orc.set_particles(H.oracle_particles(oracle_mod, wl))
+    _sync_populations(gpu, orc, rng, amp)
+    gpu.step(steps)
+    orc.step(steps)
+    fl = gpu.flags().cpu().numpy()
+    own = orc.owner()
+    assert np.array_equal(fl - 1, own), "flags differ"
+    fluid = own < 0
+    fg = gpu.populations().cpu().numpy()
+    fo = orc.populations()
+    err = np.abs(fg - fo)[:, fluid].max() if fluid.any() else 0.0
+    tol = POP_TOL[storage] * (3 if steps > 1 else 1)
+    assert err <= tol, f"population error {err:.3e} > {tol:.1e}"
+    out = dict(gpu=gpu, orc=orc, err=err)
+    if check_forces and wl["particles"]:
+        Fg, Tg = gpu.forces()
+        Fo, To = orc.forces()
+        nl = max(1, orc.counters()["nlinks"])
+        assert gpu.counters()["nlinks"] == orc.counters()["nlinks"]
+        if storage == "f64":
+            ftol = 1e-11 * nl * 0.2
+        else:
+            ftol = POP_TOL[storage] * nl + 1e-5 * max(np.abs(Fo).max(), 1e-3)
+        assert np.abs(Fg - Fo).max() <= ftol, (Fg, Fo)
+        # torque lever arms are O(radius)
+        assert np.abs(Tg - To).max() <= 20 * ftol, (Tg, To)
+        out.update(F=(Fg, Fo), T=(Tg, To))
+    return out
+
+
+# --------------------------------------------------------------------------
+# workloads for the one-step comparisons
+# --------------------------------------------------------------------------
+def wl_periodic_empty(W):
+    wl = W.empty_box(24, "f32", (1, 1, 1))
+    wl.update(nx=24, ny=20, nz=16)
+    return wl
+
+
+def wl_walls_guo_ragged(W):
+    wl = W.empty_box(8, "f32", (0, 1, 0))
+    wl.update(nx=45, ny=13, nz=9, force=(2e-5, -1e-5, 3e-5), tau=0.62)
+    return wl
+
+
+def wl_metaball(W, periodic=(0, 0, 0), n=(40, 36, 44)):
+    rng = np.random.default_rng(11)
+    cp, K = W.random_metaball(rng, 4, 4.0)
+    wl = W.empty_box(8, "f32", periodic)
+    wl.update(nx=n[0], ny=n[1], nz=n[2], tau=0.8)
+    wl["particles"] = [W._particle(cp, K, (n[0] / 2 - 0.3, n[1] / 2 + 0.2, n[2] / 2 + 0.1),
+                                   q=(0.8, 0.3, -0.4, 0.33), v=(0.01, -0.02, 0.015), w=(0.002, -0.001, 0.003),
+                                   density=1.2, fixed=1)]
+    return H.fixed_mass(wl)
+
+
+def wl_touching(W):
+    """A sphere touching the bottom wall and two overlapping metaballs: the
+    missing force points of §2.3.5 item 2 are exercised."""
+    wl = W.empty_box(8, "f32", (1, 1, 0))
+    wl.update(nx=36, ny=28, nz=24, tau=0.9)
+    wl["particles"] = [
+        W._particle([[0, 0, 0]], [16.0], (9.3, 10.1, 3.2), fixed=1, v=(0.01, 0, 0), w=(0, 0.004, 0)),
+        W._particle([[0, 0, 0], [1, 0.5, 0]], [9.0, 7.0], (20.3, 12.1, 11.6), fixed=1, v=(0, 0.01, 0)),
+        W._particle([[0, 0, 0]], [12.0], (26.2, 12.4, 12.2), fixed=1, w=(0.002, 0, 0.001)),
+    ]
+    return H.fixed_mass(wl)
+
+
+def wl_multi(W, n=48, nz=48, count=12):
+    wl = W.multi_particle(count, n=n, nz=nz, storage="f32", steps=4, seed_offset=7)
+    for p in wl["particles"]:
+        p["fixed"] = 1
+        p["v"] = np.array([0.005, -0.004, 0.006])
+    return H.fixed_mass(wl)
+
+
+def wl_wrap(W):
+    """A metaball straddling the periodic x and y faces."""
+    rng = np.random.default_rng(5)
+    cp, K = W.random_metaball(rng, 3, 3.0)
+    wl = W.empty_box(8, "f32", (1, 1, 0))
+    wl.update(nx=32, ny=24, nz=20)
+    wl["particles"] = [W._particle(cp, K, (0.4, 23.3, 9.8), q=(0.6, 0.2, 0.7, 0.33), v=(0.01, 0.0, -0.01),
+                                   fixed=1)]
+    return H.fixed_mass(wl)
+
+
+CASES = ["periodic_empty", "walls_guo_ragged", "metaball", "touching", "multi", "wrap"]
+
+
+def _case(W, name):
+    return {"periodic_empty": wl_periodic_empty, "walls_guo_ragged": wl_walls_guo_ragged, "metaball": wl_metaball,
+            "touching": wl_touching, "multi": wl_multi, "wrap": wl_wrap}[name](W)
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["metaball", "touching", "multi", "wrap"])
+def test_flags_bit_exact(pkg, oracle_mod, W, case):
+    wl = H.with_margin(oracle_mod, _case(W, case))
+    gpu = H.make_gpu(pkg, wl, n_sub=0)
+    gpu.set_particles(H.gpu_particles(pkg, wl))
+    gpu.step(1)
+    o = H.make_oracle(oracle_mod, wl)
+    o.set_particles(H.oracle_particles(oracle_mod, wl))
+    own = o.classify()
+    fl = gpu.flags().cpu().numpy()
+    assert (own >= 0).sum() > 50
+    assert np.array_equal(fl - 1, own)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("case", CASES)
+def test_one_step(pkg, oracle_mod, W, case, storage):
+    _compare_step(pkg, oracle_mod, _case(W, case), storage)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("case", ["walls_guo_ragged", "metaball", "touching"])
+def test_one_step_d3q15(pkg, oracle_mod, W, case, storage):
+    _compare_step(pkg, oracle_mod, _case(W, case), storage, Q=15)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("case", ["metaball", "touching"])
+def test_one_step_reduced_storage(pkg, oracle_mod, W, case, storage):
+    _compare_step(pkg, oracle_mod, _case(W, case), storage)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_three_steps_moving_geometry(pkg, oracle_mod, W, storage):
+    """Particles that move between steps (DEM off, positions set by hand):
+    new fluid nodes are refilled (§2.3.3) on both sides."""
+    wl = wl_metaball(W, periodic=(1, 1, 1), n=(36, 36, 36))
+    wl = H.with_margin(oracle_mod, wl)
+    gpu = H.make_gpu(pkg, wl, storage=storage)
+    orc = H.make_oracle(oracle_mod, wl)
+    rng = np.random.default_rng(3)
+    refilled = 0
+    p0 = wl["particles"][0]
+    for k in range(3):
+        p0["x"] = p0["x"] + np.array([0.37, -0.29, 0.21])
+        wl = H.with_margin(oracle_mod, wl)
+        gpu.set_particles(H.gpu_particles(pkg, wl))
+        orc.set_particles(H.oracle_particles(oracle_mod, wl))
+        _sync_populations(gpu, orc, rng)
+        gpu.step(1)
+        orc.step(1)
+        assert gpu.counters()["nrefill"] == orc.counters()["nrefill"]
+        refilled += orc.counters()["nrefill"]
+        own = orc.owner()
+        assert np.array_equal(gpu.flags().cpu().numpy() - 1, own)
+        err = np.abs(gpu.populations().cpu().numpy() - orc.populations())[:, own < 0].max()
+        assert err <= POP_TOL[storage]
+    assert refilled > 20
+
+
+def test_settling_sphere_trajectory_fp64(pkg, oracle_mod, W):
+    """Workload 1 (sphere of §3.1 geometry, FP64), 12 steps with 100 DEM
+    sub-steps each: particle state, force and populations agree."""
+    wl = W.settling_sphere()
+    wl["gravity"] = (0.0, 0.0, -2e-3)   # faster, so the 12 steps move it
+    wl = H.with_margin(oracle_mod, wl)
+    gpu = H.make_gpu(pkg, wl)
+    orc = H.make_oracle(oracle_mod, wl)
+    gpu.set_particles(H.gpu_particles(pkg, wl))
+    orc.set_particles(H.oracle_particles(oracle_mod, wl))
+    for _ in range(12):
+        gpu.step(1)
+        orc.step(1)
+    sg, so = gpu.particles()[0], orc.get_particles()[0]
+    assert abs(sg["mass"] - so["mass"]) < 1e-9 * so["mass"]
+    assert np.abs(sg["x"] - so["x"]).max() < 1e-10
+    assert np.abs(sg["v"] - so["v"]).max() < 1e-11
+    assert np.abs(sg["x"] - np.array([15.5, 15.5, 34.0])).max() > 1e-3
+    Fg, Tg = gpu.forces()
+    Fo, To = orc.forces()
+    assert np.abs(Fg - Fo).max() < 1e-9 * max(1.0, np.abs(Fo).max())
+    own = orc.owner()
+    assert np.array_equal(gpu.flags().cpu().numpy() - 1, own)
+    assert np.abs(gpu.populations().cpu().numpy() - orc.populations())[:, own < 0].max() < 1e-12
+
+
+def test_settling_metaball_trajectory_fp32(pkg, oracle_mod, W):
+    """A reduced box of workload 2 (FP32), 20 steps with DEM: the force
+    history stays within FP32 accumulation error of the oracle's."""
+    wl = W.settling_metaball(nx=48, ny=48, nz=64, steps=20)
+    wl["particles"][0]["x"] = np.array([23.7, 24.2, 40.3])
+    wl["gravity"] = (0.0, 0.0, -5e-3)
+    wl = H.with_margin(oracle_mod, wl)
+    gpu = H.make_gpu(pkg, wl)
+    orc = H.make_oracle(oracle_mod, wl)
+    gpu.set_particles(H.gpu_particles(pkg, wl))
+    orc.set_particles(H.oracle_particles(oracle_mod, wl))
+    for _ in range(20):
+        gpu.step(1)
+        orc.step(1)
+        Fg, _ = gpu.forces()
+        Fo, _ = orc.forces()
+        assert np.abs(Fg - Fo).max() <= 1e-3 * np.abs(Fo).max() + 1e-4
+    sg, so = gpu.particles()[0], orc.get_particles()[0]
+    assert np.abs(sg["x"] - so["x"]).max() < 1e-4
+    assert np.abs(sg["v"] - so["v"]).max() < 1e-5
+
+
+def test_full_size_settling_metaball_one_step(pkg, oracle_mod, W):
+    """Workload 2 at its full 128x128x256 size in the benchmark's launch
+    configuration: one step from a perturbed state, every fluid node and the
+    force compared."""
+    wl = W.settling_metaball()
+    p = wl["particles"][0]
+    p["v"] = np.array([0.004, -0.003, -0.02])
+    p["w"] = np.array([0.001, 0.002, -0.001])
+    wl = H.with_margin(oracle_mod, wl)
+    _compare_step(pkg, oracle_mod, wl, "f32", amp=5e-3)
+
+
+def test_deterministic(pkg, oracle_mod, W):
+    wl = H.with_margin(oracle_mod, wl_multi(W))
+    outs = []
+    for _ in range(2):
+        gpu = H.make_gpu(pkg, wl, n_sub=0)
+        gpu.set_particles(H.gpu_particles(pkg, wl))
+        gpu.step(3)
+        F, T = gpu.forces()
+        outs.append((F, T, gpu.populations().cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
+
+
+def test_mass_conserved_closed_box_fp64(pkg, W):
+    wl = wl_walls_guo_ragged(W)
+    wl["force"] = (0.0, 0.0, 0.0)
+    gpu = H.make_gpu(pkg, wl, storage="f64")
+    rng = np.random.default_rng(0)
+    f = rng.uniform(0.99, 1.01, (19,) + gpu.shape) / 19
+    gpu.set_populations(torch.from_numpy(f).cuda())
+    m0 = gpu.populations().sum().item()
+    gpu.step(50)
+    assert abs(gpu.populations().sum().item() - m0) < 1e-13 * m0
+
+
+def test_brick_overflow_reported(pkg, W):
+    """More particles than one brick's list holds: reported, not silent."""
+    wl = W.empty_box(8, "f32", (1, 1, 1))
+    wl.update(nx=32, ny=16, nz=16)
+    wl["particles"] = [W._particle([[0, 0, 0]], [1.0], (1.0 + 1.7 * k, 2.0, 1.0), fixed=1) for k in range(17)]
+    H.fixed_mass(wl)
+    gpu = H.make_gpu(pkg, wl)
+    gpu.set_particles(H.gpu_particles(pkg, wl))
+    gpu.step(1)
+    with pytest.raises(pkg.LbmError) as e:
+        gpu.forces()
+    assert e.value.code == -3
+
+
+def test_divergence_reported(pkg, W):
+    gpu = H.make_gpu(pkg, wl_periodic_empty(W))
+    f = gpu.populations()
+    f[3, 2, 3, 4] = float("nan")
+    gpu.set_populations(f)
+    gpu.step(1)
+    with pytest.raises(pkg.LbmError) as e:
+        gpu.check()
+    assert e.value.code == -4
