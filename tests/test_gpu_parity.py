@@ -130,7 +130,7 @@ def wl_touching(W):
     return H.fixed_mass(wl)
 
 
-def wl_multi(W, n=48, nz=48, count=12):
+def wl_multi(W, n=64, nz=64, count=10):
     wl = W.multi_particle(count, n=n, nz=nz, storage="f32", steps=4, seed_offset=7)
     for p in wl["particles"]:
         p["fixed"] = 1
