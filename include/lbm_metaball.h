@@ -182,6 +182,30 @@ int lbm_profile_read(lbm_handle *h, int kernel, double *total_ms, int64_t *launc
 /* Change the stream later work is issued on. */
 int lbm_set_stream(lbm_handle *h, void *cuda_stream);
 
+/* Node classification without any device allocation, for callers that
+ * cannot call cudaMalloc (a host application that owns the whole device
+ * memory pool, or a process that allows no allocation once running).  The
+ * paper has no counterpart: this is a deployment variant of the
+ * classification step of lbm_step().
+ *
+ * Writes to dev_flags (device, uint16[nz][ny][nx]) the flags lbm_step()
+ * would compute for the n host particles at their given poses: 0 = fluid,
+ * j+1 = solid node owned by particle j.  Only cfg's lattice size, periodic
+ * axes, lattice and storage fields and c0 are read; particle masses are not
+ * needed.  The scratch (particle table, brick lists, counters) lives in one
+ * fixed __device__ array of under 5 MB inside the library, reserved on
+ * every device that loads the library until the process exits.  Limits: at
+ * most 65536 bricks of 32x4x2 nodes (256^3 nodes) and 256 particles; larger
+ * inputs return LBM_ERR_CAPACITY before any GPU work, as does a brick met by
+ * more than 16 particles.  Invalid arguments return LBM_ERR_BAD_ARG, CUDA
+ * failures LBM_ERR_CUDA.  The call runs on cuda_stream and synchronises it
+ * before returning.  The first call on a device looks up the array's device
+ * address (make it before any stream capture).  Every call on a device
+ * shares the array and clears what must start at zero; calls that overlap on
+ * the GPU (concurrent streams or processes sharing the library's context)
+ * race on it.  Host calls are serialised by a lock. */
+int lbm_flags_noalloc(const lbm_config *cfg, const lbm_particle *host, int n, void *dev_flags, void *cuda_stream);
+
 /* Release the handle (not the workspace).  Synchronises its stream. */
 int lbm_destroy(lbm_handle *h);
 

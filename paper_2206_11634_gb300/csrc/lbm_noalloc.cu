@@ -1,0 +1,141 @@
+// lbm_flags_noalloc: node classification for callers that cannot allocate
+// device memory.
+//
+// Some callers cannot call cudaMalloc: a host application that owns the
+// whole device memory pool and hands out no extra buffers, or a process with
+// a strict no-allocation policy once its steady state has started.  This
+// entry point classifies nodes for a set of particles with the same kernels
+// as lbm_step() (k_bin + k_flags), but keeps their scratch (particle table,
+// brick lists, per-brick occupancy, counters, status) in one file-scope
+// __device__ array of fixed size instead of a caller workspace.  The caller
+// still passes the particles (host) and the output flag array (device).
+//
+// The array is reserved by the CUDA runtime when the library's device code
+// is loaded on a device and stays reserved on every device that loads the
+// library until the process exits.  The first call on each device looks up
+// its device address (cudaGetSymbolAddress, with that device current); make
+// that first call before any stream capture.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "lbm_internal.cuh"
+
+using namespace lbmmb;
+
+namespace {
+
+constexpr int kMaxBricks = 1 << 16;   // e.g. 256 x 256 x 256 nodes (32x4x2-node bricks)
+constexpr int kMaxParticles = 256;
+constexpr int kMaxDevices = 64;
+
+constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+constexpr size_t kOffBin = 0;                                                    // bcount + 4 counters
+constexpr size_t kOffList = align256(kOffBin + (size_t)(kMaxBricks + 4) * 4);    // brick lists
+constexpr size_t kOffOcc = align256(kOffList + (size_t)kMaxBricks * MAXPB * 4);  // two occupancy arrays
+constexpr size_t kOffStatus = align256(kOffOcc + 2 * (size_t)kMaxBricks);
+constexpr size_t kOffParts = align256(kOffStatus + ST_SLOTS * 4);
+constexpr size_t kScratchBytes = align256(kOffParts + (size_t)kMaxParticles * sizeof(DevParticle));
+
+// Shared by every call on a device; holds the last call's contents.
+__device__ __align__(256) unsigned char g_flags_scratch[kScratchBytes];
+
+std::mutex g_mu;                       // serialises host calls (the host staging table below)
+void *g_scratch_addr[kMaxDevices];     // device address of g_flags_scratch, per device
+DevParticle g_host_parts[kMaxParticles];  // host staging of the particle table
+
+}  // namespace
+
+extern "C" int lbm_flags_noalloc(const lbm_config *cfg, const lbm_particle *host, int n, void *dev_flags,
+                                 void *cuda_stream) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!cfg || !dev_flags || n < 0 || (n > 0 && !host)) return LBM_ERR_BAD_ARG;
+    if (cfg->nx < 2 || cfg->ny < 2 || cfg->nz < 2) return LBM_ERR_BAD_ARG;
+    if (cfg->lattice != 19 && cfg->lattice != 15) return LBM_ERR_BAD_ARG;
+    if (cfg->storage < LBM_STORE_F64 || cfg->storage > LBM_STORE_BF16) return LBM_ERR_BAD_ARG;
+    if (!(cfg->c0 > 0.0)) return LBM_ERR_BAD_ARG;
+    const int nbx = (cfg->nx + BX - 1) / BX, nby = (cfg->ny + BY - 1) / BY, nbz = (cfg->nz + BZ - 1) / BZ;
+    const long long nbricks = (long long)nbx * nby * nbz;
+    if (nbricks > kMaxBricks) return LBM_ERR_CAPACITY;
+    if (n > kMaxParticles) return LBM_ERR_CAPACITY;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ERR_CUDA;
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_flags_scratch);
+        if (e != cudaSuccess || !p) return LBM_ERR_CUDA;
+        g_scratch_addr[dev] = p;
+    }
+    char *base = static_cast<char *>(g_scratch_addr[dev]);
+
+    // particle table: shape and pose only (classification needs no mass)
+    for (int j = 0; j < n; j++) {
+        const lbm_particle &p = host[j];
+        if (p.n_cp < 1 || p.n_cp > LBM_MAX_CP) return LBM_ERR_BAD_ARG;
+        DevParticle &d = g_host_parts[j];
+        std::memset(&d, 0, sizeof(d));
+        const double qn = std::sqrt(p.q[0] * p.q[0] + p.q[1] * p.q[1] + p.q[2] * p.q[2] + p.q[3] * p.q[3]);
+        if (!(qn > 0.0)) return LBM_ERR_BAD_ARG;
+        for (int a = 0; a < 4; a++) d.q[a] = p.q[a] / qn;
+        for (int a = 0; a < 3; a++) { d.x[a] = p.x[a]; d.v[a] = p.v[a]; d.w[a] = p.w[a]; }
+        d.ncp = p.n_cp;
+        double Ks = 0.0;
+        for (int k = 0; k < p.n_cp; k++) {
+            if (!(p.K[k] >= 0.0)) return LBM_ERR_BAD_ARG;
+            for (int a = 0; a < 3; a++) d.cpb[k][a] = p.cp[k][a];
+            d.K[k] = p.K[k];
+            Ks += p.K[k];
+        }
+        d.sumK = Ks;
+    }
+
+    cudaError_t e = cudaSuccess;
+    if (n > 0) e = cudaMemcpyAsync(base + kOffParts, g_host_parts, sizeof(DevParticle) * (size_t)n,
+                                   cudaMemcpyHostToDevice, st);
+    // what must start at zero: brick counts and counters, occupancy, status,
+    // and the output (bricks without particles are never written)
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffBin, 0, (size_t)(nbricks + 4) * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffOcc, 0, 2 * (size_t)kMaxBricks, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffStatus, 0, ST_SLOTS * 4, st);
+    const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
+    if (e == cudaSuccess) e = cudaMemsetAsync(dev_flags, 0, (size_t)N * 2, st);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+
+    Params P;
+    std::memset(&P, 0, sizeof(P));
+    P.nx = cfg->nx; P.ny = cfg->ny; P.nz = cfg->nz; P.Q = cfg->lattice;
+    for (int a = 0; a < 3; a++) P.per[a] = cfg->periodic[a] != 0;
+    P.N = N;
+    P.nbx = nbx; P.nby = nby; P.nbz = nbz; P.nbricks = (int)nbricks;
+    P.np = n;
+    P.tau = cfg->tau; P.rho0 = cfg->rho0; P.c0 = cfg->c0;
+    P.bcount = reinterpret_cast<int *>(base + kOffBin);
+    P.counters = reinterpret_cast<int *>(base + kOffBin + (size_t)nbricks * 4);
+    P.blist = reinterpret_cast<int *>(base + kOffList);
+    P.occ_new = reinterpret_cast<uint8_t *>(base + kOffOcc);
+    P.occ_old = reinterpret_cast<uint8_t *>(base + kOffOcc + kMaxBricks);
+    P.status = reinterpret_cast<int *>(base + kOffStatus);
+    P.parts = reinterpret_cast<DevParticle *>(base + kOffParts);
+    // the output doubles as the "previous" flags: every node of it reads back
+    // the value just written (or the cleared 0), so no node is refilled and no
+    // population array is touched
+    P.flag_new = static_cast<uint16_t *>(dev_flags);
+    P.flag_old = static_cast<const uint16_t *>(dev_flags);
+
+    launch_bin(P, st);
+    switch (cfg->storage) {
+        case LBM_STORE_F64: launch_flags_t<double>(P, st); break;
+        case LBM_STORE_F32: launch_flags_t<float>(P, st); break;
+        case LBM_STORE_F16: launch_flags_t<__half>(P, st); break;
+        default: launch_flags_t<__nv_bfloat16>(P, st); break;
+    }
+    int status[ST_SLOTS];
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status, base + kOffStatus, sizeof(status), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    if (status[ST_ERR] & ERRB_BRICK_OVERFLOW) return LBM_ERR_CAPACITY;
+    return LBM_OK;
+}

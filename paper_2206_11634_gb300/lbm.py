@@ -74,6 +74,7 @@ _SIGS = {
     "lbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "lbm_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lbm_flags_noalloc": (C.c_int, [C.POINTER(LbmConfig), C.POINTER(LbmParticle), C.c_int, C.c_void_p, C.c_void_p]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
 }
