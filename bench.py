@@ -37,15 +37,29 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS and % of HBM roofline per lattice sweep; drag rel. error vs FP64 oracle"
 UNIT = "MLUPS"
-BYTES_PER_FLUID_NODE = 2 * 19 * 4  # FP32 D3Q19: 19 loads + 19 stores
+BYTES_PER_VALUE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}  # one stored population
 BYTES_PER_NODE_FLAGS = 2           # uint16 flag per node
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_settling_metaball_128x128x256.txt")
 SWEEP_SOURCES = ["k_sweep.cuh", "k_flags.cuh", "lbm_internal.cuh", "launch_impl.cuh", "sweep_f32.cu"]
 
 
-def workload():
+WORKLOADS = ("settling_metaball", "empty_box", "settling_sphere", "multi_particle")
+
+
+def workload(name: str = "settling_metaball"):
+    """The benchmark's workload (default) or a diagnostic one."""
     from paper_2206_11634_gb300 import workloads
-    return workloads.settling_metaball(tau=0.8)
+    if name == "settling_metaball":
+        return workloads.settling_metaball(tau=0.8)
+    if name == "empty_box":  # the same walled 128x128x256 lattice without a particle
+        wl = workloads.empty_box(8, "f32", (0, 0, 0))
+        wl.update(nx=128, ny=128, nz=256, name="empty_128x128x256")
+        return wl
+    if name == "settling_sphere":
+        return workloads.settling_sphere()
+    if name == "multi_particle":
+        return workloads.multi_particle()
+    raise ValueError(name)
 
 
 def measured_peak_gbs():
@@ -170,7 +184,7 @@ def max_over_ranks(dist, value: float) -> float:
 
 def make_lattice(pkg, wl, stream):
     kw = dict(periodic=wl["periodic"], lattice=19, storage=wl["storage"], n_sub=wl["n_sub"],
-              max_particles=len(wl["particles"]), tau=wl["tau"], gravity=wl["gravity"], force=wl["force"],
+              max_particles=max(1, len(wl["particles"])), tau=wl["tau"], gravity=wl["gravity"], force=wl["force"],
               kn=wl["kn"], eta_n=wl["eta_n"], kt=wl["kt"], eta_t=wl["eta_t"], mu_s=wl["mu_s"], c_tol=wl["c_tol"])
     lat = pkg.Lattice(wl["nx"], wl["ny"], wl["nz"], stream=stream, **kw)
     parts = [pkg.make_particle(p["cp"], p["K"], p["x"], q=p["q"], v=p["v"], w=p["w"], Rs=p["Rs"],
@@ -204,7 +218,7 @@ def run_reference(args):
     world, rank, local, dist = dist_setup()
     if rank != 0:
         return 0
-    wl = workload()
+    wl = workload(args.workload)
     import oracle
     oracle.build()
     steps = max(1, args.steps)
@@ -235,7 +249,7 @@ def run_gpu(args):
     if rank == 0 or not os.path.exists(pkg.LIB_PATH):
         lib_build.build()
     barrier(dist)
-    wl = workload()
+    wl = workload(args.workload)
     nodes = wl["nx"] * wl["ny"] * wl["nz"]
     stream = torch.cuda.Stream()
     lat = make_lattice(pkg, wl, stream)
@@ -268,9 +282,9 @@ def run_gpu(args):
     # the particle state, step, read back forces, torques and state
     import numpy as np
     np_ = len(wl["particles"])
-    state = (pkg.LbmParticle * np_)()
-    F = np.zeros((np_, 3))
-    T = np.zeros((np_, 3))
+    state = (pkg.LbmParticle * max(1, np_))()
+    F = np.zeros((max(1, np_), 3))
+    T = np.zeros((max(1, np_), 3))
     import ctypes as C
     L = lat.L
     L.lbm_get_forces(lat.h, None, None, state)
@@ -297,9 +311,14 @@ def run_gpu(args):
             dist.destroy_process_group()
         return 0
 
-    sweep_ms, sweep_n = prof["k_sweep"]
-    sweep_avg_s = sweep_ms / max(1, sweep_n) * 1e-3
-    alg_bytes = BYTES_PER_FLUID_NODE * n_fluid + BYTES_PER_NODE_FLAGS * nodes
+    # the lattice sweep of one step is two launches: the plain bricks (on the
+    # auxiliary stream) and the near bricks after them; together they move
+    # every node's populations once
+    plain_ms, plain_n = prof["k_sweep_plain"]
+    near_ms, near_n = prof["k_sweep_near"]
+    sweep_avg_s = (plain_ms / max(1, plain_n) + near_ms / max(1, near_n)) * 1e-3
+    # 19 loads + 19 stores per fluid node, plus the 2-byte flag of every node
+    alg_bytes = 2 * 19 * BYTES_PER_VALUE[wl["storage"]] * n_fluid + BYTES_PER_NODE_FLAGS * nodes
     peak, peak_kind = measured_peak_gbs()
     achieved = alg_bytes / sweep_avg_s / 1e9
     traffic = profiled_traffic()
@@ -319,8 +338,8 @@ def run_gpu(args):
 
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl["name"], "lattice": "D3Q19", "storage": "f32", "tau": wl["tau"],
+            "scaling": "weak", "vs_baseline": None, "dtype": wl["storage"], "data": "synthetic",
+            "config": {"workload": wl["name"], "lattice": "D3Q19", "storage": wl["storage"], "tau": wl["tau"],
                        "n_sub": wl["n_sub"], "particles": len(wl["particles"]), "nodes": nodes,
                        "fluid_nodes": n_fluid, "l2": "no flush: populations 2x319 MB exceed the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
@@ -328,7 +347,7 @@ def run_gpu(args):
                     "steps": e2e_steps},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": f"{peak_kind} copy",
-                         "kernel": "k_sweep", "bytes_per_launch": alg_bytes,
+                         "kernel": "k_sweep_plain + k_sweep_near", "bytes_per_launch": alg_bytes,
                          "avg_launch_us": round(sweep_avg_s * 1e6, 3)},
             "kernels": kernels,
             "gpu_launches": int(sum(v[1] for v in prof.values())),
@@ -348,6 +367,8 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=WORKLOADS, default="settling_metaball",
+                    help="diagnostic workloads besides the default benchmark workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -136,7 +136,13 @@ int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_st
  * node flags are recomputed at the start of the next lbm_step(). */
 int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n);
 
-/* Advance nsteps >= 0 LBM steps on the handle's stream (asynchronous). */
+/* Advance nsteps >= 0 LBM steps on the handle's stream (asynchronous).  The
+ * work runs on two streams the handle owns (a high-priority one for the
+ * particle kernels and the sweep of the bricks particles reach, a
+ * low-priority one for the sweep of all other bricks), forked from and joined
+ * back into the handle's stream with events inside this call, so the call as
+ * a whole is ordered on the handle's stream (and can be captured into a CUDA
+ * graph from it). */
 int lbm_step(lbm_handle *h, int nsteps);
 
 /* Synchronise and copy out the hydrodynamic force and torque of the last
@@ -169,13 +175,14 @@ int lbm_get_counters(lbm_handle *h, int64_t *steps, int32_t *nrefill, int32_t *n
 int lbm_kernels_per_step(const lbm_handle *h);
 
 /* Kernel timing.  With enable = 1, every later lbm_step() records a CUDA
- * event pair around each of its kernels on the handle's stream (up to 65536
- * launches per kernel; later ones are not recorded).  lbm_profile_read()
- * synchronises and returns, for kernel k (0 bin, 1 flags, 2 sweep, 3 force
- * reduce, 4 DEM), the summed device time in milliseconds and the number of
- * launches recorded since profiling was enabled; enable = 0 stops recording
- * and releases the events.  The events are created on the host side of the
- * CUDA runtime (no device memory is allocated). */
+ * event pair around each of its kernels on the stream the kernel runs on (up
+ * to 65536 launches per kernel; later ones are not recorded).
+ * lbm_profile_read() synchronises and returns, for kernel k (0 bin, 1 flags,
+ * 2 plain sweep, 3 near sweep, 4 force reduce, 5 DEM), the summed device time
+ * in milliseconds and the number of launches recorded since profiling was
+ * enabled; enable = 0 stops recording and releases the events.  The events
+ * are created on the host side of the CUDA runtime (no device memory is
+ * allocated). */
 int lbm_profile(lbm_handle *h, int enable);
 int lbm_profile_read(lbm_handle *h, int kernel, double *total_ms, int64_t *launches);
 
@@ -193,7 +200,7 @@ int lbm_set_stream(lbm_handle *h, void *cuda_stream);
  * j+1 = solid node owned by particle j.  Only cfg's lattice size, periodic
  * axes, lattice and storage fields and c0 are read; particle masses are not
  * needed.  The scratch (particle table, brick lists, counters) lives in one
- * fixed __device__ array of under 5 MB inside the library, reserved on
+ * fixed __device__ array of under 6 MB inside the library, reserved on
  * every device that loads the library until the process exits.  Limits: at
  * most 65536 bricks of 32x4x2 nodes (256^3 nodes) and 256 particles; larger
  * inputs return LBM_ERR_CAPACITY before any GPU work, as does a brick met by

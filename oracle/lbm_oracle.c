@@ -36,7 +36,7 @@
 #define ORC_MAXCP 16
 #define ORC_MAXQ 19
 #define ORC_NWALL 6
-#define ORC_ROT_ITERS 4
+#define ORC_ROT_ITERS 2
 
 /* ------------------------------------------------------------------------- */
 /* Public structs (mirrored by ctypes in oracle/oracle.py).                   */

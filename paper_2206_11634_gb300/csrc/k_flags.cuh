@@ -30,33 +30,24 @@ __device__ __forceinline__ C feq_i(int ex, int ey, int ez, C w, C rho, C ux, C u
 }
 
 template <typename S, int Q>
-__global__ void __launch_bounds__(BRICK) k_flags(Params P) {
+__device__ __forceinline__ void flags_brick(const Params &P, SmemParticles &sp, int b) {
     using L = Lat<Q>;
     using Cd = Codec<S>;
     using C = typename Cd::C;
     constexpr bool kF64 = sizeof(C) == 8;
-    const int b = blockIdx.x;
     const int tid = threadIdx.x;
-    __shared__ SmemParticles sp;
-    __shared__ int s_cnt;
-
     int cnt = P.bcount[b];
     if (cnt > MAXPB) cnt = MAXPB;
-    const bool need = cnt > 0 || P.occ_new[b] || P.occ_old[b];
-    if (!need) return;  // uniform: nothing solid here now, before, or in this buffer
-    if (tid == 0) {
-        // ascending particle order makes the list, and hence every sum over
-        // it, independent of the scatter's atomic order
-        int ids[MAXPB];
-        for (int s = 0; s < cnt; s++) ids[s] = P.blist[b * MAXPB + s];
-        for (int s = 1; s < cnt; s++) {
-            int v = ids[s], k = s - 1;
-            while (k >= 0 && ids[k] > v) { ids[k + 1] = ids[k]; k--; }
-            ids[k + 1] = v;
-        }
-        for (int s = 0; s < cnt; s++) P.blist[b * MAXPB + s] = ids[s];
-        P.bcount[b] = cnt;
-        s_cnt = cnt;
+    __syncthreads();  // the previous brick's use of sp and of the list is over
+    // ascending particle order makes the list, and hence every sum over it,
+    // independent of the scatter's atomic order: lane s of warp 0 places its
+    // id at its rank (ids are distinct)
+    if (tid < 32) {
+        const int id = tid < cnt ? P.blist[b * MAXPB + tid] : 0x7fffffff;
+        int rank = 0;
+        for (int o = 0; o < cnt; o++) rank += __shfl_sync(0xffffffffu, id, o) < id;
+        if (tid < cnt) P.blist[b * MAXPB + rank] = id;
+        if (tid == 0) P.bcount[b] = cnt;
     }
     __syncthreads();
     int bxi, byi, bzi;
@@ -84,7 +75,7 @@ __global__ void __launch_bounds__(BRICK) k_flags(Params P) {
                 Md = metaball64(P, P.parts[sp.id[s]], (double)x, (double)y, (double)z);
                 inside = Md >= P.c0;
             } else {
-                inside = M >= (float)P.c0;
+                inside = M >= P.c0_f;
             }
             if (inside) {
                 cand[ncand] = s;
@@ -112,8 +103,7 @@ __global__ void __launch_bounds__(BRICK) k_flags(Params P) {
     }
     const uint16_t fl = own >= 0 ? (uint16_t)(own + 1) : (uint16_t)0;
     if (active) P.flag_new[n] = fl;
-    const int any_solid = __syncthreads_or(fl != 0);
-    if (tid == 0) P.occ_new[b] = (uint8_t)(any_solid != 0);
+    __syncthreads();
 
     // Local refilling, §2.3.3.  Reading: f_i' at x_new is "known after
     // streaming" when it streams in from x_new + e_i and that node was a fluid
@@ -155,6 +145,34 @@ __global__ void __launch_bounds__(BRICK) k_flags(Params P) {
             }
             atomicAdd(&P.counters[CNT_NREFILL], 1);
         }
+    }
+}
+
+// Persistent grid over the bricks listed this step and in the two steps
+// before; a brick listed in several of these lists is visited once (its most
+// recent listing).
+template <typename S, int Q>
+__global__ void __launch_bounds__(BRICK) k_flags(Params P) {
+    __shared__ SmemParticles sp;
+    const int t = P.step;
+    const int r0 = t % 3, r1 = (t + 2) % 3, r2 = (t + 1) % 3;
+    const int c0 = P.counters[CNT_LISTED];
+    const int c1 = t >= 1 ? P.wl_count[r1] : 0;
+    const int c2 = t >= 2 ? P.wl_count[r2] : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.wl_count[r0] = c0;  // read by the next two steps
+    const int total = c0 + c1 + c2;
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        int b;
+        if (w < c0) {
+            b = P.wl_list[r0 * P.nbricks + w];
+        } else if (w < c0 + c1) {
+            b = P.wl_list[r1 * P.nbricks + (w - c0)];
+            if (P.stamp[b] == t) continue;      // also listed this step
+        } else {
+            b = P.wl_list[r2 * P.nbricks + (w - c0 - c1)];
+            if (P.stamp[b] >= t - 1) continue;  // listed again since
+        }
+        flags_brick<S, Q>(P, sp, b);
     }
 }
 

@@ -51,6 +51,30 @@ __global__ void __launch_bounds__(256) k_bin(Params P) {
         const int slot = atomicAdd(&P.bcount[b], 1);
         if (slot < MAXPB) P.blist[b * MAXPB + slot] = j;
         else atomicOr(&P.status[ST_ERR], ERRB_BRICK_OVERFLOW);
+        if (slot == 0) {  // first particle of this brick: list it for k_flags
+            const int pos = atomicAdd(&P.counters[CNT_LISTED], 1);
+            P.wl_list[(P.step % 3) * P.nbricks + pos] = b;
+            P.stamp[b] = P.step;
+        }
+    }
+    if (!P.pred_stamp_next) return;
+    // bricks the next step's near sweep takes: the box grown by two nodes (a
+    // link, plus one node of motion); every node the next refill writes and
+    // every node next to one lies inside
+    const BrickRange gx = brick_range(P, p, 0, 2.0), gy = brick_range(P, p, 1, 2.0), gz = brick_range(P, p, 2, 2.0);
+    const int gxb = gx.hi - gx.lo + 1, gyb = gy.hi - gy.lo + 1, gzb = gz.hi - gz.lo + 1;
+    if (gxb <= 0 || gyb <= 0 || gzb <= 0) return;
+    const int gtotal = gxb * gyb * gzb;
+    const int next = P.step + 1;
+    for (int k = t; k < gtotal; k += blockDim.x) {
+        const int bxi = (gx.lo + k % gxb) % P.nbx;
+        const int byi = (gy.lo + (k / gxb) % gyb) % P.nby;
+        const int bzi = (gz.lo + k / (gxb * gyb)) % P.nbz;
+        const int b = bxi + P.nbx * (byi + P.nby * bzi);
+        if (atomicExch(&P.pred_stamp_next[b], next) != next) {
+            const int pos = atomicAdd(&P.pred_count[next & 1], 1);
+            P.pred_list_next[pos] = b;
+        }
     }
 }
 
@@ -82,6 +106,9 @@ __global__ void __launch_bounds__(256) k_force_reduce(Params P) {
             }
         }
     }
+    // this step's predicted list has been consumed by the near sweep; clear
+    // its count for the next step but one
+    if (j == 0 && t == 0 && P.pred_count) P.pred_count[P.step & 1] = 0;
     __shared__ double red[8][6];
     const int lane = t & 31, warp = t >> 5;
     for (int q = 0; q < 6; q++) {
@@ -380,31 +407,76 @@ __device__ void contacts(const Params &P, double h) {
     __syncthreads();
 }
 
-__device__ void euler_rate(const DevParticle &p, const double wb[3], const double Tb[3], double out[3]) {
-    double Iw[3], wIw[3], rhs[3];
-    mv(p.I, wb, Iw);
-    cross3(wb, Iw, wIw);
-    for (int a = 0; a < 3; a++) rhs[a] = Tb[a] - wIw[a];
-    mv(p.Iinv, rhs, out);
+// Euler's equations in the principal frame (Eq. (1), rotational part):
+// dw_l/dt = T_l / I_l + (I_{l+1} - I_{l+2}) / I_l w_{l+1} w_{l+2}.
+__device__ __forceinline__ void euler_rate(const DevParticle &p, const double wb[3], const double Tb[3], double out[3]) {
+    out[0] = fma(p.cI[0] * wb[1], wb[2], p.iI[0] * Tb[0]);
+    out[1] = fma(p.cI[1] * wb[2], wb[0], p.iI[1] * Tb[1]);
+    out[2] = fma(p.cI[2] * wb[0], wb[1], p.iI[2] * Tb[2]);
 }
 
-__device__ void quat_step(double q[4], const double wb[3], double h) {
-    const double wn = sqrt(dot3(wb, wb));
-    const double th = wn * h;
-    double dq[4];
-    if (th > 0.0) {
-        const double sn = sin(0.5 * th) / wn;
-        dq[0] = cos(0.5 * th); dq[1] = sn * wb[0]; dq[2] = sn * wb[1]; dq[3] = sn * wb[2];
+// R(q) v and R(q)^T v for a unit quaternion (w, u): with c = u x v,
+// R v = v + 2 w c + 2 u x c and R^T v = v - 2 w c + 2 u x c.
+__device__ __forceinline__ void rot_world(const double q[4], const double v[3], double r[3]) {
+    const double u[3] = {q[1], q[2], q[3]};
+    double c[3], uc[3];
+    cross3(u, v, c);
+    cross3(u, c, uc);
+    for (int a = 0; a < 3; a++) r[a] = v[a] + 2.0 * (q[0] * c[a] + uc[a]);
+}
+__device__ __forceinline__ void rot_body(const double q[4], const double v[3], double r[3]) {
+    const double u[3] = {q[1], q[2], q[3]};
+    double c[3], uc[3];
+    cross3(u, v, c);
+    cross3(u, c, uc);
+    for (int a = 0; a < 3; a++) r[a] = v[a] + 2.0 * (uc[a] - q[0] * c[a]);
+}
+
+// q <- q (x) exp(h w_b / 2), the rotation by the body-frame angular velocity
+// w_b over h.  For |w_b| h / 2 <= 1/16 the sine and cosine come from their
+// Taylor series (truncation below 1e-19), which needs no square root.
+__device__ __forceinline__ void quat_step(double q[4], const double wb[3], double h) {
+    const double w2 = dot3(wb, wb);
+    const double a2 = 0.25 * h * h * w2;  // (theta/2)^2
+    double s, c;  // s = sin(theta/2) / |w_b|, c = cos(theta/2)
+    if (a2 <= 1.0 / 256.0) {
+        s = 0.5 * h * (1.0 + a2 * (-1.0 / 6.0 + a2 * (1.0 / 120.0 + a2 * (-1.0 / 5040.0 + a2 * (1.0 / 362880.0 + a2 * (-1.0 / 39916800.0))))));
+        c = 1.0 + a2 * (-0.5 + a2 * (1.0 / 24.0 + a2 * (-1.0 / 720.0 + a2 * (1.0 / 40320.0 + a2 * (-1.0 / 3628800.0)))));
     } else {
-        dq[0] = 1.0; dq[1] = dq[2] = dq[3] = 0.0;
+        const double wn = sqrt(w2);
+        double sn;
+        sincos(0.5 * h * wn, &sn, &c);
+        s = sn / wn;
     }
-    double r[4];
-    r[0] = q[0] * dq[0] - q[1] * dq[1] - q[2] * dq[2] - q[3] * dq[3];
-    r[1] = q[0] * dq[1] + q[1] * dq[0] + q[2] * dq[3] - q[3] * dq[2];
-    r[2] = q[0] * dq[2] - q[1] * dq[3] + q[2] * dq[0] + q[3] * dq[1];
-    r[3] = q[0] * dq[3] + q[1] * dq[2] - q[2] * dq[1] + q[3] * dq[0];
-    const double nq = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
-    for (int a = 0; a < 4; a++) q[a] = r[a] / nq;
+    const double d[4] = {c, s * wb[0], s * wb[1], s * wb[2]};
+    const double r0 = q[0] * d[0] - q[1] * d[1] - q[2] * d[2] - q[3] * d[3];
+    const double r1 = q[0] * d[1] + q[1] * d[0] + q[2] * d[3] - q[3] * d[2];
+    const double r2 = q[0] * d[2] - q[1] * d[3] + q[2] * d[0] + q[3] * d[1];
+    const double r3 = q[0] * d[3] + q[1] * d[2] - q[2] * d[1] + q[3] * d[0];
+    q[0] = r0; q[1] = r1; q[2] = r2; q[3] = r3;
+}
+
+__device__ __forceinline__ void quat_normalize(double q[4]) {
+    const double in = rsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int a = 0; a < 4; a++) q[a] *= in;
+}
+
+// One rotational sub-step: half-kick, rotate with the half-step rate, then
+// the closing half-kick solved by ROT_ITERS fixed-point sweeps; wb and Tb are
+// body-frame (principal) quantities, Tb is refreshed for the new orientation.
+__device__ __forceinline__ void rotate_substep(const DevParticle &p, double q[4], double wb[3], double Tb[3],
+                                               const double Tw[3], double h) {
+    double dw[3], wh[3];
+    euler_rate(p, wb, Tb, dw);
+    for (int a = 0; a < 3; a++) wh[a] = wb[a] + 0.5 * h * dw[a];
+    quat_step(q, wh, h);
+    rot_body(q, Tw, Tb);
+    double w1[3] = {wh[0], wh[1], wh[2]};
+    for (int it = 0; it < ROT_ITERS; it++) {
+        euler_rate(p, w1, Tb, dw);
+        for (int a = 0; a < 3; a++) w1[a] = wh[a] + 0.5 * h * dw[a];
+    }
+    for (int a = 0; a < 3; a++) wb[a] = w1[a];
 }
 
 __device__ void refresh_cpw(const Params &P) {
@@ -420,11 +492,212 @@ __device__ void refresh_cpw(const Params &P) {
     __syncthreads();
 }
 
-// One CTA; kick-drift-kick velocity Verlet, the rotation advanced with the
-// half-step body angular velocity and closed by an implicit half-kick
-// (ROT_ITERS fixed-point sweeps of Euler's equations).
+constexpr int kFastMaxParticles = 256;
+
+// Whether some contact can occur during this LBM step.  Without contacts a
+// particle moves by at most |v| + |a| over the unit step (a = the frozen
+// acceleration), so when every bounding-sphere gap to a wall exceeds the
+// particle's bound, every gap between two particles exceeds the sum of their
+// bounds, and no contact is active, none starts during the step (the first
+// one would need a larger displacement first).  Tested in FP32 with a margin
+// of 1e-2 that covers its rounding; a doubtful case counts as "possible".
+__device__ bool contact_possible(const Params &P) {
+    __shared__ float xs[kFastMaxParticles][3], reach[kFastMaxParticles], br[kFastMaxParticles];
+    __shared__ int s_possible;
+    const int np = P.np;
+    if (np > kFastMaxParticles) return true;
+    if (threadIdx.x == 0) s_possible = 0;
+    __syncthreads();
+    int possible = 0;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const DevParticle &p = P.parts[k];
+        double D = 0.0;
+        if (!p.fixed) {
+            const double gr = 1.0 - P.rho0 / p.density;
+            double a2 = 0.0;
+            for (int a = 0; a < 3; a++) {
+                const double acc = gr * P.g[a] + P.Fh[3 * k + a] / p.mass;
+                a2 += acc * acc;
+            }
+            D = sqrt(dot3(p.v, p.v)) + sqrt(a2);
+        }
+        const float Df = (float)D * 1.0001f + 1e-4f;
+        for (int a = 0; a < 3; a++) xs[k][a] = (float)p.x[a];
+        reach[k] = Df;
+        br[k] = (float)p.brad;
+        for (int wall = 0; wall < NWALL; wall++) {
+            if (P.wall_on[k * NWALL + wall]) possible = 1;
+            const int ax = wall / 2, side = wall % 2;
+            if (P.per[ax]) continue;
+            const float plane = side ? (float)dim_of(P, ax) - 0.5f : -0.5f;
+            if (fabsf(plane - (float)p.x[ax]) - br[k] <= Df + 1e-2f) possible = 1;
+        }
+    }
+    __syncthreads();
+    const long long npairs = (long long)np * (np - 1) / 2;
+    for (long long idx = threadIdx.x; idx < npairs && !possible; idx += blockDim.x) {
+        // pair index -> (i, j), i < j
+        int i = (int)((2.0 * np - 1.0 - sqrt((2.0 * np - 1.0) * (2.0 * np - 1.0) - 8.0 * (double)idx)) * 0.5);
+        while ((long long)i * (2 * np - i - 1) / 2 > idx) i--;
+        while ((long long)(i + 1) * (2 * np - i - 2) / 2 <= idx) i++;
+        const int j = (int)(idx - (long long)i * (2 * np - i - 1) / 2) + i + 1;
+        if (P.pair_on[i * np + j]) { possible = 1; break; }
+        float d2 = 0.f;
+        for (int a = 0; a < 3; a++) {
+            float d = xs[j][a] - xs[i][a];
+            if (P.per[a]) {
+                const float L = (float)dim_of(P, a);
+                d -= L * rintf(d / L);
+            }
+            d2 += d * d;
+        }
+        const float lim = br[i] + br[j] + reach[i] + reach[j] + 1e-2f;
+        if (d2 <= lim * lim) possible = 1;
+    }
+    if (possible) atomicOr(&s_possible, 1);
+    __syncthreads();
+    return s_possible != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Rotation of a contact-free particle, four lanes per particle.  Lane 0 holds
+// the quaternion's scalar part, lanes 1..3 its vector part and the x,y,z
+// components of every vector (lane 0's vector slot is unused), so the cross
+// products, the quaternion product and Euler's equations run one component
+// per lane with width-4 shuffles.  FP64 throughout.
+// ---------------------------------------------------------------------------
+// lanes of the quads that take part (whole quads); set by the caller
+__device__ __forceinline__ double qget(unsigned mask, double v, int lane) { return __shfl_sync(mask, v, lane, 4); }
+
+// (a x b) for this lane's axis m = lane - 1 (lanes 1..3)
+// Per-lane shuffle sources, fixed for the whole sub-step loop.
+struct QuadLanes {
+    int lane;      // 0..3
+    int l1, l2;    // lanes of the next two axes (cyclic) of this lane's axis
+    int p1, p2, p3;        // quaternion product: lanes of d paired with q1, q2, q3
+    double s1, s2, s3;     // and their signs
+};
+
+__device__ __forceinline__ QuadLanes quad_lanes() {
+    QuadLanes L;
+    L.lane = threadIdx.x & 3;
+    const int m = L.lane == 0 ? 0 : L.lane - 1;
+    L.l1 = 1 + (m + 1) % 3;
+    L.l2 = 1 + (m + 2) % 3;
+    // r = q (x) d:  r_k = q0 d_k + s1 q1 d_p1 + s2 q2 d_p2 + s3 q3 d_p3
+    const int P1[4] = {1, 0, 3, 2}, P2[4] = {2, 3, 0, 1}, P3[4] = {3, 2, 1, 0};
+    const double S1[4] = {-1, 1, -1, 1}, S2[4] = {-1, 1, 1, -1}, S3[4] = {-1, -1, 1, 1};
+    L.p1 = P1[L.lane]; L.p2 = P2[L.lane]; L.p3 = P3[L.lane];
+    L.s1 = S1[L.lane]; L.s2 = S2[L.lane]; L.s3 = S3[L.lane];
+    return L;
+}
+
+// (a x b), this lane's axis (lanes 1..3)
+__device__ __forceinline__ double qcross(unsigned mk, const QuadLanes &L, double a, double b) {
+    const double a1 = qget(mk, a, L.l1), a2 = qget(mk, a, L.l2), b1 = qget(mk, b, L.l1), b2 = qget(mk, b, L.l2);
+    return a1 * b2 - a2 * b1;
+}
+// sum over lanes 1..3
+__device__ __forceinline__ double qsum3(unsigned mk, const QuadLanes &L, double v) {
+    double t = L.lane == 0 ? 0.0 : v;
+    t += __shfl_xor_sync(mk, t, 1, 4);
+    t += __shfl_xor_sync(mk, t, 2, 4);
+    return t;
+}
+// Euler's equations in the principal frame, this lane's axis
+__device__ __forceinline__ double qeuler(unsigned mk, const QuadLanes &L, double w, double Tb, double iI, double cI) {
+    const double w1 = qget(mk, w, L.l1), w2 = qget(mk, w, L.l2);
+    return fma(cI * w1, w2, iI * Tb);
+}
+// R(q)^T v (body components of a world vector), R(q) v when toward_world
+__device__ __forceinline__ double qrotate(unsigned mk, const QuadLanes &L, double q, double v, bool toward_world) {
+    const double c = qcross(mk, L, q, v);      // u x v
+    const double uc = qcross(mk, L, q, c);     // u x (u x v)
+    const double w = qget(mk, q, 0);
+    return v + 2.0 * (toward_world ? fma(w, c, uc) : fma(-w, c, uc));
+}
+
+// Rotation sub-steps of one free particle by its quad of lanes; mk holds the
+// lanes of every quad of this warp that takes part.
+__device__ void rotate_free_quad(unsigned mk, const DevParticle &p, const double *Th_world, double h, int n_sub,
+                                 DevParticle &out) {
+    const QuadLanes L = quad_lanes();
+    const int lane = L.lane;
+    const int m = lane == 0 ? 0 : lane - 1;
+    double q = p.q[lane];
+    const double Tw = lane == 0 ? 0.0 : Th_world[m];
+    const double iI = p.iI[m], cI = p.cI[m];
+    double wb = qrotate(mk, L, q, lane == 0 ? 0.0 : p.w[m], false);
+    double Tb = qrotate(mk, L, q, Tw, false);
+    if (__all_sync(mk, wb == 0.0 && Tb == 0.0)) return;  // nothing turns
+    const double hh = 0.5 * h, qh2 = 0.25 * h * h;
+    for (int sub = 0; sub < n_sub; sub++) {
+        const double wh = wb + hh * qeuler(mk, L, wb, Tb, iI, cI);
+        // q <- q (x) exp(h wh / 2), sine and cosine from their Taylor series
+        const double a2 = qh2 * qsum3(mk, L, wh * wh);
+        double sc, c;
+        if (a2 <= 1e-10) {
+            sc = hh * (1.0 - a2 * (1.0 / 6.0));
+            c = 1.0 + a2 * (-0.5 + a2 * (1.0 / 24.0));
+        } else if (a2 <= 1.0 / 256.0) {
+            sc = hh * (1.0 + a2 * (-1.0 / 6.0 + a2 * (1.0 / 120.0 + a2 * (-1.0 / 5040.0 + a2 * (1.0 / 362880.0 + a2 * (-1.0 / 39916800.0))))));
+            c = 1.0 + a2 * (-0.5 + a2 * (1.0 / 24.0 + a2 * (-1.0 / 720.0 + a2 * (1.0 / 40320.0 + a2 * (-1.0 / 3628800.0)))));
+        } else {
+            const double wn = sqrt(4.0 * a2) / h;
+            double sn;
+            sincos(hh * wn, &sn, &c);
+            sc = sn / wn;
+        }
+        const double d = lane == 0 ? c : sc * wh;
+        const double q0 = qget(mk, q, 0), q1 = qget(mk, q, 1), q2 = qget(mk, q, 2), q3 = qget(mk, q, 3);
+        const double dk = d, dp1 = qget(mk, d, L.p1), dp2 = qget(mk, d, L.p2), dp3 = qget(mk, d, L.p3);
+        q = fma(L.s3 * q3, dp3, fma(L.s2 * q2, dp2, fma(L.s1 * q1, dp1, q0 * dk)));
+        Tb = qrotate(mk, L, q, Tw, false);
+        double w1 = wh;
+        for (int it = 0; it < ROT_ITERS; it++) w1 = wh + hh * qeuler(mk, L, w1, Tb, iI, cI);
+        wb = w1;
+    }
+    // renormalise once per LBM step, back to world frame
+    double n2 = q * q;
+    n2 += __shfl_xor_sync(mk, n2, 1, 4);
+    n2 += __shfl_xor_sync(mk, n2, 2, 4);
+    q *= rsqrt(n2);
+    const double ww = qrotate(mk, L, q, wb, true);
+    out.q[lane] = q;
+    if (lane > 0) out.w[m] = ww;
+}
+
+// One CTA.  Kick-drift-kick velocity Verlet with the hydrodynamic load frozen
+// over the n_s sub-steps (§2.3.4); rotation by Euler's equations in the body
+// frame.  When no contact can occur during the step, the translation of the
+// n_s sub-steps under the constant force is taken in closed form (x += v +
+// a/2, v += a over the unit step: what the sub-steps compute in exact
+// arithmetic) and the rotation is sub-stepped by four lanes per particle.
 __global__ void __launch_bounds__(256) k_dem(Params P) {
     const double h = 1.0 / P.n_sub;
+    if (!contact_possible(P)) {
+        for (int k = threadIdx.x; k < P.np; k += blockDim.x) {
+            DevParticle &p = P.parts[k];
+            if (p.fixed) continue;
+            const double gr = 1.0 - P.rho0 / p.density;
+            for (int a = 0; a < 3; a++) {
+                const double acc = gr * P.g[a] + P.Fh[3 * k + a] / p.mass;
+                p.x[a] += p.v[a] + 0.5 * acc;
+                p.v[a] += acc;
+            }
+            for (int a = 0; a < 3; a++) { P.Fc[3 * k + a] = 0.0; P.Tc[3 * k + a] = 0.0; }
+        }
+        // rotation, one quad of lanes per moving particle; the shuffles name
+        // exactly the quads that take part
+        const int per_pass = blockDim.x / 4;
+        for (int base = 0; base < P.np; base += per_pass) {
+            const int k = base + (int)(threadIdx.x >> 2);
+            const bool moving = k < P.np && !P.parts[k].fixed;
+            const unsigned mk = __ballot_sync(0xffffffffu, moving);
+            if (moving) rotate_free_quad(mk, P.parts[k], P.Th + 3 * k, h, P.n_sub, P.parts[k]);
+        }
+        return;
+    }
     contacts(P, 0.0);
     for (int sub = 0; sub < P.n_sub; sub++) {
         for (int k = threadIdx.x; k < P.np; k += blockDim.x) {
@@ -436,16 +709,19 @@ __global__ void __launch_bounds__(256) k_dem(Params P) {
                 p.v[a] += 0.5 * h * Ft / p.mass;
             }
             for (int a = 0; a < 3; a++) p.x[a] += h * p.v[a];
-            double R[9], wb[3], Tw[3], Tb[3], dw[3];
-            rotm(p.q, R);
-            mtv(R, p.w, wb);
+            // first rotational half-kick and the rotation (the closing
+            // half-kick follows the new contact torque)
+            double q[4] = {p.q[0], p.q[1], p.q[2], p.q[3]};
+            double Tw[3], wb[3], Tb[3], dw[3];
             for (int a = 0; a < 3; a++) Tw[a] = P.Th[3 * k + a] + P.Tc[3 * k + a];
-            mtv(R, Tw, Tb);
+            rot_body(q, p.w, wb);
+            rot_body(q, Tw, Tb);
             euler_rate(p, wb, Tb, dw);
             for (int a = 0; a < 3; a++) wb[a] += 0.5 * h * dw[a];
-            quat_step(p.q, wb, h);
-            rotm(p.q, R);
-            mv(R, wb, p.w);
+            quat_step(q, wb, h);
+            quat_normalize(q);
+            for (int a = 0; a < 4; a++) p.q[a] = q[a];
+            rot_world(q, wb, p.w);
         }
         __syncthreads();
         refresh_cpw(P);
@@ -458,17 +734,16 @@ __global__ void __launch_bounds__(256) k_dem(Params P) {
                 const double Ft = p.mass * gr * P.g[a] + P.Fh[3 * k + a] + P.Fc[3 * k + a];
                 p.v[a] += 0.5 * h * Ft / p.mass;
             }
-            double R[9], wb[3], Tw[3], Tb[3], dw[3];
-            rotm(p.q, R);
-            mtv(R, p.w, wb);
+            double Tw[3], wb[3], Tb[3], dw[3];
             for (int a = 0; a < 3; a++) Tw[a] = P.Th[3 * k + a] + P.Tc[3 * k + a];
-            mtv(R, Tw, Tb);
+            rot_body(p.q, p.w, wb);
+            rot_body(p.q, Tw, Tb);
             double w1[3] = {wb[0], wb[1], wb[2]};
             for (int it = 0; it < ROT_ITERS; it++) {
                 euler_rate(p, w1, Tb, dw);
                 for (int a = 0; a < 3; a++) w1[a] = wb[a] + 0.5 * h * dw[a];
             }
-            mv(R, w1, p.w);
+            rot_world(p.q, w1, p.w);
         }
         __syncthreads();
     }

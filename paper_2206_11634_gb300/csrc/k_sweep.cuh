@@ -42,33 +42,33 @@ __device__ __forceinline__ int slot_of(const SmemParticles &sp, int id) {
 // Whether world node (x,y,z) + brick offset lies inside listed particle s,
 // decided exactly: FP32 outside the error band, FP64 inside it.  Mval gets a
 // value of M (FP32 or FP64) usable for q.
-template <bool kF64>
+template <typename C>
 __device__ __forceinline__ bool inside_exact(const Params &P, const SmemParticles &sp, int s, int lx, int ly, int lz,
-                                             int bx0, int by0, int bz0, double &Mval) {
-    if (!kF64) {
+                                             int bx0, int by0, int bz0, C &Mval) {
+    if (sizeof(C) == 4) {
         bool unsure;
         const float M = metaball32(P, sp, s, (float)lx, (float)ly, (float)lz, unsure);
-        if (!unsure) {
-            Mval = M;
-            return M >= (float)P.c0;
-        }
+        Mval = (C)M;
+        if (!unsure) return M >= P.c0_f;
     }
     const double M = metaball64(P, P.parts[sp.id[s]], (double)(bx0 + lx), (double)(by0 + ly), (double)(bz0 + lz));
-    Mval = M;
+    if (sizeof(C) == 8) Mval = (C)M;
     return M >= P.c0;
 }
 
 // M value for the link fraction (no exactness needed beyond the working
 // precision).
-template <bool kF64>
-__device__ __forceinline__ double m_value(const Params &P, const SmemParticles &sp, int s, int lx, int ly, int lz,
-                                          int bx0, int by0, int bz0) {
-    if (!kF64) {
+template <typename C>
+__device__ __forceinline__ C m_value(const Params &P, const SmemParticles &sp, int s, int lx, int ly, int lz, int bx0,
+                                     int by0, int bz0) {
+    if (sizeof(C) == 4) {
         bool unsure;
-        return (double)metaball32(P, sp, s, (float)lx, (float)ly, (float)lz, unsure);
+        return (C)metaball32(P, sp, s, (float)lx, (float)ly, (float)lz, unsure);
     }
-    return metaball64(P, P.parts[sp.id[s]], (double)(bx0 + lx), (double)(by0 + ly), (double)(bz0 + lz));
+    return (C)metaball64(P, P.parts[sp.id[s]], (double)(bx0 + lx), (double)(by0 + ly), (double)(bz0 + lz));
 }
+
+template <typename C> __device__ __forceinline__ C c0_of(const Params &P) { return sizeof(C) == 4 ? (C)P.c0_f : (C)P.c0; }
 
 // Lever arm from particle s's centroid to the brick-local point p (minimum
 // image), in the working precision.
@@ -128,45 +128,49 @@ __device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, cons
                                                           const typename Codec<S>::C *fown,
                                                           typename Codec<S>::C rho_f,
                                                           const typename Codec<S>::C *u_f,
-                                                          typename Codec<S>::C (*acc)[6]) {
+                                                          typename Codec<S>::C (*acc)[6],
+                                                          typename Codec<S>::C *Mf_cache, int *Mf_slot) {
     using L = Lat<Q>;
     using Cd = Codec<S>;
     using C = typename Cd::C;
-    constexpr bool kF64 = sizeof(C) == 8;
     const int io = L::opp(i);
-    const int dx = L::e(io, 0), dy = L::e(io, 1), dz = L::e(io, 2);  // d, into the solid
+    const int dx = lat_e<Q>(io, 0), dy = lat_e<Q>(io, 1), dz = lat_e<Q>(io, 2);  // d, into the solid
     const int j = (int)P.flag_new[ns_solid] - 1;
     const int s = slot_of(sp, j);
-    const C w_io = (C)L::w(io);
-    const C rho0 = (C)P.rho0;
+    const C w_io = (C)lat_w<Q>(io);
+    const C rho0 = Prm<C>::rho0(P);
     const S *A = (const S *)P.fA;
     const long long N = P.N;
     if (s < 0) {  // cannot happen for a consistent brick list; bounce back plainly
         atomicOr(&P.status[ST_ERR], ERRB_BRICK_OVERFLOW);
         return fown[io];
     }
-    // q by Eq. (27), clamped to [0,1] (rounding can push it past the ends)
-    const double Mf = m_value<kF64>(P, sp, s, lx, ly, lz, bx0, by0, bz0);
-    const double Ms = m_value<kF64>(P, sp, s, lx + dx, ly + dy, lz + dz, bx0, by0, bz0);
-    C q = (C)((P.c0 - Mf) / (Ms - Mf));
+    // q by Eq. (27), clamped to [0,1] (rounding can push it past the ends);
+    // M_j(x_f) is shared by all links of the node to the same particle
+    if (*Mf_slot != s) {
+        *Mf_cache = m_value<C>(P, sp, s, lx, ly, lz, bx0, by0, bz0);
+        *Mf_slot = s;
+    }
+    const C Mf = *Mf_cache;
+    const C Ms = m_value<C>(P, sp, s, lx + dx, ly + dy, lz + dz, bx0, by0, bz0);
+    C q = (c0_of<C>(P) - Mf) / (Ms - Mf);
     q = q < C(0) ? C(0) : (q > C(1) ? C(1) : q);
     C r[3], uw[3];
     lever<C>(P, sp, s, bx0, by0, bz0, (C)lx + q * dx, (C)ly + q * dy, (C)lz + q * dz, r);
     particle_velocity<C>(P, sp, s, r, uw);
     const C eu_w = -(dx * uw[0] + dy * uw[1] + dz * uw[2]);  // e_i . u_w with e_i = -d
-    // second fluid node x_ff = x - d
+    // second fluid node x_ff = x - d; its flag and populations are fetched
+    // together (the address is clamped to x itself beyond a wall, where the
+    // values are not used)
     int fx = x - dx, fy = y - dy, fz = z - dz;
-    bool ff_ok = true;
-    if (fx < 0 || fx >= P.nx) { if (P.per[0]) fx = (fx + P.nx) % P.nx; else ff_ok = false; }
-    if (fy < 0 || fy >= P.ny) { if (P.per[1]) fy = (fy + P.ny) % P.ny; else ff_ok = false; }
-    if (fz < 0 || fz >= P.nz) { if (P.per[2]) fz = (fz + P.nz) % P.nz; else ff_ok = false; }
-    const long long nff = (long long)fx + (long long)P.nx * ((long long)fy + (long long)P.ny * fz);
-    if (ff_ok) ff_ok = P.flag_new[nff] == 0;
-    C fin;
-    if (!P.vibb || !ff_ok) {
-        fin = fown[io] + C(6) * w_io * rho_f * eu_w;
-    } else {
-        C rho_ff = 0, m_ff[3] = {0, 0, 0}, fff_io = 0;
+    bool ff_in = true;
+    if (fx < 0 || fx >= P.nx) { if (P.per[0]) fx = (fx + P.nx) % P.nx; else ff_in = false; }
+    if (fy < 0 || fy >= P.ny) { if (P.per[1]) fy = (fy + P.ny) % P.ny; else ff_in = false; }
+    if (fz < 0 || fz >= P.nz) { if (P.per[2]) fz = (fz + P.nz) % P.nz; else ff_in = false; }
+    const int nff = ff_in ? fx + P.nx * (fy + P.ny * fz) : x + P.nx * (y + P.ny * z);
+    const uint16_t flag_ff = P.flag_new[nff];
+    C rho_ff = 0, m_ff[3] = {0, 0, 0}, fff_io = 0;
+    if (P.vibb) {
 #pragma unroll
         for (int k = 0; k < Q; k++) {
             const C fk = Cd::ld(A + (long long)k * N + nff, (C)L::w(k), rho0);
@@ -176,31 +180,43 @@ __device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, cons
             m_ff[2] += fk * L::e(k, 2);
             if (k == io) fff_io = fk;
         }
+    }
+    const C fown_io = fown[io];
+    const bool ff_ok = ff_in && flag_ff == 0;
+    C fin;
+    if (!P.vibb || !ff_ok) {
+        fin = fown_io + C(6) * w_io * rho_f * eu_w;
+    } else {
         C u_ff[3];
-        for (int a = 0; a < 3; a++) u_ff[a] = (m_ff[a] - C(0.5) * (C)P.F[a]) / rho_ff;
+        const C inv_rho_ff = C(1) / rho_ff;
+        for (int a = 0; a < 3; a++) u_ff[a] = (m_ff[a] - C(0.5) * Prm<C>::F(P, a)) * inv_rho_ff;
         const C feq_f = feq_i<C>(dx, dy, dz, w_io, rho_f, u_f[0], u_f[1], u_f[2]);
         const C feq_ff = feq_i<C>(dx, dy, dz, w_io, rho_ff, u_ff[0], u_ff[1], u_ff[2]);
         // Eq. (21): non-equilibrium part, interpolated (q <= 1/2) or
         // extrapolated (q > 1/2) from x_f and x_ff
-        const C fneq_d = C(2) * q * (fown[io] - feq_f) + (C(1) - C(2) * q) * (fff_io - feq_ff);
+        const C fneq_d = C(2) * q * (fown_io - feq_f) + (C(1) - C(2) * q) * (fff_io - feq_ff);
         C rho_d, us[3], uss[3], ud[3];
         if (q <= C(0.5)) {  // Eqs. (22)-(23), first branches
             rho_d = C(2) * q * rho_f + (C(1) - C(2) * q) * rho_ff;
             for (int a = 0; a < 3; a++) us[a] = C(2) * q * u_f[a] + (C(1) - C(2) * q) * u_ff[a];
         } else {            // second branches
             rho_d = rho_f;
-            for (int a = 0; a < 3; a++) us[a] = (C(1) - q) / q * u_f[a] + (C(2) * q - C(1)) / q * uw[a];
+            const C inv_q = C(1) / q;
+            const C a_f = (C(1) - q) * inv_q, a_w = (C(2) * q - C(1)) * inv_q;
+            for (int a = 0; a < 3; a++) us[a] = a_f * u_f[a] + a_w * uw[a];
         }
-        for (int a = 0; a < 3; a++) uss[a] = (C(1) - q) / (C(1) + q) * u_ff[a] + C(2) * q / (C(1) + q) * uw[a];  // (24)
-        for (int a = 0; a < 3; a++) ud[a] = us[a] / C(3) + C(2) * uss[a] / C(3);                                 // (25)
+        const C inv_1q = C(1) / (C(1) + q);
+        const C b_ff = (C(1) - q) * inv_1q, b_w = C(2) * q * inv_1q;
+        for (int a = 0; a < 3; a++) uss[a] = b_ff * u_ff[a] + b_w * uw[a];                 // (24)
+        for (int a = 0; a < 3; a++) ud[a] = (us[a] + C(2) * uss[a]) * C(1.0 / 3.0);        // (25)
         const C fplus_d = feq_i<C>(dx, dy, dz, w_io, rho_d, ud[0], ud[1], ud[2]) + fneq_d;                       // (20)
         fin = fplus_d + C(6) * w_io * rho_f * eu_w;                                                              // (19)
     }
     // Eq. (28): (e_i' - u_w) f+_i'(x,t) - (e_i - u_w) f_i(x,t+1), e_i' = d
     C dP[3];
-    dP[0] = (C(dx) - uw[0]) * fown[io] - (C(-dx) - uw[0]) * fin;
-    dP[1] = (C(dy) - uw[1]) * fown[io] - (C(-dy) - uw[1]) * fin;
-    dP[2] = (C(dz) - uw[2]) * fown[io] - (C(-dz) - uw[2]) * fin;
+    dP[0] = (C(dx) - uw[0]) * fown_io - (C(-dx) - uw[0]) * fin;
+    dP[1] = (C(dy) - uw[1]) * fown_io - (C(-dy) - uw[1]) * fin;
+    dP[2] = (C(dz) - uw[2]) * fown_io - (C(-dz) - uw[2]) * fin;
     add_term<C>(acc, s, dP, r);
     return fin;
 }
@@ -217,38 +233,50 @@ __device__ __noinline__ void solid_node(const Params &P, const SmemParticles &sp
                                         typename Codec<S>::C (*acc)[6]) {
     using L = Lat<Q>;
     using C = typename Codec<S>::C;
-    constexpr bool kF64 = sizeof(C) == 8;
-    const C rho0 = (C)P.rho0;
+    const C rho0 = Prm<C>::rho0(P);
+    // neighbour flags, fetched together (kWall beyond a wall)
+    constexpr uint32_t kWall = 0xFFFFFFFFu;
+    uint32_t nf[Q];
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        int yx = x - L::e(i, 0), yy = y - L::e(i, 1), yz = z - L::e(i, 2);
+        bool in = true;
+        if (yx < 0 || yx >= P.nx) { if (P.per[0]) yx = (yx + P.nx) % P.nx; else in = false; }
+        if (yy < 0 || yy >= P.ny) { if (P.per[1]) yy = (yy + P.ny) % P.ny; else in = false; }
+        if (yz < 0 || yz >= P.nz) { if (P.per[2]) yz = (yz + P.nz) % P.nz; else in = false; }
+        nf[i] = in ? (uint32_t)P.flag_new[yx + P.nx * (yy + P.ny * yz)] : kWall;
+    }
     for (int s = 0; s < sp.n; s++) {
         const int j = sp.id[s];
-        double Ms;
+        // a node whose neighbours all belong to j, or are fluid with j the
+        // owner, has no missing force point of j
+        uint32_t cand = 0;
+#pragma unroll
+        for (int i = 1; i < Q; i++) {
+            const bool seen = (nf[i] == 0 && j == owner) || nf[i] == (uint32_t)(j + 1);
+            if (!seen) cand |= 1u << i;
+        }
+        if (!cand) continue;
+        C Ms;
         if (j == owner) {
-            Ms = m_value<kF64>(P, sp, s, lx, ly, lz, bx0, by0, bz0);
-        } else if (!inside_exact<kF64>(P, sp, s, lx, ly, lz, bx0, by0, bz0, Ms)) {
+            Ms = m_value<C>(P, sp, s, lx, ly, lz, bx0, by0, bz0);
+        } else if (!inside_exact<C>(P, sp, s, lx, ly, lz, bx0, by0, bz0, Ms)) {
             continue;
         }
-        for (int i = 1; i < Q; i++) {
-            const int dx = L::e(i, 0), dy = L::e(i, 1), dz = L::e(i, 2);
-            int yx = x - dx, yy = y - dy, yz = z - dz;
-            bool in = true;
-            if (yx < 0 || yx >= P.nx) { if (P.per[0]) yx = (yx + P.nx) % P.nx; else in = false; }
-            if (yy < 0 || yy >= P.ny) { if (P.per[1]) yy = (yy + P.ny) % P.ny; else in = false; }
-            if (yz < 0 || yz >= P.nz) { if (P.per[2]) yz = (yz + P.nz) % P.nz; else in = false; }
-            if (in) {
-                const uint16_t fy = P.flag_new[(long long)yx + (long long)P.nx * ((long long)yy + (long long)P.ny * yz)];
-                if (fy == 0 && j == owner) continue;  // an ordinary link of j
-                if (fy == (uint16_t)(j + 1)) continue;  // interior of j
-            }
-            double My;
-            if (inside_exact<kF64>(P, sp, s, lx - dx, ly - dy, lz - dz, bx0, by0, bz0, My)) continue;
-            C q = (C)((P.c0 - My) / (Ms - My));
+        while (cand) {
+            const int i = __ffs(cand) - 1;
+            cand &= cand - 1;
+            const int dx = lat_e<Q>(i, 0), dy = lat_e<Q>(i, 1), dz = lat_e<Q>(i, 2);
+            C My;
+            if (inside_exact<C>(P, sp, s, lx - dx, ly - dy, lz - dz, bx0, by0, bz0, My)) continue;
+            C q = (c0_of<C>(P) - My) / (Ms - My);
             q = q < C(0) ? C(0) : (q > C(1) ? C(1) : q);
             C r[3], uw[3];
             lever<C>(P, sp, s, bx0, by0, bz0, (C)(lx - dx) + q * dx, (C)(ly - dy) + q * dy, (C)(lz - dz) + q * dz, r);
             particle_velocity<C>(P, sp, s, r, uw);
-            const int io = L::opp(i);
-            const C fi = feq_i<C>(dx, dy, dz, (C)L::w(i), rho0, uw[0], uw[1], uw[2]);
-            const C fo = feq_i<C>(-dx, -dy, -dz, (C)L::w(io), rho0, uw[0], uw[1], uw[2]);
+            const C w = (C)lat_w<Q>(i);
+            const C fi = feq_i<C>(dx, dy, dz, w, rho0, uw[0], uw[1], uw[2]);
+            const C fo = feq_i<C>(-dx, -dy, -dz, w, rho0, uw[0], uw[1], uw[2]);
             C dP[3];
             dP[0] = (C(dx) - uw[0]) * fi - (C(-dx) - uw[0]) * fo;
             dP[1] = (C(dy) - uw[1]) * fi - (C(-dy) - uw[1]) * fo;
@@ -259,14 +287,15 @@ __device__ __noinline__ void solid_node(const Params &P, const SmemParticles &sp
 }
 
 // Collide one node and store it: moments (Eq. (18)) with the half-force
-// shift, BGK toward f^eq (Eqs. (15)-(16)) plus Guo's forcing term.
-template <typename S, int Q>
+// shift, BGK toward f^eq (Eqs. (15)-(16)) plus Guo's forcing term (compiled
+// out when the body force is zero).
+template <typename S, int Q, bool kForce>
 __device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>::C (&fin)[Q], S *B, long long N,
-                                              long long n) {
+                                              int n) {
     using L = Lat<Q>;
     using Cd = Codec<S>;
     using C = typename Cd::C;
-    const C rho0 = (C)P.rho0;
+    const C rho0 = Prm<C>::rho0(P);
     C rho = 0, mx = 0, my = 0, mz = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -275,22 +304,30 @@ __device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>
         my += fin[i] * L::e(i, 1);
         mz += fin[i] * L::e(i, 2);
     }
-    const C Fx = (C)P.F[0], Fy = (C)P.F[1], Fz = (C)P.F[2];
-    const C inv_rho = C(1) / rho;
+    const C Fx = kForce ? Prm<C>::F(P, 0) : C(0), Fy = kForce ? Prm<C>::F(P, 1) : C(0),
+            Fz = kForce ? Prm<C>::F(P, 2) : C(0);
+    C inv_rho;
+    if (sizeof(C) == 4) inv_rho = (C)__frcp_rn((float)rho);
+    else inv_rho = C(1) / rho;
     const C ux = (mx + C(0.5) * Fx) * inv_rho, uy = (my + C(0.5) * Fy) * inv_rho, uz = (mz + C(0.5) * Fz) * inv_rho;
-    const C omega = (C)(1.0 / P.tau);
-    const C gfac = (C)(1.0 - 0.5 / P.tau);
+    const C omega = Prm<C>::omega(P);
     const C uu = ux * ux + uy * uy + uz * uz;
-    const C uF = ux * Fx + uy * Fy + uz * Fz;
+    const C w_rho_omega0 = omega * rho;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
         const C w = (C)L::w(i);
         const C eu = ex * ux + ey * uy + ez * uz;
-        const C feq = w * rho * (C(1) + C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu);
-        const C eF = ex * Fx + ey * Fy + ez * Fz;
-        const C Si = gfac * w * (C(3) * (eF - uF) + C(9) * eu * eF);
-        Cd::st(B + (long long)i * N + n, fin[i] + omega * (feq - fin[i]) + Si, w, rho0);
+        // omega f^eq = w (omega rho) (1 + 3 eu + 4.5 eu^2 - 1.5 uu)
+        const C feq_om = w * w_rho_omega0 * (C(1) + C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu);
+        C out = fin[i] - omega * fin[i] + feq_om;
+        if (kForce) {
+            const C gfac = Prm<C>::gfac(P);
+            const C uF = ux * Fx + uy * Fy + uz * Fz;
+            const C eF = ex * Fx + ey * Fy + ez * Fz;
+            out += gfac * w * (C(3) * (eF - uF) + C(9) * eu * eF);
+        }
+        Cd::st(B + (long long)i * N + n, out, w, rho0);
     }
 }
 
@@ -308,33 +345,100 @@ __device__ __forceinline__ void neighbour_coords(const Params &P, int x, int y, 
 }
 
 // A node of a brick no particle reaches: pull, halfway bounce-back at walls
-// (the node's own outgoing population), collide.  No flags are read.
-template <typename S, int Q>
-__device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z, long long n) {
+// (the node's own outgoing population), collide.  No flags are read.  Node
+// indices are 32-bit (the lattice holds fewer than 2^31 nodes).
+template <typename S, int Q, bool kForce>
+__device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z, int n) {
     using L = Lat<Q>;
     using Cd = Codec<S>;
     using C = typename Cd::C;
     const S *A = (const S *)P.fA;
     S *B = (S *)P.fB;
     const long long N = P.N;
-    const C rho0 = (C)P.rho0;
+    const C rho0 = Prm<C>::rho0(P);
     int xs[3], ys[3], zs[3];
     neighbour_coords(P, x, y, z, xs, ys, zs);
+    int row[3][3];  // nx * (y' + ny * z') for the neighbour rows
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) row[b][c] = P.nx * (ys[b] + P.ny * zs[c]);
     C fin[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
-        const long long src = ((sx | sy | sz) < 0)
-                                  ? (long long)L::opp(i) * N + n  // wall: f_i = f+_i'(x)
-                                  : (long long)i * N + (long long)sx + (long long)P.nx * ((long long)sy + (long long)P.ny * sz);
-        fin[i] = Cd::ld(A + src, (C)L::w(((sx | sy | sz) < 0) ? L::opp(i) : i), rho0);
+        const int bx = 1 - L::e(i, 0), by = 1 - L::e(i, 1), bz = 1 - L::e(i, 2);
+        const bool wall = (xs[bx] | ys[by] | zs[bz]) < 0;
+        // wall: f_i = f+_i'(x), the node's own opposite population
+        const S *src = wall ? A + (long long)L::opp(i) * N + n : A + (long long)i * N + (xs[bx] + row[by][bz]);
+        fin[i] = Cd::ld(src, (C)L::w(i), rho0);
     }
-    collide_store<S, Q>(P, fin, B, N, n);
+    collide_store<S, Q, kForce>(P, fin, B, N, n);
 }
 
-// Bricks some particle reaches: flags, particle links, missing force points
-// and the deterministic reduction of the per-particle terms.
-template <typename S, int Q>
+// A fluid node with at least one particle link, in a brick some particle
+// reaches: pull, walls, VIBB / halfway bounce-back on the particle links with
+// their momentum exchange, collide, store.
+template <typename S, int Q, bool kForce>
+__device__ __noinline__ void boundary_node(const Params &P, const SmemParticles &sp, int x, int y, int z, int lx,
+                                           int ly, int lz, int bx0, int by0, int bz0, int n,
+                                           typename Codec<S>::C (*acc)[6], int *nlinks) {
+    using L = Lat<Q>;
+    using Cd = Codec<S>;
+    using C = typename Cd::C;
+    const S *A = (const S *)P.fA;
+    S *B = (S *)P.fB;
+    const long long N = P.N;
+    const C rho0 = Prm<C>::rho0(P);
+    int xs[3], ys[3], zs[3];
+    neighbour_coords(P, x, y, z, xs, ys, zs);
+    C fown[Q];
+    C rho_f = 0, m_f[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < Q; k++) {
+        fown[k] = Cd::ld(A + (long long)k * N + n, (C)L::w(k), rho0);
+        rho_f += fown[k];
+        m_f[0] += fown[k] * L::e(k, 0);
+        m_f[1] += fown[k] * L::e(k, 1);
+        m_f[2] += fown[k] * L::e(k, 2);
+    }
+    C u_f[3];
+    const C inv_rho_f = C(1) / rho_f;
+    for (int a = 0; a < 3; a++) u_f[a] = (m_f[a] - C(0.5) * Prm<C>::F(P, a)) * inv_rho_f;
+    C fin[Q];
+    int srcs[Q];
+    uint32_t links = 0;
+    fin[0] = fown[0];
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
+        if ((sx | sy | sz) < 0) {
+            fin[i] = fown[L::opp(i)];  // box wall: halfway bounce-back
+            srcs[i] = n;
+            continue;
+        }
+        const int src = sx + P.nx * (sy + P.ny * sz);
+        srcs[i] = src;
+        fin[i] = Cd::ld(A + (long long)i * N + src, (C)L::w(i), rho0);
+        if (P.flag_new[src] != 0) links |= 1u << i;
+    }
+    // each thread visits its own links only, so a warp runs as many link
+    // updates as its busiest node has links
+    C Mf_cache = 0;
+    int Mf_slot = -1;
+    while (links) {
+        const int i = __ffs(links) - 1;
+        links &= links - 1;
+        fin[i] = particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, srcs[i], fown, rho_f, u_f, acc,
+                                     &Mf_cache, &Mf_slot);
+        (*nlinks)++;
+    }
+    collide_store<S, Q, kForce>(P, fin, B, N, n);
+}
+
+// Bricks some particle reaches: nodes without particle links take the plain
+// path (plus 19 flag reads); boundary and solid nodes go out of line; then
+// the deterministic reduction of the per-particle terms.
+template <typename S, int Q, bool kForce>
 __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, double (*red)[6], int *s_links, int b,
                                         int bx0, int by0, int bz0, int cnt) {
     using L = Lat<Q>;
@@ -345,10 +449,10 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
     const int x = bx0 + lx, y = by0 + ly, z = bz0 + lz;
     const bool active = x < P.nx && y < P.ny && z < P.nz;
     const long long N = P.N;
-    const long long n = (long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z);
+    const int n = x + P.nx * (y + P.ny * z);
     const S *A = (const S *)P.fA;
     S *B = (S *)P.fB;
-    const C rho0 = (C)P.rho0;
+    const C rho0 = Prm<C>::rho0(P);
 
     C acc[MAXPB][6];
     for (int s = 0; s < cnt; s++)
@@ -362,48 +466,19 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
         } else {
             int xs[3], ys[3], zs[3];
             neighbour_coords(P, x, y, z, xs, ys, zs);
+            bool linked = false;
             C fin[Q];
-            uint32_t wallmask = 0, linkmask = 0;
 #pragma unroll
             for (int i = 0; i < Q; i++) {
                 const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
-                if ((sx | sy | sz) < 0) {
-                    wallmask |= 1u << i;
-                    fin[i] = 0;
-                } else {
-                    const long long src = (long long)sx + (long long)P.nx * ((long long)sy + (long long)P.ny * sz);
-                    fin[i] = Cd::ld(A + (long long)i * N + src, (C)L::w(i), rho0);
-                    if (P.flag_new[src] != 0) linkmask |= 1u << i;
-                }
+                const bool wall = (sx | sy | sz) < 0;
+                const int src = wall ? n : sx + P.nx * (sy + P.ny * sz);
+                if (!wall) linked |= P.flag_new[src] != 0;
+                const S *ptr = wall ? A + (long long)L::opp(i) * N + n : A + (long long)i * N + src;
+                fin[i] = Cd::ld(ptr, (C)L::w(i), rho0);
             }
-            if (wallmask | linkmask) {
-                C fown[Q];
-                C rho_f = 0, m_f[3] = {0, 0, 0};
-#pragma unroll
-                for (int k = 0; k < Q; k++) {
-                    fown[k] = Cd::ld(A + (long long)k * N + n, (C)L::w(k), rho0);
-                    rho_f += fown[k];
-                    m_f[0] += fown[k] * L::e(k, 0);
-                    m_f[1] += fown[k] * L::e(k, 1);
-                    m_f[2] += fown[k] * L::e(k, 2);
-                }
-                C u_f[3];
-                for (int a = 0; a < 3; a++) u_f[a] = (m_f[a] - C(0.5) * (C)P.F[a]) / rho_f;
-#pragma unroll
-                for (int i = 1; i < Q; i++) {
-                    if (wallmask & (1u << i)) {
-                        fin[i] = fown[L::opp(i)];
-                    } else if (linkmask & (1u << i)) {
-                        const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
-                        const long long src =
-                            (long long)sx + (long long)P.nx * ((long long)sy + (long long)P.ny * sz);
-                        fin[i] = particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, src, fown, rho_f,
-                                                     u_f, acc);
-                        nlinks++;
-                    }
-                }
-            }
-            collide_store<S, Q>(P, fin, B, N, n);
+            if (!linked) collide_store<S, Q, kForce>(P, fin, B, N, n);
+            else boundary_node<S, Q, kForce>(P, sp, x, y, z, lx, ly, lz, bx0, by0, bz0, n, acc, &nlinks);
         }
     }
 
@@ -431,26 +506,55 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
     }
 }
 
-template <typename S, int Q>
-__global__ void __launch_bounds__(BRICK, 3) k_sweep(Params P) {
+// The sweep of every brick outside this step's predicted near set: the plain
+// path only.  Runs on its own stream, concurrently with the particle kernels.
+template <typename S, int Q, bool kForce>
+__global__ void __launch_bounds__(BRICK, 4) k_sweep_plain(Params P) {
+    const int b = blockIdx.x;
+    if (P.pred_stamp_cur && P.pred_stamp_cur[b] == P.step) return;  // the near sweep takes it
+    int bxi, byi, bzi;
+    brick_coords(P, b, bxi, byi, bzi);
+    const int tid = threadIdx.x;
+    const int x = bxi * BX + tid % BX, y = byi * BY + (tid / BX) % BY, z = bzi * BZ + tid / (BX * BY);
+    if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce>(P, x, y, z, x + P.nx * (y + P.ny * z));
+}
+
+// The sweep of the bricks listed this step (exactly those some particle's
+// grown search box meets) and of the predicted-near bricks that are not
+// listed (plain path).  Persistent grid; runs after k_sweep_plain, so a
+// listed brick the plain sweep also took is overwritten with its correct
+// update.
+template <typename S, int Q, bool kForce>
+__global__ void __launch_bounds__(BRICK, 4) k_sweep_near(Params P) {
     __shared__ SmemParticles sp;
     __shared__ double red[BRICK / 32][6];
     __shared__ int s_links;
-    const int b = blockIdx.x;
     const int tid = threadIdx.x;
-    int bxi, byi, bzi;
-    brick_coords(P, b, bxi, byi, bzi);
-    const int bx0 = bxi * BX, by0 = byi * BY, bz0 = bzi * BZ;
-    const int cnt = min(P.bcount[b], MAXPB);  // uniform over the CTA
-    if (cnt == 0) {
-        const int x = bx0 + tid % BX, y = by0 + (tid / BX) % BY, z = bz0 + tid / (BX * BY);
-        if (x < P.nx && y < P.ny && z < P.nz)
-            plain_node<S, Q>(P, x, y, z, (long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z));
-        return;
+    const int t = P.step;
+    const int c_exact = P.counters[CNT_LISTED];
+    const int c_pred = P.pred_stamp_cur ? P.pred_count[t & 1] : 0;
+    for (int w = blockIdx.x; w < c_exact + c_pred; w += gridDim.x) {
+        int b;
+        if (w < c_exact) {
+            b = P.wl_list[(t % 3) * P.nbricks + w];
+        } else {
+            b = P.pred_list_cur[w - c_exact];
+            if (P.stamp[b] == t) continue;  // listed: taken above
+        }
+        int bxi, byi, bzi;
+        brick_coords(P, b, bxi, byi, bzi);
+        const int bx0 = bxi * BX, by0 = byi * BY, bz0 = bzi * BZ;
+        const int cnt = min(P.bcount[b], MAXPB);
+        __syncthreads();  // the previous brick is done with the shared state
+        if (cnt == 0) {
+            const int x = bx0 + tid % BX, y = by0 + (tid / BX) % BY, z = bz0 + tid / (BX * BY);
+            if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce>(P, x, y, z, x + P.nx * (y + P.ny * z));
+            continue;
+        }
+        if (tid == 0) s_links = 0;
+        load_smem_particles(P, sp, b, bx0, by0, bz0);
+        near_brick<S, Q, kForce>(P, sp, red, &s_links, b, bx0, by0, bz0, cnt);
     }
-    if (tid == 0) s_links = 0;
-    load_smem_particles(P, sp, b, bx0, by0, bz0);
-    near_brick<S, Q>(P, sp, red, &s_links, b, bx0, by0, bz0, cnt);
 }
 
 }  // namespace lbmmb

@@ -15,13 +15,32 @@ void launch_init_t(const Params &P, void *f, cudaStream_t st) {
 }
 template <typename S>
 void launch_flags_t(const Params &P, cudaStream_t st) {
-    if (P.Q == 19) k_flags<S, 19><<<P.nbricks, BRICK, 0, st>>>(P);
-    else k_flags<S, 15><<<P.nbricks, BRICK, 0, st>>>(P);
+    const int grid = P.nbricks < kGridStrideBlocks / 2 ? P.nbricks : kGridStrideBlocks / 2;
+    if (P.Q == 19) k_flags<S, 19><<<grid, BRICK, 0, st>>>(P);
+    else k_flags<S, 15><<<grid, BRICK, 0, st>>>(P);
 }
 template <typename S>
-void launch_sweep_t(const Params &P, cudaStream_t st) {
-    if (P.Q == 19) k_sweep<S, 19><<<P.nbricks, BRICK, 0, st>>>(P);
-    else k_sweep<S, 15><<<P.nbricks, BRICK, 0, st>>>(P);
+void launch_sweep_plain_t(const Params &P, cudaStream_t st) {
+    const bool force = P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0;
+    if (P.Q == 19) {
+        if (force) k_sweep_plain<S, 19, true><<<P.nbricks, BRICK, 0, st>>>(P);
+        else k_sweep_plain<S, 19, false><<<P.nbricks, BRICK, 0, st>>>(P);
+    } else {
+        if (force) k_sweep_plain<S, 15, true><<<P.nbricks, BRICK, 0, st>>>(P);
+        else k_sweep_plain<S, 15, false><<<P.nbricks, BRICK, 0, st>>>(P);
+    }
+}
+template <typename S>
+void launch_sweep_near_t(const Params &P, cudaStream_t st) {
+    const bool force = P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0;
+    const int grid = P.nbricks < kGridStrideBlocks / 2 ? P.nbricks : kGridStrideBlocks / 2;
+    if (P.Q == 19) {
+        if (force) k_sweep_near<S, 19, true><<<grid, BRICK, 0, st>>>(P);
+        else k_sweep_near<S, 19, false><<<grid, BRICK, 0, st>>>(P);
+    } else {
+        if (force) k_sweep_near<S, 15, true><<<grid, BRICK, 0, st>>>(P);
+        else k_sweep_near<S, 15, false><<<grid, BRICK, 0, st>>>(P);
+    }
 }
 template <typename S>
 void launch_fields_t(const Params &P, const void *f, const uint16_t *flags, double *rho, double *u, uint16_t *fl,
@@ -48,7 +67,8 @@ void launch_check_t(const Params &P, const void *f, const uint16_t *flags, cudaS
 #define LBMMB_INSTANTIATE(S)                                                                                     \
     template void launch_init_t<S>(const Params &, void *, cudaStream_t);                                        \
     template void launch_flags_t<S>(const Params &, cudaStream_t);                                               \
-    template void launch_sweep_t<S>(const Params &, cudaStream_t);                                               \
+    template void launch_sweep_plain_t<S>(const Params &, cudaStream_t);                                         \
+    template void launch_sweep_near_t<S>(const Params &, cudaStream_t);                                          \
     template void launch_fields_t<S>(const Params &, const void *, const uint16_t *, double *, double *,         \
                                      uint16_t *, cudaStream_t);                                                  \
     template void launch_get_pop_t<S>(const Params &, const void *, double *, cudaStream_t);                     \

@@ -22,7 +22,9 @@ size_t storage_bytes(int s) { return s == LBM_STORE_F64 ? 8 : (s == LBM_STORE_F3
 
 // Byte offsets of every array in the workspace.
 struct Layout {
-    size_t f[2], flags[2], occ[2];
+    size_t f[2], flags[2];
+    size_t wl_list, wl_count, stamp;
+    size_t pred_stamp, pred_list, pred_count;
     size_t bin;        // bcount[nbricks] followed by the per-step counters
     size_t bin_bytes;
     size_t blist, partial, parts, Fh, Th, Fc, Tc;
@@ -38,7 +40,7 @@ constexpr int kStepCounters = 4;  // nrefill, nlinks, 2 spare
 const char *check_config(const lbm_config *c) {
     if (!c) return "config is NULL";
     if (c->nx < 2 || c->ny < 2 || c->nz < 2) return "nx, ny, nz must be >= 2";
-    if ((long long)c->nx * c->ny * c->nz > (1LL << 40)) return "lattice too large";
+    if ((long long)c->nx * c->ny * c->nz >= (1LL << 31)) return "lattice must hold fewer than 2^31 nodes";
     if (c->lattice != 19 && c->lattice != 15) return "lattice must be 19 (D3Q19) or 15 (D3Q15)";
     if (c->storage < LBM_STORE_F64 || c->storage > LBM_STORE_BF16) return "storage must be one of enum lbm_storage";
     if (!(c->tau > 0.5) || !std::isfinite(c->tau)) return "tau must be > 1/2";
@@ -71,8 +73,12 @@ void make_layout(const lbm_config *c, Layout *L) {
     L->f[1] = take(fbytes);
     L->flags[0] = take((size_t)N * 2);
     L->flags[1] = take((size_t)N * 2);
-    L->occ[0] = take(nb);
-    L->occ[1] = take(nb);
+    L->wl_list = take(3 * nb * 4);
+    L->wl_count = take(3 * 4);
+    L->stamp = take(nb * 4);
+    L->pred_stamp = take(2 * nb * 4);
+    L->pred_list = take(2 * nb * 4);
+    L->pred_count = take(2 * 4);
     L->bin_bytes = nb * 4 + kStepCounters * 4;
     L->bin = take(L->bin_bytes);
     L->blist = take(nb * MAXPB * 4);
@@ -97,11 +103,18 @@ thread_local char g_init_error[256] = "no error";
 
 }  // namespace
 
-constexpr int kProfKernels = 5;
+constexpr int kProfKernels = 6;
 constexpr int kProfCap = 65536;
 
 struct lbm_handle {
     lbm_config cfg;
+    // Each lbm_step() call forks two library streams from `stream` and joins
+    // them back: `hi` (highest priority) runs the latency-bound chain (binning,
+    // flags, near sweep, force reduction, DEM), `aux` (lowest priority) the
+    // plain sweep of the next step, so the chain's small grids are dispatched
+    // ahead of the plain sweep's bricks while both run.
+    cudaStream_t aux, hi;
+    cudaEvent_t ev_fork, ev_plain, ev_near, ev_join;
     // kernel timing (lbm_profile): event pairs per kernel, in launch order
     bool prof;
     std::vector<cudaEvent_t> ev[kProfKernels][2];
@@ -141,20 +154,22 @@ Params make_params(lbm_handle *h) {
     const lbm_config &c = h->cfg;
     Params P;
     std::memset(&P, 0, sizeof(P));
-    P.nx = c.nx; P.ny = c.ny; P.nz = c.nz; P.Q = c.lattice;
-    for (int a = 0; a < 3; a++) P.per[a] = c.periodic[a];
-    P.N = h->L.N;
-    P.nbx = h->L.nbx; P.nby = h->L.nby; P.nbz = h->L.nbz; P.nbricks = h->L.nbricks;
-    P.np = h->np; P.n_sub = c.n_sub; P.vibb = c.vibb; P.missing_force = c.missing_force;
-    P.tau = c.tau; P.rho0 = c.rho0; P.c0 = c.c0;
-    for (int a = 0; a < 3; a++) { P.F[a] = c.force[a]; P.g[a] = c.gravity[a]; P.u0[a] = c.u0[a]; }
-    P.kn = c.kn; P.eta_n = c.eta_n; P.kt = c.kt; P.eta_t = c.eta_t; P.mu_s = c.mu_s; P.c_tol = c.c_tol;
+    fill_scalar_params(c, P);
+    P.np = h->np;
     P.fA = h->ws + h->L.f[h->cur];
     P.fB = h->ws + h->L.f[1 - h->cur];
     P.flag_new = at<uint16_t>(h, h->L.flags[1 - h->fcur]);
     P.flag_old = at<uint16_t>(h, h->L.flags[h->fcur]);
-    P.occ_new = at<uint8_t>(h, h->L.occ[1 - h->fcur]);
-    P.occ_old = at<uint8_t>(h, h->L.occ[h->fcur]);
+    P.step = (int)h->steps;
+    P.wl_list = at<int>(h, h->L.wl_list);
+    P.wl_count = at<int>(h, h->L.wl_count);
+    P.stamp = at<int>(h, h->L.stamp);
+    const int cur = (int)(h->steps & 1);
+    P.pred_stamp_cur = at<int>(h, h->L.pred_stamp + (size_t)cur * h->L.nbricks * 4);
+    P.pred_stamp_next = at<int>(h, h->L.pred_stamp + (size_t)(1 - cur) * h->L.nbricks * 4);
+    P.pred_list_cur = at<int>(h, h->L.pred_list + (size_t)cur * h->L.nbricks * 4);
+    P.pred_list_next = at<int>(h, h->L.pred_list + (size_t)(1 - cur) * h->L.nbricks * 4);
+    P.pred_count = at<int>(h, h->L.pred_count);
     P.bcount = at<int>(h, h->L.bin);
     P.blist = at<int>(h, h->L.blist);
     P.partial = at<double>(h, h->L.partial);
@@ -195,7 +210,8 @@ void by_storage(int storage, A &&...args) {
 }
 template <typename S> struct DoInit { static void run(const Params &P, void *f, cudaStream_t st) { launch_init_t<S>(P, f, st); } };
 template <typename S> struct DoFlags { static void run(const Params &P, cudaStream_t st) { launch_flags_t<S>(P, st); } };
-template <typename S> struct DoSweep { static void run(const Params &P, cudaStream_t st) { launch_sweep_t<S>(P, st); } };
+template <typename S> struct DoPlain { static void run(const Params &P, cudaStream_t st) { launch_sweep_plain_t<S>(P, st); } };
+template <typename S> struct DoNear { static void run(const Params &P, cudaStream_t st) { launch_sweep_near_t<S>(P, st); } };
 template <typename S> struct DoFields {
     static void run(const Params &P, double *rho, double *u, uint16_t *fl, cudaStream_t st) {
         launch_fields_t<S>(P, P.fA, P.flag_new, rho, u, fl, st);
@@ -215,17 +231,71 @@ void quat_matrix(const double q[4], double R[9]) {
     R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
 }
 
-bool invert3(const double A[9], double B[9]) {
-    const double c0 = A[4] * A[8] - A[5] * A[7];
-    const double c1 = A[5] * A[6] - A[3] * A[8];
-    const double c2 = A[3] * A[7] - A[4] * A[6];
-    const double det = A[0] * c0 + A[1] * c1 + A[2] * c2;
-    if (det == 0.0 || !std::isfinite(det)) return false;
-    const double id = 1.0 / det;
-    B[0] = c0 * id; B[1] = (A[2] * A[7] - A[1] * A[8]) * id; B[2] = (A[1] * A[5] - A[2] * A[4]) * id;
-    B[3] = c1 * id; B[4] = (A[0] * A[8] - A[2] * A[6]) * id; B[5] = (A[2] * A[3] - A[0] * A[5]) * id;
-    B[6] = c2 * id; B[7] = (A[1] * A[6] - A[0] * A[7]) * id; B[8] = (A[0] * A[4] - A[1] * A[3]) * id;
-    return true;
+// Eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations:
+// A = V diag(d) V^T, V's columns the eigenvectors, det V = +1.
+void jacobi3(const double A_in[9], double d[3], double V[9]) {
+    double A[9];
+    for (int i = 0; i < 9; i++) { A[i] = A_in[i]; V[i] = (i % 4 == 0) ? 1.0 : 0.0; }
+    for (int sweep = 0; sweep < 50; sweep++) {
+        const double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+        const double dia = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+        if (off <= 1e-34 * dia || off == 0.0) break;
+        for (int p = 0; p < 2; p++)
+            for (int q = p + 1; q < 3; q++) {
+                const double apq = A[3 * p + q];
+                if (apq == 0.0) continue;
+                const double theta = (A[3 * q + q] - A[3 * p + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 3; k++) {  // A <- J^T A J
+                    const double akp = A[3 * k + p], akq = A[3 * k + q];
+                    A[3 * k + p] = c * akp - s * akq;
+                    A[3 * k + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; k++) {
+                    const double apk = A[3 * p + k], aqk = A[3 * q + k];
+                    A[3 * p + k] = c * apk - s * aqk;
+                    A[3 * q + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; k++) {  // V <- V J
+                    const double vkp = V[3 * k + p], vkq = V[3 * k + q];
+                    V[3 * k + p] = c * vkp - s * vkq;
+                    V[3 * k + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < 3; i++) d[i] = A[4 * i];
+    const double det = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
+                       V[2] * (V[3] * V[7] - V[4] * V[6]);
+    if (det < 0.0)
+        for (int k = 0; k < 3; k++) V[3 * k + 2] = -V[3 * k + 2];
+}
+
+// Unit quaternion (w,x,y,z) of a rotation matrix.
+void matrix_quat(const double R[9], double q[4]) {
+    const double tr = R[0] + R[4] + R[8];
+    if (tr > 0.0) {
+        const double s = std::sqrt(tr + 1.0) * 2.0;
+        q[0] = 0.25 * s; q[1] = (R[7] - R[5]) / s; q[2] = (R[2] - R[6]) / s; q[3] = (R[3] - R[1]) / s;
+    } else if (R[0] > R[4] && R[0] > R[8]) {
+        const double s = std::sqrt(1.0 + R[0] - R[4] - R[8]) * 2.0;
+        q[0] = (R[7] - R[5]) / s; q[1] = 0.25 * s; q[2] = (R[1] + R[3]) / s; q[3] = (R[2] + R[6]) / s;
+    } else if (R[4] > R[8]) {
+        const double s = std::sqrt(1.0 + R[4] - R[0] - R[8]) * 2.0;
+        q[0] = (R[2] - R[6]) / s; q[1] = (R[1] + R[3]) / s; q[2] = 0.25 * s; q[3] = (R[5] + R[7]) / s;
+    } else {
+        const double s = std::sqrt(1.0 + R[8] - R[0] - R[4]) * 2.0;
+        q[0] = (R[3] - R[1]) / s; q[1] = (R[2] + R[6]) / s; q[2] = (R[5] + R[7]) / s; q[3] = 0.25 * s;
+    }
+    const double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int a = 0; a < 4; a++) q[a] /= n;
+}
+
+void quat_mul(const double a[4], const double b[4], double r[4]) {
+    r[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    r[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    r[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    r[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
 }
 
 // Volume, centroid and inertia of {M >= c0} by counting cell-centre samples
@@ -321,7 +391,21 @@ int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_st
     // everything but the populations starts at zero: all nodes fluid, no
     // bricks occupied, no contacts, no errors
     const size_t zero_from = L.flags[0];
-    int rc = cuda_check(h, cudaMemsetAsync(h->ws + zero_from, 0, L.total - zero_from, h->stream), "cudaMemsetAsync");
+    h->aux = h->hi = nullptr;
+    h->ev_fork = h->ev_plain = h->ev_near = h->ev_join = nullptr;
+    int prio_low = 0, prio_high = 0;
+    int rc = cuda_check(h, cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high), "cudaDeviceGetStreamPriorityRange");
+    if (rc == LBM_OK)
+        rc = cuda_check(h, cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_low), "cudaStreamCreateWithPriority");
+    if (rc == LBM_OK)
+        rc = cuda_check(h, cudaStreamCreateWithPriority(&h->hi, cudaStreamNonBlocking, prio_high), "cudaStreamCreateWithPriority");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_plain, cudaEventDisableTiming), "cudaEventCreate");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_near, cudaEventDisableTiming), "cudaEventCreate");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + zero_from, 0, L.total - zero_from, h->stream), "cudaMemsetAsync");
+    if (rc == LBM_OK)  // no brick is predicted near before the first step
+        rc = cuda_check(h, cudaMemsetAsync(h->ws + L.pred_stamp, 0xFF, 2 * (size_t)L.nbricks * 4, h->stream), "cudaMemsetAsync");
     if (rc == LBM_OK) {
         Params P = make_params(h);
         by_storage<DoInit>(h->cfg.storage, P, (void *)(h->ws + L.f[0]), h->stream);
@@ -331,6 +415,12 @@ int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_st
     if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (rc != LBM_OK) {
         std::snprintf(g_init_error, sizeof(g_init_error), "%s", h->err);
+        if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+        if (h->ev_plain) cudaEventDestroy(h->ev_plain);
+        if (h->ev_near) cudaEventDestroy(h->ev_near);
+        if (h->ev_join) cudaEventDestroy(h->ev_join);
+        if (h->aux) cudaStreamDestroy(h->aux);
+        if (h->hi) cudaStreamDestroy(h->hi);
         delete h;
         return rc;
     }
@@ -363,7 +453,6 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
         d.fixed = p.fixed != 0;
         double Ks = 0.0, rmax = 0.0;
         for (int k = 0; k < p.n_cp; k++) {
-            for (int a = 0; a < 3; a++) d.cpb[k][a] = p.cp[k][a];
             d.K[k] = p.K[k];
             Ks += p.K[k];
             rmax = std::fmax(rmax, std::sqrt(p.cp[k][0] * p.cp[k][0] + p.cp[k][1] * p.cp[k][1] + p.cp[k][2] * p.cp[k][2]));
@@ -373,11 +462,25 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
         d.mass = p.mass;
         d.density = p.density;
         d.Rs = p.Rs;
-        for (int a = 0; a < 9; a++) d.I[a] = p.inertia[a];
-        if (!invert3(d.I, d.Iinv)) {
-            if (!d.fixed) return fail(h, LBM_ERR_BAD_ARG, "particle %d: singular inertia", j);
-            for (int a = 0; a < 9; a++) d.Iinv[a] = 0.0;
+        // principal frame: I_user = U diag(Ip) U^T, q_principal = q_user (x) q(U)
+        double Ip[3], U[9], qU[4];
+        jacobi3(p.inertia, Ip, U);
+        matrix_quat(U, qU);
+        for (int a = 0; a < 9; a++) d.Iu[a] = p.inertia[a];
+        for (int a = 0; a < 4; a++) d.qU[a] = qU[a];
+        quat_mul(p.q, qU, d.q);
+        for (int l = 0; l < 3; l++) {
+            d.Ip[l] = Ip[l];
+            d.iI[l] = Ip[l] != 0.0 ? 1.0 / Ip[l] : 0.0;
+            d.cI[l] = Ip[l] != 0.0 ? (Ip[(l + 1) % 3] - Ip[(l + 2) % 3]) / Ip[l] : 0.0;
         }
+        if (!d.fixed && !(Ip[0] > 0.0 && Ip[1] > 0.0 && Ip[2] > 0.0))
+            return fail(h, LBM_ERR_BAD_ARG, "particle %d: inertia not positive definite", j);
+        for (int k = 0; k < p.n_cp; k++)
+            for (int a = 0; a < 3; a++) {
+                d.cpu[k][a] = p.cp[k][a];
+                d.cpb[k][a] = U[a] * p.cp[k][0] + U[3 + a] * p.cp[k][1] + U[6 + a] * p.cp[k][2];  // U^T cp
+            }
         // world control points and search box (refreshed by every step)
         double R[9];
         quat_matrix(d.q, R);
@@ -410,7 +513,9 @@ struct ProfScope {
     lbm_handle *h;
     int k;
     bool on;
-    ProfScope(lbm_handle *h_, int k_, bool launched) : h(h_), k(k_), on(h_->prof && launched && h_->nrec[k_] < kProfCap) {
+    cudaStream_t st;
+    ProfScope(lbm_handle *h_, int k_, bool launched, cudaStream_t st_)
+        : h(h_), k(k_), on(h_->prof && launched && h_->nrec[k_] < kProfCap), st(st_) {
         if (!on) return;
         const size_t i = (size_t)h->nrec[k];
         if (h->ev[k][0].size() <= i) {
@@ -419,11 +524,11 @@ struct ProfScope {
             h->ev[k][0].push_back(a);
             h->ev[k][1].push_back(b);
         }
-        cudaEventRecord(h->ev[k][0][i], h->stream);
+        cudaEventRecord(h->ev[k][0][i], st);
     }
     ~ProfScope() {
         if (!on) return;
-        cudaEventRecord(h->ev[k][1][(size_t)h->nrec[k]], h->stream);
+        cudaEventRecord(h->ev[k][1][(size_t)h->nrec[k]], st);
         h->nrec[k]++;
     }
 };
@@ -431,28 +536,49 @@ struct ProfScope {
 int lbm_step(lbm_handle *h, int nsteps) {
     if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
     if (nsteps < 0) return fail(h, LBM_ERR_BAD_ARG, "nsteps < 0");
+    if (nsteps == 0) return LBM_OK;
+    // fork: both library streams start after everything issued so far
+    cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->hi, h->ev_fork, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_fork, 0);
+    if (e != cudaSuccess) return cuda_check(h, e, "stream fork");
+    cudaStream_t hs = h->hi;
     for (int t = 0; t < nsteps; t++) {
         Params P = make_params(h);
         // fresh brick lists and step counters
-        cudaError_t e = cudaMemsetAsync(h->ws + h->L.bin, 0, h->L.bin_bytes, h->stream);
+        e = cudaMemsetAsync(h->ws + h->L.bin, 0, h->L.bin_bytes, hs);
         if (e != cudaSuccess) return cuda_check(h, e, "cudaMemsetAsync(bricks)");
-        { ProfScope s(h, 0, P.np > 0); launch_bin(P, h->stream); }
-        { ProfScope s(h, 1, true); by_storage<DoFlags>(h->cfg.storage, P, h->stream); }
-        { ProfScope s(h, 2, true); by_storage<DoSweep>(h->cfg.storage, P, h->stream); }
-        { ProfScope s(h, 3, P.np > 0); launch_force_reduce(P, h->stream); }
-        { ProfScope s(h, 4, P.np > 0 && P.n_sub > 0); launch_dem(P, h->stream); }
+        { ProfScope s(h, 0, P.np > 0, hs); launch_bin(P, hs); }
+        { ProfScope s(h, 1, true, hs); by_storage<DoFlags>(h->cfg.storage, P, hs); }
+        // plain bricks on the low-priority stream: they need only the
+        // previous step's populations (the previous near sweep was joined in)
+        { ProfScope s(h, 2, true, h->aux); by_storage<DoPlain>(h->cfg.storage, P, h->aux); }
+        e = cudaEventRecord(h->ev_plain, h->aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, h->ev_plain, 0);
+        if (e != cudaSuccess) return cuda_check(h, e, "stream join");
+        { ProfScope s(h, 3, true, hs); by_storage<DoNear>(h->cfg.storage, P, hs); }
+        e = cudaEventRecord(h->ev_near, hs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_near, 0);
+        if (e != cudaSuccess) return cuda_check(h, e, "stream fork");
+        { ProfScope s(h, 4, P.np > 0, hs); launch_force_reduce(P, hs); }
+        { ProfScope s(h, 5, P.np > 0 && P.n_sub > 0, hs); launch_dem(P, hs); }
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_check(h, e, "kernel launch");
         h->cur ^= 1;
         h->fcur ^= 1;
         h->steps++;
     }
+    // join: the caller's stream continues after the last DEM (the last plain
+    // sweep precedes the last near sweep on hi)
+    e = cudaEventRecord(h->ev_join, hs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+    if (e != cudaSuccess) return cuda_check(h, e, "stream join");
     return LBM_OK;
 }
 
 int lbm_kernels_per_step(const lbm_handle *h) {
     if (!h) return 0;
-    return h->np > 0 ? (h->cfg.n_sub > 0 ? 5 : 4) : 2;
+    return h->np > 0 ? (h->cfg.n_sub > 0 ? 6 : 5) : 3;
 }
 
 static int read_status(lbm_handle *h, int *st) {
@@ -495,13 +621,14 @@ int lbm_get_forces(lbm_handle *h, double *F, double *T, lbm_particle *state_out)
             p.n_cp = d.ncp;
             p.fixed = d.fixed;
             for (int k = 0; k < d.ncp; k++) {
-                for (int a = 0; a < 3; a++) p.cp[k][a] = d.cpb[k][a];
+                for (int a = 0; a < 3; a++) p.cp[k][a] = d.cpu[k][a];
                 p.K[k] = d.K[k];
             }
             p.Rs = d.Rs; p.density = d.density; p.mass = d.mass;
-            for (int a = 0; a < 9; a++) p.inertia[a] = d.I[a];
+            for (int a = 0; a < 9; a++) p.inertia[a] = d.Iu[a];
             for (int a = 0; a < 3; a++) { p.x[a] = d.x[a]; p.v[a] = d.v[a]; p.w[a] = d.w[a]; }
-            for (int a = 0; a < 4; a++) p.q[a] = d.q[a];
+            const double qUc[4] = {d.qU[0], -d.qU[1], -d.qU[2], -d.qU[3]};
+            quat_mul(d.q, qUc, p.q);  // back to the caller's body frame
         }
     }
     return rc;
@@ -576,6 +703,8 @@ static void release_profile(lbm_handle *h) {
 int lbm_profile(lbm_handle *h, int enable) {
     if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
     cudaStreamSynchronize(h->stream);
+    cudaStreamSynchronize(h->aux);
+    cudaStreamSynchronize(h->hi);
     release_profile(h);
     h->prof = enable != 0;
     return LBM_OK;
@@ -608,7 +737,15 @@ int lbm_set_stream(lbm_handle *h, void *cuda_stream) {
 int lbm_destroy(lbm_handle *h) {
     if (!h) return LBM_OK;
     cudaStreamSynchronize(h->stream);
+    cudaStreamSynchronize(h->aux);
     release_profile(h);
+    cudaEventDestroy(h->ev_fork);
+    cudaEventDestroy(h->ev_plain);
+    cudaEventDestroy(h->ev_near);
+    cudaEventDestroy(h->ev_join);
+    cudaStreamSynchronize(h->hi);
+    cudaStreamDestroy(h->aux);
+    cudaStreamDestroy(h->hi);
     delete h;
     return LBM_OK;
 }

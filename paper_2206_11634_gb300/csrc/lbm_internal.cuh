@@ -27,11 +27,11 @@ constexpr int BRICK = BX * BY * BZ;  // nodes per brick = threads per sweep CTA
 constexpr int MAXPB = LBM_MAX_PER_BRICK;
 constexpr int MAXCP = LBM_MAX_CP;
 constexpr int NWALL = 6;
-constexpr int ROT_ITERS = 4;  // fixed-point sweeps of the implicit rotational half-kick
+constexpr int ROT_ITERS = 2;  // fixed-point sweeps of the implicit rotational half-kick
 
 // Status words in the workspace.
 enum StatusSlot { ST_ERR = 0, ST_SLOTS = 16 };
-enum StepCounter { CNT_NREFILL = 0, CNT_NLINKS = 1 };
+enum StepCounter { CNT_NREFILL = 0, CNT_NLINKS = 1, CNT_LISTED = 2 };
 enum ErrBits { ERRB_BRICK_OVERFLOW = 1, ERRB_DIVERGED = 2, ERRB_TIMEOUT = 4 };
 
 // ---------------------------------------------------------------------------
@@ -72,6 +72,34 @@ struct Lat<15> {
     }
     __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 };
+
+// Lattice entries for a direction known only at run time (out-of-line code):
+// every component e+1 in {0,1,2} packed as 2 bits, 6 bits per direction,
+// into two 64-bit constants, so no table has to be materialised.
+template <int Q>
+struct LatPack {
+    static constexpr unsigned long long word(int half) {
+        unsigned long long v = 0;
+        for (int i = 0; i < Q; i++)
+            for (int a = 0; a < 3; a++) {
+                const int bit = 6 * i + 2 * a;
+                if ((bit >= 64) == (half == 1))
+                    v |= (unsigned long long)(Lat<Q>::e(i, a) + 1) << (bit - 64 * half);
+            }
+        return v;
+    }
+    static constexpr unsigned long long lo = word(0), hi = word(1);
+};
+template <int Q>
+__device__ __forceinline__ int lat_e(int i, int a) {
+    const int bit = 6 * i + 2 * a;  // 2-bit fields never straddle the words (6*10 = 60, 60+4 < 64)
+    const unsigned long long w = bit < 64 ? LatPack<Q>::lo : LatPack<Q>::hi;
+    return (int)((w >> (bit & 63)) & 3ull) - 1;
+}
+template <int Q>
+__device__ __forceinline__ double lat_w(int i) {
+    return i == 0 ? Lat<Q>::w(0) : (i <= 6 ? Lat<Q>::w(1) : Lat<Q>::w(Q - 1));
+}
 
 // ---------------------------------------------------------------------------
 // Storage codecs.  FP64/FP32 store f itself; FP16/BF16 store the offset
@@ -124,13 +152,21 @@ struct Codec<__nv_bfloat16> {
 // ---------------------------------------------------------------------------
 // Particle table entry (device, FP64).
 // ---------------------------------------------------------------------------
+// Internally the body frame is the principal frame of the inertia tensor
+// (diagonal I), so Euler's equations need no matrix products; the caller's
+// body frame is restored on output through qU.
 struct DevParticle {
-    double x[3], q[4], v[3], w[3];
-    double cpb[MAXCP][3];  // body frame
+    double x[3], q[4], v[3], w[3];   // q: principal frame -> world
+    double cpb[MAXCP][3];  // control points, principal frame
     double cpw[MAXCP][3];  // world, refreshed after every DEM phase
     double K[MAXCP];
     double mass, density, Rs, sumK;
-    double I[9], Iinv[9];
+    double Ip[3];          // principal moments
+    double iI[3];          // 1 / Ip (0 for a zero moment)
+    double cI[3];          // (I_{l+1} - I_{l+2}) / I_l, Euler's equations
+    double qU[4];          // principal frame -> caller's body frame
+    double cpu[MAXCP][3];  // control points in the caller's body frame
+    double Iu[9];          // inertia in the caller's body frame
     double lo[3], hi[3];   // search box: AABB(cpw) -+ sqrt(sum K / c0)
     double brad;           // bounding radius about x (DEM broad phase)
     int ncp, fixed, pad0, pad1;
@@ -145,13 +181,35 @@ struct Params {
     int np, n_sub, vibb, missing_force;
     double tau, rho0, c0;
     double F[3], g[3], u0[3];
+    // collision constants precomputed on the host (FP64 arithmetic runs at a
+    // small fraction of the FP32 rate, so kernels take these ready-made)
+    double omega_d, gfac_d;   // 1/tau, 1 - 1/(2 tau)
+    double inv_n[3];          // 1/nx, 1/ny, 1/nz
+    float omega_f, gfac_f, rho0_f, c0_f;
+    float Ff[3];
     double kn, eta_n, kt, eta_t, mu_s, c_tol;
     void *fA;  // read (post-collision, time t)
     void *fB;  // write (post-collision, time t+1)
     uint16_t *flag_new;
     const uint16_t *flag_old;
-    uint8_t *occ_new;  // bricks of flag_new that hold solid nodes
-    const uint8_t *occ_old;
+    // Bricks whose flags need work: k_bin lists the bricks that gain a
+    // particle this step (list ring slot step % 3, stamp = step); k_flags
+    // visits the union of the lists of this step and the two before (solid
+    // nodes of the previous step's flags, and stale ones in the buffer being
+    // overwritten, lie only there).
+    int step;
+    int *wl_list;      // [3][nbricks]
+    int *wl_count;     // [3], ring of list lengths (slot step % 3 is written by k_flags)
+    int *stamp;        // [nbricks], last step the brick was listed
+    // Predicted near set of a step: the bricks within two nodes of the
+    // particles' search boxes of the step before (k_bin of that step scatters
+    // them).  The plain sweep skips these bricks; the near sweep covers them
+    // and the exactly listed ones, so a wrong prediction costs time only.
+    int *pred_stamp_cur;   // [nbricks], == step: predicted near this step
+    int *pred_stamp_next;  // [nbricks], written for step + 1 (NULL: no prediction)
+    int *pred_list_cur;    // [nbricks]
+    int *pred_list_next;   // [nbricks]
+    int *pred_count;       // [2], by step parity
     int *bcount;       // [nbricks]
     int *blist;        // [nbricks][MAXPB]
     double *partial;   // [nbricks][MAXPB][6]
@@ -169,10 +227,52 @@ struct Params {
 
 __host__ __device__ __forceinline__ int dim_of(const Params &P, int a) { return a == 0 ? P.nx : (a == 1 ? P.ny : P.nz); }
 
+// Scalar fields of Params from a configuration (host): lattice size, brick
+// grid, physics constants and their FP32 copies.  Pointers are left alone.
+inline void fill_scalar_params(const lbm_config &c, Params &P) {
+    P.nx = c.nx; P.ny = c.ny; P.nz = c.nz; P.Q = c.lattice;
+    for (int a = 0; a < 3; a++) P.per[a] = c.periodic[a] != 0;
+    P.N = (long long)c.nx * c.ny * c.nz;
+    P.nbx = (c.nx + BX - 1) / BX;
+    P.nby = (c.ny + BY - 1) / BY;
+    P.nbz = (c.nz + BZ - 1) / BZ;
+    P.nbricks = P.nbx * P.nby * P.nbz;
+    P.n_sub = c.n_sub; P.vibb = c.vibb; P.missing_force = c.missing_force;
+    P.tau = c.tau; P.rho0 = c.rho0; P.c0 = c.c0;
+    for (int a = 0; a < 3; a++) { P.F[a] = c.force[a]; P.g[a] = c.gravity[a]; P.u0[a] = c.u0[a]; }
+    P.kn = c.kn; P.eta_n = c.eta_n; P.kt = c.kt; P.eta_t = c.eta_t; P.mu_s = c.mu_s; P.c_tol = c.c_tol;
+    P.omega_d = 1.0 / c.tau;
+    P.gfac_d = 1.0 - 0.5 / c.tau;
+    P.inv_n[0] = 1.0 / c.nx;
+    P.inv_n[1] = 1.0 / c.ny;
+    P.inv_n[2] = 1.0 / c.nz;
+    P.omega_f = (float)P.omega_d;
+    P.gfac_f = (float)P.gfac_d;
+    P.rho0_f = (float)c.rho0;
+    P.c0_f = (float)c.c0;
+    for (int a = 0; a < 3; a++) P.Ff[a] = (float)c.force[a];
+}
+
+// Scalar parameters in the working precision C (float copies are made on the
+// host, so no FP64 arithmetic happens per node).
+template <typename C> struct Prm;
+template <> struct Prm<float> {
+    __device__ __forceinline__ static float rho0(const Params &P) { return P.rho0_f; }
+    __device__ __forceinline__ static float omega(const Params &P) { return P.omega_f; }
+    __device__ __forceinline__ static float gfac(const Params &P) { return P.gfac_f; }
+    __device__ __forceinline__ static float F(const Params &P, int a) { return P.Ff[a]; }
+};
+template <> struct Prm<double> {
+    __device__ __forceinline__ static double rho0(const Params &P) { return P.rho0; }
+    __device__ __forceinline__ static double omega(const Params &P) { return P.omega_d; }
+    __device__ __forceinline__ static double gfac(const Params &P) { return P.gfac_d; }
+    __device__ __forceinline__ static double F(const Params &P, int a) { return P.F[a]; }
+};
+
 __device__ __forceinline__ double minimg_d(const Params &P, int a, double d) {
     if (P.per[a]) {
-        double L = (double)dim_of(P, a);
-        d -= L * floor(d / L + 0.5);
+        const double L = (double)dim_of(P, a);
+        d -= L * floor(d * P.inv_n[a] + 0.5);
     }
     return d;
 }
@@ -187,12 +287,12 @@ struct BrickRange {
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
-__device__ __forceinline__ BrickRange brick_range(const Params &P, const DevParticle &p, int a) {
+__device__ __forceinline__ BrickRange brick_range(const Params &P, const DevParticle &p, int a, double grow = 1.0) {
     const int B = a == 0 ? BX : (a == 1 ? BY : BZ);
     const int nb = a == 0 ? P.nbx : (a == 1 ? P.nby : P.nbz);
     const int L = dim_of(P, a);
-    int nlo = (int)floor(p.lo[a] - 1.0 - 1e-6);
-    int nhi = (int)ceil(p.hi[a] + 1.0 + 1e-6);
+    int nlo = (int)floor(p.lo[a] - grow - 1e-6);
+    int nhi = (int)ceil(p.hi[a] + grow + 1e-6);
     BrickRange r;
     r.all = false;
     if (P.per[a]) {
@@ -267,8 +367,9 @@ struct SmemParticles {
 // Error budget: the control point's brick-relative position is rounded once
 // to FP32 (|error| <= 2^-24 times its magnitude, < 2^-16 for magnitudes
 // below 256), each difference along an axis is exact or rounded once, the
-// square sum and the division add 4 roundings; for distances r >= 1/2 each
-// term K/r^2 is off by at most 2^-13 relative, well inside the band.
+// square sum, the reciprocal and the product add 5 roundings; for distances
+// r >= 1/2 each term K/r^2 is off by at most 2^-13 relative, well inside the
+// band.
 __device__ __forceinline__ float metaball32(const Params &P, const SmemParticles &sp, int s, float lx, float ly,
                                             float lz, bool &unsure) {
     float M = 0.f;
@@ -283,9 +384,9 @@ __device__ __forceinline__ float metaball32(const Params &P, const SmemParticles
         if (P.per[2]) { if (dz > 0.5f * Lz) dz -= Lz; else if (dz < -0.5f * Lz) dz += Lz; }
         float r2 = dx * dx + dy * dy + dz * dz;
         close |= r2 < 0.25f;
-        M += sp.K[s][k] / r2;
+        M += sp.K[s][k] * __frcp_rn(r2);  // correctly rounded 1/r2, then one more rounding
     }
-    const float c0 = (float)P.c0;
+    const float c0 = P.c0_f;
     unsure = close || fabsf(M - c0) <= c0 * (1.0f / 4096.0f);
     return M;
 }
@@ -335,7 +436,8 @@ void launch_dem(const Params &P, cudaStream_t st);
 // instantiation per storage type in sweep_<type>.cu).
 template <typename S> void launch_init_t(const Params &P, void *f, cudaStream_t st);
 template <typename S> void launch_flags_t(const Params &P, cudaStream_t st);
-template <typename S> void launch_sweep_t(const Params &P, cudaStream_t st);
+template <typename S> void launch_sweep_plain_t(const Params &P, cudaStream_t st);
+template <typename S> void launch_sweep_near_t(const Params &P, cudaStream_t st);
 template <typename S>
 void launch_fields_t(const Params &P, const void *f, const uint16_t *flags, double *rho, double *u, uint16_t *fl,
                      cudaStream_t st);

@@ -6,7 +6,7 @@
 // a strict no-allocation policy once its steady state has started.  This
 // entry point classifies nodes for a set of particles with the same kernels
 // as lbm_step() (k_bin + k_flags), but keeps their scratch (particle table,
-// brick lists, per-brick occupancy, counters, status) in one file-scope
+// brick lists and work lists, counters, status) in one file-scope
 // __device__ array of fixed size instead of a caller workspace.  The caller
 // still passes the particles (host) and the output flag array (device).
 //
@@ -32,8 +32,9 @@ constexpr int kMaxDevices = 64;
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kOffBin = 0;                                                    // bcount + 4 counters
 constexpr size_t kOffList = align256(kOffBin + (size_t)(kMaxBricks + 4) * 4);    // brick lists
-constexpr size_t kOffOcc = align256(kOffList + (size_t)kMaxBricks * MAXPB * 4);  // two occupancy arrays
-constexpr size_t kOffStatus = align256(kOffOcc + 2 * (size_t)kMaxBricks);
+constexpr size_t kOffWork = align256(kOffList + (size_t)kMaxBricks * MAXPB * 4);  // work list ring, counts, stamps
+constexpr size_t kWorkBytes = (size_t)kMaxBricks * 4 * 4 + 3 * 4;
+constexpr size_t kOffStatus = align256(kOffWork + kWorkBytes);
 constexpr size_t kOffParts = align256(kOffStatus + ST_SLOTS * 4);
 constexpr size_t kScratchBytes = align256(kOffParts + (size_t)kMaxParticles * sizeof(DevParticle));
 
@@ -94,10 +95,11 @@ extern "C" int lbm_flags_noalloc(const lbm_config *cfg, const lbm_particle *host
     cudaError_t e = cudaSuccess;
     if (n > 0) e = cudaMemcpyAsync(base + kOffParts, g_host_parts, sizeof(DevParticle) * (size_t)n,
                                    cudaMemcpyHostToDevice, st);
-    // what must start at zero: brick counts and counters, occupancy, status,
-    // and the output (bricks without particles are never written)
+    // what must start at zero: brick counts and counters, work lists and
+    // stamps, status, and the output (bricks without particles are never
+    // written)
     if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffBin, 0, (size_t)(nbricks + 4) * 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffOcc, 0, 2 * (size_t)kMaxBricks, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffWork, 0, kWorkBytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffStatus, 0, ST_SLOTS * 4, st);
     const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
     if (e == cudaSuccess) e = cudaMemsetAsync(dev_flags, 0, (size_t)N * 2, st);
@@ -105,17 +107,15 @@ extern "C" int lbm_flags_noalloc(const lbm_config *cfg, const lbm_particle *host
 
     Params P;
     std::memset(&P, 0, sizeof(P));
-    P.nx = cfg->nx; P.ny = cfg->ny; P.nz = cfg->nz; P.Q = cfg->lattice;
-    for (int a = 0; a < 3; a++) P.per[a] = cfg->periodic[a] != 0;
-    P.N = N;
-    P.nbx = nbx; P.nby = nby; P.nbz = nbz; P.nbricks = (int)nbricks;
+    fill_scalar_params(*cfg, P);
     P.np = n;
-    P.tau = cfg->tau; P.rho0 = cfg->rho0; P.c0 = cfg->c0;
     P.bcount = reinterpret_cast<int *>(base + kOffBin);
     P.counters = reinterpret_cast<int *>(base + kOffBin + (size_t)nbricks * 4);
     P.blist = reinterpret_cast<int *>(base + kOffList);
-    P.occ_new = reinterpret_cast<uint8_t *>(base + kOffOcc);
-    P.occ_old = reinterpret_cast<uint8_t *>(base + kOffOcc + kMaxBricks);
+    P.step = 0;  // a single classification: only this step's list
+    P.wl_list = reinterpret_cast<int *>(base + kOffWork);
+    P.stamp = reinterpret_cast<int *>(base + kOffWork + (size_t)kMaxBricks * 3 * 4);
+    P.wl_count = reinterpret_cast<int *>(base + kOffWork + (size_t)kMaxBricks * 4 * 4);
     P.status = reinterpret_cast<int *>(base + kOffStatus);
     P.parts = reinterpret_cast<DevParticle *>(base + kOffParts);
     // the output doubles as the "previous" flags: every node of it reads back

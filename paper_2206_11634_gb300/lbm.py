@@ -250,7 +250,7 @@ class Lattice:
     def check(self) -> None:
         self._ok(self.L.lbm_check(self.h), self.h)
 
-    KERNELS = ("k_bin", "k_flags", "k_sweep", "k_force_reduce", "k_dem")
+    KERNELS = ("k_bin", "k_flags", "k_sweep_plain", "k_sweep_near", "k_force_reduce", "k_dem")
 
     def profile(self, enable: bool = True) -> None:
         self._ok(self.L.lbm_profile(self.h, int(enable)), self.h)
