@@ -375,6 +375,53 @@ __device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z,
     collide_store<S, Q, kForce>(P, fin, B, N, n);
 }
 
+// The unknown of one particle link, computed by any lane of the warp: the
+// node (brick-local lx,ly,lz) loads its own post-collision populations and
+// moments, then the link is evaluated as in particle_link.
+template <typename S, int Q>
+__device__ __noinline__ typename Codec<S>::C link_coop(const Params &P, const SmemParticles &sp, int i, int lx, int ly,
+                                                      int lz, int bx0, int by0, int bz0,
+                                                      typename Codec<S>::C (*acc)[6]) {
+    using L = Lat<Q>;
+    using Cd = Codec<S>;
+    using C = typename Cd::C;
+    const int x = bx0 + lx, y = by0 + ly, z = bz0 + lz;
+    const int n = x + P.nx * (y + P.ny * z);
+    const S *A = (const S *)P.fA;
+    const long long N = P.N;
+    const C rho0 = Prm<C>::rho0(P);
+    C fown[Q];
+    C rho_f = 0, m_f[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < Q; k++) {
+        fown[k] = Cd::ld(A + (long long)k * N + n, (C)L::w(k), rho0);
+        rho_f += fown[k];
+        m_f[0] += fown[k] * L::e(k, 0);
+        m_f[1] += fown[k] * L::e(k, 1);
+        m_f[2] += fown[k] * L::e(k, 2);
+    }
+    C u_f[3];
+    const C inv_rho_f = C(1) / rho_f;
+    for (int a = 0; a < 3; a++) u_f[a] = (m_f[a] - C(0.5) * Prm<C>::F(P, a)) * inv_rho_f;
+    // the solid source x - e_i (inside the domain: the link exists)
+    int sx = x - lat_e<Q>(i, 0), sy = y - lat_e<Q>(i, 1), sz = z - lat_e<Q>(i, 2);
+    if (sx < 0) sx += P.nx; else if (sx >= P.nx) sx -= P.nx;
+    if (sy < 0) sy += P.ny; else if (sy >= P.ny) sy -= P.ny;
+    if (sz < 0) sz += P.nz; else if (sz >= P.nz) sz -= P.nz;
+    C Mf_cache = 0;
+    int Mf_slot = -1;
+    return particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, sx + P.nx * (sy + P.ny * sz), fown,
+                               rho_f, u_f, acc, &Mf_cache, &Mf_slot);
+}
+
+// Shared scratch of the warp-cooperative link evaluation: per warp a queue of
+// (lane, direction) link entries and their results.
+constexpr int kLinkQueue = 32 * 18;
+struct LinkScratch {
+    unsigned short entry[BRICK / 32][kLinkQueue];
+    float result[BRICK / 32][kLinkQueue];
+};
+
 // A fluid node with at least one particle link, in a brick some particle
 // reaches: pull, walls, VIBB / halfway bounce-back on the particle links with
 // their momentum exchange, collide, store.
@@ -439,12 +486,13 @@ __device__ __noinline__ void boundary_node(const Params &P, const SmemParticles 
 // path (plus 19 flag reads); boundary and solid nodes go out of line; then
 // the deterministic reduction of the per-particle terms.
 template <typename S, int Q, bool kForce>
-__device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, double (*red)[6], int *s_links, int b,
-                                        int bx0, int by0, int bz0, int cnt) {
+__device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, double (*red)[6], int *s_links,
+                                        LinkScratch *ls, int b, int bx0, int by0, int bz0, int cnt) {
     using L = Lat<Q>;
     using Cd = Codec<S>;
     using C = typename Cd::C;
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int lx = tid % BX, ly = (tid / BX) % BY, lz = tid / (BX * BY);
     const int x = bx0 + lx, y = by0 + ly, z = bz0 + lz;
     const bool active = x < P.nx && y < P.ny && z < P.nz;
@@ -459,26 +507,68 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
         for (int c = 0; c < 6; c++) acc[s][c] = 0;
     int nlinks = 0;
 
-    if (active) {
-        const uint16_t fl = P.flag_new[n];
-        if (fl != 0) {
-            if (P.missing_force) solid_node<S, Q>(P, sp, x, y, z, lx, ly, lz, bx0, by0, bz0, fl - 1, acc);
-        } else {
-            int xs[3], ys[3], zs[3];
-            neighbour_coords(P, x, y, z, xs, ys, zs);
-            bool linked = false;
-            C fin[Q];
+    const uint16_t fl = active ? P.flag_new[n] : (uint16_t)1;
+    const bool fluid = active && fl == 0;
+    if (active && fl != 0 && P.missing_force)
+        solid_node<S, Q>(P, sp, x, y, z, lx, ly, lz, bx0, by0, bz0, fl - 1, acc);
+
+    C fin[Q];
+    uint32_t links = 0;
+    if (fluid) {
+        int xs[3], ys[3], zs[3];
+        neighbour_coords(P, x, y, z, xs, ys, zs);
 #pragma unroll
-            for (int i = 0; i < Q; i++) {
-                const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
-                const bool wall = (sx | sy | sz) < 0;
-                const int src = wall ? n : sx + P.nx * (sy + P.ny * sz);
-                if (!wall) linked |= P.flag_new[src] != 0;
-                const S *ptr = wall ? A + (long long)L::opp(i) * N + n : A + (long long)i * N + src;
-                fin[i] = Cd::ld(ptr, (C)L::w(i), rho0);
+        for (int i = 0; i < Q; i++) {
+            const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
+            const bool wall = (sx | sy | sz) < 0;
+            const int src = wall ? n : sx + P.nx * (sy + P.ny * sz);
+            if (!wall && P.flag_new[src] != 0) links |= 1u << i;
+            const S *ptr = wall ? A + (long long)L::opp(i) * N + n : A + (long long)i * N + src;
+            fin[i] = Cd::ld(ptr, (C)L::w(i), rho0);
+        }
+    }
+    if (sizeof(C) == 8) {
+        // FP64 storage: every node evaluates its own links
+        if (links) boundary_node<S, Q, kForce>(P, sp, x, y, z, lx, ly, lz, bx0, by0, bz0, n, acc, &nlinks);
+        else if (fluid) collide_store<S, Q, kForce>(P, fin, B, N, n);
+    } else {
+        // the warp's links in a queue (lane order, then direction order);
+        // all 32 lanes evaluate them, then each node takes its results back
+        const int mine = __popc(links);
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int first = incl - mine;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        {
+            uint32_t m = links;
+            for (int k = first; m; k++) {
+                const int i = __ffs(m) - 1;
+                m &= m - 1;
+                ls->entry[warp][k] = (unsigned short)((lane << 5) | i);
             }
-            if (!linked) collide_store<S, Q, kForce>(P, fin, B, N, n);
-            else boundary_node<S, Q, kForce>(P, sp, x, y, z, lx, ly, lz, bx0, by0, bz0, n, acc, &nlinks);
+        }
+        __syncwarp();
+        for (int e = lane; e < total; e += 32) {
+            const int ent = ls->entry[warp][e];
+            const int L_ = ent >> 5, i = ent & 31;
+            const int t = warp * 32 + L_;  // the node's thread index in the brick
+            ls->result[warp][e] = (float)link_coop<S, Q>(P, sp, i, t % BX, (t / BX) % BY, t / (BX * BY), bx0, by0,
+                                                         bz0, acc);
+            nlinks++;
+        }
+        __syncwarp();
+        if (fluid) {
+            if (links) {
+                int k = first;
+#pragma unroll
+                for (int i = 1; i < Q; i++)
+                    if (links & (1u << i)) fin[i] = (C)ls->result[warp][k++];
+            }
+            collide_store<S, Q, kForce>(P, fin, B, N, n);
         }
     }
 
@@ -529,6 +619,7 @@ __global__ void __launch_bounds__(BRICK, 4) k_sweep_near(Params P) {
     __shared__ SmemParticles sp;
     __shared__ double red[BRICK / 32][6];
     __shared__ int s_links;
+    __shared__ LinkScratch ls;
     const int tid = threadIdx.x;
     const int t = P.step;
     const int c_exact = P.counters[CNT_LISTED];
@@ -553,7 +644,7 @@ __global__ void __launch_bounds__(BRICK, 4) k_sweep_near(Params P) {
         }
         if (tid == 0) s_links = 0;
         load_smem_particles(P, sp, b, bx0, by0, bz0);
-        near_brick<S, Q, kForce>(P, sp, red, &s_links, b, bx0, by0, bz0, cnt);
+        near_brick<S, Q, kForce>(P, sp, red, &s_links, &ls, b, bx0, by0, bz0, cnt);
     }
 }
 
