@@ -84,6 +84,12 @@ typedef struct lbm_config {
     int32_t vibb;              /* 1 = VIBB on particle links; 0 = halfway bounce-back on all of them */
     int32_t missing_force;     /* 1 = add the missing-force-point terms of §2.3.5 item 2 */
     int32_t max_particles;     /* capacity reserved in the workspace, >= 1 */
+    int32_t dem_fp64;          /* 1 = DEM in FP64 arithmetic for every storage.  0 = FP64 for FP64
+                                  storage; for FP32/FP16/BF16 storage the DEM computes in FP32 with
+                                  the rigid-body state kept as compensated FP32 pairs (about 48
+                                  significant bits), when n <= 256 and the particles' control points
+                                  number <= 2048 in all, else in FP64 */
+    int32_t reserved0;         /* 0 */
     double tau;                /* BGK relaxation time, > 1/2 */
     double rho0;               /* reference density (initial fluid, refill, Eq. (31)) */
     double c0;                 /* surface value of M (Eq. (26)); 1 for the metaball of Eq. (4) */
@@ -141,14 +147,25 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n);
  * particle kernels and the sweep of the bricks particles reach, a
  * low-priority one for the sweep of all other bricks), forked from and joined
  * back into the handle's stream with events inside this call, so the call as
- * a whole is ordered on the handle's stream (and can be captured into a CUDA
- * graph from it). */
+ * a whole is ordered on the handle's stream.  Step numbers and buffer parity
+ * are kept on the host and passed to the kernels, so a CUDA graph captured
+ * from the handle's stream repeats the captured steps' numbers when replayed:
+ * do not replay one. */
 int lbm_step(lbm_handle *h, int nsteps);
 
 /* Synchronise and copy out the hydrodynamic force and torque of the last
  * step (F, T: host double[n][3], either may be NULL) and, if state_out is not
  * NULL, the current particle states (host lbm_particle[n]). */
 int lbm_get_forces(lbm_handle *h, double *F, double *T, lbm_particle *state_out);
+
+/* Synchronise and copy out the contact force and torque (Eqs. (2)-(3), pair
+ * and wall terms summed per particle, world frame, torque about the centre)
+ * in the current state, i.e. after the last step, with the tangential springs
+ * as they stand: the contact load the next step starts from (F, T: host
+ * double[n][3], either may be NULL).  Zero before the first step after
+ * lbm_set_particles() and whenever no contact could occur during the last
+ * step. */
+int lbm_get_contact_forces(lbm_handle *h, double *F, double *T);
 
 /* Synchronise and write the macroscopic fields of the stored populations to
  * caller device buffers (any may be NULL): dev_rho double[nz][ny][nx],

@@ -1227,6 +1227,10 @@ void orc_get_forces(const orc_state *s, double *F, double *T) {
             T[3 * j + a] = s->Th[j][a];
         }
 }
+/* Contact load of the current state (springs not advanced): the load the
+ * next DEM step starts from.  Re-evaluating it leaves the state as the next
+ * step's first evaluation would (the same geometry, an idempotent projection
+ * of the springs onto the tangent plane). */
 void orc_get_contact_forces(orc_state *s, double *F, double *T) {
     update_world_cps(s);
     contacts(s, 0.0);

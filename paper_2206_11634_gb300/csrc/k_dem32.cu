@@ -1,0 +1,747 @@
+// k_dem32: the DEM of §2.3.4 for lattices stored in FP32 or below.
+//
+// On this GPU an FP64 warp instruction occupies its SM sub-partition for 64
+// cycles whether or not its lanes depend on one another (measured with
+// clock64: dependent and independent FP64 FMAs alike; FP64 division ~560
+// cycles, square root ~680, an FP64<->FP32 conversion ~100), against ~5
+// cycles for a dependent FP32 FMA.  The n_s sub-steps of an LBM step are one
+// serial chain, so this kernel computes them in FP32:
+// - the rigid-body state (x, v, q and the principal-frame angular velocity)
+//   is kept as compensated pairs hi + lo (Knuth's two-sum, renormalised), so
+//   the state carries ~48 significant bits, while each increment is computed
+//   in FP32 from the leading words (relative error ~6e-8 of an increment of
+//   size ~h |v|);
+// - the contact geometry of Eqs. (5)-(13) is solved by Newton iterations in
+//   FP32 in a frame centred on the particle, where coordinates are O(radius),
+//   so the overlap delta carries an absolute error of ~1e-6 lu;
+// - contact forces are summed per particle in the order of the FP64 path:
+//   pairs (m, k) by ascending m, pairs (k, m) by ascending m, walls 0..5.
+// The sub-step sequence is that of k_dem: contact forces at the start, then
+// per sub-step the first half-kick and drift, the rotation q <- q (x) exp(h
+// w/2), the contacts at the new positions, the closing half-kick (implicit in
+// w).  Candidate pairs come from a Verlet list (bounding spheres closer than a
+// skin), rebuilt when a particle has moved half the skin since.
+#include "lbm_internal.cuh"
+
+namespace lbmmb {
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kMaxP = kDem32MaxParticles;
+constexpr int kMaxAdj = kDemMaxAdj;
+constexpr int kWords = kMaxP / 32;
+constexpr float kSkin = 1.0f;
+
+// ---------------------------------------------------------------------------
+// compensated scalar
+// ---------------------------------------------------------------------------
+struct DF { float hi, lo; };
+__device__ __forceinline__ DF df_load(const float s[2]) { return {s[0], s[1]}; }
+__device__ __forceinline__ void df_store(float s[2], DF a) { s[0] = a.hi; s[1] = a.lo; }
+// a + b: two-sum of hi and b, error and lo folded into the new low word
+__device__ __forceinline__ DF df_add(DF a, float b) {
+    const float s = __fadd_rn(a.hi, b);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    const float lo = __fadd_rn(a.lo, e);
+    const float hi = __fadd_rn(s, lo);
+    return {hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+// the leading word after adding b (what the increments downstream use)
+__device__ __forceinline__ float df_lead(DF a, float b) { return __fadd_rn(a.hi, b); }
+
+// ---------------------------------------------------------------------------
+// FP32 vector helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float dot3f(const float a[3], const float b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+__device__ __forceinline__ void cross3f(const float a[3], const float b[3], float c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+// R(q) v (to_world) or R(q)^T v: v + 2(+-w c + u x c), c = u x v
+__device__ __forceinline__ void qrot_f(const float q[4], const float v[3], float r[3], bool to_world) {
+    const float u[3] = {q[1], q[2], q[3]};
+    float c[3], uc[3];
+    cross3f(u, v, c);
+    cross3f(u, c, uc);
+    const float s = to_world ? q[0] : -q[0];
+    for (int a = 0; a < 3; a++) r[a] = v[a] + 2.0f * fmaf(s, c[a], uc[a]);
+}
+// Euler's equations, principal frame
+__device__ __forceinline__ void euler_f(const float iI[3], const float cI[3], const float w[3], const float T[3],
+                                        float out[3]) {
+    out[0] = fmaf(cI[0] * w[1], w[2], iI[0] * T[0]);
+    out[1] = fmaf(cI[1] * w[2], w[0], iI[1] * T[1]);
+    out[2] = fmaf(cI[2] * w[0], w[1], iI[2] * T[2]);
+}
+__device__ __forceinline__ float minimg_f(const Params &P, int a, float d) {
+    if (P.per[a]) d -= P.dim_f[a] * rintf(d * P.inv_n_f[a]);
+    return d;
+}
+
+// exp(h w / 2) as (cos - 1, sin(|a|)/|a| * h/2): a = h w / 2
+__device__ __forceinline__ void exp_half(float hh, float qh2, const float w[3], float &cm1, float &sc) {
+    const float a2 = qh2 * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    if (a2 <= 1.0f / 256.0f) {
+        sc = hh * (1.0f + a2 * (-1.0f / 6.0f + a2 * (1.0f / 120.0f)));
+        cm1 = a2 * (-0.5f + a2 * (1.0f / 24.0f + a2 * (-1.0f / 720.0f)));
+    } else {
+        const float an = sqrtf(a2);
+        float sn, cs;
+        sincosf(an, &sn, &cs);
+        const float s2 = sinf(0.5f * an);
+        sc = hh * sn / an;
+        cm1 = -2.0f * s2 * s2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// shared tables
+// ---------------------------------------------------------------------------
+struct Shared {
+    float xh[kMaxP][3], xl[kMaxP][3];   // position, compensated
+    float v[kMaxP][3];                  // velocity (world)
+    float w[kMaxP][3];                  // angular velocity (world)
+    float xref[kMaxP][3];               // position at the last list build
+    float Fc[kMaxP][3], Tc[kMaxP][3];   // contact force / torque of the last evaluation
+    float rc[kDem32MaxCp][3];           // control points R(q) cpb, relative to x
+    int cpo[kMaxP + 1];                 // offsets into rc
+    unsigned bits[kMaxP][kWords];       // candidate pairs (i < j)
+    unsigned short up[kMaxP][kMaxAdj];  // partners j > i, ascending
+    int dn[kMaxP][kMaxAdj];             // (m << 8 | slot of k in up[m]), m < k, ascending
+    int nup[kMaxP], ndn[kMaxP];
+    int ioff[kMaxP + 1];                // prefix sums of nup (pair items)
+    float reach[kMaxP];
+};
+
+__device__ __forceinline__ void rel_vec(const Shared &S, const Params &P, int i, int j, float d[3]) {
+    for (int a = 0; a < 3; a++)
+        d[a] = minimg_f(P, a, (S.xh[j][a] - S.xh[i][a]) + (S.xl[j][a] - S.xl[i][a]));
+}
+
+// M, grad M and Hessian (xx yy zz xy xz yz) of one metaball at y, control
+// points at rc + off
+__device__ void mb_dd_f(const float (*rc)[3], const float *K, int ncp, const float off[3], const float y[3], float &M,
+                        float g[3], float H[6]) {
+    M = 0.f;
+    for (int a = 0; a < 3; a++) g[a] = 0.f;
+    for (int a = 0; a < 6; a++) H[a] = 0.f;
+    for (int c = 0; c < ncp; c++) {
+        const float r0 = y[0] - (rc[c][0] + off[0]), r1 = y[1] - (rc[c][1] + off[1]), r2_ = y[2] - (rc[c][2] + off[2]);
+        const float r2 = r0 * r0 + r1 * r1 + r2_ * r2_;
+        const float ir = __frcp_rn(r2);
+        const float Kr = K[c] * ir;          // K / r^2
+        const float a1 = -2.0f * Kr * ir;    // -2 K / r^4
+        const float a2 = 8.0f * Kr * ir * ir;  // 8 K / r^6
+        M += Kr;
+        g[0] = fmaf(a1, r0, g[0]);
+        g[1] = fmaf(a1, r1, g[1]);
+        g[2] = fmaf(a1, r2_, g[2]);
+        H[0] += fmaf(a2 * r0, r0, a1);
+        H[1] += fmaf(a2 * r1, r1, a1);
+        H[2] += fmaf(a2 * r2_, r2_, a1);
+        H[3] = fmaf(a2 * r0, r1, H[3]);
+        H[4] = fmaf(a2 * r0, r2_, H[4]);
+        H[5] = fmaf(a2 * r1, r2_, H[5]);
+    }
+}
+
+// Contact law of §2.1.1 (Eqs. (2)-(3)) in FP32; xi: tangential spring.
+__device__ void contact_law_f(const Params &P, float delta, const float n[3], const float vij[3], float xi[3], float h,
+                              float F[3]) {
+    const float vn = dot3f(vij, n);
+    float Fn = P.kn_f * delta - P.eta_n_f * vn;
+    if (Fn < 0.f) Fn = 0.f;
+    float vt[3];
+    for (int a = 0; a < 3; a++) vt[a] = vij[a] - vn * n[a];
+    const float xn = dot3f(xi, n);
+    for (int a = 0; a < 3; a++) xi[a] = xi[a] - xn * n[a] + vt[a] * h;
+    float Ft[3];
+    for (int a = 0; a < 3; a++) Ft[a] = -P.kt_f * xi[a] - P.eta_t_f * vt[a];
+    const float ft = sqrtf(dot3f(Ft, Ft));
+    if (ft > P.mu_s_f * Fn) {
+        const float sc = ft > 0.f ? P.mu_s_f * Fn * __frcp_rn(ft) : 0.f;
+        for (int a = 0; a < 3; a++) {
+            Ft[a] *= sc;
+            xi[a] = -(Ft[a] + P.eta_t_f * vt[a]) * P.inv_kt_f;
+        }
+    }
+    for (int a = 0; a < 3; a++) F[a] = Fn * n[a] + Ft[a];
+}
+
+// Pair geometry, Eqs. (5)-(9), in the frame centred on particle i (d = x_j -
+// x_i).  Same steps as the FP64 path: Newton on grad(M_i + M_j) = 0, valid
+// when c_tol < M < 1 for both, closest points by the first-order step, contact
+// point in the middle of the overlap.
+__device__ bool pair_geom_f(const Params &P, const Shared &S, const DevParticle &pi, const DevParticle &pj, int i,
+                            int j, const float d[3], bool warm, float xm[3], float &delta, float nv[3], float xcp[3]) {
+    const float(*rci)[3] = S.rc + S.cpo[i];
+    const float(*rcj)[3] = S.rc + S.cpo[j];
+    const float zero[3] = {0.f, 0.f, 0.f};
+    float x[3];
+    if (warm) {
+        for (int a = 0; a < 3; a++) x[a] = xm[a];
+    } else {
+        float best = 3.4e38f;
+        x[0] = x[1] = x[2] = 0.f;
+        for (int a = 0; a < pi.ncp; a++)
+            for (int b = 0; b < pj.ncp; b++) {
+                float dd[3];
+                for (int c = 0; c < 3; c++) dd[c] = (d[c] + rcj[b][c]) - rci[a][c];
+                const float d2 = dot3f(dd, dd);
+                if (d2 < best) {
+                    best = d2;
+                    for (int c = 0; c < 3; c++) x[c] = rci[a][c] + 0.5f * dd[c];
+                }
+            }
+    }
+    float M0, g0[3], H0[6], M1, g1[3], H1[6];
+    for (int it = 0; it < 30; it++) {
+        mb_dd_f(rci, pi.K_f, pi.ncp, zero, x, M0, g0, H0);
+        mb_dd_f(rcj, pj.K_f, pj.ncp, d, x, M1, g1, H1);
+        float H[6], g[3];
+        for (int a = 0; a < 6; a++) H[a] = H0[a] + H1[a];
+        for (int a = 0; a < 3; a++) g[a] = -(g0[a] + g1[a]);
+        // symmetric 3x3 solve by cofactors
+        const float c0 = H[1] * H[2] - H[5] * H[5];
+        const float c1 = H[5] * H[4] - H[3] * H[2];
+        const float c2 = H[3] * H[5] - H[1] * H[4];
+        const float det = H[0] * c0 + H[3] * c1 + H[4] * c2;
+        if (det == 0.f || !isfinite(det)) break;
+        const float id = __frcp_rn(det);
+        const float b01 = H[4] * H[5] - H[3] * H[2], b02 = H[3] * H[5] - H[4] * H[1];
+        const float b11 = H[0] * H[2] - H[4] * H[4], b12 = H[4] * H[3] - H[0] * H[5];
+        const float b22 = H[0] * H[1] - H[3] * H[3];
+        float dx[3];
+        dx[0] = (c0 * g[0] + b01 * g[1] + b02 * g[2]) * id;
+        dx[1] = (c1 * g[0] + b11 * g[1] + b12 * g[2]) * id;
+        dx[2] = (c2 * g[0] + b12 * g[1] + b22 * g[2]) * id;
+        for (int a = 0; a < 3; a++) x[a] += dx[a];
+        if (dot3f(dx, dx) < 1e-10f) break;
+    }
+    for (int a = 0; a < 3; a++) xm[a] = x[a];
+    mb_dd_f(rci, pi.K_f, pi.ncp, zero, x, M0, g0, H0);
+    mb_dd_f(rcj, pj.K_f, pj.ncp, d, x, M1, g1, H1);
+    if (!(M0 > P.c_tol_f && M0 < 1.0f && M1 > P.c_tol_f && M1 < 1.0f)) return false;
+    const float q0 = (1.0f - M0) * __frcp_rn(dot3f(g0, g0)), q1 = (1.0f - M1) * __frcp_rn(dot3f(g1, g1));
+    float dc[3];
+    for (int a = 0; a < 3; a++) dc[a] = q0 * g0[a] - q1 * g1[a];
+    const float dist = sqrtf(dot3f(dc, dc));
+    delta = pi.Rs_f + pj.Rs_f - dist;
+    if (!(delta > 0.f) || dist == 0.f) return false;
+    const float idist = __frcp_rn(dist);
+    for (int a = 0; a < 3; a++) {
+        nv[a] = dc[a] * idist;
+        xcp[a] = (x[a] + q0 * g0[a]) - (pi.Rs_f - 0.5f * delta) * nv[a];
+    }
+    return true;
+}
+
+// Wall geometry, Eqs. (10)-(13), frame centred on the particle; prel: the
+// wall plane's coordinate relative to x along its axis.
+__device__ bool wall_geom_f(const Params &P, const Shared &S, const DevParticle &p, int k, int wall, float prel,
+                            bool warm, float xcw[3], float &delta, float nv[3], float xcp[3]) {
+    const int ax = wall / 2, side = wall % 2;
+    const float m_ax = side ? 1.0f : -1.0f;
+    const int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+    const float(*rc)[3] = S.rc + S.cpo[k];
+    const float zero[3] = {0.f, 0.f, 0.f};
+    float x[3];
+    if (warm) {
+        for (int a = 0; a < 3; a++) x[a] = xcw[a];
+    } else {
+        int kb = 0;
+        float best = 3.4e38f;
+        for (int c = 0; c < p.ncp; c++) {
+            const float dd = fabsf(prel - rc[c][ax]);
+            if (dd < best) { best = dd; kb = c; }
+        }
+        for (int a = 0; a < 3; a++) x[a] = rc[kb][a];
+    }
+    x[ax] = prel;
+    // H index of (a, b)
+    auto hidx = [](int a, int b) { return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5)); };
+    const int i11 = hidx(t1, t1), i12 = hidx(t1, t2), i22 = hidx(t2, t2);
+    float M, g[3], H[6];
+    for (int it = 0; it < 30; it++) {
+        mb_dd_f(rc, p.K_f, p.ncp, zero, x, M, g, H);
+        const float J00 = H[i11], J01 = H[i12], J11 = H[i22];
+        const float det = J00 * J11 - J01 * J01;
+        if (det == 0.f || !isfinite(det)) break;
+        const float id = __frcp_rn(det);
+        const float r0 = -g[t1], r1 = -g[t2];
+        const float d0 = (J11 * r0 - J01 * r1) * id, d1 = (-J01 * r0 + J00 * r1) * id;
+        x[t1] += d0;
+        x[t2] += d1;
+        if (d0 * d0 + d1 * d1 < 1e-10f) break;
+    }
+    for (int a = 0; a < 3; a++) xcw[a] = x[a];
+    mb_dd_f(rc, p.K_f, p.ncp, zero, x, M, g, H);
+    if (!(g[ax] * m_ax < 0.f)) return false;
+    const float qR = (1.0f - M) * __frcp_rn(dot3f(g, g));
+    float dc[3];
+    for (int a = 0; a < 3; a++) dc[a] = qR * g[a];
+    const float dist = sqrtf(dot3f(dc, dc));
+    delta = p.Rs_f - dist;
+    if (!(delta > 0.f) || dist == 0.f) return false;
+    const float idist = __frcp_rn(dist);
+    for (int a = 0; a < 3; a++) {
+        nv[a] = dc[a] * idist;
+        xcp[a] = x[a] - 0.5f * delta * nv[a];
+    }
+    return true;
+}
+
+// Candidate pairs: bounding spheres closer than the skin.  Pairs that drop
+// out lose their contact history, as in the FP64 path.  Sets *possible when
+// some pair is within reach of a contact this step (or one is active).
+__device__ void build_lists(const Params &P, Shared &S, int *possible) {
+    const int np = P.np, tid = threadIdx.x;
+    const int nw = (np + 31) / 32;
+    for (int idx = tid; idx < np * nw; idx += blockDim.x) {
+        const int i = idx / nw, wd = idx % nw;
+        unsigned m = 0;
+        const float bri = P.parts[i].brad_f, ri = S.reach[i];
+        for (int b = 0; b < 32; b++) {
+            const int j = wd * 32 + b;
+            if (j <= i || j >= np) continue;
+            float d[3];
+            rel_vec(S, P, i, j, d);
+            const float d2 = dot3f(d, d);
+            const float brs = bri + P.parts[j].brad_f;
+            const float lim = brs + kSkin;
+            const bool on = P.pair_on[i * np + j] != 0;
+            if (d2 < lim * lim) {
+                m |= 1u << b;
+                const float lr = brs + ri + S.reach[j] + 1e-2f;
+                if (on || d2 <= lr * lr) *possible = 1;
+            } else if (on) {
+                P.pair_on[i * np + j] = 0;
+                *possible = 1;
+            }
+        }
+        S.bits[i][wd] = m;
+    }
+    for (int k = tid; k < np; k += blockDim.x) S.ndn[k] = 0;
+    __syncthreads();
+    for (int i = tid; i < np; i += blockDim.x) {
+        int n = 0;
+        for (int wd = 0; wd < nw; wd++) {
+            unsigned m = S.bits[i][wd];
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const int j = wd * 32 + b;
+                if (n < kMaxAdj) {
+                    S.up[i][n] = (unsigned short)j;
+                    const int pos = atomicAdd(&S.ndn[j], 1);
+                    if (pos < kMaxAdj) S.dn[j][pos] = (i << 8) | n;
+                    else atomicOr(&P.status[ST_ERR], ERRB_DEM_CAPACITY);
+                    n++;
+                } else {
+                    atomicOr(&P.status[ST_ERR], ERRB_DEM_CAPACITY);
+                }
+            }
+        }
+        S.nup[i] = n;
+    }
+    __syncthreads();
+    for (int k = tid; k < np; k += blockDim.x) {
+        const int n = min(S.ndn[k], kMaxAdj);
+        S.ndn[k] = n;
+        for (int a = 1; a < n; a++) {  // ascending m
+            const int e = S.dn[k][a];
+            int b = a - 1;
+            while (b >= 0 && S.dn[k][b] > e) { S.dn[k][b + 1] = S.dn[k][b]; b--; }
+            S.dn[k][b + 1] = e;
+        }
+        for (int a = 0; a < 3; a++) S.xref[k][a] = S.xh[k][a] + S.xl[k][a];
+    }
+    if (tid == 0) {
+        int o = 0;
+        for (int i = 0; i < np; i++) { S.ioff[i] = o; o += S.nup[i]; }
+        S.ioff[np] = o;
+    }
+    __syncthreads();
+}
+
+// Pair contacts of the candidate list (one item per thread); results into
+// dem_res[i][slot] (zeros when not in contact).
+__device__ void pair_contacts(const Params &P, Shared &S, float h) {
+    const int np = P.np;
+    const int total = S.ioff[np];
+    for (int it = threadIdx.x; it < total; it += blockDim.x) {
+        int lo = 0, hi = np - 1;  // item -> (i, slot): last i with ioff[i] <= it
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (S.ioff[mid] <= it) lo = mid; else hi = mid - 1;
+        }
+        const int i = lo, s = it - S.ioff[i], j = S.up[i][s];
+        float *out = P.dem_res + ((size_t)i * kMaxAdj + s) * 9;
+        const DevParticle &pi = P.parts[i], &pj = P.parts[j];
+        const int pidx = i * np + j;
+        float d[3];
+        rel_vec(S, P, i, j, d);
+        const float brs = pi.brad_f + pj.brad_f;
+        float Fi[3] = {0.f, 0.f, 0.f}, ti[3] = {0.f, 0.f, 0.f}, tj[3] = {0.f, 0.f, 0.f};
+        if (dot3f(d, d) > brs * brs) {
+            P.pair_on[pidx] = 0;
+        } else {
+            const bool warm = P.pair_on[pidx] != 0;
+            float xm[3], delta, nv[3], xcp[3];
+            for (int a = 0; a < 3; a++) xm[a] = P.pair_xm_f[3 * pidx + a];
+            if (!pair_geom_f(P, S, pi, pj, i, j, d, warm, xm, delta, nv, xcp)) {
+                P.pair_on[pidx] = 0;
+            } else {
+                float xi[3];
+                for (int a = 0; a < 3; a++) xi[a] = warm ? P.pair_xi_f[3 * pidx + a] : 0.f;
+                P.pair_on[pidx] = 1;
+                for (int a = 0; a < 3; a++) P.pair_xm_f[3 * pidx + a] = xm[a];
+                float rj[3], wri[3], wrj[3], vij[3];
+                for (int a = 0; a < 3; a++) rj[a] = xcp[a] - d[a];
+                cross3f(S.w[i], xcp, wri);
+                cross3f(S.w[j], rj, wrj);
+                for (int a = 0; a < 3; a++) vij[a] = (S.v[i][a] + wri[a]) - (S.v[j][a] + wrj[a]);
+                contact_law_f(P, delta, nv, vij, xi, h, Fi);
+                for (int a = 0; a < 3; a++) P.pair_xi_f[3 * pidx + a] = xi[a];
+                const float Fj[3] = {-Fi[0], -Fi[1], -Fi[2]};
+                cross3f(xcp, Fi, ti);
+                cross3f(rj, Fj, tj);
+            }
+        }
+        for (int a = 0; a < 3; a++) { out[a] = Fi[a]; out[3 + a] = ti[a]; out[6 + a] = tj[a]; }
+    }
+}
+
+// Per particle: pair terms in index order, then the walls.
+__device__ void gather_contacts(const Params &P, Shared &S, int k, float h, float F[3], float T[3]) {
+    for (int a = 0; a < 3; a++) { F[a] = 0.f; T[a] = 0.f; }
+    for (int e = 0; e < S.ndn[k]; e++) {
+        const int m = S.dn[k][e] >> 8, s = S.dn[k][e] & 255;
+        const float *o = P.dem_res + ((size_t)m * kMaxAdj + s) * 9;
+        for (int a = 0; a < 3; a++) { F[a] += -o[a]; T[a] += o[6 + a]; }
+    }
+    for (int s = 0; s < S.nup[k]; s++) {
+        const float *o = P.dem_res + ((size_t)k * kMaxAdj + s) * 9;
+        for (int a = 0; a < 3; a++) { F[a] += o[a]; T[a] += o[3 + a]; }
+    }
+    const DevParticle &p = P.parts[k];
+    for (int wall = 0; wall < NWALL; wall++) {
+        const int ax = wall / 2, side = wall % 2;
+        const int wj = k * NWALL + wall;
+        if (P.per[ax]) { P.wall_on[wj] = 0; continue; }
+        const float plane = side ? P.dim_f[ax] - 0.5f : -0.5f;
+        const float prel = (plane - S.xh[k][ax]) - S.xl[k][ax];
+        if (fabsf(prel) > p.brad_f) { P.wall_on[wj] = 0; continue; }
+        const bool warm = P.wall_on[wj] != 0;
+        float xcw[3], delta, nv[3], xcp[3];
+        for (int a = 0; a < 3; a++) xcw[a] = P.wall_xcw_f[3 * wj + a];
+        if (!wall_geom_f(P, S, p, k, wall, prel, warm, xcw, delta, nv, xcp)) { P.wall_on[wj] = 0; continue; }
+        float xi[3];
+        for (int a = 0; a < 3; a++) xi[a] = warm ? P.wall_xi_f[3 * wj + a] : 0.f;
+        P.wall_on[wj] = 1;
+        for (int a = 0; a < 3; a++) P.wall_xcw_f[3 * wj + a] = xcw[a];
+        float wr[3], vi[3], Fi[3], ti[3];
+        cross3f(S.w[k], xcp, wr);
+        for (int a = 0; a < 3; a++) vi[a] = S.v[k][a] + wr[a];
+        contact_law_f(P, delta, nv, vi, xi, h, Fi);
+        for (int a = 0; a < 3; a++) P.wall_xi_f[3 * wj + a] = xi[a];
+        cross3f(xcp, Fi, ti);
+        for (int a = 0; a < 3; a++) { F[a] += Fi[a]; T[a] += ti[a]; }
+    }
+}
+
+// Rotated control points of particle k into the shared table.
+__device__ __forceinline__ void put_rc(const Params &P, Shared &S, int k, const float q[4]) {
+    const DevParticle &p = P.parts[k];
+    for (int c = 0; c < p.ncp; c++) qrot_f(q, p.cpb_f[c], S.rc[S.cpo[k] + c], true);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads) k_dem32(Params P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Shared &S = *reinterpret_cast<Shared *>(smem_raw);
+    const int tid = threadIdx.x, np = P.np;
+    const float h = P.h_f, hh = 0.5f * h, qh2 = 0.25f * h * h;
+    const bool own = tid < np;
+    const DevParticle *pp = own ? &P.parts[tid] : nullptr;
+
+    DF x[3], v[3], q[4], wb[3];
+    float Fh[3] = {0.f, 0.f, 0.f}, Th[3] = {0.f, 0.f, 0.f}, iI[3], cI[3], bg[3], inv_m = 0.f;
+    bool mov = false;
+    if (own) {
+        for (int a = 0; a < 3; a++) {
+            x[a] = df_load(pp->sx[a]);
+            v[a] = df_load(pp->sv[a]);
+            wb[a] = df_load(pp->swb[a]);
+            Fh[a] = (float)P.Fh[3 * tid + a];
+            Th[a] = (float)P.Th[3 * tid + a];
+            iI[a] = pp->iI_f[a];
+            cI[a] = pp->cI_f[a];
+            bg[a] = pp->bg_f[a];
+        }
+        for (int a = 0; a < 4; a++) q[a] = df_load(pp->sq[a]);
+        inv_m = pp->inv_mass_f;
+        mov = !pp->fixed;
+    }
+    if (tid == 0) {
+        int o = 0;
+        for (int k = 0; k < np; k++) { S.cpo[k] = o; o += P.parts[k].ncp; }
+        S.cpo[np] = o;
+    }
+    __syncthreads();
+
+    // shared state, reach over the step without contacts (|v| + |a|), walls
+    int possible = 0;
+    if (own) {
+        float qf[4] = {q[0].hi, q[1].hi, q[2].hi, q[3].hi}, wbf[3] = {wb[0].hi, wb[1].hi, wb[2].hi}, ww[3];
+        qrot_f(qf, wbf, ww, true);
+        float a2 = 0.f, v2 = 0.f;
+        for (int a = 0; a < 3; a++) {
+            S.xh[tid][a] = x[a].hi;
+            S.xl[tid][a] = x[a].lo;
+            S.v[tid][a] = v[a].hi;
+            S.w[tid][a] = ww[a];
+            const float acc = bg[a] + Fh[a] * inv_m;
+            a2 += acc * acc;
+            v2 += v[a].hi * v[a].hi;
+        }
+        const float reach = mov ? (sqrtf(v2) + sqrtf(a2)) * 1.001f + 1e-4f : 0.f;
+        S.reach[tid] = reach;
+        if (reach > 0.4f * kSkin) possible = 1;
+        put_rc(P, S, tid, qf);
+        for (int wall = 0; wall < NWALL; wall++) {
+            const int ax = wall / 2, side = wall % 2;
+            if (P.wall_on[tid * NWALL + wall]) possible = 1;
+            if (P.per[ax]) continue;
+            const float plane = side ? P.dim_f[ax] - 0.5f : -0.5f;
+            const float prel = (plane - x[ax].hi) - x[ax].lo;
+            if (fabsf(prel) - pp->brad_f <= reach + 1e-2f) possible = 1;
+        }
+    }
+    __syncthreads();
+    if (np > 1) build_lists(P, S, &possible);
+    else if (tid == 0) {
+        S.nup[0] = 0; S.ndn[0] = 0; S.ioff[0] = 0; S.ioff[1] = 0;
+        for (int a = 0; a < 3; a++) S.xref[0][a] = S.xh[0][a] + S.xl[0][a];
+    }
+    possible = __syncthreads_or(possible);
+
+    if (!possible) {
+        // translation in closed form over the unit step (what the sub-steps
+        // give in exact arithmetic), rotation sub-stepped
+        if (own) {
+            for (int a = 0; a < 3; a++) {
+                const float acc = bg[a] + Fh[a] * inv_m;
+                x[a] = df_add(df_add(x[a], v[a].hi), v[a].lo + 0.5f * acc);
+                v[a] = df_add(v[a], acc);
+            }
+            bool turns = mov;
+            if (turns) {
+                float qf[4] = {q[0].hi, q[1].hi, q[2].hi, q[3].hi};
+                float Tb[3];
+                qrot_f(qf, Th, Tb, false);
+                turns = !(wb[0].hi == 0.f && wb[1].hi == 0.f && wb[2].hi == 0.f && Tb[0] == 0.f && Tb[1] == 0.f &&
+                          Tb[2] == 0.f);
+                for (int sub = 0; turns && sub < P.n_sub; sub++) {
+                    float wbf[3] = {wb[0].hi, wb[1].hi, wb[2].hi}, dw[3];
+                    euler_f(iI, cI, wbf, Tb, dw);
+                    DF wh[3];
+                    float xf[3];
+                    for (int a = 0; a < 3; a++) {
+                        xf[a] = df_lead(wb[a], hh * dw[a]);
+                        wh[a] = df_add(wb[a], hh * dw[a]);
+                    }
+                    float cm1, sc;
+                    exp_half(hh, qh2, xf, cm1, sc);
+                    const float d1 = sc * xf[0], d2 = sc * xf[1], d3 = sc * xf[2];
+                    const float q0 = q[0].hi, q1 = q[1].hi, q2 = q[2].hi, q3 = q[3].hi;
+                    const float i0 = q0 * cm1 - (q1 * d1 + q2 * d2 + q3 * d3);
+                    const float i1 = q0 * d1 + q1 * cm1 + (q2 * d3 - q3 * d2);
+                    const float i2 = q0 * d2 + q2 * cm1 + (q3 * d1 - q1 * d3);
+                    const float i3 = q0 * d3 + q3 * cm1 + (q1 * d2 - q2 * d1);
+                    qf[0] = df_lead(q[0], i0); qf[1] = df_lead(q[1], i1); qf[2] = df_lead(q[2], i2); qf[3] = df_lead(q[3], i3);
+                    q[0] = df_add(q[0], i0); q[1] = df_add(q[1], i1); q[2] = df_add(q[2], i2); q[3] = df_add(q[3], i3);
+                    qrot_f(qf, Th, Tb, false);
+                    float w1[3] = {xf[0], xf[1], xf[2]};
+                    for (int it = 0; it + 1 < ROT_ITERS; it++) {
+                        euler_f(iI, cI, w1, Tb, dw);
+                        for (int a = 0; a < 3; a++) w1[a] = xf[a] + hh * dw[a];
+                    }
+                    euler_f(iI, cI, w1, Tb, dw);
+                    for (int a = 0; a < 3; a++) wb[a] = df_add(wh[a], hh * dw[a]);
+                }
+            }
+            for (int a = 0; a < 3; a++) { S.Fc[tid][a] = 0.f; S.Tc[tid][a] = 0.f; }
+        }
+    } else {
+        // contact load at the start: left by the previous step's DEM (same
+        // state), unless the particles were set since
+        if (!P.fc_valid) {
+            pair_contacts(P, S, 0.f);
+            __syncthreads();
+            if (own) {
+                float F[3], T[3];
+                gather_contacts(P, S, tid, 0.f, F, T);
+                for (int a = 0; a < 3; a++) { S.Fc[tid][a] = F[a]; S.Tc[tid][a] = T[a]; }
+            }
+        } else if (own) {
+            for (int a = 0; a < 3; a++) {
+                S.Fc[tid][a] = (float)P.Fc[3 * tid + a];
+                S.Tc[tid][a] = (float)P.Tc[3 * tid + a];
+            }
+        }
+        __syncthreads();
+        for (int sub = 0; sub < P.n_sub; sub++) {
+            DF wh[3];
+            float whf[3] = {0.f, 0.f, 0.f};
+            int moved = 0;
+            if (own) {
+                float qf[4] = {q[0].hi, q[1].hi, q[2].hi, q[3].hi};
+                if (mov) {
+                    // first half-kick and drift
+                    for (int a = 0; a < 3; a++) {
+                        const float acc = bg[a] + (Fh[a] + S.Fc[tid][a]) * inv_m;
+                        const float vl = df_lead(v[a], hh * acc);
+                        v[a] = df_add(v[a], hh * acc);
+                        x[a] = df_add(x[a], h * vl);
+                    }
+                    // rotation: half-kick, q <- q (x) exp(h wh / 2)
+                    float Tw[3], Tb[3], wbf[3] = {wb[0].hi, wb[1].hi, wb[2].hi}, dw[3];
+                    for (int a = 0; a < 3; a++) Tw[a] = Th[a] + S.Tc[tid][a];
+                    qrot_f(qf, Tw, Tb, false);
+                    euler_f(iI, cI, wbf, Tb, dw);
+                    for (int a = 0; a < 3; a++) {
+                        whf[a] = df_lead(wb[a], hh * dw[a]);
+                        wh[a] = df_add(wb[a], hh * dw[a]);
+                    }
+                    float cm1, sc;
+                    exp_half(hh, qh2, whf, cm1, sc);
+                    const float d1 = sc * whf[0], d2 = sc * whf[1], d3 = sc * whf[2];
+                    const float q0 = qf[0], q1 = qf[1], q2 = qf[2], q3 = qf[3];
+                    const float i0 = q0 * cm1 - (q1 * d1 + q2 * d2 + q3 * d3);
+                    const float i1 = q0 * d1 + q1 * cm1 + (q2 * d3 - q3 * d2);
+                    const float i2 = q0 * d2 + q2 * cm1 + (q3 * d1 - q1 * d3);
+                    const float i3 = q0 * d3 + q3 * cm1 + (q1 * d2 - q2 * d1);
+                    qf[0] = df_lead(q[0], i0); qf[1] = df_lead(q[1], i1); qf[2] = df_lead(q[2], i2); qf[3] = df_lead(q[3], i3);
+                    q[0] = df_add(q[0], i0); q[1] = df_add(q[1], i1); q[2] = df_add(q[2], i2); q[3] = df_add(q[3], i3);
+                } else {
+                    for (int a = 0; a < 3; a++) { wh[a] = wb[a]; whf[a] = wb[a].hi; }
+                }
+                float ww[3];
+                qrot_f(qf, whf, ww, true);
+                float dr2 = 0.f;
+                for (int a = 0; a < 3; a++) {
+                    S.xh[tid][a] = x[a].hi;
+                    S.xl[tid][a] = x[a].lo;
+                    S.v[tid][a] = v[a].hi;
+                    S.w[tid][a] = ww[a];
+                    const float dd = (x[a].hi - S.xref[tid][a]) + x[a].lo;
+                    dr2 += dd * dd;
+                }
+                if (mov) put_rc(P, S, tid, qf);
+                moved = dr2 > 0.25f * kSkin * kSkin;
+            }
+            moved = __syncthreads_or(moved);
+            if (moved && np > 1) {
+                int dummy = 0;
+                build_lists(P, S, &dummy);
+            }
+            pair_contacts(P, S, h);
+            __syncthreads();
+            if (own) {
+                float F[3], T[3];
+                gather_contacts(P, S, tid, h, F, T);
+                for (int a = 0; a < 3; a++) { S.Fc[tid][a] = F[a]; S.Tc[tid][a] = T[a]; }
+                if (mov) {
+                    // closing half-kick with the new contact load
+                    for (int a = 0; a < 3; a++) v[a] = df_add(v[a], hh * (bg[a] + (Fh[a] + F[a]) * inv_m));
+                    float qf[4] = {q[0].hi, q[1].hi, q[2].hi, q[3].hi}, Tw[3], Tb[3], dw[3];
+                    for (int a = 0; a < 3; a++) Tw[a] = Th[a] + T[a];
+                    qrot_f(qf, Tw, Tb, false);
+                    float w1[3] = {whf[0], whf[1], whf[2]};
+                    for (int it = 0; it + 1 < ROT_ITERS; it++) {
+                        euler_f(iI, cI, w1, Tb, dw);
+                        for (int a = 0; a < 3; a++) w1[a] = whf[a] + hh * dw[a];
+                    }
+                    euler_f(iI, cI, w1, Tb, dw);
+                    for (int a = 0; a < 3; a++) wb[a] = df_add(wh[a], hh * dw[a]);
+                }
+            }
+            __syncthreads();
+        }
+        // contact load of the end state (springs not advanced): reported by
+        // lbm_get_contact_forces and the start load of the next step
+        if (own) {
+            float qf[4] = {q[0].hi, q[1].hi, q[2].hi, q[3].hi}, wbf[3] = {wb[0].hi, wb[1].hi, wb[2].hi}, ww[3];
+            qrot_f(qf, wbf, ww, true);
+            for (int a = 0; a < 3; a++) { S.v[tid][a] = v[a].hi; S.w[tid][a] = ww[a]; }
+        }
+        __syncthreads();
+        pair_contacts(P, S, 0.f);
+        __syncthreads();
+        if (own) {
+            float F[3], T[3];
+            gather_contacts(P, S, tid, 0.f, F, T);
+            for (int a = 0; a < 3; a++) { S.Fc[tid][a] = F[a]; S.Tc[tid][a] = T[a]; }
+        }
+    }
+
+    // Write back: the compensated state, then the FP64 fields the other
+    // kernels read.  q is renormalised to first order (|q|^2 - 1 is ~1e-12):
+    // q <- q (1 - e/2), e = |q|^2 - 1 from exact products and a compensated sum.
+    if (own) {
+        DevParticle &p = P.parts[tid];
+        float e_hi = -1.0f, e_lo = 0.f;
+        for (int a = 0; a < 4; a++) {
+            const float pr = q[a].hi * q[a].hi;
+            const float er = fmaf(q[a].hi, q[a].hi, -pr) + 2.0f * q[a].hi * q[a].lo;
+            const DF t = df_add({e_hi, e_lo}, pr);
+            e_hi = t.hi;
+            e_lo = t.lo + er;
+        }
+        const float e = e_hi + e_lo;
+        for (int a = 0; a < 4; a++) {
+            const DF t = df_add({q[a].hi, 0.f}, q[a].lo - 0.5f * e * q[a].hi);
+            q[a] = t;
+        }
+        for (int a = 0; a < 3; a++) {
+            df_store(p.sx[a], x[a]);
+            df_store(p.sv[a], v[a]);
+            df_store(p.swb[a], wb[a]);
+        }
+        for (int a = 0; a < 4; a++) df_store(p.sq[a], q[a]);
+        float qf[4] = {q[0].hi, q[1].hi, q[2].hi, q[3].hi}, wbf[3] = {wb[0].hi, wb[1].hi, wb[2].hi}, ww[3];
+        qrot_f(qf, wbf, ww, true);
+        for (int a = 0; a < 3; a++) S.w[tid][a] = ww[a];
+    }
+    __syncthreads();
+    // FP64 fields, one lane per component: x(3) v(3) q(4) w(3) Fc(3) Tc(3)
+    for (int idx = tid; idx < np * 19; idx += blockDim.x) {
+        const int k = idx / 19, c = idx % 19;
+        DevParticle &p = P.parts[k];
+        if (c < 3) p.x[c] = (double)p.sx[c][0] + (double)p.sx[c][1];
+        else if (c < 6) p.v[c - 3] = (double)p.sv[c - 3][0] + (double)p.sv[c - 3][1];
+        else if (c < 10) p.q[c - 6] = (double)p.sq[c - 6][0] + (double)p.sq[c - 6][1];
+        else if (c < 13) p.w[c - 10] = (double)S.w[k][c - 10];
+        else if (c < 16) P.Fc[3 * k + c - 13] = (double)S.Fc[k][c - 13];
+        else P.Tc[3 * k + c - 16] = (double)S.Tc[k][c - 16];
+    }
+}
+
+void launch_dem32(const Params &P, cudaStream_t st) {
+    // the dynamic shared memory limit is raised once per device
+    static bool attr_set[64] = {};
+    const int bytes = (int)sizeof(Shared);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    if (!attr_set[dev]) {
+        if (cudaFuncSetAttribute(k_dem32, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return;
+        attr_set[dev] = true;
+    }
+    k_dem32<<<1, kThreads, bytes, st>>>(P);
+}
+
+}  // namespace lbmmb

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(256) k_bin(Params P) {
             const int pos = atomicAdd(&P.counters[CNT_LISTED], 1);
             P.wl_list[(P.step % 3) * P.nbricks + pos] = b;
             P.stamp[b] = P.step;
+            if (P.skip) P.skip[(P.step % 3) * P.nbricks + b] = P.step;
         }
     }
     if (!P.pred_stamp_next) return;
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(256) k_bin(Params P) {
         if (atomicExch(&P.pred_stamp_next[b], next) != next) {
             const int pos = atomicAdd(&P.pred_count[next & 1], 1);
             P.pred_list_next[pos] = b;
+            if (P.skip) P.skip[(next % 3) * P.nbricks + b] = next;
         }
     }
 }
@@ -513,10 +515,9 @@ __device__ bool contact_possible(const Params &P) {
         const DevParticle &p = P.parts[k];
         double D = 0.0;
         if (!p.fixed) {
-            const double gr = 1.0 - P.rho0 / p.density;
             double a2 = 0.0;
             for (int a = 0; a < 3; a++) {
-                const double acc = gr * P.g[a] + P.Fh[3 * k + a] / p.mass;
+                const double acc = p.buoy * P.g[a] + P.Fh[3 * k + a] * p.inv_mass;
                 a2 += acc * acc;
             }
             D = sqrt(dot3(p.v, p.v)) + sqrt(a2);
@@ -672,16 +673,16 @@ __device__ void rotate_free_quad(unsigned mk, const DevParticle &p, const double
 // frame.  When no contact can occur during the step, the translation of the
 // n_s sub-steps under the constant force is taken in closed form (x += v +
 // a/2, v += a over the unit step: what the sub-steps compute in exact
-// arithmetic) and the rotation is sub-stepped by four lanes per particle.
+// arithmetic) and the rotation is sub-stepped by four FP64 lanes per
+// particle.  (Lattices stored below FP64 use k_dem32 instead.)
 __global__ void __launch_bounds__(256) k_dem(Params P) {
     const double h = 1.0 / P.n_sub;
     if (!contact_possible(P)) {
         for (int k = threadIdx.x; k < P.np; k += blockDim.x) {
             DevParticle &p = P.parts[k];
             if (p.fixed) continue;
-            const double gr = 1.0 - P.rho0 / p.density;
             for (int a = 0; a < 3; a++) {
-                const double acc = gr * P.g[a] + P.Fh[3 * k + a] / p.mass;
+                const double acc = p.buoy * P.g[a] + P.Fh[3 * k + a] * p.inv_mass;
                 p.x[a] += p.v[a] + 0.5 * acc;
                 p.v[a] += acc;
             }
@@ -698,15 +699,16 @@ __global__ void __launch_bounds__(256) k_dem(Params P) {
         }
         return;
     }
-    contacts(P, 0.0);
+    // the load at the start: left by the previous step's DEM (same state),
+    // unless the particles were set since
+    if (!P.fc_valid) contacts(P, 0.0);
     for (int sub = 0; sub < P.n_sub; sub++) {
         for (int k = threadIdx.x; k < P.np; k += blockDim.x) {
             DevParticle &p = P.parts[k];
             if (p.fixed) continue;
-            const double gr = 1.0 - P.rho0 / p.density;
             for (int a = 0; a < 3; a++) {
-                const double Ft = p.mass * gr * P.g[a] + P.Fh[3 * k + a] + P.Fc[3 * k + a];
-                p.v[a] += 0.5 * h * Ft / p.mass;
+                const double acc = p.buoy * P.g[a] + (P.Fh[3 * k + a] + P.Fc[3 * k + a]) * p.inv_mass;
+                p.v[a] += 0.5 * h * acc;
             }
             for (int a = 0; a < 3; a++) p.x[a] += h * p.v[a];
             // first rotational half-kick and the rotation (the closing
@@ -729,10 +731,9 @@ __global__ void __launch_bounds__(256) k_dem(Params P) {
         for (int k = threadIdx.x; k < P.np; k += blockDim.x) {
             DevParticle &p = P.parts[k];
             if (p.fixed) continue;
-            const double gr = 1.0 - P.rho0 / p.density;
             for (int a = 0; a < 3; a++) {
-                const double Ft = p.mass * gr * P.g[a] + P.Fh[3 * k + a] + P.Fc[3 * k + a];
-                p.v[a] += 0.5 * h * Ft / p.mass;
+                const double acc = p.buoy * P.g[a] + (P.Fh[3 * k + a] + P.Fc[3 * k + a]) * p.inv_mass;
+                p.v[a] += 0.5 * h * acc;
             }
             double Tw[3], wb[3], Tb[3], dw[3];
             for (int a = 0; a < 3; a++) Tw[a] = P.Th[3 * k + a] + P.Tc[3 * k + a];
@@ -747,6 +748,9 @@ __global__ void __launch_bounds__(256) k_dem(Params P) {
         }
         __syncthreads();
     }
+    // contact load of the end state (springs not advanced): reported by
+    // lbm_get_contact_forces and the start load of the next step
+    contacts(P, 0.0);
 }
 
 void launch_bin(const Params &P, cudaStream_t st) {
@@ -756,7 +760,9 @@ void launch_force_reduce(const Params &P, cudaStream_t st) {
     if (P.np > 0) k_force_reduce<<<P.np, 256, 0, st>>>(P);
 }
 void launch_dem(const Params &P, cudaStream_t st) {
-    if (P.np > 0 && P.n_sub > 0) k_dem<<<1, 256, 0, st>>>(P);
+    if (P.np <= 0 || P.n_sub <= 0) return;
+    if (P.dem_f32) launch_dem32(P, st);
+    else k_dem<<<1, 256, 0, st>>>(P);
 }
 
 }  // namespace lbmmb

@@ -601,7 +601,7 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
 template <typename S, int Q, bool kForce>
 __global__ void __launch_bounds__(BRICK, 4) k_sweep_plain(Params P) {
     const int b = blockIdx.x;
-    if (P.pred_stamp_cur && P.pred_stamp_cur[b] == P.step) return;  // the near sweep takes it
+    if (P.skip && P.skip[(P.step % 3) * P.nbricks + b] == P.step) return;  // the near sweep takes it
     int bxi, byi, bzi;
     brick_coords(P, b, bxi, byi, bzi);
     const int tid = threadIdx.x;
@@ -611,9 +611,7 @@ __global__ void __launch_bounds__(BRICK, 4) k_sweep_plain(Params P) {
 
 // The sweep of the bricks listed this step (exactly those some particle's
 // grown search box meets) and of the predicted-near bricks that are not
-// listed (plain path).  Persistent grid; runs after k_sweep_plain, so a
-// listed brick the plain sweep also took is overwritten with its correct
-// update.
+// listed (plain path): every brick k_sweep_plain leaves.  Persistent grid.
 template <typename S, int Q, bool kForce>
 __global__ void __launch_bounds__(BRICK, 4) k_sweep_near(Params P) {
     __shared__ SmemParticles sp;

@@ -20,15 +20,22 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 size_t storage_bytes(int s) { return s == LBM_STORE_F64 ? 8 : (s == LBM_STORE_F32 ? 4 : 2); }
 
+// A double as a compensated FP32 pair: hi = fl32(v), lo = fl32(v - hi).
+void split_pair(double v, float out[2]) {
+    out[0] = (float)v;
+    out[1] = (float)(v - (double)out[0]);
+}
+
 // Byte offsets of every array in the workspace.
 struct Layout {
     size_t f[2], flags[2];
     size_t wl_list, wl_count, stamp;
-    size_t pred_stamp, pred_list, pred_count;
+    size_t pred_stamp, pred_list, pred_count, skip;
     size_t bin;        // bcount[nbricks] followed by the per-step counters
     size_t bin_bytes;
     size_t blist, partial, parts, Fh, Th, Fc, Tc;
     size_t pairF, pair_on, pair_xi, pair_xm, wall_on, wall_xi, wall_xcw;
+    size_t pair_xi_f, pair_xm_f, wall_xi_f, wall_xcw_f, dem_res;
     size_t status;
     size_t total;
     long long N;
@@ -51,6 +58,7 @@ const char *check_config(const lbm_config *c) {
     for (int a = 0; a < 3; a++)
         if (c->periodic[a] != 0 && c->periodic[a] != 1) return "periodic[] must be 0 or 1";
     if (c->mass_spacing < 0.0) return "mass_spacing must be >= 0";
+    if (c->dem_fp64 != 0 && c->dem_fp64 != 1) return "dem_fp64 must be 0 or 1";
     return nullptr;
 }
 
@@ -79,6 +87,7 @@ void make_layout(const lbm_config *c, Layout *L) {
     L->pred_stamp = take(2 * nb * 4);
     L->pred_list = take(2 * nb * 4);
     L->pred_count = take(2 * 4);
+    L->skip = take(3 * nb * 4);
     L->bin_bytes = nb * 4 + kStepCounters * 4;
     L->bin = take(L->bin_bytes);
     L->blist = take(nb * MAXPB * 4);
@@ -95,6 +104,11 @@ void make_layout(const lbm_config *c, Layout *L) {
     L->wall_on = take(P * NWALL * 4);
     L->wall_xi = take(P * NWALL * 24);
     L->wall_xcw = take(P * NWALL * 24);
+    L->pair_xi_f = take(P * P * 12);
+    L->pair_xm_f = take(P * P * 12);
+    L->wall_xi_f = take(P * NWALL * 12);
+    L->wall_xcw_f = take(P * NWALL * 12);
+    L->dem_res = take(P * kDemMaxAdj * 9 * 4);
     L->status = take(ST_SLOTS * 4);
     L->total = o;
 }
@@ -111,10 +125,13 @@ struct lbm_handle {
     // Each lbm_step() call forks two library streams from `stream` and joins
     // them back: `hi` (highest priority) runs the latency-bound chain (binning,
     // flags, near sweep, force reduction, DEM), `aux` (lowest priority) the
-    // plain sweep of the next step, so the chain's small grids are dispatched
-    // ahead of the plain sweep's bricks while both run.
+    // plain sweep, so the chain's small grids are dispatched ahead of the
+    // plain sweep's bricks while both run.  The plain sweep of step t starts
+    // after the binning of t (it leaves the bricks binned or predicted near)
+    // and the near sweep of t-1 (whose input buffer it overwrites); the near
+    // sweep of t+1 waits for it (it reads its halo).
     cudaStream_t aux, hi;
-    cudaEvent_t ev_fork, ev_plain, ev_near, ev_join;
+    cudaEvent_t ev_fork, ev_bin, ev_plain, ev_near, ev_join;
     // kernel timing (lbm_profile): event pairs per kernel, in launch order
     bool prof;
     std::vector<cudaEvent_t> ev[kProfKernels][2];
@@ -125,6 +142,8 @@ struct lbm_handle {
     int cur;    // populations consistent with flags[fcur] live in f[cur]
     int fcur;
     int np;
+    int dem_f32;   // the FP32 DEM runs (storage, dem_fp64 and the particle set allow it)
+    int fc_valid;  // the DEM of the last step left the contact load of the current state
     int64_t steps;
     char err[256];
 };
@@ -170,6 +189,7 @@ Params make_params(lbm_handle *h) {
     P.pred_list_cur = at<int>(h, h->L.pred_list + (size_t)cur * h->L.nbricks * 4);
     P.pred_list_next = at<int>(h, h->L.pred_list + (size_t)(1 - cur) * h->L.nbricks * 4);
     P.pred_count = at<int>(h, h->L.pred_count);
+    P.skip = at<int>(h, h->L.skip);
     P.bcount = at<int>(h, h->L.bin);
     P.blist = at<int>(h, h->L.blist);
     P.partial = at<double>(h, h->L.partial);
@@ -185,6 +205,13 @@ Params make_params(lbm_handle *h) {
     P.wall_on = at<int>(h, h->L.wall_on);
     P.wall_xi = at<double>(h, h->L.wall_xi);
     P.wall_xcw = at<double>(h, h->L.wall_xcw);
+    P.pair_xi_f = at<float>(h, h->L.pair_xi_f);
+    P.pair_xm_f = at<float>(h, h->L.pair_xm_f);
+    P.wall_xi_f = at<float>(h, h->L.wall_xi_f);
+    P.wall_xcw_f = at<float>(h, h->L.wall_xcw_f);
+    P.dem_res = at<float>(h, h->L.dem_res);
+    P.dem_f32 = h->dem_f32;
+    P.fc_valid = h->fc_valid;
     P.status = at<int>(h, h->L.status);
     P.counters = at<int>(h, h->L.bin + (size_t)h->L.nbricks * 4);
     return P;
@@ -392,7 +419,7 @@ int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_st
     // bricks occupied, no contacts, no errors
     const size_t zero_from = L.flags[0];
     h->aux = h->hi = nullptr;
-    h->ev_fork = h->ev_plain = h->ev_near = h->ev_join = nullptr;
+    h->ev_fork = h->ev_bin = h->ev_plain = h->ev_near = h->ev_join = nullptr;
     int prio_low = 0, prio_high = 0;
     int rc = cuda_check(h, cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high), "cudaDeviceGetStreamPriorityRange");
     if (rc == LBM_OK)
@@ -401,11 +428,14 @@ int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_st
         rc = cuda_check(h, cudaStreamCreateWithPriority(&h->hi, cudaStreamNonBlocking, prio_high), "cudaStreamCreateWithPriority");
     if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "cudaEventCreate");
     if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_bin, cudaEventDisableTiming), "cudaEventCreate");
     if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_plain, cudaEventDisableTiming), "cudaEventCreate");
     if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_near, cudaEventDisableTiming), "cudaEventCreate");
     if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + zero_from, 0, L.total - zero_from, h->stream), "cudaMemsetAsync");
-    if (rc == LBM_OK)  // no brick is predicted near before the first step
+    if (rc == LBM_OK)  // no brick is predicted near (or skipped) before the first step
         rc = cuda_check(h, cudaMemsetAsync(h->ws + L.pred_stamp, 0xFF, 2 * (size_t)L.nbricks * 4, h->stream), "cudaMemsetAsync");
+    if (rc == LBM_OK)
+        rc = cuda_check(h, cudaMemsetAsync(h->ws + L.skip, 0xFF, 3 * (size_t)L.nbricks * 4, h->stream), "cudaMemsetAsync");
     if (rc == LBM_OK) {
         Params P = make_params(h);
         by_storage<DoInit>(h->cfg.storage, P, (void *)(h->ws + L.f[0]), h->stream);
@@ -416,6 +446,7 @@ int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_st
     if (rc != LBM_OK) {
         std::snprintf(g_init_error, sizeof(g_init_error), "%s", h->err);
         if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+        if (h->ev_bin) cudaEventDestroy(h->ev_bin);
         if (h->ev_plain) cudaEventDestroy(h->ev_plain);
         if (h->ev_near) cudaEventDestroy(h->ev_near);
         if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -434,6 +465,7 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
     if (n > h->cfg.max_particles)
         return fail(h, LBM_ERR_CAPACITY, "%d particles, capacity %d", n, h->cfg.max_particles);
     std::vector<DevParticle> dev((size_t)(n > 0 ? n : 1));
+    int nc_total = 0;
     for (int j = 0; j < n; j++) {
         lbm_particle p = host[j];
         if (p.n_cp < 1 || p.n_cp > LBM_MAX_CP) return fail(h, LBM_ERR_BAD_ARG, "particle %d: n_cp out of range", j);
@@ -492,7 +524,36 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
                 d.hi[a] = std::fmax(d.hi[a], d.cpw[k][a]);
             }
         for (int a = 0; a < 3; a++) { d.lo[a] -= std::sqrt(Ks / h->cfg.c0); d.hi[a] += std::sqrt(Ks / h->cfg.c0); }
+        // divisions done here once (FP64 division is slow on the device)
+        d.inv_mass = p.mass > 0.0 ? 1.0 / p.mass : 0.0;
+        d.buoy = 1.0 - h->cfg.rho0 / p.density;
+        // FP32 DEM: constants and the compensated state
+        for (int k = 0; k < d.ncp; k++) {
+            for (int a = 0; a < 3; a++) d.cpb_f[k][a] = (float)d.cpb[k][a];
+            d.K_f[k] = (float)d.K[k];
+        }
+        for (int l = 0; l < 3; l++) {
+            d.iI_f[l] = (float)d.iI[l];
+            d.cI_f[l] = (float)d.cI[l];
+            d.bg_f[l] = (float)(d.buoy * h->cfg.gravity[l]);
+        }
+        d.inv_mass_f = (float)d.inv_mass;
+        d.Rs_f = (float)d.Rs;
+        d.brad_f = (float)d.brad;
+        d.sumK_f = (float)d.sumK;
+        double wb[3];
+        for (int a = 0; a < 3; a++) wb[a] = R[a] * d.w[0] + R[3 + a] * d.w[1] + R[6 + a] * d.w[2];  // R^T w
+        for (int a = 0; a < 3; a++) {
+            split_pair(d.x[a], d.sx[a]);
+            split_pair(d.v[a], d.sv[a]);
+            split_pair(wb[a], d.swb[a]);
+        }
+        for (int a = 0; a < 4; a++) split_pair(d.q[a], d.sq[a]);
+        nc_total += d.ncp;
     }
+    // the FP32 DEM keeps its per-particle tables in shared memory
+    h->dem_f32 = h->cfg.storage != LBM_STORE_F64 && !h->cfg.dem_fp64 && n <= kDem32MaxParticles &&
+                 nc_total <= kDem32MaxCp;
     int rc = LBM_OK;
     if (n > 0)
         rc = cuda_check(h, cudaMemcpyAsync(h->ws + h->L.parts, dev.data(), sizeof(DevParticle) * (size_t)n,
@@ -505,6 +566,7 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
     // the staging vector dies with this call
     if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (rc == LBM_OK) h->np = n;
+    h->fc_valid = 0;
     return rc;
 }
 
@@ -549,13 +611,21 @@ int lbm_step(lbm_handle *h, int nsteps) {
         e = cudaMemsetAsync(h->ws + h->L.bin, 0, h->L.bin_bytes, hs);
         if (e != cudaSuccess) return cuda_check(h, e, "cudaMemsetAsync(bricks)");
         { ProfScope s(h, 0, P.np > 0, hs); launch_bin(P, hs); }
+        e = cudaEventRecord(h->ev_bin, hs);
+        if (e != cudaSuccess) return cuda_check(h, e, "event record");
         { ProfScope s(h, 1, true, hs); by_storage<DoFlags>(h->cfg.storage, P, hs); }
-        // plain bricks on the low-priority stream: they need only the
-        // previous step's populations (the previous near sweep was joined in)
+        // the near sweep reads the halo the previous plain sweep wrote (this
+        // wait is issued before ev_plain is recorded again below; the plain
+        // sweep of the call before was joined into `stream` before the fork,
+        // so every event waited on is recorded within this call, as stream
+        // capture requires)
+        if (t > 0) e = cudaStreamWaitEvent(hs, h->ev_plain, 0);
+        // plain bricks on the low-priority stream, concurrent with the chain
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_bin, 0);
+        if (e != cudaSuccess) return cuda_check(h, e, "stream wait");
         { ProfScope s(h, 2, true, h->aux); by_storage<DoPlain>(h->cfg.storage, P, h->aux); }
         e = cudaEventRecord(h->ev_plain, h->aux);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, h->ev_plain, 0);
-        if (e != cudaSuccess) return cuda_check(h, e, "stream join");
+        if (e != cudaSuccess) return cuda_check(h, e, "event record");
         { ProfScope s(h, 3, true, hs); by_storage<DoNear>(h->cfg.storage, P, hs); }
         e = cudaEventRecord(h->ev_near, hs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_near, 0);
@@ -567,11 +637,13 @@ int lbm_step(lbm_handle *h, int nsteps) {
         h->cur ^= 1;
         h->fcur ^= 1;
         h->steps++;
+        if (P.np > 0 && P.n_sub > 0) h->fc_valid = 1;
     }
-    // join: the caller's stream continues after the last DEM (the last plain
-    // sweep precedes the last near sweep on hi)
+    // join: the caller's stream continues after the last DEM and the last
+    // plain sweep
     e = cudaEventRecord(h->ev_join, hs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_plain, 0);
     if (e != cudaSuccess) return cuda_check(h, e, "stream join");
     return LBM_OK;
 }
@@ -591,6 +663,9 @@ static int read_status(lbm_handle *h, int *st) {
 static int status_code(lbm_handle *h, const int *st) {
     if (st[ST_ERR] & ERRB_BRICK_OVERFLOW)
         return fail(h, LBM_ERR_CAPACITY, "more than %d particles met one brick; results are invalid", MAXPB);
+    if (st[ST_ERR] & ERRB_DEM_CAPACITY)
+        return fail(h, LBM_ERR_CAPACITY, "a particle had more than %d candidate contact partners; results are invalid",
+                    kDemMaxAdj);
     if (st[ST_ERR] & ERRB_TIMEOUT) return fail(h, LBM_ERR_TIMEOUT, "a device wait gave up");
     return LBM_OK;
 }
@@ -631,6 +706,21 @@ int lbm_get_forces(lbm_handle *h, double *F, double *T, lbm_particle *state_out)
             quat_mul(d.q, qUc, p.q);  // back to the caller's body frame
         }
     }
+    return rc;
+}
+
+int lbm_get_contact_forces(lbm_handle *h, double *F, double *T) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    int st[ST_SLOTS];
+    int rc = read_status(h, st);
+    if (rc != LBM_OK) return rc;
+    if ((rc = status_code(h, st)) != LBM_OK) return rc;
+    const size_t n = (size_t)h->np;
+    if (n == 0) return LBM_OK;
+    if (F) rc = cuda_check(h, cudaMemcpyAsync(F, h->ws + h->L.Fc, n * 24, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(Fc)");
+    if (rc == LBM_OK && T)
+        rc = cuda_check(h, cudaMemcpyAsync(T, h->ws + h->L.Tc, n * 24, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(Tc)");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     return rc;
 }
 
@@ -740,6 +830,7 @@ int lbm_destroy(lbm_handle *h) {
     cudaStreamSynchronize(h->aux);
     release_profile(h);
     cudaEventDestroy(h->ev_fork);
+    cudaEventDestroy(h->ev_bin);
     cudaEventDestroy(h->ev_plain);
     cudaEventDestroy(h->ev_near);
     cudaEventDestroy(h->ev_join);

@@ -32,7 +32,12 @@ constexpr int ROT_ITERS = 2;  // fixed-point sweeps of the implicit rotational h
 // Status words in the workspace.
 enum StatusSlot { ST_ERR = 0, ST_SLOTS = 16 };
 enum StepCounter { CNT_NREFILL = 0, CNT_NLINKS = 1, CNT_LISTED = 2 };
-enum ErrBits { ERRB_BRICK_OVERFLOW = 1, ERRB_DIVERGED = 2, ERRB_TIMEOUT = 4 };
+enum ErrBits { ERRB_BRICK_OVERFLOW = 1, ERRB_DIVERGED = 2, ERRB_TIMEOUT = 4, ERRB_DEM_CAPACITY = 8 };
+
+// FP32 DEM limits: its per-particle tables live in one CTA's shared memory.
+constexpr int kDem32MaxParticles = 256;
+constexpr int kDem32MaxCp = 2048;     // control points of all particles
+constexpr int kDemMaxAdj = 24;        // candidate contact partners per particle and direction
 
 // ---------------------------------------------------------------------------
 // Lattices.  D3Q19 (rest 1/3, axes 1/18, face diagonals 1/36) and the D3Q15
@@ -169,7 +174,19 @@ struct DevParticle {
     double Iu[9];          // inertia in the caller's body frame
     double lo[3], hi[3];   // search box: AABB(cpw) -+ sqrt(sum K / c0)
     double brad;           // bounding radius about x (DEM broad phase)
+    double inv_mass;       // 1 / mass
+    double buoy;           // 1 - rho0 / rho_s (gravity factor, §3.1)
     int ncp, fixed, pad0, pad1;
+    // FP32 DEM (lattices stored below FP64): constants in FP32, and the
+    // rigid-body state as compensated pairs, value = [0] + [1] (the FP64
+    // fields above are then written from it after every step)
+    float cpb_f[MAXCP][3];
+    float K_f[MAXCP];
+    float iI_f[3], cI_f[3];
+    float bg_f[3];         // buoy * g
+    float inv_mass_f, Rs_f, brad_f, sumK_f;
+    float sx[3][2], sv[3][2], sq[4][2];
+    float swb[3][2];       // angular velocity, principal body frame
 };
 
 // Everything a kernel needs, passed by value.
@@ -179,6 +196,8 @@ struct Params {
     long long N;
     int nbx, nby, nbz, nbricks;
     int np, n_sub, vibb, missing_force;
+    int dem_f32;              // DEM in FP32 with compensated state (k_dem32)
+    int fc_valid;             // Fc/Tc hold the contact load of the current state (0 after set_particles)
     double tau, rho0, c0;
     double F[3], g[3], u0[3];
     // collision constants precomputed on the host (FP64 arithmetic runs at a
@@ -188,6 +207,9 @@ struct Params {
     float omega_f, gfac_f, rho0_f, c0_f;
     float Ff[3];
     double kn, eta_n, kt, eta_t, mu_s, c_tol;
+    // FP32 copies for the FP32 DEM
+    float kn_f, eta_n_f, kt_f, eta_t_f, mu_s_f, inv_kt_f, c_tol_f, h_f;
+    float dim_f[3], inv_n_f[3];
     void *fA;  // read (post-collision, time t)
     void *fB;  // write (post-collision, time t+1)
     uint16_t *flag_new;
@@ -210,6 +232,11 @@ struct Params {
     int *pred_list_cur;    // [nbricks]
     int *pred_list_next;   // [nbricks]
     int *pred_count;       // [2], by step parity
+    // Bricks the plain sweep of a step leaves alone, ring of three by step
+    // (== step: binned or predicted near).  The plain sweep of step t runs
+    // while the chain of t and the binning of t+1 run; the binning of t+1
+    // writes the slots of t+1 and t+2 only.
+    int *skip;             // [3][nbricks], NULL: none
     int *bcount;       // [nbricks]
     int *blist;        // [nbricks][MAXPB]
     double *partial;   // [nbricks][MAXPB][6]
@@ -221,6 +248,9 @@ struct Params {
     double *pair_xi, *pair_xm;   // [np*np][3]
     int *wall_on;      // [np*6]
     double *wall_xi, *wall_xcw;  // [np*6][3]
+    float *pair_xi_f, *pair_xm_f;   // [np*np][3], FP32 DEM: spring, warm start (relative to x_i)
+    float *wall_xi_f, *wall_xcw_f;  // [np*6][3], FP32 DEM: spring, warm start (relative to x_k)
+    float *dem_res;    // [np][kDemMaxAdj][9], FP32 DEM pair results
     int *status;       // [ST_SLOTS], sticky error bits
     int *counters;     // per-step counters, zeroed with the brick lists
 };
@@ -251,6 +281,12 @@ inline void fill_scalar_params(const lbm_config &c, Params &P) {
     P.rho0_f = (float)c.rho0;
     P.c0_f = (float)c.c0;
     for (int a = 0; a < 3; a++) P.Ff[a] = (float)c.force[a];
+    P.kn_f = (float)c.kn; P.eta_n_f = (float)c.eta_n; P.kt_f = (float)c.kt; P.eta_t_f = (float)c.eta_t;
+    P.mu_s_f = (float)c.mu_s; P.c_tol_f = (float)c.c_tol;
+    P.inv_kt_f = c.kt > 0.0 ? (float)(1.0 / c.kt) : 0.0f;
+    P.h_f = c.n_sub > 0 ? (float)(1.0 / c.n_sub) : 0.0f;
+    P.dim_f[0] = (float)c.nx; P.dim_f[1] = (float)c.ny; P.dim_f[2] = (float)c.nz;
+    for (int a = 0; a < 3; a++) P.inv_n_f[a] = (float)P.inv_n[a];
 }
 
 // Scalar parameters in the working precision C (float copies are made on the
@@ -431,6 +467,7 @@ __device__ __forceinline__ void brick_coords(const Params &P, int b, int &bx, in
 void launch_bin(const Params &P, cudaStream_t st);
 void launch_force_reduce(const Params &P, cudaStream_t st);
 void launch_dem(const Params &P, cudaStream_t st);
+void launch_dem32(const Params &P, cudaStream_t st);  // k_dem32.cu
 
 // Launchers of the storage-templated kernels (launch_impl.cuh, one
 // instantiation per storage type in sweep_<type>.cu).

@@ -31,6 +31,7 @@ class LbmConfig(C.Structure):
         ("periodic", C.c_int32 * 3),
         ("n_sub", C.c_int32), ("vibb", C.c_int32), ("missing_force", C.c_int32),
         ("max_particles", C.c_int32),
+        ("dem_fp64", C.c_int32), ("reserved0", C.c_int32),
         ("tau", C.c_double), ("rho0", C.c_double), ("c0", C.c_double),
         ("u0", C.c_double * 3), ("force", C.c_double * 3), ("gravity", C.c_double * 3),
         ("kn", C.c_double), ("eta_n", C.c_double),
@@ -65,6 +66,7 @@ _SIGS = {
     "lbm_set_particles": (C.c_int, [C.c_void_p, C.POINTER(LbmParticle), C.c_int]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_get_forces": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(LbmParticle)]),
+    "lbm_get_contact_forces": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_get_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_set_populations": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_get_populations": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -101,7 +103,7 @@ def make_config(nx: int, ny: int, nz: int, *, lattice: int = 19, storage: str | 
                 max_particles: int = 1, tau: float = 0.8, rho0: float = 1.0, c0: float = 1.0,
                 u0=(0.0, 0.0, 0.0), force=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0),
                 kn: float = 0.0, eta_n: float = 0.0, kt: float = 0.0, eta_t: float = 0.0, mu_s: float = 0.0,
-                c_tol: float = 1e-6, mass_spacing: float = 0.5) -> LbmConfig:
+                c_tol: float = 1e-6, mass_spacing: float = 0.5, dem_fp64: int = 0) -> LbmConfig:
     c = LbmConfig()
     c.nx, c.ny, c.nz = nx, ny, nz
     c.lattice = lattice
@@ -113,6 +115,7 @@ def make_config(nx: int, ny: int, nz: int, *, lattice: int = 19, storage: str | 
     c.tau, c.rho0, c.c0 = tau, rho0, c0
     c.kn, c.eta_n, c.kt, c.eta_t, c.mu_s, c.c_tol = kn, eta_n, kt, eta_t, mu_s, c_tol
     c.mass_spacing = mass_spacing
+    c.dem_fp64 = int(dem_fp64)
     return c
 
 
@@ -203,6 +206,14 @@ class Lattice:
         T = np.zeros((n, 3))
         self._ok(self.L.lbm_get_forces(self.h, F.ctypes.data_as(C.POINTER(C.c_double)),
                                        T.ctypes.data_as(C.POINTER(C.c_double)), None), self.h)
+        return F[: self.np], T[: self.np]
+
+    def contact_forces(self):
+        n = max(1, self.np)
+        F = np.zeros((n, 3))
+        T = np.zeros((n, 3))
+        self._ok(self.L.lbm_get_contact_forces(self.h, F.ctypes.data_as(C.POINTER(C.c_double)),
+                                               T.ctypes.data_as(C.POINTER(C.c_double))), self.h)
         return F[: self.np], T[: self.np]
 
     def particles(self) -> list[dict]:
