@@ -185,8 +185,19 @@ int lbm_get_populations(lbm_handle *h, void *dev_f);
  * some fluid node moves faster than 0.5 (checked over the whole lattice). */
 int lbm_check(lbm_handle *h);
 
-/* Counters of the last step: new fluid nodes refilled and particle links. */
-int lbm_get_counters(lbm_handle *h, int64_t *steps, int32_t *nrefill, int32_t *nlinks);
+/* Counters of the last step (any pointer may be NULL): steps taken since
+ * lbm_init, new fluid nodes refilled (§2.3.3), particle links (fluid node,
+ * direction) updated by VIBB or bounce-back, and 32x4x2-node bricks the sweep
+ * treated as near a particle (the rest took the plain path). */
+int lbm_get_counters(lbm_handle *h, int64_t *steps, int32_t *nrefill, int32_t *nlinks, int32_t *near_bricks);
+
+/* Launch schedule of the sweep.  plain_ctas_per_sm: CTAs per SM of the
+ * persistent plain-brick sweep (1..4; fewer leave CTA slots to the particle
+ * kernels that run beside it; 0 = one CTA per brick).  chain_ctas_per_sm:
+ * CTAs per SM of the persistent flag and near-brick sweeps (1..4; 0 = the
+ * default).  Takes effect from the next lbm_step(); results do not depend on
+ * it.  Defaults: 0 and 0 (one plain CTA per brick, 4 flag/near CTAs per SM). */
+int lbm_set_schedule(lbm_handle *h, int plain_ctas_per_sm, int chain_ctas_per_sm);
 
 /* Kernels launched per lbm_step() step (for launch accounting). */
 int lbm_kernels_per_step(const lbm_handle *h);

@@ -30,6 +30,7 @@ constexpr int kThreads = 512;
 constexpr int kMaxP = kDem32MaxParticles;
 constexpr int kMaxAdj = kDemMaxAdj;
 constexpr int kWords = kMaxP / 32;
+constexpr int kMaxItems = 1024;  // candidate pairs resident in shared memory
 constexpr float kSkin = 1.0f;
 
 // ---------------------------------------------------------------------------
@@ -97,7 +98,9 @@ __device__ __forceinline__ void exp_half(float hh, float qh2, const float w[3], 
 }
 
 // ---------------------------------------------------------------------------
-// shared tables
+// shared tables: everything a sub-step touches lives here for the whole
+// launch (the contact state is loaded from global memory once and written
+// back once), so the sub-step chain never waits on an L2 round trip
 // ---------------------------------------------------------------------------
 struct Shared {
     float xh[kMaxP][3], xl[kMaxP][3];   // position, compensated
@@ -105,14 +108,21 @@ struct Shared {
     float w[kMaxP][3];                  // angular velocity (world)
     float xref[kMaxP][3];               // position at the last list build
     float Fc[kMaxP][3], Tc[kMaxP][3];   // contact force / torque of the last evaluation
-    float rc[kDem32MaxCp][3];           // control points R(q) cpb, relative to x
+    float brad[kMaxP], Rs[kMaxP], reach[kMaxP];
+    float4 rc[kDem32MaxCp];             // control points R(q) cpb relative to x, and K
     int cpo[kMaxP + 1];                 // offsets into rc
     unsigned bits[kMaxP][kWords];       // candidate pairs (i < j)
     unsigned short up[kMaxP][kMaxAdj];  // partners j > i, ascending
     int dn[kMaxP][kMaxAdj];             // (m << 8 | slot of k in up[m]), m < k, ascending
     int nup[kMaxP], ndn[kMaxP];
-    int ioff[kMaxP + 1];                // prefix sums of nup (pair items)
-    float reach[kMaxP];
+    int ioff[kMaxP + 1];                // prefix sums of nup: item of (i, slot) = ioff[i] + slot
+    // candidate pairs: contact history and results
+    int it_on[kMaxItems];
+    float it_xm[kMaxItems][3], it_xi[kMaxItems][3];
+    float it_res[kMaxItems][9];         // F_i, T_i, T_j
+    // walls: contact history
+    int w_on[kMaxP][NWALL];
+    float w_xcw[kMaxP][NWALL][3], w_xi[kMaxP][NWALL][3];
 };
 
 __device__ __forceinline__ void rel_vec(const Shared &S, const Params &P, int i, int j, float d[3]) {
@@ -121,18 +131,19 @@ __device__ __forceinline__ void rel_vec(const Shared &S, const Params &P, int i,
 }
 
 // M, grad M and Hessian (xx yy zz xy xz yz) of one metaball at y, control
-// points at rc + off
-__device__ void mb_dd_f(const float (*rc)[3], const float *K, int ncp, const float off[3], const float y[3], float &M,
-                        float g[3], float H[6]) {
+// points at rc + off (weights in rc[].w)
+__device__ void mb_dd_f(const float4 *rc, int ncp, const float off[3], const float y[3], float &M, float g[3],
+                        float H[6]) {
     M = 0.f;
     for (int a = 0; a < 3; a++) g[a] = 0.f;
     for (int a = 0; a < 6; a++) H[a] = 0.f;
     for (int c = 0; c < ncp; c++) {
-        const float r0 = y[0] - (rc[c][0] + off[0]), r1 = y[1] - (rc[c][1] + off[1]), r2_ = y[2] - (rc[c][2] + off[2]);
+        const float4 cp = rc[c];
+        const float r0 = y[0] - (cp.x + off[0]), r1 = y[1] - (cp.y + off[1]), r2_ = y[2] - (cp.z + off[2]);
         const float r2 = r0 * r0 + r1 * r1 + r2_ * r2_;
         const float ir = __frcp_rn(r2);
-        const float Kr = K[c] * ir;          // K / r^2
-        const float a1 = -2.0f * Kr * ir;    // -2 K / r^4
+        const float Kr = cp.w * ir;            // K / r^2
+        const float a1 = -2.0f * Kr * ir;      // -2 K / r^4
         const float a2 = 8.0f * Kr * ir * ir;  // 8 K / r^6
         M += Kr;
         g[0] = fmaf(a1, r0, g[0]);
@@ -170,14 +181,20 @@ __device__ void contact_law_f(const Params &P, float delta, const float n[3], co
     for (int a = 0; a < 3; a++) F[a] = Fn * n[a] + Ft[a];
 }
 
+// Newton stops when the step is below 1e-5 lu (FP32 resolution of these
+// O(radius) coordinates is ~1e-6) or stops shrinking after a few steps.
+constexpr int kNewtonMax = 30;
+constexpr float kNewtonTol2 = 1e-10f;
+
 // Pair geometry, Eqs. (5)-(9), in the frame centred on particle i (d = x_j -
 // x_i).  Same steps as the FP64 path: Newton on grad(M_i + M_j) = 0, valid
 // when c_tol < M < 1 for both, closest points by the first-order step, contact
 // point in the middle of the overlap.
-__device__ bool pair_geom_f(const Params &P, const Shared &S, const DevParticle &pi, const DevParticle &pj, int i,
-                            int j, const float d[3], bool warm, float xm[3], float &delta, float nv[3], float xcp[3]) {
-    const float(*rci)[3] = S.rc + S.cpo[i];
-    const float(*rcj)[3] = S.rc + S.cpo[j];
+__device__ bool pair_geom_f(const Params &P, const Shared &S, int i, int j, const float d[3], bool warm, float xm[3],
+                            float &delta, float nv[3], float xcp[3]) {
+    const float4 *rci = S.rc + S.cpo[i];
+    const float4 *rcj = S.rc + S.cpo[j];
+    const int nci = S.cpo[i + 1] - S.cpo[i], ncj = S.cpo[j + 1] - S.cpo[j];
     const float zero[3] = {0.f, 0.f, 0.f};
     float x[3];
     if (warm) {
@@ -185,21 +202,24 @@ __device__ bool pair_geom_f(const Params &P, const Shared &S, const DevParticle 
     } else {
         float best = 3.4e38f;
         x[0] = x[1] = x[2] = 0.f;
-        for (int a = 0; a < pi.ncp; a++)
-            for (int b = 0; b < pj.ncp; b++) {
-                float dd[3];
-                for (int c = 0; c < 3; c++) dd[c] = (d[c] + rcj[b][c]) - rci[a][c];
+        for (int a = 0; a < nci; a++)
+            for (int b = 0; b < ncj; b++) {
+                const float dd[3] = {(d[0] + rcj[b].x) - rci[a].x, (d[1] + rcj[b].y) - rci[a].y,
+                                     (d[2] + rcj[b].z) - rci[a].z};
                 const float d2 = dot3f(dd, dd);
                 if (d2 < best) {
                     best = d2;
-                    for (int c = 0; c < 3; c++) x[c] = rci[a][c] + 0.5f * dd[c];
+                    x[0] = rci[a].x + 0.5f * dd[0];
+                    x[1] = rci[a].y + 0.5f * dd[1];
+                    x[2] = rci[a].z + 0.5f * dd[2];
                 }
             }
     }
     float M0, g0[3], H0[6], M1, g1[3], H1[6];
-    for (int it = 0; it < 30; it++) {
-        mb_dd_f(rci, pi.K_f, pi.ncp, zero, x, M0, g0, H0);
-        mb_dd_f(rcj, pj.K_f, pj.ncp, d, x, M1, g1, H1);
+    float prev = 3.4e38f;
+    for (int it = 0; it < kNewtonMax; it++) {
+        mb_dd_f(rci, nci, zero, x, M0, g0, H0);
+        mb_dd_f(rcj, ncj, d, x, M1, g1, H1);
         float H[6], g[3];
         for (int a = 0; a < 6; a++) H[a] = H0[a] + H1[a];
         for (int a = 0; a < 3; a++) g[a] = -(g0[a] + g1[a]);
@@ -210,42 +230,44 @@ __device__ bool pair_geom_f(const Params &P, const Shared &S, const DevParticle 
         const float det = H[0] * c0 + H[3] * c1 + H[4] * c2;
         if (det == 0.f || !isfinite(det)) break;
         const float id = __frcp_rn(det);
-        const float b01 = H[4] * H[5] - H[3] * H[2], b02 = H[3] * H[5] - H[4] * H[1];
         const float b11 = H[0] * H[2] - H[4] * H[4], b12 = H[4] * H[3] - H[0] * H[5];
         const float b22 = H[0] * H[1] - H[3] * H[3];
         float dx[3];
-        dx[0] = (c0 * g[0] + b01 * g[1] + b02 * g[2]) * id;
+        dx[0] = (c0 * g[0] + c1 * g[1] + c2 * g[2]) * id;
         dx[1] = (c1 * g[0] + b11 * g[1] + b12 * g[2]) * id;
         dx[2] = (c2 * g[0] + b12 * g[1] + b22 * g[2]) * id;
         for (int a = 0; a < 3; a++) x[a] += dx[a];
-        if (dot3f(dx, dx) < 1e-10f) break;
+        const float s2 = dot3f(dx, dx);
+        if (s2 < kNewtonTol2 || (it >= 3 && s2 >= prev)) break;
+        prev = s2;
     }
     for (int a = 0; a < 3; a++) xm[a] = x[a];
-    mb_dd_f(rci, pi.K_f, pi.ncp, zero, x, M0, g0, H0);
-    mb_dd_f(rcj, pj.K_f, pj.ncp, d, x, M1, g1, H1);
+    mb_dd_f(rci, nci, zero, x, M0, g0, H0);
+    mb_dd_f(rcj, ncj, d, x, M1, g1, H1);
     if (!(M0 > P.c_tol_f && M0 < 1.0f && M1 > P.c_tol_f && M1 < 1.0f)) return false;
     const float q0 = (1.0f - M0) * __frcp_rn(dot3f(g0, g0)), q1 = (1.0f - M1) * __frcp_rn(dot3f(g1, g1));
     float dc[3];
     for (int a = 0; a < 3; a++) dc[a] = q0 * g0[a] - q1 * g1[a];
     const float dist = sqrtf(dot3f(dc, dc));
-    delta = pi.Rs_f + pj.Rs_f - dist;
+    delta = S.Rs[i] + S.Rs[j] - dist;
     if (!(delta > 0.f) || dist == 0.f) return false;
     const float idist = __frcp_rn(dist);
     for (int a = 0; a < 3; a++) {
         nv[a] = dc[a] * idist;
-        xcp[a] = (x[a] + q0 * g0[a]) - (pi.Rs_f - 0.5f * delta) * nv[a];
+        xcp[a] = (x[a] + q0 * g0[a]) - (S.Rs[i] - 0.5f * delta) * nv[a];
     }
     return true;
 }
 
 // Wall geometry, Eqs. (10)-(13), frame centred on the particle; prel: the
 // wall plane's coordinate relative to x along its axis.
-__device__ bool wall_geom_f(const Params &P, const Shared &S, const DevParticle &p, int k, int wall, float prel,
-                            bool warm, float xcw[3], float &delta, float nv[3], float xcp[3]) {
+__device__ bool wall_geom_f(const Params &P, const Shared &S, int k, int wall, float prel, bool warm, float xcw[3],
+                            float &delta, float nv[3], float xcp[3]) {
     const int ax = wall / 2, side = wall % 2;
     const float m_ax = side ? 1.0f : -1.0f;
     const int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
-    const float(*rc)[3] = S.rc + S.cpo[k];
+    const float4 *rc = S.rc + S.cpo[k];
+    const int nc = S.cpo[k + 1] - S.cpo[k];
     const float zero[3] = {0.f, 0.f, 0.f};
     float x[3];
     if (warm) {
@@ -253,19 +275,21 @@ __device__ bool wall_geom_f(const Params &P, const Shared &S, const DevParticle 
     } else {
         int kb = 0;
         float best = 3.4e38f;
-        for (int c = 0; c < p.ncp; c++) {
-            const float dd = fabsf(prel - rc[c][ax]);
+        for (int c = 0; c < nc; c++) {
+            const float pc = ax == 0 ? rc[c].x : (ax == 1 ? rc[c].y : rc[c].z);
+            const float dd = fabsf(prel - pc);
             if (dd < best) { best = dd; kb = c; }
         }
-        for (int a = 0; a < 3; a++) x[a] = rc[kb][a];
+        x[0] = rc[kb].x; x[1] = rc[kb].y; x[2] = rc[kb].z;
     }
     x[ax] = prel;
     // H index of (a, b)
     auto hidx = [](int a, int b) { return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5)); };
     const int i11 = hidx(t1, t1), i12 = hidx(t1, t2), i22 = hidx(t2, t2);
     float M, g[3], H[6];
-    for (int it = 0; it < 30; it++) {
-        mb_dd_f(rc, p.K_f, p.ncp, zero, x, M, g, H);
+    float prev = 3.4e38f;
+    for (int it = 0; it < kNewtonMax; it++) {
+        mb_dd_f(rc, nc, zero, x, M, g, H);
         const float J00 = H[i11], J01 = H[i12], J11 = H[i22];
         const float det = J00 * J11 - J01 * J01;
         if (det == 0.f || !isfinite(det)) break;
@@ -274,16 +298,18 @@ __device__ bool wall_geom_f(const Params &P, const Shared &S, const DevParticle 
         const float d0 = (J11 * r0 - J01 * r1) * id, d1 = (-J01 * r0 + J00 * r1) * id;
         x[t1] += d0;
         x[t2] += d1;
-        if (d0 * d0 + d1 * d1 < 1e-10f) break;
+        const float s2 = d0 * d0 + d1 * d1;
+        if (s2 < kNewtonTol2 || (it >= 3 && s2 >= prev)) break;
+        prev = s2;
     }
     for (int a = 0; a < 3; a++) xcw[a] = x[a];
-    mb_dd_f(rc, p.K_f, p.ncp, zero, x, M, g, H);
+    mb_dd_f(rc, nc, zero, x, M, g, H);
     if (!(g[ax] * m_ax < 0.f)) return false;
     const float qR = (1.0f - M) * __frcp_rn(dot3f(g, g));
     float dc[3];
     for (int a = 0; a < 3; a++) dc[a] = qR * g[a];
     const float dist = sqrtf(dot3f(dc, dc));
-    delta = p.Rs_f - dist;
+    delta = S.Rs[k] - dist;
     if (!(delta > 0.f) || dist == 0.f) return false;
     const float idist = __frcp_rn(dist);
     for (int a = 0; a < 3; a++) {
@@ -293,23 +319,41 @@ __device__ bool wall_geom_f(const Params &P, const Shared &S, const DevParticle 
     return true;
 }
 
+// Pair contact history of the candidate items to global memory (before the
+// list is rebuilt, and at the end of the launch).
+__device__ void store_items(const Params &P, Shared &S) {
+    const int np = P.np;
+    for (int i = threadIdx.x; i < np; i += blockDim.x)
+        for (int s = 0; s < S.nup[i]; s++) {
+            const int it = S.ioff[i] + s;
+            if (it >= kMaxItems) break;
+            const int pidx = i * np + S.up[i][s];
+            P.pair_on[pidx] = S.it_on[it];
+            for (int a = 0; a < 3; a++) {
+                P.pair_xm_f[3 * pidx + a] = S.it_xm[it][a];
+                P.pair_xi_f[3 * pidx + a] = S.it_xi[it][a];
+            }
+        }
+}
+
 // Candidate pairs: bounding spheres closer than the skin.  Pairs that drop
 // out lose their contact history, as in the FP64 path.  Sets *possible when
 // some pair is within reach of a contact this step (or one is active).
+// Loads the candidates' contact history into shared memory.
 __device__ void build_lists(const Params &P, Shared &S, int *possible) {
     const int np = P.np, tid = threadIdx.x;
     const int nw = (np + 31) / 32;
     for (int idx = tid; idx < np * nw; idx += blockDim.x) {
         const int i = idx / nw, wd = idx % nw;
         unsigned m = 0;
-        const float bri = P.parts[i].brad_f, ri = S.reach[i];
+        const float bri = S.brad[i], ri = S.reach[i];
         for (int b = 0; b < 32; b++) {
             const int j = wd * 32 + b;
             if (j <= i || j >= np) continue;
             float d[3];
             rel_vec(S, P, i, j, d);
             const float d2 = dot3f(d, d);
-            const float brs = bri + P.parts[j].brad_f;
+            const float brs = bri + S.brad[j];
             const float lim = brs + kSkin;
             const bool on = P.pair_on[i * np + j] != 0;
             if (d2 < lim * lim) {
@@ -362,15 +406,28 @@ __device__ void build_lists(const Params &P, Shared &S, int *possible) {
         int o = 0;
         for (int i = 0; i < np; i++) { S.ioff[i] = o; o += S.nup[i]; }
         S.ioff[np] = o;
+        if (o > kMaxItems) atomicOr(&P.status[ST_ERR], ERRB_DEM_CAPACITY);
     }
+    __syncthreads();
+    for (int i = tid; i < np; i += blockDim.x)
+        for (int s = 0; s < S.nup[i]; s++) {
+            const int it = S.ioff[i] + s;
+            if (it >= kMaxItems) break;
+            const int pidx = i * np + S.up[i][s];
+            S.it_on[it] = P.pair_on[pidx];
+            for (int a = 0; a < 3; a++) {
+                S.it_xm[it][a] = P.pair_xm_f[3 * pidx + a];
+                S.it_xi[it][a] = P.pair_xi_f[3 * pidx + a];
+            }
+        }
     __syncthreads();
 }
 
 // Pair contacts of the candidate list (one item per thread); results into
-// dem_res[i][slot] (zeros when not in contact).
+// it_res (zeros when not in contact).
 __device__ void pair_contacts(const Params &P, Shared &S, float h) {
     const int np = P.np;
-    const int total = S.ioff[np];
+    const int total = min(S.ioff[np], kMaxItems);
     for (int it = threadIdx.x; it < total; it += blockDim.x) {
         int lo = 0, hi = np - 1;  // item -> (i, slot): last i with ioff[i] <= it
         while (lo < hi) {
@@ -378,39 +435,35 @@ __device__ void pair_contacts(const Params &P, Shared &S, float h) {
             if (S.ioff[mid] <= it) lo = mid; else hi = mid - 1;
         }
         const int i = lo, s = it - S.ioff[i], j = S.up[i][s];
-        float *out = P.dem_res + ((size_t)i * kMaxAdj + s) * 9;
-        const DevParticle &pi = P.parts[i], &pj = P.parts[j];
-        const int pidx = i * np + j;
         float d[3];
         rel_vec(S, P, i, j, d);
-        const float brs = pi.brad_f + pj.brad_f;
+        const float brs = S.brad[i] + S.brad[j];
         float Fi[3] = {0.f, 0.f, 0.f}, ti[3] = {0.f, 0.f, 0.f}, tj[3] = {0.f, 0.f, 0.f};
         if (dot3f(d, d) > brs * brs) {
-            P.pair_on[pidx] = 0;
+            S.it_on[it] = 0;
         } else {
-            const bool warm = P.pair_on[pidx] != 0;
-            float xm[3], delta, nv[3], xcp[3];
-            for (int a = 0; a < 3; a++) xm[a] = P.pair_xm_f[3 * pidx + a];
-            if (!pair_geom_f(P, S, pi, pj, i, j, d, warm, xm, delta, nv, xcp)) {
-                P.pair_on[pidx] = 0;
+            const bool warm = S.it_on[it] != 0;
+            float xm[3] = {S.it_xm[it][0], S.it_xm[it][1], S.it_xm[it][2]}, delta, nv[3], xcp[3];
+            if (!pair_geom_f(P, S, i, j, d, warm, xm, delta, nv, xcp)) {
+                S.it_on[it] = 0;
             } else {
                 float xi[3];
-                for (int a = 0; a < 3; a++) xi[a] = warm ? P.pair_xi_f[3 * pidx + a] : 0.f;
-                P.pair_on[pidx] = 1;
-                for (int a = 0; a < 3; a++) P.pair_xm_f[3 * pidx + a] = xm[a];
+                for (int a = 0; a < 3; a++) xi[a] = warm ? S.it_xi[it][a] : 0.f;
+                S.it_on[it] = 1;
+                for (int a = 0; a < 3; a++) S.it_xm[it][a] = xm[a];
                 float rj[3], wri[3], wrj[3], vij[3];
                 for (int a = 0; a < 3; a++) rj[a] = xcp[a] - d[a];
                 cross3f(S.w[i], xcp, wri);
                 cross3f(S.w[j], rj, wrj);
                 for (int a = 0; a < 3; a++) vij[a] = (S.v[i][a] + wri[a]) - (S.v[j][a] + wrj[a]);
                 contact_law_f(P, delta, nv, vij, xi, h, Fi);
-                for (int a = 0; a < 3; a++) P.pair_xi_f[3 * pidx + a] = xi[a];
+                for (int a = 0; a < 3; a++) S.it_xi[it][a] = xi[a];
                 const float Fj[3] = {-Fi[0], -Fi[1], -Fi[2]};
                 cross3f(xcp, Fi, ti);
                 cross3f(rj, Fj, tj);
             }
         }
-        for (int a = 0; a < 3; a++) { out[a] = Fi[a]; out[3 + a] = ti[a]; out[6 + a] = tj[a]; }
+        for (int a = 0; a < 3; a++) { S.it_res[it][a] = Fi[a]; S.it_res[it][3 + a] = ti[a]; S.it_res[it][6 + a] = tj[a]; }
     }
 }
 
@@ -419,34 +472,33 @@ __device__ void gather_contacts(const Params &P, Shared &S, int k, float h, floa
     for (int a = 0; a < 3; a++) { F[a] = 0.f; T[a] = 0.f; }
     for (int e = 0; e < S.ndn[k]; e++) {
         const int m = S.dn[k][e] >> 8, s = S.dn[k][e] & 255;
-        const float *o = P.dem_res + ((size_t)m * kMaxAdj + s) * 9;
-        for (int a = 0; a < 3; a++) { F[a] += -o[a]; T[a] += o[6 + a]; }
+        const int it = S.ioff[m] + s;
+        if (it >= kMaxItems) continue;
+        for (int a = 0; a < 3; a++) { F[a] += -S.it_res[it][a]; T[a] += S.it_res[it][6 + a]; }
     }
     for (int s = 0; s < S.nup[k]; s++) {
-        const float *o = P.dem_res + ((size_t)k * kMaxAdj + s) * 9;
-        for (int a = 0; a < 3; a++) { F[a] += o[a]; T[a] += o[3 + a]; }
+        const int it = S.ioff[k] + s;
+        if (it >= kMaxItems) break;
+        for (int a = 0; a < 3; a++) { F[a] += S.it_res[it][a]; T[a] += S.it_res[it][3 + a]; }
     }
-    const DevParticle &p = P.parts[k];
     for (int wall = 0; wall < NWALL; wall++) {
         const int ax = wall / 2, side = wall % 2;
-        const int wj = k * NWALL + wall;
-        if (P.per[ax]) { P.wall_on[wj] = 0; continue; }
+        if (P.per[ax]) { S.w_on[k][wall] = 0; continue; }
         const float plane = side ? P.dim_f[ax] - 0.5f : -0.5f;
         const float prel = (plane - S.xh[k][ax]) - S.xl[k][ax];
-        if (fabsf(prel) > p.brad_f) { P.wall_on[wj] = 0; continue; }
-        const bool warm = P.wall_on[wj] != 0;
-        float xcw[3], delta, nv[3], xcp[3];
-        for (int a = 0; a < 3; a++) xcw[a] = P.wall_xcw_f[3 * wj + a];
-        if (!wall_geom_f(P, S, p, k, wall, prel, warm, xcw, delta, nv, xcp)) { P.wall_on[wj] = 0; continue; }
+        if (fabsf(prel) > S.brad[k]) { S.w_on[k][wall] = 0; continue; }
+        const bool warm = S.w_on[k][wall] != 0;
+        float xcw[3] = {S.w_xcw[k][wall][0], S.w_xcw[k][wall][1], S.w_xcw[k][wall][2]}, delta, nv[3], xcp[3];
+        if (!wall_geom_f(P, S, k, wall, prel, warm, xcw, delta, nv, xcp)) { S.w_on[k][wall] = 0; continue; }
         float xi[3];
-        for (int a = 0; a < 3; a++) xi[a] = warm ? P.wall_xi_f[3 * wj + a] : 0.f;
-        P.wall_on[wj] = 1;
-        for (int a = 0; a < 3; a++) P.wall_xcw_f[3 * wj + a] = xcw[a];
+        for (int a = 0; a < 3; a++) xi[a] = warm ? S.w_xi[k][wall][a] : 0.f;
+        S.w_on[k][wall] = 1;
+        for (int a = 0; a < 3; a++) S.w_xcw[k][wall][a] = xcw[a];
         float wr[3], vi[3], Fi[3], ti[3];
         cross3f(S.w[k], xcp, wr);
         for (int a = 0; a < 3; a++) vi[a] = S.v[k][a] + wr[a];
         contact_law_f(P, delta, nv, vi, xi, h, Fi);
-        for (int a = 0; a < 3; a++) P.wall_xi_f[3 * wj + a] = xi[a];
+        for (int a = 0; a < 3; a++) S.w_xi[k][wall][a] = xi[a];
         cross3f(xcp, Fi, ti);
         for (int a = 0; a < 3; a++) { F[a] += Fi[a]; T[a] += ti[a]; }
     }
@@ -455,7 +507,11 @@ __device__ void gather_contacts(const Params &P, Shared &S, int k, float h, floa
 // Rotated control points of particle k into the shared table.
 __device__ __forceinline__ void put_rc(const Params &P, Shared &S, int k, const float q[4]) {
     const DevParticle &p = P.parts[k];
-    for (int c = 0; c < p.ncp; c++) qrot_f(q, p.cpb_f[c], S.rc[S.cpo[k] + c], true);
+    for (int c = 0; c < p.ncp; c++) {
+        float r[3];
+        qrot_f(q, p.cpb_f[c], r, true);
+        S.rc[S.cpo[k] + c] = make_float4(r[0], r[1], r[2], p.K_f[c]);
+    }
 }
 
 }  // namespace
@@ -476,8 +532,9 @@ __global__ void __launch_bounds__(kThreads) k_dem32(Params P) {
             x[a] = df_load(pp->sx[a]);
             v[a] = df_load(pp->sv[a]);
             wb[a] = df_load(pp->swb[a]);
-            Fh[a] = (float)P.Fh[3 * tid + a];
-            Th[a] = (float)P.Th[3 * tid + a];
+            // the near sweep's fixed-point totals (2^-40 units)
+            Fh[a] = (float)(long long)P.Ffix[6 * tid + a] * (1.0f / (float)(1ull << kForceFixBits));
+            Th[a] = (float)(long long)P.Ffix[6 * tid + 3 + a] * (1.0f / (float)(1ull << kForceFixBits));
             iI[a] = pp->iI_f[a];
             cI[a] = pp->cI_f[a];
             bg[a] = pp->bg_f[a];
@@ -510,11 +567,19 @@ __global__ void __launch_bounds__(kThreads) k_dem32(Params P) {
         }
         const float reach = mov ? (sqrtf(v2) + sqrtf(a2)) * 1.001f + 1e-4f : 0.f;
         S.reach[tid] = reach;
+        S.brad[tid] = pp->brad_f;
+        S.Rs[tid] = pp->Rs_f;
         if (reach > 0.4f * kSkin) possible = 1;
         put_rc(P, S, tid, qf);
         for (int wall = 0; wall < NWALL; wall++) {
             const int ax = wall / 2, side = wall % 2;
-            if (P.wall_on[tid * NWALL + wall]) possible = 1;
+            const int wj = tid * NWALL + wall;
+            S.w_on[tid][wall] = P.wall_on[wj];
+            for (int a = 0; a < 3; a++) {
+                S.w_xcw[tid][wall][a] = P.wall_xcw_f[3 * wj + a];
+                S.w_xi[tid][wall][a] = P.wall_xi_f[3 * wj + a];
+            }
+            if (P.wall_on[wj]) possible = 1;
             if (P.per[ax]) continue;
             const float plane = side ? P.dim_f[ax] - 0.5f : -0.5f;
             const float prel = (plane - x[ax].hi) - x[ax].lo;
@@ -646,6 +711,8 @@ __global__ void __launch_bounds__(kThreads) k_dem32(Params P) {
             }
             moved = __syncthreads_or(moved);
             if (moved && np > 1) {
+                store_items(P, S);
+                __syncthreads();
                 int dummy = 0;
                 build_lists(P, S, &dummy);
             }
@@ -686,7 +753,17 @@ __global__ void __launch_bounds__(kThreads) k_dem32(Params P) {
             float F[3], T[3];
             gather_contacts(P, S, tid, 0.f, F, T);
             for (int a = 0; a < 3; a++) { S.Fc[tid][a] = F[a]; S.Tc[tid][a] = T[a]; }
+            // wall contact history back to global memory
+            for (int wall = 0; wall < NWALL; wall++) {
+                const int wj = tid * NWALL + wall;
+                P.wall_on[wj] = S.w_on[tid][wall];
+                for (int a = 0; a < 3; a++) {
+                    P.wall_xcw_f[3 * wj + a] = S.w_xcw[tid][wall][a];
+                    P.wall_xi_f[3 * wj + a] = S.w_xi[tid][wall][a];
+                }
+            }
         }
+        if (np > 1) store_items(P, S);
     }
 
     // Write back: the compensated state, then the FP64 fields the other
@@ -731,17 +808,18 @@ __global__ void __launch_bounds__(kThreads) k_dem32(Params P) {
     }
 }
 
+// One CTA: a single warp for a few particles (the barriers between the
+// sub-step phases are then nearly free), else kThreads threads.
 void launch_dem32(const Params &P, cudaStream_t st) {
     // the dynamic shared memory limit is raised once per device
     static bool attr_set[64] = {};
+    static_assert(sizeof(Shared) <= 227 * 1024, "k_dem32 tables exceed the shared memory of one CTA");
     const int bytes = (int)sizeof(Shared);
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
-    if (!attr_set[dev]) {
-        if (cudaFuncSetAttribute(k_dem32, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return;
-        attr_set[dev] = true;
-    }
-    k_dem32<<<1, kThreads, bytes, st>>>(P);
+    // a failure here leaves its error for the caller's cudaGetLastError()
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev])
+        attr_set[dev] = cudaFuncSetAttribute(k_dem32, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+    k_dem32<<<1, P.np <= 16 ? 32 : kThreads, bytes, st>>>(P);
 }
 
 }  // namespace lbmmb

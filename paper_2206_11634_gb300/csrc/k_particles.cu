@@ -18,8 +18,13 @@ namespace lbmmb {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_bin(Params P) {
     const int j = blockIdx.x;
-    DevParticle &p = P.parts[j];
     const int t = threadIdx.x;
+    // predicted-near counts, ring of three by step: slot step+1 is filled
+    // below; slot step+2 (consumed by the near sweep of step-1) is cleared
+    // for the next binning
+    if (j == 0 && t == 0 && P.pred_count) P.pred_count[(P.step + 2) % 3] = 0;
+    if (j >= P.np) return;
+    DevParticle &p = P.parts[j];
     if (t < p.ncp) {
         double r[3];
         quat_rot(p.q, p.cpb[t], r);
@@ -73,7 +78,7 @@ __global__ void __launch_bounds__(256) k_bin(Params P) {
         const int bzi = (gz.lo + k / (gxb * gyb)) % P.nbz;
         const int b = bxi + P.nbx * (byi + P.nby * bzi);
         if (atomicExch(&P.pred_stamp_next[b], next) != next) {
-            const int pos = atomicAdd(&P.pred_count[next & 1], 1);
+            const int pos = atomicAdd(&P.pred_count[next % 3], 1);
             P.pred_list_next[pos] = b;
             if (P.skip) P.skip[(next % 3) * P.nbricks + b] = next;
         }
@@ -108,9 +113,6 @@ __global__ void __launch_bounds__(256) k_force_reduce(Params P) {
             }
         }
     }
-    // this step's predicted list has been consumed by the near sweep; clear
-    // its count for the next step but one
-    if (j == 0 && t == 0 && P.pred_count) P.pred_count[P.step & 1] = 0;
     __shared__ double red[8][6];
     const int lane = t & 31, warp = t >> 5;
     for (int q = 0; q < 6; q++) {
@@ -677,6 +679,16 @@ __device__ void rotate_free_quad(unsigned mk, const DevParticle &p, const double
 // particle.  (Lattices stored below FP64 use k_dem32 instead.)
 __global__ void __launch_bounds__(256) k_dem(Params P) {
     const double h = 1.0 / P.n_sub;
+    if (P.force_fixed) {
+        // an FP32 lattice left the hydrodynamic load as fixed-point totals
+        for (int i = threadIdx.x; i < P.np * 6; i += blockDim.x) {
+            const double v = (double)(long long)P.Ffix[i] * (1.0 / (double)(1ull << kForceFixBits));
+            const int k = i / 6, c = i % 6;
+            if (c < 3) P.Fh[3 * k + c] = v;
+            else P.Th[3 * k + c - 3] = v;
+        }
+        __syncthreads();
+    }
     if (!contact_possible(P)) {
         for (int k = threadIdx.x; k < P.np; k += blockDim.x) {
             DevParticle &p = P.parts[k];
@@ -754,7 +766,8 @@ __global__ void __launch_bounds__(256) k_dem(Params P) {
 }
 
 void launch_bin(const Params &P, cudaStream_t st) {
-    if (P.np > 0) k_bin<<<P.np, 256, 0, st>>>(P);
+    // runs every step, with no particle too (it keeps the count ring)
+    k_bin<<<P.np > 0 ? P.np : 1, 256, 0, st>>>(P);
 }
 void launch_force_reduce(const Params &P, cudaStream_t st) {
     if (P.np > 0) k_force_reduce<<<P.np, 256, 0, st>>>(P);

@@ -16,9 +16,11 @@
 //
 // Bricks with no particle in their list take the plain path: 19 coalesced
 // loads and 19 coalesced stores per node, no flag reads.  Per-link force and
-// torque terms are accumulated per listed particle, reduced across the CTA in
-// a fixed order (warp butterfly, then warps in order) and written as FP64
-// partials per (brick, particle); k_force_reduce sums them in brick order.
+// torque terms are accumulated per listed particle.  FP64 lattices reduce them
+// across the CTA in a fixed order (warp butterfly, then warps in order) into
+// FP64 partials per (brick, particle) that k_force_reduce sums in brick order;
+// lattices below FP64 add each warp's FP32 sums to 64-bit fixed-point totals
+// per particle with integer atomics (exact, so the order does not matter).
 #pragma once
 
 #include "k_flags.cuh"
@@ -289,7 +291,7 @@ __device__ __noinline__ void solid_node(const Params &P, const SmemParticles &sp
 // Collide one node and store it: moments (Eq. (18)) with the half-force
 // shift, BGK toward f^eq (Eqs. (15)-(16)) plus Guo's forcing term (compiled
 // out when the body force is zero).
-template <typename S, int Q, bool kForce>
+template <typename S, int Q, bool kForce, bool kStream = false>
 __device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>::C (&fin)[Q], S *B, long long N,
                                               int n) {
     using L = Lat<Q>;
@@ -327,7 +329,8 @@ __device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>
             const C eF = ex * Fx + ey * Fy + ez * Fz;
             out += gfac * w * (C(3) * (eF - uF) + C(9) * eu * eF);
         }
-        Cd::st(B + (long long)i * N + n, out, w, rho0);
+        if (kStream) Cd::st_s(B + (long long)i * N + n, out, w, rho0);
+        else Cd::st(B + (long long)i * N + n, out, w, rho0);
     }
 }
 
@@ -347,7 +350,7 @@ __device__ __forceinline__ void neighbour_coords(const Params &P, int x, int y, 
 // A node of a brick no particle reaches: pull, halfway bounce-back at walls
 // (the node's own outgoing population), collide.  No flags are read.  Node
 // indices are 32-bit (the lattice holds fewer than 2^31 nodes).
-template <typename S, int Q, bool kForce>
+template <typename S, int Q, bool kForce, bool kStream = false>
 __device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z, int n) {
     using L = Lat<Q>;
     using Cd = Codec<S>;
@@ -370,9 +373,9 @@ __device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z,
         const bool wall = (xs[bx] | ys[by] | zs[bz]) < 0;
         // wall: f_i = f+_i'(x), the node's own opposite population
         const S *src = wall ? A + (long long)L::opp(i) * N + n : A + (long long)i * N + (xs[bx] + row[by][bz]);
-        fin[i] = Cd::ld(src, (C)L::w(i), rho0);
+        fin[i] = kStream ? Cd::ld_s(src, (C)L::w(i), rho0) : Cd::ld(src, (C)L::w(i), rho0);
     }
-    collide_store<S, Q, kForce>(P, fin, B, N, n);
+    collide_store<S, Q, kForce, kStream>(P, fin, B, N, n);
 }
 
 // The unknown of one particle link, computed by any lane of the warp: the
@@ -572,9 +575,23 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
         }
     }
 
-    {
+    if (sizeof(C) == 4) {
+        // per-warp FP32 sums (fixed butterfly order) added to the exact
+        // fixed-point totals with integer atomics: no barrier, no FP64
+        for (int s = 0; s < cnt; s++) {
+            const int pid = sp.id[s];
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                const float v = warp_sum<float>((float)acc[s][c]);
+                if (lane == 0 && v != 0.0f)
+                    atomicAdd(&P.Ffix[pid * 6 + c],
+                              (unsigned long long)__float2ll_rn(v * (float)(1ull << kForceFixBits)));
+            }
+        }
+        const int nl = __reduce_add_sync(0xffffffffu, (unsigned)nlinks);
+        if (lane == 0 && nl) atomicAdd(&P.counters[CNT_NLINKS], nl);
+    } else {
         // deterministic CTA reduction of the per-particle terms
-        const int lane = tid & 31, warp = tid >> 5;
         for (int s = 0; s < cnt; s++) {
             for (int c = 0; c < 6; c++) {
                 C v = acc[s][c];
@@ -600,13 +617,16 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
 // path only.  Runs on its own stream, concurrently with the particle kernels.
 template <typename S, int Q, bool kForce>
 __global__ void __launch_bounds__(BRICK, 4) k_sweep_plain(Params P) {
-    const int b = blockIdx.x;
-    if (P.skip && P.skip[(P.step % 3) * P.nbricks + b] == P.step) return;  // the near sweep takes it
-    int bxi, byi, bzi;
-    brick_coords(P, b, bxi, byi, bzi);
     const int tid = threadIdx.x;
-    const int x = bxi * BX + tid % BX, y = byi * BY + (tid / BX) % BY, z = bzi * BZ + tid / (BX * BY);
-    if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce>(P, x, y, z, x + P.nx * (y + P.ny * z));
+    // persistent over the bricks when the grid is smaller than the brick
+    // count (it then leaves CTA slots to the particle kernels running beside)
+    for (int b = blockIdx.x; b < P.nbricks; b += gridDim.x) {
+        if (P.skip && P.skip[(P.step % 3) * P.nbricks + b] == P.step) continue;  // the near sweep takes it
+        int bxi, byi, bzi;
+        brick_coords(P, b, bxi, byi, bzi);
+        const int x = bxi * BX + tid % BX, y = byi * BY + (tid / BX) % BY, z = bzi * BZ + tid / (BX * BY);
+        if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce, true>(P, x, y, z, x + P.nx * (y + P.ny * z));
+    }
 }
 
 // The sweep of the bricks listed this step (exactly those some particle's
@@ -621,7 +641,8 @@ __global__ void __launch_bounds__(BRICK, 4) k_sweep_near(Params P) {
     const int tid = threadIdx.x;
     const int t = P.step;
     const int c_exact = P.counters[CNT_LISTED];
-    const int c_pred = P.pred_stamp_cur ? P.pred_count[t & 1] : 0;
+    const int c_pred = P.pred_stamp_cur ? P.pred_count[t % 3] : 0;
+    int done = 0;
     for (int w = blockIdx.x; w < c_exact + c_pred; w += gridDim.x) {
         int b;
         if (w < c_exact) {
@@ -630,6 +651,7 @@ __global__ void __launch_bounds__(BRICK, 4) k_sweep_near(Params P) {
             b = P.pred_list_cur[w - c_exact];
             if (P.stamp[b] == t) continue;  // listed: taken above
         }
+        done++;
         int bxi, byi, bzi;
         brick_coords(P, b, bxi, byi, bzi);
         const int bx0 = bxi * BX, by0 = byi * BY, bz0 = bzi * BZ;
@@ -644,6 +666,7 @@ __global__ void __launch_bounds__(BRICK, 4) k_sweep_near(Params P) {
         load_smem_particles(P, sp, b, bx0, by0, bz0);
         near_brick<S, Q, kForce>(P, sp, red, &s_links, &ls, b, bx0, by0, bz0, cnt);
     }
+    if (tid == 0 && done) atomicAdd(&P.counters[CNT_NEAR], done);
 }
 
 }  // namespace lbmmb

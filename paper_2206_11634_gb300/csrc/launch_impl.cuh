@@ -15,25 +15,28 @@ void launch_init_t(const Params &P, void *f, cudaStream_t st) {
 }
 template <typename S>
 void launch_flags_t(const Params &P, cudaStream_t st) {
-    const int grid = P.nbricks < kGridStrideBlocks / 2 ? P.nbricks : kGridStrideBlocks / 2;
+    const int cap = P.chain_grid > 0 ? P.chain_grid : kGridStrideBlocks / 2;
+    const int grid = P.nbricks < cap ? P.nbricks : cap;
     if (P.Q == 19) k_flags<S, 19><<<grid, BRICK, 0, st>>>(P);
     else k_flags<S, 15><<<grid, BRICK, 0, st>>>(P);
 }
 template <typename S>
 void launch_sweep_plain_t(const Params &P, cudaStream_t st) {
     const bool force = P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0;
+    const int grid = P.plain_grid > 0 && P.plain_grid < P.nbricks ? P.plain_grid : P.nbricks;
     if (P.Q == 19) {
-        if (force) k_sweep_plain<S, 19, true><<<P.nbricks, BRICK, 0, st>>>(P);
-        else k_sweep_plain<S, 19, false><<<P.nbricks, BRICK, 0, st>>>(P);
+        if (force) k_sweep_plain<S, 19, true><<<grid, BRICK, 0, st>>>(P);
+        else k_sweep_plain<S, 19, false><<<grid, BRICK, 0, st>>>(P);
     } else {
-        if (force) k_sweep_plain<S, 15, true><<<P.nbricks, BRICK, 0, st>>>(P);
-        else k_sweep_plain<S, 15, false><<<P.nbricks, BRICK, 0, st>>>(P);
+        if (force) k_sweep_plain<S, 15, true><<<grid, BRICK, 0, st>>>(P);
+        else k_sweep_plain<S, 15, false><<<grid, BRICK, 0, st>>>(P);
     }
 }
 template <typename S>
 void launch_sweep_near_t(const Params &P, cudaStream_t st) {
     const bool force = P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0;
-    const int grid = P.nbricks < kGridStrideBlocks / 2 ? P.nbricks : kGridStrideBlocks / 2;
+    const int cap = P.chain_grid > 0 ? P.chain_grid : kGridStrideBlocks / 2;
+    const int grid = P.nbricks < cap ? P.nbricks : cap;
     if (P.Q == 19) {
         if (force) k_sweep_near<S, 19, true><<<grid, BRICK, 0, st>>>(P);
         else k_sweep_near<S, 19, false><<<grid, BRICK, 0, st>>>(P);

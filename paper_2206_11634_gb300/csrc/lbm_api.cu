@@ -33,9 +33,10 @@ struct Layout {
     size_t pred_stamp, pred_list, pred_count, skip;
     size_t bin;        // bcount[nbricks] followed by the per-step counters
     size_t bin_bytes;
+    size_t ffix_off;   // offset of the fixed-point force totals within bin
     size_t blist, partial, parts, Fh, Th, Fc, Tc;
     size_t pairF, pair_on, pair_xi, pair_xm, wall_on, wall_xi, wall_xcw;
-    size_t pair_xi_f, pair_xm_f, wall_xi_f, wall_xcw_f, dem_res;
+    size_t pair_xi_f, pair_xm_f, wall_xi_f, wall_xcw_f;
     size_t status;
     size_t total;
     long long N;
@@ -86,9 +87,12 @@ void make_layout(const lbm_config *c, Layout *L) {
     L->stamp = take(nb * 4);
     L->pred_stamp = take(2 * nb * 4);
     L->pred_list = take(2 * nb * 4);
-    L->pred_count = take(2 * 4);
+    L->pred_count = take(3 * 4);
     L->skip = take(3 * nb * 4);
-    L->bin_bytes = nb * 4 + kStepCounters * 4;
+    // per-step region, cleared before every step: brick counts, counters,
+    // and (FP32 and below) the fixed-point force/torque totals
+    L->ffix_off = (nb * 4 + kStepCounters * 4 + 7) / 8 * 8;
+    L->bin_bytes = L->ffix_off + P * 6 * 8;
     L->bin = take(L->bin_bytes);
     L->blist = take(nb * MAXPB * 4);
     L->partial = take(nb * MAXPB * 6 * 8);
@@ -108,7 +112,6 @@ void make_layout(const lbm_config *c, Layout *L) {
     L->pair_xm_f = take(P * P * 12);
     L->wall_xi_f = take(P * NWALL * 12);
     L->wall_xcw_f = take(P * NWALL * 12);
-    L->dem_res = take(P * kDemMaxAdj * 9 * 4);
     L->status = take(ST_SLOTS * 4);
     L->total = o;
 }
@@ -144,6 +147,8 @@ struct lbm_handle {
     int np;
     int dem_f32;   // the FP32 DEM runs (storage, dem_fp64 and the particle set allow it)
     int fc_valid;  // the DEM of the last step left the contact load of the current state
+    int nsm;       // SMs of the device
+    int plain_per_sm, chain_per_sm;  // launch schedule (lbm_set_schedule)
     int64_t steps;
     char err[256];
 };
@@ -209,11 +214,14 @@ Params make_params(lbm_handle *h) {
     P.pair_xm_f = at<float>(h, h->L.pair_xm_f);
     P.wall_xi_f = at<float>(h, h->L.wall_xi_f);
     P.wall_xcw_f = at<float>(h, h->L.wall_xcw_f);
-    P.dem_res = at<float>(h, h->L.dem_res);
     P.dem_f32 = h->dem_f32;
     P.fc_valid = h->fc_valid;
+    P.plain_grid = h->plain_per_sm > 0 ? h->plain_per_sm * h->nsm : 0;
+    P.chain_grid = h->chain_per_sm > 0 ? h->chain_per_sm * h->nsm : 0;
     P.status = at<int>(h, h->L.status);
     P.counters = at<int>(h, h->L.bin + (size_t)h->L.nbricks * 4);
+    P.force_fixed = h->cfg.storage != LBM_STORE_F64;
+    P.Ffix = at<unsigned long long>(h, h->L.bin + h->L.ffix_off);
     return P;
 }
 
@@ -420,6 +428,14 @@ int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_st
     const size_t zero_from = L.flags[0];
     h->aux = h->hi = nullptr;
     h->ev_fork = h->ev_bin = h->ev_plain = h->ev_near = h->ev_join = nullptr;
+    {
+        int dev = 0;
+        h->nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (h->nsm <= 0) h->nsm = 1;
+        h->plain_per_sm = kDefaultPlainPerSm;
+        h->chain_per_sm = kDefaultChainPerSm;
+    }
     int prio_low = 0, prio_high = 0;
     int rc = cuda_check(h, cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high), "cudaDeviceGetStreamPriorityRange");
     if (rc == LBM_OK)
@@ -563,6 +579,8 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
     if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.wall_on, 0, P * NWALL * 4, h->stream), "cudaMemsetAsync");
     if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.Fh, 0, P * 24, h->stream), "cudaMemsetAsync");
     if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.Th, 0, P * 24, h->stream), "cudaMemsetAsync");
+    if (rc == LBM_OK)
+        rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.bin + h->L.ffix_off, 0, P * 48, h->stream), "cudaMemsetAsync");
     // the staging vector dies with this call
     if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (rc == LBM_OK) h->np = n;
@@ -610,7 +628,7 @@ int lbm_step(lbm_handle *h, int nsteps) {
         // fresh brick lists and step counters
         e = cudaMemsetAsync(h->ws + h->L.bin, 0, h->L.bin_bytes, hs);
         if (e != cudaSuccess) return cuda_check(h, e, "cudaMemsetAsync(bricks)");
-        { ProfScope s(h, 0, P.np > 0, hs); launch_bin(P, hs); }
+        { ProfScope s(h, 0, true, hs); launch_bin(P, hs); }
         e = cudaEventRecord(h->ev_bin, hs);
         if (e != cudaSuccess) return cuda_check(h, e, "event record");
         { ProfScope s(h, 1, true, hs); by_storage<DoFlags>(h->cfg.storage, P, hs); }
@@ -630,7 +648,7 @@ int lbm_step(lbm_handle *h, int nsteps) {
         e = cudaEventRecord(h->ev_near, hs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_near, 0);
         if (e != cudaSuccess) return cuda_check(h, e, "stream fork");
-        { ProfScope s(h, 4, P.np > 0, hs); launch_force_reduce(P, hs); }
+        if (!P.force_fixed) { ProfScope s(h, 4, P.np > 0, hs); launch_force_reduce(P, hs); }
         { ProfScope s(h, 5, P.np > 0 && P.n_sub > 0, hs); launch_dem(P, hs); }
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_check(h, e, "kernel launch");
@@ -650,7 +668,10 @@ int lbm_step(lbm_handle *h, int nsteps) {
 
 int lbm_kernels_per_step(const lbm_handle *h) {
     if (!h) return 0;
-    return h->np > 0 ? (h->cfg.n_sub > 0 ? 6 : 5) : 3;
+    // binning (every step), flags, plain and near sweeps; force reduction
+    // (FP64 lattices with particles); DEM (particles, n_sub > 0)
+    if (h->np == 0) return 4;
+    return 4 + (h->cfg.storage == LBM_STORE_F64 ? 1 : 0) + (h->cfg.n_sub > 0 ? 1 : 0);
 }
 
 static int read_status(lbm_handle *h, int *st) {
@@ -678,9 +699,19 @@ int lbm_get_forces(lbm_handle *h, double *F, double *T, lbm_particle *state_out)
     if ((rc = status_code(h, st)) != LBM_OK) return rc;
     const size_t n = (size_t)h->np;
     if (n == 0) return LBM_OK;
-    if (F) rc = cuda_check(h, cudaMemcpyAsync(F, h->ws + h->L.Fh, n * 24, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(F)");
-    if (rc == LBM_OK && T)
-        rc = cuda_check(h, cudaMemcpyAsync(T, h->ws + h->L.Th, n * 24, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(T)");
+    std::vector<long long> fix;
+    if (h->cfg.storage != LBM_STORE_F64) {
+        // FP32 and below: exact fixed-point totals (units of 2^-40)
+        if (F || T) {
+            fix.resize(n * 6);
+            rc = cuda_check(h, cudaMemcpyAsync(fix.data(), h->ws + h->L.bin + h->L.ffix_off, n * 48,
+                                               cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(F)");
+        }
+    } else {
+        if (F) rc = cuda_check(h, cudaMemcpyAsync(F, h->ws + h->L.Fh, n * 24, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(F)");
+        if (rc == LBM_OK && T)
+            rc = cuda_check(h, cudaMemcpyAsync(T, h->ws + h->L.Th, n * 24, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(T)");
+    }
     std::vector<DevParticle> dev;
     if (rc == LBM_OK && state_out) {
         dev.resize(n);
@@ -688,6 +719,12 @@ int lbm_get_forces(lbm_handle *h, double *F, double *T, lbm_particle *state_out)
                                            cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(particles)");
     }
     if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (rc == LBM_OK && !fix.empty())
+        for (size_t j = 0; j < n; j++)
+            for (int a = 0; a < 3; a++) {
+                if (F) F[3 * j + a] = std::ldexp((double)fix[6 * j + a], -kForceFixBits);
+                if (T) T[3 * j + a] = std::ldexp((double)fix[6 * j + 3 + a], -kForceFixBits);
+            }
     if (rc == LBM_OK && state_out) {
         for (size_t j = 0; j < n; j++) {
             const DevParticle &d = dev[j];
@@ -767,7 +804,7 @@ int lbm_check(lbm_handle *h) {
     return LBM_OK;
 }
 
-int lbm_get_counters(lbm_handle *h, int64_t *steps, int32_t *nrefill, int32_t *nlinks) {
+int lbm_get_counters(lbm_handle *h, int64_t *steps, int32_t *nrefill, int32_t *nlinks, int32_t *near_bricks) {
     if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
     int c[kStepCounters];
     int rc = cuda_check(h, cudaMemcpyAsync(c, h->ws + h->L.bin + (size_t)h->L.nbricks * 4, sizeof(c),
@@ -775,8 +812,9 @@ int lbm_get_counters(lbm_handle *h, int64_t *steps, int32_t *nrefill, int32_t *n
     if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (rc != LBM_OK) return rc;
     if (steps) *steps = h->steps;
-    if (nrefill) *nrefill = c[0];
-    if (nlinks) *nlinks = c[1];
+    if (nrefill) *nrefill = c[CNT_NREFILL];
+    if (nlinks) *nlinks = c[CNT_NLINKS];
+    if (near_bricks) *near_bricks = c[CNT_NEAR];
     return LBM_OK;
 }
 
@@ -815,6 +853,15 @@ int lbm_profile_read(lbm_handle *h, int kernel, double *total_ms, int64_t *launc
     }
     if (total_ms) *total_ms = sum;
     if (launches) *launches = h->nrec[kernel];
+    return LBM_OK;
+}
+
+int lbm_set_schedule(lbm_handle *h, int plain_ctas_per_sm, int chain_ctas_per_sm) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    if (plain_ctas_per_sm < 0 || plain_ctas_per_sm > 4 || chain_ctas_per_sm < 0 || chain_ctas_per_sm > 4)
+        return fail(h, LBM_ERR_BAD_ARG, "CTAs per SM must be in 0..4");
+    h->plain_per_sm = plain_ctas_per_sm;
+    h->chain_per_sm = chain_ctas_per_sm;
     return LBM_OK;
 }
 

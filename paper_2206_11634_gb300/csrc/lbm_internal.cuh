@@ -31,13 +31,26 @@ constexpr int ROT_ITERS = 2;  // fixed-point sweeps of the implicit rotational h
 
 // Status words in the workspace.
 enum StatusSlot { ST_ERR = 0, ST_SLOTS = 16 };
-enum StepCounter { CNT_NREFILL = 0, CNT_NLINKS = 1, CNT_LISTED = 2 };
+enum StepCounter { CNT_NREFILL = 0, CNT_NLINKS = 1, CNT_LISTED = 2, CNT_NEAR = 3 };
 enum ErrBits { ERRB_BRICK_OVERFLOW = 1, ERRB_DIVERGED = 2, ERRB_TIMEOUT = 4, ERRB_DEM_CAPACITY = 8 };
+
+// Lattices stored below FP64 accumulate the per-particle force and torque
+// totals in 64-bit fixed point with integer atomics: exact and independent of
+// the order of the additions, without FP64 arithmetic.  Resolution 2^-40
+// (~9e-13), range +-2^23 (~8e6) per component.
+constexpr int kForceFixBits = 40;
+
+// Default launch schedule: one plain-sweep CTA per brick, flags and near
+// sweep persistent over 4 CTAs per SM (measured fastest on the settling
+// metaball: persistent plain grids that leave CTA slots to the particle
+// kernels ran 12-35 % slower per step).
+constexpr int kDefaultPlainPerSm = 0;
+constexpr int kDefaultChainPerSm = 0;
 
 // FP32 DEM limits: its per-particle tables live in one CTA's shared memory.
 constexpr int kDem32MaxParticles = 256;
 constexpr int kDem32MaxCp = 2048;     // control points of all particles
-constexpr int kDemMaxAdj = 24;        // candidate contact partners per particle and direction
+constexpr int kDemMaxAdj = 16;        // candidate contact partners per particle and direction
 
 // ---------------------------------------------------------------------------
 // Lattices.  D3Q19 (rest 1/3, axes 1/18, face diagonals 1/36) and the D3Q15
@@ -109,6 +122,9 @@ __device__ __forceinline__ double lat_w(int i) {
 // ---------------------------------------------------------------------------
 // Storage codecs.  FP64/FP32 store f itself; FP16/BF16 store the offset
 // s_i = f_i/w_i - rho0 (a few 1e-3 in magnitude), decoded as w_i (rho0 + s_i).
+// ld_s / st_s: the same with evict-first cache hints, for the plain sweep,
+// whose data cannot survive in L2 until the next step anyway; it then leaves
+// L2 to the working set of the particle kernels running beside it.
 // ---------------------------------------------------------------------------
 template <typename S>
 struct Codec;
@@ -119,6 +135,8 @@ struct Codec<double> {
     __device__ __forceinline__ static double ld(const double *p, double, double) { return __ldg(p); }
     __device__ __forceinline__ static void st(double *p, double f, double, double) { *p = f; }
     __device__ __forceinline__ static double ld_plain(const double *p, double, double) { return *p; }
+    __device__ __forceinline__ static double ld_s(const double *p, double, double) { return __ldcs(p); }
+    __device__ __forceinline__ static void st_s(double *p, double f, double, double) { __stcs(p, f); }
 };
 template <>
 struct Codec<float> {
@@ -126,6 +144,8 @@ struct Codec<float> {
     __device__ __forceinline__ static float ld(const float *p, float, float) { return __ldg(p); }
     __device__ __forceinline__ static void st(float *p, float f, float, float) { *p = f; }
     __device__ __forceinline__ static float ld_plain(const float *p, float, float) { return *p; }
+    __device__ __forceinline__ static float ld_s(const float *p, float, float) { return __ldcs(p); }
+    __device__ __forceinline__ static void st_s(float *p, float f, float, float) { __stcs(p, f); }
 };
 template <>
 struct Codec<__half> {
@@ -139,6 +159,12 @@ struct Codec<__half> {
     __device__ __forceinline__ static void st(__half *p, float f, float w, float rho0) {
         *p = __float2half_rn(f * (1.0f / w) - rho0);
     }
+    __device__ __forceinline__ static float ld_s(const __half *p, float w, float rho0) {
+        return w * (rho0 + __half2float(__ldcs(p)));
+    }
+    __device__ __forceinline__ static void st_s(__half *p, float f, float w, float rho0) {
+        __stcs(p, __float2half_rn(f * (1.0f / w) - rho0));
+    }
 };
 template <>
 struct Codec<__nv_bfloat16> {
@@ -151,6 +177,12 @@ struct Codec<__nv_bfloat16> {
     }
     __device__ __forceinline__ static void st(__nv_bfloat16 *p, float f, float w, float rho0) {
         *p = __float2bfloat16_rn(f * (1.0f / w) - rho0);
+    }
+    __device__ __forceinline__ static float ld_s(const __nv_bfloat16 *p, float w, float rho0) {
+        return w * (rho0 + __bfloat162float(__ldcs(p)));
+    }
+    __device__ __forceinline__ static void st_s(__nv_bfloat16 *p, float f, float w, float rho0) {
+        __stcs(p, __float2bfloat16_rn(f * (1.0f / w) - rho0));
     }
 };
 
@@ -196,6 +228,8 @@ struct Params {
     long long N;
     int nbx, nby, nbz, nbricks;
     int np, n_sub, vibb, missing_force;
+    int plain_grid;           // CTAs of k_sweep_plain (0: one per brick)
+    int chain_grid;           // CTAs of the persistent k_flags / k_sweep_near (0: default)
     int dem_f32;              // DEM in FP32 with compensated state (k_dem32)
     int fc_valid;             // Fc/Tc hold the contact load of the current state (0 after set_particles)
     double tau, rho0, c0;
@@ -231,7 +265,7 @@ struct Params {
     int *pred_stamp_next;  // [nbricks], written for step + 1 (NULL: no prediction)
     int *pred_list_cur;    // [nbricks]
     int *pred_list_next;   // [nbricks]
-    int *pred_count;       // [2], by step parity
+    int *pred_count;       // [3], ring by step
     // Bricks the plain sweep of a step leaves alone, ring of three by step
     // (== step: binned or predicted near).  The plain sweep of step t runs
     // while the chain of t and the binning of t+1 run; the binning of t+1
@@ -239,7 +273,9 @@ struct Params {
     int *skip;             // [3][nbricks], NULL: none
     int *bcount;       // [nbricks]
     int *blist;        // [nbricks][MAXPB]
-    double *partial;   // [nbricks][MAXPB][6]
+    double *partial;   // [nbricks][MAXPB][6] (FP64 lattices)
+    unsigned long long *Ffix;  // [np][6] fixed-point totals (lattices below FP64), cleared every step
+    int force_fixed, pad_ff;
     DevParticle *parts;
     double *Fh, *Th;   // [np][3]
     double *Fc, *Tc;   // [np][3]
@@ -250,7 +286,6 @@ struct Params {
     double *wall_xi, *wall_xcw;  // [np*6][3]
     float *pair_xi_f, *pair_xm_f;   // [np*np][3], FP32 DEM: spring, warm start (relative to x_i)
     float *wall_xi_f, *wall_xcw_f;  // [np*6][3], FP32 DEM: spring, warm start (relative to x_k)
-    float *dem_res;    // [np][kDemMaxAdj][9], FP32 DEM pair results
     int *status;       // [ST_SLOTS], sticky error bits
     int *counters;     // per-step counters, zeroed with the brick lists
 };

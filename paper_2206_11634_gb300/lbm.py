@@ -71,11 +71,13 @@ _SIGS = {
     "lbm_set_populations": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_get_populations": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_check": (C.c_int, [C.c_void_p]),
-    "lbm_get_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lbm_get_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32)]),
     "lbm_kernels_per_step": (C.c_int, [C.c_void_p]),
     "lbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "lbm_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lbm_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "lbm_flags_noalloc": (C.c_int, [C.POINTER(LbmConfig), C.POINTER(LbmParticle), C.c_int, C.c_void_p, C.c_void_p]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
@@ -225,6 +227,9 @@ class Lattice:
     def step(self, n: int = 1) -> None:
         self._ok(self.L.lbm_step(self.h, int(n)), self.h)
 
+    def set_schedule(self, plain_ctas_per_sm: int, chain_ctas_per_sm: int) -> None:
+        self._ok(self.L.lbm_set_schedule(self.h, int(plain_ctas_per_sm), int(chain_ctas_per_sm)), self.h)
+
     def kernels_per_step(self) -> int:
         return self.L.lbm_kernels_per_step(self.h)
 
@@ -276,6 +281,6 @@ class Lattice:
         return out
 
     def counters(self) -> dict:
-        st, nr, nl = C.c_int64(), C.c_int32(), C.c_int32()
-        self._ok(self.L.lbm_get_counters(self.h, C.byref(st), C.byref(nr), C.byref(nl)), self.h)
-        return dict(step=st.value, nrefill=nr.value, nlinks=nl.value)
+        st, nr, nl, nb = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32()
+        self._ok(self.L.lbm_get_counters(self.h, C.byref(st), C.byref(nr), C.byref(nl), C.byref(nb)), self.h)
+        return dict(step=st.value, nrefill=nr.value, nlinks=nl.value, near_bricks=nb.value)
