@@ -48,8 +48,17 @@ SWEEP_SOURCES = ["k_sweep.cuh", "k_flags.cuh", "lbm_internal.cuh", "launch_impl.
 WORKLOADS = ("settling_metaball", "empty_box", "settling_sphere", "multi_particle")
 
 
-def workload(name: str = "settling_metaball"):
-    """The benchmark's workload (default) or a diagnostic one."""
+def workload(name: str = "settling_metaball", storage: str | None = None):
+    """The benchmark's workload (default) or a diagnostic one; storage
+    overrides the workload's population storage."""
+    wl = _workload(name)
+    if storage:
+        wl["storage"] = storage
+        wl["name"] = f"{wl['name']}_{storage}" if storage != "f32" else wl["name"]
+    return wl
+
+
+def _workload(name: str):
     from paper_2206_11634_gb300 import workloads
     if name == "settling_metaball":
         return workloads.settling_metaball(tau=0.8)
@@ -189,8 +198,13 @@ def make_lattice(pkg, wl, stream):
               max_particles=max(1, len(wl["particles"])), tau=wl["tau"], gravity=wl["gravity"], force=wl["force"],
               kn=wl["kn"], eta_n=wl["eta_n"], kt=wl["kt"], eta_t=wl["eta_t"], mu_s=wl["mu_s"], c_tol=wl["c_tol"])
     lat = pkg.Lattice(wl["nx"], wl["ny"], wl["nz"], stream=stream, **kw)
-    parts = [pkg.make_particle(p["cp"], p["K"], p["x"], q=p["q"], v=p["v"], w=p["w"], Rs=p["Rs"],
-                               density=p["density"], fixed=p["fixed"]) for p in wl["particles"]]
+    parts = []
+    for p in wl["particles"]:
+        kw = dict(q=p["q"], v=p["v"], w=p["w"], Rs=p["Rs"], density=p["density"], fixed=p["fixed"],
+                  mass=p.get("mass", 0.0))
+        if p.get("inertia") is not None:
+            kw["inertia"] = p["inertia"]
+        parts.append(pkg.make_particle(p["cp"], p["K"], p["x"], **kw))
     lat.set_particles(parts)
     return lat
 
@@ -211,9 +225,35 @@ def oracle_sample(wl, steps: int):
     return n * steps / dt / 1e6, dt
 
 
+DRAG_REFERENCE = os.path.join(ROOT, "tests", "golden", "drag_reference.json")
+
+
+def drag_check(pkg, storage: str):
+    """Relative error of the drag F_x of the drag case (a fixed metaball in a
+    periodic, body-force-driven 48^3 box, 1000 steps) in this storage form,
+    against the FP64 oracle's value stored in tests/golden/drag_reference.json
+    (written by tests/golden/make_drag_reference.py)."""
+    import numpy as np
+    from paper_2206_11634_gb300 import workloads
+    ref = json.load(open(DRAG_REFERENCE))
+    wl = workloads.drag_case(storage)
+    wl["particles"][0]["x"] = np.array(ref["x"])
+    lat = make_lattice(pkg, wl, None)
+    lat.step(ref["steps"])
+    F, _ = lat.forces()
+    return {"rel_error_Fx": float(f"{abs(F[0, 0] - ref['F'][0]) / abs(ref['F'][0]):.3e}"), "case": ref["case"],
+            "steps": ref["steps"], "storage": storage, "reference": "FP64 oracle, tests/golden/drag_reference.json"}
+
+
 def omp_threads() -> int:
     v = os.environ.get("OMP_NUM_THREADS")
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+# the oracle takes ~80 ms per step of the 4.2 M-node workload on 16 cores:
+# the reference arm times at most this many of the requested steps
+REFERENCE_MAX_STEPS = 300
+REFERENCE_MAX_WARMUP = 2
 
 
 def run_reference(args):
@@ -223,8 +263,8 @@ def run_reference(args):
     wl = workload(args.workload)
     import oracle
     oracle.build()
-    steps = max(1, args.steps)
-    warm = max(0, args.warmup)
+    steps = max(1, min(args.steps, REFERENCE_MAX_STEPS))
+    warm = max(0, min(args.warmup, REFERENCE_MAX_WARMUP))
     if warm:
         oracle_sample(wl, warm)
     mlups, dt = oracle_sample(wl, steps)
@@ -235,7 +275,8 @@ def run_reference(args):
             "config": {"workload": wl["name"], "lattice": "D3Q19", "storage": "f64", "tau": wl["tau"],
                        "n_sub": wl["n_sub"], "particles": len(wl["particles"])},
             "cpu_baseline": {"value": round(mlups, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{steps} steps of the full {wl['nx']}x{wl['ny']}x{wl['nz']} workload"},
+                             "sample": f"{steps} of the {args.steps} requested steps of the full "
+                                       f"{wl['nx']}x{wl['ny']}x{wl['nz']} workload, {dt:.1f} s"},
             "e2e": {"value": round(mlups, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -251,7 +292,7 @@ def run_gpu(args):
     if rank == 0 or not os.path.exists(pkg.LIB_PATH):
         lib_build.build()
     barrier(dist)
-    wl = workload(args.workload)
+    wl = workload(args.workload, args.storage)
     nodes = wl["nx"] * wl["ny"] * wl["nz"]
     stream = torch.cuda.Stream()
     lat = make_lattice(pkg, wl, stream)
@@ -340,12 +381,15 @@ def run_gpu(args):
                "sample": f"{cpu_steps} steps of the full {wl['nx']}x{wl['ny']}x{wl['nz']} workload, FP64, "
                          f"{dt:.1f} s"}
 
+    pop_mb = 19 * BYTES_PER_VALUE[wl["storage"]] * nodes / 1e6
+    l2_note = (f"no flush: populations 2x{pop_mb:.0f} MB exceed the 129 MB L2" if pop_mb > 129 else
+               f"populations 2x{pop_mb:.0f} MB fit the 129 MB L2 (no flush; L2-resident)")
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": wl["storage"], "data": "synthetic",
             "config": {"workload": wl["name"], "lattice": "D3Q19", "storage": wl["storage"], "tau": wl["tau"],
                        "n_sub": wl["n_sub"], "particles": len(wl["particles"]), "nodes": nodes,
-                       "fluid_nodes": n_fluid, "l2": "no flush: populations 2x319 MB exceed the 129 MB L2",
+                       "fluid_nodes": n_fluid, "l2": l2_note,
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
@@ -356,7 +400,8 @@ def run_gpu(args):
             "kernels": kernels,
             "gpu_launches": int(sum(v[1] for v in prof.values())),
             "clocks": clocks.summary(),
-            "cpu_baseline": cpu}
+            "cpu_baseline": cpu,
+            "drag": drag_check(pkg, wl["storage"])}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -371,6 +416,8 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--cpu-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16", "f64"], default=None,
+                    help="population storage (default: the workload's own)")
     ap.add_argument("--workload", choices=WORKLOADS, default="settling_metaball",
                     help="diagnostic workloads besides the default benchmark workload")
     args = ap.parse_args()

@@ -28,6 +28,14 @@ __device__ __forceinline__ C feq_i(int ex, int ey, int ez, C w, C rho, C ux, C u
     const C uu = ux * ux + uy * uy + uz * uz;
     return w * rho * (C(1) + C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu);
 }
+// The same equilibrium in offset form: f^eq_i - w_i rho0 for density
+// rho = rho0 + drho.
+template <typename C>
+__device__ __forceinline__ C geq_i(int ex, int ey, int ez, C w, C drho, C rho, C ux, C uy, C uz) {
+    const C eu = ex * ux + ey * uy + ez * uz;
+    const C uu = ux * ux + uy * uy + uz * uz;
+    return w * (drho + rho * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu));
+}
 
 template <typename S, int Q>
 __device__ __forceinline__ void flags_brick(const Params &P, SmemParticles &sp, int b) {
@@ -132,16 +140,17 @@ __device__ __forceinline__ void flags_brick(const Params &P, SmemParticles &sp, 
                 if (sy < 0 || sy >= P.ny) { if (P.per[1]) sy = (sy + P.ny) % P.ny; else in = false; }
                 if (sz < 0 || sz >= P.nz) { if (P.per[2]) sz = (sz + P.nz) % P.nz; else in = false; }
                 const C w = (C)L::w(i);
-                C f;
+                // offset form (g = f - w rho0; opposite directions share w)
+                C g;
                 const long long nb = (long long)sx + (long long)P.nx * ((long long)sy + (long long)P.ny * sz);
                 if (i != 0 && in && P.flag_old[nb] == 0) {
                     const int io = L::opp(i);
-                    f = Cd::ld_plain(A + (long long)io * N + nb, w, rho0) +
+                    g = Cd::ld_plain(A + (long long)io * N + nb, w, rho0) +
                         C(6) * w * rho0 * (ex * ux + ey * uy + ez * uz);
                 } else {
-                    f = feq_i<C>(ex, ey, ez, w, rho0, ux, uy, uz);
+                    g = geq_i<C>(ex, ey, ez, w, C(0), rho0, ux, uy, uz);
                 }
-                Cd::st(A + (long long)i * N + n, f, w, rho0);
+                Cd::st(A + (long long)i * N + n, g, w, rho0);
             }
             atomicAdd(&P.counters[CNT_NREFILL], 1);
         }
@@ -186,7 +195,7 @@ __global__ void k_init(Params P, S *f) {
 #pragma unroll
         for (int i = 0; i < Q; i++) {
             const C w = (C)L::w(i);
-            Codec<S>::st(f + (long long)i * P.N + n, feq_i<C>(L::e(i, 0), L::e(i, 1), L::e(i, 2), w, rho0, ux, uy, uz),
+            Codec<S>::st(f + (long long)i * P.N + n, geq_i<C>(L::e(i, 0), L::e(i, 1), L::e(i, 2), w, C(0), rho0, ux, uy, uz),
                          w, rho0);
         }
     }
@@ -201,7 +210,7 @@ __global__ void k_get_pop(Params P, const S *f, double *out) {
 #pragma unroll
         for (int i = 0; i < Q; i++)
             out[(long long)i * P.N + n] =
-                (double)Codec<S>::ld_plain(f + (long long)i * P.N + n, (C)L::w(i), (C)P.rho0);
+                (double)Codec<S>::ldf(f + (long long)i * P.N + n, (C)L::w(i), (C)P.rho0);
     }
 }
 template <typename S, int Q>
@@ -211,7 +220,7 @@ __global__ void k_set_pop(Params P, S *f, const double *in) {
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < P.N; n += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int i = 0; i < Q; i++)
-            Codec<S>::st(f + (long long)i * P.N + n, (C)in[(long long)i * P.N + n], (C)L::w(i), (C)P.rho0);
+            Codec<S>::stf(f + (long long)i * P.N + n, (C)in[(long long)i * P.N + n], (C)L::w(i), (C)P.rho0);
     }
 }
 
@@ -226,14 +235,16 @@ __global__ void k_fields(Params P, const S *f, const uint16_t *flags, double *rh
         if (fl_out) fl_out[n] = fl;
         double r = 0, mx = 0, my = 0, mz = 0;
         if (fl == 0) {
+            // offsets: rho = rho0 + sum g, momentum = sum g e
 #pragma unroll
             for (int i = 0; i < Q; i++) {
-                const double fi = (double)Codec<S>::ld_plain(f + (long long)i * P.N + n, (C)L::w(i), (C)P.rho0);
-                r += fi;
-                mx += fi * L::e(i, 0);
-                my += fi * L::e(i, 1);
-                mz += fi * L::e(i, 2);
+                const double gi = (double)Codec<S>::ld_plain(f + (long long)i * P.N + n, (C)L::w(i), (C)P.rho0);
+                r += gi;
+                mx += gi * L::e(i, 0);
+                my += gi * L::e(i, 1);
+                mz += gi * L::e(i, 2);
             }
+            r += P.rho0;
         }
         if (rho) rho[n] = r;
         if (u) {
@@ -253,14 +264,14 @@ __global__ void k_check(Params P, const S *f, const uint16_t *flags) {
     bool bad = false;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < P.N; n += (long long)gridDim.x * blockDim.x) {
         if (flags[n] != 0) continue;
-        float r = 0, mx = 0, my = 0, mz = 0;
+        float r = P.rho0_f, mx = 0, my = 0, mz = 0;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            const float fi = (float)Codec<S>::ld_plain(f + (long long)i * P.N + n, (C)L::w(i), (C)P.rho0);
-            r += fi;
-            mx += fi * L::e(i, 0);
-            my += fi * L::e(i, 1);
-            mz += fi * L::e(i, 2);
+            const float gi = (float)Codec<S>::ld_plain(f + (long long)i * P.N + n, (C)L::w(i), (C)P.rho0);
+            r += gi;
+            mx += gi * L::e(i, 0);
+            my += gi * L::e(i, 1);
+            mz += gi * L::e(i, 2);
         }
         const float u2 = (mx * mx + my * my + mz * mz) / (r * r);
         if (!(r > 0.f) || !isfinite(r) || !(u2 <= 0.25f)) bad = true;

@@ -122,13 +122,21 @@ __device__ __forceinline__ void add_term(C (*acc)[6], int s, const C dP[3], cons
 }
 
 // The unknown population of one particle link (direction i arrives at x from
-// the solid node x + d, d = -e_i) and its momentum-exchange term.
+// the solid node x + d, d = -e_i) and its momentum-exchange term, in offset
+// form: gown are the node's post-collision offsets g = f - w rho0, drho_f =
+// rho_f - rho0, and the unknown is returned as an offset.  Eq. (28)'s term is
+// (d - u_w) f+_d + (d + u_w) f_-d = 2 d w rho0 + (d - u_w) g+_d + (d + u_w)
+// g_-d; the constant 2 d w rho0 sums to exactly zero over all links that cross
+// a particle's surface (those of Eq. (28) and the missing force points of
+// §2.3.5 together: every pair of solid nodes of the particle cancels), and so
+// does its torque (x_s - x_p) x 2 d w rho0, so both are left out unless the
+// missing force points are switched off.
 template <typename S, int Q>
 __device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, const SmemParticles &sp, int i, int x,
                                                           int y, int z, int lx, int ly, int lz, int bx0, int by0,
                                                           int bz0, long long ns_solid,
                                                           const typename Codec<S>::C *fown,
-                                                          typename Codec<S>::C rho_f,
+                                                          typename Codec<S>::C drho_f,
                                                           const typename Codec<S>::C *u_f,
                                                           typename Codec<S>::C (*acc)[6],
                                                           typename Codec<S>::C *Mf_cache, int *Mf_slot) {
@@ -171,12 +179,13 @@ __device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, cons
     if (fz < 0 || fz >= P.nz) { if (P.per[2]) fz = (fz + P.nz) % P.nz; else ff_in = false; }
     const int nff = ff_in ? fx + P.nx * (fy + P.ny * fz) : x + P.nx * (y + P.ny * z);
     const uint16_t flag_ff = P.flag_new[nff];
-    C rho_ff = 0, m_ff[3] = {0, 0, 0}, fff_io = 0;
+    const C rho_f = rho0 + drho_f;
+    C drho_ff = 0, m_ff[3] = {0, 0, 0}, fff_io = 0;
     if (P.vibb) {
 #pragma unroll
         for (int k = 0; k < Q; k++) {
             const C fk = Cd::ld(A + (long long)k * N + nff, (C)L::w(k), rho0);
-            rho_ff += fk;
+            drho_ff += fk;
             m_ff[0] += fk * L::e(k, 0);
             m_ff[1] += fk * L::e(k, 1);
             m_ff[2] += fk * L::e(k, 2);
@@ -190,19 +199,20 @@ __device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, cons
         fin = fown_io + C(6) * w_io * rho_f * eu_w;
     } else {
         C u_ff[3];
+        const C rho_ff = rho0 + drho_ff;
         const C inv_rho_ff = C(1) / rho_ff;
         for (int a = 0; a < 3; a++) u_ff[a] = (m_ff[a] - C(0.5) * Prm<C>::F(P, a)) * inv_rho_ff;
-        const C feq_f = feq_i<C>(dx, dy, dz, w_io, rho_f, u_f[0], u_f[1], u_f[2]);
-        const C feq_ff = feq_i<C>(dx, dy, dz, w_io, rho_ff, u_ff[0], u_ff[1], u_ff[2]);
+        const C feq_f = geq_i<C>(dx, dy, dz, w_io, drho_f, rho_f, u_f[0], u_f[1], u_f[2]);
+        const C feq_ff = geq_i<C>(dx, dy, dz, w_io, drho_ff, rho_ff, u_ff[0], u_ff[1], u_ff[2]);
         // Eq. (21): non-equilibrium part, interpolated (q <= 1/2) or
         // extrapolated (q > 1/2) from x_f and x_ff
         const C fneq_d = C(2) * q * (fown_io - feq_f) + (C(1) - C(2) * q) * (fff_io - feq_ff);
-        C rho_d, us[3], uss[3], ud[3];
+        C drho_d, us[3], uss[3], ud[3];
         if (q <= C(0.5)) {  // Eqs. (22)-(23), first branches
-            rho_d = C(2) * q * rho_f + (C(1) - C(2) * q) * rho_ff;
+            drho_d = C(2) * q * drho_f + (C(1) - C(2) * q) * drho_ff;
             for (int a = 0; a < 3; a++) us[a] = C(2) * q * u_f[a] + (C(1) - C(2) * q) * u_ff[a];
         } else {            // second branches
-            rho_d = rho_f;
+            drho_d = drho_f;
             const C inv_q = C(1) / q;
             const C a_f = (C(1) - q) * inv_q, a_w = (C(2) * q - C(1)) * inv_q;
             for (int a = 0; a < 3; a++) us[a] = a_f * u_f[a] + a_w * uw[a];
@@ -211,14 +221,19 @@ __device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, cons
         const C b_ff = (C(1) - q) * inv_1q, b_w = C(2) * q * inv_1q;
         for (int a = 0; a < 3; a++) uss[a] = b_ff * u_ff[a] + b_w * uw[a];                 // (24)
         for (int a = 0; a < 3; a++) ud[a] = (us[a] + C(2) * uss[a]) * C(1.0 / 3.0);        // (25)
-        const C fplus_d = feq_i<C>(dx, dy, dz, w_io, rho_d, ud[0], ud[1], ud[2]) + fneq_d;                       // (20)
+        const C fplus_d = geq_i<C>(dx, dy, dz, w_io, drho_d, rho0 + drho_d, ud[0], ud[1], ud[2]) + fneq_d;        // (20)
         fin = fplus_d + C(6) * w_io * rho_f * eu_w;                                                              // (19)
     }
-    // Eq. (28): (e_i' - u_w) f+_i'(x,t) - (e_i - u_w) f_i(x,t+1), e_i' = d
+    // Eq. (28): (e_i' - u_w) f+_i'(x,t) - (e_i - u_w) f_i(x,t+1), e_i' = d,
+    // in offsets (the constant part left out, see above)
     C dP[3];
-    dP[0] = (C(dx) - uw[0]) * fown_io - (C(-dx) - uw[0]) * fin;
-    dP[1] = (C(dy) - uw[1]) * fown_io - (C(-dy) - uw[1]) * fin;
-    dP[2] = (C(dz) - uw[2]) * fown_io - (C(-dz) - uw[2]) * fin;
+    dP[0] = (C(dx) - uw[0]) * fown_io + (C(dx) + uw[0]) * fin;
+    dP[1] = (C(dy) - uw[1]) * fown_io + (C(dy) + uw[1]) * fin;
+    dP[2] = (C(dz) - uw[2]) * fown_io + (C(dz) + uw[2]) * fin;
+    if (!P.missing_force) {
+        const C c = C(2) * w_io * rho0;
+        dP[0] += c * dx; dP[1] += c * dy; dP[2] += c * dz;
+    }
     add_term<C>(acc, s, dP, r);
     return fin;
 }
@@ -277,12 +292,14 @@ __device__ __noinline__ void solid_node(const Params &P, const SmemParticles &sp
             lever<C>(P, sp, s, bx0, by0, bz0, (C)(lx - dx) + q * dx, (C)(ly - dy) + q * dy, (C)(lz - dz) + q * dz, r);
             particle_velocity<C>(P, sp, s, r, uw);
             const C w = (C)lat_w<Q>(i);
-            const C fi = feq_i<C>(dx, dy, dz, w, rho0, uw[0], uw[1], uw[2]);
-            const C fo = feq_i<C>(-dx, -dy, -dz, w, rho0, uw[0], uw[1], uw[2]);
+            // Eqs. (31)-(32) in offsets; the constant 2 d w rho0 cancels
+            // with those of the other crossing links (see particle_link)
+            const C fi = geq_i<C>(dx, dy, dz, w, C(0), rho0, uw[0], uw[1], uw[2]);
+            const C fo = geq_i<C>(-dx, -dy, -dz, w, C(0), rho0, uw[0], uw[1], uw[2]);
             C dP[3];
-            dP[0] = (C(dx) - uw[0]) * fi - (C(-dx) - uw[0]) * fo;
-            dP[1] = (C(dy) - uw[1]) * fi - (C(-dy) - uw[1]) * fo;
-            dP[2] = (C(dz) - uw[2]) * fi - (C(-dz) - uw[2]) * fo;
+            dP[0] = (C(dx) - uw[0]) * fi + (C(dx) + uw[0]) * fo;
+            dP[1] = (C(dy) - uw[1]) * fi + (C(dy) + uw[1]) * fo;
+            dP[2] = (C(dz) - uw[2]) * fi + (C(dz) + uw[2]) * fo;
             add_term<C>(acc, s, dP, r);
         }
     }
@@ -298,14 +315,16 @@ __device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>
     using Cd = Codec<S>;
     using C = typename Cd::C;
     const C rho0 = Prm<C>::rho0(P);
-    C rho = 0, mx = 0, my = 0, mz = 0;
+    // offsets: rho = rho0 + sum g, momentum = sum g e
+    C drho = 0, mx = 0, my = 0, mz = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        rho += fin[i];
+        drho += fin[i];
         mx += fin[i] * L::e(i, 0);
         my += fin[i] * L::e(i, 1);
         mz += fin[i] * L::e(i, 2);
     }
+    const C rho = rho0 + drho;
     const C Fx = kForce ? Prm<C>::F(P, 0) : C(0), Fy = kForce ? Prm<C>::F(P, 1) : C(0),
             Fz = kForce ? Prm<C>::F(P, 2) : C(0);
     C inv_rho;
@@ -314,15 +333,15 @@ __device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>
     const C ux = (mx + C(0.5) * Fx) * inv_rho, uy = (my + C(0.5) * Fy) * inv_rho, uz = (mz + C(0.5) * Fz) * inv_rho;
     const C omega = Prm<C>::omega(P);
     const C uu = ux * ux + uy * uy + uz * uz;
-    const C w_rho_omega0 = omega * rho;
+    const C om_rho = omega * rho, om_drho = omega * drho;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
         const C w = (C)L::w(i);
         const C eu = ex * ux + ey * uy + ez * uz;
-        // omega f^eq = w (omega rho) (1 + 3 eu + 4.5 eu^2 - 1.5 uu)
-        const C feq_om = w * w_rho_omega0 * (C(1) + C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu);
-        C out = fin[i] - omega * fin[i] + feq_om;
+        // omega g^eq = w (omega drho + omega rho (3 eu + 4.5 eu^2 - 1.5 uu))
+        const C geq_om = w * (om_drho + om_rho * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu));
+        C out = fin[i] - omega * fin[i] + geq_om;
         if (kForce) {
             const C gfac = Prm<C>::gfac(P);
             const C uF = ux * Fx + uy * Fy + uz * Fz;
@@ -394,17 +413,17 @@ __device__ __noinline__ typename Codec<S>::C link_coop(const Params &P, const Sm
     const long long N = P.N;
     const C rho0 = Prm<C>::rho0(P);
     C fown[Q];
-    C rho_f = 0, m_f[3] = {0, 0, 0};
+    C drho_f = 0, m_f[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < Q; k++) {
         fown[k] = Cd::ld(A + (long long)k * N + n, (C)L::w(k), rho0);
-        rho_f += fown[k];
+        drho_f += fown[k];
         m_f[0] += fown[k] * L::e(k, 0);
         m_f[1] += fown[k] * L::e(k, 1);
         m_f[2] += fown[k] * L::e(k, 2);
     }
     C u_f[3];
-    const C inv_rho_f = C(1) / rho_f;
+    const C inv_rho_f = C(1) / (rho0 + drho_f);
     for (int a = 0; a < 3; a++) u_f[a] = (m_f[a] - C(0.5) * Prm<C>::F(P, a)) * inv_rho_f;
     // the solid source x - e_i (inside the domain: the link exists)
     int sx = x - lat_e<Q>(i, 0), sy = y - lat_e<Q>(i, 1), sz = z - lat_e<Q>(i, 2);
@@ -414,7 +433,7 @@ __device__ __noinline__ typename Codec<S>::C link_coop(const Params &P, const Sm
     C Mf_cache = 0;
     int Mf_slot = -1;
     return particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, sx + P.nx * (sy + P.ny * sz), fown,
-                               rho_f, u_f, acc, &Mf_cache, &Mf_slot);
+                               drho_f, u_f, acc, &Mf_cache, &Mf_slot);
 }
 
 // Shared scratch of the warp-cooperative link evaluation: per warp a queue of
@@ -442,17 +461,17 @@ __device__ __noinline__ void boundary_node(const Params &P, const SmemParticles 
     int xs[3], ys[3], zs[3];
     neighbour_coords(P, x, y, z, xs, ys, zs);
     C fown[Q];
-    C rho_f = 0, m_f[3] = {0, 0, 0};
+    C drho_f = 0, m_f[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < Q; k++) {
         fown[k] = Cd::ld(A + (long long)k * N + n, (C)L::w(k), rho0);
-        rho_f += fown[k];
+        drho_f += fown[k];
         m_f[0] += fown[k] * L::e(k, 0);
         m_f[1] += fown[k] * L::e(k, 1);
         m_f[2] += fown[k] * L::e(k, 2);
     }
     C u_f[3];
-    const C inv_rho_f = C(1) / rho_f;
+    const C inv_rho_f = C(1) / (rho0 + drho_f);
     for (int a = 0; a < 3; a++) u_f[a] = (m_f[a] - C(0.5) * Prm<C>::F(P, a)) * inv_rho_f;
     C fin[Q];
     int srcs[Q];
@@ -478,7 +497,7 @@ __device__ __noinline__ void boundary_node(const Params &P, const SmemParticles 
     while (links) {
         const int i = __ffs(links) - 1;
         links &= links - 1;
-        fin[i] = particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, srcs[i], fown, rho_f, u_f, acc,
+        fin[i] = particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, srcs[i], fown, drho_f, u_f, acc,
                                      &Mf_cache, &Mf_slot);
         (*nlinks)++;
     }

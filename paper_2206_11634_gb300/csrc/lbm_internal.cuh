@@ -120,11 +120,16 @@ __device__ __forceinline__ double lat_w(int i) {
 }
 
 // ---------------------------------------------------------------------------
-// Storage codecs.  FP64/FP32 store f itself; FP16/BF16 store the offset
-// s_i = f_i/w_i - rho0 (a few 1e-3 in magnitude), decoded as w_i (rho0 + s_i).
-// ld_s / st_s: the same with evict-first cache hints, for the plain sweep,
-// whose data cannot survive in L2 until the next step anyway; it then leaves
-// L2 to the working set of the particle kernels running beside it.
+// Storage codecs, in offset form.  The sweep computes with
+// g_i = f_i - w_i rho0, the deviation from the rest state (~w_i (rho' +
+// 3 e_i.u + ...)): its rounding is then relative to the flow signal rather
+// than to w_i rho0, which at low Mach keeps three to four more digits of the
+// flow in FP32.  FP64 and FP32 store g; FP16 and BF16 store s = g / w_i
+// (= f_i/w_i - rho0, O(|u|) in every direction, so no direction falls into
+// the subnormal range).  ld/st read and write g; ldf/stf convert to and from
+// f itself (set/get of populations, initialisation); ld_s/st_s carry
+// evict-first cache hints (the plain sweep, whose data cannot survive in L2
+// until the next step anyway, so the particle kernels beside it keep theirs).
 // ---------------------------------------------------------------------------
 template <typename S>
 struct Codec;
@@ -133,56 +138,64 @@ template <>
 struct Codec<double> {
     using C = double;
     __device__ __forceinline__ static double ld(const double *p, double, double) { return __ldg(p); }
-    __device__ __forceinline__ static void st(double *p, double f, double, double) { *p = f; }
     __device__ __forceinline__ static double ld_plain(const double *p, double, double) { return *p; }
     __device__ __forceinline__ static double ld_s(const double *p, double, double) { return __ldcs(p); }
-    __device__ __forceinline__ static void st_s(double *p, double f, double, double) { __stcs(p, f); }
+    __device__ __forceinline__ static void st(double *p, double g, double, double) { *p = g; }
+    __device__ __forceinline__ static void st_s(double *p, double g, double, double) { __stcs(p, g); }
+    __device__ __forceinline__ static double ldf(const double *p, double w, double rho0) { return w * rho0 + *p; }
+    __device__ __forceinline__ static void stf(double *p, double f, double w, double rho0) { *p = f - w * rho0; }
 };
 template <>
 struct Codec<float> {
     using C = float;
     __device__ __forceinline__ static float ld(const float *p, float, float) { return __ldg(p); }
-    __device__ __forceinline__ static void st(float *p, float f, float, float) { *p = f; }
     __device__ __forceinline__ static float ld_plain(const float *p, float, float) { return *p; }
     __device__ __forceinline__ static float ld_s(const float *p, float, float) { return __ldcs(p); }
-    __device__ __forceinline__ static void st_s(float *p, float f, float, float) { __stcs(p, f); }
+    __device__ __forceinline__ static void st(float *p, float g, float, float) { *p = g; }
+    __device__ __forceinline__ static void st_s(float *p, float g, float, float) { __stcs(p, g); }
+    __device__ __forceinline__ static float ldf(const float *p, float w, float rho0) { return w * rho0 + *p; }
+    __device__ __forceinline__ static void stf(float *p, float f, float w, float rho0) { *p = f - w * rho0; }
 };
 template <>
 struct Codec<__half> {
     using C = float;
-    __device__ __forceinline__ static float ld(const __half *p, float w, float rho0) {
-        return w * (rho0 + __half2float(__ldg(p)));
+    __device__ __forceinline__ static float ld(const __half *p, float w, float) { return w * __half2float(__ldg(p)); }
+    __device__ __forceinline__ static float ld_plain(const __half *p, float w, float) { return w * __half2float(*p); }
+    __device__ __forceinline__ static float ld_s(const __half *p, float w, float) { return w * __half2float(__ldcs(p)); }
+    __device__ __forceinline__ static void st(__half *p, float g, float w, float) { *p = __float2half_rn(g * (1.0f / w)); }
+    __device__ __forceinline__ static void st_s(__half *p, float g, float w, float) {
+        __stcs(p, __float2half_rn(g * (1.0f / w)));
     }
-    __device__ __forceinline__ static float ld_plain(const __half *p, float w, float rho0) {
+    __device__ __forceinline__ static float ldf(const __half *p, float w, float rho0) {
         return w * (rho0 + __half2float(*p));
     }
-    __device__ __forceinline__ static void st(__half *p, float f, float w, float rho0) {
+    __device__ __forceinline__ static void stf(__half *p, float f, float w, float rho0) {
         *p = __float2half_rn(f * (1.0f / w) - rho0);
-    }
-    __device__ __forceinline__ static float ld_s(const __half *p, float w, float rho0) {
-        return w * (rho0 + __half2float(__ldcs(p)));
-    }
-    __device__ __forceinline__ static void st_s(__half *p, float f, float w, float rho0) {
-        __stcs(p, __float2half_rn(f * (1.0f / w) - rho0));
     }
 };
 template <>
 struct Codec<__nv_bfloat16> {
     using C = float;
-    __device__ __forceinline__ static float ld(const __nv_bfloat16 *p, float w, float rho0) {
-        return w * (rho0 + __bfloat162float(__ldg(p)));
+    __device__ __forceinline__ static float ld(const __nv_bfloat16 *p, float w, float) {
+        return w * __bfloat162float(__ldg(p));
     }
-    __device__ __forceinline__ static float ld_plain(const __nv_bfloat16 *p, float w, float rho0) {
+    __device__ __forceinline__ static float ld_plain(const __nv_bfloat16 *p, float w, float) {
+        return w * __bfloat162float(*p);
+    }
+    __device__ __forceinline__ static float ld_s(const __nv_bfloat16 *p, float w, float) {
+        return w * __bfloat162float(__ldcs(p));
+    }
+    __device__ __forceinline__ static void st(__nv_bfloat16 *p, float g, float w, float) {
+        *p = __float2bfloat16_rn(g * (1.0f / w));
+    }
+    __device__ __forceinline__ static void st_s(__nv_bfloat16 *p, float g, float w, float) {
+        __stcs(p, __float2bfloat16_rn(g * (1.0f / w)));
+    }
+    __device__ __forceinline__ static float ldf(const __nv_bfloat16 *p, float w, float rho0) {
         return w * (rho0 + __bfloat162float(*p));
     }
-    __device__ __forceinline__ static void st(__nv_bfloat16 *p, float f, float w, float rho0) {
+    __device__ __forceinline__ static void stf(__nv_bfloat16 *p, float f, float w, float rho0) {
         *p = __float2bfloat16_rn(f * (1.0f / w) - rho0);
-    }
-    __device__ __forceinline__ static float ld_s(const __nv_bfloat16 *p, float w, float rho0) {
-        return w * (rho0 + __bfloat162float(__ldcs(p)));
-    }
-    __device__ __forceinline__ static void st_s(__nv_bfloat16 *p, float f, float w, float rho0) {
-        __stcs(p, __float2bfloat16_rn(f * (1.0f / w) - rho0));
     }
 };
 

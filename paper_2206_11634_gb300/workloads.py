@@ -123,6 +123,21 @@ def multi_particle(nparticles: int = 200, n: int = 256, nz: int | None = None, s
                 particles=parts)
 
 
+def drag_case(storage: str = "f32", n: int = 48, steps: int = 1000, ncp: int = 4, seed_offset: int = 5):
+    """One drag case of the batched sweep: a fixed metaball of ncp control
+    points (offsets uniform in +-2.5, nominal radius 6) at the centre of a
+    periodic n^3 box, flow driven by a Guo body force 2e-6 along x, tau 0.8,
+    fluid at rest initially, 1000 steps (the length of the batched drag sweep)."""
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    cp, K = nominal_radius_metaball(rng, ncp, 2.5, 6.0)
+    c = n / 2.0 - 0.5
+    return dict(name=f"drag_{ncp}cp_{n}^3", nx=n, ny=n, nz=n, periodic=(1, 1, 1), tau=0.8, storage=storage, n_sub=0,
+                gravity=(0.0, 0.0, 0.0), force=(2e-6, 0.0, 0.0), steps=steps, kn=0.0, eta_n=0.0, kt=0.0, eta_t=0.0,
+                mu_s=0.0, c_tol=1e-6,
+                particles=[_particle(cp, K, (c + 0.21, c - 0.13, c + 0.07), q=_random_quaternion(rng), fixed=1,
+                                     mass=1.0, inertia=np.eye(3))])
+
+
 def empty_box(n: int = 256, storage: str = "f32", periodic=(1, 1, 1)):
     """A lattice with no particles (the sweep's bandwidth ceiling)."""
     return dict(name=f"empty_{n}^3", nx=n, ny=n, nz=n, periodic=periodic, tau=0.8, storage=storage, n_sub=0,
