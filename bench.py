@@ -45,7 +45,7 @@ BRICK_NODES = 32 * 4 * 2
 SWEEP_SOURCES = ["k_sweep.cuh", "k_flags.cuh", "lbm_internal.cuh", "launch_impl.cuh", "sweep_f32.cu"]
 
 
-WORKLOADS = ("settling_metaball", "empty_box", "settling_sphere", "multi_particle")
+WORKLOADS = ("settling_metaball", "empty_box", "settling_sphere", "multi_particle", "batched_drag")
 
 
 def workload(name: str = "settling_metaball", storage: str | None = None):
@@ -70,6 +70,8 @@ def _workload(name: str):
         return workloads.settling_sphere()
     if name == "multi_particle":
         return workloads.multi_particle()
+    if name == "batched_drag":  # the reference arm times its first case
+        return workloads.batched_drag(64)[0]
     raise ValueError(name)
 
 
@@ -408,6 +410,88 @@ def run_gpu(args):
     return 0
 
 
+def run_batch(args):
+    """Workload 5: 64 independent periodic drag cases, sides 48..128, one
+    fixed metaball each, stepped as a batch (one launch per phase for all
+    cases, each call a replayed CUDA graph) after the autotuner picked the
+    schedule.  value = aggregate MLUPS over all cases."""
+    import torch
+    import numpy as np
+
+    world, rank, local, dist = dist_setup()
+    torch.cuda.set_device(local)
+    import paper_2206_11634_gb300 as pkg
+    from paper_2206_11634_gb300 import build as lib_build, workloads
+    if rank == 0 or not os.path.exists(pkg.LIB_PATH):
+        lib_build.build()
+    barrier(dist)
+    storage = args.storage or "f32"
+    cases = workloads.batched_drag(64, storage)
+    nodes = sum(c["nx"] * c["ny"] * c["nz"] for c in cases)
+    kws = []
+    for c in cases:
+        kw = dict(nx=c["nx"], ny=c["ny"], nz=c["nz"], periodic=c["periodic"], lattice=19, storage=storage,
+                  n_sub=0, max_particles=1, tau=c["tau"], force=c["force"])
+        kws.append(kw)
+    stream = torch.cuda.Stream()
+    bt = pkg.Batch(kws, stream=stream)
+    for k, c in enumerate(cases):
+        p = c["particles"][0]
+        bt.set_particles(k, [pkg.make_particle(p["cp"], p["K"], p["x"], q=p["q"], fixed=1, mass=p["mass"],
+                                               inertia=p["inertia"])])
+    g, chunk, tune_ms = bt.tune(2)
+    bt.step(max(3, args.warmup))
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier(dist)
+        torch.cuda.synchronize()
+        start.record(stream)
+        bt.step(args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        barrier(dist)
+    ms = max_over_ranks(dist, start.elapsed_time(stop))
+    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+    # end to end: per call of one step, read back every case's drag
+    e2e_steps = max(1, args.steps // 10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        bt.step(1)
+        for k in range(len(cases)):
+            bt.forces(k)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
+    e2e_value = world * nodes * e2e_steps / e2e_s / 1e6
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    peak, peak_kind = measured_peak_gbs()
+    alg = 2 * 19 * BYTES_PER_VALUE[storage] * nodes
+    achieved = alg / (ms / args.steps * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
+            "config": {"workload": f"batched_drag_64cases_{storage}", "lattice": "D3Q19", "storage": storage,
+                       "cases": len(cases), "nodes": nodes, "sides": "48..128", "tau": 0.8,
+                       "schedule": {"chain_ctas_per_case": g, "plain_bricks_per_cta": chunk,
+                                    "tuned_ms_per_step": round(tune_ms, 4)},
+                       "l2": "no flush: populations exceed the 129 MB L2", "parallelism": f"replicas x{world}"},
+            "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 48 * len(cases), "steps": e2e_steps},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": f"{peak_kind} copy",
+                         "kernel": "whole batched step (all phases, all cases)", "bytes_per_launch": alg},
+            "gpu_launches": 4 * (args.steps + max(3, args.warmup)),
+            "clocks": clocks.summary(), "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,6 +507,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched_drag":
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -248,6 +248,69 @@ int lbm_destroy(lbm_handle *h);
  * NULL); never NULL. */
 const char *lbm_last_error(const lbm_handle *h);
 
+/* ---------------------------------------------------------------------------
+ * Batched lattices: many independent drag cases of different box sizes
+ * stepped together.  The method per case is that of lbm_step() (§2.2-§2.3;
+ * the cases hold fixed particles, so there is no DEM): binning, flags with
+ * refilling, the plain and near sweeps with VIBB and momentum exchange.  Each
+ * phase is one kernel launch for all cases, and lbm_batch_step() runs its
+ * steps as a CUDA graph captured on first use (the step numbers live in
+ * device counters, so the graph is replayed by every later call with the same
+ * nsteps).  The paper steps one lattice; the batched form has no counterpart
+ * there.
+ *
+ * All cases share the lattice (D3Q19 or D3Q15) and the storage (FP32, FP16
+ * or BF16; FP64 is rejected), and have n_sub = 0; sizes, tau, body force and
+ * particles may differ.  The workspace (lbm_batch_workspace_size) holds every
+ * case's single-lattice layout plus a second per-step region per case and the
+ * batch's tables; it is caller-owned, 256-byte aligned and borrowed until
+ * lbm_batch_destroy().  Errors as for a single handle; the message of the
+ * last failure is lbm_batch_last_error(b) (or of the last failed
+ * lbm_batch_init when b is NULL).
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+
+int lbm_batch_workspace_size(const lbm_config *cfgs, int ncases, size_t *bytes);
+
+/* cfgs: host array of ncases configurations.  Initialises every case to
+ * f^eq(rho0, u0) with no particles, on cuda_stream (NULL = default stream). */
+int lbm_batch_init(const lbm_config *cfgs, int ncases, void *dev_ws, size_t ws_bytes, void *cuda_stream,
+                   lbm_batch **out);
+
+/* Replace the particles of case c (all with fixed = 1), as lbm_set_particles.
+ * Synchronises. */
+int lbm_batch_set_particles(lbm_batch *b, int c, const lbm_particle *host, int n);
+
+/* Advance every case by nsteps steps (asynchronous on the batch's stream). */
+int lbm_batch_step(lbm_batch *b, int nsteps);
+
+/* Synchronise and copy out the hydrodynamic force and torque of case c's
+ * particles after the last step (host double[n][3], either may be NULL). */
+int lbm_batch_get_forces(lbm_batch *b, int c, double *F, double *T);
+
+/* Synchronise and write case c's populations as FP64 f[i][z][y][x] to a
+ * caller device buffer (as lbm_get_populations). */
+int lbm_batch_get_populations(lbm_batch *b, int c, void *dev_f);
+
+/* Launch schedule: CTAs per case of the flag and near sweeps (1..64) and
+ * bricks per CTA of the plain sweep (1..64).  Results do not depend on it. */
+int lbm_batch_set_schedule(lbm_batch *b, int chain_ctas_per_case, int plain_bricks_per_cta);
+
+/* Autotuner: times trial_steps steps (after trial_steps of warm-up) for each
+ * schedule of CTAs per case in {4, 8, 16, 32, 64} and bricks per plain CTA in
+ * {1, 2, 4, 8}, keeps the fastest and reports it (any output may be NULL).
+ * The trials are real steps: the batch advances by 40 * trial_steps steps. */
+int lbm_batch_tune(lbm_batch *b, int trial_steps, int *chain_ctas_per_case, int *plain_bricks_per_cta,
+                   double *best_ms_per_step);
+
+/* Steps taken since lbm_batch_init. */
+int64_t lbm_batch_steps(const lbm_batch *b);
+
+/* Release the batch and its cases (not the workspace).  Synchronises. */
+int lbm_batch_destroy(lbm_batch *b);
+
+const char *lbm_batch_last_error(const lbm_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

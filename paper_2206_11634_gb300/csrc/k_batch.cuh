@@ -1,0 +1,62 @@
+// Batched forms of the flag pass and the two sweeps: one launch for all cases
+// of a batch.  Each CTA takes its case's Params from the device table (row =
+// step parity, step from the device counter) into shared memory and runs the
+// single-lattice body on it.
+#pragma once
+
+#include "k_sweep.cuh"
+
+namespace lbmmb {
+
+// g_chain CTAs per case, persistent over that case's flag work list.
+template <typename S, int Q>
+__global__ void __launch_bounds__(BRICK) k_flags_batch(BatchArgs B) {
+    __shared__ Params sP;
+    __shared__ SmemParticles sp;
+    const int c = blockIdx.x / B.g_chain, lb = blockIdx.x % B.g_chain;
+    load_case_params(B, c, B.ctr, sP);
+    flags_work<S, Q>(sP, sp, lb, B.g_chain);
+}
+
+// g_chain CTAs per case over its near bricks; the last CTA of the launch
+// advances the particle chain's step counter.
+template <typename S, int Q, bool kForce>
+__global__ void __launch_bounds__(BRICK, 4) k_sweep_near_batch(BatchArgs B) {
+    __shared__ Params sP;
+    __shared__ SmemParticles sp;
+    __shared__ double red[BRICK / 32][6];
+    __shared__ int s_links;
+    __shared__ LinkScratch ls;
+    const int c = blockIdx.x / B.g_chain, lb = blockIdx.x % B.g_chain;
+    load_case_params(B, c, B.ctr, sP);
+    near_work<S, Q, kForce>(sP, sp, red, s_links, ls, lb, B.g_chain);
+    advance_step_when_last(B.ctr + 2, B.ctr);
+}
+
+// plain_chunk consecutive bricks of the concatenated brick ranges of all
+// cases per CTA.  The plain path needs only a few of a case's parameters, so
+// they are read straight from the table (L1-cached) instead of copied to
+// shared memory; the brick's case comes from a per-brick map.  The last CTA
+// advances the plain sweep's step counter.
+template <typename S, int Q, bool kForce>
+__global__ void __launch_bounds__(BRICK, 4) k_sweep_plain_batch(BatchArgs B) {
+    const int total = B.brick_off[B.ncases];
+    const unsigned step = *(volatile const unsigned *)(B.ctr + 1);
+    const Params *row = B.tab + (size_t)(step & 1) * B.ncases;
+    const int g0 = blockIdx.x * B.plain_chunk;
+    const int g1 = min(total, g0 + B.plain_chunk);
+    for (int g = g0; g < g1; g++) {
+        const int c = B.brick_case[g];
+        const Params &P = row[c];
+        const int b = g - B.brick_off[c];
+        if (P.skip[(step % 3) * P.nbricks + b] == (int)step) continue;  // the near sweep takes it
+        const int tid = threadIdx.x;
+        int bxi, byi, bzi;
+        brick_coords(P, b, bxi, byi, bzi);
+        const int x = bxi * BX + tid % BX, y = byi * BY + (tid / BX) % BY, z = bzi * BZ + tid / (BX * BY);
+        if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce, true>(P, x, y, z, x + P.nx * (y + P.ny * z));
+    }
+    advance_step_when_last(B.ctr + 3, B.ctr + 1);
+}
+
+}  // namespace lbmmb

@@ -111,7 +111,10 @@ __device__ __forceinline__ void flags_brick(const Params &P, SmemParticles &sp, 
     }
     const uint16_t fl = own >= 0 ? (uint16_t)(own + 1) : (uint16_t)0;
     if (active) P.flag_new[n] = fl;
-    __syncthreads();
+    // whether the brick holds a solid node now (the near sweep takes the
+    // plain path for bricks with no solid node around them)
+    const int any_solid = __syncthreads_or(active && fl != 0);
+    if (threadIdx.x == 0 && P.brick_solid) P.brick_solid[b] = (uint8_t)(any_solid != 0);
 
     // Local refilling, §2.3.3.  Reading: f_i' at x_new is "known after
     // streaming" when it streams in from x_new + e_i and that node was a fluid
@@ -161,16 +164,15 @@ __device__ __forceinline__ void flags_brick(const Params &P, SmemParticles &sp, 
 // before; a brick listed in several of these lists is visited once (its most
 // recent listing).
 template <typename S, int Q>
-__global__ void __launch_bounds__(BRICK) k_flags(Params P) {
-    __shared__ SmemParticles sp;
+__device__ __forceinline__ void flags_work(const Params &P, SmemParticles &sp, int blk, int nblk) {
     const int t = P.step;
     const int r0 = t % 3, r1 = (t + 2) % 3, r2 = (t + 1) % 3;
     const int c0 = P.counters[CNT_LISTED];
     const int c1 = t >= 1 ? P.wl_count[r1] : 0;
     const int c2 = t >= 2 ? P.wl_count[r2] : 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) P.wl_count[r0] = c0;  // read by the next two steps
+    if (blk == 0 && threadIdx.x == 0) P.wl_count[r0] = c0;  // read by the next two steps
     const int total = c0 + c1 + c2;
-    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    for (int w = blk; w < total; w += nblk) {
         int b;
         if (w < c0) {
             b = P.wl_list[r0 * P.nbricks + w];
@@ -183,6 +185,11 @@ __global__ void __launch_bounds__(BRICK) k_flags(Params P) {
         }
         flags_brick<S, Q>(P, sp, b);
     }
+}
+template <typename S, int Q>
+__global__ void __launch_bounds__(BRICK) k_flags(Params P) {
+    __shared__ SmemParticles sp;
+    flags_work<S, Q>(P, sp, blockIdx.x, gridDim.x);
 }
 
 // Every node to f^eq(rho0, u0).

@@ -16,14 +16,8 @@ namespace lbmmb {
 // the particle.  The particle is appended to the list of each brick the grown
 // box meets (k_flags sorts the lists).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_bin(Params P) {
-    const int j = blockIdx.x;
+__device__ void bin_particle(const Params &P, int j) {
     const int t = threadIdx.x;
-    // predicted-near counts, ring of three by step: slot step+1 is filled
-    // below; slot step+2 (consumed by the near sweep of step-1) is cleared
-    // for the next binning
-    if (j == 0 && t == 0 && P.pred_count) P.pred_count[(P.step + 2) % 3] = 0;
-    if (j >= P.np) return;
     DevParticle &p = P.parts[j];
     if (t < p.ncp) {
         double r[3];
@@ -84,6 +78,34 @@ __global__ void __launch_bounds__(256) k_bin(Params P) {
         }
     }
 }
+
+__global__ void __launch_bounds__(256) k_bin(Params P) {
+    // predicted-near counts, ring of three by step: slot step+1 is filled by
+    // the binning; slot step+2 (consumed by the near sweep of step-1) is
+    // cleared for the next binning
+    if (blockIdx.x == 0 && threadIdx.x == 0 && P.pred_count) P.pred_count[(P.step + 2) % 3] = 0;
+    if ((int)blockIdx.x < P.np) bin_particle(P, blockIdx.x);
+}
+
+// Batched binning: one CTA per (case, particle), at least one per case.  The
+// first CTA of a case also clears the other parity's per-step region for the
+// next step (the forces of this step's predecessor stay readable until then).
+__global__ void __launch_bounds__(256) k_bin_batch(BatchArgs B) {
+    __shared__ Params sP;
+    const int item = blockIdx.x;
+    const int c = case_of(B.item_off, B.ncases, item);
+    const int j = item - B.item_off[c];
+    load_case_params(B, c, B.ctr, sP);
+    if (j == 0) {
+        if (threadIdx.x == 0 && sP.pred_count) sP.pred_count[(sP.step + 2) % 3] = 0;
+        int4 *z = static_cast<int4 *>(sP.bin_next);
+        const long long n16 = sP.bin_next_bytes / 16;
+        for (long long k = threadIdx.x; k < n16; k += blockDim.x) z[k] = make_int4(0, 0, 0, 0);
+    }
+    if (j < sP.np) bin_particle(sP, j);
+}
+
+void launch_bin_batch(const BatchArgs &B, int grid, cudaStream_t st) { k_bin_batch<<<grid, 256, 0, st>>>(B); }
 
 // ---------------------------------------------------------------------------
 // k_force_reduce: one CTA per particle; each thread sums the partials of a

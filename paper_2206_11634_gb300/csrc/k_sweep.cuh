@@ -635,34 +635,33 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
 // The sweep of every brick outside this step's predicted near set: the plain
 // path only.  Runs on its own stream, concurrently with the particle kernels.
 template <typename S, int Q, bool kForce>
-__global__ void __launch_bounds__(BRICK, 4) k_sweep_plain(Params P) {
+__device__ __forceinline__ void plain_brick(const Params &P, int b) {
+    if (P.skip && P.skip[(P.step % 3) * P.nbricks + b] == P.step) return;  // the near sweep takes it
     const int tid = threadIdx.x;
+    int bxi, byi, bzi;
+    brick_coords(P, b, bxi, byi, bzi);
+    const int x = bxi * BX + tid % BX, y = byi * BY + (tid / BX) % BY, z = bzi * BZ + tid / (BX * BY);
+    if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce, true>(P, x, y, z, x + P.nx * (y + P.ny * z));
+}
+template <typename S, int Q, bool kForce>
+__global__ void __launch_bounds__(BRICK, 4) k_sweep_plain(Params P) {
     // persistent over the bricks when the grid is smaller than the brick
     // count (it then leaves CTA slots to the particle kernels running beside)
-    for (int b = blockIdx.x; b < P.nbricks; b += gridDim.x) {
-        if (P.skip && P.skip[(P.step % 3) * P.nbricks + b] == P.step) continue;  // the near sweep takes it
-        int bxi, byi, bzi;
-        brick_coords(P, b, bxi, byi, bzi);
-        const int x = bxi * BX + tid % BX, y = byi * BY + (tid / BX) % BY, z = bzi * BZ + tid / (BX * BY);
-        if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce, true>(P, x, y, z, x + P.nx * (y + P.ny * z));
-    }
+    for (int b = blockIdx.x; b < P.nbricks; b += gridDim.x) plain_brick<S, Q, kForce>(P, b);
 }
 
 // The sweep of the bricks listed this step (exactly those some particle's
 // grown search box meets) and of the predicted-near bricks that are not
 // listed (plain path): every brick k_sweep_plain leaves.  Persistent grid.
 template <typename S, int Q, bool kForce>
-__global__ void __launch_bounds__(BRICK, 4) k_sweep_near(Params P) {
-    __shared__ SmemParticles sp;
-    __shared__ double red[BRICK / 32][6];
-    __shared__ int s_links;
-    __shared__ LinkScratch ls;
+__device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, double (*red)[6], int &s_links,
+                                          LinkScratch &ls, int blk, int nblk) {
     const int tid = threadIdx.x;
     const int t = P.step;
     const int c_exact = P.counters[CNT_LISTED];
     const int c_pred = P.pred_stamp_cur ? P.pred_count[t % 3] : 0;
     int done = 0;
-    for (int w = blockIdx.x; w < c_exact + c_pred; w += gridDim.x) {
+    for (int w = blk; w < c_exact + c_pred; w += nblk) {
         int b;
         if (w < c_exact) {
             b = P.wl_list[(t % 3) * P.nbricks + w];
@@ -674,8 +673,26 @@ __global__ void __launch_bounds__(BRICK, 4) k_sweep_near(Params P) {
         int bxi, byi, bzi;
         brick_coords(P, b, bxi, byi, bzi);
         const int bx0 = bxi * BX, by0 = byi * BY, bz0 = bzi * BZ;
-        const int cnt = min(P.bcount[b], MAXPB);
+        int cnt = min(P.bcount[b], MAXPB);
         __syncthreads();  // the previous brick is done with the shared state
+        if (cnt > 0 && P.brick_solid) {
+            // particle links and missing force points need a solid node in
+            // the brick or next to it: look at the 27 bricks around
+            bool near_solid = false;
+            if (tid < 27) {
+                int q[3] = {bxi + tid % 3 - 1, byi + (tid / 3) % 3 - 1, bzi + tid / 9 - 1};
+                const int nbs[3] = {P.nbx, P.nby, P.nbz};
+                bool in = true;
+                for (int a = 0; a < 3; a++) {
+                    if (q[a] < 0 || q[a] >= nbs[a]) {
+                        if (P.per[a]) q[a] = (q[a] + nbs[a]) % nbs[a];
+                        else in = false;
+                    }
+                }
+                near_solid = in && P.brick_solid[q[0] + P.nbx * (q[1] + P.nby * q[2])] != 0;
+            }
+            if (!__syncthreads_or(near_solid)) cnt = 0;
+        }
         if (cnt == 0) {
             const int x = bx0 + tid % BX, y = by0 + (tid / BX) % BY, z = bz0 + tid / (BX * BY);
             if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce>(P, x, y, z, x + P.nx * (y + P.ny * z));
@@ -686,6 +703,14 @@ __global__ void __launch_bounds__(BRICK, 4) k_sweep_near(Params P) {
         near_brick<S, Q, kForce>(P, sp, red, &s_links, &ls, b, bx0, by0, bz0, cnt);
     }
     if (tid == 0 && done) atomicAdd(&P.counters[CNT_NEAR], done);
+}
+template <typename S, int Q, bool kForce>
+__global__ void __launch_bounds__(BRICK, 4) k_sweep_near(Params P) {
+    __shared__ SmemParticles sp;
+    __shared__ double red[BRICK / 32][6];
+    __shared__ int s_links;
+    __shared__ LinkScratch ls;
+    near_work<S, Q, kForce>(P, sp, red, s_links, ls, blockIdx.x, gridDim.x);
 }
 
 }  // namespace lbmmb

@@ -2,7 +2,7 @@
 // instantiates them for one storage type.
 #pragma once
 
-#include "k_sweep.cuh"
+#include "k_batch.cuh"
 
 namespace lbmmb {
 
@@ -67,6 +67,34 @@ void launch_check_t(const Params &P, const void *f, const uint16_t *flags, cudaS
     else k_check<S, 15><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, flags);
 }
 
+template <typename S>
+void launch_flags_batch_t(const BatchArgs &B, int Q, cudaStream_t st) {
+    const int grid = B.ncases * B.g_chain;
+    if (Q == 19) k_flags_batch<S, 19><<<grid, BRICK, 0, st>>>(B);
+    else k_flags_batch<S, 15><<<grid, BRICK, 0, st>>>(B);
+}
+template <typename S>
+void launch_near_batch_t(const BatchArgs &B, int Q, bool force, cudaStream_t st) {
+    const int grid = B.ncases * B.g_chain;
+    if (Q == 19) {
+        if (force) k_sweep_near_batch<S, 19, true><<<grid, BRICK, 0, st>>>(B);
+        else k_sweep_near_batch<S, 19, false><<<grid, BRICK, 0, st>>>(B);
+    } else {
+        if (force) k_sweep_near_batch<S, 15, true><<<grid, BRICK, 0, st>>>(B);
+        else k_sweep_near_batch<S, 15, false><<<grid, BRICK, 0, st>>>(B);
+    }
+}
+template <typename S>
+void launch_plain_batch_t(const BatchArgs &B, int Q, bool force, int grid, cudaStream_t st) {
+    if (Q == 19) {
+        if (force) k_sweep_plain_batch<S, 19, true><<<grid, BRICK, 0, st>>>(B);
+        else k_sweep_plain_batch<S, 19, false><<<grid, BRICK, 0, st>>>(B);
+    } else {
+        if (force) k_sweep_plain_batch<S, 15, true><<<grid, BRICK, 0, st>>>(B);
+        else k_sweep_plain_batch<S, 15, false><<<grid, BRICK, 0, st>>>(B);
+    }
+}
+
 #define LBMMB_INSTANTIATE(S)                                                                                     \
     template void launch_init_t<S>(const Params &, void *, cudaStream_t);                                        \
     template void launch_flags_t<S>(const Params &, cudaStream_t);                                               \
@@ -76,6 +104,9 @@ void launch_check_t(const Params &P, const void *f, const uint16_t *flags, cudaS
                                      uint16_t *, cudaStream_t);                                                  \
     template void launch_get_pop_t<S>(const Params &, const void *, double *, cudaStream_t);                     \
     template void launch_set_pop_t<S>(const Params &, void *, const double *, cudaStream_t);                     \
-    template void launch_check_t<S>(const Params &, const void *, const uint16_t *, cudaStream_t);
+    template void launch_check_t<S>(const Params &, const void *, const uint16_t *, cudaStream_t);             \
+    template void launch_flags_batch_t<S>(const BatchArgs &, int, cudaStream_t);                                  \
+    template void launch_near_batch_t<S>(const BatchArgs &, int, bool, cudaStream_t);                             \
+    template void launch_plain_batch_t<S>(const BatchArgs &, int, bool, int, cudaStream_t);
 
 }  // namespace lbmmb

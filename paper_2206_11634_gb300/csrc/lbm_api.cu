@@ -30,7 +30,7 @@ void split_pair(double v, float out[2]) {
 struct Layout {
     size_t f[2], flags[2];
     size_t wl_list, wl_count, stamp;
-    size_t pred_stamp, pred_list, pred_count, skip;
+    size_t pred_stamp, pred_list, pred_count, skip, brick_solid;
     size_t bin;        // bcount[nbricks] followed by the per-step counters
     size_t bin_bytes;
     size_t ffix_off;   // offset of the fixed-point force totals within bin
@@ -89,6 +89,7 @@ void make_layout(const lbm_config *c, Layout *L) {
     L->pred_list = take(2 * nb * 4);
     L->pred_count = take(3 * 4);
     L->skip = take(3 * nb * 4);
+    L->brick_solid = take(nb);
     // per-step region, cleared before every step: brick counts, counters,
     // and (FP32 and below) the fixed-point force/torque totals
     L->ffix_off = (nb * 4 + kStepCounters * 4 + 7) / 8 * 8;
@@ -195,6 +196,7 @@ Params make_params(lbm_handle *h) {
     P.pred_list_next = at<int>(h, h->L.pred_list + (size_t)(1 - cur) * h->L.nbricks * 4);
     P.pred_count = at<int>(h, h->L.pred_count);
     P.skip = at<int>(h, h->L.skip);
+    P.brick_solid = at<uint8_t>(h, h->L.brick_solid);
     P.bcount = at<int>(h, h->L.bin);
     P.blist = at<int>(h, h->L.blist);
     P.partial = at<double>(h, h->L.partial);
@@ -394,7 +396,13 @@ int lbm_workspace_size(const lbm_config *cfg, size_t *bytes) {
     return LBM_OK;
 }
 
-int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_stream, lbm_handle **out) {
+}  // extern "C"
+
+namespace {
+// A handle on its workspace; own_streams = false for the cases of a batch
+// (the batch owns the streams, events and step sequence).
+int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_stream, bool own_streams,
+                lbm_handle **out) {
     if (!out) return fail(nullptr, LBM_ERR_BAD_ARG, "out is NULL");
     *out = nullptr;
     if (const char *m = check_config(cfg)) return fail(nullptr, LBM_ERR_BAD_ARG, "%s", m);
@@ -436,17 +444,20 @@ int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_st
         h->plain_per_sm = kDefaultPlainPerSm;
         h->chain_per_sm = kDefaultChainPerSm;
     }
-    int prio_low = 0, prio_high = 0;
-    int rc = cuda_check(h, cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high), "cudaDeviceGetStreamPriorityRange");
-    if (rc == LBM_OK)
-        rc = cuda_check(h, cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_low), "cudaStreamCreateWithPriority");
-    if (rc == LBM_OK)
-        rc = cuda_check(h, cudaStreamCreateWithPriority(&h->hi, cudaStreamNonBlocking, prio_high), "cudaStreamCreateWithPriority");
-    if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "cudaEventCreate");
-    if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
-    if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_bin, cudaEventDisableTiming), "cudaEventCreate");
-    if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_plain, cudaEventDisableTiming), "cudaEventCreate");
-    if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_near, cudaEventDisableTiming), "cudaEventCreate");
+    int rc = LBM_OK;
+    if (own_streams) {
+        int prio_low = 0, prio_high = 0;
+        rc = cuda_check(h, cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high), "cudaDeviceGetStreamPriorityRange");
+        if (rc == LBM_OK)
+            rc = cuda_check(h, cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_low), "cudaStreamCreateWithPriority");
+        if (rc == LBM_OK)
+            rc = cuda_check(h, cudaStreamCreateWithPriority(&h->hi, cudaStreamNonBlocking, prio_high), "cudaStreamCreateWithPriority");
+        if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+        if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+        if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_bin, cudaEventDisableTiming), "cudaEventCreate");
+        if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_plain, cudaEventDisableTiming), "cudaEventCreate");
+        if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_near, cudaEventDisableTiming), "cudaEventCreate");
+    }
     if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + zero_from, 0, L.total - zero_from, h->stream), "cudaMemsetAsync");
     if (rc == LBM_OK)  // no brick is predicted near (or skipped) before the first step
         rc = cuda_check(h, cudaMemsetAsync(h->ws + L.pred_stamp, 0xFF, 2 * (size_t)L.nbricks * 4, h->stream), "cudaMemsetAsync");
@@ -473,6 +484,13 @@ int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_st
     }
     *out = h;
     return LBM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_stream, lbm_handle **out) {
+    return init_handle(cfg, dev_ws, ws_bytes, cuda_stream, true, out);
 }
 
 int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
@@ -874,20 +892,474 @@ int lbm_set_stream(lbm_handle *h, void *cuda_stream) {
 int lbm_destroy(lbm_handle *h) {
     if (!h) return LBM_OK;
     cudaStreamSynchronize(h->stream);
-    cudaStreamSynchronize(h->aux);
+    if (h->aux) cudaStreamSynchronize(h->aux);
+    if (h->hi) cudaStreamSynchronize(h->hi);
     release_profile(h);
-    cudaEventDestroy(h->ev_fork);
-    cudaEventDestroy(h->ev_bin);
-    cudaEventDestroy(h->ev_plain);
-    cudaEventDestroy(h->ev_near);
-    cudaEventDestroy(h->ev_join);
-    cudaStreamSynchronize(h->hi);
-    cudaStreamDestroy(h->aux);
-    cudaStreamDestroy(h->hi);
+    for (cudaEvent_t e : {h->ev_fork, h->ev_bin, h->ev_plain, h->ev_near, h->ev_join})
+        if (e) cudaEventDestroy(e);
+    if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->hi) cudaStreamDestroy(h->hi);
     delete h;
     return LBM_OK;
 }
 
 const char *lbm_last_error(const lbm_handle *h) { return h ? h->err : g_init_error; }
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched lattices
+// ===========================================================================
+struct lbm_batch {
+    int n;
+    std::vector<lbm_handle *> cases;
+    std::vector<size_t> bin1;   // workspace offset of each case's second per-step region
+    char *ws;
+    // `stream` is the caller's; graphs are captured on and launched into the
+    // private `cap` (capture is not allowed on the legacy default stream),
+    // ordered after and before `stream` by ev_pre / ev_post
+    cudaStream_t stream, cap, hi, aux;
+    cudaEvent_t ev_fork, ev_bin, ev_plain, ev_near, ev_join, ev_pre, ev_post;
+    size_t tab_off, brick_off, item_off, ctr_off, brick_case_off;   // device tables at the workspace start
+    int Q, storage;
+    bool force;
+    int g_chain, plain_chunk;
+    int total_bricks, bin_items;
+    bool dirty;
+    int64_t steps;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int graph_steps;
+    char err[256];
+};
+
+namespace {
+
+thread_local char g_batch_error[256] = "no error";
+
+int bfail(lbm_batch *b, int code, const char *fmt, ...) {
+    char *buf = b ? b->err : g_batch_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+int bcheck(lbm_batch *b, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return LBM_OK;
+    return bfail(b, LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Workspace: tables, then per case its single-lattice layout followed by a
+// second per-step region (the per-step region alternates by step parity).
+struct BatchLayout {
+    size_t tab, brick_off, item_off, ctr, brick_case, total;
+    std::vector<size_t> base, bin1;
+};
+
+const char *batch_check(const lbm_config *cfgs, int n) {
+    if (!cfgs || n < 1) return "need at least one case";
+    if (n > 65535) return "at most 65535 cases";
+    for (int c = 0; c < n; c++) {
+        if (const char *m = check_config(&cfgs[c])) return m;
+        if (cfgs[c].lattice != cfgs[0].lattice) return "all cases must use the same lattice";
+        if (cfgs[c].storage != cfgs[0].storage) return "all cases must use the same storage";
+        if (cfgs[c].storage == LBM_STORE_F64) return "batched cases store FP32, FP16 or BF16";
+        if (cfgs[c].n_sub != 0) return "batched cases hold fixed particles (n_sub = 0)";
+    }
+    return nullptr;
+}
+
+void batch_layout(const lbm_config *cfgs, int n, BatchLayout *B) {
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    B->tab = take(2 * (size_t)n * sizeof(Params));
+    B->brick_off = take(((size_t)n + 1) * 4);
+    B->item_off = take(((size_t)n + 1) * 4);
+    B->ctr = take(4 * 4);
+    size_t nb_total = 0;
+    for (int c = 0; c < n; c++) {
+        Layout L;
+        make_layout(&cfgs[c], &L);
+        nb_total += (size_t)L.nbricks;
+    }
+    B->brick_case = take(nb_total * 2);
+    B->base.resize(n);
+    B->bin1.resize(n);
+    for (int c = 0; c < n; c++) {
+        Layout L;
+        make_layout(&cfgs[c], &L);
+        B->base[c] = take(L.total);
+        B->bin1[c] = take(L.bin_bytes);
+    }
+    B->total = o;
+}
+
+// Device tables: per case its Params for either step parity, and the prefix
+// sums the batched kernels map their CTAs with.
+int batch_tables(lbm_batch *b) {
+    std::vector<Params> tab(2 * (size_t)b->n);
+    std::vector<int> boff(b->n + 1), ioff(b->n + 1);
+    boff[0] = ioff[0] = 0;
+    for (int c = 0; c < b->n; c++) {
+        lbm_handle *h = b->cases[c];
+        const int64_t keep_steps = h->steps;
+        const int keep_cur = h->cur, keep_fcur = h->fcur;
+        for (int p = 0; p < 2; p++) {
+            h->cur = p;
+            h->fcur = p;
+            h->steps = p;
+            Params P = make_params(h);
+            char *bin_p = p == 0 ? h->ws + h->L.bin : b->ws + b->bin1[c];
+            char *bin_q = p == 0 ? b->ws + b->bin1[c] : h->ws + h->L.bin;
+            P.bcount = reinterpret_cast<int *>(bin_p);
+            P.counters = reinterpret_cast<int *>(bin_p + (size_t)h->L.nbricks * 4);
+            P.Ffix = reinterpret_cast<unsigned long long *>(bin_p + h->L.ffix_off);
+            P.bin_next = bin_q;
+            // rounded up to whole 16-byte stores: each region is a 256-byte
+            // aligned allocation of its own
+            P.bin_next_bytes = (long long)((h->L.bin_bytes + 15) / 16 * 16);
+            tab[(size_t)p * b->n + c] = P;
+        }
+        h->steps = keep_steps;
+        h->cur = keep_cur;
+        h->fcur = keep_fcur;
+        boff[c + 1] = boff[c] + h->L.nbricks;
+        ioff[c + 1] = ioff[c] + (h->np > 0 ? h->np : 1);
+    }
+    b->total_bricks = boff[b->n];
+    b->bin_items = ioff[b->n];
+    int rc = bcheck(b, cudaMemcpyAsync(b->ws + b->tab_off, tab.data(), tab.size() * sizeof(Params),
+                                       cudaMemcpyHostToDevice, b->stream), "cudaMemcpyAsync(tables)");
+    if (rc == LBM_OK)
+        rc = bcheck(b, cudaMemcpyAsync(b->ws + b->brick_off, boff.data(), boff.size() * 4, cudaMemcpyHostToDevice,
+                                       b->stream), "cudaMemcpyAsync(tables)");
+    if (rc == LBM_OK)
+        rc = bcheck(b, cudaMemcpyAsync(b->ws + b->item_off, ioff.data(), ioff.size() * 4, cudaMemcpyHostToDevice,
+                                       b->stream), "cudaMemcpyAsync(tables)");
+    std::vector<uint16_t> bcase((size_t)boff[b->n]);
+    for (int c = 0; c < b->n; c++)
+        for (int k = boff[c]; k < boff[c + 1]; k++) bcase[(size_t)k] = (uint16_t)c;
+    if (rc == LBM_OK)
+        rc = bcheck(b, cudaMemcpyAsync(b->ws + b->brick_case_off, bcase.data(), bcase.size() * 2,
+                                       cudaMemcpyHostToDevice, b->stream), "cudaMemcpyAsync(tables)");
+    if (rc == LBM_OK) rc = bcheck(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    if (rc == LBM_OK) b->dirty = false;
+    return rc;
+}
+
+BatchArgs batch_args(lbm_batch *b) {
+    BatchArgs B;
+    B.tab = reinterpret_cast<const Params *>(b->ws + b->tab_off);
+    B.ncases = b->n;
+    B.brick_off = reinterpret_cast<const int *>(b->ws + b->brick_off);
+    B.item_off = reinterpret_cast<const int *>(b->ws + b->item_off);
+    B.brick_case = reinterpret_cast<const uint16_t *>(b->ws + b->brick_case_off);
+    B.ctr = reinterpret_cast<unsigned *>(b->ws + b->ctr_off);
+    B.g_chain = b->g_chain;
+    B.plain_chunk = b->plain_chunk;
+    return B;
+}
+
+template <typename S>
+struct DoBatchStep {
+    static void flags(const BatchArgs &B, int Q, cudaStream_t st) { launch_flags_batch_t<S>(B, Q, st); }
+    static void near(const BatchArgs &B, int Q, bool f, cudaStream_t st) { launch_near_batch_t<S>(B, Q, f, st); }
+    static void plain(const BatchArgs &B, int Q, bool f, int grid, cudaStream_t st) {
+        launch_plain_batch_t<S>(B, Q, f, grid, st);
+    }
+};
+
+template <typename Fn>
+void by_batch_storage(int storage, Fn &&fn) {
+    switch (storage) {
+        case LBM_STORE_F32: fn(DoBatchStep<float>()); break;
+        case LBM_STORE_F16: fn(DoBatchStep<__half>()); break;
+        default: fn(DoBatchStep<__nv_bfloat16>()); break;
+    }
+}
+
+// nsteps steps on the batch's streams, forked from and joined into b->cap
+// (the sequence a graph is captured from).
+int batch_issue(lbm_batch *b, int nsteps) {
+    const BatchArgs B = batch_args(b);
+    const int plain_grid = (b->total_bricks + b->plain_chunk - 1) / b->plain_chunk;
+    cudaError_t e = cudaEventRecord(b->ev_fork, b->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->hi, b->ev_fork, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
+    for (int t = 0; t < nsteps && e == cudaSuccess; t++) {
+        launch_bin_batch(B, b->bin_items, b->hi);
+        e = cudaEventRecord(b->ev_bin, b->hi);
+        if (e != cudaSuccess) break;
+        by_batch_storage(b->storage, [&](auto D) { D.flags(B, b->Q, b->hi); });
+        if (t > 0) e = cudaStreamWaitEvent(b->hi, b->ev_plain, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_bin, 0);
+        if (e != cudaSuccess) break;
+        by_batch_storage(b->storage, [&](auto D) { D.plain(B, b->Q, b->force, plain_grid, b->aux); });
+        e = cudaEventRecord(b->ev_plain, b->aux);
+        if (e != cudaSuccess) break;
+        by_batch_storage(b->storage, [&](auto D) { D.near(B, b->Q, b->force, b->hi); });
+        e = cudaEventRecord(b->ev_near, b->hi);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_near, 0);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->hi);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->ev_join, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->ev_plain, 0);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return bcheck(b, e, "batched step launch");
+}
+
+void drop_graph(lbm_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_steps = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_workspace_size(const lbm_config *cfgs, int ncases, size_t *bytes) {
+    if (const char *m = batch_check(cfgs, ncases)) return bfail(nullptr, LBM_ERR_BAD_ARG, "%s", m);
+    if (!bytes) return bfail(nullptr, LBM_ERR_BAD_ARG, "bytes is NULL");
+    BatchLayout BL;
+    batch_layout(cfgs, ncases, &BL);
+    *bytes = BL.total;
+    return LBM_OK;
+}
+
+int lbm_batch_init(const lbm_config *cfgs, int ncases, void *dev_ws, size_t ws_bytes, void *cuda_stream,
+                   lbm_batch **out) {
+    if (!out) return bfail(nullptr, LBM_ERR_BAD_ARG, "out is NULL");
+    *out = nullptr;
+    if (const char *m = batch_check(cfgs, ncases)) return bfail(nullptr, LBM_ERR_BAD_ARG, "%s", m);
+    if (!dev_ws || reinterpret_cast<uintptr_t>(dev_ws) % kAlign)
+        return bfail(nullptr, LBM_ERR_BAD_ARG, "workspace NULL or not 256-byte aligned");
+    BatchLayout BL;
+    batch_layout(cfgs, ncases, &BL);
+    if (ws_bytes < BL.total)
+        return bfail(nullptr, LBM_ERR_WS_TOO_SMALL, "workspace of %zu bytes, %zu needed", ws_bytes, BL.total);
+    lbm_batch *b = new (std::nothrow) lbm_batch();
+    if (!b) return bfail(nullptr, LBM_ERR_BAD_ARG, "out of host memory");
+    b->n = ncases;
+    b->ws = static_cast<char *>(dev_ws);
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->tab_off = BL.tab;
+    b->brick_off = BL.brick_off;
+    b->item_off = BL.item_off;
+    b->ctr_off = BL.ctr;
+    b->brick_case_off = BL.brick_case;
+    b->bin1 = BL.bin1;
+    b->Q = cfgs[0].lattice;
+    b->storage = cfgs[0].storage;
+    b->force = false;
+    for (int c = 0; c < ncases; c++)
+        for (int a = 0; a < 3; a++) b->force = b->force || cfgs[c].force[a] != 0.0;
+    b->g_chain = kDefaultBatchChainCtas;
+    b->plain_chunk = kDefaultBatchPlainChunk;
+    b->steps = 0;
+    std::snprintf(b->err, sizeof(b->err), "no error");
+    int rc = LBM_OK;
+    int prio_low = 0, prio_high = 0;
+    rc = bcheck(b, cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high), "cudaDeviceGetStreamPriorityRange");
+    if (rc == LBM_OK)
+        rc = bcheck(b, cudaStreamCreateWithPriority(&b->aux, cudaStreamNonBlocking, prio_low), "cudaStreamCreate");
+    if (rc == LBM_OK)
+        rc = bcheck(b, cudaStreamCreateWithPriority(&b->hi, cudaStreamNonBlocking, prio_high), "cudaStreamCreate");
+    if (rc == LBM_OK) rc = bcheck(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    for (cudaEvent_t *e : {&b->ev_fork, &b->ev_bin, &b->ev_plain, &b->ev_near, &b->ev_join, &b->ev_pre, &b->ev_post})
+        if (rc == LBM_OK) rc = bcheck(b, cudaEventCreateWithFlags(e, cudaEventDisableTiming), "cudaEventCreate");
+    // tables, counters and the second per-step regions start at zero
+    if (rc == LBM_OK) rc = bcheck(b, cudaMemsetAsync(b->ws, 0, BL.total, b->stream), "cudaMemsetAsync");
+    for (int c = 0; c < ncases && rc == LBM_OK; c++) {
+        lbm_handle *h = nullptr;
+        Layout L;
+        make_layout(&cfgs[c], &L);
+        rc = init_handle(&cfgs[c], b->ws + BL.base[c], L.total, b->stream, false, &h);
+        if (rc != LBM_OK) {
+            bfail(b, rc, "case %d: %s", c, g_init_error);
+            break;
+        }
+        b->cases.push_back(h);
+    }
+    if (rc == LBM_OK) rc = batch_tables(b);
+    if (rc != LBM_OK) {
+        std::snprintf(g_batch_error, sizeof(g_batch_error), "%s", b->err);
+        lbm_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_set_particles(lbm_batch *b, int c, const lbm_particle *host, int n) {
+    if (!b) return bfail(nullptr, LBM_ERR_BAD_ARG, "batch is NULL");
+    if (c < 0 || c >= b->n) return bfail(b, LBM_ERR_BAD_ARG, "case %d out of range", c);
+    for (int j = 0; j < n; j++)
+        if (host && !host[j].fixed) return bfail(b, LBM_ERR_BAD_ARG, "batched cases hold fixed particles");
+    const int rc = lbm_set_particles(b->cases[c], host, n);
+    if (rc != LBM_OK) return bfail(b, rc, "case %d: %s", c, b->cases[c]->err);
+    b->dirty = true;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch *b, int nsteps) {
+    if (!b) return bfail(nullptr, LBM_ERR_BAD_ARG, "batch is NULL");
+    if (nsteps < 0) return bfail(b, LBM_ERR_BAD_ARG, "nsteps < 0");
+    if (nsteps == 0) return LBM_OK;
+    int rc = LBM_OK;
+    if (b->dirty) {
+        const int items = b->bin_items;
+        rc = batch_tables(b);
+        if (rc != LBM_OK) return rc;
+        if (b->bin_items != items) drop_graph(b);
+    }
+    if (!b->exec || b->graph_steps != nsteps) {
+        // capture nsteps steps once; replays read the step numbers from the
+        // device counters, so the same graph serves every later call
+        drop_graph(b);
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return bcheck(b, e, "cudaStreamBeginCapture");
+        const int rc_issue = batch_issue(b, nsteps);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(b->cap, &g);
+        if (rc_issue != LBM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc_issue;
+        }
+        if (e != cudaSuccess) return bcheck(b, e, "cudaStreamEndCapture");
+        b->graph = g;
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (e != cudaSuccess) {
+            drop_graph(b);
+            return bcheck(b, e, "cudaGraphInstantiate");
+        }
+        b->graph_steps = nsteps;
+    }
+    // the graph runs on `cap`, after everything issued on the caller's stream
+    // so far, and the caller's stream continues after it
+    rc = bcheck(b, cudaEventRecord(b->ev_pre, b->stream), "cudaEventRecord");
+    if (rc == LBM_OK) rc = bcheck(b, cudaStreamWaitEvent(b->cap, b->ev_pre, 0), "cudaStreamWaitEvent");
+    if (rc == LBM_OK) rc = bcheck(b, cudaGraphLaunch(b->exec, b->cap), "cudaGraphLaunch");
+    if (rc == LBM_OK) rc = bcheck(b, cudaEventRecord(b->ev_post, b->cap), "cudaEventRecord");
+    if (rc == LBM_OK) rc = bcheck(b, cudaStreamWaitEvent(b->stream, b->ev_post, 0), "cudaStreamWaitEvent");
+    if (rc != LBM_OK) return rc;
+    b->steps += nsteps;
+    for (lbm_handle *h : b->cases) {
+        h->steps = b->steps;
+        h->cur = (int)(b->steps & 1);
+        h->fcur = h->cur;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_get_forces(lbm_batch *b, int c, double *F, double *T) {
+    if (!b) return bfail(nullptr, LBM_ERR_BAD_ARG, "batch is NULL");
+    if (c < 0 || c >= b->n) return bfail(b, LBM_ERR_BAD_ARG, "case %d out of range", c);
+    lbm_handle *h = b->cases[c];
+    const size_t n = (size_t)h->np;
+    if (n == 0) return LBM_OK;
+    // the last step's per-step region (parity of step steps-1)
+    const char *bin = b->steps > 0 && ((b->steps - 1) & 1) ? b->ws + b->bin1[c] : h->ws + h->L.bin;
+    std::vector<long long> fix(n * 6);
+    int st[ST_SLOTS];
+    int rc = bcheck(b, cudaMemcpyAsync(fix.data(), bin + h->L.ffix_off, n * 48, cudaMemcpyDeviceToHost, b->stream),
+                    "cudaMemcpyAsync(F)");
+    if (rc == LBM_OK)
+        rc = bcheck(b, cudaMemcpyAsync(st, h->ws + h->L.status, sizeof(st), cudaMemcpyDeviceToHost, b->stream),
+                    "cudaMemcpyAsync(status)");
+    if (rc == LBM_OK) rc = bcheck(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    if (rc != LBM_OK) return rc;
+    if (st[ST_ERR] & ERRB_BRICK_OVERFLOW)
+        return bfail(b, LBM_ERR_CAPACITY, "case %d: more than %d particles met one brick", c, MAXPB);
+    for (size_t j = 0; j < n; j++)
+        for (int a = 0; a < 3; a++) {
+            if (F) F[3 * j + a] = std::ldexp((double)fix[6 * j + a], -kForceFixBits);
+            if (T) T[3 * j + a] = std::ldexp((double)fix[6 * j + 3 + a], -kForceFixBits);
+        }
+    return LBM_OK;
+}
+
+int lbm_batch_get_populations(lbm_batch *b, int c, void *dev_f) {
+    if (!b) return bfail(nullptr, LBM_ERR_BAD_ARG, "batch is NULL");
+    if (c < 0 || c >= b->n) return bfail(b, LBM_ERR_BAD_ARG, "case %d out of range", c);
+    const int rc = lbm_get_populations(b->cases[c], dev_f);
+    if (rc != LBM_OK) return bfail(b, rc, "case %d: %s", c, b->cases[c]->err);
+    return LBM_OK;
+}
+
+int lbm_batch_set_schedule(lbm_batch *b, int chain_ctas_per_case, int plain_bricks_per_cta) {
+    if (!b) return bfail(nullptr, LBM_ERR_BAD_ARG, "batch is NULL");
+    if (chain_ctas_per_case < 1 || chain_ctas_per_case > 64 || plain_bricks_per_cta < 1 || plain_bricks_per_cta > 64)
+        return bfail(b, LBM_ERR_BAD_ARG, "schedule out of range");
+    if (chain_ctas_per_case != b->g_chain || plain_bricks_per_cta != b->plain_chunk) drop_graph(b);
+    b->g_chain = chain_ctas_per_case;
+    b->plain_chunk = plain_bricks_per_cta;
+    return LBM_OK;
+}
+
+int lbm_batch_tune(lbm_batch *b, int trial_steps, int *chain_ctas_per_case, int *plain_bricks_per_cta,
+                   double *best_ms_per_step) {
+    if (!b) return bfail(nullptr, LBM_ERR_BAD_ARG, "batch is NULL");
+    if (trial_steps < 1) return bfail(b, LBM_ERR_BAD_ARG, "trial_steps < 1");
+    static const int kChain[] = {4, 8, 16, 32, 64};
+    static const int kChunk[] = {1, 2, 4, 8};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = bcheck(b, cudaEventCreate(&e0), "cudaEventCreate");
+    if (rc == LBM_OK) rc = bcheck(b, cudaEventCreate(&e1), "cudaEventCreate");
+    float best = 0.f;
+    int bg = b->g_chain, bc = b->plain_chunk;
+    for (int gi = 0; gi < 5 && rc == LBM_OK; gi++)
+        for (int ci = 0; ci < 4 && rc == LBM_OK; ci++) {
+            rc = lbm_batch_set_schedule(b, kChain[gi], kChunk[ci]);
+            if (rc == LBM_OK) rc = lbm_batch_step(b, trial_steps);  // capture and warm up
+            if (rc == LBM_OK) rc = bcheck(b, cudaEventRecord(e0, b->stream), "cudaEventRecord");
+            if (rc == LBM_OK) rc = lbm_batch_step(b, trial_steps);
+            if (rc == LBM_OK) rc = bcheck(b, cudaEventRecord(e1, b->stream), "cudaEventRecord");
+            if (rc == LBM_OK) rc = bcheck(b, cudaEventSynchronize(e1), "cudaEventSynchronize");
+            float ms = 0.f;
+            if (rc == LBM_OK) rc = bcheck(b, cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+            if (rc == LBM_OK && (best == 0.f || ms < best)) {
+                best = ms;
+                bg = kChain[gi];
+                bc = kChunk[ci];
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc != LBM_OK) return rc;
+    rc = lbm_batch_set_schedule(b, bg, bc);
+    if (chain_ctas_per_case) *chain_ctas_per_case = bg;
+    if (plain_bricks_per_cta) *plain_bricks_per_cta = bc;
+    if (best_ms_per_step) *best_ms_per_step = best / trial_steps;
+    return rc;
+}
+
+int64_t lbm_batch_steps(const lbm_batch *b) { return b ? b->steps : 0; }
+
+int lbm_batch_destroy(lbm_batch *b) {
+    if (!b) return LBM_OK;
+    cudaStreamSynchronize(b->stream);
+    if (b->hi) cudaStreamSynchronize(b->hi);
+    if (b->aux) cudaStreamSynchronize(b->aux);
+    if (b->cap) cudaStreamSynchronize(b->cap);
+    drop_graph(b);
+    for (lbm_handle *h : b->cases) lbm_destroy(h);
+    for (cudaEvent_t e : {b->ev_fork, b->ev_bin, b->ev_plain, b->ev_near, b->ev_join, b->ev_pre, b->ev_post})
+        if (e) cudaEventDestroy(e);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->aux) cudaStreamDestroy(b->aux);
+    if (b->hi) cudaStreamDestroy(b->hi);
+    delete b;
+    return LBM_OK;
+}
+
+const char *lbm_batch_last_error(const lbm_batch *b) { return b ? b->err : g_batch_error; }
 
 }  // extern "C"

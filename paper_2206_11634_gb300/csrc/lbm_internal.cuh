@@ -45,6 +45,10 @@ constexpr int kForceFixBits = 40;
 // metaball: persistent plain grids that leave CTA slots to the particle
 // kernels ran 12-35 % slower per step).
 constexpr int kDefaultPlainPerSm = 0;
+// Batched lattices: CTAs per case of the flag and near sweeps, bricks per CTA
+// of the plain sweep (lbm_batch_tune chooses them by measurement).
+constexpr int kDefaultBatchChainCtas = 4;
+constexpr int kDefaultBatchPlainChunk = 2;
 constexpr int kDefaultChainPerSm = 0;
 
 // FP32 DEM limits: its per-particle tables live in one CTA's shared memory.
@@ -285,6 +289,7 @@ struct Params {
     // writes the slots of t+1 and t+2 only.
     int *skip;             // [3][nbricks], NULL: none
     int *bcount;       // [nbricks]
+    uint8_t *brick_solid;  // [nbricks], the brick held a solid node at its last classification
     int *blist;        // [nbricks][MAXPB]
     double *partial;   // [nbricks][MAXPB][6] (FP64 lattices)
     unsigned long long *Ffix;  // [np][6] fixed-point totals (lattices below FP64), cleared every step
@@ -299,6 +304,8 @@ struct Params {
     double *wall_xi, *wall_xcw;  // [np*6][3]
     float *pair_xi_f, *pair_xm_f;   // [np*np][3], FP32 DEM: spring, warm start (relative to x_i)
     float *wall_xi_f, *wall_xcw_f;  // [np*6][3], FP32 DEM: spring, warm start (relative to x_k)
+    void *bin_next;    // batched lattices: the other parity's per-step region (cleared by the binning)
+    long long bin_next_bytes;
     int *status;       // [ST_SLOTS], sticky error bits
     int *counters;     // per-step counters, zeroed with the brick lists
 };
@@ -517,6 +524,67 @@ void launch_force_reduce(const Params &P, cudaStream_t st);
 void launch_dem(const Params &P, cudaStream_t st);
 void launch_dem32(const Params &P, cudaStream_t st);  // k_dem32.cu
 
+// ---------------------------------------------------------------------------
+// Batched lattices (lbm_batch_*): independent cases stepped together, one
+// launch per phase for all cases.  Each case keeps the single-lattice layout
+// in its own part of the workspace; its Params live in a device table with
+// one row per step parity, and the step numbers come from device counters, so
+// a captured CUDA graph replays correctly.
+// ---------------------------------------------------------------------------
+struct BatchArgs {
+    const Params *tab;      // [2][ncases], row = step parity
+    int ncases;
+    const int *brick_off;   // [ncases + 1] prefix sums of the cases' brick counts
+    const int *item_off;    // [ncases + 1] prefix sums of max(1, particles) (binning CTAs)
+    const uint16_t *brick_case;  // [total bricks] case of each brick of the concatenated ranges
+    unsigned *ctr;          // [0] step of the particle chain, [1] step of the plain sweep,
+                            // [2], [3] CTAs done in the last kernel of each (reset by the last)
+    int g_chain;            // CTAs per case of the flag and near sweeps
+    int plain_chunk;        // bricks per CTA of the plain sweep
+};
+
+// The case's Params for the current step into shared memory (all threads).
+__device__ __forceinline__ void load_case_params(const BatchArgs &B, int c, const volatile unsigned *step_ctr,
+                                                 Params &sP) {
+    __shared__ unsigned s_step;
+    if (threadIdx.x == 0) s_step = *step_ctr;
+    __syncthreads();
+    const unsigned step = s_step;
+    const int *src = reinterpret_cast<const int *>(B.tab + (size_t)(step & 1) * B.ncases + c);
+    int *dst = reinterpret_cast<int *>(&sP);
+    for (int k = threadIdx.x; k < (int)(sizeof(Params) / 4); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    if (threadIdx.x == 0) sP.step = (int)step;
+    __syncthreads();
+}
+
+// The last CTA of a kernel to finish advances a step counter (every CTA read
+// it at its start, and all have finished once the arrival count is full).
+__device__ __forceinline__ void advance_step_when_last(unsigned *arrived, unsigned *step_ctr) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned n = atomicAdd(arrived, 1u);
+        if (n == gridDim.x - 1) {
+            *arrived = 0;
+            __threadfence();
+            atomicAdd(step_ctr, 1u);
+        }
+    }
+}
+
+// Case of a global index given the prefix sums off[0..n] (off[n] > i).
+__device__ __forceinline__ int case_of(const int *off, int n, int i) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+void launch_bin_batch(const BatchArgs &B, int grid, cudaStream_t st);
+
 // Launchers of the storage-templated kernels (launch_impl.cuh, one
 // instantiation per storage type in sweep_<type>.cu).
 template <typename S> void launch_init_t(const Params &P, void *f, cudaStream_t st);
@@ -529,5 +597,8 @@ void launch_fields_t(const Params &P, const void *f, const uint16_t *flags, doub
 template <typename S> void launch_get_pop_t(const Params &P, const void *f, double *out, cudaStream_t st);
 template <typename S> void launch_set_pop_t(const Params &P, void *f, const double *in, cudaStream_t st);
 template <typename S> void launch_check_t(const Params &P, const void *f, const uint16_t *flags, cudaStream_t st);
+template <typename S> void launch_flags_batch_t(const BatchArgs &B, int Q, cudaStream_t st);
+template <typename S> void launch_near_batch_t(const BatchArgs &B, int Q, bool force, cudaStream_t st);
+template <typename S> void launch_plain_batch_t(const BatchArgs &B, int Q, bool force, int grid, cudaStream_t st);
 
 }  // namespace lbmmb

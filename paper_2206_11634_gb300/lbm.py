@@ -78,6 +78,19 @@ _SIGS = {
     "lbm_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "lbm_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "lbm_batch_workspace_size": (C.c_int, [C.POINTER(LbmConfig), C.c_int, C.POINTER(C.c_size_t)]),
+    "lbm_batch_init": (C.c_int, [C.POINTER(LbmConfig), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
+                                 C.POINTER(C.c_void_p)]),
+    "lbm_batch_set_particles": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(LbmParticle), C.c_int]),
+    "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_batch_get_forces": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "lbm_batch_get_populations": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "lbm_batch_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "lbm_batch_tune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_double)]),
+    "lbm_batch_steps": (C.c_int64, [C.c_void_p]),
+    "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
+    "lbm_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_flags_noalloc": (C.c_int, [C.POINTER(LbmConfig), C.POINTER(LbmParticle), C.c_int, C.c_void_p, C.c_void_p]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
@@ -284,3 +297,90 @@ class Lattice:
         st, nr, nl, nb = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32()
         self._ok(self.L.lbm_get_counters(self.h, C.byref(st), C.byref(nr), C.byref(nl), C.byref(nb)), self.h)
         return dict(step=st.value, nrefill=nr.value, nlinks=nl.value, near_bricks=nb.value)
+
+
+class Batch:
+    """Independent lattices stepped together (lbm_batch_*): one launch per
+    phase for all cases, the steps of a call run as a captured CUDA graph.
+    cases: list of make_config keyword dicts, each with nx, ny, nz."""
+
+    def __init__(self, cases: list, *, device: str = "cuda", stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.L = load_library()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        n = len(cases)
+        self.cfgs = (LbmConfig * n)()
+        self.shapes = []
+        for c, kw in enumerate(cases):
+            kw = dict(kw)
+            nx, ny, nz = kw.pop("nx"), kw.pop("ny"), kw.pop("nz")
+            self.cfgs[c] = make_config(nx, ny, nz, **kw)
+            self.shapes.append((nz, ny, nx))
+        self.n = n
+        self.Q = self.cfgs[0].lattice
+        size = C.c_size_t()
+        self._ok(self.L.lbm_batch_workspace_size(self.cfgs, n, C.byref(size)), None)
+        self.ws_bytes = size.value
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self.L.lbm_batch_init(self.cfgs, n, C.c_void_p(self.ws.data_ptr()), self.ws_bytes,
+                                       C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        self._ok(rc, None)
+        self.h = h
+        self.np = [0] * n
+
+    def _ok(self, rc: int, h) -> None:
+        if rc != 0:
+            raise LbmError(rc, self.L.lbm_batch_last_error(h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_particles(self, c: int, particles: Iterable[LbmParticle]) -> None:
+        plist = list(particles)
+        arr = (LbmParticle * max(1, len(plist)))(*plist)
+        self._ok(self.L.lbm_batch_set_particles(self.h, c, arr, len(plist)), self.h)
+        self.np[c] = len(plist)
+
+    def step(self, n: int = 1) -> None:
+        self._ok(self.L.lbm_batch_step(self.h, int(n)), self.h)
+
+    @property
+    def steps(self) -> int:
+        return int(self.L.lbm_batch_steps(self.h))
+
+    def forces(self, c: int):
+        n = max(1, self.np[c])
+        F = np.zeros((n, 3))
+        T = np.zeros((n, 3))
+        self._ok(self.L.lbm_batch_get_forces(self.h, c, F.ctypes.data_as(C.POINTER(C.c_double)),
+                                             T.ctypes.data_as(C.POINTER(C.c_double))), self.h)
+        return F[: self.np[c]], T[: self.np[c]]
+
+    def populations(self, c: int):
+        t = self.torch
+        f = t.empty((self.Q,) + self.shapes[c], dtype=t.float64, device=self.device)
+        self._ok(self.L.lbm_batch_get_populations(self.h, c, C.c_void_p(f.data_ptr())), self.h)
+        return f
+
+    def set_schedule(self, chain_ctas_per_case: int, plain_bricks_per_cta: int) -> None:
+        self._ok(self.L.lbm_batch_set_schedule(self.h, int(chain_ctas_per_case), int(plain_bricks_per_cta)), self.h)
+
+    def tune(self, trial_steps: int = 5):
+        g, k, ms = C.c_int(), C.c_int(), C.c_double()
+        self._ok(self.L.lbm_batch_tune(self.h, int(trial_steps), C.byref(g), C.byref(k), C.byref(ms)), self.h)
+        return g.value, k.value, ms.value

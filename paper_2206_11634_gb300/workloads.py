@@ -138,6 +138,31 @@ def drag_case(storage: str = "f32", n: int = 48, steps: int = 1000, ncp: int = 4
                                      mass=1.0, inertia=np.eye(3))])
 
 
+def batched_drag(ncases: int = 64, storage: str = "f32", lo: int = 48, hi: int = 128, steps: int = 1000,
+                 seed_offset: int = 5):
+    """Workload 5, the batched drag sweep: ncases independent periodic cubes
+    whose side is uniform on {lo..hi} (reading: uniform on the side length),
+    each holding one fixed random metaball of 1-6 control points (offsets
+    uniform in +-0.15 side, nominal radius 0.12 side) near its centre, flow
+    driven by a Guo body force along x scaled so the Stokes-limit mean speed is
+    about the same in every box; tau 0.8; 1000 steps."""
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    cases = []
+    for c in range(ncases):
+        n = int(rng.integers(lo, hi + 1))
+        ncp = int(rng.integers(1, 7))
+        R = 0.12 * n
+        cp, K = nominal_radius_metaball(rng, ncp, 0.15 * n / 2.0, R)
+        ctr = n / 2.0 - 0.5 + rng.uniform(-0.5, 0.5, 3)
+        force = 2e-6 * (48.0 / n) ** 2
+        cases.append(dict(name=f"batched_drag_{c}_{n}^3", nx=n, ny=n, nz=n, periodic=(1, 1, 1), tau=0.8,
+                          storage=storage, n_sub=0, gravity=(0.0, 0.0, 0.0), force=(force, 0.0, 0.0), steps=steps,
+                          kn=0.0, eta_n=0.0, kt=0.0, eta_t=0.0, mu_s=0.0, c_tol=1e-6,
+                          particles=[_particle(cp, K, ctr, q=_random_quaternion(rng), fixed=1, mass=1.0,
+                                               inertia=np.eye(3))]))
+    return cases
+
+
 def empty_box(n: int = 256, storage: str = "f32", periodic=(1, 1, 1)):
     """A lattice with no particles (the sweep's bandwidth ceiling)."""
     return dict(name=f"empty_{n}^3", nx=n, ny=n, nz=n, periodic=periodic, tau=0.8, storage=storage, n_sub=0,
