@@ -99,6 +99,7 @@ typedef struct {
     long step;
     int nrefill;  /* new fluid nodes refilled in the last step */
     int nlinks;   /* particle boundary links in the last sweep */
+    int frozen;   /* 1: node flags kept as they are (no classification, no refill) */
 } orc_state;
 
 /* ------------------------------------------------------------------------- */
@@ -1164,8 +1165,13 @@ int orc_get_particles(const orc_state *s, orc_particle *out) {
 int orc_step(orc_state *s, int nsteps) {
     for (int t = 0; t < nsteps; t++) {
         update_world_cps(s);
-        classify(s, s->own_new);
-        refill(s);
+        if (s->frozen) {
+            /* flags held: the link set stays, while q follows the particles */
+            memcpy(s->own_new, s->own, (size_t)s->N * sizeof(int));
+        } else {
+            classify(s, s->own_new);
+            refill(s);
+        }
         sweep(s);
         double *tmp = s->f; s->f = s->g; s->g = tmp;
         int *to = s->own; s->own = s->own_new; s->own_new = to;
@@ -1173,6 +1179,20 @@ int orc_step(orc_state *s, int nsteps) {
         update_world_cps(s);
         s->step++;
     }
+    return 0;
+}
+
+/* Freeze the node flags (on = 1): classify the current particles once and
+ * keep those flags for every later step, whatever the particles do; the link
+ * fractions q still follow the particles.  This is the "flags frozen over
+ * the window" setting of the drag gradient: a finite difference in the shape
+ * then differentiates the method through q only.  on = 0 releases them. */
+int orc_freeze_flags(orc_state *s, int on) {
+    if (on) {
+        update_world_cps(s);
+        classify(s, s->own);
+    }
+    s->frozen = on != 0;
     return 0;
 }
 

@@ -87,6 +87,7 @@ def lib():
         L.orc_get_particles.argtypes = [P, C.POINTER(Particle)]
         L.orc_step.argtypes = [P, C.c_int]
         L.orc_classify.argtypes = [P, ip]
+        L.orc_freeze_flags.argtypes = [P, C.c_int]
         L.orc_metaball.argtypes = [P, C.c_int, dp]
         L.orc_metaball.restype = C.c_double
         L.orc_metaball_dd.argtypes = [P, C.c_int, dp, dp, dp, dp]
@@ -248,6 +249,11 @@ class Oracle:
     def set_owner(self, own: np.ndarray):
         own = np.ascontiguousarray(own, dtype=np.int32).reshape(self.shape)
         self.L.orc_set_owner(self.h, _ip(own))
+
+    def freeze_flags(self, on: bool = True) -> None:
+        """Classify the current particles once and keep those node flags
+        (q still follows the particles); on=False releases them."""
+        self.L.orc_freeze_flags(self.h, int(on))
 
     def classify(self) -> np.ndarray:
         out = np.empty(self.shape, dtype=np.int32)

@@ -20,7 +20,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "liblbmmb.so")
 
-SOURCES = ["lbm_api.cu", "k_particles.cu", "k_dem32.cu", "sweep_f32.cu", "sweep_f64.cu", "sweep_f16.cu", "sweep_bf16.cu",
+SOURCES = ["lbm_api.cu", "k_particles.cu", "k_dem32.cu", "adjoint.cu", "sweep_f32.cu", "sweep_f64.cu", "sweep_f16.cu", "sweep_bf16.cu",
            "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

@@ -91,6 +91,15 @@ _SIGS = {
     "lbm_batch_steps": (C.c_int64, [C.c_void_p]),
     "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
     "lbm_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "lbm_adj_workspace_size": (C.c_int, [C.POINTER(LbmConfig), C.POINTER(LbmParticle), C.c_int, C.c_int,
+                                         C.POINTER(C.c_size_t)]),
+    "lbm_adj_init": (C.c_int, [C.POINTER(LbmConfig), C.POINTER(LbmParticle), C.c_int, C.c_int, C.c_void_p,
+                               C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lbm_adj_forward": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "lbm_adj_backward": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "lbm_adj_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "lbm_adj_destroy": (C.c_int, [C.c_void_p]),
+    "lbm_adj_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_flags_noalloc": (C.c_int, [C.POINTER(LbmConfig), C.POINTER(LbmParticle), C.c_int, C.c_void_p, C.c_void_p]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),

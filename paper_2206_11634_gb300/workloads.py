@@ -163,6 +163,25 @@ def batched_drag(ncases: int = 64, storage: str = "f32", lo: int = 48, hi: int =
     return cases
 
 
+def adjoint_case(n: int = 96, ncp: int = 6, T: int = 500, W: int = 100, U: float = 0.02, tau: float = 0.8,
+                 seed_offset: int = 4):
+    """Workload 4: the drag gradient.  A fixed metaball of ncp control points
+    (offsets uniform in +-0.06 n, nominal radius n/9.6 = 10 lu at n = 96) at
+    the centre of a periodic n^3 box; fluid started at u = U x (Re = U 2R / nu =
+    4 at the defaults), a Guo body force of twice the Stokes drag per unit
+    volume along x holds the mean flow; J = mean F_x over the last W of T
+    steps.  Control points are given in the world frame (identity
+    orientation, x at the box centre)."""
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    R = n / 9.6
+    cp, K = nominal_radius_metaball(rng, ncp, 0.06 * n, R)
+    c = np.full(3, n / 2.0 - 0.5) + rng.uniform(-0.3, 0.3, 3)
+    nu = (tau - 0.5) / 3.0
+    force = 2.0 * 6.0 * np.pi * nu * R * U / float(n) ** 3
+    return dict(name=f"adjoint_{ncp}cp_{n}^3", nx=n, ny=n, nz=n, periodic=(1, 1, 1), tau=tau, u0=(U, 0.0, 0.0),
+                force=(force, 0.0, 0.0), T=T, W=W, x=c, cp_world=cp + c, K=K)
+
+
 def empty_box(n: int = 256, storage: str = "f32", periodic=(1, 1, 1)):
     """A lattice with no particles (the sweep's bandwidth ceiling)."""
     return dict(name=f"empty_{n}^3", nx=n, ny=n, nz=n, periodic=periodic, tau=0.8, storage=storage, n_sub=0,

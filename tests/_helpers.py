@@ -70,3 +70,38 @@ def fixed_mass(wl, mass=50.0, inertia=500.0):
 
 def fluid_mask_from_flags(flags):
     return np.asarray(flags) == 0
+
+
+# --------------------------------------------------------------------------
+# drag gradient (flags frozen): the oracle's objective for finite differences
+# --------------------------------------------------------------------------
+def adjoint_particle_kw(case, cp_world, K):
+    """A fixed particle with identity orientation whose world control points
+    are cp_world (body frame = cp_world - x)."""
+    x = np.asarray(case["x"], dtype=np.float64)
+    return dict(cp=np.asarray(cp_world, dtype=np.float64) - x, K=np.asarray(K, dtype=np.float64), x=x,
+                q=(1.0, 0.0, 0.0, 0.0), fixed=1, mass=1.0, inertia=np.eye(3))
+
+
+def oracle_drag_J(oracle_mod, case, cp_world, K, base=None):
+    """Mean F_x over the last W of T steps of the FP64 oracle, with the node
+    flags classified from `base` (cp_world, K) and frozen while the particle
+    has (cp_world, K); missing force points off (with frozen flags and one
+    particle every crossing link is an Eq. (28) link)."""
+    base = base or (case["cp_world"], case["K"])
+    o = oracle_mod.Oracle(case["nx"], case["ny"], case["nz"], periodic=(1, 1, 1), tau=case["tau"],
+                          u0=tuple(case["u0"]), force=tuple(case["force"]), missing_force=0)
+    kw = adjoint_particle_kw(case, *base)
+    o.set_particles([oracle_mod.make_particle(kw.pop("cp"), kw.pop("K"), kw.pop("x"), **kw)])
+    o.freeze_flags(True)
+    kw = adjoint_particle_kw(case, cp_world, K)
+    o.set_particles([oracle_mod.make_particle(kw.pop("cp"), kw.pop("K"), kw.pop("x"), **kw)])
+    T, W = case["T"], case["W"]
+    o.step(T - W)
+    J = 0.0
+    for _ in range(W):
+        o.step(1)
+        F, _ = o.forces()
+        J += F[0, 0]
+    return J / W, o
+

@@ -1,6 +1,7 @@
 """CPU checks of the C ABI: the library loads without a GPU, exports every
-function include/lbm_metaball.h declares, sizes workspaces and rejects bad
-configurations with a message.  No compute call is made."""
+function the headers under include/ declare (and the Python binding gives
+each a signature), sizes workspaces and rejects bad configurations with a
+message.  No compute call is made."""
 import ctypes as C
 import os
 import re
@@ -10,7 +11,8 @@ import pytest
 import paper_2206_11634_gb300 as pkg
 from paper_2206_11634_gb300 import build as build_mod
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbm_metaball.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+HEADER = os.path.join(INCLUDE, "lbm_metaball.h")
 
 
 @pytest.fixture(scope="module")
@@ -20,9 +22,12 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(lbm_\w+)\s*\(", text, flags=re.M)))
+    names = set()
+    for h in sorted(os.listdir(INCLUDE)):
+        if h.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(INCLUDE, h)).read(), flags=re.S)
+            names |= set(re.findall(r"^\s*(?:int|int64_t|const char \*)\s*(lbm_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
@@ -34,9 +39,12 @@ def test_header_declares_the_boundary():
 
 def test_every_declared_symbol_is_exported(lib):
     names = declared_functions()
-    assert len(names) >= 13
+    assert len(names) >= 30
     for n in names:
         assert hasattr(lib, n), n
+    # and the binding marshals every one of them
+    from paper_2206_11634_gb300 import lbm
+    assert set(names) <= set(lbm._SIGS), sorted(set(names) - set(lbm._SIGS))
 
 
 def test_struct_layout_matches_c_compiler(tmp_path):
