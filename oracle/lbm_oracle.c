@@ -49,6 +49,7 @@ typedef struct {
     int vibb;           /* 1: VIBB on particle links (§2.3.1); 0: halfway on all */
     int missing_force;  /* 1: missing-force-point treatment, §2.3.5 item 2 */
     int nthreads;       /* OpenMP threads for the lattice loops; 0 = default */
+    int q_exact;        /* 1: link fraction q by Newton on Eq. (26); 0: Eq. (27) */
     double tau, rho0, c0;
     double u0[3];       /* initial uniform fluid velocity */
     double force[3];    /* body force density on the fluid (Guo forcing) */
@@ -394,6 +395,16 @@ int orc_q_newton(const orc_state *s, int j, const double xf[3], const double d[3
     return -1;
 }
 
+/* The link fraction the sweep uses for the link x_f -> x_f + d of particle j
+ * (M_j(x_f) = Mf < c0 <= Ms = M_j(x_f + d)): Eq. (27), or, with q_exact, the
+ * root of Eq. (26) by the Newton iteration above with the tolerance 1e-7 and
+ * the cap of 100 iterations of §2.3.1 (the last iterate when the cap is hit). */
+static double link_q(const orc_state *s, int j, const double xf[3], const double d[3], double Mf, double Ms) {
+    double q = q_linear(s->c.c0, Mf, Ms);
+    if (s->c.q_exact) orc_q_newton(s, j, xf, d, 1e-7, 100, &q);
+    return q;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Local refilling of new fluid nodes, §2.3.3 (Eq. (30)).                     */
 /* Reading: a population f_i' at x_new is "known after streaming" when it
@@ -500,7 +511,7 @@ static link_result particle_link(const orc_state *s, int x, int y, int z, long n
     double d[3] = {s->e[io][0], s->e[io][1], s->e[io][2]};
     double xf[3] = {x, y, z};
     double xs[3] = {x + d[0], y + d[1], z + d[2]};
-    double q = q_linear(s->c.c0, metaball(s, j, xf), metaball(s, j, xs));
+    double q = link_q(s, j, xf, d, metaball(s, j, xf), metaball(s, j, xs));
     for (int a = 0; a < 3; a++) L.xw[a] = xf[a] + q * d[a];
     surface_velocity(s, j, L.xw, L.uw, L.rarm);
     double ff[ORC_MAXQ], fff[ORC_MAXQ];
@@ -576,8 +587,8 @@ static void sweep(orc_state *s) {
                             double yp[3] = {x + mo[0], y + mo[1], z + mo[2]};
                             double My = metaball(s, j, yp);
                             if (My >= s->c.c0) continue;
-                            double q = q_linear(s->c.c0, My, Ms);
                             double d[3] = {s->e[i][0], s->e[i][1], s->e[i][2]};
+                            double q = link_q(s, j, yp, d, My, Ms);
                             double xw[3], uw[3], r[3];
                             for (int c = 0; c < 3; c++) xw[c] = yp[c] + q * d[c];
                             surface_velocity(s, j, xw, uw, r);

@@ -46,6 +46,7 @@ class Config(C.Structure):
         ("vibb", C.c_int),
         ("missing_force", C.c_int),
         ("nthreads", C.c_int),
+        ("q_exact", C.c_int),
         ("tau", C.c_double), ("rho0", C.c_double), ("c0", C.c_double),
         ("u0", C.c_double * 3),
         ("force", C.c_double * 3),
@@ -130,7 +131,7 @@ def _vec(x) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
 
 
-DEFAULTS = dict(Q=19, periodic=(0, 0, 0), n_sub=0, vibb=1, missing_force=1, nthreads=0,
+DEFAULTS = dict(Q=19, periodic=(0, 0, 0), n_sub=0, vibb=1, missing_force=1, nthreads=0, q_exact=0,
                 tau=0.8, rho0=1.0, c0=1.0, u0=(0.0, 0.0, 0.0), force=(0.0, 0.0, 0.0),
                 gravity=(0.0, 0.0, 0.0), kn=0.0, eta_n=0.0, kt=0.0, eta_t=0.0, mu_s=0.0,
                 c_tol=1e-6, mass_spacing=0.5)

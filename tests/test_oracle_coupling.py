@@ -4,7 +4,8 @@ invariants that do not come from the oracle itself.
 - flags: a one-control-point metaball is the sphere |x - c|^2 <= K (§2.1.2);
 - q: Eq. (27) stays in [0,1] (§2.3.1); Newton's root of Eq. (26) equals the
   closed-form line-sphere intersection; Eq. (27)'s error against it is
-  "around 5%" as §2.3.1 reports;
+  "around 5%" as §2.3.1 reports; with the exact-q option the sweep's node
+  update equals the one rebuilt by hand from the closed-form root;
 - VIBB, Eqs. (19)-(25): in a linear velocity field at a resting wall the
   unknown equals the equilibrium of the field extended to the solid node
   (the mirror image of x_d about the wall), for every q in both branches;
@@ -234,3 +235,65 @@ def test_missing_force_points_restore_isotropy(oracle_mod, kind):
     assert np.abs(F).max() < 1e-12 and np.abs(T).max() < 1e-12
     F0, T0 = _touching(oracle_mod, 0, kind)
     assert np.abs(F0).max() > 0.1
+
+
+def _exact_q_sweep(oracle_mod, q_exact):
+    """One step, tau = 1, around a rotating sphere (u_w depends on x_w, so on
+    q), from randomised populations."""
+    o = oracle_mod.Oracle(20, 20, 20, periodic=(1, 1, 1), tau=1.0, q_exact=q_exact)
+    c, K, v, w = np.array([9.37, 10.21, 9.83]), 16.3, np.array([0.01, 0.0, -0.005]), np.array([0.01, -0.02, 0.015])
+    o.set_particles([_sphere(oracle_mod, K, tuple(c), v=tuple(v), w=tuple(w), fixed=1)])
+    rng = np.random.default_rng(21)
+    f0 = o.w[:, None, None, None] * rng.uniform(0.99, 1.01, (o.Q, 20, 20, 20))
+    o.set_populations(f0)
+    o.step(1)
+    return o, f0, c, K, v, w
+
+
+def test_exact_q_sweep_uses_the_sphere_root(oracle_mod):
+    """With q_exact the sweep takes q from Eq. (26) (§2.3.1): at every fluid
+    node beside a sphere the step equals the node update rebuilt from the
+    closed-form line-sphere entry point (pull, Eqs. (19)-(25) for each link
+    with that q and u_w at x_w = x_f + q d, then BGK at tau = 1, where the
+    post-collision state is f^eq of the moments).  Newton stops once a step
+    is below 1e-7, so q is that close to the root, and an unknown moves by at
+    most ~0.05 per unit of q here: 1e-8.  With Eq. (27) the nodes differ by
+    ~3e-3."""
+    worst = {}
+    for qe in (1, 0):
+        o, f0, c, K, v, w = _exact_q_sweep(oracle_mod, qe)
+        own = o.owner()
+        f1 = o.populations()
+        n = 20
+        err, nodes = 0.0, 0
+        for z in range(n):
+            for y in range(n):
+                for x in range(n):
+                    if own[z, y, x] >= 0:
+                        continue
+                    xf = np.array([x, y, z], float)
+                    fin = np.empty(o.Q)
+                    link = False
+                    for i in range(o.Q):
+                        s = (np.array([x, y, z]) - o.e[i]) % n
+                        if own[s[2], s[1], s[0]] < 0:
+                            fin[i] = f0[i, s[2], s[1], s[0]]
+                            continue
+                        link = True
+                        d = -o.e[i].astype(float)
+                        a, b, cc = d @ d, 2 * d @ (xf - c), (xf - c) @ (xf - c) - K
+                        q = (-b - np.sqrt(b * b - 4 * a * cc)) / (2 * a)
+                        uw = v + np.cross(w, xf + q * d - c)
+                        ffp = (np.array([x, y, z]) - d.astype(int)) % n
+                        fff = f0[:, ffp[2], ffp[1], ffp[0]] if own[ffp[2], ffp[1], ffp[0]] < 0 else None
+                        fin[i] = o.vibb_unknown(i, q, f0[:, z, y, x], fff, uw)
+                    if not link:
+                        continue
+                    nodes += 1
+                    rho = fin.sum()
+                    u = (fin[:, None] * o.e).sum(axis=0) / rho
+                    err = max(err, np.abs(o.equilibrium(rho, u) - f1[:, z, y, x]).max())
+        assert nodes > 300
+        worst[qe] = err
+    assert worst[1] < 1e-8, worst
+    assert worst[0] > 1e-6, worst
