@@ -367,9 +367,11 @@ static double q_linear(double c0, double Mf, double Ms) { return (c0 - Mf) / (Ms
 /* Exact root of Eq. (26), M(x_f + q d) = c0, by Newton's method with the
  * tolerance 1e-7 and iteration cap 100 quoted in §2.3.1, started from
  * Eq. (27).  Reading: the root sought is the one in [0,1] (M(x_f) < c0 <=
- * M(x_s) brackets it); a Newton step that leaves the current bracket is
- * replaced by bisection, so grazing links cannot run off to the far side of
- * the particle.  Returns the iteration count, or -1 without convergence. */
+ * M(x_s) brackets it); the iteration stops when the Newton correction is
+ * below the tolerance (taking it); a larger step that leaves the current
+ * bracket is replaced by bisection, so grazing links cannot run off to the
+ * far side of the particle.  Returns the iteration count, or -1 without
+ * convergence. */
 int orc_q_newton(const orc_state *s, int j, const double xf[3], const double d[3], double tol, int maxit,
                  double *q_out) {
     double xs[3] = {xf[0] + d[0], xf[1] + d[1], xf[2] + d[2]};
@@ -382,6 +384,10 @@ int orc_q_newton(const orc_state *s, int j, const double xf[3], const double d[3
         double r = M - s->c.c0;
         if (r < 0.0) lo = q; else hi = q;
         double slope = dot(gr, d);
+        if (slope != 0.0 && fabs(r / slope) < tol) {
+            *q_out = q - r / slope;
+            return it + 1;
+        }
         double qn = slope != 0.0 ? q - r / slope : 0.5 * (lo + hi);
         if (!(qn > lo && qn < hi)) qn = 0.5 * (lo + hi);
         double dq = qn - q;
