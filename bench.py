@@ -42,7 +42,7 @@ UNIT = "MLUPS"
 BYTES_PER_VALUE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}  # one stored population
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_plain_settling_metaball_128x128x256.txt")
 BRICK_NODES = 32 * 4 * 2
-SWEEP_SOURCES = ["k_sweep.cuh", "k_flags.cuh", "lbm_internal.cuh", "launch_impl.cuh", "sweep_f32.cu"]
+SWEEP_SOURCES = ["k_plain.cuh", "lbm_internal.cuh"]
 
 
 WORKLOADS = ("settling_metaball", "empty_box", "settling_sphere", "multi_particle", "batched_drag")

@@ -89,7 +89,10 @@ typedef struct lbm_config {
                                   the rigid-body state kept as compensated FP32 pairs (about 48
                                   significant bits), when n <= 256 and the particles' control points
                                   number <= 2048 in all, else in FP64 */
-    int32_t reserved0;         /* 0 */
+    int32_t q_exact;           /* 0 = link fraction q by Eq. (27); 1 = the root of Eq. (26) by Newton's
+                                  method from Eq. (27)'s value (§2.3.1: tolerance 1e-7, at most 100
+                                  iterations; a step leaving the bracket [0,1] bisects), in the
+                                  storage's working precision (FP64 for FP64, else FP32) */
     double tau;                /* BGK relaxation time, > 1/2 */
     double rho0;               /* reference density (initial fluid, refill, Eq. (31)) */
     double c0;                 /* surface value of M (Eq. (26)); 1 for the metaball of Eq. (4) */

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(BRICK) k_flags_batch(BatchArgs B) {
 // g_chain CTAs per case over its near bricks; the last CTA of the launch
 // advances the particle chain's step counter.
 template <typename S, int Q, bool kForce>
-__global__ void __launch_bounds__(BRICK, 4) k_sweep_near_batch(BatchArgs B) {
+__global__ void __launch_bounds__(BRICK, kNearCtasPerSm) k_sweep_near_batch(BatchArgs B) {
     __shared__ Params sP;
     __shared__ SmemParticles sp;
     __shared__ double red[BRICK / 32][6];

@@ -5,7 +5,8 @@
 //   walls   a source beyond a non-periodic face: halfway bounce-back
 //           f_i = f+_i'(x) (resting wall);
 //   links   a source inside particle j: the unknown by VIBB, Eqs. (19)-(25),
-//           with q from Eq. (27), or halfway bounce-back with the moving-wall
+//           with q from Eq. (27) (or Eq. (26) solved by Newton's method,
+//           option q_exact), or halfway bounce-back with the moving-wall
 //           term when x - d is not a fluid node (§2.3.5 item 1); the
 //           Galilean-invariant momentum exchange of Eqs. (28)-(29) goes to
 //           particle j;
@@ -19,13 +20,20 @@
 // torque terms are accumulated per listed particle.  FP64 lattices reduce them
 // across the CTA in a fixed order (warp butterfly, then warps in order) into
 // FP64 partials per (brick, particle) that k_force_reduce sums in brick order;
-// lattices below FP64 add each warp's FP32 sums to 64-bit fixed-point totals
-// per particle with integer atomics (exact, so the order does not matter).
+// lattices below FP64 turn every term into 64-bit fixed point, sum it per warp
+// in shared memory and add the warp's sums to the totals per particle, all
+// with integer atomics (exact, so the order does not matter).
 #pragma once
 
 #include "k_flags.cuh"
+#include "k_plain.cuh"
 
 namespace lbmmb {
+// Resident CTAs per SM of the near sweep: its link evaluation needs more than
+// the 64 registers per thread that four 256-thread CTAs leave (it spilled to
+// local memory there, and one brick's latency sets the step when few bricks
+// are near), so it is compiled for two.
+constexpr int kNearCtasPerSm = 2;
 
 template <typename C>
 __device__ __forceinline__ C warp_sum(C v) {
@@ -72,6 +80,71 @@ __device__ __forceinline__ C m_value(const Params &P, const SmemParticles &sp, i
 
 template <typename C> __device__ __forceinline__ C c0_of(const Params &P) { return sizeof(C) == 4 ? (C)P.c0_f : (C)P.c0; }
 
+// M of listed particle s and its derivative along d at x_b + q d, x_b the
+// brick-local node (lx,ly,lz): M = sum K/r^2, dM/dq = -2 sum K (r.d)/r^4.
+// FP32 works on brick-relative offsets, minimum image taken at the node.
+template <typename C>
+__device__ __forceinline__ void m_line(const Params &P, const SmemParticles &sp, int s, int lx, int ly, int lz,
+                                       int dx, int dy, int dz, int bx0, int by0, int bz0, C q, C &M, C &dM) {
+    M = 0;
+    dM = 0;
+    if (sizeof(C) == 8) {
+        const DevParticle &p = P.parts[sp.id[s]];
+        for (int k = 0; k < p.ncp; k++) {
+            const double r0 = minimg_d(P, 0, (double)(bx0 + lx) - p.cpw[k][0]) + (double)q * dx;
+            const double r1 = minimg_d(P, 1, (double)(by0 + ly) - p.cpw[k][1]) + (double)q * dy;
+            const double r2 = minimg_d(P, 2, (double)(bz0 + lz) - p.cpw[k][2]) + (double)q * dz;
+            const double inv = 1.0 / (r0 * r0 + r1 * r1 + r2 * r2);
+            const double t = p.K[k] * inv;
+            M += (C)t;
+            dM += (C)(-2.0 * t * inv * (r0 * dx + r1 * dy + r2 * dz));
+        }
+        return;
+    }
+    const float Ls[3] = {(float)P.nx, (float)P.ny, (float)P.nz};
+    const int l[3] = {lx, ly, lz}, d[3] = {dx, dy, dz};
+    for (int k = 0; k < sp.ncp[s]; k++) {
+        float r[3];
+        for (int a = 0; a < 3; a++) {
+            float b = (float)l[a] - sp.crel[s][k][a];
+            if (P.per[a]) { if (b > 0.5f * Ls[a]) b -= Ls[a]; else if (b < -0.5f * Ls[a]) b += Ls[a]; }
+            r[a] = b + (float)q * (float)d[a];
+        }
+        const float inv = 1.0f / (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        const float t = sp.K[s][k] * inv;
+        M += (C)t;
+        dM += (C)(-2.0f * t * inv * (r[0] * d[0] + r[1] * d[1] + r[2] * d[2]));
+    }
+}
+
+// Exact link fraction (§2.3.1): the root of Eq. (26), M(x_b + q d) = c0, in
+// [0,1] (M(x_b) < c0 <= M(x_b + d) brackets it), by Newton's method started
+// from Eq. (27)'s value q, with the tolerance 1e-7 and the cap of 100
+// iterations the paper states: a Newton correction below the tolerance is
+// taken and ends the iteration; a larger step that would leave the current
+// bracket bisects it instead.  Below FP64 the residual is FP32, so near the
+// root its sign is noise; the bracket then shrinks by bisection and the loop
+// still ends within the cap.
+template <typename C>
+__device__ __noinline__ C q_root(const Params &P, const SmemParticles &sp, int s, int lx, int ly, int lz, int dx,
+                                 int dy, int dz, int bx0, int by0, int bz0, C q) {
+    const C c0 = c0_of<C>(P);
+    C lo = 0, hi = 1;
+    for (int it = 0; it < 100; it++) {
+        C M, dM;
+        m_line<C>(P, sp, s, lx, ly, lz, dx, dy, dz, bx0, by0, bz0, q, M, dM);
+        const C r = M - c0;
+        if (r < C(0)) lo = q; else hi = q;
+        if (dM != C(0) && fabs(r / dM) < C(1e-7)) return q - r / dM;
+        C qn = dM != C(0) ? q - r / dM : C(0.5) * (lo + hi);
+        if (!(qn > lo && qn < hi)) qn = C(0.5) * (lo + hi);
+        const C dq = qn - q;
+        q = qn;
+        if (fabs(dq) < C(1e-7)) break;
+    }
+    return q;
+}
+
 // Lever arm from particle s's centroid to the brick-local point p (minimum
 // image), in the working precision.
 template <typename C>
@@ -111,20 +184,37 @@ __device__ __forceinline__ void particle_velocity(const Params &P, const SmemPar
     uw[2] = v[2] + w[0] * r[1] - w[1] * r[0];
 }
 
+// Where a thread's force and torque terms go.  FP64 lattices add them to a
+// per-thread array [MAXPB][6] that the CTA reduces in a fixed order.
+// Lattices below FP64 turn each term into 64-bit fixed point (2^-40 lu; the
+// FP32 value is kept exactly down to that unit) and add it to the warp's
+// totals in shared memory with integer atomics: exact, so the result does
+// not depend on the order, and no per-thread array lives in local memory.
 template <typename C>
-__device__ __forceinline__ void add_term(C (*acc)[6], int s, const C dP[3], const C r[3]) {
-    acc[s][0] += dP[0];
-    acc[s][1] += dP[1];
-    acc[s][2] += dP[2];
-    acc[s][3] += r[1] * dP[2] - r[2] * dP[1];
-    acc[s][4] += r[2] * dP[0] - r[0] * dP[2];
-    acc[s][5] += r[0] * dP[1] - r[1] * dP[0];
+struct ForceSink {
+    C (*acc)[6];
+    unsigned long long (*fix)[6];
+};
+
+template <typename C>
+__device__ __forceinline__ void add_term(ForceSink<C> sink, int s, const C dP[3], const C r[3]) {
+    const C t[6] = {dP[0], dP[1], dP[2], r[1] * dP[2] - r[2] * dP[1], r[2] * dP[0] - r[0] * dP[2],
+                    r[0] * dP[1] - r[1] * dP[0]};
+    if (sizeof(C) == 8) {
+#pragma unroll
+        for (int c = 0; c < 6; c++) sink.acc[s][c] += t[c];
+    } else {
+        const float scale = (float)(1ull << kForceFixBits);
+#pragma unroll
+        for (int c = 0; c < 6; c++)
+            if (t[c] != C(0)) atomicAdd(&sink.fix[s][c], (unsigned long long)__float2ll_rn((float)t[c] * scale));
+    }
 }
 
 // The unknown population of one particle link (direction i arrives at x from
 // the solid node x + d, d = -e_i) and its momentum-exchange term, in offset
-// form: gown are the node's post-collision offsets g = f - w rho0, drho_f =
-// rho_f - rho0, and the unknown is returned as an offset.  Eq. (28)'s term is
+// form: fown_io is the node's post-collision offset g = f - w rho0 along d,
+// drho_f = rho_f - rho0, and the unknown is returned as an offset.  Eq. (28)'s term is
 // (d - u_w) f+_d + (d + u_w) f_-d = 2 d w rho0 + (d - u_w) g+_d + (d + u_w)
 // g_-d; the constant 2 d w rho0 sums to exactly zero over all links that cross
 // a particle's surface (those of Eq. (28) and the missing force points of
@@ -132,14 +222,14 @@ __device__ __forceinline__ void add_term(C (*acc)[6], int s, const C dP[3], cons
 // does its torque (x_s - x_p) x 2 d w rho0, so both are left out unless the
 // missing force points are switched off.
 template <typename S, int Q>
-__device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, const SmemParticles &sp, int i, int x,
-                                                          int y, int z, int lx, int ly, int lz, int bx0, int by0,
-                                                          int bz0, long long ns_solid,
-                                                          const typename Codec<S>::C *fown,
-                                                          typename Codec<S>::C drho_f,
-                                                          const typename Codec<S>::C *u_f,
-                                                          typename Codec<S>::C (*acc)[6],
-                                                          typename Codec<S>::C *Mf_cache, int *Mf_slot) {
+__device__ __forceinline__ typename Codec<S>::C particle_link(const Params &P, const SmemParticles &sp, int i, int x,
+                                                             int y, int z, int lx, int ly, int lz, int bx0, int by0,
+                                                             int bz0, long long ns_solid,
+                                                             typename Codec<S>::C fown_io,
+                                                             typename Codec<S>::C drho_f,
+                                                             const typename Codec<S>::C *u_f,
+                                                             ForceSink<typename Codec<S>::C> sink,
+                                                             typename Codec<S>::C *Mf_cache, int *Mf_slot) {
     using L = Lat<Q>;
     using Cd = Codec<S>;
     using C = typename Cd::C;
@@ -153,7 +243,7 @@ __device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, cons
     const long long N = P.N;
     if (s < 0) {  // cannot happen for a consistent brick list; bounce back plainly
         atomicOr(&P.status[ST_ERR], ERRB_BRICK_OVERFLOW);
-        return fown[io];
+        return fown_io;
     }
     // q by Eq. (27), clamped to [0,1] (rounding can push it past the ends);
     // M_j(x_f) is shared by all links of the node to the same particle
@@ -165,6 +255,7 @@ __device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, cons
     const C Ms = m_value<C>(P, sp, s, lx + dx, ly + dy, lz + dz, bx0, by0, bz0);
     C q = (c0_of<C>(P) - Mf) / (Ms - Mf);
     q = q < C(0) ? C(0) : (q > C(1) ? C(1) : q);
+    if (P.q_exact) q = q_root<C>(P, sp, s, lx, ly, lz, dx, dy, dz, bx0, by0, bz0, q);
     C r[3], uw[3];
     lever<C>(P, sp, s, bx0, by0, bz0, (C)lx + q * dx, (C)ly + q * dy, (C)lz + q * dz, r);
     particle_velocity<C>(P, sp, s, r, uw);
@@ -192,7 +283,6 @@ __device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, cons
             if (k == io) fff_io = fk;
         }
     }
-    const C fown_io = fown[io];
     const bool ff_ok = ff_in && flag_ff == 0;
     C fin;
     if (!P.vibb || !ff_ok) {
@@ -234,7 +324,7 @@ __device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, cons
         const C c = C(2) * w_io * rho0;
         dP[0] += c * dx; dP[1] += c * dy; dP[2] += c * dz;
     }
-    add_term<C>(acc, s, dP, r);
+    add_term<C>(sink, s, dP, r);
     return fin;
 }
 
@@ -245,9 +335,9 @@ __device__ __noinline__ typename Codec<S>::C particle_link(const Params &P, cons
 // x_s inside j but owned by another particle) is a missing force point and
 // gets Eqs. (31)-(32) with f^eq(rho0, u_w).
 template <typename S, int Q>
-__device__ __noinline__ void solid_node(const Params &P, const SmemParticles &sp, int x, int y, int z, int lx, int ly,
-                                        int lz, int bx0, int by0, int bz0, int owner,
-                                        typename Codec<S>::C (*acc)[6]) {
+__device__ __noinline__ int solid_node(const Params &P, const SmemParticles &sp, int x, int y, int z, int lx, int ly,
+                                       int lz, int bx0, int by0, int bz0, int owner,
+                                       ForceSink<typename Codec<S>::C> sink) {
     using L = Lat<Q>;
     using C = typename Codec<S>::C;
     const C rho0 = Prm<C>::rho0(P);
@@ -263,6 +353,7 @@ __device__ __noinline__ void solid_node(const Params &P, const SmemParticles &sp
         if (yz < 0 || yz >= P.nz) { if (P.per[2]) yz = (yz + P.nz) % P.nz; else in = false; }
         nf[i] = in ? (uint32_t)P.flag_new[yx + P.nx * (yy + P.ny * yz)] : kWall;
     }
+    int terms = 0;
     for (int s = 0; s < sp.n; s++) {
         const int j = sp.id[s];
         // a node whose neighbours all belong to j, or are fluid with j the
@@ -288,6 +379,7 @@ __device__ __noinline__ void solid_node(const Params &P, const SmemParticles &sp
             if (inside_exact<C>(P, sp, s, lx - dx, ly - dy, lz - dz, bx0, by0, bz0, My)) continue;
             C q = (c0_of<C>(P) - My) / (Ms - My);
             q = q < C(0) ? C(0) : (q > C(1) ? C(1) : q);
+            if (P.q_exact) q = q_root<C>(P, sp, s, lx - dx, ly - dy, lz - dz, dx, dy, dz, bx0, by0, bz0, q);
             C r[3], uw[3];
             lever<C>(P, sp, s, bx0, by0, bz0, (C)(lx - dx) + q * dx, (C)(ly - dy) + q * dy, (C)(lz - dz) + q * dz, r);
             particle_velocity<C>(P, sp, s, r, uw);
@@ -300,101 +392,11 @@ __device__ __noinline__ void solid_node(const Params &P, const SmemParticles &sp
             dP[0] = (C(dx) - uw[0]) * fi + (C(dx) + uw[0]) * fo;
             dP[1] = (C(dy) - uw[1]) * fi + (C(dy) + uw[1]) * fo;
             dP[2] = (C(dz) - uw[2]) * fi + (C(dz) + uw[2]) * fo;
-            add_term<C>(acc, s, dP, r);
+            add_term<C>(sink, s, dP, r);
+            terms++;
         }
     }
-}
-
-// Collide one node and store it: moments (Eq. (18)) with the half-force
-// shift, BGK toward f^eq (Eqs. (15)-(16)) plus Guo's forcing term (compiled
-// out when the body force is zero).
-template <typename S, int Q, bool kForce, bool kStream = false>
-__device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>::C (&fin)[Q], S *B, long long N,
-                                              int n) {
-    using L = Lat<Q>;
-    using Cd = Codec<S>;
-    using C = typename Cd::C;
-    const C rho0 = Prm<C>::rho0(P);
-    // offsets: rho = rho0 + sum g, momentum = sum g e
-    C drho = 0, mx = 0, my = 0, mz = 0;
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        drho += fin[i];
-        mx += fin[i] * L::e(i, 0);
-        my += fin[i] * L::e(i, 1);
-        mz += fin[i] * L::e(i, 2);
-    }
-    const C rho = rho0 + drho;
-    const C Fx = kForce ? Prm<C>::F(P, 0) : C(0), Fy = kForce ? Prm<C>::F(P, 1) : C(0),
-            Fz = kForce ? Prm<C>::F(P, 2) : C(0);
-    C inv_rho;
-    if (sizeof(C) == 4) inv_rho = (C)__frcp_rn((float)rho);
-    else inv_rho = C(1) / rho;
-    const C ux = (mx + C(0.5) * Fx) * inv_rho, uy = (my + C(0.5) * Fy) * inv_rho, uz = (mz + C(0.5) * Fz) * inv_rho;
-    const C omega = Prm<C>::omega(P);
-    const C uu = ux * ux + uy * uy + uz * uz;
-    const C om_rho = omega * rho, om_drho = omega * drho;
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
-        const C w = (C)L::w(i);
-        const C eu = ex * ux + ey * uy + ez * uz;
-        // omega g^eq = w (omega drho + omega rho (3 eu + 4.5 eu^2 - 1.5 uu))
-        const C geq_om = w * (om_drho + om_rho * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu));
-        C out = fin[i] - omega * fin[i] + geq_om;
-        if (kForce) {
-            const C gfac = Prm<C>::gfac(P);
-            const C uF = ux * Fx + uy * Fy + uz * Fz;
-            const C eF = ex * Fx + ey * Fy + ez * Fz;
-            out += gfac * w * (C(3) * (eF - uF) + C(9) * eu * eF);
-        }
-        if (kStream) Cd::st_s(B + (long long)i * N + n, out, w, rho0);
-        else Cd::st(B + (long long)i * N + n, out, w, rho0);
-    }
-}
-
-// Neighbour coordinates of a node along each axis (index 0: -1, 1: 0, 2: +1),
-// wrapped on periodic axes, -1 beyond a wall.
-__device__ __forceinline__ void neighbour_coords(const Params &P, int x, int y, int z, int xs[3], int ys[3], int zs[3]) {
-    xs[1] = x; ys[1] = y; zs[1] = z;
-    xs[0] = x - 1; xs[2] = x + 1; ys[0] = y - 1; ys[2] = y + 1; zs[0] = z - 1; zs[2] = z + 1;
-    if (xs[0] < 0) xs[0] = P.per[0] ? P.nx - 1 : -1;
-    if (xs[2] >= P.nx) xs[2] = P.per[0] ? 0 : -1;
-    if (ys[0] < 0) ys[0] = P.per[1] ? P.ny - 1 : -1;
-    if (ys[2] >= P.ny) ys[2] = P.per[1] ? 0 : -1;
-    if (zs[0] < 0) zs[0] = P.per[2] ? P.nz - 1 : -1;
-    if (zs[2] >= P.nz) zs[2] = P.per[2] ? 0 : -1;
-}
-
-// A node of a brick no particle reaches: pull, halfway bounce-back at walls
-// (the node's own outgoing population), collide.  No flags are read.  Node
-// indices are 32-bit (the lattice holds fewer than 2^31 nodes).
-template <typename S, int Q, bool kForce, bool kStream = false>
-__device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z, int n) {
-    using L = Lat<Q>;
-    using Cd = Codec<S>;
-    using C = typename Cd::C;
-    const S *A = (const S *)P.fA;
-    S *B = (S *)P.fB;
-    const long long N = P.N;
-    const C rho0 = Prm<C>::rho0(P);
-    int xs[3], ys[3], zs[3];
-    neighbour_coords(P, x, y, z, xs, ys, zs);
-    int row[3][3];  // nx * (y' + ny * z') for the neighbour rows
-#pragma unroll
-    for (int b = 0; b < 3; b++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) row[b][c] = P.nx * (ys[b] + P.ny * zs[c]);
-    C fin[Q];
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const int bx = 1 - L::e(i, 0), by = 1 - L::e(i, 1), bz = 1 - L::e(i, 2);
-        const bool wall = (xs[bx] | ys[by] | zs[bz]) < 0;
-        // wall: f_i = f+_i'(x), the node's own opposite population
-        const S *src = wall ? A + (long long)L::opp(i) * N + n : A + (long long)i * N + (xs[bx] + row[by][bz]);
-        fin[i] = kStream ? Cd::ld_s(src, (C)L::w(i), rho0) : Cd::ld(src, (C)L::w(i), rho0);
-    }
-    collide_store<S, Q, kForce, kStream>(P, fin, B, N, n);
+    return terms;
 }
 
 // The unknown of one particle link, computed by any lane of the warp: the
@@ -403,7 +405,7 @@ __device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z,
 template <typename S, int Q>
 __device__ __noinline__ typename Codec<S>::C link_coop(const Params &P, const SmemParticles &sp, int i, int lx, int ly,
                                                       int lz, int bx0, int by0, int bz0,
-                                                      typename Codec<S>::C (*acc)[6]) {
+                                                      ForceSink<typename Codec<S>::C> sink) {
     using L = Lat<Q>;
     using Cd = Codec<S>;
     using C = typename Cd::C;
@@ -412,15 +414,19 @@ __device__ __noinline__ typename Codec<S>::C link_coop(const Params &P, const Sm
     const S *A = (const S *)P.fA;
     const long long N = P.N;
     const C rho0 = Prm<C>::rho0(P);
-    C fown[Q];
+    // moments of the node's post-collision populations, and the one along
+    // d = -e_i (picked in the unrolled loop, so nothing is indexed at run time)
+    const int io = L::opp(i);
+    C fown_io = 0;
     C drho_f = 0, m_f[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < Q; k++) {
-        fown[k] = Cd::ld(A + (long long)k * N + n, (C)L::w(k), rho0);
-        drho_f += fown[k];
-        m_f[0] += fown[k] * L::e(k, 0);
-        m_f[1] += fown[k] * L::e(k, 1);
-        m_f[2] += fown[k] * L::e(k, 2);
+        const C fk = Cd::ld(A + (long long)k * N + n, (C)L::w(k), rho0);
+        drho_f += fk;
+        m_f[0] += fk * L::e(k, 0);
+        m_f[1] += fk * L::e(k, 1);
+        m_f[2] += fk * L::e(k, 2);
+        if (k == io) fown_io = fk;
     }
     C u_f[3];
     const C inv_rho_f = C(1) / (rho0 + drho_f);
@@ -432,8 +438,8 @@ __device__ __noinline__ typename Codec<S>::C link_coop(const Params &P, const Sm
     if (sz < 0) sz += P.nz; else if (sz >= P.nz) sz -= P.nz;
     C Mf_cache = 0;
     int Mf_slot = -1;
-    return particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, sx + P.nx * (sy + P.ny * sz), fown,
-                               drho_f, u_f, acc, &Mf_cache, &Mf_slot);
+    return particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, sx + P.nx * (sy + P.ny * sz), fown_io,
+                               drho_f, u_f, sink, &Mf_cache, &Mf_slot);
 }
 
 // Shared scratch of the warp-cooperative link evaluation: per warp a queue of
@@ -442,6 +448,7 @@ constexpr int kLinkQueue = 32 * 18;
 struct LinkScratch {
     unsigned short entry[BRICK / 32][kLinkQueue];
     float result[BRICK / 32][kLinkQueue];
+    unsigned long long fix[BRICK / 32][MAXPB][6];  // the warp's fixed-point force/torque terms
 };
 
 // A fluid node with at least one particle link, in a brick some particle
@@ -450,7 +457,7 @@ struct LinkScratch {
 template <typename S, int Q, bool kForce>
 __device__ __noinline__ void boundary_node(const Params &P, const SmemParticles &sp, int x, int y, int z, int lx,
                                            int ly, int lz, int bx0, int by0, int bz0, int n,
-                                           typename Codec<S>::C (*acc)[6], int *nlinks) {
+                                           ForceSink<typename Codec<S>::C> sink, int *nlinks) {
     using L = Lat<Q>;
     using Cd = Codec<S>;
     using C = typename Cd::C;
@@ -497,8 +504,8 @@ __device__ __noinline__ void boundary_node(const Params &P, const SmemParticles 
     while (links) {
         const int i = __ffs(links) - 1;
         links &= links - 1;
-        fin[i] = particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, srcs[i], fown, drho_f, u_f, acc,
-                                     &Mf_cache, &Mf_slot);
+        fin[i] = particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, srcs[i], fown[L::opp(i)], drho_f,
+                                     u_f, sink, &Mf_cache, &Mf_slot);
         (*nlinks)++;
     }
     collide_store<S, Q, kForce>(P, fin, B, N, n);
@@ -524,15 +531,22 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
     S *B = (S *)P.fB;
     const C rho0 = Prm<C>::rho0(P);
 
-    C acc[MAXPB][6];
-    for (int s = 0; s < cnt; s++)
-        for (int c = 0; c < 6; c++) acc[s][c] = 0;
+    C acc[MAXPB][6];  // FP64 only
+    const ForceSink<C> sink{acc, ls->fix[warp]};
+    if (sizeof(C) == 8) {
+        for (int s = 0; s < cnt; s++)
+            for (int c = 0; c < 6; c++) acc[s][c] = 0;
+    } else {
+        for (int e = lane; e < cnt * 6; e += 32) ls->fix[warp][e / 6][e % 6] = 0ull;
+        __syncwarp();
+    }
     int nlinks = 0;
 
     const uint16_t fl = active ? P.flag_new[n] : (uint16_t)1;
     const bool fluid = active && fl == 0;
+    int nterms = 0;  // missing-force-point terms this thread added
     if (active && fl != 0 && P.missing_force)
-        solid_node<S, Q>(P, sp, x, y, z, lx, ly, lz, bx0, by0, bz0, fl - 1, acc);
+        nterms = solid_node<S, Q>(P, sp, x, y, z, lx, ly, lz, bx0, by0, bz0, fl - 1, sink);
 
     C fin[Q];
     uint32_t links = 0;
@@ -545,13 +559,15 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
             const bool wall = (sx | sy | sz) < 0;
             const int src = wall ? n : sx + P.nx * (sy + P.ny * sz);
             if (!wall && P.flag_new[src] != 0) links |= 1u << i;
-            const S *ptr = wall ? A + (long long)L::opp(i) * N + n : A + (long long)i * N + src;
-            fin[i] = Cd::ld(ptr, (C)L::w(i), rho0);
+            if (sizeof(C) == 8) {
+                const S *ptr = wall ? A + (long long)L::opp(i) * N + n : A + (long long)i * N + src;
+                fin[i] = Cd::ld(ptr, (C)L::w(i), rho0);
+            }
         }
     }
     if (sizeof(C) == 8) {
         // FP64 storage: every node evaluates its own links
-        if (links) boundary_node<S, Q, kForce>(P, sp, x, y, z, lx, ly, lz, bx0, by0, bz0, n, acc, &nlinks);
+        if (links) boundary_node<S, Q, kForce>(P, sp, x, y, z, lx, ly, lz, bx0, by0, bz0, n, sink, &nlinks);
         else if (fluid) collide_store<S, Q, kForce>(P, fin, B, N, n);
     } else {
         // the warp's links in a queue (lane order, then direction order);
@@ -579,32 +595,42 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
             const int L_ = ent >> 5, i = ent & 31;
             const int t = warp * 32 + L_;  // the node's thread index in the brick
             ls->result[warp][e] = (float)link_coop<S, Q>(P, sp, i, t % BX, (t / BX) % BY, t / (BX * BY), bx0, by0,
-                                                         bz0, acc);
+                                                         bz0, sink);
             nlinks++;
         }
         __syncwarp();
         if (fluid) {
-            if (links) {
-                int k = first;
+            // pull after the link evaluation: populations held across the
+            // out-of-line link calls would be spilled around them
+            int xs[3], ys[3], zs[3];
+            neighbour_coords(P, x, y, z, xs, ys, zs);
+            int k = first;
 #pragma unroll
-                for (int i = 1; i < Q; i++)
-                    if (links & (1u << i)) fin[i] = (C)ls->result[warp][k++];
+            for (int i = 0; i < Q; i++) {
+                if (links & (1u << i)) {
+                    fin[i] = (C)ls->result[warp][k];
+                    k++;
+                } else {
+                    const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
+                    const bool wall = (sx | sy | sz) < 0;
+                    const S *ptr = wall ? A + (long long)L::opp(i) * N + n
+                                        : A + (long long)i * N + (sx + P.nx * (sy + P.ny * sz));
+                    fin[i] = Cd::ld(ptr, (C)L::w(i), rho0);
+                }
             }
             collide_store<S, Q, kForce>(P, fin, B, N, n);
         }
     }
 
     if (sizeof(C) == 4) {
-        // per-warp FP32 sums (fixed butterfly order) added to the exact
-        // fixed-point totals with integer atomics: no barrier, no FP64
-        for (int s = 0; s < cnt; s++) {
-            const int pid = sp.id[s];
-#pragma unroll
-            for (int c = 0; c < 6; c++) {
-                const float v = warp_sum<float>((float)acc[s][c]);
-                if (lane == 0 && v != 0.0f)
-                    atomicAdd(&P.Ffix[pid * 6 + c],
-                              (unsigned long long)__float2ll_rn(v * (float)(1ull << kForceFixBits)));
+        // the warp's fixed-point totals go to the particles' totals with
+        // integer atomics (exact, order-independent, no barrier); a warp that
+        // evaluated no link and no missing force point has nothing to add
+        if (__any_sync(0xffffffffu, nlinks > 0 || nterms > 0)) {
+            __syncwarp();
+            for (int e = lane; e < cnt * 6; e += 32) {
+                const unsigned long long v = ls->fix[warp][e / 6][e % 6];
+                if (v) atomicAdd(&P.Ffix[sp.id[e / 6] * 6 + e % 6], v);
             }
         }
         const int nl = __reduce_add_sync(0xffffffffu, (unsigned)nlinks);
@@ -630,24 +656,6 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
         __syncthreads();
         if (tid == 0 && *s_links) atomicAdd(&P.counters[CNT_NLINKS], *s_links);
     }
-}
-
-// The sweep of every brick outside this step's predicted near set: the plain
-// path only.  Runs on its own stream, concurrently with the particle kernels.
-template <typename S, int Q, bool kForce>
-__device__ __forceinline__ void plain_brick(const Params &P, int b) {
-    if (P.skip && P.skip[(P.step % 3) * P.nbricks + b] == P.step) return;  // the near sweep takes it
-    const int tid = threadIdx.x;
-    int bxi, byi, bzi;
-    brick_coords(P, b, bxi, byi, bzi);
-    const int x = bxi * BX + tid % BX, y = byi * BY + (tid / BX) % BY, z = bzi * BZ + tid / (BX * BY);
-    if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce, true>(P, x, y, z, x + P.nx * (y + P.ny * z));
-}
-template <typename S, int Q, bool kForce>
-__global__ void __launch_bounds__(BRICK, 4) k_sweep_plain(Params P) {
-    // persistent over the bricks when the grid is smaller than the brick
-    // count (it then leaves CTA slots to the particle kernels running beside)
-    for (int b = blockIdx.x; b < P.nbricks; b += gridDim.x) plain_brick<S, Q, kForce>(P, b);
 }
 
 // The sweep of the bricks listed this step (exactly those some particle's
@@ -705,7 +713,7 @@ __device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, do
     if (tid == 0 && done) atomicAdd(&P.counters[CNT_NEAR], done);
 }
 template <typename S, int Q, bool kForce>
-__global__ void __launch_bounds__(BRICK, 4) k_sweep_near(Params P) {
+__global__ void __launch_bounds__(BRICK, kNearCtasPerSm) k_sweep_near(Params P) {
     __shared__ SmemParticles sp;
     __shared__ double red[BRICK / 32][6];
     __shared__ int s_links;

@@ -6,7 +6,8 @@
 
 namespace lbmmb {
 
-constexpr int kGridStrideBlocks = 152 * 8;
+constexpr int kSmCount = 152;  // GB300
+constexpr int kGridStrideBlocks = kSmCount * 8;
 
 template <typename S>
 void launch_init_t(const Params &P, void *f, cudaStream_t st) {
@@ -35,7 +36,7 @@ void launch_sweep_plain_t(const Params &P, cudaStream_t st) {
 template <typename S>
 void launch_sweep_near_t(const Params &P, cudaStream_t st) {
     const bool force = P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0;
-    const int cap = P.chain_grid > 0 ? P.chain_grid : kGridStrideBlocks / 2;
+    const int cap = P.chain_grid > 0 ? P.chain_grid : kNearCtasPerSm * kSmCount;
     const int grid = P.nbricks < cap ? P.nbricks : cap;
     if (P.Q == 19) {
         if (force) k_sweep_near<S, 19, true><<<grid, BRICK, 0, st>>>(P);

@@ -60,6 +60,7 @@ const char *check_config(const lbm_config *c) {
         if (c->periodic[a] != 0 && c->periodic[a] != 1) return "periodic[] must be 0 or 1";
     if (c->mass_spacing < 0.0) return "mass_spacing must be >= 0";
     if (c->dem_fp64 != 0 && c->dem_fp64 != 1) return "dem_fp64 must be 0 or 1";
+    if (c->q_exact != 0 && c->q_exact != 1) return "q_exact must be 0 or 1";
     return nullptr;
 }
 

@@ -245,6 +245,7 @@ struct Params {
     long long N;
     int nbx, nby, nbz, nbricks;
     int np, n_sub, vibb, missing_force;
+    int q_exact;              // link fraction by Newton on Eq. (26) instead of Eq. (27)
     int plain_grid;           // CTAs of k_sweep_plain (0: one per brick)
     int chain_grid;           // CTAs of the persistent k_flags / k_sweep_near (0: default)
     int dem_f32;              // DEM in FP32 with compensated state (k_dem32)
@@ -323,6 +324,7 @@ inline void fill_scalar_params(const lbm_config &c, Params &P) {
     P.nbz = (c.nz + BZ - 1) / BZ;
     P.nbricks = P.nbx * P.nby * P.nbz;
     P.n_sub = c.n_sub; P.vibb = c.vibb; P.missing_force = c.missing_force;
+    P.q_exact = c.q_exact;
     P.tau = c.tau; P.rho0 = c.rho0; P.c0 = c.c0;
     for (int a = 0; a < 3; a++) { P.F[a] = c.force[a]; P.g[a] = c.gravity[a]; P.u0[a] = c.u0[a]; }
     P.kn = c.kn; P.eta_n = c.eta_n; P.kt = c.kt; P.eta_t = c.eta_t; P.mu_s = c.mu_s; P.c_tol = c.c_tol;

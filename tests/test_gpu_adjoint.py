@@ -12,7 +12,9 @@ Tolerances:
   forward run, whose drag differs from the FP64 one by ~1e-5; the central
   differences use h = 1e-5, where the oracle's rounding noise is ~1e-11
   relative and q crosses no branch point);
-- the autograd wrapper returns exactly the library's gradient.
+- the autograd wrapper returns the library's gradient (to the run-to-run
+  spread of the adjoint's FP32 atomic scatter, ~1e-7 of the largest
+  component; the test allows 1e-5).
 """
 import numpy as np
 import pytest
@@ -97,7 +99,11 @@ def test_autograd_wrapper(pkg):
     J = eng(cp, K)
     J.backward()
     g_cp, g_K = eng.backward_np()
-    assert np.allclose(cp.grad.numpy(), g_cp, rtol=1e-6, atol=0) and np.allclose(K.grad.numpy(), g_K, rtol=1e-6, atol=0)
+    # a second backward run differs only by the order of the adjoint's FP32
+    # atomic scatter (~1e-7 of the largest component)
+    scale = max(np.abs(g_cp).max(), np.abs(g_K * case["K"]).max())
+    assert np.abs(cp.grad.numpy() - g_cp).max() <= 1e-5 * scale
+    assert np.abs((K.grad.numpy() - g_K) * case["K"]).max() <= 1e-5 * scale
     assert np.isclose(J.item(), eng.forward_np(case["cp_world"], case["K"]), rtol=0, atol=0)
 
 

@@ -55,11 +55,11 @@ def _sync_populations(gpu, orc, rng, amp=1e-2):
     return back
 
 
-def _compare_step(pkg, oracle_mod, wl, storage, Q=19, rng_seed=0, steps=1, amp=1e-2, check_forces=True):
+def _compare_step(pkg, oracle_mod, wl, storage, Q=19, rng_seed=0, steps=1, amp=1e-2, check_forces=True, **over):
     rng = np.random.default_rng(rng_seed)
     wl = H.with_margin(oracle_mod, wl)
-    gpu = H.make_gpu(pkg, wl, Q=Q, storage=storage)
-    orc = H.make_oracle(oracle_mod, wl, Q=Q)
+    gpu = H.make_gpu(pkg, wl, Q=Q, storage=storage, **over)
+    orc = H.make_oracle(oracle_mod, wl, Q=Q, **over)
     gpu.set_particles(H.gpu_particles(pkg, wl))
     orc.set_particles(H.oracle_particles(oracle_mod, wl))
     _sync_populations(gpu, orc, rng, amp)
@@ -182,6 +182,60 @@ def test_one_step(pkg, oracle_mod, W, case, storage):
 @pytest.mark.parametrize("case", ["walls_guo_ragged", "metaball", "touching"])
 def test_one_step_d3q15(pkg, oracle_mod, W, case, storage):
     _compare_step(pkg, oracle_mod, _case(W, case), storage, Q=15)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("case", ["metaball", "touching", "wrap"])
+def test_one_step_exact_q(pkg, oracle_mod, W, case, storage):
+    """Link fraction by Newton's method on Eq. (26) (option q_exact, §2.3.1)
+    on both sides, for the links of Eq. (28) and the missing force points.
+    The tolerances stay those of Eq. (27): the FP64 iterations follow the
+    oracle's; in FP32 the root is found to the residual's rounding, a q error
+    of a few 1e-7 that moves an unknown by ~1e-8.  The option must change the
+    result: the forces differ from the Eq. (27) run by far more than the
+    tolerance."""
+    ex = _compare_step(pkg, oracle_mod, _case(W, case), storage, q_exact=1)
+    lin = _compare_step(pkg, oracle_mod, _case(W, case), storage, q_exact=0)
+    Fe, Fl = ex["F"][0], lin["F"][0]
+    assert np.abs(Fe - Fl).max() > 1e-4 * np.abs(Fl).max(), (Fe, Fl)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("kind", ["wall", "pair"])
+def test_missing_force_points_ab(pkg, oracle_mod, W, storage, kind):
+    """§2.3.5 item 2 as an A/B comparison (the two-sphere test of §3.3, at
+    rest): particles resting against a wall or against each other in fluid
+    at rest.  With the missing force points the force and torque are exactly
+    zero (every crossing link is counted once, and in offset form each term
+    is zero at rest), without them the links hidden by the contact leave a
+    net force of order 0.1, equal to the oracle's within the one-step force
+    tolerance."""
+    wl = W.empty_box(8, storage, (1, 1, 0) if kind == "wall" else (1, 1, 1))
+    if kind == "wall":
+        wl.update(nx=20, ny=20, nz=20)
+        wl["particles"] = [W._particle([[0, 0, 0]], [16.0], (9.3, 10.1, 3.2), fixed=1)]
+    else:
+        wl.update(nx=24, ny=24, nz=24)
+        wl["particles"] = [W._particle([[0, 0, 0], [1, 0.5, 0]], [9.0, 7.0], (8.3, 12.1, 11.6), fixed=1),
+                           W._particle([[0, 0, 0]], [12.0], (14.2, 12.4, 12.2), fixed=1)]
+    wl = H.with_margin(oracle_mod, H.fixed_mass(wl, mass=1.0, inertia=1.0))
+    out = {}
+    for mf in (1, 0):
+        gpu = H.make_gpu(pkg, wl, missing_force=mf)
+        orc = H.make_oracle(oracle_mod, wl, missing_force=mf)
+        gpu.set_particles(H.gpu_particles(pkg, wl))
+        orc.set_particles(H.oracle_particles(oracle_mod, wl))
+        gpu.step(3)
+        orc.step(3)
+        assert np.array_equal(gpu.flags().cpu().numpy() - 1, orc.owner())
+        out[mf] = (gpu.forces(), orc.forces(), orc.counters()["nlinks"])
+    (Fg, Tg), _, _ = out[1]
+    assert np.abs(Fg).max() <= 1e-12 and np.abs(Tg).max() <= 1e-12, (Fg, Tg)
+    (Fg, Tg), (Fo, To), nl = out[0]
+    assert np.abs(Fo).max() > 0.1
+    ftol = 1e-11 * nl * 0.2 if storage == "f64" else POP_TOL[storage] * nl + 1e-5 * np.abs(Fo).max()
+    assert np.abs(Fg - Fo).max() <= ftol, (Fg, Fo)
+    assert np.abs(Tg - To).max() <= 20 * ftol, (Tg, To)
 
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
