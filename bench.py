@@ -476,7 +476,7 @@ def run_batch(args):
             "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
             "config": {"workload": f"batched_drag_64cases_{storage}", "lattice": "D3Q19", "storage": storage,
                        "cases": len(cases), "nodes": nodes, "sides": "48..128", "tau": 0.8,
-                       "schedule": {"chain_ctas_per_case": g, "plain_bricks_per_cta": chunk,
+                       "schedule": {"chain_ctas_per_case": g, "plain_blocks_per_cta": chunk,
                                     "tuned_ms_per_step": round(tune_ms, 4)},
                        "l2": "no flush: populations exceed the 129 MB L2", "parallelism": f"replicas x{world}"},
             "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -484,7 +484,9 @@ def run_batch(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": f"{peak_kind} copy",
                          "kernel": "whole batched step (all phases, all cases)", "bytes_per_launch": alg},
-            "gpu_launches": 4 * (args.steps + max(3, args.warmup)),
+            # binning, plain and near sweeps: the flag pass runs only in the
+            # first three steps after the particles were set (they are fixed)
+            "gpu_launches": 3 * args.steps,
             "clocks": clocks.summary(), "cpu_baseline": None}
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -153,7 +153,9 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n);
  * a whole is ordered on the handle's stream.  Step numbers and buffer parity
  * are kept on the host and passed to the kernels, so a CUDA graph captured
  * from the handle's stream repeats the captured steps' numbers when replayed:
- * do not replay one. */
+ * do not replay one.  When every particle is fixed (fixed = 1) the geometry
+ * cannot change, and from the fourth step after lbm_set_particles() on the
+ * flag pass (§2.3.1, §2.3.3) is left out: its result would be the same. */
 int lbm_step(lbm_handle *h, int nsteps);
 
 /* Synchronise and copy out the hydrodynamic force and torque of the last
@@ -256,11 +258,14 @@ const char *lbm_last_error(const lbm_handle *h);
  * stepped together.  The method per case is that of lbm_step() (§2.2-§2.3;
  * the cases hold fixed particles, so there is no DEM): binning, flags with
  * refilling, the plain and near sweeps with VIBB and momentum exchange.  Each
- * phase is one kernel launch for all cases, and lbm_batch_step() runs its
- * steps as a CUDA graph captured on first use (the step numbers live in
- * device counters, so the graph is replayed by every later call with the same
- * nsteps).  The paper steps one lattice; the batched form has no counterpart
- * there.
+ * phase is one kernel launch for all cases.  The particles being fixed, the
+ * node flags cannot change: the first three steps after particles are set run
+ * the flag pass, later steps leave it out (as lbm_step() does for a lattice
+ * whose particles are all fixed).  Those static steps run as replays of a
+ * CUDA graph of 16 steps captured on first use (the step numbers live in
+ * device counters, so the same graph serves every later call); a remainder of
+ * fewer than 16 steps is launched directly.  The paper steps one lattice; the
+ * batched form has no counterpart there.
  *
  * All cases share the lattice (D3Q19 or D3Q15) and the storage (FP32, FP16
  * or BF16; FP64 is rejected), and have n_sub = 0; sizes, tau, body force and
@@ -296,14 +301,16 @@ int lbm_batch_get_forces(lbm_batch *b, int c, double *F, double *T);
 int lbm_batch_get_populations(lbm_batch *b, int c, void *dev_f);
 
 /* Launch schedule: CTAs per case of the flag and near sweeps (1..64) and
- * bricks per CTA of the plain sweep (1..64).  Results do not depend on it. */
-int lbm_batch_set_schedule(lbm_batch *b, int chain_ctas_per_case, int plain_bricks_per_cta);
+ * blocks of 256 consecutive nodes per CTA of the plain sweep (1..64).
+ * Results do not depend on it. */
+int lbm_batch_set_schedule(lbm_batch *b, int chain_ctas_per_case, int plain_blocks_per_cta);
 
 /* Autotuner: times trial_steps steps (after trial_steps of warm-up) for each
- * schedule of CTAs per case in {4, 8, 16, 32, 64} and bricks per plain CTA in
- * {1, 2, 4, 8}, keeps the fastest and reports it (any output may be NULL).
- * The trials are real steps: the batch advances by 40 * trial_steps steps. */
-int lbm_batch_tune(lbm_batch *b, int trial_steps, int *chain_ctas_per_case, int *plain_bricks_per_cta,
+ * schedule of CTAs per case in {4, 8, 16, 32, 64} and 256-node blocks per
+ * plain CTA in {1, 2, 4, 8}, keeps the fastest and reports it (any output may
+ * be NULL).  The trials are real steps: the batch advances by
+ * 40 * trial_steps steps. */
+int lbm_batch_tune(lbm_batch *b, int trial_steps, int *chain_ctas_per_case, int *plain_blocks_per_cta,
                    double *best_ms_per_step);
 
 /* Steps taken since lbm_batch_init. */

@@ -33,28 +33,33 @@ __global__ void __launch_bounds__(BRICK, kNearCtasPerSm) k_sweep_near_batch(Batc
     advance_step_when_last(B.ctr + 2, B.ctr);
 }
 
-// plain_chunk consecutive bricks of the concatenated brick ranges of all
-// cases per CTA.  The plain path needs only a few of a case's parameters, so
-// they are read straight from the table (L1-cached) instead of copied to
-// shared memory; the brick's case comes from a per-brick map.  The last CTA
-// advances the plain sweep's step counter.
+// plain_chunk consecutive spans of the concatenated span ranges of all cases
+// per CTA.  A span is BRICK consecutive node indices of one case, so each
+// warp's loads and stores cover whole 128-byte rows whatever the box's nx
+// (bricks of a box whose nx is not a multiple of 32 leave lanes idle and
+// start rows mid-line); a node the near sweep takes (its brick is in the
+// skip set) is left out.  The plain path needs only a few of a case's
+// parameters, so they are read straight from the table (L1-cached) instead of
+// copied to shared memory; the span's case comes from a per-span map.  The
+// last CTA advances the plain sweep's step counter.
 template <typename S, int Q, bool kForce>
 __global__ void __launch_bounds__(BRICK, 4) k_sweep_plain_batch(BatchArgs B) {
-    const int total = B.brick_off[B.ncases];
+    const int total = B.span_off[B.ncases];
     const unsigned step = *(volatile const unsigned *)(B.ctr + 1);
     const Params *row = B.tab + (size_t)(step & 1) * B.ncases;
     const int g0 = blockIdx.x * B.plain_chunk;
     const int g1 = min(total, g0 + B.plain_chunk);
     for (int g = g0; g < g1; g++) {
-        const int c = B.brick_case[g];
+        const int c = B.span_case[g];
         const Params &P = row[c];
-        const int b = g - B.brick_off[c];
+        const int n = (g - B.span_off[c]) * BRICK + (int)threadIdx.x;
+        if (n >= P.N) continue;
+        const int nxy = P.nx * P.ny;
+        const int z = n / nxy, r = n - z * nxy;
+        const int y = r / P.nx, x = r - y * P.nx;
+        const int b = x / BX + P.nbx * (y / BY + P.nby * (z / BZ));
         if (P.skip[(step % 3) * P.nbricks + b] == (int)step) continue;  // the near sweep takes it
-        const int tid = threadIdx.x;
-        int bxi, byi, bzi;
-        brick_coords(P, b, bxi, byi, bzi);
-        const int x = bxi * BX + tid % BX, y = byi * BY + (tid / BX) % BY, z = bzi * BZ + tid / (BX * BY);
-        if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce, true>(P, x, y, z, x + P.nx * (y + P.ny * z));
+        plain_node<S, Q, kForce, true>(P, x, y, z, n);
     }
     advance_step_when_last(B.ctr + 3, B.ctr + 1);
 }

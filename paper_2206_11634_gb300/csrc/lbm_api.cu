@@ -44,6 +44,13 @@ struct Layout {
 };
 
 constexpr int kStepCounters = 4;  // nrefill, nlinks, 2 spare
+// Steps with the flag pass after the particles were set, before a geometry of
+// fixed particles counts as static: the pass visits the bricks listed in the
+// last three steps, so three passes leave both flag buffers and the per-brick
+// solid marks holding exactly the fixed particles' flags.
+constexpr int kStaticFlagSteps = 3;
+// Steps per captured graph of a batch (replayed as often as a call needs).
+constexpr int kBatchGraphSteps = 16;
 
 const char *check_config(const lbm_config *c) {
     if (!c) return "config is NULL";
@@ -149,6 +156,8 @@ struct lbm_handle {
     int np;
     int dem_f32;   // the FP32 DEM runs (storage, dem_fp64 and the particle set allow it)
     int fc_valid;  // the DEM of the last step left the contact load of the current state
+    int all_fixed;     // every particle is fixed: the geometry cannot change between set_particles calls
+    int static_steps;  // steps run since set_particles with all_fixed (saturating)
     int nsm;       // SMs of the device
     int plain_per_sm, chain_per_sm;  // launch schedule (lbm_set_schedule)
     int64_t steps;
@@ -429,6 +438,8 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
     h->fcur = 0;
     h->np = 0;
     h->steps = 0;
+    h->all_fixed = 1;
+    h->static_steps = 0;
     h->prof = false;
     for (int k = 0; k < kProfKernels; k++) h->nrec[k] = 0;
     std::snprintf(h->err, sizeof(h->err), "no error");
@@ -604,6 +615,10 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
     if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (rc == LBM_OK) h->np = n;
     h->fc_valid = 0;
+    h->all_fixed = 1;
+    for (int j = 0; j < n; j++)
+        if (!host[j].fixed) h->all_fixed = 0;
+    h->static_steps = 0;
     return rc;
 }
 
@@ -650,7 +665,11 @@ int lbm_step(lbm_handle *h, int nsteps) {
         { ProfScope s(h, 0, true, hs); launch_bin(P, hs); }
         e = cudaEventRecord(h->ev_bin, hs);
         if (e != cudaSuccess) return cuda_check(h, e, "event record");
-        { ProfScope s(h, 1, true, hs); by_storage<DoFlags>(h->cfg.storage, P, hs); }
+        // with every particle fixed the flags cannot change: once both flag
+        // buffers and the per-brick solid marks hold them (the pass visits the
+        // bricks listed in the last three steps), it is left out
+        const bool flags = !(h->all_fixed && h->static_steps >= kStaticFlagSteps);
+        { ProfScope s(h, 1, flags, hs); if (flags) by_storage<DoFlags>(h->cfg.storage, P, hs); }
         // the near sweep reads the halo the previous plain sweep wrote (this
         // wait is issued before ev_plain is recorded again below; the plain
         // sweep of the call before was joined into `stream` before the fork,
@@ -675,6 +694,7 @@ int lbm_step(lbm_handle *h, int nsteps) {
         h->fcur ^= 1;
         h->steps++;
         if (P.np > 0 && P.n_sub > 0) h->fc_valid = 1;
+        if (h->all_fixed && h->static_steps < kStaticFlagSteps) h->static_steps++;
     }
     // join: the caller's stream continues after the last DEM and the last
     // plain sweep
@@ -687,10 +707,12 @@ int lbm_step(lbm_handle *h, int nsteps) {
 
 int lbm_kernels_per_step(const lbm_handle *h) {
     if (!h) return 0;
-    // binning (every step), flags, plain and near sweeps; force reduction
-    // (FP64 lattices with particles); DEM (particles, n_sub > 0)
-    if (h->np == 0) return 4;
-    return 4 + (h->cfg.storage == LBM_STORE_F64 ? 1 : 0) + (h->cfg.n_sub > 0 ? 1 : 0);
+    // binning (every step), flags (left out once the geometry is static),
+    // plain and near sweeps; force reduction (FP64 lattices with particles);
+    // DEM (particles, n_sub > 0)
+    const int flags = h->all_fixed && h->static_steps >= kStaticFlagSteps ? 0 : 1;
+    if (h->np == 0) return 3 + flags;
+    return 3 + flags + (h->cfg.storage == LBM_STORE_F64 ? 1 : 0) + (h->cfg.n_sub > 0 ? 1 : 0);
 }
 
 static int read_status(lbm_handle *h, int *st) {
@@ -921,13 +943,14 @@ struct lbm_batch {
     // ordered after and before `stream` by ev_pre / ev_post
     cudaStream_t stream, cap, hi, aux;
     cudaEvent_t ev_fork, ev_bin, ev_plain, ev_near, ev_join, ev_pre, ev_post;
-    size_t tab_off, brick_off, item_off, ctr_off, brick_case_off;   // device tables at the workspace start
+    size_t tab_off, span_off, item_off, ctr_off, span_case_off;   // device tables at the workspace start
     int Q, storage;
     bool force;
     int g_chain, plain_chunk;
-    int total_bricks, bin_items;
+    int total_spans, bin_items;
     bool dirty;
     int64_t steps;
+    int static_steps;  // steps since the last lbm_batch_set_particles (saturating)
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     int graph_steps;
@@ -954,7 +977,7 @@ int bcheck(lbm_batch *b, cudaError_t e, const char *what) {
 // Workspace: tables, then per case its single-lattice layout followed by a
 // second per-step region (the per-step region alternates by step parity).
 struct BatchLayout {
-    size_t tab, brick_off, item_off, ctr, brick_case, total;
+    size_t tab, span_off, item_off, ctr, span_case, total;
     std::vector<size_t> base, bin1;
 };
 
@@ -979,16 +1002,16 @@ void batch_layout(const lbm_config *cfgs, int n, BatchLayout *B) {
         return at;
     };
     B->tab = take(2 * (size_t)n * sizeof(Params));
-    B->brick_off = take(((size_t)n + 1) * 4);
+    B->span_off = take(((size_t)n + 1) * 4);
     B->item_off = take(((size_t)n + 1) * 4);
     B->ctr = take(4 * 4);
-    size_t nb_total = 0;
+    size_t spans = 0;
     for (int c = 0; c < n; c++) {
         Layout L;
         make_layout(&cfgs[c], &L);
-        nb_total += (size_t)L.nbricks;
+        spans += (size_t)((L.N + BRICK - 1) / BRICK);
     }
-    B->brick_case = take(nb_total * 2);
+    B->span_case = take(spans * 2);
     B->base.resize(n);
     B->bin1.resize(n);
     for (int c = 0; c < n; c++) {
@@ -1004,8 +1027,8 @@ void batch_layout(const lbm_config *cfgs, int n, BatchLayout *B) {
 // sums the batched kernels map their CTAs with.
 int batch_tables(lbm_batch *b) {
     std::vector<Params> tab(2 * (size_t)b->n);
-    std::vector<int> boff(b->n + 1), ioff(b->n + 1);
-    boff[0] = ioff[0] = 0;
+    std::vector<int> soff(b->n + 1), ioff(b->n + 1);
+    soff[0] = ioff[0] = 0;
     for (int c = 0; c < b->n; c++) {
         lbm_handle *h = b->cases[c];
         const int64_t keep_steps = h->steps;
@@ -1029,24 +1052,24 @@ int batch_tables(lbm_batch *b) {
         h->steps = keep_steps;
         h->cur = keep_cur;
         h->fcur = keep_fcur;
-        boff[c + 1] = boff[c] + h->L.nbricks;
+        soff[c + 1] = soff[c] + (int)((h->L.N + BRICK - 1) / BRICK);
         ioff[c + 1] = ioff[c] + (h->np > 0 ? h->np : 1);
     }
-    b->total_bricks = boff[b->n];
+    b->total_spans = soff[b->n];
     b->bin_items = ioff[b->n];
     int rc = bcheck(b, cudaMemcpyAsync(b->ws + b->tab_off, tab.data(), tab.size() * sizeof(Params),
                                        cudaMemcpyHostToDevice, b->stream), "cudaMemcpyAsync(tables)");
     if (rc == LBM_OK)
-        rc = bcheck(b, cudaMemcpyAsync(b->ws + b->brick_off, boff.data(), boff.size() * 4, cudaMemcpyHostToDevice,
+        rc = bcheck(b, cudaMemcpyAsync(b->ws + b->span_off, soff.data(), soff.size() * 4, cudaMemcpyHostToDevice,
                                        b->stream), "cudaMemcpyAsync(tables)");
     if (rc == LBM_OK)
         rc = bcheck(b, cudaMemcpyAsync(b->ws + b->item_off, ioff.data(), ioff.size() * 4, cudaMemcpyHostToDevice,
                                        b->stream), "cudaMemcpyAsync(tables)");
-    std::vector<uint16_t> bcase((size_t)boff[b->n]);
+    std::vector<uint16_t> scase((size_t)soff[b->n]);
     for (int c = 0; c < b->n; c++)
-        for (int k = boff[c]; k < boff[c + 1]; k++) bcase[(size_t)k] = (uint16_t)c;
+        for (int k = soff[c]; k < soff[c + 1]; k++) scase[(size_t)k] = (uint16_t)c;
     if (rc == LBM_OK)
-        rc = bcheck(b, cudaMemcpyAsync(b->ws + b->brick_case_off, bcase.data(), bcase.size() * 2,
+        rc = bcheck(b, cudaMemcpyAsync(b->ws + b->span_case_off, scase.data(), scase.size() * 2,
                                        cudaMemcpyHostToDevice, b->stream), "cudaMemcpyAsync(tables)");
     if (rc == LBM_OK) rc = bcheck(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
     if (rc == LBM_OK) b->dirty = false;
@@ -1057,9 +1080,9 @@ BatchArgs batch_args(lbm_batch *b) {
     BatchArgs B;
     B.tab = reinterpret_cast<const Params *>(b->ws + b->tab_off);
     B.ncases = b->n;
-    B.brick_off = reinterpret_cast<const int *>(b->ws + b->brick_off);
+    B.span_off = reinterpret_cast<const int *>(b->ws + b->span_off);
     B.item_off = reinterpret_cast<const int *>(b->ws + b->item_off);
-    B.brick_case = reinterpret_cast<const uint16_t *>(b->ws + b->brick_case_off);
+    B.span_case = reinterpret_cast<const uint16_t *>(b->ws + b->span_case_off);
     B.ctr = reinterpret_cast<unsigned *>(b->ws + b->ctr_off);
     B.g_chain = b->g_chain;
     B.plain_chunk = b->plain_chunk;
@@ -1086,9 +1109,9 @@ void by_batch_storage(int storage, Fn &&fn) {
 
 // nsteps steps on the batch's streams, forked from and joined into b->cap
 // (the sequence a graph is captured from).
-int batch_issue(lbm_batch *b, int nsteps) {
+int batch_issue(lbm_batch *b, int nsteps, bool flags) {
     const BatchArgs B = batch_args(b);
-    const int plain_grid = (b->total_bricks + b->plain_chunk - 1) / b->plain_chunk;
+    const int plain_grid = (b->total_spans + b->plain_chunk - 1) / b->plain_chunk;
     cudaError_t e = cudaEventRecord(b->ev_fork, b->cap);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->hi, b->ev_fork, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
@@ -1096,7 +1119,7 @@ int batch_issue(lbm_batch *b, int nsteps) {
         launch_bin_batch(B, b->bin_items, b->hi);
         e = cudaEventRecord(b->ev_bin, b->hi);
         if (e != cudaSuccess) break;
-        by_batch_storage(b->storage, [&](auto D) { D.flags(B, b->Q, b->hi); });
+        if (flags) by_batch_storage(b->storage, [&](auto D) { D.flags(B, b->Q, b->hi); });
         if (t > 0) e = cudaStreamWaitEvent(b->hi, b->ev_plain, 0);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_bin, 0);
         if (e != cudaSuccess) break;
@@ -1152,10 +1175,10 @@ int lbm_batch_init(const lbm_config *cfgs, int ncases, void *dev_ws, size_t ws_b
     b->ws = static_cast<char *>(dev_ws);
     b->stream = static_cast<cudaStream_t>(cuda_stream);
     b->tab_off = BL.tab;
-    b->brick_off = BL.brick_off;
+    b->span_off = BL.span_off;
     b->item_off = BL.item_off;
     b->ctr_off = BL.ctr;
-    b->brick_case_off = BL.brick_case;
+    b->span_case_off = BL.span_case;
     b->bin1 = BL.bin1;
     b->Q = cfgs[0].lattice;
     b->storage = cfgs[0].storage;
@@ -1165,6 +1188,7 @@ int lbm_batch_init(const lbm_config *cfgs, int ncases, void *dev_ws, size_t ws_b
     b->g_chain = kDefaultBatchChainCtas;
     b->plain_chunk = kDefaultBatchPlainChunk;
     b->steps = 0;
+    b->static_steps = 0;
     std::snprintf(b->err, sizeof(b->err), "no error");
     int rc = LBM_OK;
     int prio_low = 0, prio_high = 0;
@@ -1207,6 +1231,7 @@ int lbm_batch_set_particles(lbm_batch *b, int c, const lbm_particle *host, int n
     const int rc = lbm_set_particles(b->cases[c], host, n);
     if (rc != LBM_OK) return bfail(b, rc, "case %d: %s", c, b->cases[c]->err);
     b->dirty = true;
+    b->static_steps = 0;
     return LBM_OK;
 }
 
@@ -1221,13 +1246,19 @@ int lbm_batch_step(lbm_batch *b, int nsteps) {
         if (rc != LBM_OK) return rc;
         if (b->bin_items != items) drop_graph(b);
     }
-    if (!b->exec || b->graph_steps != nsteps) {
-        // capture nsteps steps once; replays read the step numbers from the
-        // device counters, so the same graph serves every later call
-        drop_graph(b);
+    // every particle of a batch is fixed, so after kStaticFlagSteps steps with
+    // the flag pass (both flag buffers and the per-brick solid marks then hold
+    // the flags) the steps leave it out; the static steps run as replays of
+    // one captured graph of kBatchGraphSteps steps, the remainder directly
+    const int direct = std::min(nsteps, std::max(0, kStaticFlagSteps - b->static_steps));
+    const int reps = (nsteps - direct) / kBatchGraphSteps;
+    const int rest = (nsteps - direct) % kBatchGraphSteps;
+    if (reps > 0 && !b->exec) {
+        // replays read the step numbers from the device counters, so the same
+        // graph serves every later call
         cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return bcheck(b, e, "cudaStreamBeginCapture");
-        const int rc_issue = batch_issue(b, nsteps);
+        const int rc_issue = batch_issue(b, kBatchGraphSteps, false);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(b->cap, &g);
         if (rc_issue != LBM_OK) {
@@ -1236,21 +1267,26 @@ int lbm_batch_step(lbm_batch *b, int nsteps) {
         }
         if (e != cudaSuccess) return bcheck(b, e, "cudaStreamEndCapture");
         b->graph = g;
-        e = cudaGraphInstantiate(&b->exec, g, 0);
+        // the kernel nodes keep the priorities of the streams they were
+        // captured from (the particle chain above the plain sweep)
+        e = cudaGraphInstantiateWithFlags(&b->exec, g, cudaGraphInstantiateFlagUseNodePriority);
         if (e != cudaSuccess) {
             drop_graph(b);
             return bcheck(b, e, "cudaGraphInstantiate");
         }
-        b->graph_steps = nsteps;
+        b->graph_steps = kBatchGraphSteps;
     }
-    // the graph runs on `cap`, after everything issued on the caller's stream
-    // so far, and the caller's stream continues after it
+    // the steps run on `cap`, after everything issued on the caller's stream
+    // so far, and the caller's stream continues after them
     rc = bcheck(b, cudaEventRecord(b->ev_pre, b->stream), "cudaEventRecord");
     if (rc == LBM_OK) rc = bcheck(b, cudaStreamWaitEvent(b->cap, b->ev_pre, 0), "cudaStreamWaitEvent");
-    if (rc == LBM_OK) rc = bcheck(b, cudaGraphLaunch(b->exec, b->cap), "cudaGraphLaunch");
+    if (rc == LBM_OK && direct > 0) rc = batch_issue(b, direct, true);
+    for (int k = 0; k < reps && rc == LBM_OK; k++) rc = bcheck(b, cudaGraphLaunch(b->exec, b->cap), "cudaGraphLaunch");
+    if (rc == LBM_OK && rest > 0) rc = batch_issue(b, rest, false);
     if (rc == LBM_OK) rc = bcheck(b, cudaEventRecord(b->ev_post, b->cap), "cudaEventRecord");
     if (rc == LBM_OK) rc = bcheck(b, cudaStreamWaitEvent(b->stream, b->ev_post, 0), "cudaStreamWaitEvent");
     if (rc != LBM_OK) return rc;
+    b->static_steps = std::min(kStaticFlagSteps, b->static_steps + nsteps);
     b->steps += nsteps;
     for (lbm_handle *h : b->cases) {
         h->steps = b->steps;
@@ -1295,17 +1331,17 @@ int lbm_batch_get_populations(lbm_batch *b, int c, void *dev_f) {
     return LBM_OK;
 }
 
-int lbm_batch_set_schedule(lbm_batch *b, int chain_ctas_per_case, int plain_bricks_per_cta) {
+int lbm_batch_set_schedule(lbm_batch *b, int chain_ctas_per_case, int plain_blocks_per_cta) {
     if (!b) return bfail(nullptr, LBM_ERR_BAD_ARG, "batch is NULL");
-    if (chain_ctas_per_case < 1 || chain_ctas_per_case > 64 || plain_bricks_per_cta < 1 || plain_bricks_per_cta > 64)
+    if (chain_ctas_per_case < 1 || chain_ctas_per_case > 64 || plain_blocks_per_cta < 1 || plain_blocks_per_cta > 64)
         return bfail(b, LBM_ERR_BAD_ARG, "schedule out of range");
-    if (chain_ctas_per_case != b->g_chain || plain_bricks_per_cta != b->plain_chunk) drop_graph(b);
+    if (chain_ctas_per_case != b->g_chain || plain_blocks_per_cta != b->plain_chunk) drop_graph(b);
     b->g_chain = chain_ctas_per_case;
-    b->plain_chunk = plain_bricks_per_cta;
+    b->plain_chunk = plain_blocks_per_cta;
     return LBM_OK;
 }
 
-int lbm_batch_tune(lbm_batch *b, int trial_steps, int *chain_ctas_per_case, int *plain_bricks_per_cta,
+int lbm_batch_tune(lbm_batch *b, int trial_steps, int *chain_ctas_per_case, int *plain_blocks_per_cta,
                    double *best_ms_per_step) {
     if (!b) return bfail(nullptr, LBM_ERR_BAD_ARG, "batch is NULL");
     if (trial_steps < 1) return bfail(b, LBM_ERR_BAD_ARG, "trial_steps < 1");
@@ -1337,7 +1373,7 @@ int lbm_batch_tune(lbm_batch *b, int trial_steps, int *chain_ctas_per_case, int 
     if (rc != LBM_OK) return rc;
     rc = lbm_batch_set_schedule(b, bg, bc);
     if (chain_ctas_per_case) *chain_ctas_per_case = bg;
-    if (plain_bricks_per_cta) *plain_bricks_per_cta = bc;
+    if (plain_blocks_per_cta) *plain_blocks_per_cta = bc;
     if (best_ms_per_step) *best_ms_per_step = best / trial_steps;
     return rc;
 }

@@ -536,13 +536,13 @@ void launch_dem32(const Params &P, cudaStream_t st);  // k_dem32.cu
 struct BatchArgs {
     const Params *tab;      // [2][ncases], row = step parity
     int ncases;
-    const int *brick_off;   // [ncases + 1] prefix sums of the cases' brick counts
+    const int *span_off;    // [ncases + 1] prefix sums of the cases' plain spans (ceil(N / BRICK) each)
     const int *item_off;    // [ncases + 1] prefix sums of max(1, particles) (binning CTAs)
-    const uint16_t *brick_case;  // [total bricks] case of each brick of the concatenated ranges
+    const uint16_t *span_case;  // [total spans] case of each span of the concatenated ranges
     unsigned *ctr;          // [0] step of the particle chain, [1] step of the plain sweep,
                             // [2], [3] CTAs done in the last kernel of each (reset by the last)
     int g_chain;            // CTAs per case of the flag and near sweeps
-    int plain_chunk;        // bricks per CTA of the plain sweep
+    int plain_chunk;        // spans per CTA of the plain sweep
 };
 
 // The case's Params for the current step into shared memory (all threads).

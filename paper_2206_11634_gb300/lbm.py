@@ -387,8 +387,8 @@ class Batch:
         self._ok(self.L.lbm_batch_get_populations(self.h, c, C.c_void_p(f.data_ptr())), self.h)
         return f
 
-    def set_schedule(self, chain_ctas_per_case: int, plain_bricks_per_cta: int) -> None:
-        self._ok(self.L.lbm_batch_set_schedule(self.h, int(chain_ctas_per_case), int(plain_bricks_per_cta)), self.h)
+    def set_schedule(self, chain_ctas_per_case: int, plain_blocks_per_cta: int) -> None:
+        self._ok(self.L.lbm_batch_set_schedule(self.h, int(chain_ctas_per_case), int(plain_blocks_per_cta)), self.h)
 
     def tune(self, trial_steps: int = 5):
         g, k, ms = C.c_int(), C.c_int(), C.c_double()

@@ -272,6 +272,53 @@ def test_three_steps_moving_geometry(pkg, oracle_mod, W, storage):
     assert refilled > 20
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_static_geometry_skips_flag_pass(pkg, oracle_mod, W, storage):
+    """All particles fixed: from the fourth step on the flag pass is left out
+    (the flags cannot change), and five steps still agree with the oracle,
+    which classifies every step.  Setting the particles again (moved, still
+    fixed) brings the pass back: the moved geometry's flags, refilled nodes
+    and populations agree after two more steps.  Tolerances: those of one
+    step, times the number of steps."""
+    wl = H.with_margin(oracle_mod, wl_touching(W))
+    gpu = H.make_gpu(pkg, wl, storage=storage)
+    orc = H.make_oracle(oracle_mod, wl)
+    gpu.set_particles(H.gpu_particles(pkg, wl))
+    orc.set_particles(H.oracle_particles(oracle_mod, wl))
+    _sync_populations(gpu, orc, np.random.default_rng(4))
+    k_full = gpu.kernels_per_step()
+    for _ in range(5):
+        gpu.step(1)
+        orc.step(1)
+    assert gpu.kernels_per_step() == k_full - 1
+    own = orc.owner()
+    assert np.array_equal(gpu.flags().cpu().numpy() - 1, own)
+    err = np.abs(gpu.populations().cpu().numpy() - orc.populations())[:, own < 0].max()
+    assert err <= 5 * POP_TOL[storage], err
+    Fg, _ = gpu.forces()
+    Fo, _ = orc.forces()
+    nl = orc.counters()["nlinks"]
+    ftol = (1e-11 * nl * 0.2 if storage == "f64" else POP_TOL[storage] * nl + 1e-5 * np.abs(Fo).max())
+    assert np.abs(Fg - Fo).max() <= 5 * ftol, (Fg, Fo)
+    # move the first particle (still fixed): the flags must follow
+    wl["particles"][0]["x"] = wl["particles"][0]["x"] + np.array([0.6, -0.4, 0.3])
+    wl = H.with_margin(oracle_mod, wl)
+    gpu.set_particles(H.gpu_particles(pkg, wl))
+    orc.set_particles(H.oracle_particles(oracle_mod, wl))
+    assert gpu.kernels_per_step() == k_full
+    refilled = 0
+    for _ in range(2):
+        gpu.step(1)
+        orc.step(1)
+        assert gpu.counters()["nrefill"] == orc.counters()["nrefill"]
+        refilled += orc.counters()["nrefill"]
+    assert refilled > 5
+    own = orc.owner()
+    assert np.array_equal(gpu.flags().cpu().numpy() - 1, own)
+    err = np.abs(gpu.populations().cpu().numpy() - orc.populations())[:, own < 0].max()
+    assert err <= 7 * POP_TOL[storage], err
+
+
 def test_settling_sphere_trajectory_fp64(pkg, oracle_mod, W):
     """Workload 1 (sphere of §3.1 geometry, FP64), 12 steps with 100 DEM
     sub-steps each: particle state, force and populations agree."""
