@@ -45,7 +45,7 @@ BRICK_NODES = 32 * 4 * 2
 SWEEP_SOURCES = ["k_plain.cuh", "lbm_internal.cuh"]
 
 
-WORKLOADS = ("settling_metaball", "empty_box", "settling_sphere", "multi_particle", "batched_drag")
+WORKLOADS = ("settling_metaball", "empty_box", "settling_sphere", "multi_particle", "batched_drag", "drag_gradient")
 
 
 def workload(name: str = "settling_metaball", storage: str | None = None):
@@ -72,7 +72,22 @@ def _workload(name: str):
         return workloads.multi_particle()
     if name == "batched_drag":  # the reference arm times its first case
         return workloads.batched_drag(64)[0]
+    if name == "drag_gradient":  # the forward run of the gradient workload, as a lattice
+        return gradient_lattice(workloads.adjoint_case())
     raise ValueError(name)
+
+
+def gradient_lattice(case):
+    """The drag-gradient case as a lattice workload: its fixed particle in the
+    periodic box, started from the uniform flow u0 (the forward run)."""
+    import numpy as np
+    x = np.asarray(case["x"], dtype=np.float64)
+    part = dict(cp=np.asarray(case["cp_world"]) - x, K=np.asarray(case["K"]), x=x, Rs=0.0, density=1.0,
+                q=np.array([1.0, 0.0, 0.0, 0.0]), v=np.zeros(3), w=np.zeros(3), fixed=1, mass=1.0, inertia=np.eye(3))
+    name = f"drag_gradient_{len(case['K'])}cp_{case['nx']}^3"
+    return dict(name=name, nx=case["nx"], ny=case["ny"], nz=case["nz"], periodic=(1, 1, 1), tau=case["tau"],
+                storage="f32", n_sub=0, gravity=(0.0, 0.0, 0.0), force=tuple(case["force"]), u0=tuple(case["u0"]),
+                kn=0.0, eta_n=0.0, kt=0.0, eta_t=0.0, mu_s=0.0, c_tol=1e-6, particles=[part])
 
 
 def measured_peak_gbs():
@@ -216,7 +231,8 @@ def oracle_sample(wl, steps: int):
     import oracle
     o = oracle.Oracle(wl["nx"], wl["ny"], wl["nz"], Q=19, periodic=tuple(wl["periodic"]), tau=wl["tau"],
                       n_sub=wl["n_sub"], gravity=wl["gravity"], force=wl["force"], kn=wl["kn"], eta_n=wl["eta_n"],
-                      kt=wl["kt"], eta_t=wl["eta_t"], mu_s=wl["mu_s"], c_tol=wl["c_tol"])
+                      kt=wl["kt"], eta_t=wl["eta_t"], mu_s=wl["mu_s"], c_tol=wl["c_tol"],
+                      u0=tuple(wl.get("u0", (0.0, 0.0, 0.0))))
     o.set_particles([oracle.make_particle(p["cp"], p["K"], p["x"], q=p["q"], v=p["v"], w=p["w"], Rs=p["Rs"],
                                           density=p["density"], fixed=p["fixed"]) for p in wl["particles"]])
     o.step(1)  # first step pays the page-in of the arrays
@@ -471,6 +487,17 @@ def run_batch(args):
     peak, peak_kind = measured_peak_gbs()
     alg = 2 * 19 * BYTES_PER_VALUE[storage] * nodes
     achieved = alg / (ms / args.steps * 1e-3) / 1e9
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        c0 = dict(cases[0])
+        c0["n_sub"] = 0
+        cpu_steps = max(1, args.cpu_steps // 2)
+        mlups, dt = oracle_sample(c0, cpu_steps)
+        cpu = {"value": round(mlups, 4), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+               "sample": f"{cpu_steps} steps of case 0 ({c0['nx']}x{c0['ny']}x{c0['nz']}), FP64, {dt:.1f} s; "
+                         f"the oracle steps the cases one after another"}
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
@@ -487,7 +514,122 @@ def run_batch(args):
             # binning, plain and near sweeps: the flag pass runs only in the
             # first three steps after the particles were set (they are fixed)
             "gpu_launches": 3 * args.steps,
-            "clocks": clocks.summary(), "cpu_baseline": None}
+            "clocks": clocks.summary(), "cpu_baseline": cpu, "drag": drag_check(pkg, storage)}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+# gradient evaluations timed per run (each is a 500-step forward run plus its
+# adjoint, ~0.2 s): the requested step count is capped at this
+GRADIENT_MAX = 8
+
+
+def run_gradient(args):
+    """Workload 4: d(mean drag)/d(control points, weights) of one fixed
+    six-control-point metaball in a periodic 96^3 box, T = 500 steps, window
+    W = 100, through the library's hand-written adjoint (flags frozen, sqrt(T)
+    checkpoints).  A "step" here is one gradient evaluation (forward run and
+    backward run); value = lattice updates of the objective (N x T per
+    gradient) per second of forward plus backward time."""
+    import torch
+    import numpy as np
+
+    world, rank, local, dist = dist_setup()
+    torch.cuda.set_device(local)
+    import paper_2206_11634_gb300 as pkg
+    from paper_2206_11634_gb300 import build as lib_build, workloads
+    if rank == 0 or not os.path.exists(pkg.LIB_PATH):
+        lib_build.build()
+    barrier(dist)
+    from paper_2206_11634_gb300.adjoint import AdjointDrag
+    case = workloads.adjoint_case()
+    x = np.asarray(case["x"], dtype=np.float64)
+    part = pkg.make_particle(np.asarray(case["cp_world"]) - x, case["K"], x, q=(1.0, 0.0, 0.0, 0.0), fixed=1,
+                             mass=1.0, inertia=np.eye(3))
+    stream = torch.cuda.Stream()
+    eng = AdjointDrag(case["nx"], case["ny"], case["nz"], particle=part, T=case["T"], W=case["W"], tau=case["tau"],
+                      u0=case["u0"], force=case["force"], stream=stream)
+    nodes = case["nx"] * case["ny"] * case["nz"]
+    grads = max(1, min(args.steps, GRADIENT_MAX))
+    warm = max(1, min(args.warmup, 2))
+    cp, K = case["cp_world"], case["K"]
+    for _ in range(warm):
+        eng.forward_np(cp, K)
+        eng.backward_np()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ms_f = ms_b = 0.0
+    with ClockSampler(local) as clocks:
+        barrier(dist)
+        torch.cuda.synchronize()
+        for _ in range(grads):
+            ev[0].record(stream)
+            eng.forward_np(cp, K)
+            ev[1].record(stream)
+            g_cp, g_K = eng.backward_np()
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            ms_f += ev[0].elapsed_time(ev[1])
+            ms_b += ev[1].elapsed_time(ev[2])
+        barrier(dist)
+    ms = max_over_ranks(dist, ms_f + ms_b)
+    T = case["T"]
+    value = world * nodes * T * grads / (ms * 1e-3) / 1e6
+    # end to end: the autograd function from host tensors to host gradients
+    e2e_grads = max(1, grads // 2)
+    cpt = torch.tensor(cp, dtype=torch.float64, requires_grad=True)
+    Kt = torch.tensor(K, dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_grads):
+        cpt.grad = None
+        Kt.grad = None
+        J = eng(cpt, Kt)
+        J.backward()
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
+    e2e_value = world * nodes * T * e2e_grads / e2e_s / 1e6
+    ncp = len(K)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    # the forward step kernel: 19 loads and 19 stores of FP32 per node and step
+    peak, peak_kind = measured_peak_gbs()
+    step_s = ms_f / grads / T * 1e-3
+    alg = 2 * 19 * 4 * nodes
+    achieved = alg / step_s / 1e9
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cpu_steps = max(1, args.cpu_steps // 2)
+        mlups, dt = oracle_sample(gradient_lattice(case), cpu_steps)
+        cpu = {"value": round(mlups, 4), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+               "sample": f"{cpu_steps} forward steps of the {case['nx']}^3 case, FP64, {dt:.1f} s (the oracle has "
+                         f"no adjoint: its gradient by central differences takes {2 * 4 * ncp} such runs)"}
+    info = eng.info()
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": grads,
+            "warmup": warm, "ms_per_step": round(ms / grads, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"drag_gradient_{ncp}cp_{case['nx']}^3", "lattice": "D3Q19", "storage": "f32",
+                       "T": T, "W": case["W"], "tau": case["tau"], "links": info["nlinks"],
+                       "checkpoint_every": info["checkpoint_every"], "step": "one gradient (forward + backward)",
+                       "forward_ms": round(ms_f / grads, 3), "backward_ms": round(ms_b / grads, 3),
+                       "l2": "no flush: two FP32 population arrays of 67 MB each, about the 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": 32 * ncp,
+                    "d2h_bytes_per_step": 8 + 32 * ncp, "steps": e2e_grads},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": f"{peak_kind} copy",
+                         "kernel": "forward step (k_adj_step)", "bytes_per_launch": alg,
+                         "avg_launch_us": round(step_s * 1e6, 3)},
+            "gradient": {"dJ_dK": [float(f"{v:.6e}") for v in g_K]},
+            # per gradient: q and the initial state, T forward steps; T - C
+            # recomputed steps (C checkpoints), three adjoint kernels per step
+            # and the chain rule to the shape
+            "gpu_launches": grads * (2 + T + (T - -(-T // info["checkpoint_every"])) + 3 * T + 1),
+            "clocks": clocks.summary(), "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -511,6 +653,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched_drag":
         return run_batch(args)
+    if args.workload == "drag_gradient":
+        return run_gradient(args)
     return run_gpu(args)
 
 

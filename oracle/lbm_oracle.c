@@ -413,7 +413,7 @@ static double link_q(const orc_state *s, int j, const double xf[3], const double
 
 /* ------------------------------------------------------------------------- */
 /* Local refilling of new fluid nodes, §2.3.3 (Eq. (30)).                     */
-/* Reading: a population f_i' at x_new is "known after streaming" when it
+/* Reading: a population f_i' at x_new counts as known (Eq. (30)) when it
  * streams in from x_new + e_i and that node was fluid before the particle
  * moved; then f_i(x_new) = f_i'(x_new) + 6 w_i' rho_f e_i.u_w with u_w the
  * surface velocity at x_new of the particle that uncovered it and rho_f =

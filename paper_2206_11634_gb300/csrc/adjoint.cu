@@ -142,8 +142,9 @@ __device__ __forceinline__ T geq_t(int ex, int ey, int ez, float w, T drho, T rh
 template <typename T>
 __device__ __forceinline__ T vibb_t(const AdjConst &A, int io, T q, T drf, T mfx, T mfy, T mfz, T gf, T drff, T mffx,
                                     T mffy, T mffz, T gff) {
-    const int dx = L19::e(io, 0), dy = L19::e(io, 1), dz = L19::e(io, 2);
-    const float w = (float)L19::w(io);
+    // io is a run-time index: packed lattice entries, no table in local memory
+    const int dx = lat_e<19>(io, 0), dy = lat_e<19>(io, 1), dz = lat_e<19>(io, 2);
+    const float w = (float)lat_w<19>(io);
     const T rf = drf + A.rho0, rff = drff + A.rho0;
     const T irf = 1.0f / rf, irff = 1.0f / rff;
     const T ufx = (mfx - 0.5f * A.F[0]) * irf, ufy = (mfy - 0.5f * A.F[1]) * irf, ufz = (mfz - 0.5f * A.F[2]) * irf;
@@ -213,51 +214,59 @@ struct AdjDev {
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// The pulled values g_in of fluid node (x, y, z) from the state S; also the
-// node's own populations and its link values when it has links.
-__device__ __forceinline__ void gather(const AdjDev &D, const float *__restrict__ S, int x, int y, int z, long long n,
-                                       uint32_t lm, float gin[Q], float gown[Q], float &drho_f, float mf[3]) {
+// The value a particle link of direction i (the unknown, arriving from the
+// solid node x - e_i) takes at fluid node n: VIBB of Eqs. (19)-(25) from the
+// node's moments (drho_f, m_f) and x_ff's populations, or halfway
+// bounce-back when x_ff is solid.  i is a run-time index: populations are
+// read from the state by address, never from an indexed local array.
+__device__ __noinline__ float link_value(const AdjDev &D, const float *__restrict__ S, long long n, int i,
+                                         float drho_f, float mfx, float mfy, float mfz) {
     const AdjConst &A = D.c;
     const long long N = A.N;
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        if ((lm >> i) & 1u) continue;
-        const int sx = wrapi(x - L19::e(i, 0), A.nx), sy = wrapi(y - L19::e(i, 1), A.ny), sz = wrapi(z - L19::e(i, 2), A.nz);
-        gin[i] = S[(long long)i * N + sx + (long long)A.nx * (sy + (long long)A.ny * sz)];
-    }
-    if (!lm) return;
-    drho_f = 0.f;
-    mf[0] = mf[1] = mf[2] = 0.f;
+    const int io = L19::opp(i);
+    const float gown_io = S[(long long)io * N + n];
+    const int L = D.linkid[(long long)i * N + n];
+    const int nff = D.l_nff[L];
+    if (nff < 0) return gown_io;  // halfway bounce-back, u_w = 0
+    float drff = 0.f, mff[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < Q; k++) {
-        gown[k] = S[(long long)k * N + n];
-        drho_f += gown[k];
-        mf[0] += gown[k] * L19::e(k, 0);
-        mf[1] += gown[k] * L19::e(k, 1);
-        mf[2] += gown[k] * L19::e(k, 2);
+        const float gk = S[(long long)k * N + nff];
+        drff += gk;
+        mff[0] += gk * L19::e(k, 0);
+        mff[1] += gk * L19::e(k, 1);
+        mff[2] += gk * L19::e(k, 2);
     }
-    uint32_t m = lm;
-    while (m) {
-        const int i = __ffs(m) - 1;
-        m &= m - 1;
-        const int io = L19::opp(i);
-        const int L = D.linkid[(long long)i * N + n];
-        const int nff = D.l_nff[L];
-        if (nff < 0) {
-            gin[i] = gown[io];  // halfway bounce-back, u_w = 0
-        } else {
-            float drff = 0.f, mff[3] = {0.f, 0.f, 0.f}, gff_io = 0.f;
+    const float gff_io = S[(long long)io * N + nff];
+    return vibb_t<float>(A, io, D.l_q[L], drho_f, mfx, mfy, mfz, gown_io, drff, mff[0], mff[1], mff[2], gff_io);
+}
+
+// The pulled values g_in of fluid node (x, y, z) from the state S, with the
+// link values substituted on its particle links (lm).  Every array here is
+// indexed by unrolled loop counters only, so it stays in registers.
+__device__ __forceinline__ void gather(const AdjDev &D, const float *__restrict__ S, int x, int y, int z, long long n,
+                                       uint32_t lm, float gin[Q]) {
+    const AdjConst &A = D.c;
+    const long long N = A.N;
+    float drho_f = 0.f, mf[3] = {0.f, 0.f, 0.f};
+    if (lm) {
 #pragma unroll
-            for (int k = 0; k < Q; k++) {
-                const float gk = S[(long long)k * N + nff];
-                drff += gk;
-                mff[0] += gk * L19::e(k, 0);
-                mff[1] += gk * L19::e(k, 1);
-                mff[2] += gk * L19::e(k, 2);
-                if (k == io) gff_io = gk;
-            }
-            gin[i] = vibb_t<float>(A, io, D.l_q[L], drho_f, mf[0], mf[1], mf[2], gown[io], drff, mff[0], mff[1],
-                                   mff[2], gff_io);
+        for (int k = 0; k < Q; k++) {
+            const float g = S[(long long)k * N + n];
+            drho_f += g;
+            mf[0] += g * L19::e(k, 0);
+            mf[1] += g * L19::e(k, 1);
+            mf[2] += g * L19::e(k, 2);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        if ((lm >> i) & 1u) {
+            gin[i] = link_value(D, S, n, i, drho_f, mf[0], mf[1], mf[2]);
+        } else {
+            const int sx = wrapi(x - L19::e(i, 0), A.nx), sy = wrapi(y - L19::e(i, 1), A.ny),
+                      sz = wrapi(z - L19::e(i, 2), A.nz);
+            gin[i] = S[(long long)i * N + sx + (long long)A.nx * (sy + (long long)A.ny * sz)];
         }
     }
 }
@@ -288,7 +297,7 @@ __global__ void k_adj_q(AdjDev D) {
         const int io = L19::opp(D.l_dir[L]);
         const int x = (int)(n % A.nx), y = (int)((n / A.nx) % A.ny), z = (int)(n / ((long long)A.nx * A.ny));
         const double pf[3] = {(double)x, (double)y, (double)z};
-        const double ps[3] = {pf[0] + L19::e(io, 0), pf[1] + L19::e(io, 1), pf[2] + L19::e(io, 2)};
+        const double ps[3] = {pf[0] + lat_e<19>(io, 0), pf[1] + lat_e<19>(io, 1), pf[2] + lat_e<19>(io, 2)};
         const int dims[3] = {A.nx, A.ny, A.nz};
         double Mf = 0.0, Ms = 0.0;
         for (int c = 0; c < D.ncp; c++) {
@@ -324,15 +333,15 @@ __global__ void __launch_bounds__(256) k_adj_step(AdjDev D, const float *__restr
     float Fx = 0.f;
     if (act) {
         const uint32_t lm = D.lmask[n];
-        float gin[Q], gown[Q], drho_f = 0.f, mf[3];
-        gather(D, S, x, y, z, n, lm, gin, gown, drho_f, mf);
-        if (window) {
-            uint32_t m = lm;
-            while (m) {
-                const int i = __ffs(m) - 1;
-                m &= m - 1;
+        float gin[Q];
+        gather(D, S, x, y, z, n, lm, gin);
+        if (window && lm) {
+#pragma unroll
+            for (int i = 1; i < Q; i++) {
+                if (!((lm >> i) & 1u)) continue;
                 const int io = L19::opp(i);
-                Fx += (float)L19::e(io, 0) * (gown[io] + gin[i]);  // Eq. (28), x, offsets
+                // Eq. (28), x component, offsets
+                Fx += (float)L19::e(io, 0) * (S[(long long)io * A.N + n] + gin[i]);
             }
         }
         float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
@@ -356,15 +365,15 @@ __global__ void __launch_bounds__(256) k_adj_step(AdjDev D, const float *__restr
 
 // A1: lambda_in from lambda' = dJ/dg+(t+1) through the collision, plus the
 // drag's dependence on the pulled link values.
-__global__ void __launch_bounds__(256) k_adj_bgk(AdjDev D, const float *__restrict__ S, const float *__restrict__ lamN,
+__global__ void __launch_bounds__(256, 3) k_adj_bgk(AdjDev D, const float *__restrict__ S, const float *__restrict__ lamN,
                                                   float *__restrict__ lamIn, int window) {
     const AdjConst &A = D.c;
     int x, y, z;
     long long n;
     if (!node_of(A, x, y, z, n) || D.solid[n]) return;
     const uint32_t lm = D.lmask[n];
-    float gin[Q], gown[Q], drho_f = 0.f, mf[3];
-    gather(D, S, x, y, z, n, lm, gin, gown, drho_f, mf);
+    float gin[Q];
+    gather(D, S, x, y, z, n, lm, gin);
     float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -407,14 +416,16 @@ __global__ void __launch_bounds__(256) k_adj_pull(AdjDev D, const float *__restr
         const long long t = tx + (long long)A.nx * (ty + (long long)A.ny * tz);
         acc[k] = D.solid[t] ? 0.f : lamIn[(long long)k * A.N + t];
     }
-    uint32_t m = D.lmask[n];
-    while (m) {
-        const int i = __ffs(m) - 1;
-        m &= m - 1;
-        const int io = L19::opp(i);
-        const int L = D.linkid[(long long)i * A.N + n];
-        if (D.l_nff[L] < 0) acc[io] += lamIn[(long long)i * A.N + n];
-        if (window) acc[io] += D.inv_W * (float)L19::e(io, 0);
+    const uint32_t lm = D.lmask[n];
+    if (lm) {
+#pragma unroll
+        for (int io = 1; io < Q; io++) {
+            const int i = L19::opp(io);  // the link's unknown direction
+            if (!((lm >> i) & 1u)) continue;
+            const int L = D.linkid[(long long)i * A.N + n];
+            if (D.l_nff[L] < 0) acc[io] += lamIn[(long long)i * A.N + n];
+            if (window) acc[io] += D.inv_W * (float)L19::e(io, 0);
+        }
     }
 #pragma unroll
     for (int k = 0; k < Q; k++) lamT[(long long)k * A.N + n] = acc[k];
@@ -477,7 +488,7 @@ __global__ void __launch_bounds__(256) k_adj_grad(AdjDev D) {
         const long long n = D.l_nf[L];
         const int io = L19::opp(D.l_dir[L]);
         const double pf[3] = {(double)(n % A.nx), (double)((n / A.nx) % A.ny), (double)(n / ((long long)A.nx * A.ny))};
-        const double ps[3] = {pf[0] + L19::e(io, 0), pf[1] + L19::e(io, 1), pf[2] + L19::e(io, 2)};
+        const double ps[3] = {pf[0] + lat_e<19>(io, 0), pf[1] + lat_e<19>(io, 1), pf[2] + lat_e<19>(io, 2)};
         for (int c = 0; c < D.ncp; c++) {
             double rf[3], rs[3], rf2 = 0.0, rs2 = 0.0;
             for (int a = 0; a < 3; a++) {

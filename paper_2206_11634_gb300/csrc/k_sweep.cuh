@@ -333,68 +333,45 @@ __device__ __forceinline__ typename Codec<S>::C particle_link(const Params &P, c
 // is seen by Eq. (28) when y is a fluid node and x_s is owned by j; every
 // other crossing link (y covered by another particle or beyond a wall, or
 // x_s inside j but owned by another particle) is a missing force point and
-// gets Eqs. (31)-(32) with f^eq(rho0, u_w).
+// gets Eqs. (31)-(32) with f^eq(rho0, u_w).  The caller passes the candidate
+// directions of listed particle s (those whose neighbour y = x - d is not a
+// fluid node of j's or j's own node): this evaluates them.
 template <typename S, int Q>
-__device__ __noinline__ int solid_node(const Params &P, const SmemParticles &sp, int x, int y, int z, int lx, int ly,
-                                       int lz, int bx0, int by0, int bz0, int owner,
-                                       ForceSink<typename Codec<S>::C> sink) {
-    using L = Lat<Q>;
+__device__ __noinline__ int solid_links(const Params &P, const SmemParticles &sp, int s, bool owner, uint32_t cand,
+                                        int lx, int ly, int lz, int bx0, int by0, int bz0,
+                                        ForceSink<typename Codec<S>::C> sink) {
     using C = typename Codec<S>::C;
     const C rho0 = Prm<C>::rho0(P);
-    // neighbour flags, fetched together (kWall beyond a wall)
-    constexpr uint32_t kWall = 0xFFFFFFFFu;
-    uint32_t nf[Q];
-#pragma unroll
-    for (int i = 1; i < Q; i++) {
-        int yx = x - L::e(i, 0), yy = y - L::e(i, 1), yz = z - L::e(i, 2);
-        bool in = true;
-        if (yx < 0 || yx >= P.nx) { if (P.per[0]) yx = (yx + P.nx) % P.nx; else in = false; }
-        if (yy < 0 || yy >= P.ny) { if (P.per[1]) yy = (yy + P.ny) % P.ny; else in = false; }
-        if (yz < 0 || yz >= P.nz) { if (P.per[2]) yz = (yz + P.nz) % P.nz; else in = false; }
-        nf[i] = in ? (uint32_t)P.flag_new[yx + P.nx * (yy + P.ny * yz)] : kWall;
-    }
     int terms = 0;
-    for (int s = 0; s < sp.n; s++) {
-        const int j = sp.id[s];
-        // a node whose neighbours all belong to j, or are fluid with j the
-        // owner, has no missing force point of j
-        uint32_t cand = 0;
-#pragma unroll
-        for (int i = 1; i < Q; i++) {
-            const bool seen = (nf[i] == 0 && j == owner) || nf[i] == (uint32_t)(j + 1);
-            if (!seen) cand |= 1u << i;
-        }
-        if (!cand) continue;
-        C Ms;
-        if (j == owner) {
-            Ms = m_value<C>(P, sp, s, lx, ly, lz, bx0, by0, bz0);
-        } else if (!inside_exact<C>(P, sp, s, lx, ly, lz, bx0, by0, bz0, Ms)) {
-            continue;
-        }
-        while (cand) {
-            const int i = __ffs(cand) - 1;
-            cand &= cand - 1;
-            const int dx = lat_e<Q>(i, 0), dy = lat_e<Q>(i, 1), dz = lat_e<Q>(i, 2);
-            C My;
-            if (inside_exact<C>(P, sp, s, lx - dx, ly - dy, lz - dz, bx0, by0, bz0, My)) continue;
-            C q = (c0_of<C>(P) - My) / (Ms - My);
-            q = q < C(0) ? C(0) : (q > C(1) ? C(1) : q);
-            if (P.q_exact) q = q_root<C>(P, sp, s, lx - dx, ly - dy, lz - dz, dx, dy, dz, bx0, by0, bz0, q);
-            C r[3], uw[3];
-            lever<C>(P, sp, s, bx0, by0, bz0, (C)(lx - dx) + q * dx, (C)(ly - dy) + q * dy, (C)(lz - dz) + q * dz, r);
-            particle_velocity<C>(P, sp, s, r, uw);
-            const C w = (C)lat_w<Q>(i);
-            // Eqs. (31)-(32) in offsets; the constant 2 d w rho0 cancels
-            // with those of the other crossing links (see particle_link)
-            const C fi = geq_i<C>(dx, dy, dz, w, C(0), rho0, uw[0], uw[1], uw[2]);
-            const C fo = geq_i<C>(-dx, -dy, -dz, w, C(0), rho0, uw[0], uw[1], uw[2]);
-            C dP[3];
-            dP[0] = (C(dx) - uw[0]) * fi + (C(dx) + uw[0]) * fo;
-            dP[1] = (C(dy) - uw[1]) * fi + (C(dy) + uw[1]) * fo;
-            dP[2] = (C(dz) - uw[2]) * fi + (C(dz) + uw[2]) * fo;
-            add_term<C>(sink, s, dP, r);
-            terms++;
-        }
+    C Ms;
+    if (owner) {
+        Ms = m_value<C>(P, sp, s, lx, ly, lz, bx0, by0, bz0);
+    } else if (!inside_exact<C>(P, sp, s, lx, ly, lz, bx0, by0, bz0, Ms)) {
+        return 0;
+    }
+    while (cand) {
+        const int i = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const int dx = lat_e<Q>(i, 0), dy = lat_e<Q>(i, 1), dz = lat_e<Q>(i, 2);
+        C My;
+        if (inside_exact<C>(P, sp, s, lx - dx, ly - dy, lz - dz, bx0, by0, bz0, My)) continue;
+        C q = (c0_of<C>(P) - My) / (Ms - My);
+        q = q < C(0) ? C(0) : (q > C(1) ? C(1) : q);
+        if (P.q_exact) q = q_root<C>(P, sp, s, lx - dx, ly - dy, lz - dz, dx, dy, dz, bx0, by0, bz0, q);
+        C r[3], uw[3];
+        lever<C>(P, sp, s, bx0, by0, bz0, (C)(lx - dx) + q * dx, (C)(ly - dy) + q * dy, (C)(lz - dz) + q * dz, r);
+        particle_velocity<C>(P, sp, s, r, uw);
+        const C w = (C)lat_w<Q>(i);
+        // Eqs. (31)-(32) in offsets; the constant 2 d w rho0 cancels
+        // with those of the other crossing links (see particle_link)
+        const C fi = geq_i<C>(dx, dy, dz, w, C(0), rho0, uw[0], uw[1], uw[2]);
+        const C fo = geq_i<C>(-dx, -dy, -dz, w, C(0), rho0, uw[0], uw[1], uw[2]);
+        C dP[3];
+        dP[0] = (C(dx) - uw[0]) * fi + (C(dx) + uw[0]) * fo;
+        dP[1] = (C(dy) - uw[1]) * fi + (C(dy) + uw[1]) * fo;
+        dP[2] = (C(dz) - uw[2]) * fi + (C(dz) + uw[2]) * fo;
+        add_term<C>(sink, s, dP, r);
+        terms++;
     }
     return terms;
 }
@@ -542,27 +519,55 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
     }
     int nlinks = 0;
 
-    const uint16_t fl = active ? P.flag_new[n] : (uint16_t)1;
-    const bool fluid = active && fl == 0;
-    int nterms = 0;  // missing-force-point terms this thread added
-    if (active && fl != 0 && P.missing_force)
-        nterms = solid_node<S, Q>(P, sp, x, y, z, lx, ly, lz, bx0, by0, bz0, fl - 1, sink);
-
+    // the node's flag and its neighbours' (y = x - e_i; kWall beyond a wall),
+    // read in one round by fluid and solid nodes alike and issued before the
+    // brick's particles are loaded, so the two latencies overlap
+    constexpr uint32_t kWall = 0xFFFFFFFFu;
+    uint32_t nf[Q];
     C fin[Q];
-    uint32_t links = 0;
-    if (fluid) {
+    {
         int xs[3], ys[3], zs[3];
         neighbour_coords(P, x, y, z, xs, ys, zs);
+        nf[0] = active ? (uint32_t)P.flag_new[n] : 1u;
 #pragma unroll
-        for (int i = 0; i < Q; i++) {
+        for (int i = 1; i < Q; i++) {
             const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
             const bool wall = (sx | sy | sz) < 0;
-            const int src = wall ? n : sx + P.nx * (sy + P.ny * sz);
-            if (!wall && P.flag_new[src] != 0) links |= 1u << i;
-            if (sizeof(C) == 8) {
-                const S *ptr = wall ? A + (long long)L::opp(i) * N + n : A + (long long)i * N + src;
+            nf[i] = (!active || wall) ? kWall : (uint32_t)P.flag_new[sx + P.nx * (sy + P.ny * sz)];
+        }
+        if (sizeof(C) == 8 && active) {  // FP64: the pulls in the same round
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
+                const bool wall = (sx | sy | sz) < 0;
+                const S *ptr = wall ? A + (long long)L::opp(i) * N + n
+                                    : A + (long long)i * N + (sx + P.nx * (sy + P.ny * sz));
                 fin[i] = Cd::ld(ptr, (C)L::w(i), rho0);
             }
+        }
+    }
+    load_smem_particles(P, sp, b, bx0, by0, bz0);
+    const bool fluid = active && nf[0] == 0;
+    uint32_t links = 0;
+    if (fluid) {
+#pragma unroll
+        for (int i = 1; i < Q; i++)
+            if (nf[i] != 0 && nf[i] != kWall) links |= 1u << i;
+    }
+    int nterms = 0;  // missing-force-point terms this thread added
+    if (active && !fluid && P.missing_force) {
+        // per listed particle j, the directions whose neighbour is neither a
+        // fluid node next to j's own node nor a node of j
+        const int owner = (int)nf[0] - 1;
+        for (int s = 0; s < sp.n; s++) {
+            const int j = sp.id[s];
+            uint32_t cand = 0;
+#pragma unroll
+            for (int i = 1; i < Q; i++) {
+                const bool seen = (nf[i] == 0 && j == owner) || nf[i] == (uint32_t)(j + 1);
+                if (!seen) cand |= 1u << i;
+            }
+            if (cand) nterms += solid_links<S, Q>(P, sp, s, j == owner, cand, lx, ly, lz, bx0, by0, bz0, sink);
         }
     }
     if (sizeof(C) == 8) {
@@ -707,7 +712,6 @@ __device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, do
             continue;
         }
         if (tid == 0) s_links = 0;
-        load_smem_particles(P, sp, b, bx0, by0, bz0);
         near_brick<S, Q, kForce>(P, sp, red, &s_links, &ls, b, bx0, by0, bz0, cnt);
     }
     if (tid == 0 && done) atomicAdd(&P.counters[CNT_NEAR], done);

@@ -4,7 +4,7 @@ invariants that do not come from the oracle itself.
 - flags: a one-control-point metaball is the sphere |x - c|^2 <= K (§2.1.2);
 - q: Eq. (27) stays in [0,1] (§2.3.1); Newton's root of Eq. (26) equals the
   closed-form line-sphere intersection; Eq. (27)'s error against it is
-  "around 5%" as §2.3.1 reports; with the exact-q option the sweep's node
+  about 5 %, the size §2.3.1 reports; with the exact-q option the sweep's node
   update equals the one rebuilt by hand from the closed-form root;
 - VIBB, Eqs. (19)-(25): in a linear velocity field at a resting wall the
   unknown equals the equilibrium of the field extended to the solid node
@@ -111,7 +111,7 @@ def test_q_linear_and_newton_against_sphere_root(oracle_mod):
         qn, it = o.q_newton(0, xf, d, tol, maxit)
         assert it > 0 and abs(qn - q_exact) < 1e-6
         rel.append(abs(ql - q_exact) / q_exact)
-    # §2.3.1: "the relative error is around 5%"; the median over every link
+    # §2.3.1 puts the relative error of Eq. (27) at about 5 %; the median over every link
     # of this sphere is 6.0%
     med = float(np.median(rel))
     assert 0.02 < med < 0.10
