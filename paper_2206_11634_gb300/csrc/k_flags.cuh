@@ -37,6 +37,11 @@ __device__ __forceinline__ C geq_i(int ex, int ey, int ez, C w, C drho, C rho, C
     return w * (drho + rho * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu));
 }
 
+// Per-brick solid marks written by the flag pass (brick_solid): bit 7 when
+// the brick holds a solid node, bits 0-5 when one lies on its low-x, high-x,
+// low-y, high-y, low-z or high-z face.
+constexpr uint32_t kSolidAny = 0x80u;
+
 template <typename S, int Q>
 __device__ __forceinline__ void flags_brick(const Params &P, SmemParticles &sp, int b) {
     using L = Lat<Q>;
@@ -57,16 +62,20 @@ __device__ __forceinline__ void flags_brick(const Params &P, SmemParticles &sp, 
         if (tid < cnt) P.blist[b * MAXPB + rank] = id;
         if (tid == 0) P.bcount[b] = cnt;
     }
+    __shared__ unsigned s_faces;
+    if (tid == 0) s_faces = 0u;
     __syncthreads();
     int bxi, byi, bzi;
     brick_coords(P, b, bxi, byi, bzi);
     const int bx0 = bxi * BX, by0 = byi * BY, bz0 = bzi * BZ;
-    if (cnt > 0) load_smem_particles(P, sp, b, bx0, by0, bz0);
-
     const int lx = tid % BX, ly = (tid / BX) % BY, lz = tid / (BX * BY);
     const int x = bx0 + lx, y = by0 + ly, z = bz0 + lz;
     const bool active = x < P.nx && y < P.ny && z < P.nz;
     const long long n = (long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z);
+    // the previous flag (the refill below needs it), issued with the
+    // particles' loads so that the two latencies overlap
+    const uint16_t old = active ? P.flag_old[n] : (uint16_t)0;
+    if (cnt > 0) load_smem_particles(P, sp, b, bx0, by0, bz0);
 
     int own = -1;
     if (active && cnt > 0) {
@@ -111,19 +120,34 @@ __device__ __forceinline__ void flags_brick(const Params &P, SmemParticles &sp, 
     }
     const uint16_t fl = own >= 0 ? (uint16_t)(own + 1) : (uint16_t)0;
     if (active) P.flag_new[n] = fl;
-    // whether the brick holds a solid node now (the near sweep takes the
-    // plain path for bricks with no solid node around them)
-    const int any_solid = __syncthreads_or(active && fl != 0);
-    if (threadIdx.x == 0 && P.brick_solid) P.brick_solid[b] = (uint8_t)(any_solid != 0);
+    // where the brick holds solid nodes now: bit 7 anywhere, bits 0-5 on its
+    // faces (low x, high x, low y, high y, low z, high z; a high face is the
+    // last node inside the box on a ragged edge).  The near sweep takes the
+    // plain path for a brick none of whose nodes has a solid neighbour.
+    {
+        uint32_t m = 0;
+        if (active && fl != 0) {
+            m = kSolidAny;
+            if (lx == 0) m |= 1u;
+            if (lx == BX - 1 || x == P.nx - 1) m |= 2u;
+            if (ly == 0) m |= 4u;
+            if (ly == BY - 1 || y == P.ny - 1) m |= 8u;
+            if (lz == 0) m |= 16u;
+            if (lz == BZ - 1 || z == P.nz - 1) m |= 32u;
+        }
+        m = __reduce_or_sync(0xffffffffu, m);
+        if ((tid & 31) == 0 && m) atomicOr(&s_faces, m);
+        __syncthreads();
+        if (tid == 0 && P.brick_solid) P.brick_solid[b] = (uint8_t)s_faces;
+    }
 
-    // Local refilling, §2.3.3.  Reading: f_i' at x_new is "known after
-    // streaming" when it streams in from x_new + e_i and that node was a fluid
+    // Local refilling, §2.3.3.  Reading: f_i' at x_new counts as known
+    // (Eq. (30)) when it streams in from x_new + e_i and that node was a fluid
     // node of the previous step; then f_i = f_i'(x_new+e_i) + 6 w_i rho0
     // e_i.u_w, else f_i = f^eq_i(rho0, u_new); u_w = u_new is the surface
     // velocity at x_new of the particle that uncovered it.  The values become
     // the node's post-collision populations.
     if (active && fl == 0) {
-        const uint16_t old = P.flag_old[n];
         if (old != 0) {
             const DevParticle &pj = P.parts[old - 1];
             double r[3] = {minimg_d(P, 0, (double)x - pj.x[0]), minimg_d(P, 1, (double)y - pj.x[1]),

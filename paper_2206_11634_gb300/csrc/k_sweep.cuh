@@ -690,10 +690,13 @@ __device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, do
         __syncthreads();  // the previous brick is done with the shared state
         if (cnt > 0 && P.brick_solid) {
             // particle links and missing force points need a solid node in
-            // the brick or next to it: look at the 27 bricks around
+            // the brick or a solid neighbour of one of its nodes: the brick's
+            // own mark, and for each of the 26 bricks around it the faces
+            // turned towards it (all of them, for an edge or corner brick)
             bool near_solid = false;
             if (tid < 27) {
-                int q[3] = {bxi + tid % 3 - 1, byi + (tid / 3) % 3 - 1, bzi + tid / 9 - 1};
+                const int o[3] = {tid % 3 - 1, (tid / 3) % 3 - 1, tid / 9 - 1};
+                int q[3] = {bxi + o[0], byi + o[1], bzi + o[2]};
                 const int nbs[3] = {P.nbx, P.nby, P.nbz};
                 bool in = true;
                 for (int a = 0; a < 3; a++) {
@@ -702,7 +705,10 @@ __device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, do
                         else in = false;
                     }
                 }
-                near_solid = in && P.brick_solid[q[0] + P.nbx * (q[1] + P.nby * q[2])] != 0;
+                const uint32_t m = in ? (uint32_t)P.brick_solid[q[0] + P.nbx * (q[1] + P.nby * q[2])] : 0u;
+                near_solid = (m & kSolidAny) != 0;
+                for (int a = 0; a < 3; a++)  // a brick below faces us with its high face, and so on
+                    if (o[a] != 0) near_solid = near_solid && (m & (1u << (2 * a + (o[a] < 0 ? 1 : 0)))) != 0;
             }
             if (!__syncthreads_or(near_solid)) cnt = 0;
         }
