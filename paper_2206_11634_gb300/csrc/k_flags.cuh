@@ -77,46 +77,39 @@ __device__ __forceinline__ void flags_brick(const Params &P, SmemParticles &sp, 
     const uint16_t old = active ? P.flag_old[n] : (uint16_t)0;
     if (cnt > 0) load_smem_particles(P, sp, b, bx0, by0, bz0);
 
+    // owner: the covering particle with the largest M, ties to the lower
+    // index (the list is ascending); with one cover its FP32 decision is
+    // enough, several covers compare their M in FP64.  Kept as running
+    // values, so no per-thread array is indexed at run time.
     int own = -1;
     if (active && cnt > 0) {
-        int ncand = 0;
-        int cand[MAXPB];
-        double m64[MAXPB];
-        float m32[MAXPB];
+        int own_s = -1;
+        double own_M = -1.0;  // FP64 M of the current owner, < 0 until computed
         for (int s = 0; s < cnt; s++) {
             bool unsure;
             const float M = metaball32(P, sp, s, (float)lx, (float)ly, (float)lz, unsure);
             bool inside;
-            double Md = (double)M;
+            double Md = -1.0;
             if (kF64 || unsure) {
                 Md = metaball64(P, P.parts[sp.id[s]], (double)x, (double)y, (double)z);
                 inside = Md >= P.c0;
             } else {
                 inside = M >= P.c0_f;
             }
-            if (inside) {
-                cand[ncand] = s;
-                m32[ncand] = M;
-                m64[ncand] = (kF64 || unsure) ? Md : -1.0;
-                ncand++;
+            if (!inside) continue;
+            if (own_s < 0) {
+                own_s = s;
+                own_M = Md;
+                continue;
+            }
+            if (own_M < 0.0) own_M = metaball64(P, P.parts[sp.id[own_s]], (double)x, (double)y, (double)z);
+            if (Md < 0.0) Md = metaball64(P, P.parts[sp.id[s]], (double)x, (double)y, (double)z);
+            if (Md > own_M) {
+                own_s = s;
+                own_M = Md;
             }
         }
-        if (ncand == 1) {
-            own = sp.id[cand[0]];
-        } else if (ncand > 1) {
-            // several particles cover the node: decide the largest M in FP64
-            double best = 0.0;
-            for (int c = 0; c < ncand; c++) {
-                const int s = cand[c];
-                double M = m64[c] >= 0.0 ? m64[c]
-                                         : metaball64(P, P.parts[sp.id[s]], (double)x, (double)y, (double)z);
-                (void)m32;
-                if (own < 0 || M > best) {
-                    own = sp.id[s];
-                    best = M;
-                }
-            }
-        }
+        if (own_s >= 0) own = sp.id[own_s];
     }
     const uint16_t fl = own >= 0 ? (uint16_t)(own + 1) : (uint16_t)0;
     if (active) P.flag_new[n] = fl;

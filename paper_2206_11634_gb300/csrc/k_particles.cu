@@ -22,7 +22,19 @@ __device__ void bin_particle(const Params &P, int j) {
     if (t < p.ncp) {
         double r[3];
         quat_rot(p.q, p.cpb[t], r);
-        for (int a = 0; a < 3; a++) p.cpw[t][a] = p.x[a] + r[a];
+        for (int a = 0; a < 3; a++) {
+            const double c = p.x[a] + r[a];
+            p.cpw[t][a] = c;
+            // the FP32 pair the sweeps form brick-relative positions from
+            const float hi = (float)c;
+            p.cpw_hl[t][a][0] = hi;
+            p.cpw_hl[t][a][1] = (float)(c - (double)hi);
+        }
+    } else if (t >= 32 && t < 35) {
+        const int a = t - 32;
+        const float hi = (float)p.x[a];
+        p.x_hl[a][0] = hi;
+        p.x_hl[a][1] = (float)(p.x[a] - (double)hi);
     }
     __syncthreads();
     if (t == 0) {

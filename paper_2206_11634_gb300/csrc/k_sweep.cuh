@@ -211,6 +211,50 @@ __device__ __forceinline__ void add_term(ForceSink<C> sink, int s, const C dP[3]
     }
 }
 
+// The second fluid node x_ff = x - d of a link (d = e_io, into the solid):
+// whether it is a fluid node inside the box, and, for VIBB, the density
+// offset, momentum and the io population of its post-collision state.  Its
+// flag and populations are fetched together (beyond a wall the address is
+// clamped to x itself, whose values are then not used).
+template <typename C>
+struct FFData {
+    C drho, m[3], g_io;
+    bool ok;
+};
+template <typename S, int Q>
+__device__ __forceinline__ FFData<typename Codec<S>::C> ff_fetch(const Params &P, int x, int y, int z, int io) {
+    using L = Lat<Q>;
+    using Cd = Codec<S>;
+    using C = typename Cd::C;
+    const int dx = lat_e<Q>(io, 0), dy = lat_e<Q>(io, 1), dz = lat_e<Q>(io, 2);
+    int fx = x - dx, fy = y - dy, fz = z - dz;
+    bool ff_in = true;
+    if (fx < 0 || fx >= P.nx) { if (P.per[0]) fx = (fx + P.nx) % P.nx; else ff_in = false; }
+    if (fy < 0 || fy >= P.ny) { if (P.per[1]) fy = (fy + P.ny) % P.ny; else ff_in = false; }
+    if (fz < 0 || fz >= P.nz) { if (P.per[2]) fz = (fz + P.nz) % P.nz; else ff_in = false; }
+    const int nff = ff_in ? fx + P.nx * (fy + P.ny * fz) : x + P.nx * (y + P.ny * z);
+    const uint16_t flag_ff = P.flag_new[nff];
+    FFData<C> f;
+    f.drho = 0;
+    f.m[0] = f.m[1] = f.m[2] = 0;
+    f.g_io = 0;
+    if (P.vibb) {
+        const S *A = (const S *)P.fA;
+        const C rho0 = Prm<C>::rho0(P);
+#pragma unroll
+        for (int k = 0; k < Q; k++) {
+            const C fk = Cd::ld(A + (long long)k * P.N + nff, (C)L::w(k), rho0);
+            f.drho += fk;
+            f.m[0] += fk * L::e(k, 0);
+            f.m[1] += fk * L::e(k, 1);
+            f.m[2] += fk * L::e(k, 2);
+            if (k == io) f.g_io = fk;
+        }
+    }
+    f.ok = ff_in && flag_ff == 0;
+    return f;
+}
+
 // The unknown population of one particle link (direction i arrives at x from
 // the solid node x + d, d = -e_i) and its momentum-exchange term, in offset
 // form: fown_io is the node's post-collision offset g = f - w rho0 along d,
@@ -224,7 +268,7 @@ __device__ __forceinline__ void add_term(ForceSink<C> sink, int s, const C dP[3]
 template <typename S, int Q>
 __device__ __forceinline__ typename Codec<S>::C particle_link(const Params &P, const SmemParticles &sp, int i, int x,
                                                              int y, int z, int lx, int ly, int lz, int bx0, int by0,
-                                                             int bz0, long long ns_solid,
+                                                             int bz0, int j, const FFData<typename Codec<S>::C> &ff,
                                                              typename Codec<S>::C fown_io,
                                                              typename Codec<S>::C drho_f,
                                                              const typename Codec<S>::C *u_f,
@@ -235,12 +279,9 @@ __device__ __forceinline__ typename Codec<S>::C particle_link(const Params &P, c
     using C = typename Cd::C;
     const int io = L::opp(i);
     const int dx = lat_e<Q>(io, 0), dy = lat_e<Q>(io, 1), dz = lat_e<Q>(io, 2);  // d, into the solid
-    const int j = (int)P.flag_new[ns_solid] - 1;
     const int s = slot_of(sp, j);
     const C w_io = (C)lat_w<Q>(io);
     const C rho0 = Prm<C>::rho0(P);
-    const S *A = (const S *)P.fA;
-    const long long N = P.N;
     if (s < 0) {  // cannot happen for a consistent brick list; bounce back plainly
         atomicOr(&P.status[ST_ERR], ERRB_BRICK_OVERFLOW);
         return fown_io;
@@ -260,30 +301,9 @@ __device__ __forceinline__ typename Codec<S>::C particle_link(const Params &P, c
     lever<C>(P, sp, s, bx0, by0, bz0, (C)lx + q * dx, (C)ly + q * dy, (C)lz + q * dz, r);
     particle_velocity<C>(P, sp, s, r, uw);
     const C eu_w = -(dx * uw[0] + dy * uw[1] + dz * uw[2]);  // e_i . u_w with e_i = -d
-    // second fluid node x_ff = x - d; its flag and populations are fetched
-    // together (the address is clamped to x itself beyond a wall, where the
-    // values are not used)
-    int fx = x - dx, fy = y - dy, fz = z - dz;
-    bool ff_in = true;
-    if (fx < 0 || fx >= P.nx) { if (P.per[0]) fx = (fx + P.nx) % P.nx; else ff_in = false; }
-    if (fy < 0 || fy >= P.ny) { if (P.per[1]) fy = (fy + P.ny) % P.ny; else ff_in = false; }
-    if (fz < 0 || fz >= P.nz) { if (P.per[2]) fz = (fz + P.nz) % P.nz; else ff_in = false; }
-    const int nff = ff_in ? fx + P.nx * (fy + P.ny * fz) : x + P.nx * (y + P.ny * z);
-    const uint16_t flag_ff = P.flag_new[nff];
     const C rho_f = rho0 + drho_f;
-    C drho_ff = 0, m_ff[3] = {0, 0, 0}, fff_io = 0;
-    if (P.vibb) {
-#pragma unroll
-        for (int k = 0; k < Q; k++) {
-            const C fk = Cd::ld(A + (long long)k * N + nff, (C)L::w(k), rho0);
-            drho_ff += fk;
-            m_ff[0] += fk * L::e(k, 0);
-            m_ff[1] += fk * L::e(k, 1);
-            m_ff[2] += fk * L::e(k, 2);
-            if (k == io) fff_io = fk;
-        }
-    }
-    const bool ff_ok = ff_in && flag_ff == 0;
+    const C drho_ff = ff.drho, m_ff[3] = {ff.m[0], ff.m[1], ff.m[2]}, fff_io = ff.g_io;
+    const bool ff_ok = ff.ok;
     C fin;
     if (!P.vibb || !ff_ok) {
         fin = fown_io + C(6) * w_io * rho_f * eu_w;
@@ -377,8 +397,9 @@ __device__ __noinline__ int solid_links(const Params &P, const SmemParticles &sp
 }
 
 // The unknown of one particle link, computed by any lane of the warp: the
-// node (brick-local lx,ly,lz) loads its own post-collision populations and
-// moments, then the link is evaluated as in particle_link.
+// node's (brick-local lx,ly,lz) own post-collision populations, the owner of
+// the solid node and x_ff's flag and populations are all fetched in one
+// round, then the link is evaluated as in particle_link.
 template <typename S, int Q>
 __device__ __noinline__ typename Codec<S>::C link_coop(const Params &P, const SmemParticles &sp, int i, int lx, int ly,
                                                       int lz, int bx0, int by0, int bz0,
@@ -391,9 +412,17 @@ __device__ __noinline__ typename Codec<S>::C link_coop(const Params &P, const Sm
     const S *A = (const S *)P.fA;
     const long long N = P.N;
     const C rho0 = Prm<C>::rho0(P);
+    // the solid source x - e_i (inside the domain: the link exists) and its
+    // owner; x_ff
+    int sx = x - lat_e<Q>(i, 0), sy = y - lat_e<Q>(i, 1), sz = z - lat_e<Q>(i, 2);
+    if (sx < 0) sx += P.nx; else if (sx >= P.nx) sx -= P.nx;
+    if (sy < 0) sy += P.ny; else if (sy >= P.ny) sy -= P.ny;
+    if (sz < 0) sz += P.nz; else if (sz >= P.nz) sz -= P.nz;
+    const int j = (int)P.flag_new[sx + P.nx * (sy + P.ny * sz)] - 1;
+    const int io = L::opp(i);
+    const FFData<C> ff = ff_fetch<S, Q>(P, x, y, z, io);
     // moments of the node's post-collision populations, and the one along
     // d = -e_i (picked in the unrolled loop, so nothing is indexed at run time)
-    const int io = L::opp(i);
     C fown_io = 0;
     C drho_f = 0, m_f[3] = {0, 0, 0};
 #pragma unroll
@@ -408,15 +437,10 @@ __device__ __noinline__ typename Codec<S>::C link_coop(const Params &P, const Sm
     C u_f[3];
     const C inv_rho_f = C(1) / (rho0 + drho_f);
     for (int a = 0; a < 3; a++) u_f[a] = (m_f[a] - C(0.5) * Prm<C>::F(P, a)) * inv_rho_f;
-    // the solid source x - e_i (inside the domain: the link exists)
-    int sx = x - lat_e<Q>(i, 0), sy = y - lat_e<Q>(i, 1), sz = z - lat_e<Q>(i, 2);
-    if (sx < 0) sx += P.nx; else if (sx >= P.nx) sx -= P.nx;
-    if (sy < 0) sy += P.ny; else if (sy >= P.ny) sy -= P.ny;
-    if (sz < 0) sz += P.nz; else if (sz >= P.nz) sz -= P.nz;
     C Mf_cache = 0;
     int Mf_slot = -1;
-    return particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, sx + P.nx * (sy + P.ny * sz), fown_io,
-                               drho_f, u_f, sink, &Mf_cache, &Mf_slot);
+    return particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, j, ff, fown_io, drho_f, u_f, sink,
+                               &Mf_cache, &Mf_slot);
 }
 
 // Shared scratch of the warp-cooperative link evaluation: per warp a queue of
@@ -481,8 +505,9 @@ __device__ __noinline__ void boundary_node(const Params &P, const SmemParticles 
     while (links) {
         const int i = __ffs(links) - 1;
         links &= links - 1;
-        fin[i] = particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, srcs[i], fown[L::opp(i)], drho_f,
-                                     u_f, sink, &Mf_cache, &Mf_slot);
+        const FFData<C> ff = ff_fetch<S, Q>(P, x, y, z, L::opp(i));
+        fin[i] = particle_link<S, Q>(P, sp, i, x, y, z, lx, ly, lz, bx0, by0, bz0, (int)P.flag_new[srcs[i]] - 1, ff,
+                                     fown[L::opp(i)], drho_f, u_f, sink, &Mf_cache, &Mf_slot);
         (*nlinks)++;
     }
     collide_store<S, Q, kForce>(P, fin, B, N, n);
@@ -546,7 +571,7 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
             }
         }
     }
-    load_smem_particles(P, sp, b, bx0, by0, bz0);
+    load_particle_records(P, sp, cnt, bx0, by0, bz0);  // ids staged by the caller
     const bool fluid = active && nf[0] == 0;
     uint32_t links = 0;
     if (fluid) {
@@ -688,6 +713,10 @@ __device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, do
         const int bx0 = bxi * BX, by0 = byi * BY, bz0 = bzi * BZ;
         int cnt = min(P.bcount[b], MAXPB);
         __syncthreads();  // the previous brick is done with the shared state
+        // the brick's particle ids, staged with the neighbourhood check below
+        // (made visible by its barrier)
+        if (tid >= 32 && tid < 32 + cnt) sp.id[tid - 32] = P.blist[b * MAXPB + (tid - 32)];
+        if (tid == 0) sp.n = cnt;
         if (cnt > 0 && P.brick_solid) {
             // particle links and missing force points need a solid node in
             // the brick or a solid neighbour of one of its nodes: the brick's
@@ -711,6 +740,8 @@ __device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, do
                     if (o[a] != 0) near_solid = near_solid && (m & (1u << (2 * a + (o[a] < 0 ? 1 : 0)))) != 0;
             }
             if (!__syncthreads_or(near_solid)) cnt = 0;
+        } else {
+            __syncthreads();
         }
         if (cnt == 0) {
             const int x = bx0 + tid % BX, y = by0 + (tid / BX) % BY, z = bz0 + tid / (BX * BY);

@@ -236,6 +236,10 @@ struct DevParticle {
     float inv_mass_f, Rs_f, brad_f, sumK_f;
     float sx[3][2], sv[3][2], sq[4][2];
     float swb[3][2];       // angular velocity, principal body frame
+    // cpw and x split into FP32 pairs (value = [0] + [1]) by the binning, so
+    // that brick-relative FP32 positions are formed without FP64 arithmetic
+    float cpw_hl[MAXCP][3][2];
+    float x_hl[3][2];
 };
 
 // Everything a kernel needs, passed by value.
@@ -458,7 +462,9 @@ struct SmemParticles {
 // closer than 1/2, where the rounding of its position dominates).
 //
 // Error budget: the control point's brick-relative position is rounded once
-// to FP32 (|error| <= 2^-24 times its magnitude, < 2^-16 for magnitudes
+// to FP32 (from the FP32 pair of its FP64 value, see df_minus_int: within a
+// 2^-24 fraction of an ulp of that; |error| <= 2^-24 times its magnitude
+// plus 2^-48 of it, < 2^-16 for magnitudes
 // below 256), each difference along an axis is exact or rounded once, the
 // square sum, the reciprocal and the product add 5 roundings; for distances
 // r >= 1/2 each term K/r^2 is off by at most 2^-13 relative, well inside the
@@ -484,34 +490,64 @@ __device__ __forceinline__ float metaball32(const Params &P, const SmemParticles
     return M;
 }
 
-// Load the listed particles of brick b into shared memory (called by the
-// whole CTA; ends with __syncthreads()).
-__device__ inline void load_smem_particles(const Params &P, SmemParticles &sp, int b, int bx0, int by0, int bz0) {
-    const int cnt = min(P.bcount[b], MAXPB);
-    if (threadIdx.x == 0) sp.n = cnt;
+// c - o rounded once to FP32, for c = hl[0] + hl[1] (an FP64 value split into
+// two floats) and an integer-valued o: Knuth's two-sum gives hl[0] - o
+// exactly as s + e, and s + (e + hl[1]) rounds once (up to a 2^-24 fraction
+// of an ulp from the correctly rounded c - o).  Adds only, so nothing is
+// contracted into an FMA.
+__device__ __forceinline__ float df_minus_int(const float hl[2], float o) {
+    const float s = hl[0] - o;
+    const float bb = s - hl[0];
+    const float e = (hl[0] - (s - bb)) + (-o - bb);
+    return s + (e + hl[1]);
+}
+
+// Periodic minimum image of a brick-relative FP32 coordinate about the brick
+// centre (h = half the brick's extent along the axis); the shift by the box
+// length is exact.
+__device__ __forceinline__ float minimg_rel_f(const Params &P, int a, float d, float h) {
+    if (P.per[a]) {
+        const float L = (float)dim_of(P, a);
+        d -= L * rintf((d - h) * P.inv_n_f[a]);
+    }
+    return d;
+}
+
+// The records of the particles whose ids are in sp.id[0..cnt) into shared
+// memory, positions brick-relative in FP32 (called by the whole CTA; ends
+// with __syncthreads()).
+__device__ inline void load_particle_records(const Params &P, SmemParticles &sp, int cnt, int bx0, int by0,
+                                             int bz0) {
+    const float org[3] = {(float)bx0, (float)by0, (float)bz0};
+    const float half[3] = {0.5f * BX, 0.5f * BY, 0.5f * BZ};
     for (int t = threadIdx.x; t < cnt * MAXCP; t += blockDim.x) {
         int s = t / MAXCP, k = t % MAXCP;
-        const DevParticle &p = P.parts[P.blist[b * MAXPB + s]];
+        const DevParticle &p = P.parts[sp.id[s]];
         if (k == 0) {
-            sp.id[s] = P.blist[b * MAXPB + s];
             sp.ncp[s] = p.ncp;
-            double org[3] = {(double)bx0, (double)by0, (double)bz0};
-            double ctr[3] = {bx0 + 0.5 * BX, by0 + 0.5 * BY, bz0 + 0.5 * BZ};
             for (int a = 0; a < 3; a++) {
-                sp.prel[s][a] = (float)(ctr[a] - org[a] + minimg_d(P, a, p.x[a] - ctr[a]));
+                sp.prel[s][a] = minimg_rel_f(P, a, df_minus_int(p.x_hl[a], org[a]), half[a]);
                 sp.v[s][a] = (float)p.v[a];
                 sp.w[s][a] = (float)p.w[a];
             }
         }
         if (k < p.ncp) {
-            double ctr[3] = {bx0 + 0.5 * BX, by0 + 0.5 * BY, bz0 + 0.5 * BZ};
-            double org[3] = {(double)bx0, (double)by0, (double)bz0};
             for (int a = 0; a < 3; a++)
-                sp.crel[s][k][a] = (float)(ctr[a] - org[a] + minimg_d(P, a, p.cpw[k][a] - ctr[a]));
+                sp.crel[s][k][a] = minimg_rel_f(P, a, df_minus_int(p.cpw_hl[k][a], org[a]), half[a]);
             sp.K[s][k] = (float)p.K[k];
         }
     }
     __syncthreads();
+}
+
+// Load the listed particles of brick b into shared memory (called by the
+// whole CTA; ends with __syncthreads()).
+__device__ inline void load_smem_particles(const Params &P, SmemParticles &sp, int b, int bx0, int by0, int bz0) {
+    const int cnt = min(P.bcount[b], MAXPB);
+    if ((int)threadIdx.x < cnt) sp.id[threadIdx.x] = P.blist[b * MAXPB + threadIdx.x];
+    if (threadIdx.x == 0) sp.n = cnt;
+    __syncthreads();
+    load_particle_records(P, sp, cnt, bx0, by0, bz0);
 }
 
 __device__ __forceinline__ void brick_coords(const Params &P, int b, int &bx, int &by, int &bz) {
