@@ -73,16 +73,16 @@ __device__ __forceinline__ void neighbour_coords(const Params &P, int x, int y, 
     if (zs[2] >= P.nz) zs[2] = P.per[2] ? 0 : -1;
 }
 
-// A node of a brick no particle reaches: pull, halfway bounce-back at walls
-// (the node's own outgoing population), collide.  No flags are read.  Node
-// indices are 32-bit (the lattice holds fewer than 2^31 nodes).
-template <typename S, int Q, bool kForce, bool kStream = false>
-__device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z, int n) {
+// The pull of a node no particle link reaches: f_i from x - e_i, halfway
+// bounce-back at walls (the node's own opposite population).  No flags are
+// read.  Node indices are 32-bit (the lattice holds fewer than 2^31 nodes).
+template <typename S, int Q, bool kStream>
+__device__ __forceinline__ void plain_pull(const Params &P, int x, int y, int z, int n,
+                                           typename Codec<S>::C (&fin)[Q]) {
     using L = Lat<Q>;
     using Cd = Codec<S>;
     using C = typename Cd::C;
     const S *A = (const S *)P.fA;
-    S *B = (S *)P.fB;
     const long long N = P.N;
     const C rho0 = Prm<C>::rho0(P);
     int xs[3], ys[3], zs[3];
@@ -92,7 +92,6 @@ __device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z,
     for (int b = 0; b < 3; b++)
 #pragma unroll
         for (int c = 0; c < 3; c++) row[b][c] = P.nx * (ys[b] + P.ny * zs[c]);
-    C fin[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const int bx = 1 - L::e(i, 0), by = 1 - L::e(i, 1), bz = 1 - L::e(i, 2);
@@ -101,7 +100,14 @@ __device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z,
         const S *src = wall ? A + (long long)L::opp(i) * N + n : A + (long long)i * N + (xs[bx] + row[by][bz]);
         fin[i] = kStream ? Cd::ld_s(src, (C)L::w(i), rho0) : Cd::ld(src, (C)L::w(i), rho0);
     }
-    collide_store<S, Q, kForce, kStream>(P, fin, B, N, n);
+}
+
+// A node of a brick no particle reaches: pull, collide, store.
+template <typename S, int Q, bool kForce, bool kStream = false>
+__device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z, int n) {
+    typename Codec<S>::C fin[Q];
+    plain_pull<S, Q, kStream>(P, x, y, z, n, fin);
+    collide_store<S, Q, kForce, kStream>(P, fin, (S *)P.fB, P.N, n);
 }
 
 // The sweep of every brick outside this step's predicted near set: the plain

@@ -196,18 +196,32 @@ struct ForceSink {
     unsigned long long (*fix)[6];
 };
 
+// Force and torque (r x dP) of one term, and the same in 64-bit fixed point.
+template <typename C>
+__device__ __forceinline__ void force_terms(const C dP[3], const C r[3], C t[6]) {
+    t[0] = dP[0];
+    t[1] = dP[1];
+    t[2] = dP[2];
+    t[3] = r[1] * dP[2] - r[2] * dP[1];
+    t[4] = r[2] * dP[0] - r[0] * dP[2];
+    t[5] = r[0] * dP[1] - r[1] * dP[0];
+}
+template <typename C>
+__device__ __forceinline__ unsigned long long to_fixed(C v) {
+    return (unsigned long long)__float2ll_rn((float)v * (float)(1ull << kForceFixBits));
+}
+
 template <typename C>
 __device__ __forceinline__ void add_term(ForceSink<C> sink, int s, const C dP[3], const C r[3]) {
-    const C t[6] = {dP[0], dP[1], dP[2], r[1] * dP[2] - r[2] * dP[1], r[2] * dP[0] - r[0] * dP[2],
-                    r[0] * dP[1] - r[1] * dP[0]};
+    C t[6];
+    force_terms<C>(dP, r, t);
     if (sizeof(C) == 8) {
 #pragma unroll
         for (int c = 0; c < 6; c++) sink.acc[s][c] += t[c];
     } else {
-        const float scale = (float)(1ull << kForceFixBits);
 #pragma unroll
         for (int c = 0; c < 6; c++)
-            if (t[c] != C(0)) atomicAdd(&sink.fix[s][c], (unsigned long long)__float2ll_rn((float)t[c] * scale));
+            if (t[c] != C(0)) atomicAdd(&sink.fix[s][c], to_fixed<C>(t[c]));
     }
 }
 
@@ -255,51 +269,70 @@ __device__ __forceinline__ FFData<typename Codec<S>::C> ff_fetch(const Params &P
     return f;
 }
 
-// The unknown population of one particle link (direction i arrives at x from
-// the solid node x + d, d = -e_i) and its momentum-exchange term, in offset
-// form: fown_io is the node's post-collision offset g = f - w rho0 along d,
-// drho_f = rho_f - rho0, and the unknown is returned as an offset.  Eq. (28)'s term is
-// (d - u_w) f+_d + (d + u_w) f_-d = 2 d w rho0 + (d - u_w) g+_d + (d + u_w)
-// g_-d; the constant 2 d w rho0 sums to exactly zero over all links that cross
-// a particle's surface (those of Eq. (28) and the missing force points of
-// §2.3.5 together: every pair of solid nodes of the particle cancels), and so
-// does its torque (x_s - x_p) x 2 d w rho0, so both are left out unless the
-// missing force points are switched off.
+// Geometry of one particle link (direction i arrives at x from the solid node
+// x + d, d = -e_i, of listed particle slot s): the link fraction q of Eq. (27)
+// (clamped to [0,1]: rounding can push it past the ends; or Eq. (26) by
+// Newton with q_exact), the lever arm r from the particle's centroid to the
+// wall point x_w = x + q d and the wall velocity u_w there.  M_j(x_f) is
+// shared by all links of the node to the same particle (Mf_cache).
+template <typename C>
+struct LinkGeom {
+    C q, r[3], uw[3];
+};
 template <typename S, int Q>
-__device__ __forceinline__ typename Codec<S>::C particle_link(const Params &P, const SmemParticles &sp, int i, int x,
-                                                             int y, int z, int lx, int ly, int lz, int bx0, int by0,
-                                                             int bz0, int j, const FFData<typename Codec<S>::C> &ff,
-                                                             typename Codec<S>::C fown_io,
-                                                             typename Codec<S>::C drho_f,
-                                                             const typename Codec<S>::C *u_f,
-                                                             ForceSink<typename Codec<S>::C> sink,
-                                                             typename Codec<S>::C *Mf_cache, int *Mf_slot) {
+__device__ __forceinline__ LinkGeom<typename Codec<S>::C> link_geometry(const Params &P, const SmemParticles &sp,
+                                                                       int i, int s, int lx, int ly, int lz, int bx0,
+                                                                       int by0, int bz0,
+                                                                       typename Codec<S>::C *Mf_cache,
+                                                                       int *Mf_slot) {
     using L = Lat<Q>;
-    using Cd = Codec<S>;
-    using C = typename Cd::C;
+    using C = typename Codec<S>::C;
     const int io = L::opp(i);
     const int dx = lat_e<Q>(io, 0), dy = lat_e<Q>(io, 1), dz = lat_e<Q>(io, 2);  // d, into the solid
-    const int s = slot_of(sp, j);
-    const C w_io = (C)lat_w<Q>(io);
-    const C rho0 = Prm<C>::rho0(P);
-    if (s < 0) {  // cannot happen for a consistent brick list; bounce back plainly
-        atomicOr(&P.status[ST_ERR], ERRB_BRICK_OVERFLOW);
-        return fown_io;
-    }
-    // q by Eq. (27), clamped to [0,1] (rounding can push it past the ends);
-    // M_j(x_f) is shared by all links of the node to the same particle
     if (*Mf_slot != s) {
         *Mf_cache = m_value<C>(P, sp, s, lx, ly, lz, bx0, by0, bz0);
         *Mf_slot = s;
     }
     const C Mf = *Mf_cache;
     const C Ms = m_value<C>(P, sp, s, lx + dx, ly + dy, lz + dz, bx0, by0, bz0);
+    LinkGeom<C> g;
     C q = (c0_of<C>(P) - Mf) / (Ms - Mf);
     q = q < C(0) ? C(0) : (q > C(1) ? C(1) : q);
     if (P.q_exact) q = q_root<C>(P, sp, s, lx, ly, lz, dx, dy, dz, bx0, by0, bz0, q);
-    C r[3], uw[3];
-    lever<C>(P, sp, s, bx0, by0, bz0, (C)lx + q * dx, (C)ly + q * dy, (C)lz + q * dz, r);
-    particle_velocity<C>(P, sp, s, r, uw);
+    g.q = q;
+    lever<C>(P, sp, s, bx0, by0, bz0, (C)lx + q * dx, (C)ly + q * dy, (C)lz + q * dz, g.r);
+    particle_velocity<C>(P, sp, s, g.r, g.uw);
+    return g;
+}
+
+// The unknown population of a particle link of geometry g and its
+// momentum-exchange term dP, in offset form: fown_io is the node's
+// post-collision offset g = f - w rho0 along d, drho_f = rho_f - rho0, u_f its
+// velocity, ff the second fluid node x_ff = x - d, and the unknown is
+// returned as an offset.  Eq. (28)'s term is (d - u_w) f+_d + (d + u_w) f_-d =
+// 2 d w rho0 + (d - u_w) g+_d + (d + u_w) g_-d; the constant 2 d w rho0 sums
+// to exactly zero over all links that cross a particle's surface (those of
+// Eq. (28) and the missing force points of §2.3.5 together: every pair of
+// solid nodes of the particle cancels), and so does its torque
+// (x_s - x_p) x 2 d w rho0, so both are left out unless the missing force
+// points are switched off.
+template <typename S, int Q>
+__device__ __forceinline__ typename Codec<S>::C link_update(const Params &P, int i,
+                                                           const LinkGeom<typename Codec<S>::C> &g,
+                                                           const FFData<typename Codec<S>::C> &ff,
+                                                           typename Codec<S>::C fown_io,
+                                                           typename Codec<S>::C drho_f,
+                                                           const typename Codec<S>::C *u_f,
+                                                           typename Codec<S>::C dP[3]) {
+    using L = Lat<Q>;
+    using Cd = Codec<S>;
+    using C = typename Cd::C;
+    const int io = L::opp(i);
+    const int dx = lat_e<Q>(io, 0), dy = lat_e<Q>(io, 1), dz = lat_e<Q>(io, 2);  // d, into the solid
+    const C w_io = (C)lat_w<Q>(io);
+    const C rho0 = Prm<C>::rho0(P);
+    const C q = g.q;
+    const C *uw = g.uw;
     const C eu_w = -(dx * uw[0] + dy * uw[1] + dz * uw[2]);  // e_i . u_w with e_i = -d
     const C rho_f = rho0 + drho_f;
     const C drho_ff = ff.drho, m_ff[3] = {ff.m[0], ff.m[1], ff.m[2]}, fff_io = ff.g_io;
@@ -336,7 +369,6 @@ __device__ __forceinline__ typename Codec<S>::C particle_link(const Params &P, c
     }
     // Eq. (28): (e_i' - u_w) f+_i'(x,t) - (e_i - u_w) f_i(x,t+1), e_i' = d,
     // in offsets (the constant part left out, see above)
-    C dP[3];
     dP[0] = (C(dx) - uw[0]) * fown_io + (C(dx) + uw[0]) * fin;
     dP[1] = (C(dy) - uw[1]) * fown_io + (C(dy) + uw[1]) * fin;
     dP[2] = (C(dz) - uw[2]) * fown_io + (C(dz) + uw[2]) * fin;
@@ -344,7 +376,30 @@ __device__ __forceinline__ typename Codec<S>::C particle_link(const Params &P, c
         const C c = C(2) * w_io * rho0;
         dP[0] += c * dx; dP[1] += c * dy; dP[2] += c * dz;
     }
-    add_term<C>(sink, s, dP, r);
+    return fin;
+}
+
+// One particle link of listed particle j at node x: its geometry, its
+// unknown and its momentum-exchange term added to the sink.
+template <typename S, int Q>
+__device__ __forceinline__ typename Codec<S>::C particle_link(const Params &P, const SmemParticles &sp, int i, int x,
+                                                             int y, int z, int lx, int ly, int lz, int bx0, int by0,
+                                                             int bz0, int j, const FFData<typename Codec<S>::C> &ff,
+                                                             typename Codec<S>::C fown_io,
+                                                             typename Codec<S>::C drho_f,
+                                                             const typename Codec<S>::C *u_f,
+                                                             ForceSink<typename Codec<S>::C> sink,
+                                                             typename Codec<S>::C *Mf_cache, int *Mf_slot) {
+    using C = typename Codec<S>::C;
+    const int s = slot_of(sp, j);
+    if (s < 0) {  // cannot happen for a consistent brick list; bounce back plainly
+        atomicOr(&P.status[ST_ERR], ERRB_BRICK_OVERFLOW);
+        return fown_io;
+    }
+    const LinkGeom<C> g = link_geometry<S, Q>(P, sp, i, s, lx, ly, lz, bx0, by0, bz0, Mf_cache, Mf_slot);
+    C dP[3];
+    const C fin = link_update<S, Q>(P, i, g, ff, fown_io, drho_f, u_f, dP);
+    add_term<C>(sink, s, dP, g.r);
     return fin;
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "k_batch.cuh"
+#include "k_static.cuh"
 
 namespace lbmmb {
 
@@ -96,6 +97,63 @@ void launch_plain_batch_t(const BatchArgs &B, int Q, bool force, int grid, cudaS
     }
 }
 
+template <typename S>
+void launch_static_build_t(const Params &P, cudaStream_t st) {
+    const int cap = kGridStrideBlocks / 2;
+    const int grid = P.nbricks < cap ? P.nbricks : cap;
+    if (P.Q == 19) k_static_build<S, 19><<<grid, BRICK, 0, st>>>(P);
+    else k_static_build<S, 15><<<grid, BRICK, 0, st>>>(P);
+}
+template <typename S>
+void launch_static_plain_t(const Params &P, cudaStream_t st) {
+    const bool force = P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0;
+    const int grid = (int)((P.N + BRICK - 1) / BRICK);
+    if (P.Q == 19) {
+        if (force) k_static_plain<S, 19, true><<<grid, BRICK, 0, st>>>(P);
+        else k_static_plain<S, 19, false><<<grid, BRICK, 0, st>>>(P);
+    } else {
+        if (force) k_static_plain<S, 15, true><<<grid, BRICK, 0, st>>>(P);
+        else k_static_plain<S, 15, false><<<grid, BRICK, 0, st>>>(P);
+    }
+}
+template <typename S>
+void launch_static_links_t(const Params &P, cudaStream_t st) {
+    const bool force = P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0;
+    const int warps = (P.snodes_n + 31) / 32;
+    const int cap = kNearCtasPerSm * kSmCount;
+    int grid = (warps + BRICK / 32 - 1) / (BRICK / 32);
+    grid = grid < 1 ? 1 : (grid > cap ? cap : grid);
+    if (P.Q == 19) {
+        if (force) k_static_links<S, 19, true><<<grid, BRICK, 0, st>>>(P);
+        else k_static_links<S, 19, false><<<grid, BRICK, 0, st>>>(P);
+    } else {
+        if (force) k_static_links<S, 15, true><<<grid, BRICK, 0, st>>>(P);
+        else k_static_links<S, 15, false><<<grid, BRICK, 0, st>>>(P);
+    }
+}
+
+template <typename S>
+void launch_static_plain_batch_t(const BatchArgs &B, int Q, bool force, int grid, cudaStream_t st) {
+    if (Q == 19) {
+        if (force) k_static_plain_batch<S, 19, true><<<grid, BRICK, 0, st>>>(B);
+        else k_static_plain_batch<S, 19, false><<<grid, BRICK, 0, st>>>(B);
+    } else {
+        if (force) k_static_plain_batch<S, 15, true><<<grid, BRICK, 0, st>>>(B);
+        else k_static_plain_batch<S, 15, false><<<grid, BRICK, 0, st>>>(B);
+    }
+}
+template <typename S>
+void launch_static_links_batch_t(const BatchArgs &B, int Q, bool force, int warps, cudaStream_t st) {
+    const int grid = (warps + BRICK / 32 - 1) / (BRICK / 32);
+    if (Q == 19) {
+        if (force) k_static_links_batch<S, 19, true><<<grid, BRICK, 0, st>>>(B);
+        else k_static_links_batch<S, 19, false><<<grid, BRICK, 0, st>>>(B);
+    } else {
+        if (force) k_static_links_batch<S, 15, true><<<grid, BRICK, 0, st>>>(B);
+        else k_static_links_batch<S, 15, false><<<grid, BRICK, 0, st>>>(B);
+    }
+}
+
 #define LBMMB_INSTANTIATE(S)                                                                                     \
     template void launch_init_t<S>(const Params &, void *, cudaStream_t);                                        \
     template void launch_flags_t<S>(const Params &, cudaStream_t);                                               \
@@ -108,6 +166,11 @@ void launch_plain_batch_t(const BatchArgs &B, int Q, bool force, int grid, cudaS
     template void launch_check_t<S>(const Params &, const void *, const uint16_t *, cudaStream_t);             \
     template void launch_flags_batch_t<S>(const BatchArgs &, int, cudaStream_t);                                  \
     template void launch_near_batch_t<S>(const BatchArgs &, int, bool, cudaStream_t);                             \
-    template void launch_plain_batch_t<S>(const BatchArgs &, int, bool, int, cudaStream_t);
+    template void launch_plain_batch_t<S>(const BatchArgs &, int, bool, int, cudaStream_t);                       \
+    template void launch_static_build_t<S>(const Params &, cudaStream_t);                                        \
+    template void launch_static_plain_t<S>(const Params &, cudaStream_t);                                        \
+    template void launch_static_links_t<S>(const Params &, cudaStream_t);                                        \
+    template void launch_static_plain_batch_t<S>(const BatchArgs &, int, bool, int, cudaStream_t);               \
+    template void launch_static_links_batch_t<S>(const BatchArgs &, int, bool, int, cudaStream_t);
 
 }  // namespace lbmmb

@@ -37,6 +37,8 @@ struct Layout {
     size_t blist, partial, parts, Fh, Th, Fc, Tc;
     size_t pairF, pair_on, pair_xi, pair_xm, wall_on, wall_xi, wall_xcw;
     size_t pair_xi_f, pair_xm_f, wall_xi_f, wall_xcw_f;
+    size_t sskip, snodes, slinks, scount, smf;  // fixed-geometry sweep (below FP64)
+    int snode_cap, slink_cap;
     size_t status;
     size_t total;
     long long N;
@@ -121,6 +123,19 @@ void make_layout(const lbm_config *c, Layout *L) {
     L->pair_xm_f = take(P * P * 12);
     L->wall_xi_f = take(P * NWALL * 12);
     L->wall_xcw_f = take(P * NWALL * 12);
+    // fixed-geometry sweep: link nodes lie next to particle surfaces, so room
+    // for an eighth of the nodes as link nodes and a quarter as links (at
+    // least 4096 and 16384, for small boxes holding large particles) is
+    // ample: about 10 bytes per node beside the populations' 76-304; a build
+    // that does not fit falls back to the brick sweeps
+    const bool fixed_sweep = c->storage != LBM_STORE_F64;
+    L->snode_cap = fixed_sweep ? (int)std::max<long long>(4096, N / 8) : 0;
+    L->slink_cap = fixed_sweep ? (int)std::max<long long>(16384, N / 4) : 0;
+    L->sskip = take(fixed_sweep ? (size_t)N : 0);
+    L->snodes = take((size_t)L->snode_cap * sizeof(StaticNode));
+    L->slinks = take((size_t)L->slink_cap * sizeof(StaticLink));
+    L->scount = take(fixed_sweep ? 8 : 0);
+    L->smf = take(fixed_sweep ? P * 48 : 0);
     L->status = take(ST_SLOTS * 4);
     L->total = o;
 }
@@ -158,6 +173,8 @@ struct lbm_handle {
     int fc_valid;  // the DEM of the last step left the contact load of the current state
     int all_fixed;     // every particle is fixed: the geometry cannot change between set_particles calls
     int static_steps;  // steps run since set_particles with all_fixed (saturating)
+    int static_state;  // fixed-geometry sweep: 0 not built, 1 built, -1 did not fit (brick sweeps)
+    int snodes_n;      // its link nodes
     int nsm;       // SMs of the device
     int plain_per_sm, chain_per_sm;  // launch schedule (lbm_set_schedule)
     int64_t steps;
@@ -207,6 +224,16 @@ Params make_params(lbm_handle *h) {
     P.pred_count = at<int>(h, h->L.pred_count);
     P.skip = at<int>(h, h->L.skip);
     P.brick_solid = at<uint8_t>(h, h->L.brick_solid);
+    if (h->L.snode_cap > 0) {
+        P.sskip = at<uint8_t>(h, h->L.sskip);
+        P.snodes = at<StaticNode>(h, h->L.snodes);
+        P.slinks = at<StaticLink>(h, h->L.slinks);
+        P.scount = at<int>(h, h->L.scount);
+        P.smf = at<unsigned long long>(h, h->L.smf);
+    }
+    P.snode_cap = h->L.snode_cap;
+    P.slink_cap = h->L.slink_cap;
+    P.snodes_n = h->snodes_n;
     P.bcount = at<int>(h, h->L.bin);
     P.blist = at<int>(h, h->L.blist);
     P.partial = at<double>(h, h->L.partial);
@@ -267,6 +294,9 @@ template <typename S> struct DoFields {
 template <typename S> struct DoGetPop { static void run(const Params &P, double *out, cudaStream_t st) { launch_get_pop_t<S>(P, P.fA, out, st); } };
 template <typename S> struct DoSetPop { static void run(const Params &P, const double *in, cudaStream_t st) { launch_set_pop_t<S>(P, P.fA, in, st); } };
 template <typename S> struct DoCheck { static void run(const Params &P, cudaStream_t st) { launch_check_t<S>(P, P.fA, P.flag_new, st); } };
+template <typename S> struct DoStaticBuild { static void run(const Params &P, cudaStream_t st) { launch_static_build_t<S>(P, st); } };
+template <typename S> struct DoStaticPlain { static void run(const Params &P, cudaStream_t st) { launch_static_plain_t<S>(P, st); } };
+template <typename S> struct DoStaticLinks { static void run(const Params &P, cudaStream_t st) { launch_static_links_t<S>(P, st); } };
 
 // ---------------------------------------------------------------------------
 // Host particle set-up.
@@ -440,6 +470,8 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
     h->steps = 0;
     h->all_fixed = 1;
     h->static_steps = 0;
+    h->static_state = 0;
+    h->snodes_n = 0;
     h->prof = false;
     for (int k = 0; k < kProfKernels; k++) h->nrec[k] = 0;
     std::snprintf(h->err, sizeof(h->err), "no error");
@@ -619,6 +651,8 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
     for (int j = 0; j < n; j++)
         if (!host[j].fixed) h->all_fixed = 0;
     h->static_steps = 0;
+    h->static_state = 0;
+    h->snodes_n = 0;
     return rc;
 }
 
@@ -659,33 +693,81 @@ int lbm_step(lbm_handle *h, int nsteps) {
     cudaStream_t hs = h->hi;
     for (int t = 0; t < nsteps; t++) {
         Params P = make_params(h);
+        // with every particle fixed the flags cannot change: once both flag
+        // buffers and the per-brick solid marks hold them (the pass visits the
+        // bricks listed in the last three steps), it is left out, and below
+        // FP64 the fixed-geometry sweep takes over
+        const bool geom_static = h->all_fixed && h->static_steps >= kStaticFlagSteps;
+        const bool fixed_sweep = geom_static && h->L.snode_cap > 0 && h->static_state >= 0;
         // fresh brick lists and step counters
         e = cudaMemsetAsync(h->ws + h->L.bin, 0, h->L.bin_bytes, hs);
         if (e != cudaSuccess) return cuda_check(h, e, "cudaMemsetAsync(bricks)");
-        { ProfScope s(h, 0, true, hs); launch_bin(P, hs); }
-        e = cudaEventRecord(h->ev_bin, hs);
-        if (e != cudaSuccess) return cuda_check(h, e, "event record");
-        // with every particle fixed the flags cannot change: once both flag
-        // buffers and the per-brick solid marks hold them (the pass visits the
-        // bricks listed in the last three steps), it is left out
-        const bool flags = !(h->all_fixed && h->static_steps >= kStaticFlagSteps);
-        { ProfScope s(h, 1, flags, hs); if (flags) by_storage<DoFlags>(h->cfg.storage, P, hs); }
-        // the near sweep reads the halo the previous plain sweep wrote (this
-        // wait is issued before ev_plain is recorded again below; the plain
-        // sweep of the call before was joined into `stream` before the fork,
-        // so every event waited on is recorded within this call, as stream
-        // capture requires)
-        if (t > 0) e = cudaStreamWaitEvent(hs, h->ev_plain, 0);
-        // plain bricks on the low-priority stream, concurrent with the chain
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_bin, 0);
-        if (e != cudaSuccess) return cuda_check(h, e, "stream wait");
-        { ProfScope s(h, 2, true, h->aux); by_storage<DoPlain>(h->cfg.storage, P, h->aux); }
-        e = cudaEventRecord(h->ev_plain, h->aux);
-        if (e != cudaSuccess) return cuda_check(h, e, "event record");
-        { ProfScope s(h, 3, true, hs); by_storage<DoNear>(h->cfg.storage, P, hs); }
-        e = cudaEventRecord(h->ev_near, hs);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_near, 0);
-        if (e != cudaSuccess) return cuda_check(h, e, "stream fork");
+        if (fixed_sweep && h->static_state == 0) {
+            // record the fixed geometry once, from this step's brick lists
+            { ProfScope s(h, 0, true, hs); launch_bin(P, hs); }
+            e = cudaMemsetAsync(h->ws + h->L.sskip, 0, (size_t)h->L.N, hs);
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->L.scount, 0, 8, hs);
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->L.smf, 0, (size_t)h->cfg.max_particles * 48, hs);
+            if (e != cudaSuccess) return cuda_check(h, e, "cudaMemsetAsync(static)");
+            by_storage<DoStaticBuild>(h->cfg.storage, P, hs);
+            int cnt[2] = {0, 0}, st[ST_SLOTS];
+            e = cudaMemcpyAsync(cnt, h->ws + h->L.scount, 8, cudaMemcpyDeviceToHost, hs);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(st, h->ws + h->L.status, ST_SLOTS * 4, cudaMemcpyDeviceToHost, hs);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(hs);
+            if (e != cudaSuccess) return cuda_check(h, e, "fixed-geometry build");
+            if (st[ST_ERR] & ERRB_STATIC_CAPACITY) {
+                // did not fit: clear the mark and keep the brick sweeps
+                st[ST_ERR] &= ~ERRB_STATIC_CAPACITY;
+                e = cudaMemcpyAsync(h->ws + h->L.status, st, ST_SLOTS * 4, cudaMemcpyHostToDevice, hs);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(hs);
+                if (e != cudaSuccess) return cuda_check(h, e, "fixed-geometry build");
+                h->static_state = -1;
+                std::snprintf(h->err, sizeof(h->err),
+                              "fixed-geometry sweep: %d link nodes and %d links exceed %d and %d; brick sweeps kept",
+                              cnt[0], cnt[1], h->L.snode_cap, h->L.slink_cap);
+            } else {
+                h->static_state = 1;
+                h->snodes_n = cnt[0];
+                P = make_params(h);
+            }
+            // the lists this build read are cleared again for the step
+            e = cudaMemsetAsync(h->ws + h->L.bin, 0, h->L.bin_bytes, hs);
+            if (e != cudaSuccess) return cuda_check(h, e, "cudaMemsetAsync(bricks)");
+        }
+        if (fixed_sweep && h->static_state == 1) {
+            // the link nodes after the previous step's plain nodes (they read
+            // them, and overwrite the array that sweep read), the plain nodes
+            // after the previous step's link nodes, concurrently otherwise
+            if (t > 0) e = cudaStreamWaitEvent(hs, h->ev_plain, 0);
+            if (e == cudaSuccess && t > 0) e = cudaStreamWaitEvent(h->aux, h->ev_near, 0);
+            if (e != cudaSuccess) return cuda_check(h, e, "stream wait");
+            { ProfScope s(h, 3, true, hs); by_storage<DoStaticLinks>(h->cfg.storage, P, hs); }
+            { ProfScope s(h, 2, true, h->aux); by_storage<DoStaticPlain>(h->cfg.storage, P, h->aux); }
+            e = cudaEventRecord(h->ev_plain, h->aux);
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_near, hs);
+            if (e != cudaSuccess) return cuda_check(h, e, "event record");
+        } else {
+            { ProfScope s(h, 0, true, hs); launch_bin(P, hs); }
+            e = cudaEventRecord(h->ev_bin, hs);
+            if (e != cudaSuccess) return cuda_check(h, e, "event record");
+            { ProfScope s(h, 1, !geom_static, hs); if (!geom_static) by_storage<DoFlags>(h->cfg.storage, P, hs); }
+            // the near sweep reads the halo the previous plain sweep wrote (this
+            // wait is issued before ev_plain is recorded again below; the plain
+            // sweep of the call before was joined into `stream` before the fork,
+            // so every event waited on is recorded within this call, as stream
+            // capture requires)
+            if (t > 0) e = cudaStreamWaitEvent(hs, h->ev_plain, 0);
+            // plain bricks on the low-priority stream, concurrent with the chain
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_bin, 0);
+            if (e != cudaSuccess) return cuda_check(h, e, "stream wait");
+            { ProfScope s(h, 2, true, h->aux); by_storage<DoPlain>(h->cfg.storage, P, h->aux); }
+            e = cudaEventRecord(h->ev_plain, h->aux);
+            if (e != cudaSuccess) return cuda_check(h, e, "event record");
+            { ProfScope s(h, 3, true, hs); by_storage<DoNear>(h->cfg.storage, P, hs); }
+            e = cudaEventRecord(h->ev_near, hs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_near, 0);
+            if (e != cudaSuccess) return cuda_check(h, e, "stream fork");
+        }
         if (!P.force_fixed) { ProfScope s(h, 4, P.np > 0, hs); launch_force_reduce(P, hs); }
         { ProfScope s(h, 5, P.np > 0 && P.n_sub > 0, hs); launch_dem(P, hs); }
         e = cudaGetLastError();
@@ -710,9 +792,13 @@ int lbm_kernels_per_step(const lbm_handle *h) {
     // binning (every step), flags (left out once the geometry is static),
     // plain and near sweeps; force reduction (FP64 lattices with particles);
     // DEM (particles, n_sub > 0)
-    const int flags = h->all_fixed && h->static_steps >= kStaticFlagSteps ? 0 : 1;
+    // once the fixed-geometry sweep runs: its link and plain kernels
+    const bool geom_static = h->all_fixed && h->static_steps >= kStaticFlagSteps;
+    const int dem = h->np > 0 && h->cfg.n_sub > 0 ? 1 : 0;
+    if (geom_static && h->static_state == 1) return 2 + dem;
+    const int flags = geom_static ? 0 : 1;
     if (h->np == 0) return 3 + flags;
-    return 3 + flags + (h->cfg.storage == LBM_STORE_F64 ? 1 : 0) + (h->cfg.n_sub > 0 ? 1 : 0);
+    return 3 + flags + (h->cfg.storage == LBM_STORE_F64 ? 1 : 0) + dem;
 }
 
 static int read_status(lbm_handle *h, int *st) {
@@ -943,11 +1029,14 @@ struct lbm_batch {
     // ordered after and before `stream` by ev_pre / ev_post
     cudaStream_t stream, cap, hi, aux;
     cudaEvent_t ev_fork, ev_bin, ev_plain, ev_near, ev_join, ev_pre, ev_post;
-    size_t tab_off, span_off, item_off, ctr_off, span_case_off;   // device tables at the workspace start
+    size_t tab_off, span_off, item_off, ctr_off, span_case_off, swarp_off;  // device tables at the workspace start
     int Q, storage;
     bool force;
     int g_chain, plain_chunk;
-    int total_spans, bin_items;
+    int total_spans, bin_items, total_swarps;
+    int static_state;            // fixed-geometry sweep of all cases: 0 not built, 1 built, -1 did not fit
+    bool graph_fixed;            // the captured graph runs the fixed-geometry sweep
+    std::vector<Params> tab_host;  // the device table's rows
     bool dirty;
     int64_t steps;
     int static_steps;  // steps since the last lbm_batch_set_particles (saturating)
@@ -977,7 +1066,7 @@ int bcheck(lbm_batch *b, cudaError_t e, const char *what) {
 // Workspace: tables, then per case its single-lattice layout followed by a
 // second per-step region (the per-step region alternates by step parity).
 struct BatchLayout {
-    size_t tab, span_off, item_off, ctr, span_case, total;
+    size_t tab, span_off, item_off, ctr, span_case, swarp_off, total;
     std::vector<size_t> base, bin1;
 };
 
@@ -1005,6 +1094,7 @@ void batch_layout(const lbm_config *cfgs, int n, BatchLayout *B) {
     B->span_off = take(((size_t)n + 1) * 4);
     B->item_off = take(((size_t)n + 1) * 4);
     B->ctr = take(4 * 4);
+    B->swarp_off = take(((size_t)n + 1) * 4);
     size_t spans = 0;
     for (int c = 0; c < n; c++) {
         Layout L;
@@ -1027,8 +1117,8 @@ void batch_layout(const lbm_config *cfgs, int n, BatchLayout *B) {
 // sums the batched kernels map their CTAs with.
 int batch_tables(lbm_batch *b) {
     std::vector<Params> tab(2 * (size_t)b->n);
-    std::vector<int> soff(b->n + 1), ioff(b->n + 1);
-    soff[0] = ioff[0] = 0;
+    std::vector<int> soff(b->n + 1), ioff(b->n + 1), woff(b->n + 1);
+    soff[0] = ioff[0] = woff[0] = 0;
     for (int c = 0; c < b->n; c++) {
         lbm_handle *h = b->cases[c];
         const int64_t keep_steps = h->steps;
@@ -1053,9 +1143,13 @@ int batch_tables(lbm_batch *b) {
         h->cur = keep_cur;
         h->fcur = keep_fcur;
         soff[c + 1] = soff[c] + (int)((h->L.N + BRICK - 1) / BRICK);
+        // link-node warps of the fixed-geometry sweep, at least one per case
+        woff[c + 1] = woff[c] + std::max(1, (h->snodes_n + 31) / 32);
         ioff[c + 1] = ioff[c] + (h->np > 0 ? h->np : 1);
     }
     b->total_spans = soff[b->n];
+    b->total_swarps = woff[b->n];
+    b->tab_host = tab;
     b->bin_items = ioff[b->n];
     int rc = bcheck(b, cudaMemcpyAsync(b->ws + b->tab_off, tab.data(), tab.size() * sizeof(Params),
                                        cudaMemcpyHostToDevice, b->stream), "cudaMemcpyAsync(tables)");
@@ -1071,6 +1165,9 @@ int batch_tables(lbm_batch *b) {
     if (rc == LBM_OK)
         rc = bcheck(b, cudaMemcpyAsync(b->ws + b->span_case_off, scase.data(), scase.size() * 2,
                                        cudaMemcpyHostToDevice, b->stream), "cudaMemcpyAsync(tables)");
+    if (rc == LBM_OK)
+        rc = bcheck(b, cudaMemcpyAsync(b->ws + b->swarp_off, woff.data(), woff.size() * 4, cudaMemcpyHostToDevice,
+                                       b->stream), "cudaMemcpyAsync(tables)");
     if (rc == LBM_OK) rc = bcheck(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
     if (rc == LBM_OK) b->dirty = false;
     return rc;
@@ -1086,6 +1183,7 @@ BatchArgs batch_args(lbm_batch *b) {
     B.ctr = reinterpret_cast<unsigned *>(b->ws + b->ctr_off);
     B.g_chain = b->g_chain;
     B.plain_chunk = b->plain_chunk;
+    B.swarp_off = reinterpret_cast<const int *>(b->ws + b->swarp_off);
     return B;
 }
 
@@ -1096,6 +1194,13 @@ struct DoBatchStep {
     static void plain(const BatchArgs &B, int Q, bool f, int grid, cudaStream_t st) {
         launch_plain_batch_t<S>(B, Q, f, grid, st);
     }
+    static void static_plain(const BatchArgs &B, int Q, bool f, int grid, cudaStream_t st) {
+        launch_static_plain_batch_t<S>(B, Q, f, grid, st);
+    }
+    static void static_links(const BatchArgs &B, int Q, bool f, int warps, cudaStream_t st) {
+        launch_static_links_batch_t<S>(B, Q, f, warps, st);
+    }
+    static void static_build(const Params &P, cudaStream_t st) { launch_static_build_t<S>(P, st); }
 };
 
 template <typename Fn>
@@ -1109,13 +1214,24 @@ void by_batch_storage(int storage, Fn &&fn) {
 
 // nsteps steps on the batch's streams, forked from and joined into b->cap
 // (the sequence a graph is captured from).
-int batch_issue(lbm_batch *b, int nsteps, bool flags) {
+int batch_issue(lbm_batch *b, int nsteps, bool flags, bool fixed) {
     const BatchArgs B = batch_args(b);
     const int plain_grid = (b->total_spans + b->plain_chunk - 1) / b->plain_chunk;
     cudaError_t e = cudaEventRecord(b->ev_fork, b->cap);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->hi, b->ev_fork, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
-    for (int t = 0; t < nsteps && e == cudaSuccess; t++) {
+    for (int t = 0; fixed && t < nsteps && e == cudaSuccess; t++) {
+        // fixed-geometry sweep: the link nodes after the previous step's plain
+        // nodes, the plain nodes after the previous step's link nodes
+        if (t > 0) e = cudaStreamWaitEvent(b->hi, b->ev_plain, 0);
+        if (e == cudaSuccess && t > 0) e = cudaStreamWaitEvent(b->aux, b->ev_near, 0);
+        if (e != cudaSuccess) break;
+        by_batch_storage(b->storage, [&](auto D) { D.static_links(B, b->Q, b->force, b->total_swarps, b->hi); });
+        by_batch_storage(b->storage, [&](auto D) { D.static_plain(B, b->Q, b->force, plain_grid, b->aux); });
+        e = cudaEventRecord(b->ev_plain, b->aux);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_near, b->hi);
+    }
+    for (int t = 0; !fixed && t < nsteps && e == cudaSuccess; t++) {
         launch_bin_batch(B, b->bin_items, b->hi);
         e = cudaEventRecord(b->ev_bin, b->hi);
         if (e != cudaSuccess) break;
@@ -1135,6 +1251,55 @@ int batch_issue(lbm_batch *b, int nsteps, bool flags) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->ev_plain, 0);
     if (e == cudaSuccess) e = cudaGetLastError();
     return bcheck(b, e, "batched step launch");
+}
+
+void drop_graph(lbm_batch *b);
+
+// Record the fixed geometry of every case from the brick lists of the last
+// step taken (steps_done of them), on `cap`, and synchronise; all cases take
+// the fixed-geometry sweep, or none if one did not fit.
+int batch_build_static(lbm_batch *b, int64_t steps_done) {
+    const int p = (int)((steps_done - 1) & 1);
+    int rc = LBM_OK;
+    for (int c = 0; c < b->n && rc == LBM_OK; c++) {
+        lbm_handle *h = b->cases[c];
+        Params P = b->tab_host[(size_t)p * b->n + c];
+        P.step = (int)(steps_done - 1);
+        cudaError_t e = cudaMemsetAsync(h->ws + h->L.sskip, 0, (size_t)h->L.N, b->cap);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->L.scount, 0, 8, b->cap);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->L.smf, 0, (size_t)h->cfg.max_particles * 48, b->cap);
+        if (e == cudaSuccess) by_batch_storage(b->storage, [&](auto D) { D.static_build(P, b->cap); });
+        if (e == cudaSuccess) e = cudaGetLastError();
+        rc = bcheck(b, e, "fixed-geometry build");
+    }
+    std::vector<int> cnt(2 * (size_t)b->n), st((size_t)ST_SLOTS * b->n);
+    for (int c = 0; c < b->n && rc == LBM_OK; c++) {
+        lbm_handle *h = b->cases[c];
+        cudaError_t e = cudaMemcpyAsync(&cnt[2 * (size_t)c], h->ws + h->L.scount, 8, cudaMemcpyDeviceToHost, b->cap);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&st[(size_t)ST_SLOTS * c], h->ws + h->L.status, ST_SLOTS * 4, cudaMemcpyDeviceToHost,
+                                b->cap);
+        rc = bcheck(b, e, "fixed-geometry build");
+    }
+    if (rc == LBM_OK) rc = bcheck(b, cudaStreamSynchronize(b->cap), "cudaStreamSynchronize");
+    if (rc != LBM_OK) return rc;
+    bool fits = true;
+    for (int c = 0; c < b->n; c++)
+        if (st[(size_t)ST_SLOTS * c + ST_ERR] & ERRB_STATIC_CAPACITY) fits = false;
+    for (int c = 0; c < b->n && rc == LBM_OK; c++) {
+        lbm_handle *h = b->cases[c];
+        if (st[(size_t)ST_SLOTS * c + ST_ERR] & ERRB_STATIC_CAPACITY) {
+            int *err = &st[(size_t)ST_SLOTS * c + ST_ERR];
+            *err &= ~ERRB_STATIC_CAPACITY;
+            rc = bcheck(b, cudaMemcpy(h->ws + h->L.status, err, 4, cudaMemcpyHostToDevice), "cudaMemcpy(status)");
+        }
+        h->static_state = fits ? 1 : -1;
+        h->snodes_n = fits ? cnt[2 * (size_t)c] : 0;
+    }
+    if (rc != LBM_OK) return rc;
+    b->static_state = fits ? 1 : -1;
+    drop_graph(b);
+    return batch_tables(b);
 }
 
 void drop_graph(lbm_batch *b) {
@@ -1179,6 +1344,7 @@ int lbm_batch_init(const lbm_config *cfgs, int ncases, void *dev_ws, size_t ws_b
     b->item_off = BL.item_off;
     b->ctr_off = BL.ctr;
     b->span_case_off = BL.span_case;
+    b->swarp_off = BL.swarp_off;
     b->bin1 = BL.bin1;
     b->Q = cfgs[0].lattice;
     b->storage = cfgs[0].storage;
@@ -1189,6 +1355,9 @@ int lbm_batch_init(const lbm_config *cfgs, int ncases, void *dev_ws, size_t ws_b
     b->plain_chunk = kDefaultBatchPlainChunk;
     b->steps = 0;
     b->static_steps = 0;
+    b->static_state = 0;
+    b->graph_fixed = false;
+    b->total_swarps = 0;
     std::snprintf(b->err, sizeof(b->err), "no error");
     int rc = LBM_OK;
     int prio_low = 0, prio_high = 0;
@@ -1232,6 +1401,7 @@ int lbm_batch_set_particles(lbm_batch *b, int c, const lbm_particle *host, int n
     if (rc != LBM_OK) return bfail(b, rc, "case %d: %s", c, b->cases[c]->err);
     b->dirty = true;
     b->static_steps = 0;
+    b->static_state = 0;
     return LBM_OK;
 }
 
@@ -1246,19 +1416,34 @@ int lbm_batch_step(lbm_batch *b, int nsteps) {
         if (rc != LBM_OK) return rc;
         if (b->bin_items != items) drop_graph(b);
     }
-    // every particle of a batch is fixed, so after kStaticFlagSteps steps with
-    // the flag pass (both flag buffers and the per-brick solid marks then hold
-    // the flags) the steps leave it out; the static steps run as replays of
-    // one captured graph of kBatchGraphSteps steps, the remainder directly
+    // the steps run on `cap`, after everything issued on the caller's stream
+    // so far, and the caller's stream continues after them
+    rc = bcheck(b, cudaEventRecord(b->ev_pre, b->stream), "cudaEventRecord");
+    if (rc == LBM_OK) rc = bcheck(b, cudaStreamWaitEvent(b->cap, b->ev_pre, 0), "cudaStreamWaitEvent");
+    if (rc != LBM_OK) return rc;
+    // every particle of a batch is fixed: the first kStaticFlagSteps steps
+    // after particles are set run the flag pass (then both flag buffers and
+    // the per-brick solid marks hold the flags); the fixed geometry is then
+    // recorded once, and the later steps run the fixed-geometry sweep (or the
+    // brick sweeps without the flag pass, if it did not fit), as replays of
+    // one captured graph of kBatchGraphSteps steps and a direct remainder
     const int direct = std::min(nsteps, std::max(0, kStaticFlagSteps - b->static_steps));
+    if (direct > 0) rc = batch_issue(b, direct, true, false);
+    if (rc != LBM_OK) return rc;
+    if (direct < nsteps && b->static_state == 0) {
+        rc = batch_build_static(b, b->steps + direct);
+        if (rc != LBM_OK) return rc;
+    }
+    const bool fixed = b->static_state == 1;
     const int reps = (nsteps - direct) / kBatchGraphSteps;
     const int rest = (nsteps - direct) % kBatchGraphSteps;
+    if (reps > 0 && b->exec && b->graph_fixed != fixed) drop_graph(b);
     if (reps > 0 && !b->exec) {
         // replays read the step numbers from the device counters, so the same
         // graph serves every later call
         cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return bcheck(b, e, "cudaStreamBeginCapture");
-        const int rc_issue = batch_issue(b, kBatchGraphSteps, false);
+        const int rc_issue = batch_issue(b, kBatchGraphSteps, false, fixed);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(b->cap, &g);
         if (rc_issue != LBM_OK) {
@@ -1275,14 +1460,10 @@ int lbm_batch_step(lbm_batch *b, int nsteps) {
             return bcheck(b, e, "cudaGraphInstantiate");
         }
         b->graph_steps = kBatchGraphSteps;
+        b->graph_fixed = fixed;
     }
-    // the steps run on `cap`, after everything issued on the caller's stream
-    // so far, and the caller's stream continues after them
-    rc = bcheck(b, cudaEventRecord(b->ev_pre, b->stream), "cudaEventRecord");
-    if (rc == LBM_OK) rc = bcheck(b, cudaStreamWaitEvent(b->cap, b->ev_pre, 0), "cudaStreamWaitEvent");
-    if (rc == LBM_OK && direct > 0) rc = batch_issue(b, direct, true);
     for (int k = 0; k < reps && rc == LBM_OK; k++) rc = bcheck(b, cudaGraphLaunch(b->exec, b->cap), "cudaGraphLaunch");
-    if (rc == LBM_OK && rest > 0) rc = batch_issue(b, rest, false);
+    if (rc == LBM_OK && rest > 0) rc = batch_issue(b, rest, false, fixed);
     if (rc == LBM_OK) rc = bcheck(b, cudaEventRecord(b->ev_post, b->cap), "cudaEventRecord");
     if (rc == LBM_OK) rc = bcheck(b, cudaStreamWaitEvent(b->stream, b->ev_post, 0), "cudaStreamWaitEvent");
     if (rc != LBM_OK) return rc;

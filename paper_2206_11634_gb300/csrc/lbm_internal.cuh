@@ -32,7 +32,20 @@ constexpr int ROT_ITERS = 2;  // fixed-point sweeps of the implicit rotational h
 // Status words in the workspace.
 enum StatusSlot { ST_ERR = 0, ST_SLOTS = 16 };
 enum StepCounter { CNT_NREFILL = 0, CNT_NLINKS = 1, CNT_LISTED = 2, CNT_NEAR = 3 };
-enum ErrBits { ERRB_BRICK_OVERFLOW = 1, ERRB_DIVERGED = 2, ERRB_TIMEOUT = 4, ERRB_DEM_CAPACITY = 8 };
+enum ErrBits { ERRB_BRICK_OVERFLOW = 1, ERRB_DIVERGED = 2, ERRB_TIMEOUT = 4, ERRB_DEM_CAPACITY = 8,
+               ERRB_STATIC_CAPACITY = 16 };
+
+// A fluid node with particle links in a fixed geometry, and one of its links
+// (geometry of Eq. (27): q, lever arm from the centroid to x_w, u_w).
+struct StaticNode {
+    int n;          // node index
+    uint32_t mask;  // link directions (the unknowns)
+    int base;       // its first StaticLink
+};
+struct StaticLink {
+    float q, r[3], uw[3];
+    int jf;  // particle index in bits 0-15; bit 31: x_ff is a fluid node in the box
+};
 
 // Lattices stored below FP64 accumulate the per-particle force and torque
 // totals in 64-bit fixed point with integer atomics: exact and independent of
@@ -313,6 +326,16 @@ struct Params {
     long long bin_next_bytes;
     int *status;       // [ST_SLOTS], sticky error bits
     int *counters;     // per-step counters, zeroed with the brick lists
+    // fixed-geometry sweep (every particle fixed, lattices below FP64): built
+    // once by k_static_build, then every step runs k_static_plain over the
+    // nodes with sskip == 0 and k_static_links over the listed link nodes
+    uint8_t *sskip;             // [N] 1: solid node or fluid node with a particle link
+    struct StaticNode *snodes;  // [snode_cap] the fluid nodes with particle links
+    struct StaticLink *slinks;  // [slink_cap] their links, per node in direction order
+    int *scount;                // [2] nodes, links written by the build
+    unsigned long long *smf;    // [np][6] missing-force-point totals (fixed point, constant)
+    int snode_cap, slink_cap;
+    int snodes_n;               // link nodes (set by the host after the build)
 };
 
 __host__ __device__ __forceinline__ int dim_of(const Params &P, int a) { return a == 0 ? P.nx : (a == 1 ? P.ny : P.nz); }
@@ -579,6 +602,8 @@ struct BatchArgs {
                             // [2], [3] CTAs done in the last kernel of each (reset by the last)
     int g_chain;            // CTAs per case of the flag and near sweeps
     int plain_chunk;        // spans per CTA of the plain sweep
+    const int *swarp_off;   // [ncases + 1] prefix sums of the cases' link-node warps (>= 1 each;
+                            // fixed-geometry sweep)
 };
 
 // The case's Params for the current step into shared memory (all threads).
@@ -638,5 +663,11 @@ template <typename S> void launch_check_t(const Params &P, const void *f, const 
 template <typename S> void launch_flags_batch_t(const BatchArgs &B, int Q, cudaStream_t st);
 template <typename S> void launch_near_batch_t(const BatchArgs &B, int Q, bool force, cudaStream_t st);
 template <typename S> void launch_plain_batch_t(const BatchArgs &B, int Q, bool force, int grid, cudaStream_t st);
+template <typename S> void launch_static_build_t(const Params &P, cudaStream_t st);
+template <typename S> void launch_static_plain_t(const Params &P, cudaStream_t st);
+template <typename S> void launch_static_links_t(const Params &P, cudaStream_t st);
+template <typename S> void launch_static_plain_batch_t(const BatchArgs &B, int Q, bool force, int grid, cudaStream_t st);
+template <typename S> void launch_static_links_batch_t(const BatchArgs &B, int Q, bool force, int warps,
+                                                       cudaStream_t st);
 
 }  // namespace lbmmb

@@ -275,8 +275,9 @@ def test_three_steps_moving_geometry(pkg, oracle_mod, W, storage):
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_static_geometry_skips_flag_pass(pkg, oracle_mod, W, storage):
     """All particles fixed: from the fourth step on the flag pass is left out
-    (the flags cannot change), and five steps still agree with the oracle,
-    which classifies every step.  Setting the particles again (moved, still
+    (the flags cannot change) and, below FP64, the fixed-geometry sweep runs
+    (links and their geometry recorded once); five steps still agree with the
+    oracle, which classifies every step.  Setting the particles again (moved, still
     fixed) brings the pass back: the moved geometry's flags, refilled nodes
     and populations agree after two more steps.  Tolerances: those of one
     step, times the number of steps."""
@@ -290,7 +291,9 @@ def test_static_geometry_skips_flag_pass(pkg, oracle_mod, W, storage):
     for _ in range(5):
         gpu.step(1)
         orc.step(1)
-    assert gpu.kernels_per_step() == k_full - 1
+    # FP64: the brick sweeps without the flag pass; below FP64 the
+    # fixed-geometry sweep (its link and plain kernels)
+    assert gpu.kernels_per_step() == (k_full - 1 if storage == "f64" else 2)
     own = orc.owner()
     assert np.array_equal(gpu.flags().cpu().numpy() - 1, own)
     err = np.abs(gpu.populations().cpu().numpy() - orc.populations())[:, own < 0].max()
@@ -317,6 +320,28 @@ def test_static_geometry_skips_flag_pass(pkg, oracle_mod, W, storage):
     assert np.array_equal(gpu.flags().cpu().numpy() - 1, own)
     err = np.abs(gpu.populations().cpu().numpy() - orc.populations())[:, own < 0].max()
     assert err <= 7 * POP_TOL[storage], err
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("case", ["touching", "multi", "wrap"])
+def test_fixed_geometry_sweep_same_bits(pkg, W, case, storage):
+    """The fixed-geometry sweep (every particle fixed, from the fourth step)
+    and the brick sweeps (the same particles not fixed, with no DEM
+    sub-steps, so they do not move either) run the same arithmetic: after
+    ten steps populations and force/torque totals are bit-identical."""
+    wl = _case(W, case)
+    runs = []
+    for fixed in (1, 0):
+        for p in wl["particles"]:
+            p["fixed"] = fixed
+        gpu = H.make_gpu(pkg, wl, storage=storage, n_sub=0)
+        gpu.set_particles(H.gpu_particles(pkg, wl))
+        gpu.step(10)
+        runs.append((gpu.populations().cpu().numpy(), *gpu.forces(), gpu.kernels_per_step()))
+    (f1, F1, T1, k1), (f0, F0, T0, k0) = runs
+    assert k1 == 2 and k0 == 4, (k1, k0)
+    assert np.array_equal(f1, f0)
+    assert np.array_equal(F1, F0) and np.array_equal(T1, T0)
 
 
 def test_settling_sphere_trajectory_fp64(pkg, oracle_mod, W):
