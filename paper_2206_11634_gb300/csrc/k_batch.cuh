@@ -49,9 +49,22 @@ __global__ void __launch_bounds__(BRICK, 4) k_sweep_plain_batch(BatchArgs B) {
     const Params *row = B.tab + (size_t)(step & 1) * B.ncases;
     const int g0 = blockIdx.x * B.plain_chunk;
     const int g1 = min(total, g0 + B.plain_chunk);
+    // the case's parameters in shared memory (re-read when the CTA's spans
+    // cross into the next case): loads from there cannot alias the stores to
+    // the populations, so they stay in registers
+    __shared__ Params sP;
+    int cur = -1;
     for (int g = g0; g < g1; g++) {
         const int c = B.span_case[g];
-        const Params &P = row[c];
+        if (c != cur) {
+            __syncthreads();
+            const int *src = reinterpret_cast<const int *>(row + c);
+            int *dst = reinterpret_cast<int *>(&sP);
+            for (int k = threadIdx.x; k < (int)(sizeof(Params) / 4); k += blockDim.x) dst[k] = src[k];
+            __syncthreads();
+            cur = c;
+        }
+        const Params &P = sP;
         const int n = (g - B.span_off[c]) * BRICK + (int)threadIdx.x;
         if (n >= P.N) continue;
         const int nxy = P.nx * P.ny;
