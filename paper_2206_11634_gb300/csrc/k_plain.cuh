@@ -12,15 +12,14 @@
 
 namespace lbmmb {
 
-// Collide one node and store it: moments (Eq. (18)) with the half-force
-// shift, BGK toward f^eq (Eqs. (15)-(16)) plus Guo's forcing term (compiled
-// out when the body force is zero).
-template <typename S, int Q, bool kForce, bool kStream = false>
-__device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>::C (&fin)[Q], S *B, long long N,
-                                              int n) {
+// Collide one node: moments (Eq. (18)) with the half-force shift, BGK toward
+// f^eq (Eqs. (15)-(16)) plus Guo's forcing term (compiled out when the body
+// force is zero); out receives the post-collision offsets.
+template <typename S, int Q, bool kForce>
+__device__ __forceinline__ void collide_values(const Params &P, const typename Codec<S>::C (&fin)[Q],
+                                               typename Codec<S>::C (&out)[Q]) {
     using L = Lat<Q>;
-    using Cd = Codec<S>;
-    using C = typename Cd::C;
+    using C = typename Codec<S>::C;
     const C rho0 = Prm<C>::rho0(P);
     // offsets: rho = rho0 + sum g, momentum = sum g e
     C drho = 0, mx = 0, my = 0, mz = 0;
@@ -48,15 +47,32 @@ __device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>
         const C eu = ex * ux + ey * uy + ez * uz;
         // omega g^eq = w (omega drho + omega rho (3 eu + 4.5 eu^2 - 1.5 uu))
         const C geq_om = w * (om_drho + om_rho * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu));
-        C out = fin[i] - omega * fin[i] + geq_om;
+        C o = fin[i] - omega * fin[i] + geq_om;
         if (kForce) {
             const C gfac = Prm<C>::gfac(P);
             const C uF = ux * Fx + uy * Fy + uz * Fz;
             const C eF = ex * Fx + ey * Fy + ez * Fz;
-            out += gfac * w * (C(3) * (eF - uF) + C(9) * eu * eF);
+            o += gfac * w * (C(3) * (eF - uF) + C(9) * eu * eF);
         }
-        if (kStream) Cd::st_s(B + (long long)i * N + n, out, w, rho0);
-        else Cd::st(B + (long long)i * N + n, out, w, rho0);
+        out[i] = o;
+    }
+}
+
+// Collide one node and store it.
+template <typename S, int Q, bool kForce, bool kStream = false>
+__device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>::C (&fin)[Q], S *B, long long N,
+                                              int n) {
+    using L = Lat<Q>;
+    using Cd = Codec<S>;
+    using C = typename Cd::C;
+    const C rho0 = Prm<C>::rho0(P);
+    C out[Q];
+    collide_values<S, Q, kForce>(P, fin, out);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const C w = (C)L::w(i);
+        if (kStream) Cd::st_s(B + (long long)i * N + n, out[i], w, rho0);
+        else Cd::st(B + (long long)i * N + n, out[i], w, rho0);
     }
 }
 

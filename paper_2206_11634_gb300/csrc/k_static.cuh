@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(BRICK, 4) k_static_plain(Params P) {
 }
 
 // ---------------------------------------------------------------------------
-// link nodes: one warp per 32 listed link nodes
+// link nodes: one warp per kStaticNodesPerWarp listed link nodes
 // ---------------------------------------------------------------------------
 constexpr int kStaticSlots = 4;  // particles per warp with shared-memory force sums
 struct StaticScratch {
@@ -271,8 +271,8 @@ __device__ __forceinline__ void static_links_warp(const Params &P, StaticScratch
     const C rho0 = Prm<C>::rho0(P);
     if (lane < kStaticSlots) ss.ids[warp][lane] = -1;
     for (int e = lane; e < kStaticSlots * 6; e += 32) ss.fix[warp][e / 6][e % 6] = 0ull;
-    const int idx = wg * 32 + lane;
-    const bool has = idx < P.snodes_n;
+    const int idx = wg * kStaticNodesPerWarp + lane;
+    const bool has = lane < kStaticNodesPerWarp && idx < P.snodes_n;
     StaticNode sn;
     sn.n = 0;
     sn.mask = 0u;
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(BRICK, kNearCtasPerSm) k_static_links(Params P
     if (sizeof(typename Codec<S>::C) == 8) return;
     __shared__ StaticScratch ss;
     if (blockIdx.x == 0 && threadIdx.x == 0) static_constants(P);
-    const int warps = (P.snodes_n + 31) / 32;
+    const int warps = (P.snodes_n + kStaticNodesPerWarp - 1) / kStaticNodesPerWarp;
     for (int wg = blockIdx.x * (BRICK / 32) + (threadIdx.x >> 5); wg < warps; wg += gridDim.x * (BRICK / 32))
         static_links_warp<S, Q, kForce>(P, ss, wg);
 }
@@ -370,8 +370,8 @@ __global__ void __launch_bounds__(BRICK, 4) k_static_plain_batch(BatchArgs B) {
     const int g0 = blockIdx.x * B.plain_chunk;
     const int g1 = min(total, g0 + B.plain_chunk);
     // the case's parameters in shared memory (re-read when the CTA's spans
-    // cross into the next case): loads from there cannot alias the stores to
-    // the populations, so they stay in registers
+    // cross into the next case): loads from there cannot alias the stores
+    // to the populations, so they stay in registers
     __shared__ Params sP;
     int cur = -1;
     for (int g = g0; g < g1; g++) {
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(BRICK, 4) k_static_plain_batch(BatchArgs B) {
     advance_step_when_last(B.ctr + 3, B.ctr + 1);
 }
 
-// One warp per 32 link nodes of a case (each case at least one warp, whose
+// One warp per kStaticNodesPerWarp link nodes of a case (each case at least one warp, whose
 // first also adds the case's constant parts); the last CTA advances the
 // particle chain's step counter.
 template <typename S, int Q, bool kForce>
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(BRICK, kNearCtasPerSm) k_static_links_batch(Ba
         const Params &P = row[lo];
         const int wl = gw - B.swarp_off[lo];
         if (wl == 0 && (threadIdx.x & 31) == 0) static_constants(P);
-        if (wl * 32 < P.snodes_n) static_links_warp<S, Q, kForce>(P, ss, wl);
+        if (wl * kStaticNodesPerWarp < P.snodes_n) static_links_warp<S, Q, kForce>(P, ss, wl);
     }
     advance_step_when_last(B.ctr + 2, B.ctr);
 }

@@ -119,7 +119,7 @@ void launch_static_plain_t(const Params &P, cudaStream_t st) {
 template <typename S>
 void launch_static_links_t(const Params &P, cudaStream_t st) {
     const bool force = P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0;
-    const int warps = (P.snodes_n + 31) / 32;
+    const int warps = (P.snodes_n + kStaticNodesPerWarp - 1) / kStaticNodesPerWarp;
     const int cap = kNearCtasPerSm * kSmCount;
     int grid = (warps + BRICK / 32 - 1) / (BRICK / 32);
     grid = grid < 1 ? 1 : (grid > cap ? cap : grid);

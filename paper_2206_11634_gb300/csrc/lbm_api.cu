@@ -1144,7 +1144,7 @@ int batch_tables(lbm_batch *b) {
         h->fcur = keep_fcur;
         soff[c + 1] = soff[c] + (int)((h->L.N + BRICK - 1) / BRICK);
         // link-node warps of the fixed-geometry sweep, at least one per case
-        woff[c + 1] = woff[c] + std::max(1, (h->snodes_n + 31) / 32);
+        woff[c + 1] = woff[c] + std::max(1, (h->snodes_n + kStaticNodesPerWarp - 1) / kStaticNodesPerWarp);
         ioff[c + 1] = ioff[c] + (h->np > 0 ? h->np : 1);
     }
     b->total_spans = soff[b->n];

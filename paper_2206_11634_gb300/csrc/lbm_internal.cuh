@@ -46,6 +46,10 @@ struct StaticLink {
     float q, r[3], uw[3];
     int jf;  // particle index in bits 0-15; bit 31: x_ff is a fluid node in the box
 };
+// Link nodes per warp of the fixed-geometry link kernel: few, so that a
+// warp's lanes evaluate its links in about one round (a link node has a few
+// links) and small cases spread over many warps.
+constexpr int kStaticNodesPerWarp = 8;
 
 // Lattices stored below FP64 accumulate the per-particle force and torque
 // totals in 64-bit fixed point with integer atomics: exact and independent of
