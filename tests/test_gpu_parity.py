@@ -344,6 +344,23 @@ def test_fixed_geometry_sweep_same_bits(pkg, W, case, storage):
     assert np.array_equal(F1, F0) and np.array_equal(T1, T0)
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("case", ["periodic_empty", "walls_guo_ragged"])
+def test_empty_lattice_fixed_geometry_steps(pkg, oracle_mod, W, case, storage):
+    """No particles (a fixed geometry with no links): from the fourth step
+    the fixed-geometry sweep runs every node through its plain kernel; six
+    steps agree with the oracle (one-step tolerance times the steps)."""
+    wl = _case(W, case)
+    gpu = H.make_gpu(pkg, wl, storage=storage)
+    orc = H.make_oracle(oracle_mod, wl)
+    _sync_populations(gpu, orc, np.random.default_rng(6))
+    gpu.step(6)
+    orc.step(6)
+    assert gpu.kernels_per_step() == 2
+    err = np.abs(gpu.populations().cpu().numpy() - orc.populations()).max()
+    assert err <= 6 * POP_TOL[storage], err
+
+
 def test_settling_sphere_trajectory_fp64(pkg, oracle_mod, W):
     """Workload 1 (sphere of §3.1 geometry, FP64), 12 steps with 100 DEM
     sub-steps each: particle state, force and populations agree."""
