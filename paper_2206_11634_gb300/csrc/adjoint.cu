@@ -247,28 +247,28 @@ __device__ __noinline__ float link_value(const AdjDev &D, const float *__restric
 __device__ __forceinline__ void gather(const AdjDev &D, const float *__restrict__ S, int x, int y, int z, long long n,
                                        uint32_t lm, float gin[Q]) {
     const AdjConst &A = D.c;
-    const long long N = A.N;
-    float drho_f = 0.f, mf[3] = {0.f, 0.f, 0.f};
-    if (lm) {
-#pragma unroll
-        for (int k = 0; k < Q; k++) {
-            const float g = S[(long long)k * N + n];
-            drho_f += g;
-            mf[0] += g * L19::e(k, 0);
-            mf[1] += g * L19::e(k, 1);
-            mf[2] += g * L19::e(k, 2);
-        }
-    }
+    const int N = (int)A.N;  // fewer than 2^31 nodes
+    // every pull is issued at once (on a link direction its value is replaced
+    // below), so the loads do not wait for the link mask
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        if ((lm >> i) & 1u) {
-            gin[i] = link_value(D, S, n, i, drho_f, mf[0], mf[1], mf[2]);
-        } else {
-            const int sx = wrapi(x - L19::e(i, 0), A.nx), sy = wrapi(y - L19::e(i, 1), A.ny),
-                      sz = wrapi(z - L19::e(i, 2), A.nz);
-            gin[i] = S[(long long)i * N + sx + (long long)A.nx * (sy + (long long)A.ny * sz)];
-        }
+        const int sx = wrapi(x - L19::e(i, 0), A.nx), sy = wrapi(y - L19::e(i, 1), A.ny),
+                  sz = wrapi(z - L19::e(i, 2), A.nz);
+        gin[i] = S[(long long)i * N + (sx + A.nx * (sy + A.ny * sz))];
     }
+    if (!lm) return;
+    float drho_f = 0.f, mf[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < Q; k++) {
+        const float g = S[(long long)k * N + n];
+        drho_f += g;
+        mf[0] += g * L19::e(k, 0);
+        mf[1] += g * L19::e(k, 1);
+        mf[2] += g * L19::e(k, 2);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; i++)
+        if ((lm >> i) & 1u) gin[i] = link_value(D, S, n, i, drho_f, mf[0], mf[1], mf[2]);
 }
 
 // Node of this thread: CTA = 32 x 4 x 2 nodes
@@ -329,10 +329,13 @@ __global__ void __launch_bounds__(256) k_adj_step(AdjDev D, const float *__restr
     const AdjConst &A = D.c;
     int x, y, z;
     long long n;
-    const bool act = node_of(A, x, y, z, n) && !D.solid[n];
+    const bool in = node_of(A, x, y, z, n);
+    // the node's solid mark and link mask in one round
+    const bool solid = in ? D.solid[n] != 0 : true;
+    const uint32_t lm = in ? D.lmask[n] : 0u;
+    const bool act = in && !solid;
     float Fx = 0.f;
     if (act) {
-        const uint32_t lm = D.lmask[n];
         float gin[Q];
         gather(D, S, x, y, z, n, lm, gin);
         if (window && lm) {
@@ -370,8 +373,10 @@ __global__ void __launch_bounds__(256, 3) k_adj_bgk(AdjDev D, const float *__res
     const AdjConst &A = D.c;
     int x, y, z;
     long long n;
-    if (!node_of(A, x, y, z, n) || D.solid[n]) return;
-    const uint32_t lm = D.lmask[n];
+    if (!node_of(A, x, y, z, n)) return;
+    const bool solid = D.solid[n] != 0;
+    const uint32_t lm = D.lmask[n];  // with the solid mark, in one round
+    if (solid) return;
     float gin[Q];
     gather(D, S, x, y, z, n, lm, gin);
     float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
@@ -413,8 +418,10 @@ __global__ void __launch_bounds__(256) k_adj_pull(AdjDev D, const float *__restr
 #pragma unroll
     for (int k = 0; k < Q; k++) {
         const int tx = wrapi(x + L19::e(k, 0), A.nx), ty = wrapi(y + L19::e(k, 1), A.ny), tz = wrapi(z + L19::e(k, 2), A.nz);
-        const long long t = tx + (long long)A.nx * (ty + (long long)A.ny * tz);
-        acc[k] = D.solid[t] ? 0.f : lamIn[(long long)k * A.N + t];
+        const int t = tx + A.nx * (ty + A.ny * tz);
+        // the neighbour's value and its solid mark in one round
+        const float v = lamIn[(long long)k * A.N + t];
+        acc[k] = D.solid[t] ? 0.f : v;
     }
     const uint32_t lm = D.lmask[n];
     if (lm) {
