@@ -204,6 +204,17 @@ int lbm_get_counters(lbm_handle *h, int64_t *steps, int32_t *nrefill, int32_t *n
  * it.  Defaults: 0 and 0 (one plain CTA per brick, 4 flag/near CTAs per SM). */
 int lbm_set_schedule(lbm_handle *h, int plain_ctas_per_sm, int chain_ctas_per_sm);
 
+/* Whether the plain sweep issues a brick's 19 pulls before it has read that
+ * brick's entry of the near set (the near sweep takes the brick when it is
+ * there; its pulls are then wasted).  That removes one dependent load from
+ * the start of every plain CTA, at the cost of the reads of the near bricks,
+ * and puts more loads in flight, which also slows the latency-bound particle
+ * kernels running beside the sweep.  mode 1: always, 0: never, -1 (default):
+ * when the particles' search boxes cover under a tenth of the bricks,
+ * estimated at lbm_set_particles().  Takes effect from the next lbm_step();
+ * results do not depend on it.  LBM_ERR_BAD_ARG for another mode. */
+int lbm_set_plain_speculation(lbm_handle *h, int mode);
+
 /* Kernels launched per lbm_step() step (for launch accounting). */
 int lbm_kernels_per_step(const lbm_handle *h);
 
@@ -217,6 +228,12 @@ int lbm_kernels_per_step(const lbm_handle *h);
  * are created on the host side of the CUDA runtime (no device memory is
  * allocated). */
 int lbm_profile(lbm_handle *h, int enable);
+/* As lbm_profile(), recording only the kernels whose bit is set in mask (bit
+ * k: kernel k above); 0 stops recording.  The event records on the stream of
+ * the particle chain lengthen a step by a few microseconds each, so a caller
+ * timing whole steps records the plain sweep (bit 2, its own stream) alone.
+ * LBM_ERR_BAD_ARG for bits beyond kernel 5. */
+int lbm_profile_mask(lbm_handle *h, unsigned mask);
 int lbm_profile_read(lbm_handle *h, int kernel, double *total_ms, int64_t *launches);
 
 /* Change the stream later work is issued on. */

@@ -71,6 +71,13 @@ __global__ void __launch_bounds__(BRICK, 4) k_sweep_plain_batch(BatchArgs B) {
         const int z = n / nxy, r = n - z * nxy;
         const int y = r / P.nx, x = r - y * P.nx;
         const int b = x / BX + P.nbx * (y / BY + P.nby * (z / BZ));
+        if (P.plain_spec) {  // pulls issued with the skip entry (see plain_brick)
+            const bool skipped = P.skip[(step % 3) * P.nbricks + b] == (int)step;
+            typename Codec<S>::C fin[Q];
+            plain_pull<S, Q, true>(P, x, y, z, n, fin);
+            if (!skipped) collide_store<S, Q, kForce, true>(P, fin, (S *)P.fB, P.N, n);
+            continue;
+        }
         if (P.skip[(step % 3) * P.nbricks + b] == (int)step) continue;  // the near sweep takes it
         plain_node<S, Q, kForce, true>(P, x, y, z, n);
     }

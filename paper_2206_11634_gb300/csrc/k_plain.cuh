@@ -12,6 +12,27 @@
 
 namespace lbmmb {
 
+// e . v over the nonzero components of a lattice direction, taken in x, y, z
+// order.  The zero components are left out rather than multiplied: x * 0 is
+// not folded away under IEEE rules, and for D3Q19 that is 27 of the 57 terms
+// of each sum over directions.  The sum is the same (up to the sign of a zero
+// result) as e_x v_x + e_y v_y + e_z v_z evaluated left to right.
+template <typename C>
+__device__ __forceinline__ C dot_e(int ex, int ey, int ez, C vx, C vy, C vz) {
+    C s = C(0);
+    bool any = false;
+    if (ex != 0) { s = ex > 0 ? vx : -vx; any = true; }
+    if (ey != 0) { s = any ? (ey > 0 ? s + vy : s - vy) : (ey > 0 ? vy : -vy); any = true; }
+    if (ez != 0) { s = any ? (ez > 0 ? s + vz : s - vz) : (ez > 0 ? vz : -vz); }
+    return s;
+}
+
+// acc + e v for a component e in {-1, 0, 1}
+template <typename C>
+__device__ __forceinline__ C add_e(C acc, int e, C v) {
+    return e > 0 ? acc + v : (e < 0 ? acc - v : acc);
+}
+
 // Collide one node: moments (Eq. (18)) with the half-force shift, BGK toward
 // f^eq (Eqs. (15)-(16)) plus Guo's forcing term (compiled out when the body
 // force is zero); out receives the post-collision offsets.
@@ -26,9 +47,9 @@ __device__ __forceinline__ void collide_values(const Params &P, const typename C
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         drho += fin[i];
-        mx += fin[i] * L::e(i, 0);
-        my += fin[i] * L::e(i, 1);
-        mz += fin[i] * L::e(i, 2);
+        mx = add_e(mx, L::e(i, 0), fin[i]);
+        my = add_e(my, L::e(i, 1), fin[i]);
+        mz = add_e(mz, L::e(i, 2), fin[i]);
     }
     const C rho = rho0 + drho;
     const C Fx = kForce ? Prm<C>::F(P, 0) : C(0), Fy = kForce ? Prm<C>::F(P, 1) : C(0),
@@ -44,14 +65,14 @@ __device__ __forceinline__ void collide_values(const Params &P, const typename C
     for (int i = 0; i < Q; i++) {
         const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
         const C w = (C)L::w(i);
-        const C eu = ex * ux + ey * uy + ez * uz;
+        const C eu = dot_e(ex, ey, ez, ux, uy, uz);
         // omega g^eq = w (omega drho + omega rho (3 eu + 4.5 eu^2 - 1.5 uu))
         const C geq_om = w * (om_drho + om_rho * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu));
         C o = fin[i] - omega * fin[i] + geq_om;
         if (kForce) {
             const C gfac = Prm<C>::gfac(P);
             const C uF = ux * Fx + uy * Fy + uz * Fz;
-            const C eF = ex * Fx + ey * Fy + ez * Fz;
+            const C eF = dot_e(ex, ey, ez, Fx, Fy, Fz);
             o += gfac * w * (C(3) * (eF - uF) + C(9) * eu * eF);
         }
         out[i] = o;
@@ -91,7 +112,11 @@ __device__ __forceinline__ void neighbour_coords(const Params &P, int x, int y, 
 
 // The pull of a node no particle link reaches: f_i from x - e_i, halfway
 // bounce-back at walls (the node's own opposite population).  No flags are
-// read.  Node indices are 32-bit (the lattice holds fewer than 2^31 nodes).
+// read.  A row off the y and z faces (one warp of a brick) takes the source
+// n - e_i . (1, nx, nx ny) as a 32-bit index, corrected only on its two
+// x-face lanes (wrap or bounce-back); other rows, and lattices whose
+// population indices need more than 31 bits, resolve each neighbour's
+// coordinates.
 template <typename S, int Q, bool kStream>
 __device__ __forceinline__ void plain_pull(const Params &P, int x, int y, int z, int n,
                                            typename Codec<S>::C (&fin)[Q]) {
@@ -99,8 +124,25 @@ __device__ __forceinline__ void plain_pull(const Params &P, int x, int y, int z,
     using Cd = Codec<S>;
     using C = typename Cd::C;
     const S *A = (const S *)P.fA;
-    const long long N = P.N;
     const C rho0 = Prm<C>::rho0(P);
+    if (P.idx32 && y > 0 && y < P.ny - 1 && z > 0 && z < P.nz - 1) {
+        const int N = (int)P.N, nx = P.nx, nxy = P.nx * P.ny;
+        int cm = 0, cp = 0;        // source x - 1 (e_x = +1) and x + 1 (e_x = -1) wrapped
+        bool wm = false, wp = false;  // ... or beyond a wall
+        if (x == 0) { if (P.per[0]) cm = nx; else wm = true; }
+        if (x == nx - 1) { if (P.per[0]) cp = -nx; else wp = true; }
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const int ex = L::e(i, 0);
+            int idx = i * N + n - (ex + nx * L::e(i, 1) + nxy * L::e(i, 2));
+            if (ex > 0) idx = wm ? L::opp(i) * N + n : idx + cm;
+            if (ex < 0) idx = wp ? L::opp(i) * N + n : idx + cp;
+            const S *src = A + (unsigned)idx;
+            fin[i] = kStream ? Cd::ld_s(src, (C)L::w(i), rho0) : Cd::ld(src, (C)L::w(i), rho0);
+        }
+        return;
+    }
+    const long long N = P.N;
     int xs[3], ys[3], zs[3];
     neighbour_coords(P, x, y, z, xs, ys, zs);
     int row[3][3];  // nx * (y' + ny * z') for the neighbour rows
@@ -128,14 +170,27 @@ __device__ __forceinline__ void plain_node(const Params &P, int x, int y, int z,
 
 // The sweep of every brick outside this step's predicted near set: the plain
 // path only.  Runs on its own stream, concurrently with the particle kernels.
+// With few near bricks expected (plain_spec) the pulls are issued together
+// with the brick's skip entry and only the stores wait for it, so a CTA does
+// not start with a lone dependent load; a skipped brick then costs its reads.
 template <typename S, int Q, bool kForce>
 __device__ __forceinline__ void plain_brick(const Params &P, int b) {
-    if (P.skip && P.skip[(P.step % 3) * P.nbricks + b] == P.step) return;  // the near sweep takes it
     const int tid = threadIdx.x;
     int bxi, byi, bzi;
     brick_coords(P, b, bxi, byi, bzi);
     const int x = bxi * BX + tid % BX, y = byi * BY + (tid / BX) % BY, z = bzi * BZ + tid / (BX * BY);
-    if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce, true>(P, x, y, z, x + P.nx * (y + P.ny * z));
+    const bool inside = x < P.nx && y < P.ny && z < P.nz;
+    const int n = x + P.nx * (y + P.ny * z);
+    if (P.plain_spec) {
+        const bool skipped = P.skip && P.skip[(P.step % 3) * P.nbricks + b] == P.step;
+        if (!inside) return;
+        typename Codec<S>::C fin[Q];
+        plain_pull<S, Q, true>(P, x, y, z, n, fin);
+        if (!skipped) collide_store<S, Q, kForce, true>(P, fin, (S *)P.fB, P.N, n);
+        return;
+    }
+    if (P.skip && P.skip[(P.step % 3) * P.nbricks + b] == P.step) return;  // the near sweep takes it
+    if (inside) plain_node<S, Q, kForce, true>(P, x, y, z, n);
 }
 template <typename S, int Q, bool kForce>
 __global__ void __launch_bounds__(BRICK, 4) k_sweep_plain(Params P) {

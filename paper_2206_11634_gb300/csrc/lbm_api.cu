@@ -160,7 +160,7 @@ struct lbm_handle {
     cudaStream_t aux, hi;
     cudaEvent_t ev_fork, ev_bin, ev_plain, ev_near, ev_join;
     // kernel timing (lbm_profile): event pairs per kernel, in launch order
-    bool prof;
+    unsigned prof;  // kernels whose launches are bracketed by events (bit k: kernel k)
     std::vector<cudaEvent_t> ev[kProfKernels][2];
     int64_t nrec[kProfKernels];
     Layout L;
@@ -177,6 +177,8 @@ struct lbm_handle {
     int snodes_n;      // its link nodes
     int nsm;       // SMs of the device
     int plain_per_sm, chain_per_sm;  // launch schedule (lbm_set_schedule)
+    int plain_spec;       // the particles' search boxes cover under a tenth of the bricks (set_particles)
+    int plain_spec_mode;  // lbm_set_plain_speculation: -1 auto (plain_spec), 0 off, 1 on
     int64_t steps;
     char err[256];
 };
@@ -257,6 +259,8 @@ Params make_params(lbm_handle *h) {
     P.fc_valid = h->fc_valid;
     P.plain_grid = h->plain_per_sm > 0 ? h->plain_per_sm * h->nsm : 0;
     P.chain_grid = h->chain_per_sm > 0 ? h->chain_per_sm * h->nsm : 0;
+    P.plain_spec = h->plain_spec_mode >= 0 ? h->plain_spec_mode : h->plain_spec;
+    P.idx32 = (long long)c.lattice * (long long)c.nx * c.ny * c.nz <= 0x7fffffffLL;
     P.status = at<int>(h, h->L.status);
     P.counters = at<int>(h, h->L.bin + (size_t)h->L.nbricks * 4);
     P.force_fixed = h->cfg.storage != LBM_STORE_F64;
@@ -472,7 +476,7 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
     h->static_steps = 0;
     h->static_state = 0;
     h->snodes_n = 0;
-    h->prof = false;
+    h->prof = 0u;
     for (int k = 0; k < kProfKernels; k++) h->nrec[k] = 0;
     std::snprintf(h->err, sizeof(h->err), "no error");
     // everything but the populations starts at zero: all nodes fluid, no
@@ -487,6 +491,8 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
         if (h->nsm <= 0) h->nsm = 1;
         h->plain_per_sm = kDefaultPlainPerSm;
         h->chain_per_sm = kDefaultChainPerSm;
+        h->plain_spec = 1;
+        h->plain_spec_mode = -1;
     }
     int rc = LBM_OK;
     if (own_streams) {
@@ -535,6 +541,30 @@ extern "C" {
 
 int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_stream, lbm_handle **out) {
     return init_handle(cfg, dev_ws, ws_bytes, cuda_stream, true, out);
+}
+
+// Whether the plain sweep may issue its pulls before it knows if the near
+// sweep takes the brick: worth it when the near set is a small share of the
+// bricks (its pulls are then wasted on few bricks), not when many particles
+// fill the box.  Estimated from each particle's bounding sphere (control
+// points, the radius where M falls to c0, Rs) plus two nodes of margin,
+// counted in whole bricks.
+static int plain_speculates(const lbm_config &c, const lbm_particle *host, int n) {
+    const int nbx = (c.nx + BX - 1) / BX, nby = (c.ny + BY - 1) / BY, nbz = (c.nz + BZ - 1) / BZ;
+    const double nbricks = (double)nbx * nby * nbz;
+    double near = 0.0;
+    for (int j = 0; j < n; j++) {
+        const lbm_particle &p = host[j];
+        double Ks = 0.0, rmax = 0.0;
+        for (int k = 0; k < p.n_cp; k++) {
+            Ks += p.K[k];
+            rmax = std::fmax(rmax, std::sqrt(p.cp[k][0] * p.cp[k][0] + p.cp[k][1] * p.cp[k][1] + p.cp[k][2] * p.cp[k][2]));
+        }
+        const double d = 2.0 * (rmax + std::sqrt(Ks / c.c0) + p.Rs + 2.0);
+        near += std::fmin(std::ceil(d / BX) + 1, nbx) * std::fmin(std::ceil(d / BY) + 1, nby) *
+                std::fmin(std::ceil(d / BZ) + 1, nbz);
+    }
+    return near < 0.1 * nbricks ? 1 : 0;
 }
 
 int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
@@ -650,6 +680,7 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
     h->all_fixed = 1;
     for (int j = 0; j < n; j++)
         if (!host[j].fixed) h->all_fixed = 0;
+    h->plain_spec = plain_speculates(h->cfg, host, n);
     h->static_steps = 0;
     h->static_state = 0;
     h->snodes_n = 0;
@@ -663,7 +694,7 @@ struct ProfScope {
     bool on;
     cudaStream_t st;
     ProfScope(lbm_handle *h_, int k_, bool launched, cudaStream_t st_)
-        : h(h_), k(k_), on(h_->prof && launched && h_->nrec[k_] < kProfCap), st(st_) {
+        : h(h_), k(k_), on(((h_->prof >> k_) & 1u) && launched && h_->nrec[k_] < kProfCap), st(st_) {
         if (!on) return;
         const size_t i = (size_t)h->nrec[k];
         if (h->ev[k][0].size() <= i) {
@@ -961,7 +992,18 @@ int lbm_profile(lbm_handle *h, int enable) {
     cudaStreamSynchronize(h->aux);
     cudaStreamSynchronize(h->hi);
     release_profile(h);
-    h->prof = enable != 0;
+    h->prof = enable != 0 ? (1u << kProfKernels) - 1u : 0u;
+    return LBM_OK;
+}
+
+int lbm_profile_mask(lbm_handle *h, unsigned mask) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    if (mask >> kProfKernels) return fail(h, LBM_ERR_BAD_ARG, "mask has bits beyond the %d kernels", kProfKernels);
+    cudaStreamSynchronize(h->stream);
+    cudaStreamSynchronize(h->aux);
+    cudaStreamSynchronize(h->hi);
+    release_profile(h);
+    h->prof = mask;
     return LBM_OK;
 }
 
@@ -989,6 +1031,13 @@ int lbm_set_schedule(lbm_handle *h, int plain_ctas_per_sm, int chain_ctas_per_sm
         return fail(h, LBM_ERR_BAD_ARG, "CTAs per SM must be in 0..4");
     h->plain_per_sm = plain_ctas_per_sm;
     h->chain_per_sm = chain_ctas_per_sm;
+    return LBM_OK;
+}
+
+int lbm_set_plain_speculation(lbm_handle *h, int mode) {
+    if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
+    if (mode < -1 || mode > 1) return fail(h, LBM_ERR_BAD_ARG, "mode must be -1, 0 or 1");
+    h->plain_spec_mode = mode;
     return LBM_OK;
 }
 

@@ -269,6 +269,8 @@ struct Params {
     int q_exact;              // link fraction by Newton on Eq. (26) instead of Eq. (27)
     int plain_grid;           // CTAs of k_sweep_plain (0: one per brick)
     int chain_grid;           // CTAs of the persistent k_flags / k_sweep_near (0: default)
+    int plain_spec;           // few near bricks expected: the plain sweep pulls before its skip entry arrives
+    int idx32;                // Q N < 2^31: population indices fit 32 bits
     int dem_f32;              // DEM in FP32 with compensated state (k_dem32)
     int fc_valid;             // Fc/Tc hold the contact load of the current state (0 after set_particles)
     double tau, rho0, c0;

@@ -75,9 +75,11 @@ _SIGS = {
                                    C.POINTER(C.c_int32)]),
     "lbm_kernels_per_step": (C.c_int, [C.c_void_p]),
     "lbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_profile_mask": (C.c_int, [C.c_void_p, C.c_uint]),
     "lbm_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "lbm_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "lbm_set_plain_speculation": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_batch_workspace_size": (C.c_int, [C.POINTER(LbmConfig), C.c_int, C.POINTER(C.c_size_t)]),
     "lbm_batch_init": (C.c_int, [C.POINTER(LbmConfig), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
                                  C.POINTER(C.c_void_p)]),
@@ -253,6 +255,11 @@ class Lattice:
     def set_schedule(self, plain_ctas_per_sm: int, chain_ctas_per_sm: int) -> None:
         self._ok(self.L.lbm_set_schedule(self.h, int(plain_ctas_per_sm), int(chain_ctas_per_sm)), self.h)
 
+    def set_plain_speculation(self, mode: int) -> None:
+        """1: the plain sweep pulls before reading its near-set entry, 0: after,
+        -1: chosen from the particles' extent (lbm_set_plain_speculation)."""
+        self._ok(self.L.lbm_set_plain_speculation(self.h, int(mode)), self.h)
+
     def kernels_per_step(self) -> int:
         return self.L.lbm_kernels_per_step(self.h)
 
@@ -291,8 +298,16 @@ class Lattice:
 
     KERNELS = ("k_bin", "k_flags", "k_sweep_plain", "k_sweep_near", "k_force_reduce", "k_dem")
 
-    def profile(self, enable: bool = True) -> None:
-        self._ok(self.L.lbm_profile(self.h, int(enable)), self.h)
+    def profile(self, enable: bool = True, kernels=None) -> None:
+        """Record event pairs around every kernel (enable), or only around the
+        named ones (kernels: names from KERNELS)."""
+        if enable and kernels is not None:
+            mask = 0
+            for name in kernels:
+                mask |= 1 << self.KERNELS.index(name)
+            self._ok(self.L.lbm_profile_mask(self.h, mask), self.h)
+        else:
+            self._ok(self.L.lbm_profile(self.h, int(enable)), self.h)
 
     def profile_read(self) -> dict:
         """{kernel: (total_ms, launches)} recorded since profile(True)."""

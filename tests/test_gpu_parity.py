@@ -485,6 +485,48 @@ def test_deterministic(pkg, oracle_mod, W):
     assert np.array_equal(outs[0][2], outs[1][2])
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_plain_speculation_same_bits(pkg, oracle_mod, W, storage):
+    """Issuing the plain sweep's pulls before its near-set entry is read
+    (mode 1) or after (mode 0) changes only the order of loads: three steps
+    of a moving multi-particle case (walls and wraps, near bricks both ways)
+    give bit-identical populations and forces, and the same as the default."""
+    wl = H.with_margin(oracle_mod, wl_multi(W))
+    outs = []
+    for mode in (1, 0, -1):
+        gpu = H.make_gpu(pkg, wl, storage=storage)
+        gpu.set_particles(H.gpu_particles(pkg, wl))
+        gpu.set_plain_speculation(mode)
+        gpu.step(3)
+        F, T = gpu.forces()
+        outs.append((F, T, gpu.populations().cpu().numpy()))
+    for F, T, f in outs[1:]:
+        assert np.array_equal(F, outs[0][0]) and np.array_equal(T, outs[0][1])
+        assert np.array_equal(f, outs[0][2])
+    with pytest.raises(pkg.LbmError):
+        gpu.set_plain_speculation(2)
+
+
+def test_profile_mask_records_chosen_kernels(pkg, oracle_mod, W):
+    """Profiling every kernel records the binning, flags, plain and near
+    sweeps of each step; with only the plain sweep named, four further steps
+    record it four times and nothing else."""
+    wl = H.with_margin(oracle_mod, wl_multi(W))
+    gpu = H.make_gpu(pkg, wl)
+    gpu.set_particles(H.gpu_particles(pkg, wl))
+    gpu.profile(True)
+    gpu.step(2)
+    rec = gpu.profile_read()
+    gpu.profile(False)
+    assert all(rec[k][1] == 2 for k in ("k_bin", "k_flags", "k_sweep_plain", "k_sweep_near")), rec
+    gpu.profile(True, kernels=["k_sweep_plain"])
+    gpu.step(4)
+    rec = gpu.profile_read()
+    gpu.profile(False)
+    assert rec["k_sweep_plain"][1] == 4
+    assert all(n == 0 for k, (_, n) in rec.items() if k != "k_sweep_plain"), rec
+
+
 def test_mass_conserved_closed_box_fp64(pkg, W):
     wl = wl_walls_guo_ragged(W)
     wl["force"] = (0.0, 0.0, 0.0)
