@@ -36,11 +36,20 @@ __device__ __forceinline__ C add_e(C acc, int e, C v) {
 // Collide one node: moments (Eq. (18)) with the half-force shift, BGK toward
 // f^eq (Eqs. (15)-(16)) plus Guo's forcing term (compiled out when the body
 // force is zero); out receives the post-collision offsets.
+//
+// Per direction, with c = omega drho - 1.5 omega rho u.u,
+//   out_i = (1 - omega) g_i + w_i (c + 3 omega rho e_i.u + 4.5 omega rho (e_i.u)^2)
+//           + w_i gfac (3 (e_i.F - u.F) + 9 (e_i.u)(e_i.F)),
+// which is omega g^eq_i (offset form) plus the forcing term.  Opposite
+// directions share w_i and |e_i.u|, so each pair (i, i+1) evaluates the even
+// part once and adds or subtracts the odd part; the weights are folded into
+// per-node constants of the two weight classes of a pair.
 template <typename S, int Q, bool kForce>
 __device__ __forceinline__ void collide_values(const Params &P, const typename Codec<S>::C (&fin)[Q],
                                                typename Codec<S>::C (&out)[Q]) {
     using L = Lat<Q>;
     using C = typename Codec<S>::C;
+    static_assert(L::opp(1) == 2 && L::opp(Q - 2) == Q - 1, "directions come in opposite pairs (i, i+1), i odd");
     const C rho0 = Prm<C>::rho0(P);
     // offsets: rho = rho0 + sum g, momentum = sum g e
     C drho = 0, mx = 0, my = 0, mz = 0;
@@ -57,25 +66,43 @@ __device__ __forceinline__ void collide_values(const Params &P, const typename C
     C inv_rho;
     if (sizeof(C) == 4) inv_rho = (C)__frcp_rn((float)rho);
     else inv_rho = C(1) / rho;
-    const C ux = (mx + C(0.5) * Fx) * inv_rho, uy = (my + C(0.5) * Fy) * inv_rho, uz = (mz + C(0.5) * Fz) * inv_rho;
-    const C omega = Prm<C>::omega(P);
+    C ux, uy, uz;
+    if (kForce) {
+        ux = (mx + C(0.5) * Fx) * inv_rho; uy = (my + C(0.5) * Fy) * inv_rho; uz = (mz + C(0.5) * Fz) * inv_rho;
+    } else {
+        ux = mx * inv_rho; uy = my * inv_rho; uz = mz * inv_rho;
+    }
+    const C omega = Prm<C>::omega(P), om1 = C(1) - omega;
     const C uu = ux * ux + uy * uy + uz * uz;
-    const C om_rho = omega * rho, om_drho = omega * drho;
+    const C om_rho = omega * rho;
+    const C c = omega * drho - C(1.5) * om_rho * uu;
+    const C k3 = C(3) * om_rho, k45 = C(4.5) * om_rho;
+    C gfac = C(0), uF3 = C(0);
+    if (kForce) {
+        gfac = Prm<C>::gfac(P);
+        uF3 = C(3) * (ux * Fx + uy * Fy + uz * Fz);
+    }
+    {
+        const C w = (C)L::w(0);
+        C e = c;
+        if (kForce) e -= gfac * uF3;
+        out[0] = om1 * fin[0] + w * e;
+    }
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
+    for (int i = 1; i < Q; i += 2) {
         const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
         const C w = (C)L::w(i);
         const C eu = dot_e(ex, ey, ez, ux, uy, uz);
-        // omega g^eq = w (omega drho + omega rho (3 eu + 4.5 eu^2 - 1.5 uu))
-        const C geq_om = w * (om_drho + om_rho * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu));
-        C o = fin[i] - omega * fin[i] + geq_om;
+        C even = c + k45 * eu * eu;  // equal for i and its opposite
+        C odd = k3 * eu;             // opposite signs
         if (kForce) {
-            const C gfac = Prm<C>::gfac(P);
-            const C uF = ux * Fx + uy * Fy + uz * Fz;
             const C eF = dot_e(ex, ey, ez, Fx, Fy, Fz);
-            o += gfac * w * (C(3) * (eF - uF) + C(9) * eu * eF);
+            even += gfac * (C(9) * eu * eF - uF3);
+            odd += gfac * C(3) * eF;
         }
-        out[i] = o;
+        const C we = w * even, wo = w * odd;
+        out[i] = om1 * fin[i] + (we + wo);
+        out[i + 1] = om1 * fin[i + 1] + (we - wo);
     }
 }
 
