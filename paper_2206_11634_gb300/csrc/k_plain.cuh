@@ -35,30 +35,57 @@ __device__ __forceinline__ C add_e(C acc, int e, C v) {
 
 // Collide one node: moments (Eq. (18)) with the half-force shift, BGK toward
 // f^eq (Eqs. (15)-(16)) plus Guo's forcing term (compiled out when the body
-// force is zero); out receives the post-collision offsets.
+// force is zero).  fin and out hold collide-space values (Codec::ldv): the
+// offsets g = f - w rho0 for FP32/FP64 storage, the stored h = g / w for the
+// scaled 16-bit forms, so neither side multiplies by the weights.
 //
 // Per direction, with c = omega drho - 1.5 omega rho u.u,
-//   out_i = (1 - omega) g_i + w_i (c + 3 omega rho e_i.u + 4.5 omega rho (e_i.u)^2)
-//           + w_i gfac (3 (e_i.F - u.F) + 9 (e_i.u)(e_i.F)),
-// which is omega g^eq_i (offset form) plus the forcing term.  Opposite
-// directions share w_i and |e_i.u|, so each pair (i, i+1) evaluates the even
-// part once and adds or subtracts the odd part; the weights are folded into
-// per-node constants of the two weight classes of a pair.
+//   g_out_i = (1 - omega) g_i + w_i (c + 3 omega rho e_i.u + 4.5 omega rho (e_i.u)^2)
+//             + w_i gfac (3 (e_i.F - u.F) + 9 (e_i.u)(e_i.F)),
+// which is omega g^eq_i (offset form) plus the forcing term (h_out_i =
+// g_out_i / w_i is the same without the w_i).  Opposite directions share w_i
+// and |e_i.u|, so each pair (i, i+1) evaluates the even part once and adds or
+// subtracts the odd part.
 template <typename S, int Q, bool kForce>
 __device__ __forceinline__ void collide_values(const Params &P, const typename Codec<S>::C (&fin)[Q],
                                                typename Codec<S>::C (&out)[Q]) {
     using L = Lat<Q>;
-    using C = typename Codec<S>::C;
+    using Cd = Codec<S>;
+    using C = typename Cd::C;
     static_assert(L::opp(1) == 2 && L::opp(Q - 2) == Q - 1, "directions come in opposite pairs (i, i+1), i odd");
     const C rho0 = Prm<C>::rho0(P);
     // offsets: rho = rho0 + sum g, momentum = sum g e
     C drho = 0, mx = 0, my = 0, mz = 0;
+    if constexpr (Cd::kScaled) {
+        // g = w h: sums per weight class (rest, i = 1..6, i = 7..Q-1), then weighted
+        C s1 = 0, x1 = 0, y1 = 0, z1 = 0, s2 = 0, x2 = 0, y2 = 0, z2 = 0;
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
-        drho += fin[i];
-        mx = add_e(mx, L::e(i, 0), fin[i]);
-        my = add_e(my, L::e(i, 1), fin[i]);
-        mz = add_e(mz, L::e(i, 2), fin[i]);
+        for (int i = 1; i <= 6; i++) {
+            s1 += fin[i];
+            x1 = add_e(x1, L::e(i, 0), fin[i]);
+            y1 = add_e(y1, L::e(i, 1), fin[i]);
+            z1 = add_e(z1, L::e(i, 2), fin[i]);
+        }
+#pragma unroll
+        for (int i = 7; i < Q; i++) {
+            s2 += fin[i];
+            x2 = add_e(x2, L::e(i, 0), fin[i]);
+            y2 = add_e(y2, L::e(i, 1), fin[i]);
+            z2 = add_e(z2, L::e(i, 2), fin[i]);
+        }
+        const C w0 = (C)L::w(0), w1 = (C)L::w(1), w2 = (C)L::w(Q - 1);
+        drho = w0 * fin[0] + w1 * s1 + w2 * s2;
+        mx = w1 * x1 + w2 * x2;
+        my = w1 * y1 + w2 * y2;
+        mz = w1 * z1 + w2 * z2;
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            drho += fin[i];
+            mx = add_e(mx, L::e(i, 0), fin[i]);
+            my = add_e(my, L::e(i, 1), fin[i]);
+            mz = add_e(mz, L::e(i, 2), fin[i]);
+        }
     }
     const C rho = rho0 + drho;
     const C Fx = kForce ? Prm<C>::F(P, 0) : C(0), Fy = kForce ? Prm<C>::F(P, 1) : C(0),
@@ -83,15 +110,14 @@ __device__ __forceinline__ void collide_values(const Params &P, const typename C
         uF3 = C(3) * (ux * Fx + uy * Fy + uz * Fz);
     }
     {
-        const C w = (C)L::w(0);
         C e = c;
         if (kForce) e -= gfac * uF3;
-        out[0] = om1 * fin[0] + w * e;
+        if constexpr (Cd::kScaled) out[0] = om1 * fin[0] + e;
+        else out[0] = om1 * fin[0] + (C)L::w(0) * e;
     }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
         const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
-        const C w = (C)L::w(i);
         const C eu = dot_e(ex, ey, ez, ux, uy, uz);
         C even = c + k45 * eu * eu;  // equal for i and its opposite
         C odd = k3 * eu;             // opposite signs
@@ -100,13 +126,17 @@ __device__ __forceinline__ void collide_values(const Params &P, const typename C
             even += gfac * (C(9) * eu * eF - uF3);
             odd += gfac * C(3) * eF;
         }
-        const C we = w * even, wo = w * odd;
-        out[i] = om1 * fin[i] + (we + wo);
-        out[i + 1] = om1 * fin[i + 1] + (we - wo);
+        if constexpr (!Cd::kScaled) {
+            const C w = (C)L::w(i);
+            even *= w;
+            odd *= w;
+        }
+        out[i] = om1 * fin[i] + (even + odd);
+        out[i + 1] = om1 * fin[i + 1] + (even - odd);
     }
 }
 
-// Collide one node and store it.
+// Collide one node (collide-space values, see collide_values) and store it.
 template <typename S, int Q, bool kForce, bool kStream = false>
 __device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>::C (&fin)[Q], S *B, long long N,
                                               int n) {
@@ -119,8 +149,8 @@ __device__ __forceinline__ void collide_store(const Params &P, typename Codec<S>
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const C w = (C)L::w(i);
-        if (kStream) Cd::st_s(B + (long long)i * N + n, out[i], w, rho0);
-        else Cd::st(B + (long long)i * N + n, out[i], w, rho0);
+        if (kStream) Cd::stv_s(B + (long long)i * N + n, out[i], w, rho0);
+        else Cd::stv(B + (long long)i * N + n, out[i], w, rho0);
     }
 }
 
@@ -138,8 +168,8 @@ __device__ __forceinline__ void neighbour_coords(const Params &P, int x, int y, 
 }
 
 // The pull of a node no particle link reaches: f_i from x - e_i, halfway
-// bounce-back at walls (the node's own opposite population).  No flags are
-// read.  A row off the y and z faces (one warp of a brick) takes the source
+// bounce-back at walls (the node's own opposite population), as collide-space
+// values (Codec::ldv).  No flags are read.  A row off the y and z faces (one warp of a brick) takes the source
 // n - e_i . (1, nx, nx ny) as a 32-bit index, corrected only on its two
 // x-face lanes (wrap or bounce-back); other rows, and lattices whose
 // population indices need more than 31 bits, resolve each neighbour's
@@ -165,7 +195,7 @@ __device__ __forceinline__ void plain_pull(const Params &P, int x, int y, int z,
             if (ex > 0) idx = wm ? L::opp(i) * N + n : idx + cm;
             if (ex < 0) idx = wp ? L::opp(i) * N + n : idx + cp;
             const S *src = A + (unsigned)idx;
-            fin[i] = kStream ? Cd::ld_s(src, (C)L::w(i), rho0) : Cd::ld(src, (C)L::w(i), rho0);
+            fin[i] = kStream ? Cd::ldv_s(src, (C)L::w(i), rho0) : Cd::ldv(src, (C)L::w(i), rho0);
         }
         return;
     }
@@ -183,7 +213,7 @@ __device__ __forceinline__ void plain_pull(const Params &P, int x, int y, int z,
         const bool wall = (xs[bx] | ys[by] | zs[bz]) < 0;
         // wall: f_i = f+_i'(x), the node's own opposite population
         const S *src = wall ? A + (long long)L::opp(i) * N + n : A + (long long)i * N + (xs[bx] + row[by][bz]);
-        fin[i] = kStream ? Cd::ld_s(src, (C)L::w(i), rho0) : Cd::ld(src, (C)L::w(i), rho0);
+        fin[i] = kStream ? Cd::ldv_s(src, (C)L::w(i), rho0) : Cd::ldv(src, (C)L::w(i), rho0);
     }
 }
 

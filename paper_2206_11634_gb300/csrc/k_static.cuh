@@ -316,18 +316,18 @@ __device__ __forceinline__ void static_links_warp(const Params &P, StaticScratch
         int k = first;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            if (links & (1u << i)) {
-                fin[i] = (C)__int_as_float(ss.rec[warp][k]);
+            if (links & (1u << i)) {  // link results are offsets g
+                fin[i] = Cd::g_to_v((C)__int_as_float(ss.rec[warp][k]), (C)L::w(i));
                 k++;
             } else {
                 const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
                 const bool wall = (sx | sy | sz) < 0;
                 const S *ptr = wall ? A + (long long)L::opp(i) * N + n
                                     : A + (long long)i * N + (sx + P.nx * (sy + P.ny * sz));
-                fin[i] = Cd::ld(ptr, (C)L::w(i), rho0);
+                fin[i] = Cd::ldv(ptr, (C)L::w(i), rho0);
             }
         }
-        collide_store<S, Q, kForce>(P, fin, B, N, n);
+        collide_store<S, Q, kForce>(P, fin, B, N, n);  // collide-space values
     }
     __syncwarp();
     for (int e = lane; e < kStaticSlots * 6; e += 32) {

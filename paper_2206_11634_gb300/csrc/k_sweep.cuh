@@ -565,6 +565,8 @@ __device__ __noinline__ void boundary_node(const Params &P, const SmemParticles 
                                      fown[L::opp(i)], drho_f, u_f, sink, &Mf_cache, &Mf_slot);
         (*nlinks)++;
     }
+#pragma unroll
+    for (int i = 0; i < Q; i++) fin[i] = Cd::g_to_v(fin[i], (C)L::w(i));
     collide_store<S, Q, kForce>(P, fin, B, N, n);
 }
 
@@ -653,7 +655,11 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
     if (sizeof(C) == 8) {
         // FP64 storage: every node evaluates its own links
         if (links) boundary_node<S, Q, kForce>(P, sp, x, y, z, lx, ly, lz, bx0, by0, bz0, n, sink, &nlinks);
-        else if (fluid) collide_store<S, Q, kForce>(P, fin, B, N, n);
+        else if (fluid) {
+#pragma unroll
+            for (int i = 0; i < Q; i++) fin[i] = Cd::g_to_v(fin[i], (C)L::w(i));
+            collide_store<S, Q, kForce>(P, fin, B, N, n);
+        }
     } else {
         // the warp's links in a queue (lane order, then direction order);
         // all 32 lanes evaluate them, then each node takes its results back
@@ -692,18 +698,18 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
             int k = first;
 #pragma unroll
             for (int i = 0; i < Q; i++) {
-                if (links & (1u << i)) {
-                    fin[i] = (C)ls->result[warp][k];
+                if (links & (1u << i)) {  // link results are offsets g
+                    fin[i] = Cd::g_to_v((C)ls->result[warp][k], (C)L::w(i));
                     k++;
                 } else {
                     const int sx = xs[1 - L::e(i, 0)], sy = ys[1 - L::e(i, 1)], sz = zs[1 - L::e(i, 2)];
                     const bool wall = (sx | sy | sz) < 0;
                     const S *ptr = wall ? A + (long long)L::opp(i) * N + n
                                         : A + (long long)i * N + (sx + P.nx * (sy + P.ny * sz));
-                    fin[i] = Cd::ld(ptr, (C)L::w(i), rho0);
+                    fin[i] = Cd::ldv(ptr, (C)L::w(i), rho0);
                 }
             }
-            collide_store<S, Q, kForce>(P, fin, B, N, n);
+            collide_store<S, Q, kForce>(P, fin, B, N, n);  // collide-space values
         }
     }
 

@@ -158,6 +158,12 @@ struct Codec;
 template <>
 struct Codec<double> {
     using C = double;
+    static constexpr bool kScaled = false;  // collide-space values are the offsets g themselves
+    __device__ __forceinline__ static double ldv(const double *p, double, double) { return __ldg(p); }
+    __device__ __forceinline__ static double ldv_s(const double *p, double, double) { return __ldcs(p); }
+    __device__ __forceinline__ static void stv(double *p, double v, double, double) { *p = v; }
+    __device__ __forceinline__ static void stv_s(double *p, double v, double, double) { __stcs(p, v); }
+    __device__ __forceinline__ static double g_to_v(double g, double) { return g; }
     __device__ __forceinline__ static double ld(const double *p, double, double) { return __ldg(p); }
     __device__ __forceinline__ static double ld_plain(const double *p, double, double) { return *p; }
     __device__ __forceinline__ static double ld_s(const double *p, double, double) { return __ldcs(p); }
@@ -169,6 +175,12 @@ struct Codec<double> {
 template <>
 struct Codec<float> {
     using C = float;
+    static constexpr bool kScaled = false;
+    __device__ __forceinline__ static float ldv(const float *p, float, float) { return __ldg(p); }
+    __device__ __forceinline__ static float ldv_s(const float *p, float, float) { return __ldcs(p); }
+    __device__ __forceinline__ static void stv(float *p, float v, float, float) { *p = v; }
+    __device__ __forceinline__ static void stv_s(float *p, float v, float, float) { __stcs(p, v); }
+    __device__ __forceinline__ static float g_to_v(float g, float) { return g; }
     __device__ __forceinline__ static float ld(const float *p, float, float) { return __ldg(p); }
     __device__ __forceinline__ static float ld_plain(const float *p, float, float) { return *p; }
     __device__ __forceinline__ static float ld_s(const float *p, float, float) { return __ldcs(p); }
@@ -180,6 +192,14 @@ struct Codec<float> {
 template <>
 struct Codec<__half> {
     using C = float;
+    // collide-space values are the stored h = g / w, decoded without the
+    // weight (the collision takes the weights into its constants)
+    static constexpr bool kScaled = true;
+    __device__ __forceinline__ static float ldv(const __half *p, float, float) { return __half2float(__ldg(p)); }
+    __device__ __forceinline__ static float ldv_s(const __half *p, float, float) { return __half2float(__ldcs(p)); }
+    __device__ __forceinline__ static void stv(__half *p, float v, float, float) { *p = __float2half_rn(v); }
+    __device__ __forceinline__ static void stv_s(__half *p, float v, float, float) { __stcs(p, __float2half_rn(v)); }
+    __device__ __forceinline__ static float g_to_v(float g, float w) { return g * (1.0f / w); }
     __device__ __forceinline__ static float ld(const __half *p, float w, float) { return w * __half2float(__ldg(p)); }
     __device__ __forceinline__ static float ld_plain(const __half *p, float w, float) { return w * __half2float(*p); }
     __device__ __forceinline__ static float ld_s(const __half *p, float w, float) { return w * __half2float(__ldcs(p)); }
@@ -197,6 +217,18 @@ struct Codec<__half> {
 template <>
 struct Codec<__nv_bfloat16> {
     using C = float;
+    static constexpr bool kScaled = true;
+    __device__ __forceinline__ static float ldv(const __nv_bfloat16 *p, float, float) {
+        return __bfloat162float(__ldg(p));
+    }
+    __device__ __forceinline__ static float ldv_s(const __nv_bfloat16 *p, float, float) {
+        return __bfloat162float(__ldcs(p));
+    }
+    __device__ __forceinline__ static void stv(__nv_bfloat16 *p, float v, float, float) { *p = __float2bfloat16_rn(v); }
+    __device__ __forceinline__ static void stv_s(__nv_bfloat16 *p, float v, float, float) {
+        __stcs(p, __float2bfloat16_rn(v));
+    }
+    __device__ __forceinline__ static float g_to_v(float g, float w) { return g * (1.0f / w); }
     __device__ __forceinline__ static float ld(const __nv_bfloat16 *p, float w, float) {
         return w * __bfloat162float(__ldg(p));
     }
