@@ -53,3 +53,42 @@ def test_settling_sphere():
     wl = W.settling_sphere()
     p = wl["particles"][0]
     assert p["K"][0] == 36.0 and (wl["nx"], wl["ny"], wl["nz"]) == (32, 32, 48) and wl["storage"] == "f64"
+
+
+def _volume(cp, K, h=0.25):
+    """Cells inside {sum K_i / |x - x_i|^2 >= 1}, counted on a grid of spacing h."""
+    R = np.max(np.linalg.norm(cp, axis=1)) + np.sqrt(np.sum(K)) + 1.0
+    g = np.arange(-R, R + h, h)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    M = np.zeros_like(X)
+    for c, k in zip(cp, K):
+        M += k / np.maximum((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2, 1e-12)
+    inside = M >= 1.0
+    return inside.sum() * h ** 3, np.ptp(X[inside]) + h, np.ptp(Z[inside]) + h
+
+
+def test_dkt_units_and_shapes():
+    """§4's two-particle run in lattice units: 1 mm and 2e-4 s per step make
+    the paper's viscosity 7.55e-5 m^2/s nu = 0.0151 (tau 0.5453, recorded in
+    the docstring; the run uses 0.56) and gravity 9.8 m/s^2 3.92e-4; the
+    metaball and the sphere both enclose 1648 cells (1.648e-6 m^3), the
+    metaball with thickness / width 0.84 (the paper's elongation 0.84375)."""
+    nu = 7.55e-5 * 2e-4 / 1e-3 ** 2
+    assert abs(3 * nu + 0.5 - 0.5453) < 1e-4
+    m, s = W.dkt("metaball"), W.dkt("sphere")
+    for wl in (m, s):
+        assert (wl["nx"], wl["ny"], wl["nz"]) == (150, 150, 250) and wl["periodic"] == (0, 0, 0)
+        assert abs(wl["gravity"][2] + 3.92e-4) < 1e-12 and wl["tau"] == 0.56 and wl["n_sub"] == 100
+        a, b = wl["particles"]
+        assert np.allclose(a["x"], (74.5, 74.5, 219.5)) and np.allclose(b["x"], (76.5, 74.5, 204.5))
+        assert abs(a["density"] - 1200 / 927) < 1e-12
+        for p in (a, b):  # inside the walls
+            r = W.bounding_radius(p["cp"], p["K"], p["Rs"])
+            assert np.all(p["x"] - r > -0.5) and np.all(p["x"] + r < np.array([150, 150, 250]) - 0.5)
+    vm, wm, tm = _volume(m["particles"][0]["cp"], m["particles"][0]["K"])
+    # the shapes start apart: 15 nodes between centres, more than the metaball's
+    # thickness (the square faces the fall) and the sphere's diameter
+    assert np.linalg.norm(m["particles"][0]["x"] - m["particles"][1]["x"]) > max(tm, 2 * 7.325)
+    vs, _, _ = _volume(s["particles"][0]["cp"], s["particles"][0]["K"])
+    assert abs(vm - 1648) < 15 and abs(vs - 1648) < 15, (vm, vs)
+    assert abs(tm / wm - 0.84375) < 0.03, tm / wm
