@@ -50,13 +50,16 @@ __device__ __forceinline__ void flags_brick(const Params &P, SmemParticles &sp, 
     constexpr bool kF64 = sizeof(C) == 8;
     const int tid = threadIdx.x;
     int cnt = P.bcount[b];
+    // the list's slots are read in the same round as its count (slots past
+    // the count hold stale ids and are not used)
+    const int raw_id = tid < MAXPB ? P.blist[b * MAXPB + tid] : 0;
     if (cnt > MAXPB) cnt = MAXPB;
     __syncthreads();  // the previous brick's use of sp and of the list is over
     // ascending particle order makes the list, and hence every sum over it,
     // independent of the scatter's atomic order: lane s of warp 0 places its
     // id at its rank (ids are distinct)
     if (tid < 32) {
-        const int id = tid < cnt ? P.blist[b * MAXPB + tid] : 0x7fffffff;
+        const int id = tid < cnt ? raw_id : 0x7fffffff;
         int rank = 0;
         for (int o = 0; o < cnt; o++) rank += __shfl_sync(0xffffffffu, id, o) < id;
         if (tid < cnt) P.blist[b * MAXPB + rank] = id;

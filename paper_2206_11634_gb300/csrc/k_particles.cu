@@ -96,6 +96,14 @@ __global__ void __launch_bounds__(256) k_bin(Params P) {
     // the binning; slot step+2 (consumed by the near sweep of step-1) is
     // cleared for the next binning
     if (blockIdx.x == 0 && threadIdx.x == 0 && P.pred_count) P.pred_count[(P.step + 2) % 3] = 0;
+    if (P.bin_next && blockIdx.x == gridDim.x - 1) {
+        // the region of step + 1 (that of step - 1, whose readers are done:
+        // they ran before this kernel on the same stream)
+        int4 *z = static_cast<int4 *>(P.bin_next);
+        const long long n16 = P.bin_next_bytes / 16;
+        for (long long k = threadIdx.x; k < n16; k += blockDim.x) z[k] = make_int4(0, 0, 0, 0);
+        return;
+    }
     if ((int)blockIdx.x < P.np) bin_particle(P, blockIdx.x);
 }
 
@@ -800,8 +808,9 @@ __global__ void __launch_bounds__(256) k_dem(Params P) {
 }
 
 void launch_bin(const Params &P, cudaStream_t st) {
-    // runs every step, with no particle too (it keeps the count ring)
-    k_bin<<<P.np > 0 ? P.np : 1, 256, 0, st>>>(P);
+    // runs every step, with no particle too (it keeps the count ring); one
+    // more CTA clears the next step's per-step region
+    k_bin<<<(P.np > 0 ? P.np : 1) + (P.bin_next ? 1 : 0), 256, 0, st>>>(P);
 }
 void launch_force_reduce(const Params &P, cudaStream_t st) {
     if (P.np > 0) k_force_reduce<<<P.np, 256, 0, st>>>(P);

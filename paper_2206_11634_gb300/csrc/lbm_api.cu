@@ -33,6 +33,7 @@ struct Layout {
     size_t pred_stamp, pred_list, pred_count, skip, brick_solid;
     size_t bin;        // bcount[nbricks] followed by the per-step counters
     size_t bin_bytes;
+    size_t bin_alt;    // second per-step region: step t uses bin (t even) or bin_alt (t odd)
     size_t ffix_off;   // offset of the fixed-point force totals within bin
     size_t blist, partial, parts, Fh, Th, Fc, Tc;
     size_t pairF, pair_on, pair_xi, pair_xm, wall_on, wall_xi, wall_xcw;
@@ -100,11 +101,13 @@ void make_layout(const lbm_config *c, Layout *L) {
     L->pred_count = take(3 * 4);
     L->skip = take(3 * nb * 4);
     L->brick_solid = take(nb);
-    // per-step region, cleared before every step: brick counts, counters,
-    // and (FP32 and below) the fixed-point force/torque totals
+    // per-step regions, one per step parity, clear when a step starts: brick
+    // counts, counters, and (FP32 and below) the fixed-point force/torque
+    // totals; the binning of step t clears the region of step t + 1
     L->ffix_off = (nb * 4 + kStepCounters * 4 + 7) / 8 * 8;
     L->bin_bytes = L->ffix_off + P * 6 * 8;
     L->bin = take(L->bin_bytes);
+    L->bin_alt = take(L->bin_bytes);  // the other parity's region (odd steps)
     L->blist = take(nb * MAXPB * 4);
     L->partial = take(nb * MAXPB * 6 * 8);
     L->parts = take(P * sizeof(DevParticle));
@@ -177,6 +180,7 @@ struct lbm_handle {
     int snodes_n;      // its link nodes
     int nsm;       // SMs of the device
     int plain_per_sm, chain_per_sm;  // launch schedule (lbm_set_schedule)
+    int bin_clean[2];     // the per-step region of that parity is known to be all zero
     int plain_spec;       // the particles' search boxes cover under a tenth of the bricks (set_particles)
     int plain_spec_mode;  // lbm_set_plain_speculation: -1 auto (plain_spec), 0 off, 1 on
     int64_t steps;
@@ -203,6 +207,12 @@ template <typename T>
 T *at(lbm_handle *h, size_t off) {
     return reinterpret_cast<T *>(h->ws + off);
 }
+
+// The per-step region of step t (brick counts, counters, fixed-point force
+// totals): one per step parity.
+static size_t bin_region(const lbm_handle *h, int64_t t) { return (t & 1) ? h->L.bin_alt : h->L.bin; }
+// The region holding the results of the last step issued.
+static size_t last_bin_region(const lbm_handle *h) { return bin_region(h, h->steps > 0 ? h->steps - 1 : 0); }
 
 Params make_params(lbm_handle *h) {
     const lbm_config &c = h->cfg;
@@ -236,7 +246,9 @@ Params make_params(lbm_handle *h) {
     P.snode_cap = h->L.snode_cap;
     P.slink_cap = h->L.slink_cap;
     P.snodes_n = h->snodes_n;
-    P.bcount = at<int>(h, h->L.bin);
+    P.bcount = at<int>(h, bin_region(h, h->steps));
+    P.bin_next = h->ws + bin_region(h, h->steps + 1);
+    P.bin_next_bytes = (long long)((h->L.bin_bytes + 15) / 16 * 16);
     P.blist = at<int>(h, h->L.blist);
     P.partial = at<double>(h, h->L.partial);
     P.parts = at<DevParticle>(h, h->L.parts);
@@ -262,9 +274,9 @@ Params make_params(lbm_handle *h) {
     P.plain_spec = h->plain_spec_mode >= 0 ? h->plain_spec_mode : h->plain_spec;
     P.idx32 = (long long)c.lattice * (long long)c.nx * c.ny * c.nz <= 0x7fffffffLL;
     P.status = at<int>(h, h->L.status);
-    P.counters = at<int>(h, h->L.bin + (size_t)h->L.nbricks * 4);
+    P.counters = at<int>(h, bin_region(h, h->steps) + (size_t)h->L.nbricks * 4);
     P.force_fixed = h->cfg.storage != LBM_STORE_F64;
-    P.Ffix = at<unsigned long long>(h, h->L.bin + h->L.ffix_off);
+    P.Ffix = at<unsigned long long>(h, bin_region(h, h->steps) + h->L.ffix_off);
     return P;
 }
 
@@ -493,6 +505,7 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
         h->chain_per_sm = kDefaultChainPerSm;
         h->plain_spec = 1;
         h->plain_spec_mode = -1;
+        h->bin_clean[0] = h->bin_clean[1] = 1;  // the workspace is cleared below
     }
     int rc = LBM_OK;
     if (own_streams) {
@@ -671,8 +684,9 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
     if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.wall_on, 0, P * NWALL * 4, h->stream), "cudaMemsetAsync");
     if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.Fh, 0, P * 24, h->stream), "cudaMemsetAsync");
     if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.Th, 0, P * 24, h->stream), "cudaMemsetAsync");
-    if (rc == LBM_OK)
-        rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.bin + h->L.ffix_off, 0, P * 48, h->stream), "cudaMemsetAsync");
+    for (const size_t r : {h->L.bin, h->L.bin_alt})
+        if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + r, 0, h->L.bin_bytes, h->stream), "cudaMemsetAsync");
+    if (rc == LBM_OK) h->bin_clean[0] = h->bin_clean[1] = 1;
     // the staging vector dies with this call
     if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (rc == LBM_OK) h->np = n;
@@ -730,12 +744,19 @@ int lbm_step(lbm_handle *h, int nsteps) {
         // FP64 the fixed-geometry sweep takes over
         const bool geom_static = h->all_fixed && h->static_steps >= kStaticFlagSteps;
         const bool fixed_sweep = geom_static && h->L.snode_cap > 0 && h->static_state >= 0;
-        // fresh brick lists and step counters
-        e = cudaMemsetAsync(h->ws + h->L.bin, 0, h->L.bin_bytes, hs);
-        if (e != cudaSuccess) return cuda_check(h, e, "cudaMemsetAsync(bricks)");
+        // fresh brick lists and step counters: the region of this step was
+        // cleared by the previous step's binning, else here
+        const int rp = (int)(h->steps & 1);
+        const size_t region = bin_region(h, h->steps);
+        if (!h->bin_clean[rp]) {
+            e = cudaMemsetAsync(h->ws + region, 0, h->L.bin_bytes, hs);
+            if (e != cudaSuccess) return cuda_check(h, e, "cudaMemsetAsync(bricks)");
+        }
+        h->bin_clean[rp] = 0;
         if (fixed_sweep && h->static_state == 0) {
             // record the fixed geometry once, from this step's brick lists
             { ProfScope s(h, 0, true, hs); launch_bin(P, hs); }
+            h->bin_clean[rp ^ 1] = 1;
             e = cudaMemsetAsync(h->ws + h->L.sskip, 0, (size_t)h->L.N, hs);
             if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->L.scount, 0, 8, hs);
             if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->L.smf, 0, (size_t)h->cfg.max_particles * 48, hs);
@@ -762,7 +783,7 @@ int lbm_step(lbm_handle *h, int nsteps) {
                 P = make_params(h);
             }
             // the lists this build read are cleared again for the step
-            e = cudaMemsetAsync(h->ws + h->L.bin, 0, h->L.bin_bytes, hs);
+            e = cudaMemsetAsync(h->ws + region, 0, h->L.bin_bytes, hs);
             if (e != cudaSuccess) return cuda_check(h, e, "cudaMemsetAsync(bricks)");
         }
         if (fixed_sweep && h->static_state == 1) {
@@ -779,6 +800,7 @@ int lbm_step(lbm_handle *h, int nsteps) {
             if (e != cudaSuccess) return cuda_check(h, e, "event record");
         } else {
             { ProfScope s(h, 0, true, hs); launch_bin(P, hs); }
+            h->bin_clean[rp ^ 1] = 1;
             e = cudaEventRecord(h->ev_bin, hs);
             if (e != cudaSuccess) return cuda_check(h, e, "event record");
             { ProfScope s(h, 1, !geom_static, hs); if (!geom_static) by_storage<DoFlags>(h->cfg.storage, P, hs); }
@@ -862,7 +884,7 @@ int lbm_get_forces(lbm_handle *h, double *F, double *T, lbm_particle *state_out)
         // FP32 and below: exact fixed-point totals (units of 2^-40)
         if (F || T) {
             fix.resize(n * 6);
-            rc = cuda_check(h, cudaMemcpyAsync(fix.data(), h->ws + h->L.bin + h->L.ffix_off, n * 48,
+            rc = cuda_check(h, cudaMemcpyAsync(fix.data(), h->ws + last_bin_region(h) + h->L.ffix_off, n * 48,
                                                cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(F)");
         }
     } else {
@@ -965,7 +987,7 @@ int lbm_check(lbm_handle *h) {
 int lbm_get_counters(lbm_handle *h, int64_t *steps, int32_t *nrefill, int32_t *nlinks, int32_t *near_bricks) {
     if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
     int c[kStepCounters];
-    int rc = cuda_check(h, cudaMemcpyAsync(c, h->ws + h->L.bin + (size_t)h->L.nbricks * 4, sizeof(c),
+    int rc = cuda_check(h, cudaMemcpyAsync(c, h->ws + last_bin_region(h) + (size_t)h->L.nbricks * 4, sizeof(c),
                                            cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(counters)");
     if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (rc != LBM_OK) return rc;
