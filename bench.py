@@ -392,7 +392,8 @@ def run_gpu(args):
     sweep_avg_s = plain_ms / max(1, plain_n) * 1e-3
     peak, peak_kind = measured_peak_gbs()
     achieved = alg_bytes / sweep_avg_s / 1e9
-    traffic = profiled_traffic()
+    # the committed capture is of the FP32 default workload's plain sweep
+    traffic = profiled_traffic() if (wl["name"], wl["storage"]) == ("settling_metaball_128x128x256", "f32") else None
     kernels = {k: {"avg_us": round(v[0] / max(1, v[1]) * 1e3, 3), "launches": v[1],
                    "share": round(v[0] / max(1e-12, sum(x[0] for x in prof.values())), 4)}
                for k, v in prof.items() if v[1] > 0}

@@ -31,9 +31,12 @@
  * asks lbm_workspace_size() for the size, allocates one device buffer (any
  * allocator, 256-byte aligned), and passes it to lbm_init(); the handle
  * borrows it until lbm_destroy().  The handle itself is a small host
- * allocation.  All GPU work is issued on the caller's CUDA stream given to
- * lbm_init() (NULL = legacy default stream).  Host buffers passed in are
- * read or written during the call only.
+ * allocation plus one page-locked host buffer (cudaHostAlloc) of about
+ * 1.8 KB per particle of capacity, through which the particle table goes up
+ * and forces and states come back with asynchronous copies.  All GPU work is
+ * issued on the caller's CUDA stream given to lbm_init() (NULL = legacy
+ * default stream).  Host buffers passed in are read or written during the
+ * call only.
  *
  * Errors.  Every function returns LBM_OK (0) or a negative lbm_status.
  * lbm_last_error() gives a one-line message for the last failure on a handle.
@@ -141,8 +144,10 @@ int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_st
 
 /* Replace the particle set (host array of n particles, 0 <= n <=
  * max_particles).  Computes mass properties where mass <= 0, resets the
- * contact history and copies the table to the device (stream ordered).  The
- * node flags are recomputed at the start of the next lbm_step(). */
+ * contact history and copies the table to the device (stream ordered; the
+ * call does not wait for the stream, only, when the previous upload from the
+ * page-locked buffer is still pending, for that copy).  The node flags are
+ * recomputed at the start of the next lbm_step(). */
 int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n);
 
 /* Advance nsteps >= 0 LBM steps on the handle's stream (asynchronous).  The
@@ -160,7 +165,9 @@ int lbm_step(lbm_handle *h, int nsteps);
 
 /* Synchronise and copy out the hydrodynamic force and torque of the last
  * step (F, T: host double[n][3], either may be NULL) and, if state_out is not
- * NULL, the current particle states (host lbm_particle[n]). */
+ * NULL, the current particle states (host lbm_particle[n]).  One wait on the
+ * stream; a device-side error status is returned before any output is
+ * written. */
 int lbm_get_forces(lbm_handle *h, double *F, double *T, lbm_particle *state_out);
 
 /* Synchronise and copy out the contact force and torque (Eqs. (2)-(3), pair

@@ -162,6 +162,13 @@ struct lbm_handle {
     // sweep of t+1 waits for it (it reads its halo).
     cudaStream_t aux, hi;
     cudaEvent_t ev_fork, ev_bin, ev_plain, ev_near, ev_join;
+    // page-locked host buffer for the particle exchange (set_particles,
+    // get_forces): copies from and to it are asynchronous, so a call waits on
+    // the stream once; ev_pin marks the end of the last upload from it
+    unsigned char *pin;
+    size_t pin_bytes;
+    cudaEvent_t ev_pin;
+    bool pin_busy;
     // kernel timing (lbm_profile): event pairs per kernel, in launch order
     unsigned prof;  // kernels whose launches are bracketed by events (bit k: kernel k)
     std::vector<cudaEvent_t> ev[kProfKernels][2];
@@ -496,6 +503,11 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
     const size_t zero_from = L.flags[0];
     h->aux = h->hi = nullptr;
     h->ev_fork = h->ev_bin = h->ev_plain = h->ev_near = h->ev_join = nullptr;
+    h->pin = nullptr;
+    h->ev_pin = nullptr;
+    h->pin_busy = false;
+    // status slots, fixed-point totals [P][6], FP64 totals [P][6], particle records
+    h->pin_bytes = ST_SLOTS * 4 + (size_t)cfg->max_particles * (48 + 48 + sizeof(DevParticle));
     {
         int dev = 0;
         h->nsm = 0;
@@ -521,6 +533,8 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_plain, cudaEventDisableTiming), "cudaEventCreate");
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_near, cudaEventDisableTiming), "cudaEventCreate");
     }
+    if (rc == LBM_OK) rc = cuda_check(h, cudaHostAlloc((void **)&h->pin, h->pin_bytes, cudaHostAllocDefault), "cudaHostAlloc");
+    if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_pin, cudaEventDisableTiming), "cudaEventCreate");
     if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + zero_from, 0, L.total - zero_from, h->stream), "cudaMemsetAsync");
     if (rc == LBM_OK)  // no brick is predicted near (or skipped) before the first step
         rc = cuda_check(h, cudaMemsetAsync(h->ws + L.pred_stamp, 0xFF, 2 * (size_t)L.nbricks * 4, h->stream), "cudaMemsetAsync");
@@ -540,6 +554,8 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
         if (h->ev_plain) cudaEventDestroy(h->ev_plain);
         if (h->ev_near) cudaEventDestroy(h->ev_near);
         if (h->ev_join) cudaEventDestroy(h->ev_join);
+        if (h->ev_pin) cudaEventDestroy(h->ev_pin);
+        if (h->pin) cudaFreeHost(h->pin);
         if (h->aux) cudaStreamDestroy(h->aux);
         if (h->hi) cudaStreamDestroy(h->hi);
         delete h;
@@ -676,9 +692,19 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
     h->dem_f32 = h->cfg.storage != LBM_STORE_F64 && !h->cfg.dem_fp64 && n <= kDem32MaxParticles &&
                  nc_total <= kDem32MaxCp;
     int rc = LBM_OK;
-    if (n > 0)
-        rc = cuda_check(h, cudaMemcpyAsync(h->ws + h->L.parts, dev.data(), sizeof(DevParticle) * (size_t)n,
-                                           cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(particles)");
+    if (n > 0) {
+        // through the page-locked buffer (once its previous upload is done),
+        // so the call returns without waiting for the stream
+        if (h->pin_busy) rc = cuda_check(h, cudaEventSynchronize(h->ev_pin), "cudaEventSynchronize");
+        DevParticle *staged = reinterpret_cast<DevParticle *>(h->pin + ST_SLOTS * 4 + (size_t)h->cfg.max_particles * 96);
+        if (rc == LBM_OK) {
+            std::memcpy(staged, dev.data(), sizeof(DevParticle) * (size_t)n);
+            rc = cuda_check(h, cudaMemcpyAsync(h->ws + h->L.parts, staged, sizeof(DevParticle) * (size_t)n,
+                                               cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(particles)");
+        }
+        if (rc == LBM_OK) rc = cuda_check(h, cudaEventRecord(h->ev_pin, h->stream), "cudaEventRecord");
+        h->pin_busy = rc == LBM_OK;
+    }
     const size_t P = (size_t)h->cfg.max_particles;
     if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.pair_on, 0, P * P * 4, h->stream), "cudaMemsetAsync");
     if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.wall_on, 0, P * NWALL * 4, h->stream), "cudaMemsetAsync");
@@ -687,8 +713,6 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
     for (const size_t r : {h->L.bin, h->L.bin_alt})
         if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + r, 0, h->L.bin_bytes, h->stream), "cudaMemsetAsync");
     if (rc == LBM_OK) h->bin_clean[0] = h->bin_clean[1] = 1;
-    // the staging vector dies with this call
-    if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (rc == LBM_OK) h->np = n;
     h->fc_valid = 0;
     h->all_fixed = 1;
@@ -873,39 +897,44 @@ static int status_code(lbm_handle *h, const int *st) {
 
 int lbm_get_forces(lbm_handle *h, double *F, double *T, lbm_particle *state_out) {
     if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
-    int st[ST_SLOTS];
-    int rc = read_status(h, st);
-    if (rc != LBM_OK) return rc;
-    if ((rc = status_code(h, st)) != LBM_OK) return rc;
+    // everything is read into the page-locked buffer with asynchronous
+    // copies and one wait; the status is checked before anything is returned
     const size_t n = (size_t)h->np;
-    if (n == 0) return LBM_OK;
-    std::vector<long long> fix;
-    if (h->cfg.storage != LBM_STORE_F64) {
-        // FP32 and below: exact fixed-point totals (units of 2^-40)
-        if (F || T) {
-            fix.resize(n * 6);
-            rc = cuda_check(h, cudaMemcpyAsync(fix.data(), h->ws + last_bin_region(h) + h->L.ffix_off, n * 48,
+    const size_t P = (size_t)h->cfg.max_particles;
+    int *st = reinterpret_cast<int *>(h->pin);
+    long long *fix = reinterpret_cast<long long *>(h->pin + ST_SLOTS * 4);
+    double *fd = reinterpret_cast<double *>(h->pin + ST_SLOTS * 4 + P * 48);
+    DevParticle *dev = reinterpret_cast<DevParticle *>(h->pin + ST_SLOTS * 4 + P * 96);
+    const bool f64 = h->cfg.storage == LBM_STORE_F64;
+    int rc = cuda_check(h, cudaMemcpyAsync(st, h->ws + h->L.status, ST_SLOTS * 4, cudaMemcpyDeviceToHost, h->stream),
+                        "cudaMemcpyAsync(status)");
+    if (rc == LBM_OK && n > 0 && (F || T)) {
+        if (!f64) {
+            // FP32 and below: exact fixed-point totals (units of 2^-40)
+            rc = cuda_check(h, cudaMemcpyAsync(fix, h->ws + last_bin_region(h) + h->L.ffix_off, n * 48,
                                                cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(F)");
+        } else {
+            rc = cuda_check(h, cudaMemcpyAsync(fd, h->ws + h->L.Fh, n * 24, cudaMemcpyDeviceToHost, h->stream),
+                            "cudaMemcpyAsync(F)");
+            if (rc == LBM_OK)
+                rc = cuda_check(h, cudaMemcpyAsync(fd + 3 * n, h->ws + h->L.Th, n * 24, cudaMemcpyDeviceToHost,
+                                                   h->stream), "cudaMemcpyAsync(T)");
         }
-    } else {
-        if (F) rc = cuda_check(h, cudaMemcpyAsync(F, h->ws + h->L.Fh, n * 24, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(F)");
-        if (rc == LBM_OK && T)
-            rc = cuda_check(h, cudaMemcpyAsync(T, h->ws + h->L.Th, n * 24, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(T)");
     }
-    std::vector<DevParticle> dev;
-    if (rc == LBM_OK && state_out) {
-        dev.resize(n);
-        rc = cuda_check(h, cudaMemcpyAsync(dev.data(), h->ws + h->L.parts, n * sizeof(DevParticle),
-                                           cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(particles)");
-    }
+    if (rc == LBM_OK && n > 0 && state_out)
+        rc = cuda_check(h, cudaMemcpyAsync(dev, h->ws + h->L.parts, n * sizeof(DevParticle), cudaMemcpyDeviceToHost,
+                                           h->stream), "cudaMemcpyAsync(particles)");
     if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-    if (rc == LBM_OK && !fix.empty())
-        for (size_t j = 0; j < n; j++)
-            for (int a = 0; a < 3; a++) {
-                if (F) F[3 * j + a] = std::ldexp((double)fix[6 * j + a], -kForceFixBits);
-                if (T) T[3 * j + a] = std::ldexp((double)fix[6 * j + 3 + a], -kForceFixBits);
-            }
-    if (rc == LBM_OK && state_out) {
+    if (rc != LBM_OK) return rc;
+    h->pin_busy = false;  // every earlier upload from the buffer is done
+    if ((rc = status_code(h, st)) != LBM_OK) return rc;
+    if (n == 0) return LBM_OK;
+    for (size_t j = 0; j < n; j++)
+        for (int a = 0; a < 3; a++) {
+            if (F) F[3 * j + a] = f64 ? fd[3 * j + a] : std::ldexp((double)fix[6 * j + a], -kForceFixBits);
+            if (T) T[3 * j + a] = f64 ? fd[3 * n + 3 * j + a] : std::ldexp((double)fix[6 * j + 3 + a], -kForceFixBits);
+        }
+    if (state_out) {
         for (size_t j = 0; j < n; j++) {
             const DevParticle &d = dev[j];
             lbm_particle &p = state_out[j];
@@ -923,7 +952,7 @@ int lbm_get_forces(lbm_handle *h, double *F, double *T, lbm_particle *state_out)
             quat_mul(d.q, qUc, p.q);  // back to the caller's body frame
         }
     }
-    return rc;
+    return LBM_OK;
 }
 
 int lbm_get_contact_forces(lbm_handle *h, double *F, double *T) {
@@ -1075,8 +1104,9 @@ int lbm_destroy(lbm_handle *h) {
     if (h->aux) cudaStreamSynchronize(h->aux);
     if (h->hi) cudaStreamSynchronize(h->hi);
     release_profile(h);
-    for (cudaEvent_t e : {h->ev_fork, h->ev_bin, h->ev_plain, h->ev_near, h->ev_join})
+    for (cudaEvent_t e : {h->ev_fork, h->ev_bin, h->ev_plain, h->ev_near, h->ev_join, h->ev_pin})
         if (e) cudaEventDestroy(e);
+    if (h->pin) cudaFreeHost(h->pin);
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->hi) cudaStreamDestroy(h->hi);
     delete h;
