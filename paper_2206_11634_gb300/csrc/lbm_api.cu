@@ -572,6 +572,21 @@ int lbm_init(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda_st
     return init_handle(cfg, dev_ws, ws_bytes, cuda_stream, true, out);
 }
 
+// Zero a few word-aligned device ranges in one launch (the resets of
+// lbm_set_particles), instead of one memset node each.
+struct ClearRanges {
+    static constexpr int kMax = 8;
+    unsigned *p[kMax];
+    long long words[kMax];
+    int n;
+};
+__global__ void k_clear_ranges(ClearRanges R) {
+    for (int r = 0; r < R.n; r++)
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < R.words[r];
+             k += (long long)gridDim.x * blockDim.x)
+            R.p[r][k] = 0u;
+}
+
 // Whether the plain sweep may issue its pulls before it knows if the near
 // sweep takes the brick: worth it when the near set is a small share of the
 // bricks (its pulls are then wasted on few bricks), not when many particles
@@ -705,13 +720,23 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventRecord(h->ev_pin, h->stream), "cudaEventRecord");
         h->pin_busy = rc == LBM_OK;
     }
+    // contact pairs and walls, hydrodynamic totals, both per-step regions
     const size_t P = (size_t)h->cfg.max_particles;
-    if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.pair_on, 0, P * P * 4, h->stream), "cudaMemsetAsync");
-    if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.wall_on, 0, P * NWALL * 4, h->stream), "cudaMemsetAsync");
-    if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.Fh, 0, P * 24, h->stream), "cudaMemsetAsync");
-    if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + h->L.Th, 0, P * 24, h->stream), "cudaMemsetAsync");
-    for (const size_t r : {h->L.bin, h->L.bin_alt})
-        if (rc == LBM_OK) rc = cuda_check(h, cudaMemsetAsync(h->ws + r, 0, h->L.bin_bytes, h->stream), "cudaMemsetAsync");
+    if (rc == LBM_OK) {
+        ClearRanges R;
+        const size_t off[6] = {h->L.pair_on, h->L.wall_on, h->L.Fh, h->L.Th, h->L.bin, h->L.bin_alt};
+        const size_t bytes[6] = {P * P * 4, P * NWALL * 4, P * 24, P * 24, h->L.bin_bytes, h->L.bin_bytes};
+        R.n = 6;
+        long long most = 0;
+        for (int r = 0; r < 6; r++) {
+            R.p[r] = reinterpret_cast<unsigned *>(h->ws + off[r]);
+            R.words[r] = (long long)(bytes[r] / 4);
+            most = std::max(most, R.words[r]);
+        }
+        const int grid = (int)std::min<long long>((most + 255) / 256, 1024);
+        k_clear_ranges<<<grid > 0 ? grid : 1, 256, 0, h->stream>>>(R);
+        rc = cuda_check(h, cudaGetLastError(), "clear launch");
+    }
     if (rc == LBM_OK) h->bin_clean[0] = h->bin_clean[1] = 1;
     if (rc == LBM_OK) h->np = n;
     h->fc_valid = 0;
