@@ -320,6 +320,13 @@ int lbm_batch_step(lbm_batch *b, int nsteps);
  * particles after the last step (host double[n][3], either may be NULL). */
 int lbm_batch_get_forces(lbm_batch *b, int c, double *F, double *T);
 
+/* The same for every case at once: F and T (host double[N][3], N the sum of
+ * the cases' particle counts, either may be NULL) receive the particles of
+ * case 0, then case 1, ...  One wait on the batch's stream for all cases
+ * (per-case calls wait once each).  LBM_ERR_CAPACITY as lbm_batch_get_forces
+ * when a case's brick lists overflowed. */
+int lbm_batch_get_all_forces(lbm_batch *b, double *F, double *T);
+
 /* Synchronise and write case c's populations as FP64 f[i][z][y][x] to a
  * caller device buffer (as lbm_get_populations). */
 int lbm_batch_get_populations(lbm_batch *b, int c, void *dev_f);

@@ -1630,6 +1630,39 @@ int lbm_batch_get_forces(lbm_batch *b, int c, double *F, double *T) {
     return LBM_OK;
 }
 
+int lbm_batch_get_all_forces(lbm_batch *b, double *F, double *T) {
+    if (!b) return bfail(nullptr, LBM_ERR_BAD_ARG, "batch is NULL");
+    // every case's status and totals into its handle's page-locked buffer
+    // with asynchronous copies, then one wait
+    int rc = LBM_OK;
+    for (int c = 0; c < b->n && rc == LBM_OK; c++) {
+        lbm_handle *h = b->cases[c];
+        const size_t n = (size_t)h->np;
+        rc = bcheck(b, cudaMemcpyAsync(h->pin, h->ws + h->L.status, ST_SLOTS * 4, cudaMemcpyDeviceToHost, b->stream),
+                    "cudaMemcpyAsync(status)");
+        if (rc != LBM_OK || n == 0) continue;
+        const char *bin = b->steps > 0 && ((b->steps - 1) & 1) ? b->ws + b->bin1[c] : h->ws + h->L.bin;
+        rc = bcheck(b, cudaMemcpyAsync(h->pin + ST_SLOTS * 4, bin + h->L.ffix_off, n * 48, cudaMemcpyDeviceToHost,
+                                       b->stream), "cudaMemcpyAsync(F)");
+    }
+    if (rc == LBM_OK) rc = bcheck(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    if (rc != LBM_OK) return rc;
+    size_t row = 0;
+    for (int c = 0; c < b->n; c++) {
+        lbm_handle *h = b->cases[c];
+        const int *st = reinterpret_cast<const int *>(h->pin);
+        if (st[ST_ERR] & ERRB_BRICK_OVERFLOW)
+            return bfail(b, LBM_ERR_CAPACITY, "case %d: more than %d particles met one brick", c, MAXPB);
+        const long long *fix = reinterpret_cast<const long long *>(h->pin + ST_SLOTS * 4);
+        for (int j = 0; j < h->np; j++, row++)
+            for (int a = 0; a < 3; a++) {
+                if (F) F[3 * row + a] = std::ldexp((double)fix[6 * j + a], -kForceFixBits);
+                if (T) T[3 * row + a] = std::ldexp((double)fix[6 * j + 3 + a], -kForceFixBits);
+            }
+    }
+    return LBM_OK;
+}
+
 int lbm_batch_get_populations(lbm_batch *b, int c, void *dev_f) {
     if (!b) return bfail(nullptr, LBM_ERR_BAD_ARG, "batch is NULL");
     if (c < 0 || c >= b->n) return bfail(b, LBM_ERR_BAD_ARG, "case %d out of range", c);

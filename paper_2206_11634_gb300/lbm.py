@@ -86,6 +86,7 @@ _SIGS = {
     "lbm_batch_set_particles": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(LbmParticle), C.c_int]),
     "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_batch_get_forces": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "lbm_batch_get_all_forces": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_batch_get_populations": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "lbm_batch_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "lbm_batch_tune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -395,6 +396,16 @@ class Batch:
         self._ok(self.L.lbm_batch_get_forces(self.h, c, F.ctypes.data_as(C.POINTER(C.c_double)),
                                              T.ctypes.data_as(C.POINTER(C.c_double))), self.h)
         return F[: self.np[c]], T[: self.np[c]]
+
+    def all_forces(self):
+        """Force and torque of every case's particles, cases in order: two
+        (sum of particle counts, 3) arrays, read with one wait."""
+        n = max(1, sum(self.np))
+        F = np.zeros((n, 3))
+        T = np.zeros((n, 3))
+        self._ok(self.L.lbm_batch_get_all_forces(self.h, F.ctypes.data_as(C.POINTER(C.c_double)),
+                                                 T.ctypes.data_as(C.POINTER(C.c_double))), self.h)
+        return F[: sum(self.np)], T[: sum(self.np)]
 
     def populations(self, c: int):
         t = self.torch

@@ -69,6 +69,11 @@ def test_batch_matches_single_lattices(pkg, storage):
         assert np.array_equal(fb, fs), f"case {c}: populations differ"
         assert np.array_equal(Fb, Fs) and np.array_equal(Tb, Ts), f"case {c}: forces differ"
         assert np.abs(Fs).max() > 0
+    # all cases at once: the per-case rows, in case order
+    Fa, Ta = b.all_forces()
+    per = [b.forces(c) for c in range(len(wls))]
+    assert np.array_equal(Fa, np.concatenate([F for F, _ in per]))
+    assert np.array_equal(Ta, np.concatenate([T for _, T in per]))
 
 
 def test_batch_graph_replay_and_schedule(pkg):
