@@ -40,6 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS and % of HBM roofline per lattice sweep; drag rel. error vs FP64 oracle"
 UNIT = "MLUPS"
 BYTES_PER_VALUE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}  # one stored population
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, the vendor's figure (the roofline's peak is the measured copy)
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_plain_settling_metaball_128x128x256.txt")
 BRICK_NODES = 32 * 4 * 2
 SWEEP_SOURCES = ["k_plain.cuh", "lbm_internal.cuh"]
@@ -226,13 +227,14 @@ def make_lattice(pkg, wl, stream):
     return lat
 
 
-def oracle_sample(wl, steps: int):
-    """Time `steps` steps of the FP64 oracle on the full workload."""
+def oracle_sample(wl, steps: int, nthreads: int = 0):
+    """Time `steps` steps of the FP64 oracle on the full workload (nthreads
+    OpenMP threads; 0: all)."""
     import oracle
     o = oracle.Oracle(wl["nx"], wl["ny"], wl["nz"], Q=19, periodic=tuple(wl["periodic"]), tau=wl["tau"],
                       n_sub=wl["n_sub"], gravity=wl["gravity"], force=wl["force"], kn=wl["kn"], eta_n=wl["eta_n"],
                       kt=wl["kt"], eta_t=wl["eta_t"], mu_s=wl["mu_s"], c_tol=wl["c_tol"],
-                      u0=tuple(wl.get("u0", (0.0, 0.0, 0.0))))
+                      u0=tuple(wl.get("u0", (0.0, 0.0, 0.0))), nthreads=nthreads)
     o.set_particles([oracle.make_particle(p["cp"], p["K"], p["x"], q=p["q"], v=p["v"], w=p["w"], Rs=p["Rs"],
                                           density=p["density"], fixed=p["fixed"]) for p in wl["particles"]])
     o.step(1)  # first step pays the page-in of the arrays
@@ -408,6 +410,11 @@ def run_gpu(args):
         cpu = {"value": round(mlups, 4), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
                "sample": f"{cpu_steps} steps of the full {wl['nx']}x{wl['ny']}x{wl['nz']} workload, FP64, "
                          f"{dt:.1f} s"}
+        # one core as well, on a short window of the same workload
+        one_steps = max(1, cpu_steps // 40)
+        mlups1, dt1 = oracle_sample(wl, one_steps, nthreads=1)
+        cpu["one_core"] = {"value": round(mlups1, 4), "unit": UNIT, "cores": 1,
+                           "sample": f"{one_steps} steps, {dt1:.1f} s"}
 
     pop_mb = 19 * BYTES_PER_VALUE[wl["storage"]] * nodes / 1e6
     l2_note = (f"no flush: populations 2x{pop_mb:.0f} MB exceed the 129 MB L2" if pop_mb > 129 else
@@ -423,6 +430,7 @@ def run_gpu(args):
                     "steps": e2e_steps},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": f"{peak_kind} copy",
+                         "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4), "nominal_peak": NOMINAL_HBM_GBS,
                          "kernel": "k_sweep_plain", "bytes_per_launch": alg_bytes, "plain_nodes": plain_nodes,
                          "avg_launch_us": round(sweep_avg_s * 1e6, 3)},
             "kernels": kernels,
