@@ -236,11 +236,13 @@ int lbm_kernels_per_step(const lbm_handle *h);
  * allocated). */
 int lbm_profile(lbm_handle *h, int enable);
 /* As lbm_profile(), recording only the kernels whose bit is set in mask (bit
- * k: kernel k above); 0 stops recording.  The event records on the stream of
- * the particle chain lengthen a step by a few microseconds each, so a caller
- * timing whole steps records the plain sweep (bit 2, its own stream) alone.
- * LBM_ERR_BAD_ARG for bits beyond kernel 5. */
-int lbm_profile_mask(lbm_handle *h, unsigned mask);
+ * k: kernel k above), and of those only every every-th launch (every >= 1;
+ * lbm_profile_read then counts the recorded launches); mask 0 stops
+ * recording.  Event records lengthen a step by microseconds (those on the
+ * particle chain's stream most), so a caller timing whole steps records the
+ * plain sweep (bit 2, its own stream) alone, on a sample of its launches.
+ * LBM_ERR_BAD_ARG for bits beyond kernel 5 or every < 1. */
+int lbm_profile_mask(lbm_handle *h, unsigned mask, int every);
 int lbm_profile_read(lbm_handle *h, int kernel, double *total_ms, int64_t *launches);
 
 /* Change the stream later work is issued on. */

@@ -173,6 +173,8 @@ struct lbm_handle {
     unsigned prof;  // kernels whose launches are bracketed by events (bit k: kernel k)
     std::vector<cudaEvent_t> ev[kProfKernels][2];
     int64_t nrec[kProfKernels];
+    int64_t nseen[kProfKernels];  // launches since profiling was enabled (recorded or not)
+    int prof_every;               // record every prof_every-th launch of a profiled kernel
     Layout L;
     char *ws;
     cudaStream_t stream;
@@ -496,7 +498,8 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
     h->static_state = 0;
     h->snodes_n = 0;
     h->prof = 0u;
-    for (int k = 0; k < kProfKernels; k++) h->nrec[k] = 0;
+    for (int k = 0; k < kProfKernels; k++) h->nrec[k] = h->nseen[k] = 0;
+    h->prof_every = 1;
     std::snprintf(h->err, sizeof(h->err), "no error");
     // everything but the populations starts at zero: all nodes fluid, no
     // bricks occupied, no contacts, no errors
@@ -757,7 +760,9 @@ struct ProfScope {
     bool on;
     cudaStream_t st;
     ProfScope(lbm_handle *h_, int k_, bool launched, cudaStream_t st_)
-        : h(h_), k(k_), on(((h_->prof >> k_) & 1u) && launched && h_->nrec[k_] < kProfCap), st(st_) {
+        : h(h_), k(k_), on(((h_->prof >> k_) & 1u) && launched && h_->nseen[k_]++ % h_->prof_every == 0 &&
+                           h_->nrec[k_] < kProfCap),
+          st(st_) {
         if (!on) return;
         const size_t i = (size_t)h->nrec[k];
         if (h->ev[k][0].size() <= i) {
@@ -1058,7 +1063,7 @@ static void release_profile(lbm_handle *h) {
             for (cudaEvent_t e : h->ev[k][a]) cudaEventDestroy(e);
             h->ev[k][a].clear();
         }
-        h->nrec[k] = 0;
+        h->nrec[k] = h->nseen[k] = 0;
     }
 }
 
@@ -1069,17 +1074,20 @@ int lbm_profile(lbm_handle *h, int enable) {
     cudaStreamSynchronize(h->hi);
     release_profile(h);
     h->prof = enable != 0 ? (1u << kProfKernels) - 1u : 0u;
+    h->prof_every = 1;
     return LBM_OK;
 }
 
-int lbm_profile_mask(lbm_handle *h, unsigned mask) {
+int lbm_profile_mask(lbm_handle *h, unsigned mask, int every) {
     if (!h) return fail(nullptr, LBM_ERR_BAD_ARG, "handle is NULL");
     if (mask >> kProfKernels) return fail(h, LBM_ERR_BAD_ARG, "mask has bits beyond the %d kernels", kProfKernels);
+    if (every < 1) return fail(h, LBM_ERR_BAD_ARG, "every must be >= 1");
     cudaStreamSynchronize(h->stream);
     cudaStreamSynchronize(h->aux);
     cudaStreamSynchronize(h->hi);
     release_profile(h);
     h->prof = mask;
+    h->prof_every = every;
     return LBM_OK;
 }
 

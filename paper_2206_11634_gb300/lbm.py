@@ -75,7 +75,7 @@ _SIGS = {
                                    C.POINTER(C.c_int32)]),
     "lbm_kernels_per_step": (C.c_int, [C.c_void_p]),
     "lbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
-    "lbm_profile_mask": (C.c_int, [C.c_void_p, C.c_uint]),
+    "lbm_profile_mask": (C.c_int, [C.c_void_p, C.c_uint, C.c_int]),
     "lbm_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "lbm_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
@@ -299,14 +299,14 @@ class Lattice:
 
     KERNELS = ("k_bin", "k_flags", "k_sweep_plain", "k_sweep_near", "k_force_reduce", "k_dem")
 
-    def profile(self, enable: bool = True, kernels=None) -> None:
+    def profile(self, enable: bool = True, kernels=None, every: int = 1) -> None:
         """Record event pairs around every kernel (enable), or only around the
-        named ones (kernels: names from KERNELS)."""
+        named ones (kernels: names from KERNELS), on every every-th launch."""
         if enable and kernels is not None:
             mask = 0
             for name in kernels:
                 mask |= 1 << self.KERNELS.index(name)
-            self._ok(self.L.lbm_profile_mask(self.h, mask), self.h)
+            self._ok(self.L.lbm_profile_mask(self.h, mask, int(every)), self.h)
         else:
             self._ok(self.L.lbm_profile(self.h, int(enable)), self.h)
 

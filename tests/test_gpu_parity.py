@@ -510,7 +510,8 @@ def test_plain_speculation_same_bits(pkg, oracle_mod, W, storage):
 def test_profile_mask_records_chosen_kernels(pkg, oracle_mod, W):
     """Profiling every kernel records the binning, flags, plain and near
     sweeps of each step; with only the plain sweep named, four further steps
-    record it four times and nothing else."""
+    record it four times and nothing else; sampling every third launch
+    records three of seven."""
     wl = H.with_margin(oracle_mod, wl_multi(W))
     gpu = H.make_gpu(pkg, wl)
     gpu.set_particles(H.gpu_particles(pkg, wl))
@@ -525,6 +526,12 @@ def test_profile_mask_records_chosen_kernels(pkg, oracle_mod, W):
     gpu.profile(False)
     assert rec["k_sweep_plain"][1] == 4
     assert all(n == 0 for k, (_, n) in rec.items() if k != "k_sweep_plain"), rec
+    # a sample: launches 0, 3 and 6 of seven
+    gpu.profile(True, kernels=["k_sweep_plain"], every=3)
+    gpu.step(7)
+    rec = gpu.profile_read()
+    gpu.profile(False)
+    assert rec["k_sweep_plain"][1] == 3 and rec["k_sweep_plain"][0] > 0, rec
 
 
 def test_mass_conserved_closed_box_fp64(pkg, W):
