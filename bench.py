@@ -52,10 +52,12 @@ SWEEP_SOURCES = ["k_plain.cuh", "lbm_internal.cuh"]
 WORKLOADS = ("settling_metaball", "empty_box", "settling_sphere", "multi_particle", "batched_drag", "drag_gradient")
 
 
-def workload(name: str = "settling_metaball", storage: str | None = None):
+def workload(name: str = "settling_metaball", storage: str | None = None, dem: str | None = None):
     """The benchmark's workload (default) or a diagnostic one; storage
     overrides the workload's population storage."""
     wl = _workload(name)
+    if dem:
+        wl["dem"] = dem
     if storage:
         wl["storage"] = storage
         wl["name"] = f"{wl['name']}_{storage}" if storage != "f32" else wl["name"]
@@ -217,7 +219,8 @@ def max_over_ranks(dist, value: float) -> float:
 def make_lattice(pkg, wl, stream):
     kw = dict(periodic=wl["periodic"], lattice=19, storage=wl["storage"], n_sub=wl["n_sub"],
               max_particles=max(1, len(wl["particles"])), tau=wl["tau"], gravity=wl["gravity"], force=wl["force"],
-              kn=wl["kn"], eta_n=wl["eta_n"], kt=wl["kt"], eta_t=wl["eta_t"], mu_s=wl["mu_s"], c_tol=wl["c_tol"])
+              kn=wl["kn"], eta_n=wl["eta_n"], kt=wl["kt"], eta_t=wl["eta_t"], mu_s=wl["mu_s"], c_tol=wl["c_tol"],
+              dem_fp64=int(wl.get("dem", "fp64") == "fp64"))
     lat = pkg.Lattice(wl["nx"], wl["ny"], wl["nz"], stream=stream, **kw)
     parts = []
     for p in wl["particles"]:
@@ -315,7 +318,7 @@ def run_gpu(args):
     if rank == 0 or not os.path.exists(pkg.LIB_PATH):
         lib_build.build()
     barrier(dist)
-    wl = workload(args.workload, args.storage)
+    wl = workload(args.workload, args.storage, args.dem)
     nodes = wl["nx"] * wl["ny"] * wl["nz"]
     stream = torch.cuda.Stream()
     lat = make_lattice(pkg, wl, stream)
@@ -671,6 +674,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16", "f64"], default=None,
                     help="population storage (default: the workload's own)")
+    ap.add_argument("--dem", choices=["fp64", "fp32"], default=None,
+                    help="rigid-body integrator arithmetic (default fp64)")
     ap.add_argument("--workload", choices=WORKLOADS, default="settling_metaball",
                     help="diagnostic workloads besides the default benchmark workload")
     args = ap.parse_args()
