@@ -22,8 +22,11 @@
  * last node and the next, at -1/2 and n-1/2.
  *
  * Pins (tests/test_oracle_*.py) tie every function here to a closed form, an
- * invariant or a textbook special case; functions without such a pin are
- * listed in the header of tests/test_oracle_pins.py as "parity unpinned".
+ * invariant, a textbook special case, or, for the whole lattice step, a
+ * brute-force transcription written from the paper (tests/_bruteforce.py).
+ * Parity unpinned: the numerical values of the contact constants k_n, eta_n,
+ * k_t, eta_t, mu_s (the paper gives none; the law itself is pinned) and the
+ * paper's experimental comparisons (their data are not in its text).
  */
 #include <math.h>
 #include <stdint.h>

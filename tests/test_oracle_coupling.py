@@ -9,6 +9,10 @@ invariants that do not come from the oracle itself.
 - VIBB, Eqs. (19)-(25): in a linear velocity field at a resting wall the
   unknown equals the equilibrium of the field extended to the solid node
   (the mirror image of x_d about the wall), for every q in both branches;
+  in a quadratic profile at a moving wall, where each of the two linear
+  interpolants of Eqs. (23)-(24) errs by its own closed-form amount, the
+  velocity the unknown carries is the 1/3-2/3 mix of Eq. (25) of those two
+  errors and no other mix;
   the scheme is continuous at q = 1/2; halfway fallback at q = 1/2 is
   halfway bounce-back;
 - rest state: fluid at rest around any resting particle stays exact and the
@@ -141,6 +145,44 @@ def test_vibb_linear_field_resting_wall(oracle_mod, Q):
         ff, fff, target = _linear_field_case(o, rng, q, i)
         worst = max(worst, abs(o.vibb_unknown(i, q, ff, fff, np.zeros(3)) - target))
     assert worst < 1e-15
+
+
+def test_vibb_eq25_weights_quadratic_profile(oracle_mod):
+    """The velocity along one axis link is u(s) = U + a s + b s^2, s the
+    distance from the wall point into the fluid: the wall moves with U, x_f
+    sits at s = q, x_ff at 1 + q and x_d at 1 - q.  u*_d interpolates through
+    (q, 1 + q) for q <= 1/2 and through (0, q) above; u**_d through (0, 1 + q).
+    Both are exact for the linear part; for the quadratic part the error of
+    a linear interpolant through (s1, s2) at s is b (s - s1)(s - s2), so
+    u*_d = u(1 - q) + b e1 and u**_d = u(1 - q) + b e2 with
+    e1 = 2q(1 - 2q) (q <= 1/2) or (1 - q)(2q - 1) (q > 1/2), e2 = 2q(1 - q).
+    With f+ = f^eq at both fluid nodes (no non-equilibrium part) and unit
+    densities, the unknown is f^eq_d(1, u_d) + 6 w rho_f e_i.u_w, from which
+    u_d is recovered and compared with u(1 - q) + b (e1/3 + 2 e2/3)."""
+    o = oracle_mod.Oracle(2, 2, 2)
+    io = next(k for k in range(o.Q) if tuple(o.e[k]) == (1, 0, 0))   # d = +x, into the solid
+    i = o.opp[io]
+    w = o.w[io]
+    rng = np.random.default_rng(25)
+    worst = 0.0
+    for q in list(rng.uniform(0.02, 0.98, 60)) + [0.25, 0.5, 0.75]:
+        U, a, b = rng.uniform(-0.03, 0.03), rng.uniform(-0.03, 0.03), rng.uniform(0.01, 0.03)
+        u = lambda s: U + a * s + b * s * s     # x-component; the fluid lies toward -x
+        ff = o.equilibrium(1.0, np.array([u(q), 0.0, 0.0]))
+        fff = o.equilibrium(1.0, np.array([u(1 + q), 0.0, 0.0]))
+        uw = np.array([U, 0.0, 0.0])
+        unknown = o.vibb_unknown(i, q, ff, fff, uw)
+        feq_d = unknown - 6.0 * w * 1.0 * (-U)           # e_i . u_w with e_i = -x
+        ud = (-3.0 + np.sqrt(9.0 - 12.0 * (1.0 - feq_d / w))) / 6.0   # f^eq = w(1 + 3u + 3u^2)
+        e1 = 2 * q * (1 - 2 * q) if q <= 0.5 else (1 - q) * (2 * q - 1)
+        e2 = 2 * q * (1 - q)
+        exact = u(1 - q)
+        worst = max(worst, abs(ud - (exact + b * (e1 / 3 + 2 * e2 / 3))))
+        # another mix (alpha e1 + (1 - alpha) e2) would be visible here
+        if abs(e1 - e2) > 0.05:
+            for alpha in (0.0, 0.5, 1.0):
+                assert abs(ud - (exact + b * (alpha * e1 + (1 - alpha) * e2))) > 1e-4 * abs(e1 - e2)
+    assert worst < 1e-13
 
 
 def test_vibb_continuous_at_half(oracle_mod):
