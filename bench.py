@@ -220,7 +220,7 @@ def make_lattice(pkg, wl, stream):
     kw = dict(periodic=wl["periodic"], lattice=19, storage=wl["storage"], n_sub=wl["n_sub"],
               max_particles=max(1, len(wl["particles"])), tau=wl["tau"], gravity=wl["gravity"], force=wl["force"],
               kn=wl["kn"], eta_n=wl["eta_n"], kt=wl["kt"], eta_t=wl["eta_t"], mu_s=wl["mu_s"], c_tol=wl["c_tol"],
-              dem_fp64=int(wl.get("dem", "fp64") == "fp64"))
+              dem_mode=pkg.DEM_MODE[wl.get("dem", "fp64")])
     lat = pkg.Lattice(wl["nx"], wl["ny"], wl["nz"], stream=stream, **kw)
     parts = []
     for p in wl["particles"]:
@@ -674,8 +674,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16", "f64"], default=None,
                     help="population storage (default: the workload's own)")
-    ap.add_argument("--dem", choices=["fp64", "fp32"], default=None,
-                    help="rigid-body integrator arithmetic (default fp64)")
+    ap.add_argument("--dem", choices=["fp64", "fp32", "fp64_all"], default=None,
+                    help="DEM arithmetic: fp64 (default) the FP64 rigid-body integrator, FP32 contact geometry "
+                         "below FP64 storage; fp32 the compensated-FP32 integrator; fp64_all FP64 contact geometry too")
     ap.add_argument("--workload", choices=WORKLOADS, default="settling_metaball",
                     help="diagnostic workloads besides the default benchmark workload")
     args = ap.parse_args()

@@ -17,11 +17,16 @@
  *      Galilean-invariant momentum exchange (§2.3.2, Eqs. (28)-(29)) and the
  *      missing-force-point terms (§2.3.5 item 2, Eqs. (31)-(32));
  *   3. a deterministic reduction of the per-link force and torque into one
- *      FP64 total per particle;
+ *      total per particle: FP64 partials summed in a fixed order on FP64
+ *      lattices; below FP64 an exact sum of the FP32 link terms in 64-bit
+ *      fixed point (units of 2^-40), read out as FP64;
  *   4. n_sub DEM sub-steps (§2.3.4) with the hydrodynamic load frozen:
  *      metaball-metaball and metaball-wall contacts (§2.1.3-2.1.4, Eqs.
  *      (5)-(13)), the contact law of §2.1.1 (Eqs. (2)-(3)), velocity Verlet
- *      and Euler's equations in the body frame (Eq. (1)), in FP64.
+ *      and Euler's equations in the body frame (Eq. (1)).  By default the
+ *      rigid-body integrator is FP64, and so is the contact geometry on FP64
+ *      lattices; below FP64 the contact geometry is FP32 (lbm_config.dem_mode
+ *      gives the choices).
  *
  * Units are lattice units: dx = dt = C = 1, c_s^2 = 1/3.  Node (i,j,k) sits
  * at position (i,j,k); a non-periodic face is a resting no-slip wall halfway
@@ -63,9 +68,11 @@ enum lbm_status {
     LBM_OK = 0,
     LBM_ERR_BAD_ARG = -1,       /* invalid argument or configuration */
     LBM_ERR_WS_TOO_SMALL = -2,  /* workspace smaller than lbm_workspace_size() */
-    LBM_ERR_CAPACITY = -3,      /* more particles than max_particles, or a brick list overflowed */
+    LBM_ERR_CAPACITY = -3,      /* more particles than max_particles, a brick list overflowed, a
+                                   DEM table overflowed, or a particle moved further in one step
+                                   than the DEM's contact planning allowed */
     LBM_ERR_DIVERGED = -4,      /* non-finite populations or |u| > 0.5 seen by lbm_check() */
-    LBM_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
+    LBM_ERR_TIMEOUT = -5,       /* reserved: no kernel of this library waits on a device flag */
     LBM_ERR_CUDA = -6           /* a CUDA call failed; the message names it */
 };
 
@@ -78,6 +85,9 @@ enum lbm_storage {
 
 /* Simulation parameters.  Zero-initialise, then set what is needed; the
  * library's defaults are noted where 0 is not meaningful. */
+/* DEM arithmetic, lbm_config.dem_mode. */
+enum lbm_dem_mode { LBM_DEM_FP64 = 0, LBM_DEM_FP32_COMPENSATED = 1, LBM_DEM_FP64_ALL = 2 };
+
 typedef struct lbm_config {
     int32_t nx, ny, nz;        /* lattice nodes per axis, >= 2 */
     int32_t lattice;           /* 19 (D3Q19) or 15 (D3Q15, §2.2) */
@@ -87,11 +97,21 @@ typedef struct lbm_config {
     int32_t vibb;              /* 1 = VIBB on particle links; 0 = halfway bounce-back on all of them */
     int32_t missing_force;     /* 1 = add the missing-force-point terms of §2.3.5 item 2 */
     int32_t max_particles;     /* capacity reserved in the workspace, >= 1 */
-    int32_t dem_fp64;          /* 1 = DEM in FP64 arithmetic for every storage.  0 = FP64 for FP64
-                                  storage; for FP32/FP16/BF16 storage the DEM computes in FP32 with
-                                  the rigid-body state kept as compensated FP32 pairs (about 48
-                                  significant bits), when n <= 256 and the particles' control points
-                                  number <= 2048 in all, else in FP64 */
+    int32_t dem_mode;          /* arithmetic of the DEM (§2.1, §2.3.4), enum lbm_dem_mode.
+                                  0 (LBM_DEM_FP64, the default): the rigid-body integrator (velocity
+                                  Verlet, Euler's equations, the quaternion update) runs in FP64.  On
+                                  FP64 lattices the contact geometry and law are FP64 too; on
+                                  FP32/FP16/BF16 lattices they are evaluated in FP32 (overlap error
+                                  ~1e-6 lu) and summed into the FP64 kicks, for up to 256 particles
+                                  with up to 2048 control points in all (else as mode 2).
+                                  1 (LBM_DEM_FP32_COMPENSATED): lattices below FP64 only (FP64
+                                  lattices ignore it): the integrator computes every increment in
+                                  FP32 and keeps the state as compensated FP32 pairs (about 48
+                                  significant bits), with the same limits; faster, below the FP64
+                                  integrator's accuracy.
+                                  2 (LBM_DEM_FP64_ALL): contact geometry and law in FP64 as well, on
+                                  any lattice (one CTA; slow for many contacts on this GPU, whose FP64
+                                  rate is a small fraction of its FP32 rate). */
     int32_t q_exact;           /* 0 = link fraction q by Eq. (27); 1 = the root of Eq. (26) by Newton's
                                   method from Eq. (27)'s value (§2.3.1: tolerance 1e-7, at most 100
                                   iterations; a step leaving the bracket [0,1] bisects), in the

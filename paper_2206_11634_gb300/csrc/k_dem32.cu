@@ -22,6 +22,7 @@
 // w).  Candidate pairs come from a Verlet list (bounding spheres closer than a
 // skin), rebuilt when a particle has moved half the skin since.
 #include "lbm_internal.cuh"
+#include "dem_fp64.cuh"
 
 namespace lbmmb {
 namespace {
@@ -115,6 +116,8 @@ struct Shared {
     unsigned short up[kMaxP][kMaxAdj];  // partners j > i, ascending
     int dn[kMaxP][kMaxAdj];             // (m << 8 | slot of k in up[m]), m < k, ascending
     int nup[kMaxP], ndn[kMaxP];
+    int gid[kMaxP];                     // particle index of table entry k (k_dem32: k itself)
+    int n;                              // entries in the tables
     int ioff[kMaxP + 1];                // prefix sums of nup: item of (i, slot) = ioff[i] + slot
     // candidate pairs: contact history and results
     int it_on[kMaxItems];
@@ -322,12 +325,12 @@ __device__ bool wall_geom_f(const Params &P, const Shared &S, int k, int wall, f
 // Pair contact history of the candidate items to global memory (before the
 // list is rebuilt, and at the end of the launch).
 __device__ void store_items(const Params &P, Shared &S) {
-    const int np = P.np;
+    const int np = S.n;
     for (int i = threadIdx.x; i < np; i += blockDim.x)
         for (int s = 0; s < S.nup[i]; s++) {
             const int it = S.ioff[i] + s;
             if (it >= kMaxItems) break;
-            const int pidx = i * np + S.up[i][s];
+            const int pidx = S.gid[i] * P.np + S.gid[S.up[i][s]];
             P.pair_on[pidx] = S.it_on[it];
             for (int a = 0; a < 3; a++) {
                 P.pair_xm_f[3 * pidx + a] = S.it_xm[it][a];
@@ -341,7 +344,7 @@ __device__ void store_items(const Params &P, Shared &S) {
 // some pair is within reach of a contact this step (or one is active).
 // Loads the candidates' contact history into shared memory.
 __device__ void build_lists(const Params &P, Shared &S, int *possible) {
-    const int np = P.np, tid = threadIdx.x;
+    const int np = S.n, tid = threadIdx.x;
     const int nw = (np + 31) / 32;
     for (int idx = tid; idx < np * nw; idx += blockDim.x) {
         const int i = idx / nw, wd = idx % nw;
@@ -355,13 +358,14 @@ __device__ void build_lists(const Params &P, Shared &S, int *possible) {
             const float d2 = dot3f(d, d);
             const float brs = bri + S.brad[j];
             const float lim = brs + kSkin;
-            const bool on = P.pair_on[i * np + j] != 0;
+            const int pidx = S.gid[i] * P.np + S.gid[j];
+            const bool on = P.pair_on[pidx] != 0;
             if (d2 < lim * lim) {
                 m |= 1u << b;
                 const float lr = brs + ri + S.reach[j] + 1e-2f;
                 if (on || d2 <= lr * lr) *possible = 1;
             } else if (on) {
-                P.pair_on[i * np + j] = 0;
+                P.pair_on[pidx] = 0;
                 *possible = 1;
             }
         }
@@ -413,7 +417,7 @@ __device__ void build_lists(const Params &P, Shared &S, int *possible) {
         for (int s = 0; s < S.nup[i]; s++) {
             const int it = S.ioff[i] + s;
             if (it >= kMaxItems) break;
-            const int pidx = i * np + S.up[i][s];
+            const int pidx = S.gid[i] * P.np + S.gid[S.up[i][s]];
             S.it_on[it] = P.pair_on[pidx];
             for (int a = 0; a < 3; a++) {
                 S.it_xm[it][a] = P.pair_xm_f[3 * pidx + a];
@@ -426,7 +430,7 @@ __device__ void build_lists(const Params &P, Shared &S, int *possible) {
 // Pair contacts of the candidate list (one item per thread); results into
 // it_res (zeros when not in contact).
 __device__ void pair_contacts(const Params &P, Shared &S, float h) {
-    const int np = P.np;
+    const int np = S.n;
     const int total = min(S.ioff[np], kMaxItems);
     for (int it = threadIdx.x; it < total; it += blockDim.x) {
         int lo = 0, hi = np - 1;  // item -> (i, slot): last i with ioff[i] <= it
@@ -506,7 +510,7 @@ __device__ void gather_contacts(const Params &P, Shared &S, int k, float h, floa
 
 // Rotated control points of particle k into the shared table.
 __device__ __forceinline__ void put_rc(const Params &P, Shared &S, int k, const float q[4]) {
-    const DevParticle &p = P.parts[k];
+    const DevParticle &p = P.parts[S.gid[k]];
     for (int c = 0; c < p.ncp; c++) {
         float r[3];
         qrot_f(q, p.cpb_f[c], r, true);
@@ -547,7 +551,9 @@ __global__ void __launch_bounds__(kThreads) k_dem32(Params P) {
         int o = 0;
         for (int k = 0; k < np; k++) { S.cpo[k] = o; o += P.parts[k].ncp; }
         S.cpo[np] = o;
+        S.n = np;
     }
+    for (int k = tid; k < np; k += blockDim.x) S.gid[k] = k;
     __syncthreads();
 
     // shared state, reach over the step without contacts (|v| + |a|), walls
@@ -806,6 +812,236 @@ __global__ void __launch_bounds__(kThreads) k_dem32(Params P) {
         else if (c < 16) P.Fc[3 * k + c - 13] = (double)S.Fc[k][c - 13];
         else P.Tc[3 * k + c - 16] = (double)S.Tc[k][c - 16];
     }
+}
+
+// ---------------------------------------------------------------------------
+// k_dem64c: the active particles of k_dem64_plan (those that can meet a wall
+// or another particle during the step), one thread each, one CTA.  The
+// rigid-body integrator is FP64: state, increments and the Verlet /
+// Euler / quaternion arithmetic are those of k_dem (velocity Verlet in
+// kick-drift-kick form, Euler's equations in the principal frame, q <- q (x)
+// exp(h w/2), the closing rotational half-kick implicit by ROT_ITERS
+// sweeps).  The contact geometry (Eqs. (5)-(13)) and the contact law
+// (Eqs. (2)-(3)) are evaluated in FP32 from FP32 copies as in k_dem32 (the
+// positions as hi + lo pairs of the FP64 values), and their per-particle
+// sums enter the FP64 kicks.  The angular velocity is carried in the
+// principal frame across the sub-steps (k_dem rotates it to the world frame
+// and back around each one, a rounding difference only).  The quaternion is
+// renormalised once, at the end of the step.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_dem64c(Params P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Shared &S = *reinterpret_cast<Shared *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int na = P.dem_list[1];
+    if (na == 0) return;
+    const int *act = P.dem_list + 2 + P.np;
+    const double h = 1.0 / P.n_sub, hh = 0.5 * h;
+    const float hf = P.h_f;
+    const bool own = tid < na;
+    const int g = own ? act[tid] : 0;
+    DevParticle *pp = own ? &P.parts[g] : nullptr;
+
+    double x[3] = {0, 0, 0}, x0[3] = {0, 0, 0}, v[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, wb[3] = {0, 0, 0};
+    double Fh[3] = {0, 0, 0}, Th[3] = {0, 0, 0}, bg[3] = {0, 0, 0}, inv_m = 0.0;
+    bool mov = false;
+    float reach = 0.f;
+    if (own) {
+        for (int a = 0; a < 3; a++) {
+            x[a] = pp->x[a];
+            x0[a] = x[a];
+            v[a] = pp->v[a];
+            Fh[a] = P.Fh[3 * g + a];
+            Th[a] = P.Th[3 * g + a];
+            bg[a] = pp->buoy * P.g[a];
+        }
+        for (int a = 0; a < 4; a++) q[a] = pp->q[a];
+        rot_body(q, pp->w, wb);
+        inv_m = pp->inv_mass;
+        mov = !pp->fixed;
+        reach = dem_reach(P, *pp, g);
+    }
+    if (tid == 0) {
+        int o = 0;
+        for (int k = 0; k < na; k++) { S.cpo[k] = o; o += P.parts[act[k]].ncp; }
+        S.cpo[na] = o;
+        S.n = na;
+        if (o > kDem32MaxCp) atomicOr(&P.status[ST_ERR], ERRB_DEM_CAPACITY);
+    }
+    for (int k = tid; k < na; k += blockDim.x) S.gid[k] = act[k];
+    __syncthreads();
+    if (S.cpo[na] > kDem32MaxCp) return;
+
+    // FP32 tables of the start state
+    auto publish = [&](const double wbody[3]) {
+        float qf[4], wf[3], ww[3];
+        for (int a = 0; a < 4; a++) qf[a] = (float)q[a];
+        for (int a = 0; a < 3; a++) wf[a] = (float)wbody[a];
+        qrot_f(qf, wf, ww, true);
+        for (int a = 0; a < 3; a++) {
+            const float hi = (float)x[a];
+            S.xh[tid][a] = hi;
+            S.xl[tid][a] = (float)(x[a] - (double)hi);
+            S.v[tid][a] = (float)v[a];
+            S.w[tid][a] = ww[a];
+        }
+    };
+    if (own) {
+        publish(wb);
+        float qf[4];
+        for (int a = 0; a < 4; a++) qf[a] = (float)q[a];
+        S.reach[tid] = reach;
+        S.brad[tid] = pp->brad_f;
+        S.Rs[tid] = pp->Rs_f;
+        put_rc(P, S, tid, qf);
+        for (int wall = 0; wall < NWALL; wall++) {
+            const int wj = g * NWALL + wall;
+            S.w_on[tid][wall] = P.wall_on[wj];
+            for (int a = 0; a < 3; a++) {
+                S.w_xcw[tid][wall][a] = P.wall_xcw_f[3 * wj + a];
+                S.w_xi[tid][wall][a] = P.wall_xi_f[3 * wj + a];
+            }
+        }
+    }
+    __syncthreads();
+    int dummy = 0;
+    if (na > 1) build_lists(P, S, &dummy);
+    else if (tid == 0) {
+        S.nup[0] = 0; S.ndn[0] = 0; S.ioff[0] = 0; S.ioff[1] = 0;
+        for (int a = 0; a < 3; a++) S.xref[0][a] = S.xh[0][a] + S.xl[0][a];
+    }
+    __syncthreads();
+    // contact load at the start: left by the previous step's DEM (same
+    // state), unless the particles were set since
+    if (!P.fc_valid) {
+        pair_contacts(P, S, 0.f);
+        __syncthreads();
+        if (own) {
+            float F[3], T[3];
+            gather_contacts(P, S, tid, 0.f, F, T);
+            for (int a = 0; a < 3; a++) { S.Fc[tid][a] = F[a]; S.Tc[tid][a] = T[a]; }
+        }
+    } else if (own) {
+        for (int a = 0; a < 3; a++) {
+            S.Fc[tid][a] = (float)P.Fc[3 * g + a];
+            S.Tc[tid][a] = (float)P.Tc[3 * g + a];
+        }
+    }
+    __syncthreads();
+    for (int sub = 0; sub < P.n_sub; sub++) {
+        double wh[3] = {wb[0], wb[1], wb[2]};
+        int moved = 0;
+        if (own) {
+            if (mov) {
+                // first half-kick and drift
+                for (int a = 0; a < 3; a++) {
+                    const double acc = bg[a] + (Fh[a] + (double)S.Fc[tid][a]) * inv_m;
+                    v[a] += hh * acc;
+                    x[a] += h * v[a];
+                }
+                // rotation: half-kick, then q <- q (x) exp(h w_half / 2)
+                double Tw[3], Tb[3], dw[3];
+                for (int a = 0; a < 3; a++) Tw[a] = Th[a] + (double)S.Tc[tid][a];
+                rot_body(q, Tw, Tb);
+                euler_rate(*pp, wb, Tb, dw);
+                for (int a = 0; a < 3; a++) wh[a] = wb[a] + hh * dw[a];
+                quat_step(q, wh, h);
+            }
+            publish(wh);
+            float dr2 = 0.f;
+            for (int a = 0; a < 3; a++) {
+                const float dd = (S.xh[tid][a] - S.xref[tid][a]) + S.xl[tid][a];
+                dr2 += dd * dd;
+            }
+            if (mov) {
+                float qf[4];
+                for (int a = 0; a < 4; a++) qf[a] = (float)q[a];
+                put_rc(P, S, tid, qf);
+            }
+            moved = dr2 > 0.25f * kSkin * kSkin;
+        }
+        moved = __syncthreads_or(moved);
+        if (moved && na > 1) {
+            store_items(P, S);
+            __syncthreads();
+            build_lists(P, S, &dummy);
+        }
+        pair_contacts(P, S, hf);
+        __syncthreads();
+        if (own) {
+            float F[3], T[3];
+            gather_contacts(P, S, tid, hf, F, T);
+            for (int a = 0; a < 3; a++) { S.Fc[tid][a] = F[a]; S.Tc[tid][a] = T[a]; }
+            if (mov) {
+                // closing half-kick with the new contact load
+                for (int a = 0; a < 3; a++) v[a] += hh * (bg[a] + (Fh[a] + (double)F[a]) * inv_m);
+                double Tw[3], Tb[3], dw[3], w1[3] = {wh[0], wh[1], wh[2]};
+                for (int a = 0; a < 3; a++) Tw[a] = Th[a] + (double)T[a];
+                rot_body(q, Tw, Tb);
+                for (int it = 0; it < ROT_ITERS; it++) {
+                    euler_rate(*pp, w1, Tb, dw);
+                    for (int a = 0; a < 3; a++) w1[a] = wh[a] + hh * dw[a];
+                }
+                for (int a = 0; a < 3; a++) wb[a] = w1[a];
+            }
+        }
+        __syncthreads();
+    }
+    if (own && mov) quat_normalize(q);
+    // contact load of the end state (springs not advanced): reported by
+    // lbm_get_contact_forces and the start load of the next step
+    if (own) {
+        publish(wb);
+        if (mov) {
+            float qf[4];
+            for (int a = 0; a < 4; a++) qf[a] = (float)q[a];
+            put_rc(P, S, tid, qf);
+        }
+    }
+    __syncthreads();
+    pair_contacts(P, S, 0.f);
+    __syncthreads();
+    if (own) {
+        float F[3], T[3];
+        gather_contacts(P, S, tid, 0.f, F, T);
+        for (int wall = 0; wall < NWALL; wall++) {
+            const int wj = g * NWALL + wall;
+            P.wall_on[wj] = S.w_on[tid][wall];
+            for (int a = 0; a < 3; a++) {
+                P.wall_xcw_f[3 * wj + a] = S.w_xcw[tid][wall][a];
+                P.wall_xi_f[3 * wj + a] = S.w_xi[tid][wall][a];
+            }
+        }
+        for (int a = 0; a < 3; a++) {
+            P.Fc[3 * g + a] = (double)F[a];
+            P.Tc[3 * g + a] = (double)T[a];
+        }
+        if (mov) {
+            double ww[3];
+            rot_world(q, wb, ww);
+            for (int a = 0; a < 3; a++) {
+                pp->x[a] = x[a];
+                pp->v[a] = v[a];
+                pp->w[a] = ww[a];
+            }
+            for (int a = 0; a < 4; a++) pp->q[a] = q[a];
+        }
+        // the planning assumed no larger displacement (contacts with
+        // inactive particles would have been missed otherwise)
+        double d2 = 0.0;
+        for (int a = 0; a < 3; a++) d2 += (x[a] - x0[a]) * (x[a] - x0[a]);
+        if (d2 > (double)reach * (double)reach) atomicOr(&P.status[ST_ERR], ERRB_DEM_REACH);
+    }
+    if (na > 1) store_items(P, S);
+}
+
+void launch_dem64c(const Params &P, cudaStream_t st) {
+    static bool attr_set[64] = {};
+    const int bytes = (int)sizeof(Shared);
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev])
+        attr_set[dev] = cudaFuncSetAttribute(k_dem64c, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+    k_dem64c<<<1, P.np <= 32 ? 32 : kThreads, bytes, st>>>(P);
 }
 
 // One CTA: a single warp for a few particles (the barriers between the

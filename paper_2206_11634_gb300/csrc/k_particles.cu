@@ -6,6 +6,7 @@
 //                  (§2.1.3-2.1.4), contact law (§2.1.1), velocity Verlet and
 //                  Euler's equations in the body frame (Eq. (1)).
 #include "k_flags.cuh"
+#include "dem_fp64.cuh"
 
 namespace lbmmb {
 
@@ -174,12 +175,6 @@ __global__ void __launch_bounds__(256) k_force_reduce(Params P) {
 // ---------------------------------------------------------------------------
 // DEM.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
-__device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
-    c[0] = a[1] * b[2] - a[2] * b[1];
-    c[1] = a[2] * b[0] - a[0] * b[2];
-    c[2] = a[0] * b[1] - a[1] * b[0];
-}
 __device__ __forceinline__ void rotm(const double q[4], double R[9]) {
     const double w = q[0], x = q[1], y = q[2], z = q[3];
     R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
@@ -453,60 +448,6 @@ __device__ void contacts(const Params &P, double h) {
     __syncthreads();
 }
 
-// Euler's equations in the principal frame (Eq. (1), rotational part):
-// dw_l/dt = T_l / I_l + (I_{l+1} - I_{l+2}) / I_l w_{l+1} w_{l+2}.
-__device__ __forceinline__ void euler_rate(const DevParticle &p, const double wb[3], const double Tb[3], double out[3]) {
-    out[0] = fma(p.cI[0] * wb[1], wb[2], p.iI[0] * Tb[0]);
-    out[1] = fma(p.cI[1] * wb[2], wb[0], p.iI[1] * Tb[1]);
-    out[2] = fma(p.cI[2] * wb[0], wb[1], p.iI[2] * Tb[2]);
-}
-
-// R(q) v and R(q)^T v for a unit quaternion (w, u): with c = u x v,
-// R v = v + 2 w c + 2 u x c and R^T v = v - 2 w c + 2 u x c.
-__device__ __forceinline__ void rot_world(const double q[4], const double v[3], double r[3]) {
-    const double u[3] = {q[1], q[2], q[3]};
-    double c[3], uc[3];
-    cross3(u, v, c);
-    cross3(u, c, uc);
-    for (int a = 0; a < 3; a++) r[a] = v[a] + 2.0 * (q[0] * c[a] + uc[a]);
-}
-__device__ __forceinline__ void rot_body(const double q[4], const double v[3], double r[3]) {
-    const double u[3] = {q[1], q[2], q[3]};
-    double c[3], uc[3];
-    cross3(u, v, c);
-    cross3(u, c, uc);
-    for (int a = 0; a < 3; a++) r[a] = v[a] + 2.0 * (uc[a] - q[0] * c[a]);
-}
-
-// q <- q (x) exp(h w_b / 2), the rotation by the body-frame angular velocity
-// w_b over h.  For |w_b| h / 2 <= 1/16 the sine and cosine come from their
-// Taylor series (truncation below 1e-19), which needs no square root.
-__device__ __forceinline__ void quat_step(double q[4], const double wb[3], double h) {
-    const double w2 = dot3(wb, wb);
-    const double a2 = 0.25 * h * h * w2;  // (theta/2)^2
-    double s, c;  // s = sin(theta/2) / |w_b|, c = cos(theta/2)
-    if (a2 <= 1.0 / 256.0) {
-        s = 0.5 * h * (1.0 + a2 * (-1.0 / 6.0 + a2 * (1.0 / 120.0 + a2 * (-1.0 / 5040.0 + a2 * (1.0 / 362880.0 + a2 * (-1.0 / 39916800.0))))));
-        c = 1.0 + a2 * (-0.5 + a2 * (1.0 / 24.0 + a2 * (-1.0 / 720.0 + a2 * (1.0 / 40320.0 + a2 * (-1.0 / 3628800.0)))));
-    } else {
-        const double wn = sqrt(w2);
-        double sn;
-        sincos(0.5 * h * wn, &sn, &c);
-        s = sn / wn;
-    }
-    const double d[4] = {c, s * wb[0], s * wb[1], s * wb[2]};
-    const double r0 = q[0] * d[0] - q[1] * d[1] - q[2] * d[2] - q[3] * d[3];
-    const double r1 = q[0] * d[1] + q[1] * d[0] + q[2] * d[3] - q[3] * d[2];
-    const double r2 = q[0] * d[2] - q[1] * d[3] + q[2] * d[0] + q[3] * d[1];
-    const double r3 = q[0] * d[3] + q[1] * d[2] - q[2] * d[1] + q[3] * d[0];
-    q[0] = r0; q[1] = r1; q[2] = r2; q[3] = r3;
-}
-
-__device__ __forceinline__ void quat_normalize(double q[4]) {
-    const double in = rsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    for (int a = 0; a < 4; a++) q[a] *= in;
-}
-
 // One rotational sub-step: half-kick, rotate with the half-step rate, then
 // the closing half-kick solved by ROT_ITERS fixed-point sweeps; wb and Tb are
 // body-frame (principal) quantities, Tb is refreshed for the new orientation.
@@ -712,6 +653,107 @@ __device__ void rotate_free_quad(unsigned mk, const DevParticle &p, const double
     if (lane > 0) out.w[m] = ww;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 rigid-body integration on lattices stored below FP64 (the default):
+// k_dem64_plan splits the particles of the step, then k_dem64_free moves the
+// ones that cannot touch anything during the step and k_dem64c (k_dem32.cu)
+// the others, on two streams at once.
+// ---------------------------------------------------------------------------
+
+// One CTA.  The hydrodynamic load as FP64 totals (from the sweep's
+// fixed-point sums), then the split: a particle is active when its bounding
+// sphere can reach a wall, or another particle's, during the step (gap <=
+// reach_i + reach_j, dem_reach); active and inactive particles keep their
+// index order in P.dem_list: [0] inactive count, [1] active count, from [2]
+// the inactive ones, from [2 + np] the active ones.  A pair in contact at the
+// end of the last step overlaps, so it is active again: the contact history
+// of inactive particles is empty.
+__global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
+    __shared__ float xs[kFastMaxParticles][3], reach[kFastMaxParticles], br[kFastMaxParticles];
+    __shared__ int act[kFastMaxParticles];
+    const int np = P.np;
+    for (int i = threadIdx.x; i < np * 6; i += blockDim.x) {
+        const double v = (double)(long long)P.Ffix[i] * (1.0 / (double)(1ull << kForceFixBits));
+        const int k = i / 6, c = i % 6;
+        if (c < 3) P.Fh[3 * k + c] = v;
+        else P.Th[3 * k + c - 3] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const DevParticle &p = P.parts[k];
+        const float r = dem_reach(P, p, k);
+        for (int a = 0; a < 3; a++) xs[k][a] = (float)p.x[a];
+        reach[k] = r;
+        br[k] = (float)p.brad;
+        int on = 0;
+        for (int wall = 0; wall < NWALL; wall++) {
+            const int ax = wall / 2, side = wall % 2;
+            if (P.per[ax]) continue;
+            const float plane = side ? (float)dim_of(P, ax) - 0.5f : -0.5f;
+            if (fabsf(plane - xs[k][ax]) - br[k] <= r + 1e-2f) on = 1;
+        }
+        act[k] = on;
+    }
+    __syncthreads();
+    const long long npairs = (long long)np * (np - 1) / 2;
+    for (long long idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
+        int i = (int)((2.0 * np - 1.0 - sqrt((2.0 * np - 1.0) * (2.0 * np - 1.0) - 8.0 * (double)idx)) * 0.5);
+        while ((long long)i * (2 * np - i - 1) / 2 > idx) i--;
+        while ((long long)(i + 1) * (2 * np - i - 2) / 2 <= idx) i++;
+        const int j = (int)(idx - (long long)i * (2 * np - i - 1) / 2) + i + 1;
+        float d2 = 0.f;
+        for (int a = 0; a < 3; a++) {
+            float d = xs[j][a] - xs[i][a];
+            if (P.per[a]) {
+                const float L = (float)dim_of(P, a);
+                d -= L * rintf(d / L);
+            }
+            d2 += d * d;
+        }
+        const float lim = br[i] + br[j] + reach[i] + reach[j] + 1e-2f;
+        if (d2 <= lim * lim) { act[i] = 1; act[j] = 1; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nf = 0, na = 0;
+        for (int k = 0; k < np; k++) {
+            if (act[k]) P.dem_list[2 + np + na++] = k;
+            else P.dem_list[2 + nf++] = k;
+        }
+        P.dem_list[0] = nf;
+        P.dem_list[1] = na;
+    }
+}
+
+// Four lanes per particle, 32 particles per CTA: the inactive particles of
+// the plan.  Translation in closed form over the unit step (x += v + a/2, v
+// += a: what the n_s kick-drift-kick sub-steps give under the constant
+// force), rotation sub-stepped by rotate_free_quad, all FP64; no contact load.
+__global__ void __launch_bounds__(128) k_dem64_free(Params P) {
+    const int nf = P.dem_list[0];
+    const int slot = blockIdx.x * 32 + (int)(threadIdx.x >> 2);
+    if (blockIdx.x * 32 + (int)((threadIdx.x & ~31u) >> 2) >= nf) return;  // the whole warp is idle
+    const bool has = slot < nf;
+    const int k = has ? P.dem_list[2 + slot] : 0;
+    const int lane = threadIdx.x & 3;
+    if (has) {
+        DevParticle &p = P.parts[k];
+        if (lane > 0) {
+            const int m = lane - 1;
+            if (!p.fixed) {
+                const double acc = p.buoy * P.g[m] + P.Fh[3 * k + m] * p.inv_mass;
+                p.x[m] += p.v[m] + 0.5 * acc;
+                p.v[m] += acc;
+            }
+            P.Fc[3 * k + m] = 0.0;
+            P.Tc[3 * k + m] = 0.0;
+        }
+    }
+    const bool moving = has && !P.parts[k].fixed;
+    const unsigned mk = __ballot_sync(0xffffffffu, moving);
+    if (moving) rotate_free_quad(mk, P.parts[k], P.Th + 3 * k, 1.0 / P.n_sub, P.n_sub, P.parts[k]);
+}
+
 // One CTA.  Kick-drift-kick velocity Verlet with the hydrodynamic load frozen
 // over the n_s sub-steps (§2.3.4); rotation by Euler's equations in the body
 // frame.  When no contact can occur during the step, the translation of the
@@ -815,10 +857,22 @@ void launch_bin(const Params &P, cudaStream_t st) {
 void launch_force_reduce(const Params &P, cudaStream_t st) {
     if (P.np > 0) k_force_reduce<<<P.np, 256, 0, st>>>(P);
 }
-void launch_dem(const Params &P, cudaStream_t st) {
+void launch_dem(const Params &P, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_split, cudaEvent_t ev_free) {
     if (P.np <= 0 || P.n_sub <= 0) return;
-    if (P.dem_f32) launch_dem32(P, st);
-    else k_dem<<<1, 256, 0, st>>>(P);
+    if (P.dem_mode == DEM_FP32) {
+        launch_dem32(P, st);
+    } else if (P.dem_mode == DEM_FP64_INTEGRATOR) {
+        // plan, then the inactive particles on st2 beside the active ones on st
+        k_dem64_plan<<<1, 256, 0, st>>>(P);
+        cudaEventRecord(ev_split, st);
+        cudaStreamWaitEvent(st2, ev_split, 0);
+        k_dem64_free<<<(P.np + 31) / 32, 128, 0, st2>>>(P);
+        cudaEventRecord(ev_free, st2);
+        launch_dem64c(P, st);
+        cudaStreamWaitEvent(st, ev_free, 0);
+    } else {
+        k_dem<<<1, 256, 0, st>>>(P);
+    }
 }
 
 }  // namespace lbmmb

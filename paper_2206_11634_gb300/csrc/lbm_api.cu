@@ -39,6 +39,7 @@ struct Layout {
     size_t pairF, pair_on, pair_xi, pair_xm, wall_on, wall_xi, wall_xcw;
     size_t pair_xi_f, pair_xm_f, wall_xi_f, wall_xcw_f;
     size_t sskip, snodes, slinks, scount, smf;  // fixed-geometry sweep (below FP64)
+    size_t dem_list;   // k_dem64_plan's split of the particles [2 + 2P]
     int snode_cap, slink_cap;
     size_t status;
     size_t total;
@@ -69,7 +70,7 @@ const char *check_config(const lbm_config *c) {
     for (int a = 0; a < 3; a++)
         if (c->periodic[a] != 0 && c->periodic[a] != 1) return "periodic[] must be 0 or 1";
     if (c->mass_spacing < 0.0) return "mass_spacing must be >= 0";
-    if (c->dem_fp64 != 0 && c->dem_fp64 != 1) return "dem_fp64 must be 0 or 1";
+    if (c->dem_mode < LBM_DEM_FP64 || c->dem_mode > LBM_DEM_FP64_ALL) return "dem_mode must be one of enum lbm_dem_mode";
     if (c->q_exact != 0 && c->q_exact != 1) return "q_exact must be 0 or 1";
     return nullptr;
 }
@@ -139,6 +140,7 @@ void make_layout(const lbm_config *c, Layout *L) {
     L->slinks = take((size_t)L->slink_cap * sizeof(StaticLink));
     L->scount = take(fixed_sweep ? 8 : 0);
     L->smf = take(fixed_sweep ? P * 48 : 0);
+    L->dem_list = take((2 + 2 * P) * 4);
     L->status = take(ST_SLOTS * 4);
     L->total = o;
 }
@@ -162,6 +164,10 @@ struct lbm_handle {
     // sweep of t+1 waits for it (it reads its halo).
     cudaStream_t aux, hi;
     cudaEvent_t ev_fork, ev_bin, ev_plain, ev_near, ev_join;
+    // FP64-integrator DEM: the particles that cannot touch anything during a
+    // step move on dem2 (high priority), forked from hi after the split
+    cudaStream_t dem2;
+    cudaEvent_t ev_dsplit, ev_dfree;
     // page-locked host buffer for the particle exchange (set_particles,
     // get_forces): copies from and to it are asynchronous, so a call waits on
     // the stream once; ev_pin marks the end of the last upload from it
@@ -181,7 +187,7 @@ struct lbm_handle {
     int cur;    // populations consistent with flags[fcur] live in f[cur]
     int fcur;
     int np;
-    int dem_f32;   // the FP32 DEM runs (storage, dem_fp64 and the particle set allow it)
+    int dem_mode;  // enum DemKernel: the DEM kernels of the current particle set
     int fc_valid;  // the DEM of the last step left the contact load of the current state
     int all_fixed;     // every particle is fixed: the geometry cannot change between set_particles calls
     int static_steps;  // steps run since set_particles with all_fixed (saturating)
@@ -276,7 +282,8 @@ Params make_params(lbm_handle *h) {
     P.pair_xm_f = at<float>(h, h->L.pair_xm_f);
     P.wall_xi_f = at<float>(h, h->L.wall_xi_f);
     P.wall_xcw_f = at<float>(h, h->L.wall_xcw_f);
-    P.dem_f32 = h->dem_f32;
+    P.dem_mode = h->dem_mode;
+    P.dem_list = at<int>(h, h->L.dem_list);
     P.fc_valid = h->fc_valid;
     P.plain_grid = h->plain_per_sm > 0 ? h->plain_per_sm * h->nsm : 0;
     P.chain_grid = h->chain_per_sm > 0 ? h->chain_per_sm * h->nsm : 0;
@@ -504,8 +511,10 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
     // everything but the populations starts at zero: all nodes fluid, no
     // bricks occupied, no contacts, no errors
     const size_t zero_from = L.flags[0];
-    h->aux = h->hi = nullptr;
+    h->aux = h->hi = h->dem2 = nullptr;
     h->ev_fork = h->ev_bin = h->ev_plain = h->ev_near = h->ev_join = nullptr;
+    h->ev_dsplit = h->ev_dfree = nullptr;
+    h->dem_mode = DEM_FP64_ALL;
     h->pin = nullptr;
     h->ev_pin = nullptr;
     h->pin_busy = false;
@@ -535,6 +544,10 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_bin, cudaEventDisableTiming), "cudaEventCreate");
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_plain, cudaEventDisableTiming), "cudaEventCreate");
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_near, cudaEventDisableTiming), "cudaEventCreate");
+        if (rc == LBM_OK)
+            rc = cuda_check(h, cudaStreamCreateWithPriority(&h->dem2, cudaStreamNonBlocking, prio_high), "cudaStreamCreateWithPriority");
+        if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_dsplit, cudaEventDisableTiming), "cudaEventCreate");
+        if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_dfree, cudaEventDisableTiming), "cudaEventCreate");
     }
     if (rc == LBM_OK) rc = cuda_check(h, cudaHostAlloc((void **)&h->pin, h->pin_bytes, cudaHostAllocDefault), "cudaHostAlloc");
     if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_pin, cudaEventDisableTiming), "cudaEventCreate");
@@ -558,9 +571,12 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
         if (h->ev_near) cudaEventDestroy(h->ev_near);
         if (h->ev_join) cudaEventDestroy(h->ev_join);
         if (h->ev_pin) cudaEventDestroy(h->ev_pin);
+        if (h->ev_dsplit) cudaEventDestroy(h->ev_dsplit);
+        if (h->ev_dfree) cudaEventDestroy(h->ev_dfree);
         if (h->pin) cudaFreeHost(h->pin);
         if (h->aux) cudaStreamDestroy(h->aux);
         if (h->hi) cudaStreamDestroy(h->hi);
+        if (h->dem2) cudaStreamDestroy(h->dem2);
         delete h;
         return rc;
     }
@@ -706,9 +722,12 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
         for (int a = 0; a < 4; a++) split_pair(d.q[a], d.sq[a]);
         nc_total += d.ncp;
     }
-    // the FP32 DEM keeps its per-particle tables in shared memory
-    h->dem_f32 = h->cfg.storage != LBM_STORE_F64 && !h->cfg.dem_fp64 && n <= kDem32MaxParticles &&
-                 nc_total <= kDem32MaxCp;
+    // the FP32-geometry DEM kernels keep their per-particle tables in shared
+    // memory; beyond those limits, and on FP64 lattices, the FP64 k_dem runs
+    const bool fits = n <= kDem32MaxParticles && nc_total <= kDem32MaxCp;
+    if (h->cfg.storage == LBM_STORE_F64 || h->cfg.dem_mode == LBM_DEM_FP64_ALL || !fits) h->dem_mode = DEM_FP64_ALL;
+    else if (h->cfg.dem_mode == LBM_DEM_FP32_COMPENSATED) h->dem_mode = DEM_FP32;
+    else h->dem_mode = DEM_FP64_INTEGRATOR;
     int rc = LBM_OK;
     if (n > 0) {
         // through the page-locked buffer (once its previous upload is done),
@@ -876,7 +895,7 @@ int lbm_step(lbm_handle *h, int nsteps) {
             if (e != cudaSuccess) return cuda_check(h, e, "stream fork");
         }
         if (!P.force_fixed) { ProfScope s(h, 4, P.np > 0, hs); launch_force_reduce(P, hs); }
-        { ProfScope s(h, 5, P.np > 0 && P.n_sub > 0, hs); launch_dem(P, hs); }
+        { ProfScope s(h, 5, P.np > 0 && P.n_sub > 0, hs); launch_dem(P, hs, h->dem2, h->ev_dsplit, h->ev_dfree); }
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_check(h, e, "kernel launch");
         h->cur ^= 1;
@@ -921,7 +940,9 @@ static int status_code(lbm_handle *h, const int *st) {
     if (st[ST_ERR] & ERRB_DEM_CAPACITY)
         return fail(h, LBM_ERR_CAPACITY, "a particle had more than %d candidate contact partners; results are invalid",
                     kDemMaxAdj);
-    if (st[ST_ERR] & ERRB_TIMEOUT) return fail(h, LBM_ERR_TIMEOUT, "a device wait gave up");
+    if (st[ST_ERR] & ERRB_DEM_REACH)
+        return fail(h, LBM_ERR_CAPACITY, "a particle moved further in one step than |v| + |a| + %.2f lu, the bound the "
+                    "DEM's contact planning assumed; results are invalid", (double)0.25f);
     return LBM_OK;
 }
 
@@ -1136,12 +1157,15 @@ int lbm_destroy(lbm_handle *h) {
     cudaStreamSynchronize(h->stream);
     if (h->aux) cudaStreamSynchronize(h->aux);
     if (h->hi) cudaStreamSynchronize(h->hi);
+    if (h->dem2) cudaStreamSynchronize(h->dem2);
     release_profile(h);
-    for (cudaEvent_t e : {h->ev_fork, h->ev_bin, h->ev_plain, h->ev_near, h->ev_join, h->ev_pin})
+    for (cudaEvent_t e : {h->ev_fork, h->ev_bin, h->ev_plain, h->ev_near, h->ev_join, h->ev_pin, h->ev_dsplit,
+                          h->ev_dfree})
         if (e) cudaEventDestroy(e);
     if (h->pin) cudaFreeHost(h->pin);
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->hi) cudaStreamDestroy(h->hi);
+    if (h->dem2) cudaStreamDestroy(h->dem2);
     delete h;
     return LBM_OK;
 }

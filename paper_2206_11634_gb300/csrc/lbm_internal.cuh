@@ -33,7 +33,12 @@ constexpr int ROT_ITERS = 2;  // fixed-point sweeps of the implicit rotational h
 enum StatusSlot { ST_ERR = 0, ST_SLOTS = 16 };
 enum StepCounter { CNT_NREFILL = 0, CNT_NLINKS = 1, CNT_LISTED = 2, CNT_NEAR = 3 };
 enum ErrBits { ERRB_BRICK_OVERFLOW = 1, ERRB_DIVERGED = 2, ERRB_TIMEOUT = 4, ERRB_DEM_CAPACITY = 8,
-               ERRB_STATIC_CAPACITY = 16 };
+               ERRB_STATIC_CAPACITY = 16, ERRB_DEM_REACH = 32 };
+// DEM kernels (lbm_config.dem_mode): the FP64 rigid-body integrator with the
+// contact geometry in FP32 (k_dem64_plan + k_dem64_free + k_dem64c, lattices
+// below FP64), the compensated-FP32 integrator (k_dem32), and everything in
+// FP64 (k_dem, always on FP64 lattices).
+enum DemKernel { DEM_FP64_INTEGRATOR = 0, DEM_FP32 = 1, DEM_FP64_ALL = 2 };
 
 // A fluid node with particle links in a fixed geometry, and one of its links
 // (geometry of Eq. (27): q, lever arm from the centroid to x_w, u_w).
@@ -303,7 +308,7 @@ struct Params {
     int chain_grid;           // CTAs of the persistent k_flags / k_sweep_near (0: default)
     int plain_spec;           // few near bricks expected: the plain sweep pulls before its skip entry arrives
     int idx32;                // Q N < 2^31: population indices fit 32 bits
-    int dem_f32;              // DEM in FP32 with compensated state (k_dem32)
+    int dem_mode;             // enum DemKernel: which DEM kernels run
     int fc_valid;             // Fc/Tc hold the contact load of the current state (0 after set_particles)
     double tau, rho0, c0;
     double F[3], g[3], u0[3];
@@ -362,6 +367,7 @@ struct Params {
     float *wall_xi_f, *wall_xcw_f;  // [np*6][3], FP32 DEM: spring, warm start (relative to x_k)
     void *bin_next;    // batched lattices: the other parity's per-step region (cleared by the binning)
     long long bin_next_bytes;
+    int *dem_list;     // [2 + 2 np], k_dem64_plan: counts, inactive and active particles
     int *status;       // [ST_SLOTS], sticky error bits
     int *counters;     // per-step counters, zeroed with the brick lists
     // fixed-geometry sweep (every particle fixed, lattices below FP64): built
@@ -620,8 +626,11 @@ __device__ __forceinline__ void brick_coords(const Params &P, int b, int &bx, in
 // Launchers of the particle-side kernels (k_particles.cu).
 void launch_bin(const Params &P, cudaStream_t st);
 void launch_force_reduce(const Params &P, cudaStream_t st);
-void launch_dem(const Params &P, cudaStream_t st);
-void launch_dem32(const Params &P, cudaStream_t st);  // k_dem32.cu
+// st2 and the two events serve the FP64-integrator DEM (inactive particles on
+// st2, forked from st after the plan and joined back)
+void launch_dem(const Params &P, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_split, cudaEvent_t ev_free);
+void launch_dem32(const Params &P, cudaStream_t st);   // k_dem32.cu
+void launch_dem64c(const Params &P, cudaStream_t st);  // k_dem32.cu
 
 // ---------------------------------------------------------------------------
 // Batched lattices (lbm_batch_*): independent cases stepped together, one

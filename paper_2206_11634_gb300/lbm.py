@@ -20,6 +20,9 @@ HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "lbm_metaball.h")
 MAX_CP = 16
 MAX_PER_BRICK = 16
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+# lbm_config.dem_mode: FP64 rigid-body integrator (default), compensated FP32
+# integrator, FP64 contact geometry as well
+DEM_MODE = {"fp64": 0, "fp32": 1, "fp64_all": 2}
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_BAD_ARG", -2: "LBM_ERR_WS_TOO_SMALL", -3: "LBM_ERR_CAPACITY",
           -4: "LBM_ERR_DIVERGED", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_CUDA"}
 
@@ -31,7 +34,7 @@ class LbmConfig(C.Structure):
         ("periodic", C.c_int32 * 3),
         ("n_sub", C.c_int32), ("vibb", C.c_int32), ("missing_force", C.c_int32),
         ("max_particles", C.c_int32),
-        ("dem_fp64", C.c_int32), ("q_exact", C.c_int32),
+        ("dem_mode", C.c_int32), ("q_exact", C.c_int32),
         ("tau", C.c_double), ("rho0", C.c_double), ("c0", C.c_double),
         ("u0", C.c_double * 3), ("force", C.c_double * 3), ("gravity", C.c_double * 3),
         ("kn", C.c_double), ("eta_n", C.c_double),
@@ -130,7 +133,7 @@ def make_config(nx: int, ny: int, nz: int, *, lattice: int = 19, storage: str | 
                 max_particles: int = 1, tau: float = 0.8, rho0: float = 1.0, c0: float = 1.0,
                 u0=(0.0, 0.0, 0.0), force=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0),
                 kn: float = 0.0, eta_n: float = 0.0, kt: float = 0.0, eta_t: float = 0.0, mu_s: float = 0.0,
-                c_tol: float = 1e-6, mass_spacing: float = 0.5, dem_fp64: int = 0, q_exact: int = 0) -> LbmConfig:
+                c_tol: float = 1e-6, mass_spacing: float = 0.5, dem_mode: int = 0, q_exact: int = 0) -> LbmConfig:
     c = LbmConfig()
     c.nx, c.ny, c.nz = nx, ny, nz
     c.lattice = lattice
@@ -142,7 +145,7 @@ def make_config(nx: int, ny: int, nz: int, *, lattice: int = 19, storage: str | 
     c.tau, c.rho0, c.c0 = tau, rho0, c0
     c.kn, c.eta_n, c.kt, c.eta_t, c.mu_s, c.c_tol = kn, eta_n, kt, eta_t, mu_s, c_tol
     c.mass_spacing = mass_spacing
-    c.dem_fp64 = int(dem_fp64)
+    c.dem_mode = int(dem_mode)
     c.q_exact = int(q_exact)
     return c
 

@@ -3,8 +3,11 @@ metaball-wall contacts, their onset and release, tangential springs, and the
 closing half-kick, against the FP64 oracle over several LBM steps of 100
 sub-steps.
 
-Modes: FP64 lattice (FP64 DEM), FP32 lattice with the FP64 DEM (dem_fp64=1),
-FP32 lattice with the FP32 DEM (compensated state, FP32 contact geometry).
+Modes (lbm_config.dem_mode): FP64 lattice (everything FP64); FP32 lattice
+with the default FP64 rigid-body integrator and FP32 contact geometry (0),
+with the compensated-FP32 integrator (1), and with FP64 contact geometry as
+well (2).  The pile of 34 particles takes the 512-thread paths of the
+FP32-geometry kernels (more than 16 or 32 particles).
 
 Tolerances:
 - FP64: contact forces within 1e-8 of their scale, positions 1e-9,
@@ -61,23 +64,24 @@ def wl_trio(W, storage):
     return wl
 
 
-def wl_pile(W, oracle_mod, storage, target=0.03):
-    """A 3x3 layer of spheres on the floor (overlaps ~0.05 lu with the floor
-    and each other) and four two-control-point metaballs lowered onto it
-    until their largest overlap reaches `target` (placed with the oracle's
-    pair geometry)."""
+def wl_pile(W, oracle_mod, storage, target=0.03, side=3):
+    """A side x side layer of spheres on the floor (overlaps ~0.05 lu with
+    the floor and each other) and (side-1)^2 two-control-point metaballs
+    lowered onto it until their largest overlap reaches `target` (placed with
+    the oracle's pair geometry): 13 particles for side 3, 41 for side 5."""
     rng = np.random.default_rng(42)
     wl = W.empty_box(8, storage, (1, 1, 0))
-    wl.update(nx=40, ny=40, nz=32, tau=0.8, n_sub=100, gravity=(0.0, 0.0, -1e-3),
-              kn=200.0, eta_n=5.0, kt=100.0, eta_t=2.0, mu_s=0.3, c_tol=1e-6)
     r, pitch = 4.5, 9.83
+    n = int(np.ceil(12.0 + (side - 1) * pitch))
+    wl.update(nx=n, ny=n, nz=32, tau=0.8, n_sub=100, gravity=(0.0, 0.0, -1e-3),
+              kn=200.0, eta_n=5.0, kt=100.0, eta_t=2.0, mu_s=0.3, c_tol=1e-6)
     parts = []
-    for iy in range(3):
-        for ix in range(3):
+    for iy in range(side):
+        for ix in range(side):
             x = (6.0 + ix * pitch + 0.01 * iy, 6.0 + iy * pitch, r - 0.5 + 0.39)
             parts.append(W._particle([[0, 0, 0]], [r * r], x, density=1.3, Rs=0.5))
-    for iy in range(2):
-        for ix in range(2):
+    for iy in range(side - 1):
+        for ix in range(side - 1):
             ax = rng.normal(size=3)
             ax /= np.linalg.norm(ax)
             x = (6.0 + (ix + 0.5) * pitch, 6.0 + (iy + 0.5) * pitch, 12.0)
@@ -89,12 +93,13 @@ def wl_pile(W, oracle_mod, storage, target=0.03):
         p["inertia"] = np.diag([0.4 * m * r * r, 0.41 * m * r * r, 0.39 * m * r * r])
     wl["particles"] = parts
     orc = H.make_oracle(oracle_mod, wl)
-    for k in range(9, 13):
+    nb = side * side
+    for k in range(nb, len(parts)):
         z = parts[0]["x"][2] + 2 * r + 1.5
         while True:
             parts[k]["x"][2] = z
             orc.set_particles(H.oracle_particles(oracle_mod, wl))
-            hits = [orc.pair_geometry(i, k) for i in range(9)]
+            hits = [orc.pair_geometry(i, k) for i in range(nb)]
             dmax = max([h[1] for h in hits if h[0]] or [-1.0])
             if dmax >= target:
                 break
@@ -102,15 +107,18 @@ def wl_pile(W, oracle_mod, storage, target=0.03):
     return wl
 
 
-MODES = [("f64", 0), ("f32", 1), ("f32", 0)]
+MODES = [("f64", 0), ("f32", 0), ("f32", 1), ("f32", 2)]
 
 
-@pytest.mark.parametrize("storage,dem_fp64", MODES)
-@pytest.mark.parametrize("case", ["trio", "pile"])
-def test_contact_trajectory(pkg, oracle_mod, W, case, storage, dem_fp64):
-    wl = wl_trio(W, storage) if case == "trio" else wl_pile(W, oracle_mod, storage)
+@pytest.mark.parametrize("storage,dem_mode", MODES)
+@pytest.mark.parametrize("case", ["trio", "pile", "pile41"])
+def test_contact_trajectory(pkg, oracle_mod, W, case, storage, dem_mode):
+    if case == "trio":
+        wl = wl_trio(W, storage)
+    else:
+        wl = wl_pile(W, oracle_mod, storage, side=5 if case == "pile41" else 3)
     wl = H.with_margin(oracle_mod, wl)
-    gpu = H.make_gpu(pkg, wl, storage=storage, dem_fp64=dem_fp64)
+    gpu = H.make_gpu(pkg, wl, storage=storage, dem_mode=dem_mode)
     orc = H.make_oracle(oracle_mod, wl)
     gpu.set_particles(H.gpu_particles(pkg, wl))
     orc.set_particles(H.oracle_particles(oracle_mod, wl))
@@ -130,7 +138,7 @@ def test_contact_trajectory(pkg, oracle_mod, W, case, storage, dem_fp64):
         Hg, _ = gpu.forces()
         Ho, _ = orc.forces()
         assert np.abs(Hg - Ho).max() <= (1e-9 if f64 else 1e-3) * max(1.0, np.abs(Ho).max())
-    assert active >= (5 if case == "trio" else 20)
+    assert active >= {"trio": 5, "pile": 20, "pile41": 80}[case]
     for sg, so in zip(gpu.particles(), orc.get_particles()):
         assert np.abs(sg["x"] - so["x"]).max() < tolx, (sg["x"], so["x"])
         assert np.abs(sg["v"] - so["v"]).max() < tolv, (sg["v"], so["v"])
@@ -148,8 +156,8 @@ def test_contact_free_fall_has_no_contact_load(pkg, oracle_mod, W):
     wl["particles"] = wl["particles"][1:2]
     wl["particles"][0]["x"] = np.array([24.0, 20.0, 18.0])
     wl = H.with_margin(oracle_mod, wl)
-    for dem_fp64 in (0, 1):
-        gpu = H.make_gpu(pkg, wl, dem_fp64=dem_fp64)
+    for dem_mode in (0, 1, 2):
+        gpu = H.make_gpu(pkg, wl, dem_mode=dem_mode)
         gpu.set_particles(H.gpu_particles(pkg, wl))
         gpu.step(2)
         F, T = gpu.contact_forces()

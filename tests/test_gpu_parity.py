@@ -409,27 +409,30 @@ def test_settling_metaball_trajectory_fp32(pkg, oracle_mod, W):
     assert np.abs(sg["v"] - so["v"]).max() < 1e-5
 
 
-@pytest.mark.parametrize("storage,n_sub,w0", [("f64", 100, 0.02), ("f32", 100, 0.02), ("f32", 1, 0.4),
-                                                ("bf16", 100, 0.02)])
-def test_free_rotation(pkg, oracle_mod, W, storage, n_sub, w0):
+@pytest.mark.parametrize("storage,n_sub,w0,dem_mode", [("f64", 100, 0.02, 0), ("f32", 100, 0.02, 0),
+                                                         ("f32", 1, 0.4, 0), ("bf16", 100, 0.02, 0),
+                                                         ("f32", 100, 0.02, 1), ("f32", 1, 0.4, 1),
+                                                         ("bf16", 100, 0.02, 1)])
+def test_free_rotation(pkg, oracle_mod, W, storage, n_sub, w0, dem_mode):
     """Torque-free rotation of an asymmetric body (Euler's equations, §2.3.4):
     a metaball whose surface encloses the whole periodic box has no fluid
     links, so the hydrodynamic load is exactly zero and only the rotation
-    sub-steps act.  Lattices below FP64 integrate the rotation in
-    compensated FP32: each of the n_s increments (size ~|w| h / 2) carries a
-    relative error ~6e-8, so after S steps the attitude is off by at most
-    ~S n_s * 6e-8 * |w| h / 2 = 3e-8 S |w| (n_s h = 1), and w, whose
-    increments are of order |w|^2 h here, by that times |w|; the test allows
-    four times these (plus 3e-7 |w| for the FP32 rotation of the reported w
-    to the world frame).  FP64 agrees to rounding.  n_s = 1 with |w| = 0.4 takes
-    the large-angle branch of the exponential map."""
+    sub-steps act.  With the FP64 rigid-body integrator (dem_mode 0, any
+    storage) the attitude and w agree with the oracle to rounding (1e-12).
+    The compensated-FP32 integrator (dem_mode 1, below FP64) computes each of
+    the n_s increments (size ~|w| h / 2) with a relative error ~6e-8, so
+    after S steps the attitude is off by at most ~S n_s * 6e-8 * |w| h / 2 =
+    3e-8 S |w| (n_s h = 1), and w, whose increments are of order |w|^2 h
+    here, by that times |w|; the test allows four times these (plus 3e-7 |w|
+    for the FP32 rotation of the reported w to the world frame).  n_s = 1
+    with |w| = 0.4 takes the large-angle branch of the exponential map."""
     inertia = np.array([[40.0, 3.0, -2.0], [3.0, 25.0, 1.5], [-2.0, 1.5, 12.0]])
     wl = W.empty_box(16, storage, (1, 1, 1))
     wl.update(n_sub=n_sub, gravity=(0.0, 0.0, -1e-4))
     wl["particles"] = [W._particle([[0.0, 0.0, 0.0], [1.0, 0.5, 0.0]], [4e4, 1e4], (8.3, 7.9, 8.1),
                                    q=(0.9, 0.1, -0.3, 0.2), v=(0.01, 0.0, 0.0), w=(w0, -0.6 * w0, 0.3 * w0),
                                    density=2.0, mass=500.0, inertia=inertia)]
-    gpu = H.make_gpu(pkg, wl)
+    gpu = H.make_gpu(pkg, wl, dem_mode=dem_mode)
     orc = H.make_oracle(oracle_mod, wl)
     gpu.set_particles(H.gpu_particles(pkg, wl))
     orc.set_particles(H.oracle_particles(oracle_mod, wl))
@@ -442,18 +445,20 @@ def test_free_rotation(pkg, oracle_mod, W, storage, n_sub, w0):
     sg, so = gpu.particles()[0], orc.get_particles()[0]
     qg = sg["q"] * np.sign(np.dot(sg["q"], so["q"]))
     steps = 10
-    tol_q = 1e-12 if storage == "f64" else 4 * 3e-8 * steps * w0
-    # below FP64 the reported world-frame w is rotated out of the principal
-    # frame in FP32 (relative error ~1e-7)
-    tol_w = 1e-12 * w0 if storage == "f64" else tol_q * w0 + 3e-7 * w0
+    fp64 = storage == "f64" or dem_mode == 0
+    tol_q = 1e-12 if fp64 else 4 * 3e-8 * steps * w0
+    # the compensated integrator rotates the reported world-frame w out of
+    # the principal frame in FP32 (relative error ~1e-7)
+    tol_w = 1e-12 * w0 if fp64 else tol_q * w0 + 3e-7 * w0
     assert np.abs(qg - so["q"]).max() < tol_q
     assert np.abs(sg["w"] - so["w"]).max() < tol_w
-    # translation: below FP64 the acceleration (1 - rho0/rho_s) g enters in
-    # FP32 (relative 6e-8, the same every step), so v drifts by up to
-    # S |a| 6e-8 and x by S^2/2 of that per step; the test allows twice these
+    # translation: the compensated integrator takes the acceleration
+    # (1 - rho0/rho_s) g in FP32 (relative 6e-8, the same every step), so v
+    # drifts by up to S |a| 6e-8 and x by S^2/2 of that per step; the test
+    # allows twice these
     acc = 0.5 * 1e-4
-    tol_v = 1e-13 if storage == "f64" else 2 * steps * acc * 6e-8
-    tol_x = 1e-12 if storage == "f64" else 2 * 0.5 * steps * steps * acc * 6e-8
+    tol_v = 1e-13 if fp64 else 2 * steps * acc * 6e-8
+    tol_x = 1e-12 if fp64 else 2 * 0.5 * steps * steps * acc * 6e-8
     assert np.abs(sg["x"] - so["x"]).max() < tol_x
     assert np.abs(sg["v"] - so["v"]).max() < tol_v
     # the body really tumbles: w is not conserved in the world frame
