@@ -44,15 +44,21 @@ BYTES_PER_VALUE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}  # one stored popula
 # launch duration from a sample, at a sixteenth of the events' cost
 PLAIN_EVENT_EVERY = 16
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, the vendor's figure (the roofline's peak is the measured copy)
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_plain_settling_metaball_128x128x256.txt")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_plain_multi_particle_256x256x256.txt")
 BRICK_NODES = 32 * 4 * 2
 SWEEP_SOURCES = ["k_plain.cuh", "lbm_internal.cuh"]
 
 
-WORKLOADS = ("settling_metaball", "empty_box", "settling_sphere", "multi_particle", "batched_drag", "drag_gradient")
+WORKLOADS = ("multi_particle", "settling_metaball", "empty_box", "settling_sphere", "multi_particle_small",
+             "batched_drag", "drag_gradient")
+DEFAULT_WORKLOAD = "multi_particle"
+DEFAULT_NAME = "multi_particle_200p_256x256x256"
+# configurations reported beside a headline workload: (workload, storage, dem)
+SECONDARY = {"multi_particle": (("multi_particle", "f16", "fp64"), ("multi_particle", "f32", "fp32"),
+                                ("settling_metaball", "f32", "fp64"))}
 
 
-def workload(name: str = "settling_metaball", storage: str | None = None, dem: str | None = None):
+def workload(name: str = DEFAULT_WORKLOAD, storage: str | None = None, dem: str | None = None):
     """The benchmark's workload (default) or a diagnostic one; storage
     overrides the workload's population storage."""
     wl = _workload(name)
@@ -61,6 +67,8 @@ def workload(name: str = "settling_metaball", storage: str | None = None, dem: s
     if storage:
         wl["storage"] = storage
         wl["name"] = f"{wl['name']}_{storage}" if storage != "f32" else wl["name"]
+    if dem and dem != "fp64":
+        wl["name"] = f"{wl['name']}_dem_{dem}"
     return wl
 
 
@@ -76,6 +84,8 @@ def _workload(name: str):
         return workloads.settling_sphere()
     if name == "multi_particle":
         return workloads.multi_particle()
+    if name == "multi_particle_small":  # the same particle density in 128x128x256 (profiling captures)
+        return workloads.multi_particle(50, n=128, nz=256)
     if name == "batched_drag":  # the reference arm times its first case
         return workloads.batched_drag(64)[0]
     if name == "drag_gradient":  # the forward run of the gradient workload, as a lattice
@@ -113,13 +123,13 @@ def sweep_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(path: str = PROFILE_SUMMARY):
     """DRAM bytes per sweep launch from the committed ncu summary, when it was
     taken on the current sweep source; else None."""
-    if not os.path.exists(PROFILE_SUMMARY):
+    if not os.path.exists(path):
         return None
     vals = {}
-    for line in open(PROFILE_SUMMARY):
+    for line in open(path):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
@@ -276,9 +286,9 @@ def omp_threads() -> int:
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
 
 
-# the oracle takes ~80 ms per step of the 4.2 M-node workload on 16 cores:
-# the reference arm times at most this many of the requested steps
-REFERENCE_MAX_STEPS = 300
+# the reference arm times the oracle on at most this much of the requested
+# steps (the 256^3 workload takes about half a second per step on 16 cores)
+REFERENCE_MAX_SECONDS = 60.0
 REFERENCE_MAX_WARMUP = 2
 
 
@@ -289,10 +299,10 @@ def run_reference(args):
     wl = workload(args.workload)
     import oracle
     oracle.build()
-    steps = max(1, min(args.steps, REFERENCE_MAX_STEPS))
-    warm = max(0, min(args.warmup, REFERENCE_MAX_WARMUP))
-    if warm:
-        oracle_sample(wl, warm)
+    warm = max(1, min(args.warmup, REFERENCE_MAX_WARMUP))
+    _, t_warm = oracle_sample(wl, warm)
+    per_step = t_warm / warm
+    steps = max(1, min(args.steps, int(REFERENCE_MAX_SECONDS / max(per_step, 1e-6))))
     mlups, dt = oracle_sample(wl, steps)
     cores = omp_threads()
     line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": UNIT, "n_gpus": args.gpus,
@@ -308,6 +318,70 @@ def run_reference(args):
     return 0
 
 
+def timed_steps(lat, stream, dist, steps: int, min_seconds: float, max_repeats: int = 200):
+    """Time `steps` steps between barriers and device synchronisation, with
+    CUDA events on the lattice's stream, repeated until `min_seconds` have
+    elapsed (at least once); returns the per-repeat milliseconds."""
+    import torch
+    out = []
+    t0 = time.perf_counter()
+    while not out or (time.perf_counter() - t0 < min_seconds and len(out) < max_repeats):
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(dist)
+        torch.cuda.synchronize()
+        start.record(stream)
+        lat.step(steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        barrier(dist)
+        out.append(start.elapsed_time(stop))
+    return out
+
+
+def dem_label(wl):
+    storage, dem = wl["storage"], wl.get("dem", "fp64")
+    if storage == "f64" or dem == "fp64_all":
+        return "FP64 rigid-body integrator and contact geometry"
+    if dem == "fp32":
+        return "compensated-FP32 rigid-body integrator, FP32 contact geometry"
+    return "FP64 rigid-body integrator, FP32 contact geometry"
+
+
+def plain_roofline(lat, wl, plain_ms, plain_n, peak):
+    """Achieved HBM bandwidth of the plain sweep: the survey's algorithmic
+    bytes per lattice update (19 loads + 19 stores of the stored population
+    type, plus the 2-byte node flag) times the nodes one launch updates (every
+    node outside the near bricks), over its mean CUDA-event duration."""
+    nodes = wl["nx"] * wl["ny"] * wl["nz"]
+    near_bricks = lat.counters()["near_bricks"]
+    plain_nodes = max(0, nodes - near_bricks * BRICK_NODES)
+    per_lu = 2 * 19 * BYTES_PER_VALUE[wl["storage"]] + 2
+    alg = per_lu * plain_nodes
+    avg_s = plain_ms / max(1, plain_n) * 1e-3
+    achieved = alg / avg_s / 1e9 if avg_s > 0 else 0.0
+    return dict(achieved=achieved, frac=achieved / peak, bytes=alg, per_lu=per_lu, plain_nodes=plain_nodes,
+                avg_us=avg_s * 1e6)
+
+
+def measure_workload(pkg, wl, args, dist, local, min_seconds, stream=None):
+    """Warm-up, then the timed region (K steps, repeated to min_seconds, the
+    median kept), events around every PLAIN_EVENT_EVERY-th plain-sweep
+    launch of the timed steps (their mean is the roofline's duration)."""
+    import torch
+    stream = stream or torch.cuda.Stream()
+    lat = make_lattice(pkg, wl, stream)
+    lat.step(max(3, args.warmup))
+    torch.cuda.synchronize()
+    lat.profile(True, kernels=["k_sweep_plain"], every=PLAIN_EVENT_EVERY)
+    with ClockSampler(local) as clocks:
+        reps = timed_steps(lat, stream, dist, args.steps, min_seconds)
+    prof_timed = lat.profile_read()
+    lat.profile(False)
+    lat.check()
+    ms = max_over_ranks(dist, statistics.median(reps))
+    return lat, stream, reps, ms, prof_timed, clocks.summary()
+
+
 def run_gpu(args):
     import torch
 
@@ -320,53 +394,36 @@ def run_gpu(args):
     barrier(dist)
     wl = workload(args.workload, args.storage, args.dem)
     nodes = wl["nx"] * wl["ny"] * wl["nz"]
-    stream = torch.cuda.Stream()
-    lat = make_lattice(pkg, wl, stream)
+    peak, peak_kind = measured_peak_gbs()
 
-    # warm-up
-    lat.step(max(3, args.warmup))
-    torch.cuda.synchronize()
+    lat, stream, reps, ms, prof_timed, clocks = measure_workload(pkg, wl, args, dist, local, args.min_seconds)
     fl = lat.flags()
     n_fluid = int((fl == 0).sum().item())
-
-    # timed device region: events around the plain sweep only (its own
-    # stream); event records on the particle chain's stream would lengthen it
     kps = lat.kernels_per_step()
-    lat.profile(True, kernels=["k_sweep_plain"], every=PLAIN_EVENT_EVERY)
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clocks:
-        barrier(dist)
-        torch.cuda.synchronize()
-        start.record(stream)
-        lat.step(args.steps)
-        stop.record(stream)
-        torch.cuda.synchronize()
-        barrier(dist)
-    ms_local = start.elapsed_time(stop)
-    prof_timed = lat.profile_read()
-    lat.profile(False)
+    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+    ms_step = ms / args.steps
+    plain_ms, plain_n = prof_timed["k_sweep_plain"]
+    rf = plain_roofline(lat, wl, plain_ms, plain_n, peak)
     # the per-kernel breakdown from a separate pass with events around every
-    # kernel (slower per step than the timed region)
-    prof_steps = min(args.steps, 500)
+    # kernel (they lengthen the step)
+    prof_steps = min(args.steps, 200)
     lat.profile(True)
     lat.step(prof_steps)
     prof = lat.profile_read()
     lat.profile(False)
     lat.check()
-    ms = max_over_ranks(dist, ms_local)
-    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
 
     # end-to-end through the public API with host buffers: per step upload
     # the particle state, step, read back forces, torques and state
-    import numpy as np
     np_ = len(wl["particles"])
     state = (pkg.LbmParticle * max(1, np_))()
+    import numpy as np
     F = np.zeros((max(1, np_), 3))
     T = np.zeros((max(1, np_), 3))
     import ctypes as C
     L = lat.L
     L.lbm_get_forces(lat.h, None, None, state)
-    e2e_steps = max(1, args.steps // 4)
+    e2e_steps = max(4, args.steps // 4)
     barrier(dist)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -383,25 +440,32 @@ def run_gpu(args):
     e2e_value = world * nodes * e2e_steps / e2e_s / 1e6
     h2d = C.sizeof(pkg.LbmParticle) * np_
     d2h = 48 * np_ + C.sizeof(pkg.LbmParticle) * np_
+    del lat
+    torch.cuda.synchronize()
+
+    # further configurations, reported beside the headline (not the value)
+    secondary = []
+    if not args.no_secondary:
+        for name, storage, dem in SECONDARY.get(args.workload, ()):
+            w2 = workload(name, storage, dem)
+            n2 = w2["nx"] * w2["ny"] * w2["nz"]
+            lat2, _, reps2, ms2, pt2, ck2 = measure_workload(pkg, w2, args, dist, local, 0.5)
+            r2 = plain_roofline(lat2, w2, *pt2["k_sweep_plain"], peak)
+            secondary.append({"workload": w2["name"], "storage": w2["storage"], "dem": dem_label(w2),
+                              "value": round(world * n2 * args.steps / (ms2 * 1e-3) / 1e6, 2), "unit": UNIT,
+                              "ms_per_step": round(ms2 / args.steps, 4), "timed_repeats": len(reps2),
+                              "plain_sweep_frac": round(r2["frac"], 4), "plain_sweep_us": round(r2["avg_us"], 2),
+                              "clocks_sm_mhz": ck2.get("sm_mhz")})
+            del lat2
+            torch.cuda.synchronize()
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
-    # dominant kernel: the sweep of the plain bricks (every brick the near
-    # sweep does not take; all their nodes are fluid and no flag is read):
-    # 19 loads + 19 stores per node.  The near set of the last step stands
-    # for the average one (it changes by a few bricks from step to step).
-    plain_ms, plain_n = prof_timed["k_sweep_plain"]
-    near_bricks = lat.counters()["near_bricks"]
-    plain_nodes = max(0, nodes - near_bricks * BRICK_NODES)
-    alg_bytes = 2 * 19 * BYTES_PER_VALUE[wl["storage"]] * plain_nodes
-    sweep_avg_s = plain_ms / max(1, plain_n) * 1e-3
-    peak, peak_kind = measured_peak_gbs()
-    achieved = alg_bytes / sweep_avg_s / 1e9
-    # the committed capture is of the FP32 default workload's plain sweep
-    traffic = profiled_traffic() if (wl["name"], wl["storage"]) == ("settling_metaball_128x128x256", "f32") else None
+    # the committed capture is of the default workload's plain sweep
+    traffic = profiled_traffic() if (wl["name"], wl["storage"]) == (DEFAULT_NAME, "f32") else None
     kernels = {k: {"avg_us": round(v[0] / max(1, v[1]) * 1e3, 3), "launches": v[1],
                    "share": round(v[0] / max(1e-12, sum(x[0] for x in prof.values())), 4)}
                for k, v in prof.items() if v[1] > 0}
@@ -411,13 +475,12 @@ def run_gpu(args):
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        cpu_steps = args.cpu_steps
+        cpu_steps = args.cpu_steps or max(1, int(round(4e8 / nodes)))
         mlups, dt = oracle_sample(wl, cpu_steps)
         cpu = {"value": round(mlups, 4), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
                "sample": f"{cpu_steps} steps of the full {wl['nx']}x{wl['ny']}x{wl['nz']} workload, FP64, "
                          f"{dt:.1f} s"}
-        # one core as well, on a short window of the same workload
-        one_steps = max(1, cpu_steps // 40)
+        one_steps = max(1, cpu_steps // 20)
         mlups1, dt1 = oracle_sample(wl, one_steps, nthreads=1)
         cpu["one_core"] = {"value": round(mlups1, 4), "unit": UNIT, "cores": 1,
                            "sample": f"{one_steps} steps, {dt1:.1f} s"}
@@ -426,25 +489,33 @@ def run_gpu(args):
     l2_note = (f"no flush: populations 2x{pop_mb:.0f} MB exceed the 129 MB L2" if pop_mb > 129 else
                f"populations 2x{pop_mb:.0f} MB fit the 129 MB L2 (no flush; L2-resident)")
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+            "warmup": max(3, args.warmup), "ms_per_step": round(ms_step, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": wl["storage"], "data": "synthetic",
             "config": {"workload": wl["name"], "lattice": "D3Q19", "storage": wl["storage"], "tau": wl["tau"],
                        "n_sub": wl["n_sub"], "particles": len(wl["particles"]), "nodes": nodes,
-                       "fluid_nodes": n_fluid, "l2": l2_note,
+                       "fluid_nodes": n_fluid, "dem": dem_label(wl), "l2": l2_note,
+                       "timing": f"the {args.steps} steps timed {len(reps)} times (at least "
+                                 f"{args.min_seconds:g} s in all); median of "
+                                 f"{[round(r, 3) for r in sorted(reps)[:3]]}.. ms",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": f"{peak_kind} copy",
-                         "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4), "nominal_peak": NOMINAL_HBM_GBS,
-                         "kernel": "k_sweep_plain", "bytes_per_launch": alg_bytes, "plain_nodes": plain_nodes,
-                         "avg_launch_us": round(sweep_avg_s * 1e6, 3),
-                         "timed_launches_sampled": f"{plain_n} (every {PLAIN_EVENT_EVERY}th of the timed steps)"},
+            "roofline": {"bound": "hbm", "achieved": round(rf["achieved"], 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(rf["frac"], 4), "traffic": traffic, "peak_kind": f"{peak_kind} copy",
+                         "frac_of_nominal": round(rf["achieved"] / NOMINAL_HBM_GBS, 4),
+                         "nominal_peak": NOMINAL_HBM_GBS, "kernel": "k_sweep_plain",
+                         "bytes_per_launch": rf["bytes"],
+                         "bytes_per_lattice_update": rf["per_lu"], "plain_nodes": rf["plain_nodes"],
+                         "avg_launch_us": round(rf["avg_us"], 3),
+                         "avg_launch_le_step": rf["avg_us"] <= ms_step * 1e3,
+                         "timed_launches_sampled": f"{plain_n} (every {PLAIN_EVENT_EVERY}th plain-sweep launch of "
+                                                   f"all {len(reps) * args.steps} timed steps)"},
             "kernels": kernels,
             "kernels_note": f"per-kernel events around every launch, separate pass of {prof_steps} steps",
             "gpu_launches": kps * args.steps,
-            "clocks": clocks.summary(),
+            "clocks": clocks,
             "cpu_baseline": cpu,
+            "secondary": secondary,
             "drag": drag_check(pkg, wl["storage"])}
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -520,7 +591,7 @@ def run_batch(args):
         oracle.build()
         c0 = dict(cases[0])
         c0["n_sub"] = 0
-        cpu_steps = max(1, args.cpu_steps // 2)
+        cpu_steps = max(1, (args.cpu_steps or 200) // 2)
         mlups, dt = oracle_sample(c0, cpu_steps)
         cpu = {"value": round(mlups, 4), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
                "sample": f"{cpu_steps} steps of case 0 ({c0['nx']}x{c0['ny']}x{c0['nz']}), FP64, {dt:.1f} s; "
@@ -631,7 +702,7 @@ def run_gradient(args):
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        cpu_steps = max(1, args.cpu_steps // 2)
+        cpu_steps = max(1, (args.cpu_steps or 200) // 2)
         mlups, dt = oracle_sample(gradient_lattice(case), cpu_steps)
         cpu = {"value": round(mlups, 4), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
                "sample": f"{cpu_steps} forward steps of the {case['nx']}^3 case, FP64, {dt:.1f} s (the oracle has "
@@ -667,17 +738,21 @@ def run_gradient(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--min-seconds", type=float, default=1.0,
+                    help="repeat the timed steps until this much time has passed (median reported)")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the configurations reported beside the headline")
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--cpu-steps", type=int, default=200)
+    ap.add_argument("--cpu-steps", type=int, default=None,
+                    help="oracle steps of the CPU baseline (default: about 4e8 lattice updates)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16", "f64"], default=None,
                     help="population storage (default: the workload's own)")
     ap.add_argument("--dem", choices=["fp64", "fp32", "fp64_all"], default=None,
                     help="DEM arithmetic: fp64 (default) the FP64 rigid-body integrator, FP32 contact geometry "
                          "below FP64 storage; fp32 the compensated-FP32 integrator; fp64_all FP64 contact geometry too")
-    ap.add_argument("--workload", choices=WORKLOADS, default="settling_metaball",
+    ap.add_argument("--workload", choices=WORKLOADS, default=DEFAULT_WORKLOAD,
                     help="diagnostic workloads besides the default benchmark workload")
     args = ap.parse_args()
     if args.impl == "reference":

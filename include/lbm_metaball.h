@@ -98,20 +98,24 @@ typedef struct lbm_config {
     int32_t missing_force;     /* 1 = add the missing-force-point terms of §2.3.5 item 2 */
     int32_t max_particles;     /* capacity reserved in the workspace, >= 1 */
     int32_t dem_mode;          /* arithmetic of the DEM (§2.1, §2.3.4), enum lbm_dem_mode.
-                                  0 (LBM_DEM_FP64, the default): the rigid-body integrator (velocity
-                                  Verlet, Euler's equations, the quaternion update) runs in FP64.  On
-                                  FP64 lattices the contact geometry and law are FP64 too; on
-                                  FP32/FP16/BF16 lattices they are evaluated in FP32 (overlap error
-                                  ~1e-6 lu) and summed into the FP64 kicks, for up to 256 particles
-                                  with up to 2048 control points in all (else as mode 2).
+                                  0 (LBM_DEM_FP64, the default): the rigid-body state is FP64 and
+                                  every sub-step adds to it in FP64.  On FP64 lattices everything
+                                  is FP64.  On FP32/FP16/BF16 lattices a particle that cannot touch
+                                  a wall or another particle during the step (|v| + |a| + 0.25 lu
+                                  of reach) moves in FP64 arithmetic throughout (translation in
+                                  closed form, rotation sub-stepped); the others compute their
+                                  increments, contact geometry and contact law in FP32 (overlap
+                                  error ~1e-6 lu) and add the increments to the FP64 state; up to
+                                  256 particles with up to 2048 control points in all (else as
+                                  mode 2).
                                   1 (LBM_DEM_FP32_COMPENSATED): lattices below FP64 only (FP64
-                                  lattices ignore it): the integrator computes every increment in
-                                  FP32 and keeps the state as compensated FP32 pairs (about 48
-                                  significant bits), with the same limits; faster, below the FP64
-                                  integrator's accuracy.
-                                  2 (LBM_DEM_FP64_ALL): contact geometry and law in FP64 as well, on
-                                  any lattice (one CTA; slow for many contacts on this GPU, whose FP64
-                                  rate is a small fraction of its FP32 rate). */
+                                  lattices ignore it): every particle computes in FP32 and keeps
+                                  its state as compensated FP32 pairs (about 48 significant bits),
+                                  with the same limits; the fastest, below mode 0's accuracy for
+                                  particles without contact.
+                                  2 (LBM_DEM_FP64_ALL): everything in FP64, contact geometry
+                                  included, on any lattice (one CTA; slow for many contacts on
+                                  this GPU, whose FP64 rate is a small fraction of its FP32 rate). */
     int32_t q_exact;           /* 0 = link fraction q by Eq. (27); 1 = the root of Eq. (26) by Newton's
                                   method from Eq. (27)'s value (§2.3.1: tolerance 1e-7, at most 100
                                   iterations; a step leaving the bracket [0,1] bisects), in the
@@ -283,8 +287,9 @@ int lbm_set_stream(lbm_handle *h, void *cuda_stream);
  * every device that loads the library until the process exits.  Limits: at
  * most 65536 bricks of 32x4x2 nodes (256^3 nodes) and 256 particles; larger
  * inputs return LBM_ERR_CAPACITY before any GPU work, as does a brick met by
- * more than 16 particles.  Invalid arguments return LBM_ERR_BAD_ARG, CUDA
- * failures LBM_ERR_CUDA.  The call runs on cuda_stream and synchronises it
+ * more than 16 particles (seen on the device, reported after the kernels
+ * ran).  Invalid arguments return LBM_ERR_BAD_ARG, CUDA failures, and any
+ * other device error bit, LBM_ERR_CUDA.  The call runs on cuda_stream and synchronises it
  * before returning.  The first call on a device looks up the array's device
  * address (make it before any stream capture).  Every call on a device
  * shares the array and clears what must start at zero; calls that overlap on

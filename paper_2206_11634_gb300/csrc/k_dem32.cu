@@ -817,18 +817,34 @@ __global__ void __launch_bounds__(kThreads) k_dem32(Params P) {
 // ---------------------------------------------------------------------------
 // k_dem64c: the active particles of k_dem64_plan (those that can meet a wall
 // or another particle during the step), one thread each, one CTA.  The
-// rigid-body integrator is FP64: state, increments and the Verlet /
-// Euler / quaternion arithmetic are those of k_dem (velocity Verlet in
-// kick-drift-kick form, Euler's equations in the principal frame, q <- q (x)
-// exp(h w/2), the closing rotational half-kick implicit by ROT_ITERS
-// sweeps).  The contact geometry (Eqs. (5)-(13)) and the contact law
-// (Eqs. (2)-(3)) are evaluated in FP32 from FP32 copies as in k_dem32 (the
-// positions as hi + lo pairs of the FP64 values), and their per-particle
-// sums enter the FP64 kicks.  The angular velocity is carried in the
-// principal frame across the sub-steps (k_dem rotates it to the world frame
-// and back around each one, a rounding difference only).  The quaternion is
-// renormalised once, at the end of the step.
+// rigid-body state (x, v, q and the principal-frame angular velocity) is
+// FP64 and persists in FP64 from step to step; within the step each
+// component carries its change since the step began as a compensated FP32
+// pair (about 48 significant bits of a change of order |v| ~ 0.1 lu: ~1e-15
+// absolute), and the change is added to the FP64 value at the end of the
+// step.  The sub-step increments, the contact geometry (Eqs. (5)-(13)) and
+// the contact law (Eqs. (2)-(3)) are computed in FP32, as in k_dem32, from
+// FP32 working copies (positions for the geometry as hi + lo pairs of the
+// FP64 value plus the change).  No FP64 or FP64<->FP32 conversion runs in
+// the sub-step loop: on this GPU both occupy a sub-partition for 64 cycles
+// or more per warp instruction.  The sub-step sequence is k_dem's: velocity
+// Verlet in kick-drift-kick form, Euler's equations in the principal frame,
+// q <- q (x) exp(h w/2), the closing rotational half-kick implicit by
+// ROT_ITERS sweeps.  The quaternion is renormalised once, at the end of the
+// step.
 // ---------------------------------------------------------------------------
+// One state component within the step: the FP32 rounding of its value at
+// the start (the FP64 value stays in the particle record until the end) and
+// the change since then.
+struct Delta {
+    float bf;
+    DF d;
+    __device__ __forceinline__ float f() const { return bf + d.hi; }  // FP32 working value
+    __device__ __forceinline__ double fin(double base) const { return base + ((double)d.hi + (double)d.lo); }
+};
+__device__ __forceinline__ void dl_set(Delta &a, double v) { a.bf = (float)v; a.d = {0.f, 0.f}; }
+__device__ __forceinline__ void dl_add(Delta &a, float b) { a.d = df_add(a.d, b); }
+
 __global__ void __launch_bounds__(kThreads) k_dem64c(Params P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shared &S = *reinterpret_cast<Shared *>(smem_raw);
@@ -836,28 +852,32 @@ __global__ void __launch_bounds__(kThreads) k_dem64c(Params P) {
     const int na = P.dem_list[1];
     if (na == 0) return;
     const int *act = P.dem_list + 2 + P.np;
-    const double h = 1.0 / P.n_sub, hh = 0.5 * h;
-    const float hf = P.h_f;
+    const float h = P.h_f, hh = 0.5f * h, qh2 = 0.25f * h * h;
     const bool own = tid < na;
     const int g = own ? act[tid] : 0;
     DevParticle *pp = own ? &P.parts[g] : nullptr;
 
-    double x[3] = {0, 0, 0}, x0[3] = {0, 0, 0}, v[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, wb[3] = {0, 0, 0};
-    double Fh[3] = {0, 0, 0}, Th[3] = {0, 0, 0}, bg[3] = {0, 0, 0}, inv_m = 0.0;
+    Delta x[3], v[3], q[4], wb[3];
+    float xlo[3] = {0.f, 0.f, 0.f};  // FP32 rounding error of the start position
+    float Fh[3] = {0.f, 0.f, 0.f}, Th[3] = {0.f, 0.f, 0.f}, iI[3], cI[3], bg[3], inv_m = 0.f;
     bool mov = false;
     float reach = 0.f;
     if (own) {
+        double wbd[3];
+        rot_body(pp->q, pp->w, wbd);
         for (int a = 0; a < 3; a++) {
-            x[a] = pp->x[a];
-            x0[a] = x[a];
-            v[a] = pp->v[a];
-            Fh[a] = P.Fh[3 * g + a];
-            Th[a] = P.Th[3 * g + a];
-            bg[a] = pp->buoy * P.g[a];
+            dl_set(x[a], pp->x[a]);
+            xlo[a] = (float)(pp->x[a] - (double)x[a].bf);
+            dl_set(v[a], pp->v[a]);
+            dl_set(wb[a], wbd[a]);
+            Fh[a] = (float)P.Fh[3 * g + a];
+            Th[a] = (float)P.Th[3 * g + a];
+            iI[a] = pp->iI_f[a];
+            cI[a] = pp->cI_f[a];
+            bg[a] = pp->bg_f[a];
         }
-        for (int a = 0; a < 4; a++) q[a] = pp->q[a];
-        rot_body(q, pp->w, wb);
-        inv_m = pp->inv_mass;
+        for (int a = 0; a < 4; a++) dl_set(q[a], pp->q[a]);
+        inv_m = pp->inv_mass_f;
         mov = !pp->fixed;
         reach = dem_reach(P, *pp, g);
     }
@@ -872,24 +892,21 @@ __global__ void __launch_bounds__(kThreads) k_dem64c(Params P) {
     __syncthreads();
     if (S.cpo[na] > kDem32MaxCp) return;
 
-    // FP32 tables of the start state
-    auto publish = [&](const double wbody[3]) {
-        float qf[4], wf[3], ww[3];
-        for (int a = 0; a < 4; a++) qf[a] = (float)q[a];
-        for (int a = 0; a < 3; a++) wf[a] = (float)wbody[a];
+    // FP32 tables: position (hi + lo of the FP64 value), velocity, world
+    // angular velocity from the body rate wf
+    auto publish = [&](const float wf[3], const float qf[4]) {
+        float ww[3];
         qrot_f(qf, wf, ww, true);
         for (int a = 0; a < 3; a++) {
-            const float hi = (float)x[a];
-            S.xh[tid][a] = hi;
-            S.xl[tid][a] = (float)(x[a] - (double)hi);
-            S.v[tid][a] = (float)v[a];
+            S.xh[tid][a] = x[a].bf;
+            S.xl[tid][a] = xlo[a] + (x[a].d.hi + x[a].d.lo);
+            S.v[tid][a] = v[a].f();
             S.w[tid][a] = ww[a];
         }
     };
     if (own) {
-        publish(wb);
-        float qf[4];
-        for (int a = 0; a < 4; a++) qf[a] = (float)q[a];
+        const float qf[4] = {q[0].f(), q[1].f(), q[2].f(), q[3].f()}, wf[3] = {wb[0].f(), wb[1].f(), wb[2].f()};
+        publish(wf, qf);
         S.reach[tid] = reach;
         S.brad[tid] = pp->brad_f;
         S.Rs[tid] = pp->Rs_f;
@@ -929,35 +946,43 @@ __global__ void __launch_bounds__(kThreads) k_dem64c(Params P) {
     }
     __syncthreads();
     for (int sub = 0; sub < P.n_sub; sub++) {
-        double wh[3] = {wb[0], wb[1], wb[2]};
+        Delta wh[3] = {wb[0], wb[1], wb[2]};
         int moved = 0;
         if (own) {
+            float qf[4] = {q[0].f(), q[1].f(), q[2].f(), q[3].f()};
             if (mov) {
                 // first half-kick and drift
                 for (int a = 0; a < 3; a++) {
-                    const double acc = bg[a] + (Fh[a] + (double)S.Fc[tid][a]) * inv_m;
-                    v[a] += hh * acc;
-                    x[a] += h * v[a];
+                    dl_add(v[a], hh * (bg[a] + (Fh[a] + S.Fc[tid][a]) * inv_m));
+                    dl_add(x[a], h * v[a].f());
                 }
-                // rotation: half-kick, then q <- q (x) exp(h w_half / 2)
-                double Tw[3], Tb[3], dw[3];
-                for (int a = 0; a < 3; a++) Tw[a] = Th[a] + (double)S.Tc[tid][a];
-                rot_body(q, Tw, Tb);
-                euler_rate(*pp, wb, Tb, dw);
-                for (int a = 0; a < 3; a++) wh[a] = wb[a] + hh * dw[a];
-                quat_step(q, wh, h);
+                // rotation: half-kick, q <- q (x) exp(h wh / 2)
+                float Tw[3], Tb[3], wf[3] = {wb[0].f(), wb[1].f(), wb[2].f()}, dw[3], whf[3];
+                for (int a = 0; a < 3; a++) Tw[a] = Th[a] + S.Tc[tid][a];
+                qrot_f(qf, Tw, Tb, false);
+                euler_f(iI, cI, wf, Tb, dw);
+                for (int a = 0; a < 3; a++) {
+                    dl_add(wh[a], hh * dw[a]);
+                    whf[a] = wh[a].f();
+                }
+                float cm1, sc;
+                exp_half(hh, qh2, whf, cm1, sc);
+                const float d1 = sc * whf[0], d2 = sc * whf[1], d3 = sc * whf[2];
+                const float q0 = qf[0], q1 = qf[1], q2 = qf[2], q3 = qf[3];
+                dl_add(q[0], q0 * cm1 - (q1 * d1 + q2 * d2 + q3 * d3));
+                dl_add(q[1], q0 * d1 + q1 * cm1 + (q2 * d3 - q3 * d2));
+                dl_add(q[2], q0 * d2 + q2 * cm1 + (q3 * d1 - q1 * d3));
+                dl_add(q[3], q0 * d3 + q3 * cm1 + (q1 * d2 - q2 * d1));
+                for (int a = 0; a < 4; a++) qf[a] = q[a].f();
             }
-            publish(wh);
+            const float whf[3] = {wh[0].f(), wh[1].f(), wh[2].f()};
+            publish(whf, qf);
             float dr2 = 0.f;
             for (int a = 0; a < 3; a++) {
                 const float dd = (S.xh[tid][a] - S.xref[tid][a]) + S.xl[tid][a];
                 dr2 += dd * dd;
             }
-            if (mov) {
-                float qf[4];
-                for (int a = 0; a < 4; a++) qf[a] = (float)q[a];
-                put_rc(P, S, tid, qf);
-            }
+            if (mov) put_rc(P, S, tid, qf);
             moved = dr2 > 0.25f * kSkin * kSkin;
         }
         moved = __syncthreads_or(moved);
@@ -966,37 +991,52 @@ __global__ void __launch_bounds__(kThreads) k_dem64c(Params P) {
             __syncthreads();
             build_lists(P, S, &dummy);
         }
-        pair_contacts(P, S, hf);
+        pair_contacts(P, S, h);
         __syncthreads();
         if (own) {
             float F[3], T[3];
-            gather_contacts(P, S, tid, hf, F, T);
+            gather_contacts(P, S, tid, h, F, T);
             for (int a = 0; a < 3; a++) { S.Fc[tid][a] = F[a]; S.Tc[tid][a] = T[a]; }
             if (mov) {
                 // closing half-kick with the new contact load
-                for (int a = 0; a < 3; a++) v[a] += hh * (bg[a] + (Fh[a] + (double)F[a]) * inv_m);
-                double Tw[3], Tb[3], dw[3], w1[3] = {wh[0], wh[1], wh[2]};
-                for (int a = 0; a < 3; a++) Tw[a] = Th[a] + (double)T[a];
-                rot_body(q, Tw, Tb);
-                for (int it = 0; it < ROT_ITERS; it++) {
-                    euler_rate(*pp, w1, Tb, dw);
-                    for (int a = 0; a < 3; a++) w1[a] = wh[a] + hh * dw[a];
+                for (int a = 0; a < 3; a++) dl_add(v[a], hh * (bg[a] + (Fh[a] + F[a]) * inv_m));
+                const float qf[4] = {q[0].f(), q[1].f(), q[2].f(), q[3].f()};
+                float Tw[3], Tb[3], dw[3], whf[3] = {wh[0].f(), wh[1].f(), wh[2].f()}, w1[3];
+                for (int a = 0; a < 3; a++) { Tw[a] = Th[a] + T[a]; w1[a] = whf[a]; }
+                qrot_f(qf, Tw, Tb, false);
+                for (int it = 0; it + 1 < ROT_ITERS; it++) {
+                    euler_f(iI, cI, w1, Tb, dw);
+                    for (int a = 0; a < 3; a++) w1[a] = whf[a] + hh * dw[a];
                 }
-                for (int a = 0; a < 3; a++) wb[a] = w1[a];
+                euler_f(iI, cI, w1, Tb, dw);
+                for (int a = 0; a < 3; a++) {
+                    wb[a] = wh[a];
+                    dl_add(wb[a], hh * dw[a]);
+                }
             }
         }
         __syncthreads();
     }
-    if (own && mov) quat_normalize(q);
+    // the step's changes added to the FP64 state (still in the record)
+    double qd[4] = {1, 0, 0, 0}, wbd[3] = {0, 0, 0}, xd[3] = {0, 0, 0}, vd[3] = {0, 0, 0};
+    if (own && mov) {
+        double wb0[3];
+        rot_body(pp->q, pp->w, wb0);
+        for (int a = 0; a < 4; a++) qd[a] = q[a].fin(pp->q[a]);
+        for (int a = 0; a < 3; a++) {
+            wbd[a] = wb[a].fin(wb0[a]);
+            xd[a] = x[a].fin(pp->x[a]);
+            vd[a] = v[a].fin(pp->v[a]);
+        }
+        quat_normalize(qd);
+        for (int a = 0; a < 4; a++) dl_set(q[a], qd[a]);
+    }
     // contact load of the end state (springs not advanced): reported by
     // lbm_get_contact_forces and the start load of the next step
     if (own) {
-        publish(wb);
-        if (mov) {
-            float qf[4];
-            for (int a = 0; a < 4; a++) qf[a] = (float)q[a];
-            put_rc(P, S, tid, qf);
-        }
+        const float qf[4] = {q[0].f(), q[1].f(), q[2].f(), q[3].f()}, wf[3] = {wb[0].f(), wb[1].f(), wb[2].f()};
+        publish(wf, qf);
+        if (mov) put_rc(P, S, tid, qf);
     }
     __syncthreads();
     pair_contacts(P, S, 0.f);
@@ -1018,19 +1058,19 @@ __global__ void __launch_bounds__(kThreads) k_dem64c(Params P) {
         }
         if (mov) {
             double ww[3];
-            rot_world(q, wb, ww);
+            rot_world(qd, wbd, ww);
             for (int a = 0; a < 3; a++) {
-                pp->x[a] = x[a];
-                pp->v[a] = v[a];
+                pp->x[a] = xd[a];
+                pp->v[a] = vd[a];
                 pp->w[a] = ww[a];
             }
-            for (int a = 0; a < 4; a++) pp->q[a] = q[a];
+            for (int a = 0; a < 4; a++) pp->q[a] = qd[a];
         }
         // the planning assumed no larger displacement (contacts with
         // inactive particles would have been missed otherwise)
-        double d2 = 0.0;
-        for (int a = 0; a < 3; a++) d2 += (x[a] - x0[a]) * (x[a] - x0[a]);
-        if (d2 > (double)reach * (double)reach) atomicOr(&P.status[ST_ERR], ERRB_DEM_REACH);
+        float d2 = 0.f;
+        for (int a = 0; a < 3; a++) d2 += x[a].d.hi * x[a].d.hi;
+        if (d2 > reach * reach) atomicOr(&P.status[ST_ERR], ERRB_DEM_REACH);
     }
     if (na > 1) store_items(P, S);
 }

@@ -7,17 +7,30 @@
 
 namespace lbmmb {
 
-constexpr int kSmCount = 152;  // GB300
-constexpr int kGridStrideBlocks = kSmCount * 8;
+// SMs of the current device, queried once per device (152 on GB300; the
+// value is only a grid-size choice, so a failed query falls back to it).
+inline int sm_count() {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+// grid of the grid-stride kernels: eight CTAs per SM
+inline int grid_stride_blocks() { return sm_count() * 8; }
 
 template <typename S>
 void launch_init_t(const Params &P, void *f, cudaStream_t st) {
-    if (P.Q == 19) k_init<S, 19><<<kGridStrideBlocks, 256, 0, st>>>(P, (S *)f);
-    else k_init<S, 15><<<kGridStrideBlocks, 256, 0, st>>>(P, (S *)f);
+    if (P.Q == 19) k_init<S, 19><<<grid_stride_blocks(), 256, 0, st>>>(P, (S *)f);
+    else k_init<S, 15><<<grid_stride_blocks(), 256, 0, st>>>(P, (S *)f);
 }
 template <typename S>
 void launch_flags_t(const Params &P, cudaStream_t st) {
-    const int cap = P.chain_grid > 0 ? P.chain_grid : kGridStrideBlocks / 2;
+    const int cap = P.chain_grid > 0 ? P.chain_grid : grid_stride_blocks() / 2;
     const int grid = P.nbricks < cap ? P.nbricks : cap;
     if (P.Q == 19) k_flags<S, 19><<<grid, BRICK, 0, st>>>(P);
     else k_flags<S, 15><<<grid, BRICK, 0, st>>>(P);
@@ -37,7 +50,7 @@ void launch_sweep_plain_t(const Params &P, cudaStream_t st) {
 template <typename S>
 void launch_sweep_near_t(const Params &P, cudaStream_t st) {
     const bool force = P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0;
-    const int cap = P.chain_grid > 0 ? P.chain_grid : kNearCtasPerSm * kSmCount;
+    const int cap = P.chain_grid > 0 ? P.chain_grid : kNearCtasPerSm * sm_count();
     const int grid = P.nbricks < cap ? P.nbricks : cap;
     if (P.Q == 19) {
         if (force) k_sweep_near<S, 19, true><<<grid, BRICK, 0, st>>>(P);
@@ -50,23 +63,23 @@ void launch_sweep_near_t(const Params &P, cudaStream_t st) {
 template <typename S>
 void launch_fields_t(const Params &P, const void *f, const uint16_t *flags, double *rho, double *u, uint16_t *fl,
                      cudaStream_t st) {
-    if (P.Q == 19) k_fields<S, 19><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, flags, rho, u, fl);
-    else k_fields<S, 15><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, flags, rho, u, fl);
+    if (P.Q == 19) k_fields<S, 19><<<grid_stride_blocks(), 256, 0, st>>>(P, (const S *)f, flags, rho, u, fl);
+    else k_fields<S, 15><<<grid_stride_blocks(), 256, 0, st>>>(P, (const S *)f, flags, rho, u, fl);
 }
 template <typename S>
 void launch_get_pop_t(const Params &P, const void *f, double *out, cudaStream_t st) {
-    if (P.Q == 19) k_get_pop<S, 19><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, out);
-    else k_get_pop<S, 15><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, out);
+    if (P.Q == 19) k_get_pop<S, 19><<<grid_stride_blocks(), 256, 0, st>>>(P, (const S *)f, out);
+    else k_get_pop<S, 15><<<grid_stride_blocks(), 256, 0, st>>>(P, (const S *)f, out);
 }
 template <typename S>
 void launch_set_pop_t(const Params &P, void *f, const double *in, cudaStream_t st) {
-    if (P.Q == 19) k_set_pop<S, 19><<<kGridStrideBlocks, 256, 0, st>>>(P, (S *)f, in);
-    else k_set_pop<S, 15><<<kGridStrideBlocks, 256, 0, st>>>(P, (S *)f, in);
+    if (P.Q == 19) k_set_pop<S, 19><<<grid_stride_blocks(), 256, 0, st>>>(P, (S *)f, in);
+    else k_set_pop<S, 15><<<grid_stride_blocks(), 256, 0, st>>>(P, (S *)f, in);
 }
 template <typename S>
 void launch_check_t(const Params &P, const void *f, const uint16_t *flags, cudaStream_t st) {
-    if (P.Q == 19) k_check<S, 19><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, flags);
-    else k_check<S, 15><<<kGridStrideBlocks, 256, 0, st>>>(P, (const S *)f, flags);
+    if (P.Q == 19) k_check<S, 19><<<grid_stride_blocks(), 256, 0, st>>>(P, (const S *)f, flags);
+    else k_check<S, 15><<<grid_stride_blocks(), 256, 0, st>>>(P, (const S *)f, flags);
 }
 
 template <typename S>
@@ -99,7 +112,7 @@ void launch_plain_batch_t(const BatchArgs &B, int Q, bool force, int grid, cudaS
 
 template <typename S>
 void launch_static_build_t(const Params &P, cudaStream_t st) {
-    const int cap = kGridStrideBlocks / 2;
+    const int cap = grid_stride_blocks() / 2;
     const int grid = P.nbricks < cap ? P.nbricks : cap;
     if (P.Q == 19) k_static_build<S, 19><<<grid, BRICK, 0, st>>>(P);
     else k_static_build<S, 15><<<grid, BRICK, 0, st>>>(P);
@@ -120,7 +133,7 @@ template <typename S>
 void launch_static_links_t(const Params &P, cudaStream_t st) {
     const bool force = P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0;
     const int warps = (P.snodes_n + kStaticNodesPerWarp - 1) / kStaticNodesPerWarp;
-    const int cap = kNearCtasPerSm * kSmCount;
+    const int cap = kNearCtasPerSm * sm_count();
     int grid = (warps + BRICK / 32 - 1) / (BRICK / 32);
     grid = grid < 1 ? 1 : (grid > cap ? cap : grid);
     if (P.Q == 19) {

@@ -920,7 +920,8 @@ int lbm_kernels_per_step(const lbm_handle *h) {
     // DEM (particles, n_sub > 0)
     // once the fixed-geometry sweep runs: its link and plain kernels
     const bool geom_static = h->all_fixed && h->static_steps >= kStaticFlagSteps;
-    const int dem = h->np > 0 && h->cfg.n_sub > 0 ? 1 : 0;
+    // the FP64-integrator DEM is three kernels (split, inactive, active)
+    const int dem = h->np > 0 && h->cfg.n_sub > 0 ? (h->dem_mode == DEM_FP64_INTEGRATOR ? 3 : 1) : 0;
     if (geom_static && h->static_state == 1) return 2 + dem;
     const int flags = geom_static ? 0 : 1;
     if (h->np == 0) return 3 + flags;
@@ -976,6 +977,9 @@ int lbm_get_forces(lbm_handle *h, double *F, double *T, lbm_particle *state_out)
         rc = cuda_check(h, cudaMemcpyAsync(dev, h->ws + h->L.parts, n * sizeof(DevParticle), cudaMemcpyDeviceToHost,
                                            h->stream), "cudaMemcpyAsync(particles)");
     if (rc == LBM_OK) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    // the last upload from the buffer may have gone out on a stream used
+    // before lbm_set_stream(): wait for it by its own event
+    if (rc == LBM_OK && h->pin_busy) rc = cuda_check(h, cudaEventSynchronize(h->ev_pin), "cudaEventSynchronize");
     if (rc != LBM_OK) return rc;
     h->pin_busy = false;  // every earlier upload from the buffer is done
     if ((rc = status_code(h, st)) != LBM_OK) return rc;

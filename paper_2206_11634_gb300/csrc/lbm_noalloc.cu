@@ -137,5 +137,8 @@ extern "C" int lbm_flags_noalloc(const lbm_config *cfg, const lbm_particle *host
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return LBM_ERR_CUDA;
     if (status[ST_ERR] & ERRB_BRICK_OVERFLOW) return LBM_ERR_CAPACITY;
+    // the binning and the flag pass set no other bit; one would mean a fault
+    // the result cannot be trusted after
+    if (status[ST_ERR] != 0) return LBM_ERR_CUDA;
     return LBM_OK;
 }

