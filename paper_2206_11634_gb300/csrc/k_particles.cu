@@ -604,7 +604,31 @@ __device__ __forceinline__ double qrotate(unsigned mk, const QuadLanes &L, doubl
 }
 
 // Rotation sub-steps of one free particle by its quad of lanes; mk holds the
-// lanes of every quad of this warp that takes part.
+// lanes of every quad of this warp that takes part.  FP64 throughout.
+//
+// On this GPU an FP64 warp instruction occupies its sub-partition for 64
+// cycles, so the sub-step is written for few of them (26 per sub-step, for
+// every quad of the warp at once); shuffles, sign flips and compares run on
+// other pipes.  It is the same sub-step as rotate_substep and the oracle's,
+// rearranged:
+// - half-kick  wh = wb + hh f(wb, Tb) as fma(hh cI w_{l+1}, w_{l+2}, wb + hh iI Tb);
+// - exp(h wh / 2) = (c, sc wh) with c and sc from their Taylor series in
+//   s2 = |wh|^2, two terms past the leading one (truncation below 1e-18 while
+//   a2 = (h/2)^2 s2 <= 1e-5, i.e. |w| h <= 6e-3; larger a2 takes the longer
+//   series or sincos);
+// - the body-frame torque of the new orientation, R(q (x) d)^T T_w =
+//   R(d)^T R(q)^T T_w, from the previous one: Tb' = Tb - 2 c X + 2 s x X,
+//   X = s x Tb, (c, s) = d (the same rotation; the rounding differs from
+//   rebuilding it from q by ~1e-16 per sub-step, and Tb is rebuilt from q at
+//   every LBM step);
+// - the closing half-kick's ROT_ITERS = 2 fixed-point sweeps with the
+//   constants hh cI, hh iI folded in;
+// - q <- q (x) d with the signs of the quaternion product applied as sign
+//   flips of the shuffled q.
+__device__ __forceinline__ double dneg_if(double v, bool neg) {
+    return __longlong_as_double(__double_as_longlong(v) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
+}
+
 __device__ void rotate_free_quad(unsigned mk, const DevParticle &p, const double *Th_world, double h, int n_sub,
                                  DevParticle &out) {
     const QuadLanes L = quad_lanes();
@@ -612,36 +636,66 @@ __device__ void rotate_free_quad(unsigned mk, const DevParticle &p, const double
     const int m = lane == 0 ? 0 : lane - 1;
     double q = p.q[lane];
     const double Tw = lane == 0 ? 0.0 : Th_world[m];
-    const double iI = p.iI[m], cI = p.cI[m];
     double wb = qrotate(mk, L, q, lane == 0 ? 0.0 : p.w[m], false);
     double Tb = qrotate(mk, L, q, Tw, false);
     if (__all_sync(mk, wb == 0.0 && Tb == 0.0)) return;  // nothing turns
     const double hh = 0.5 * h, qh2 = 0.25 * h * h;
+    // per-lane constants (lane 0 holds the quaternion's scalar part only)
+    const double cIhh = lane == 0 ? 0.0 : hh * p.cI[m];
+    const double iIhh = lane == 0 ? 0.0 : hh * p.iI[m];
+    // c = 1 - a2/2 + a2^2/24 (lane 0), sc = hh (1 - a2/6 + a2^2/120)
+    // (lanes 1..3), a2 = qh2 s2: as polynomials in s2
+    const double k2 = lane == 0 ? qh2 * qh2 * (1.0 / 24.0) : hh * qh2 * qh2 * (1.0 / 120.0);
+    const double k1 = lane == 0 ? -0.5 * qh2 : -hh * qh2 * (1.0 / 6.0);
+    const double k0 = lane == 0 ? 1.0 : hh;
+    // s2 bound for the short series: a2 <= 1e-5
+    const long long s2_short = __double_as_longlong(1e-5 / qh2);
+    const bool neg1 = L.s1 < 0.0, neg2 = L.s2 < 0.0, neg3 = L.s3 < 0.0;
+    double hT = iIhh * Tb;
     for (int sub = 0; sub < n_sub; sub++) {
-        const double wh = wb + hh * qeuler(mk, L, wb, Tb, iI, cI);
-        // q <- q (x) exp(h wh / 2), sine and cosine from their Taylor series
-        const double a2 = qh2 * qsum3(mk, L, wh * wh);
-        double sc, c;
-        if (a2 <= 1e-10) {
-            sc = hh * (1.0 - a2 * (1.0 / 6.0));
-            c = 1.0 + a2 * (-0.5 + a2 * (1.0 / 24.0));
-        } else if (a2 <= 1.0 / 256.0) {
-            sc = hh * (1.0 + a2 * (-1.0 / 6.0 + a2 * (1.0 / 120.0 + a2 * (-1.0 / 5040.0 + a2 * (1.0 / 362880.0 + a2 * (-1.0 / 39916800.0))))));
-            c = 1.0 + a2 * (-0.5 + a2 * (1.0 / 24.0 + a2 * (-1.0 / 720.0 + a2 * (1.0 / 40320.0 + a2 * (-1.0 / 3628800.0)))));
+        // first half-kick
+        const double w1 = qget(mk, wb, L.l1), w2 = qget(mk, wb, L.l2);
+        const double wh = fma(cIhh * w1, w2, wb + hT);
+        // exp(h wh / 2)
+        // (lane 0's vector slots carry qrotate's x component: left out)
+        double sq = lane == 0 ? 0.0 : wh * wh;
+        double s2 = sq + __shfl_xor_sync(mk, sq, 1, 4);
+        s2 += __shfl_xor_sync(mk, s2, 2, 4);
+        double d;
+        if (__all_sync(mk, __double_as_longlong(s2) <= s2_short)) {
+            const double poly = fma(s2, fma(s2, k2, k1), k0);
+            d = poly * (lane == 0 ? 1.0 : wh);
         } else {
-            const double wn = sqrt(4.0 * a2) / h;
-            double sn;
-            sincos(hh * wn, &sn, &c);
-            sc = sn / wn;
+            const double a2 = qh2 * s2;
+            double sc, c;
+            if (a2 <= 1.0 / 256.0) {
+                sc = hh * (1.0 + a2 * (-1.0 / 6.0 + a2 * (1.0 / 120.0 + a2 * (-1.0 / 5040.0 + a2 * (1.0 / 362880.0 + a2 * (-1.0 / 39916800.0))))));
+                c = 1.0 + a2 * (-0.5 + a2 * (1.0 / 24.0 + a2 * (-1.0 / 720.0 + a2 * (1.0 / 40320.0 + a2 * (-1.0 / 3628800.0)))));
+            } else {
+                const double wn = sqrt(s2);
+                double sn;
+                sincos(hh * wn, &sn, &c);
+                sc = sn / wn;
+            }
+            d = lane == 0 ? c : sc * wh;
         }
-        const double d = lane == 0 ? c : sc * wh;
+        // body-frame torque of the new orientation: Tb + 2 (s x (s x Tb)) - 2 c (s x Tb)
+        const double s1 = qget(mk, d, L.l1), s2v = qget(mk, d, L.l2);
+        const double T1 = qget(mk, Tb, L.l1), T2 = qget(mk, Tb, L.l2);
+        const double X = fma(s1, T2, -(s2v * T1));
+        const double X1 = qget(mk, X, L.l1), X2 = qget(mk, X, L.l2);
+        const double Y = fma(s1, X2, -(s2v * X1));
+        const double cc = qget(mk, d, 0);
+        Tb = fma(-2.0 * cc, X, fma(2.0, Y, Tb));
+        hT = iIhh * Tb;
+        // closing half-kick, two fixed-point sweeps
+        const double t1 = wh + hT;
+        const double v1 = fma(cIhh * qget(mk, wh, L.l1), qget(mk, wh, L.l2), t1);
+        wb = fma(cIhh * qget(mk, v1, L.l1), qget(mk, v1, L.l2), t1);
+        // q <- q (x) d
         const double q0 = qget(mk, q, 0), q1 = qget(mk, q, 1), q2 = qget(mk, q, 2), q3 = qget(mk, q, 3);
-        const double dk = d, dp1 = qget(mk, d, L.p1), dp2 = qget(mk, d, L.p2), dp3 = qget(mk, d, L.p3);
-        q = fma(L.s3 * q3, dp3, fma(L.s2 * q2, dp2, fma(L.s1 * q1, dp1, q0 * dk)));
-        Tb = qrotate(mk, L, q, Tw, false);
-        double w1 = wh;
-        for (int it = 0; it < ROT_ITERS; it++) w1 = wh + hh * qeuler(mk, L, w1, Tb, iI, cI);
-        wb = w1;
+        const double dp1 = qget(mk, d, L.p1), dp2 = qget(mk, d, L.p2), dp3 = qget(mk, d, L.p3);
+        q = fma(dneg_if(q3, neg3), dp3, fma(dneg_if(q2, neg2), dp2, fma(dneg_if(q1, neg1), dp1, q0 * d)));
     }
     // renormalise once per LBM step, back to world frame
     double n2 = q * q;
