@@ -103,32 +103,42 @@ __device__ __forceinline__ void exp_half(float hh, float qh2, const float w[3], 
 // launch (the contact state is loaded from global memory once and written
 // back once), so the sub-step chain never waits on an L2 round trip
 // ---------------------------------------------------------------------------
-struct Shared {
-    float xh[kMaxP][3], xl[kMaxP][3];   // position, compensated
-    float v[kMaxP][3];                  // velocity (world)
-    float w[kMaxP][3];                  // angular velocity (world)
-    float xref[kMaxP][3];               // position at the last list build
-    float Fc[kMaxP][3], Tc[kMaxP][3];   // contact force / torque of the last evaluation
-    float brad[kMaxP], Rs[kMaxP], reach[kMaxP];
-    float4 rc[kDem32MaxCp];             // control points R(q) cpb relative to x, and K
-    int cpo[kMaxP + 1];                 // offsets into rc
-    unsigned bits[kMaxP][kWords];       // candidate pairs (i < j)
-    unsigned short up[kMaxP][kMaxAdj];  // partners j > i, ascending
-    int dn[kMaxP][kMaxAdj];             // (m << 8 | slot of k in up[m]), m < k, ascending
-    int nup[kMaxP], ndn[kMaxP];
-    int gid[kMaxP];                     // particle index of table entry k (k_dem32: k itself)
-    int n;                              // entries in the tables
-    int ioff[kMaxP + 1];                // prefix sums of nup: item of (i, slot) = ioff[i] + slot
+template <int CAP, int ITEMS, int CPS>
+struct SharedT {
+    static constexpr int kCap = CAP;                // particles in the tables
+    static constexpr int kItems = ITEMS;            // candidate pairs resident in shared memory
+    static constexpr int kWordsT = (CAP + 31) / 32;
+    static constexpr int kCps = CPS;                // control points of all particles
+    float xh[CAP][3], xl[CAP][3];   // position, compensated
+    float v[CAP][3];                // velocity (world)
+    float w[CAP][3];                // angular velocity (world)
+    float xref[CAP][3];             // position at the last list build
+    float Fc[CAP][3], Tc[CAP][3];   // contact force / torque of the last evaluation
+    float brad[CAP], Rs[CAP], reach[CAP];
+    float4 rc[CPS];                 // control points R(q) cpb relative to x, and K
+    int cpo[CAP + 1];               // offsets into rc
+    unsigned bits[CAP][(CAP + 31) / 32];  // candidate pairs (i < j)
+    unsigned short up[CAP][kMaxAdj];      // partners j > i, ascending
+    int dn[CAP][kMaxAdj];                 // (m << 8 | slot of k in up[m]), m < k, ascending
+    int nup[CAP], ndn[CAP];
+    int gid[CAP];                   // particle index of table entry k (k_dem32: k itself)
+    int n;                          // entries in the tables
+    int ioff[CAP + 1];              // prefix sums of nup: item of (i, slot) = ioff[i] + slot
     // candidate pairs: contact history and results
-    int it_on[kMaxItems];
-    float it_xm[kMaxItems][3], it_xi[kMaxItems][3];
-    float it_res[kMaxItems][9];         // F_i, T_i, T_j
+    int it_on[ITEMS];
+    float it_xm[ITEMS][3], it_xi[ITEMS][3];
+    float it_res[ITEMS][9];         // F_i, T_i, T_j
     // walls: contact history
-    int w_on[kMaxP][NWALL];
-    float w_xcw[kMaxP][NWALL][3], w_xi[kMaxP][NWALL][3];
+    int w_on[CAP][NWALL];
+    float w_xcw[CAP][NWALL][3], w_xi[CAP][NWALL][3];
 };
+// every particle in one CTA (k_dem32, and k_dem64c for a large contact group)
+using Shared = SharedT<kMaxP, kMaxItems, kDem32MaxCp>;
+// a contact group of up to 32 particles (k_dem64c, one CTA per group)
+using SharedSmall = SharedT<kSmallContactGroup, 256, kSmallContactGroup * MAXCP>;
 
-__device__ __forceinline__ void rel_vec(const Shared &S, const Params &P, int i, int j, float d[3]) {
+template <class SH>
+__device__ __forceinline__ void rel_vec(const SH &S, const Params &P, int i, int j, float d[3]) {
     for (int a = 0; a < 3; a++)
         d[a] = minimg_f(P, a, (S.xh[j][a] - S.xh[i][a]) + (S.xl[j][a] - S.xl[i][a]));
 }
@@ -193,7 +203,8 @@ constexpr float kNewtonTol2 = 1e-10f;
 // x_i).  Same steps as the FP64 path: Newton on grad(M_i + M_j) = 0, valid
 // when c_tol < M < 1 for both, closest points by the first-order step, contact
 // point in the middle of the overlap.
-__device__ bool pair_geom_f(const Params &P, const Shared &S, int i, int j, const float d[3], bool warm, float xm[3],
+template <class SH>
+__device__ bool pair_geom_f(const Params &P, const SH &S, int i, int j, const float d[3], bool warm, float xm[3],
                             float &delta, float nv[3], float xcp[3]) {
     const float4 *rci = S.rc + S.cpo[i];
     const float4 *rcj = S.rc + S.cpo[j];
@@ -264,7 +275,8 @@ __device__ bool pair_geom_f(const Params &P, const Shared &S, int i, int j, cons
 
 // Wall geometry, Eqs. (10)-(13), frame centred on the particle; prel: the
 // wall plane's coordinate relative to x along its axis.
-__device__ bool wall_geom_f(const Params &P, const Shared &S, int k, int wall, float prel, bool warm, float xcw[3],
+template <class SH>
+__device__ bool wall_geom_f(const Params &P, const SH &S, int k, int wall, float prel, bool warm, float xcw[3],
                             float &delta, float nv[3], float xcp[3]) {
     const int ax = wall / 2, side = wall % 2;
     const float m_ax = side ? 1.0f : -1.0f;
@@ -324,12 +336,13 @@ __device__ bool wall_geom_f(const Params &P, const Shared &S, int k, int wall, f
 
 // Pair contact history of the candidate items to global memory (before the
 // list is rebuilt, and at the end of the launch).
-__device__ void store_items(const Params &P, Shared &S) {
+template <class SH>
+__device__ void store_items(const Params &P, SH &S) {
     const int np = S.n;
     for (int i = threadIdx.x; i < np; i += blockDim.x)
         for (int s = 0; s < S.nup[i]; s++) {
             const int it = S.ioff[i] + s;
-            if (it >= kMaxItems) break;
+            if (it >= SH::kItems) break;
             const int pidx = S.gid[i] * P.np + S.gid[S.up[i][s]];
             P.pair_on[pidx] = S.it_on[it];
             for (int a = 0; a < 3; a++) {
@@ -343,7 +356,8 @@ __device__ void store_items(const Params &P, Shared &S) {
 // out lose their contact history, as in the FP64 path.  Sets *possible when
 // some pair is within reach of a contact this step (or one is active).
 // Loads the candidates' contact history into shared memory.
-__device__ void build_lists(const Params &P, Shared &S, int *possible) {
+template <class SH>
+__device__ void build_lists(const Params &P, SH &S, int *possible) {
     const int np = S.n, tid = threadIdx.x;
     const int nw = (np + 31) / 32;
     for (int idx = tid; idx < np * nw; idx += blockDim.x) {
@@ -410,13 +424,13 @@ __device__ void build_lists(const Params &P, Shared &S, int *possible) {
         int o = 0;
         for (int i = 0; i < np; i++) { S.ioff[i] = o; o += S.nup[i]; }
         S.ioff[np] = o;
-        if (o > kMaxItems) atomicOr(&P.status[ST_ERR], ERRB_DEM_CAPACITY);
+        if (o > SH::kItems) atomicOr(&P.status[ST_ERR], ERRB_DEM_CAPACITY);
     }
     __syncthreads();
     for (int i = tid; i < np; i += blockDim.x)
         for (int s = 0; s < S.nup[i]; s++) {
             const int it = S.ioff[i] + s;
-            if (it >= kMaxItems) break;
+            if (it >= SH::kItems) break;
             const int pidx = S.gid[i] * P.np + S.gid[S.up[i][s]];
             S.it_on[it] = P.pair_on[pidx];
             for (int a = 0; a < 3; a++) {
@@ -429,9 +443,10 @@ __device__ void build_lists(const Params &P, Shared &S, int *possible) {
 
 // Pair contacts of the candidate list (one item per thread); results into
 // it_res (zeros when not in contact).
-__device__ void pair_contacts(const Params &P, Shared &S, float h) {
+template <class SH>
+__device__ void pair_contacts(const Params &P, SH &S, float h) {
     const int np = S.n;
-    const int total = min(S.ioff[np], kMaxItems);
+    const int total = min(S.ioff[np], SH::kItems);
     for (int it = threadIdx.x; it < total; it += blockDim.x) {
         int lo = 0, hi = np - 1;  // item -> (i, slot): last i with ioff[i] <= it
         while (lo < hi) {
@@ -472,17 +487,18 @@ __device__ void pair_contacts(const Params &P, Shared &S, float h) {
 }
 
 // Per particle: pair terms in index order, then the walls.
-__device__ void gather_contacts(const Params &P, Shared &S, int k, float h, float F[3], float T[3]) {
+template <class SH>
+__device__ void gather_contacts(const Params &P, SH &S, int k, float h, float F[3], float T[3]) {
     for (int a = 0; a < 3; a++) { F[a] = 0.f; T[a] = 0.f; }
     for (int e = 0; e < S.ndn[k]; e++) {
         const int m = S.dn[k][e] >> 8, s = S.dn[k][e] & 255;
         const int it = S.ioff[m] + s;
-        if (it >= kMaxItems) continue;
+        if (it >= SH::kItems) continue;
         for (int a = 0; a < 3; a++) { F[a] += -S.it_res[it][a]; T[a] += S.it_res[it][6 + a]; }
     }
     for (int s = 0; s < S.nup[k]; s++) {
         const int it = S.ioff[k] + s;
-        if (it >= kMaxItems) break;
+        if (it >= SH::kItems) break;
         for (int a = 0; a < 3; a++) { F[a] += S.it_res[it][a]; T[a] += S.it_res[it][3 + a]; }
     }
     for (int wall = 0; wall < NWALL; wall++) {
@@ -509,7 +525,8 @@ __device__ void gather_contacts(const Params &P, Shared &S, int k, float h, floa
 }
 
 // Rotated control points of particle k into the shared table.
-__device__ __forceinline__ void put_rc(const Params &P, Shared &S, int k, const float q[4]) {
+template <class SH>
+__device__ __forceinline__ void put_rc(const Params &P, SH &S, int k, const float q[4]) {
     const DevParticle &p = P.parts[S.gid[k]];
     for (int c = 0; c < p.ncp; c++) {
         float r[3];
@@ -845,13 +862,18 @@ struct Delta {
 __device__ __forceinline__ void dl_set(Delta &a, double v) { a.bf = (float)v; a.d = {0.f, 0.f}; }
 __device__ __forceinline__ void dl_add(Delta &a, float b) { a.d = df_add(a.d, b); }
 
-__global__ void __launch_bounds__(kThreads) k_dem64c(Params P) {
+// One CTA per contact group (k_dem64_plan): groups of up to 32 particles
+// with tables sized for them (kLarge = false, 32 threads), larger ones with
+// the full tables (kLarge, 512 threads).
+template <class SH, bool kLarge>
+__global__ void __launch_bounds__(kLarge ? kThreads : kSmallContactGroup) k_dem64c(Params P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Shared &S = *reinterpret_cast<Shared *>(smem_raw);
+    SH &S = *reinterpret_cast<SH *>(smem_raw);
     const int tid = threadIdx.x;
-    const int na = P.dem_list[1];
-    if (na == 0) return;
-    const int *act = P.dem_list + 2 + P.np;
+    if ((int)blockIdx.x >= P.dem_list[kLarge ? 3 : 2]) return;
+    const int *grp = dem_groups(P, kLarge) + 2 * blockIdx.x;
+    const int na = grp[1];
+    const int *act = dem_active(P) + grp[0];
     const float h = P.h_f, hh = 0.5f * h, qh2 = 0.25f * h * h;
     const bool own = tid < na;
     const int g = own ? act[tid] : 0;
@@ -886,11 +908,11 @@ __global__ void __launch_bounds__(kThreads) k_dem64c(Params P) {
         for (int k = 0; k < na; k++) { S.cpo[k] = o; o += P.parts[act[k]].ncp; }
         S.cpo[na] = o;
         S.n = na;
-        if (o > kDem32MaxCp) atomicOr(&P.status[ST_ERR], ERRB_DEM_CAPACITY);
+        if (o > SH::kCps) atomicOr(&P.status[ST_ERR], ERRB_DEM_CAPACITY);
     }
     for (int k = tid; k < na; k += blockDim.x) S.gid[k] = act[k];
     __syncthreads();
-    if (S.cpo[na] > kDem32MaxCp) return;
+    if (S.cpo[na] > SH::kCps) return;
 
     // FP32 tables: position (hi + lo of the FP64 value), velocity, world
     // angular velocity from the body rate wf
@@ -1076,12 +1098,17 @@ __global__ void __launch_bounds__(kThreads) k_dem64c(Params P) {
 }
 
 void launch_dem64c(const Params &P, cudaStream_t st) {
+    // the dynamic shared memory limits are raised once per device
     static bool attr_set[64] = {};
-    const int bytes = (int)sizeof(Shared);
+    static_assert(sizeof(SharedSmall) <= 48 * 1024, "small contact-group tables exceed 48 KB");
+    const int big = (int)sizeof(Shared);
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev])
-        attr_set[dev] = cudaFuncSetAttribute(k_dem64c, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
-    k_dem64c<<<1, P.np <= 32 ? 32 : kThreads, bytes, st>>>(P);
+        attr_set[dev] =
+            cudaFuncSetAttribute(k_dem64c<Shared, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) == cudaSuccess;
+    // every group could be small (grid np); at most np / 33 are large
+    k_dem64c<SharedSmall, false><<<P.np, kSmallContactGroup, sizeof(SharedSmall), st>>>(P);
+    k_dem64c<Shared, true><<<P.np / (kSmallContactGroup + 1) + 1, kThreads, big, st>>>(P);
 }
 
 // One CTA: a single warp for a few particles (the barriers between the

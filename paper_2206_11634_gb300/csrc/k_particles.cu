@@ -717,15 +717,21 @@ __device__ void rotate_free_quad(unsigned mk, const DevParticle &p, const double
 // One CTA.  The hydrodynamic load as FP64 totals (from the sweep's
 // fixed-point sums), then the split: a particle is active when its bounding
 // sphere can reach a wall, or another particle's, during the step (gap <=
-// reach_i + reach_j, dem_reach); active and inactive particles keep their
-// index order in P.dem_list: [0] inactive count, [1] active count, from [2]
-// the inactive ones, from [2 + np] the active ones.  A pair in contact at the
-// end of the last step overlaps, so it is active again: the contact history
-// of inactive particles is empty.
+// reach_i + reach_j, dem_reach).  Active particles that can reach each other
+// form a contact group (connected components of that relation); groups are
+// independent during the step, so each gets its own CTA.  Every list keeps
+// index order (dem_free() and below).  A pair in contact at the end of the
+// last step overlaps, so it is active again: the contact history of inactive
+// particles is empty.
+constexpr int kPlanEdges = 4096;
 __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
     __shared__ float xs[kFastMaxParticles][3], reach[kFastMaxParticles], br[kFastMaxParticles];
-    __shared__ int act[kFastMaxParticles];
+    __shared__ int act[kFastMaxParticles], parent[kFastMaxParticles], gsz[kFastMaxParticles];
+    __shared__ int gfill[kFastMaxParticles];
+    __shared__ unsigned edge[kPlanEdges];
+    __shared__ int nedge;
     const int np = P.np;
+    if (threadIdx.x == 0) nedge = 0;
     for (int i = threadIdx.x; i < np * 6; i += blockDim.x) {
         const double v = (double)(long long)P.Ffix[i] * (1.0 / (double)(1ull << kForceFixBits));
         const int k = i / 6, c = i % 6;
@@ -747,6 +753,7 @@ __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
             if (fabsf(plane - xs[k][ax]) - br[k] <= r + 1e-2f) on = 1;
         }
         act[k] = on;
+        parent[k] = k;
     }
     __syncthreads();
     const long long npairs = (long long)np * (np - 1) / 2;
@@ -765,17 +772,65 @@ __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
             d2 += d * d;
         }
         const float lim = br[i] + br[j] + reach[i] + reach[j] + 1e-2f;
-        if (d2 <= lim * lim) { act[i] = 1; act[j] = 1; }
+        if (d2 <= lim * lim) {
+            act[i] = 1;
+            act[j] = 1;
+            const int e = atomicAdd(&nedge, 1);
+            if (e < kPlanEdges) edge[e] = ((unsigned)i << 16) | (unsigned)j;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int nf = 0, na = 0;
-        for (int k = 0; k < np; k++) {
-            if (act[k]) P.dem_list[2 + np + na++] = k;
-            else P.dem_list[2 + nf++] = k;
+        // connected components of the edges (union by the smaller root, so a
+        // root is its group's smallest index); beyond the edge table, every
+        // active particle is one group
+        auto find = [&](int a) {
+            while (parent[a] != a) {
+                parent[a] = parent[parent[a]];
+                a = parent[a];
+            }
+            return a;
+        };
+        const int ne = nedge;
+        if (ne > kPlanEdges) {
+            int r = -1;
+            for (int k = 0; k < np; k++)
+                if (act[k]) {
+                    if (r < 0) r = k;
+                    parent[k] = r;
+                }
+        } else {
+            for (int e = 0; e < ne; e++) {
+                const int a = find((int)(edge[e] >> 16)), b = find((int)(edge[e] & 0xFFFFu));
+                if (a != b) {
+                    if (a < b) parent[b] = a;
+                    else parent[a] = b;
+                }
+            }
         }
+        int nf = 0;
+        for (int k = 0; k < np; k++) {
+            gsz[k] = 0;
+            if (!act[k]) dem_free(P)[nf++] = k;
+        }
+        for (int k = 0; k < np; k++)
+            if (act[k]) gsz[find(k)]++;
+        int o = 0, ns = 0, nl = 0;
+        for (int k = 0; k < np; k++) {  // groups in the order of their smallest member
+            if (!act[k] || find(k) != k) continue;
+            gfill[k] = o;
+            int *g = dem_groups(P, gsz[k] > kSmallContactGroup);
+            const int slot = gsz[k] > kSmallContactGroup ? nl++ : ns++;
+            g[2 * slot] = o;
+            g[2 * slot + 1] = gsz[k];
+            o += gsz[k];
+        }
+        for (int k = 0; k < np; k++)
+            if (act[k]) dem_active(P)[gfill[find(k)]++] = k;
         P.dem_list[0] = nf;
-        P.dem_list[1] = na;
+        P.dem_list[1] = o;
+        P.dem_list[2] = ns;
+        P.dem_list[3] = nl;
     }
 }
 
@@ -788,7 +843,7 @@ __global__ void __launch_bounds__(128) k_dem64_free(Params P) {
     const int slot = blockIdx.x * 32 + (int)(threadIdx.x >> 2);
     if (blockIdx.x * 32 + (int)((threadIdx.x & ~31u) >> 2) >= nf) return;  // the whole warp is idle
     const bool has = slot < nf;
-    const int k = has ? P.dem_list[2 + slot] : 0;
+    const int k = has ? dem_free(P)[slot] : 0;
     const int lane = threadIdx.x & 3;
     if (has) {
         DevParticle &p = P.parts[k];

@@ -39,7 +39,7 @@ struct Layout {
     size_t pairF, pair_on, pair_xi, pair_xm, wall_on, wall_xi, wall_xcw;
     size_t pair_xi_f, pair_xm_f, wall_xi_f, wall_xcw_f;
     size_t sskip, snodes, slinks, scount, smf;  // fixed-geometry sweep (below FP64)
-    size_t dem_list;   // k_dem64_plan's split of the particles [2 + 2P]
+    size_t dem_list;   // k_dem64_plan's split of the particles [4 + 6P]
     int snode_cap, slink_cap;
     size_t status;
     size_t total;
@@ -140,7 +140,7 @@ void make_layout(const lbm_config *c, Layout *L) {
     L->slinks = take((size_t)L->slink_cap * sizeof(StaticLink));
     L->scount = take(fixed_sweep ? 8 : 0);
     L->smf = take(fixed_sweep ? P * 48 : 0);
-    L->dem_list = take((2 + 2 * P) * 4);
+    L->dem_list = take((4 + 6 * P) * 4);
     L->status = take(ST_SLOTS * 4);
     L->total = o;
 }

@@ -77,6 +77,7 @@ constexpr int kDefaultChainPerSm = 0;
 constexpr int kDem32MaxParticles = 256;
 constexpr int kDem32MaxCp = 2048;     // control points of all particles
 constexpr int kDemMaxAdj = 16;        // candidate contact partners per particle and direction
+constexpr int kSmallContactGroup = 32;  // contact groups up to this size run one 32-thread CTA each
 
 // ---------------------------------------------------------------------------
 // Lattices.  D3Q19 (rest 1/3, axes 1/18, face diagonals 1/36) and the D3Q15
@@ -367,7 +368,7 @@ struct Params {
     float *wall_xi_f, *wall_xcw_f;  // [np*6][3], FP32 DEM: spring, warm start (relative to x_k)
     void *bin_next;    // batched lattices: the other parity's per-step region (cleared by the binning)
     long long bin_next_bytes;
-    int *dem_list;     // [2 + 2 np], k_dem64_plan: counts, inactive and active particles
+    int *dem_list;     // [4 + 6 np], k_dem64_plan's split of the particles (dem_free() and below)
     int *status;       // [ST_SLOTS], sticky error bits
     int *counters;     // per-step counters, zeroed with the brick lists
     // fixed-geometry sweep (every particle fixed, lattices below FP64): built
@@ -381,6 +382,16 @@ struct Params {
     int snode_cap, slink_cap;
     int snodes_n;               // link nodes (set by the host after the build)
 };
+
+// k_dem64_plan's split of the particles (P.dem_list): [0] inactive count,
+// [1] active count, [2] small contact groups, [3] large ones; then the
+// inactive particles, the active ones group by group, and per small and per
+// large group its (start in the active list, size) pair.
+__host__ __device__ __forceinline__ int *dem_free(const Params &P) { return P.dem_list + 4; }
+__host__ __device__ __forceinline__ int *dem_active(const Params &P) { return P.dem_list + 4 + P.np; }
+__host__ __device__ __forceinline__ int *dem_groups(const Params &P, bool large) {
+    return P.dem_list + 4 + (large ? 4 : 2) * P.np;
+}
 
 __host__ __device__ __forceinline__ int dim_of(const Params &P, int a) { return a == 0 ? P.nx : (a == 1 ? P.ny : P.nz); }
 
