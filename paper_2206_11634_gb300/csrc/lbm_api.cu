@@ -197,6 +197,7 @@ struct lbm_handle {
     int plain_per_sm, chain_per_sm;  // launch schedule (lbm_set_schedule)
     int bin_clean[2];     // the per-step region of that parity is known to be all zero
     int plain_spec;       // the particles' search boxes cover under a tenth of the bricks (set_particles)
+    int plain_after_near; // the plain sweep of a step follows its near sweep (else runs beside the chain)
     int plain_spec_mode;  // lbm_set_plain_speculation: -1 auto (plain_spec), 0 off, 1 on
     int64_t steps;
     char err[256];
@@ -528,6 +529,7 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
         h->plain_per_sm = kDefaultPlainPerSm;
         h->chain_per_sm = kDefaultChainPerSm;
         h->plain_spec = 1;
+        h->plain_after_near = 1;
         h->plain_spec_mode = -1;
         h->bin_clean[0] = h->bin_clean[1] = 1;  // the workspace is cleared below
     }
@@ -766,6 +768,11 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
     for (int j = 0; j < n; j++)
         if (!host[j].fixed) h->all_fixed = 0;
     h->plain_spec = plain_speculates(h->cfg, host, n);
+    // with few near bricks the flag pass and near sweep are short and run
+    // faster alone, and the plain sweep then overlaps the DEM and the next
+    // binning and flag pass; with many, the near sweep is long and the plain
+    // sweep beside it
+    h->plain_after_near = h->plain_spec;
     h->static_steps = 0;
     h->static_state = 0;
     h->snodes_n = 0;
@@ -883,16 +890,31 @@ int lbm_step(lbm_handle *h, int nsteps) {
             // so every event waited on is recorded within this call, as stream
             // capture requires)
             if (t > 0) e = cudaStreamWaitEvent(hs, h->ev_plain, 0);
-            // plain bricks on the low-priority stream, concurrent with the chain
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_bin, 0);
             if (e != cudaSuccess) return cuda_check(h, e, "stream wait");
-            { ProfScope s(h, 2, true, h->aux); by_storage<DoPlain>(h->cfg.storage, P, h->aux); }
-            e = cudaEventRecord(h->ev_plain, h->aux);
-            if (e != cudaSuccess) return cuda_check(h, e, "event record");
-            { ProfScope s(h, 3, true, hs); by_storage<DoNear>(h->cfg.storage, P, hs); }
-            e = cudaEventRecord(h->ev_near, hs);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_near, 0);
-            if (e != cudaSuccess) return cuda_check(h, e, "stream fork");
+            if (h->plain_after_near) {
+                // few near bricks: the near sweep alone, then the plain bricks
+                // on the low-priority stream beside the DEM and the next
+                // step's binning and flag pass (whose refill touches only
+                // nodes next to this step's solid ones, all in near bricks)
+                { ProfScope s(h, 3, true, hs); by_storage<DoNear>(h->cfg.storage, P, hs); }
+                e = cudaEventRecord(h->ev_near, hs);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_near, 0);
+                if (e != cudaSuccess) return cuda_check(h, e, "stream fork");
+                { ProfScope s(h, 2, true, h->aux); by_storage<DoPlain>(h->cfg.storage, P, h->aux); }
+                e = cudaEventRecord(h->ev_plain, h->aux);
+                if (e != cudaSuccess) return cuda_check(h, e, "event record");
+            } else {
+                // plain bricks on the low-priority stream, concurrent with the chain
+                e = cudaStreamWaitEvent(h->aux, h->ev_bin, 0);
+                if (e != cudaSuccess) return cuda_check(h, e, "stream wait");
+                { ProfScope s(h, 2, true, h->aux); by_storage<DoPlain>(h->cfg.storage, P, h->aux); }
+                e = cudaEventRecord(h->ev_plain, h->aux);
+                if (e != cudaSuccess) return cuda_check(h, e, "event record");
+                { ProfScope s(h, 3, true, hs); by_storage<DoNear>(h->cfg.storage, P, hs); }
+                e = cudaEventRecord(h->ev_near, hs);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_near, 0);
+                if (e != cudaSuccess) return cuda_check(h, e, "stream fork");
+            }
         }
         if (!P.force_fixed) { ProfScope s(h, 4, P.np > 0, hs); launch_force_reduce(P, hs); }
         { ProfScope s(h, 5, P.np > 0 && P.n_sub > 0, hs); launch_dem(P, hs, h->dem2, h->ev_dsplit, h->ev_dfree); }
