@@ -98,6 +98,8 @@ typedef struct {
     double (*pair_xi)[3];
     double (*pair_xm)[3];
     int *wall_on;
+    int *pair_warm;   /* the last evaluation of this potential collision found a valid x_m */
+    int *wall_warm;   /* ... a valid x_cw */
     double (*wall_xi)[3];
     double (*wall_xcw)[3];
     long step;
@@ -744,9 +746,12 @@ static void point_velocity(const orc_state *s, int j, const double x[3], double 
 }
 
 /* Metaball-metaball contact, §2.1.3, Eqs. (5)-(9).  Newton-Raphson on
- * grad(M_0 + M_1) = 0 (Eq. (6)) from the previous minimum when the pair was
- * in contact, else from the midpoint of the closest pair of control points
- * (reading: the paper defers the start point to its ref. [zhang2021metaball]).
+ * grad(M_0 + M_1) = 0 (Eq. (6)) from xm_start (the caller passes the previous
+ * minimum when the last evaluation of this potential collision found a valid
+ * one), else from the midpoint of the closest pair of control points
+ * (reading: the paper defers the start point to its ref. [zhang2021metaball];
+ * the warm start follows what §2.1.4 states for walls).  *valid: Newton
+ * converged to a minimum within Eq. (5)'s constraints.
  * The minimum must satisfy c_tol < M_k < 1 (Eq. (5)).  Closest points by
  * Eqs. (7)-(8), overlap, normal and contact point by Eq. (9).  Reading of
  * Eq. (9): the contact point is the middle of the overlap,
@@ -754,9 +759,11 @@ static void point_velocity(const orc_state *s, int j, const double x[3], double 
  * printed "+" places it outside the overlap for this n).
  * Returns 1 with delta, n (unit, from j to i) and x_cp when the dilated
  * shapes overlap. */
-int orc_pair_geometry(const orc_state *s, int i, int j, const double *xm_start, double xm_out[3], double *delta,
-                      double nvec[3], double xcp[3]) {
+static int pair_geometry(const orc_state *s, int i, int j, const double *xm_start, double xm_out[3], double *delta,
+                         double nvec[3], double xcp[3], int *valid) {
     double x[3];
+    int converged = 0;
+    *valid = 0;
     if (xm_start) {
         for (int a = 0; a < 3; a++) x[a] = xm_start[a];
     } else {
@@ -781,13 +788,14 @@ int orc_pair_geometry(const orc_state *s, int i, int j, const double *xm_start, 
         for (int a = 0; a < 9; a++) H[a] = H0[a] + H1[a];
         if (!solve3(H, g, dx)) break;
         for (int a = 0; a < 3; a++) x[a] += dx[a];
-        if (norm(dx) < 1e-12) break;
+        if (norm(dx) < 1e-12) { converged = 1; break; }
     }
     for (int a = 0; a < 3; a++) xm_out[a] = x[a];
     double M0, g0[3], H0[9], M1, g1[3], H1[9];
     metaball_dd(s, i, x, &M0, g0, H0);
     metaball_dd(s, j, x, &M1, g1, H1);
     if (!(M0 > s->c.c_tol && M0 < 1.0 && M1 > s->c.c_tol && M1 < 1.0)) return 0;
+    *valid = converged;   /* a local minimum of Eq. (5) within its constraints */
     double q0 = (1.0 - M0) / dot(g0, g0), q1 = (1.0 - M1) / dot(g1, g1);
     double xc0[3], xc1[3], dc[3];
     for (int a = 0; a < 3; a++) {
@@ -805,17 +813,27 @@ int orc_pair_geometry(const orc_state *s, int i, int j, const double *xm_start, 
     return 1;
 }
 
+int orc_pair_geometry(const orc_state *s, int i, int j, const double *xm_start, double xm_out[3], double *delta,
+                      double nvec[3], double xcp[3]) {
+    int valid;
+    return pair_geometry(s, i, j, xm_start, xm_out, delta, nvec, xcp, &valid);
+}
+
 /* Metaball-plane contact, §2.1.4, Eqs. (10)-(13).  The plane is the box wall
  * wall = 2*axis + side (side 0 at -1/2, side 1 at n-1/2).  In the rotated
  * frame whose x axis is the wall normal m (pointing out of the fluid), Newton
  * solves the two tangential components of grad M = 0 on the plane (Eq. (10))
- * with dM/dm < 0; start from the previous x_cw when the contact existed,
- * else from the projection of the control point nearest the plane.
+ * with dM/dm < 0; start from xcw_start (the caller passes the previous x_cw
+ * when this potential collision existed at the previous evaluation and that
+ * evaluation found a valid x_cw), else from the projection of the control
+ * point nearest the plane.  *valid: Newton converged and dM/dm < 0 there.
  * Closest point by Eqs. (11)-(12), delta and n by Eq. (13) with n from x_cw
  * to x_cm.  Reading of Eq. (13): x_cp = x_cw - (delta/2) n, the middle of the
  * overlap. */
-int orc_wall_geometry(const orc_state *s, int j, int wall, const double *xcw_start, double xcw_out[3],
-                      double *delta, double nvec[3], double xcp[3]) {
+static int wall_geometry(const orc_state *s, int j, int wall, const double *xcw_start, double xcw_out[3],
+                         double *delta, double nvec[3], double xcp[3], int *valid) {
+    int converged = 0;
+    *valid = 0;
     int ax = wall / 2, side = wall % 2;
     double plane = side ? dim(s, ax) - 0.5 : -0.5;
     double m[3] = {0, 0, 0};
@@ -844,12 +862,13 @@ int orc_wall_geometry(const orc_state *s, int j, int wall, const double *xcw_sta
         double d0 = (J11 * r0 - J01 * r1) / det, d1 = (-J10 * r0 + J00 * r1) / det;
         x[t1] += d0;
         x[t2] += d1;
-        if (sqrt(d0 * d0 + d1 * d1) < 1e-12) break;
+        if (sqrt(d0 * d0 + d1 * d1) < 1e-12) { converged = 1; break; }
     }
     for (int a = 0; a < 3; a++) xcw_out[a] = x[a];
     double M, g[3], H[9];
     metaball_dd(s, j, x, &M, g, H);
     if (!(dot(g, m) < 0.0)) return 0;
+    *valid = converged;   /* grad M along the outward normal at a converged x_cw */
     double qR = (1.0 - M) / dot(g, g);
     double xcm[3], dc[3];
     for (int a = 0; a < 3; a++) {
@@ -864,6 +883,12 @@ int orc_wall_geometry(const orc_state *s, int j, int wall, const double *xcw_sta
         xcp[a] = x[a] - 0.5 * *delta * nvec[a];
     }
     return 1;
+}
+
+int orc_wall_geometry(const orc_state *s, int j, int wall, const double *xcw_start, double xcw_out[3],
+                      double *delta, double nvec[3], double xcp[3]) {
+    int valid;
+    return wall_geometry(s, j, wall, xcw_start, xcw_out, delta, nvec, xcp, &valid);
 }
 
 /* All contact forces and torques at the current state (pairs, then walls),
@@ -881,10 +906,16 @@ static void contacts(orc_state *s, double h) {
             double bi = bounding_radius(&s->p[i], s->c.c0), bj = bounding_radius(&s->p[j], s->c.c0);
             if (norm(dx) > bi + bj) {
                 s->pair_on[pij] = 0;
+                s->pair_warm[pij] = 0;
                 continue;
             }
+            /* Newton from the previous x_m when this potential collision
+             * (overlapping bounding spheres) existed at the previous
+             * evaluation and found a valid x_m, as for walls (§2.1.4) */
             double xm[3], delta, nv[3], xcp[3];
-            int hit = orc_pair_geometry(s, i, j, s->pair_on[pij] ? s->pair_xm[pij] : NULL, xm, &delta, nv, xcp);
+            int hit = pair_geometry(s, i, j, s->pair_warm[pij] ? s->pair_xm[pij] : NULL, xm, &delta, nv, xcp,
+                                    &s->pair_warm[pij]);
+            for (int a = 0; a < 3; a++) s->pair_xm[pij][a] = xm[a];
             if (!hit) {
                 s->pair_on[pij] = 0;
                 continue;
@@ -892,7 +923,6 @@ static void contacts(orc_state *s, double h) {
             if (!s->pair_on[pij])
                 for (int a = 0; a < 3; a++) s->pair_xi[pij][a] = 0.0;
             s->pair_on[pij] = 1;
-            for (int a = 0; a < 3; a++) s->pair_xm[pij][a] = xm[a];
             double vi[3], vj[3], Fi[3];
             point_velocity(s, i, xcp, vi);
             point_velocity(s, j, xcp, vj);
@@ -914,19 +944,25 @@ static void contacts(orc_state *s, double h) {
         for (int wall = 0; wall < ORC_NWALL; wall++) {
             int ax = wall / 2, side = wall % 2;
             long wj = (long)j * ORC_NWALL + wall;
-            if (s->c.periodic[ax]) { s->wall_on[wj] = 0; continue; }
+            if (s->c.periodic[ax]) { s->wall_on[wj] = 0; s->wall_warm[wj] = 0; continue; }
             double plane = side ? dim(s, ax) - 0.5 : -0.5;
             if (fabs(plane - s->p[j].x[ax]) > bounding_radius(&s->p[j], s->c.c0)) {
                 s->wall_on[wj] = 0;
+                s->wall_warm[wj] = 0;
                 continue;
             }
+            /* §2.1.4: Newton starts from the previous x_cw when this
+             * potential collision (the plane within the bounding sphere)
+             * already existed at the previous evaluation, in contact or
+             * not, and that evaluation found a valid x_cw */
             double xcw[3], delta, nv[3], xcp[3];
-            int hit = orc_wall_geometry(s, j, wall, s->wall_on[wj] ? s->wall_xcw[wj] : NULL, xcw, &delta, nv, xcp);
+            int hit = wall_geometry(s, j, wall, s->wall_warm[wj] ? s->wall_xcw[wj] : NULL, xcw, &delta, nv, xcp,
+                                    &s->wall_warm[wj]);
+            for (int a = 0; a < 3; a++) s->wall_xcw[wj][a] = xcw[a];
             if (!hit) { s->wall_on[wj] = 0; continue; }
             if (!s->wall_on[wj])
                 for (int a = 0; a < 3; a++) s->wall_xi[wj][a] = 0.0;
             s->wall_on[wj] = 1;
-            for (int a = 0; a < 3; a++) s->wall_xcw[wj][a] = xcw[a];
             double vi[3], vw[3] = {0, 0, 0}, Fi[3], ri[3], ti[3];
             point_velocity(s, j, xcp, vi);
             contact_law(s, delta, nv, vi, vw, s->wall_xi[wj], h, Fi);
@@ -1094,10 +1130,10 @@ void orc_mass_properties(orc_particle *p, double c0, double h) {
 static void free_particles(orc_state *s) {
     free(s->p); free(s->cpw); free(s->Fh); free(s->Th); free(s->Fc); free(s->Tc);
     free(s->pair_on); free(s->pair_xi); free(s->pair_xm);
-    free(s->wall_on); free(s->wall_xi); free(s->wall_xcw);
+    free(s->wall_on); free(s->wall_warm); free(s->wall_xi); free(s->wall_xcw); free(s->pair_warm);
     s->p = NULL; s->cpw = NULL; s->Fh = s->Th = s->Fc = s->Tc = NULL;
     s->pair_on = NULL; s->pair_xi = s->pair_xm = NULL;
-    s->wall_on = NULL; s->wall_xi = s->wall_xcw = NULL;
+    s->wall_on = s->wall_warm = s->pair_warm = NULL; s->wall_xi = s->wall_xcw = NULL;
     s->np = 0;
 }
 
@@ -1157,6 +1193,8 @@ int orc_set_particles(orc_state *s, const orc_particle *p, int np) {
     s->pair_xi = calloc(n2, sizeof(*s->pair_xi));
     s->pair_xm = calloc(n2, sizeof(*s->pair_xm));
     s->wall_on = calloc(n1 * ORC_NWALL, sizeof(int));
+    s->wall_warm = calloc(n1 * ORC_NWALL, sizeof(int));
+    s->pair_warm = calloc(n2, sizeof(int));
     s->wall_xi = calloc(n1 * ORC_NWALL, sizeof(*s->wall_xi));
     s->wall_xcw = calloc(n1 * ORC_NWALL, sizeof(*s->wall_xcw));
     for (int j = 0; j < np; j++) {
