@@ -144,31 +144,43 @@ __device__ __forceinline__ void rel_vec(const SH &S, const Params &P, int i, int
 }
 
 // M, grad M and Hessian (xx yy zz xy xz yz) of one metaball at y, control
-// points at rc + off (weights in rc[].w)
-__device__ void mb_dd_f(const float4 *rc, int ncp, const float off[3], const float y[3], float &M, float g[3],
-                        float H[6]) {
-    M = 0.f;
-    for (int a = 0; a < 3; a++) g[a] = 0.f;
-    for (int a = 0; a < 6; a++) H[a] = 0.f;
-    for (int c = 0; c < ncp; c++) {
-        const float4 cp = rc[c];
-        const float r0 = y[0] - (cp.x + off[0]), r1 = y[1] - (cp.y + off[1]), r2_ = y[2] - (cp.z + off[2]);
-        const float r2 = r0 * r0 + r1 * r1 + r2_ * r2_;
-        const float ir = __frcp_rn(r2);
-        const float Kr = cp.w * ir;            // K / r^2
-        const float a1 = -2.0f * Kr * ir;      // -2 K / r^4
-        const float a2 = 8.0f * Kr * ir * ir;  // 8 K / r^6
-        M += Kr;
-        g[0] = fmaf(a1, r0, g[0]);
-        g[1] = fmaf(a1, r1, g[1]);
-        g[2] = fmaf(a1, r2_, g[2]);
-        H[0] += fmaf(a2 * r0, r0, a1);
-        H[1] += fmaf(a2 * r1, r1, a1);
-        H[2] += fmaf(a2 * r2_, r2_, a1);
-        H[3] = fmaf(a2 * r0, r1, H[3]);
-        H[4] = fmaf(a2 * r0, r2_, H[4]);
-        H[5] = fmaf(a2 * r1, r2_, H[5]);
+// points at rc + off (weights in rc[].w), Eq. (4).  Two interleaved partial
+// sums, so that consecutive control points do not wait on each other, and
+// the approximate FP32 reciprocal (the contact geometry is FP32 throughout).
+struct MbSum {
+    float M, g0, g1, g2, h0, h1, h2, h3, h4, h5;
+};
+__device__ __forceinline__ void mb_acc(const float4 cp, const float off[3], const float y[3], MbSum &A) {
+    const float r0 = y[0] - (cp.x + off[0]), r1 = y[1] - (cp.y + off[1]), r2_ = y[2] - (cp.z + off[2]);
+    const float r2 = r0 * r0 + r1 * r1 + r2_ * r2_;
+    const float ir = __fdividef(1.0f, r2);
+    const float Kr = cp.w * ir;            // K / r^2
+    const float a1 = -2.0f * Kr * ir;      // -2 K / r^4
+    const float a2 = 8.0f * Kr * ir * ir;  // 8 K / r^6
+    A.M += Kr;
+    A.g0 = fmaf(a1, r0, A.g0);
+    A.g1 = fmaf(a1, r1, A.g1);
+    A.g2 = fmaf(a1, r2_, A.g2);
+    A.h0 += fmaf(a2 * r0, r0, a1);
+    A.h1 += fmaf(a2 * r1, r1, a1);
+    A.h2 += fmaf(a2 * r2_, r2_, a1);
+    A.h3 = fmaf(a2 * r0, r1, A.h3);
+    A.h4 = fmaf(a2 * r0, r2_, A.h4);
+    A.h5 = fmaf(a2 * r1, r2_, A.h5);
+}
+__device__ __forceinline__ void mb_dd_f(const float4 *rc, int ncp, const float off[3], const float y[3], float &M,
+                                        float g[3], float H[6]) {
+    MbSum A = {}, B = {};
+    int c = 0;
+    for (; c + 1 < ncp; c += 2) {
+        mb_acc(rc[c], off, y, A);
+        mb_acc(rc[c + 1], off, y, B);
     }
+    if (c < ncp) mb_acc(rc[c], off, y, A);
+    M = A.M + B.M;
+    g[0] = A.g0 + B.g0; g[1] = A.g1 + B.g1; g[2] = A.g2 + B.g2;
+    H[0] = A.h0 + B.h0; H[1] = A.h1 + B.h1; H[2] = A.h2 + B.h2;
+    H[3] = A.h3 + B.h3; H[4] = A.h4 + B.h4; H[5] = A.h5 + B.h5;
 }
 
 // Contact law of §2.1.1 (Eqs. (2)-(3)) in FP32; xi: tangential spring.
@@ -205,7 +217,7 @@ constexpr float kNewtonTol2 = 1e-10f;
 // point in the middle of the overlap.
 template <class SH>
 __device__ bool pair_geom_f(const Params &P, const SH &S, int i, int j, const float d[3], bool warm, float xm[3],
-                            float &delta, float nv[3], float xcp[3]) {
+                            float &delta, float nv[3], float xcp[3], bool &valid) {
     const float4 *rci = S.rc + S.cpo[i];
     const float4 *rcj = S.rc + S.cpo[j];
     const int nci = S.cpo[i + 1] - S.cpo[i], ncj = S.cpo[j + 1] - S.cpo[j];
@@ -229,11 +241,18 @@ __device__ bool pair_geom_f(const Params &P, const SH &S, int i, int j, const fl
                 }
             }
     }
-    float M0, g0[3], H0[6], M1, g1[3], H1[6];
+    // M, grad M at the last iterate evaluated (xe): once the step is below
+    // the tolerance the point moves by less than 1e-5 lu, and the closest
+    // points of Eqs. (8)-(9) are taken there without another evaluation
+    float M0, g0[3], H0[6], M1, g1[3], H1[6], xe[3];
     float prev = 3.4e38f;
-    for (int it = 0; it < kNewtonMax; it++) {
+    bool converged = false;
+    valid = false;
+    for (int it = 0;; it++) {
         mb_dd_f(rci, nci, zero, x, M0, g0, H0);
         mb_dd_f(rcj, ncj, d, x, M1, g1, H1);
+        for (int a = 0; a < 3; a++) xe[a] = x[a];
+        if (it == kNewtonMax) break;
         float H[6], g[3];
         for (int a = 0; a < 6; a++) H[a] = H0[a] + H1[a];
         for (int a = 0; a < 3; a++) g[a] = -(g0[a] + g1[a]);
@@ -252,13 +271,13 @@ __device__ bool pair_geom_f(const Params &P, const SH &S, int i, int j, const fl
         dx[2] = (c2 * g[0] + b12 * g[1] + b22 * g[2]) * id;
         for (int a = 0; a < 3; a++) x[a] += dx[a];
         const float s2 = dot3f(dx, dx);
-        if (s2 < kNewtonTol2 || (it >= 3 && s2 >= prev)) break;
+        if (s2 < kNewtonTol2) { converged = true; break; }
+        if (it >= 3 && s2 >= prev) break;
         prev = s2;
     }
     for (int a = 0; a < 3; a++) xm[a] = x[a];
-    mb_dd_f(rci, nci, zero, x, M0, g0, H0);
-    mb_dd_f(rcj, ncj, d, x, M1, g1, H1);
     if (!(M0 > P.c_tol_f && M0 < 1.0f && M1 > P.c_tol_f && M1 < 1.0f)) return false;
+    valid = converged;
     const float q0 = (1.0f - M0) * __frcp_rn(dot3f(g0, g0)), q1 = (1.0f - M1) * __frcp_rn(dot3f(g1, g1));
     float dc[3];
     for (int a = 0; a < 3; a++) dc[a] = q0 * g0[a] - q1 * g1[a];
@@ -268,7 +287,7 @@ __device__ bool pair_geom_f(const Params &P, const SH &S, int i, int j, const fl
     const float idist = __frcp_rn(dist);
     for (int a = 0; a < 3; a++) {
         nv[a] = dc[a] * idist;
-        xcp[a] = (x[a] + q0 * g0[a]) - (S.Rs[i] - 0.5f * delta) * nv[a];
+        xcp[a] = (xe[a] + q0 * g0[a]) - (S.Rs[i] - 0.5f * delta) * nv[a];
     }
     return true;
 }
@@ -277,7 +296,7 @@ __device__ bool pair_geom_f(const Params &P, const SH &S, int i, int j, const fl
 // wall plane's coordinate relative to x along its axis.
 template <class SH>
 __device__ bool wall_geom_f(const Params &P, const SH &S, int k, int wall, float prel, bool warm, float xcw[3],
-                            float &delta, float nv[3], float xcp[3]) {
+                            float &delta, float nv[3], float xcp[3], bool &valid) {
     const int ax = wall / 2, side = wall % 2;
     const float m_ax = side ? 1.0f : -1.0f;
     const int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
@@ -301,10 +320,14 @@ __device__ bool wall_geom_f(const Params &P, const SH &S, int k, int wall, float
     // H index of (a, b)
     auto hidx = [](int a, int b) { return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5)); };
     const int i11 = hidx(t1, t1), i12 = hidx(t1, t2), i22 = hidx(t2, t2);
-    float M, g[3], H[6];
+    float M, g[3], H[6], xe[3];  // the last evaluation, at xe (as for pairs)
     float prev = 3.4e38f;
-    for (int it = 0; it < kNewtonMax; it++) {
+    bool converged = false;
+    valid = false;
+    for (int it = 0;; it++) {
         mb_dd_f(rc, nc, zero, x, M, g, H);
+        for (int a = 0; a < 3; a++) xe[a] = x[a];
+        if (it == kNewtonMax) break;
         const float J00 = H[i11], J01 = H[i12], J11 = H[i22];
         const float det = J00 * J11 - J01 * J01;
         if (det == 0.f || !isfinite(det)) break;
@@ -314,12 +337,13 @@ __device__ bool wall_geom_f(const Params &P, const SH &S, int k, int wall, float
         x[t1] += d0;
         x[t2] += d1;
         const float s2 = d0 * d0 + d1 * d1;
-        if (s2 < kNewtonTol2 || (it >= 3 && s2 >= prev)) break;
+        if (s2 < kNewtonTol2) { converged = true; break; }
+        if (it >= 3 && s2 >= prev) break;
         prev = s2;
     }
     for (int a = 0; a < 3; a++) xcw[a] = x[a];
-    mb_dd_f(rc, nc, zero, x, M, g, H);
     if (!(g[ax] * m_ax < 0.f)) return false;
+    valid = converged;
     const float qR = (1.0f - M) * __frcp_rn(dot3f(g, g));
     float dc[3];
     for (int a = 0; a < 3; a++) dc[a] = qR * g[a];
@@ -329,7 +353,7 @@ __device__ bool wall_geom_f(const Params &P, const SH &S, int k, int wall, float
     const float idist = __frcp_rn(dist);
     for (int a = 0; a < 3; a++) {
         nv[a] = dc[a] * idist;
-        xcp[a] = x[a] - 0.5f * delta * nv[a];
+        xcp[a] = xe[a] - 0.5f * delta * nv[a];
     }
     return true;
 }
@@ -373,14 +397,15 @@ __device__ void build_lists(const Params &P, SH &S, int *possible) {
             const float brs = bri + S.brad[j];
             const float lim = brs + kSkin;
             const int pidx = S.gid[i] * P.np + S.gid[j];
-            const bool on = P.pair_on[pidx] != 0;
+            const int fl = P.pair_on[pidx];
+            const bool on = (fl & CONTACT_ON) != 0;
             if (d2 < lim * lim) {
                 m |= 1u << b;
                 const float lr = brs + ri + S.reach[j] + 1e-2f;
                 if (on || d2 <= lr * lr) *possible = 1;
-            } else if (on) {
+            } else if (fl) {
                 P.pair_on[pidx] = 0;
-                *possible = 1;
+                if (on) *possible = 1;
             }
         }
         S.bits[i][wd] = m;
@@ -461,15 +486,18 @@ __device__ void pair_contacts(const Params &P, SH &S, float h) {
         if (dot3f(d, d) > brs * brs) {
             S.it_on[it] = 0;
         } else {
-            const bool warm = S.it_on[it] != 0;
+            const int was = S.it_on[it];
             float xm[3] = {S.it_xm[it][0], S.it_xm[it][1], S.it_xm[it][2]}, delta, nv[3], xcp[3];
-            if (!pair_geom_f(P, S, i, j, d, warm, xm, delta, nv, xcp)) {
-                S.it_on[it] = 0;
+            bool valid;
+            const bool hit = pair_geom_f(P, S, i, j, d, (was & CONTACT_WARM) != 0, xm, delta, nv, xcp, valid);
+            for (int a = 0; a < 3; a++) S.it_xm[it][a] = xm[a];
+            const int warm = valid ? CONTACT_WARM : 0;
+            if (!hit) {
+                S.it_on[it] = warm;
             } else {
                 float xi[3];
-                for (int a = 0; a < 3; a++) xi[a] = warm ? S.it_xi[it][a] : 0.f;
-                S.it_on[it] = 1;
-                for (int a = 0; a < 3; a++) S.it_xm[it][a] = xm[a];
+                for (int a = 0; a < 3; a++) xi[a] = (was & CONTACT_ON) ? S.it_xi[it][a] : 0.f;
+                S.it_on[it] = warm | CONTACT_ON;
                 float rj[3], wri[3], wrj[3], vij[3];
                 for (int a = 0; a < 3; a++) rj[a] = xcp[a] - d[a];
                 cross3f(S.w[i], xcp, wri);
@@ -507,13 +535,16 @@ __device__ void gather_contacts(const Params &P, SH &S, int k, float h, float F[
         const float plane = side ? P.dim_f[ax] - 0.5f : -0.5f;
         const float prel = (plane - S.xh[k][ax]) - S.xl[k][ax];
         if (fabsf(prel) > S.brad[k]) { S.w_on[k][wall] = 0; continue; }
-        const bool warm = S.w_on[k][wall] != 0;
+        const int was = S.w_on[k][wall];
         float xcw[3] = {S.w_xcw[k][wall][0], S.w_xcw[k][wall][1], S.w_xcw[k][wall][2]}, delta, nv[3], xcp[3];
-        if (!wall_geom_f(P, S, k, wall, prel, warm, xcw, delta, nv, xcp)) { S.w_on[k][wall] = 0; continue; }
-        float xi[3];
-        for (int a = 0; a < 3; a++) xi[a] = warm ? S.w_xi[k][wall][a] : 0.f;
-        S.w_on[k][wall] = 1;
+        bool valid;
+        const bool hit = wall_geom_f(P, S, k, wall, prel, (was & CONTACT_WARM) != 0, xcw, delta, nv, xcp, valid);
         for (int a = 0; a < 3; a++) S.w_xcw[k][wall][a] = xcw[a];
+        const int warm = valid ? CONTACT_WARM : 0;
+        if (!hit) { S.w_on[k][wall] = warm; continue; }
+        float xi[3];
+        for (int a = 0; a < 3; a++) xi[a] = (was & CONTACT_ON) ? S.w_xi[k][wall][a] : 0.f;
+        S.w_on[k][wall] = warm | CONTACT_ON;
         float wr[3], vi[3], Fi[3], ti[3];
         cross3f(S.w[k], xcp, wr);
         for (int a = 0; a < 3; a++) vi[a] = S.v[k][a] + wr[a];
@@ -602,7 +633,7 @@ __global__ void __launch_bounds__(kThreads) k_dem32(Params P) {
                 S.w_xcw[tid][wall][a] = P.wall_xcw_f[3 * wj + a];
                 S.w_xi[tid][wall][a] = P.wall_xi_f[3 * wj + a];
             }
-            if (P.wall_on[wj]) possible = 1;
+            if (P.wall_on[wj] & CONTACT_ON) possible = 1;
             if (P.per[ax]) continue;
             const float plane = side ? P.dim_f[ax] - 0.5f : -0.5f;
             const float prel = (plane - x[ax].hi) - x[ax].lo;
@@ -866,7 +897,7 @@ __device__ __forceinline__ void dl_add(Delta &a, float b) { a.d = df_add(a.d, b)
 // with tables sized for them (kLarge = false, 32 threads), larger ones with
 // the full tables (kLarge, 512 threads).
 template <class SH, bool kLarge>
-__global__ void __launch_bounds__(kLarge ? kThreads : kSmallContactGroup) k_dem64c(Params P) {
+__global__ void __launch_bounds__(kLarge ? kThreads : kSmallContactGroup, 1) k_dem64c(Params P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SH &S = *reinterpret_cast<SH *>(smem_raw);
     const int tid = threadIdx.x;

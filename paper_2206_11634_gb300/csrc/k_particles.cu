@@ -259,11 +259,12 @@ __device__ void point_vel(const Params &P, const DevParticle &p, const double x[
 }
 
 // Pair geometry, Eqs. (5)-(9): Newton on grad(M_i + M_j) = 0 from the warm
-// start or the midpoint of the closest control-point pair; valid when
+// start or the midpoint of the closest control-point pair; a contact needs
 // c_tol < M < 1 for both; closest points by the first-order Taylor step of
-// Eqs. (7)-(8); contact point in the middle of the overlap.
+// Eqs. (7)-(8); contact point in the middle of the overlap.  `valid`: Newton
+// converged to a point within those bounds (the next solve may start there).
 __device__ bool pair_geometry(const Params &P, const DevParticle &pi, const DevParticle &pj, bool warm,
-                              double xm[3], double &delta, double nv[3], double xcp[3]) {
+                              double xm[3], double &delta, double nv[3], double xcp[3], bool &valid) {
     double x[3];
     if (warm) {
         for (int a = 0; a < 3; a++) x[a] = xm[a];
@@ -280,6 +281,8 @@ __device__ bool pair_geometry(const Params &P, const DevParticle &pi, const DevP
                 }
             }
     }
+    bool converged = false;
+    valid = false;
     for (int it = 0; it < 50; it++) {
         double M0, g0[3], H0[9], M1, g1[3], H1[9];
         mb_dd(P, pi, x, M0, g0, H0);
@@ -289,13 +292,14 @@ __device__ bool pair_geometry(const Params &P, const DevParticle &pi, const DevP
         for (int a = 0; a < 9; a++) H[a] = H0[a] + H1[a];
         if (!solve_sym3(H, g, dx)) break;
         for (int a = 0; a < 3; a++) x[a] += dx[a];
-        if (sqrt(dot3(dx, dx)) < 1e-12) break;
+        if (sqrt(dot3(dx, dx)) < 1e-12) { converged = true; break; }
     }
     for (int a = 0; a < 3; a++) xm[a] = x[a];
     double M0, g0[3], H0[9], M1, g1[3], H1[9];
     mb_dd(P, pi, x, M0, g0, H0);
     mb_dd(P, pj, x, M1, g1, H1);
     if (!(M0 > P.c_tol && M0 < 1.0 && M1 > P.c_tol && M1 < 1.0)) return false;
+    valid = converged;
     const double q0 = (1.0 - M0) / dot3(g0, g0), q1 = (1.0 - M1) / dot3(g1, g1);
     double xc0[3], dc[3];
     for (int a = 0; a < 3; a++) {
@@ -315,8 +319,9 @@ __device__ bool pair_geometry(const Params &P, const DevParticle &pi, const DevP
 // Wall geometry, Eqs. (10)-(13): Newton on the two tangential components of
 // grad M on the wall plane, dM/dm < 0 along the outward normal m; start from
 // the warm start or the projection of the control point nearest the plane.
+// `valid`: Newton converged and dM/dm < 0 there.
 __device__ bool wall_geometry(const Params &P, const DevParticle &p, int wall, bool warm, double xcw[3],
-                              double &delta, double nv[3], double xcp[3]) {
+                              double &delta, double nv[3], double xcp[3], bool &valid) {
     const int ax = wall / 2, side = wall % 2;
     const double plane = side ? dim_of(P, ax) - 0.5 : -0.5;
     const double m_ax = side ? 1.0 : -1.0;
@@ -334,6 +339,8 @@ __device__ bool wall_geometry(const Params &P, const DevParticle &p, int wall, b
         for (int a = 0; a < 3; a++) x[a] = p.cpw[kb][a];
     }
     x[ax] = plane;
+    bool converged = false;
+    valid = false;
     for (int it = 0; it < 50; it++) {
         double M, g[3], H[9];
         mb_dd(P, p, x, M, g, H);
@@ -344,12 +351,13 @@ __device__ bool wall_geometry(const Params &P, const DevParticle &p, int wall, b
         const double d0 = (J11 * r0 - J01 * r1) / det, d1 = (-J10 * r0 + J00 * r1) / det;
         x[t1] += d0;
         x[t2] += d1;
-        if (sqrt(d0 * d0 + d1 * d1) < 1e-12) break;
+        if (sqrt(d0 * d0 + d1 * d1) < 1e-12) { converged = true; break; }
     }
     for (int a = 0; a < 3; a++) xcw[a] = x[a];
     double M, g[3], H[9];
     mb_dd(P, p, x, M, g, H);
     if (!(g[ax] * m_ax < 0.0)) return false;
+    valid = converged;
     const double qR = (1.0 - M) / dot3(g, g);
     double dc[3];
     for (int a = 0; a < 3; a++) dc[a] = qR * g[a];
@@ -383,16 +391,19 @@ __device__ void contacts(const Params &P, double h) {
             continue;
         }
         double xm[3], delta, nv[3], xcp[3];
-        const bool warm = P.pair_on[idx] != 0;
+        const int was = P.pair_on[idx];
+        bool valid;
         for (int a = 0; a < 3; a++) xm[a] = P.pair_xm[3 * idx + a];
-        if (!pair_geometry(P, pi, pj, warm, xm, delta, nv, xcp)) {
-            P.pair_on[idx] = 0;
+        const bool hit = pair_geometry(P, pi, pj, (was & CONTACT_WARM) != 0, xm, delta, nv, xcp, valid);
+        for (int a = 0; a < 3; a++) P.pair_xm[3 * idx + a] = xm[a];
+        const int warm = valid ? CONTACT_WARM : 0;
+        if (!hit) {
+            P.pair_on[idx] = warm;
             continue;
         }
         double xi[3];
-        for (int a = 0; a < 3; a++) xi[a] = warm ? P.pair_xi[3 * idx + a] : 0.0;
-        P.pair_on[idx] = 1;
-        for (int a = 0; a < 3; a++) P.pair_xm[3 * idx + a] = xm[a];
+        for (int a = 0; a < 3; a++) xi[a] = (was & CONTACT_ON) ? P.pair_xi[3 * idx + a] : 0.0;
+        P.pair_on[idx] = warm | CONTACT_ON;
         double vi[3], vj[3], Fi[3];
         point_vel(P, pi, xcp, vi);
         point_vel(P, pj, xcp, vj);
@@ -428,13 +439,16 @@ __device__ void contacts(const Params &P, double h) {
             const double plane = side ? dim_of(P, ax) - 0.5 : -0.5;
             if (fabs(plane - p.x[ax]) > p.brad) { P.wall_on[wj] = 0; continue; }
             double xcw[3], delta, nv[3], xcp[3];
-            const bool warm = P.wall_on[wj] != 0;
+            const int was = P.wall_on[wj];
+            bool valid;
             for (int a = 0; a < 3; a++) xcw[a] = P.wall_xcw[3 * wj + a];
-            if (!wall_geometry(P, p, wall, warm, xcw, delta, nv, xcp)) { P.wall_on[wj] = 0; continue; }
-            double xi[3];
-            for (int a = 0; a < 3; a++) xi[a] = warm ? P.wall_xi[3 * wj + a] : 0.0;
-            P.wall_on[wj] = 1;
+            const bool hit = wall_geometry(P, p, wall, (was & CONTACT_WARM) != 0, xcw, delta, nv, xcp, valid);
             for (int a = 0; a < 3; a++) P.wall_xcw[3 * wj + a] = xcw[a];
+            const int warm = valid ? CONTACT_WARM : 0;
+            if (!hit) { P.wall_on[wj] = warm; continue; }
+            double xi[3];
+            for (int a = 0; a < 3; a++) xi[a] = (was & CONTACT_ON) ? P.wall_xi[3 * wj + a] : 0.0;
+            P.wall_on[wj] = warm | CONTACT_ON;
             double vi[3], vw[3] = {0, 0, 0}, Fi[3], ri[3], ti[3];
             point_vel(P, p, xcp, vi);
             contact_law(P, delta, nv, vi, vw, xi, h, Fi);
@@ -512,7 +526,7 @@ __device__ bool contact_possible(const Params &P) {
         reach[k] = Df;
         br[k] = (float)p.brad;
         for (int wall = 0; wall < NWALL; wall++) {
-            if (P.wall_on[k * NWALL + wall]) possible = 1;
+            if (P.wall_on[k * NWALL + wall] & CONTACT_ON) possible = 1;
             const int ax = wall / 2, side = wall % 2;
             if (P.per[ax]) continue;
             const float plane = side ? (float)dim_of(P, ax) - 0.5f : -0.5f;
@@ -520,26 +534,23 @@ __device__ bool contact_possible(const Params &P) {
         }
     }
     __syncthreads();
-    const long long npairs = (long long)np * (np - 1) / 2;
-    for (long long idx = threadIdx.x; idx < npairs && !possible; idx += blockDim.x) {
-        // pair index -> (i, j), i < j
-        int i = (int)((2.0 * np - 1.0 - sqrt((2.0 * np - 1.0) * (2.0 * np - 1.0) - 8.0 * (double)idx)) * 0.5);
-        while ((long long)i * (2 * np - i - 1) / 2 > idx) i--;
-        while ((long long)(i + 1) * (2 * np - i - 2) / 2 <= idx) i++;
-        const int j = (int)(idx - (long long)i * (2 * np - i - 1) / 2) + i + 1;
-        if (P.pair_on[i * np + j]) { possible = 1; break; }
-        float d2 = 0.f;
-        for (int a = 0; a < 3; a++) {
-            float d = xs[j][a] - xs[i][a];
-            if (P.per[a]) {
-                const float L = (float)dim_of(P, a);
-                d -= L * rintf(d / L);
+    // warp w takes rows w, w + nwarp, ..., its lanes the columns j > i
+    const int lane = threadIdx.x & 31, nwarp = (blockDim.x + 31) >> 5;
+    for (int i = threadIdx.x >> 5; i < np && !possible; i += nwarp)
+        for (int j = i + 1 + lane; j < np; j += 32) {
+            if (P.pair_on[i * np + j] & CONTACT_ON) { possible = 1; break; }
+            float d2 = 0.f;
+            for (int a = 0; a < 3; a++) {
+                float d = xs[j][a] - xs[i][a];
+                if (P.per[a]) {
+                    const float L = (float)dim_of(P, a);
+                    d -= L * rintf(d / L);
+                }
+                d2 += d * d;
             }
-            d2 += d * d;
+            const float lim = br[i] + br[j] + reach[i] + reach[j] + 1e-2f;
+            if (d2 <= lim * lim) { possible = 1; break; }
         }
-        const float lim = br[i] + br[j] + reach[i] + reach[j] + 1e-2f;
-        if (d2 <= lim * lim) possible = 1;
-    }
     if (possible) atomicOr(&s_possible, 1);
     __syncthreads();
     return s_possible != 0;
@@ -720,14 +731,18 @@ __device__ void rotate_free_quad(unsigned mk, const DevParticle &p, const double
 // reach_i + reach_j, dem_reach).  Active particles that can reach each other
 // form a contact group (connected components of that relation); groups are
 // independent during the step, so each gets its own CTA.  Every list keeps
-// index order (dem_free() and below).  A pair in contact at the end of the
-// last step overlaps, so it is active again: the contact history of inactive
-// particles is empty.
+// index order (dem_free() and below).  A pair or wall with contact history
+// at the end of the last step (in contact, or a warm Newton start) had its
+// bounding spheres overlapping, or the wall within the bounding sphere, so
+// it is active again: the contact history of inactive particles is empty.
 constexpr int kPlanEdges = 4096;
+static_assert(kDem32MaxParticles <= kFastMaxParticles, "one plan thread per particle");
 __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
+    // one thread per particle below (np <= kFastMaxParticles = blockDim.x)
     __shared__ float xs[kFastMaxParticles][3], reach[kFastMaxParticles], br[kFastMaxParticles];
     __shared__ int act[kFastMaxParticles], parent[kFastMaxParticles], gsz[kFastMaxParticles];
-    __shared__ int gfill[kFastMaxParticles];
+    __shared__ int root[kFastMaxParticles];
+    __shared__ unsigned long long wsum[kFastMaxParticles / 32];
     __shared__ unsigned edge[kPlanEdges];
     __shared__ int nedge;
     const int np = P.np;
@@ -738,8 +753,8 @@ __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
         if (c < 3) P.Fh[3 * k + c] = v;
         else P.Th[3 * k + c - 3] = v;
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+    const int k = threadIdx.x;
+    if (k < np) {
         const DevParticle &p = P.parts[k];
         const float r = dem_reach(P, p, k);
         for (int a = 0; a < 3; a++) xs[k][a] = (float)p.x[a];
@@ -754,36 +769,39 @@ __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
         }
         act[k] = on;
         parent[k] = k;
+        gsz[k] = 0;
     }
     __syncthreads();
-    const long long npairs = (long long)np * (np - 1) / 2;
-    for (long long idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
-        int i = (int)((2.0 * np - 1.0 - sqrt((2.0 * np - 1.0) * (2.0 * np - 1.0) - 8.0 * (double)idx)) * 0.5);
-        while ((long long)i * (2 * np - i - 1) / 2 > idx) i--;
-        while ((long long)(i + 1) * (2 * np - i - 2) / 2 <= idx) i++;
-        const int j = (int)(idx - (long long)i * (2 * np - i - 1) / 2) + i + 1;
-        float d2 = 0.f;
-        for (int a = 0; a < 3; a++) {
-            float d = xs[j][a] - xs[i][a];
-            if (P.per[a]) {
-                const float L = (float)dim_of(P, a);
-                d -= L * rintf(d / L);
+    // candidate pairs: warp w takes rows w, w + 8, ..., its lanes the
+    // columns j > i (consecutive j: conflict-free shared loads)
+    float L[3], invL[3];
+    for (int a = 0; a < 3; a++) {
+        L[a] = P.per[a] ? (float)dim_of(P, a) : 0.f;
+        invL[a] = P.per[a] ? 1.f / L[a] : 0.f;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int i = warp; i < np; i += nwarp) {
+        const float xi0 = xs[i][0], xi1 = xs[i][1], xi2 = xs[i][2], ri = br[i] + reach[i] + 1e-2f;
+        for (int j = i + 1 + lane; j < np; j += 32) {
+            float d0 = xs[j][0] - xi0, d1 = xs[j][1] - xi1, d2 = xs[j][2] - xi2;
+            d0 -= L[0] * rintf(d0 * invL[0]);
+            d1 -= L[1] * rintf(d1 * invL[1]);
+            d2 -= L[2] * rintf(d2 * invL[2]);
+            const float lim = ri + br[j] + reach[j];
+            if (d0 * d0 + d1 * d1 + d2 * d2 <= lim * lim) {
+                act[i] = 1;
+                act[j] = 1;
+                const int e = atomicAdd(&nedge, 1);
+                if (e < kPlanEdges) edge[e] = ((unsigned)i << 16) | (unsigned)j;
             }
-            d2 += d * d;
-        }
-        const float lim = br[i] + br[j] + reach[i] + reach[j] + 1e-2f;
-        if (d2 <= lim * lim) {
-            act[i] = 1;
-            act[j] = 1;
-            const int e = atomicAdd(&nedge, 1);
-            if (e < kPlanEdges) edge[e] = ((unsigned)i << 16) | (unsigned)j;
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         // connected components of the edges (union by the smaller root, so a
-        // root is its group's smallest index); beyond the edge table, every
-        // active particle is one group
+        // root is its group's smallest index: the partition and its roots do
+        // not depend on the order of the edges); beyond the edge table,
+        // every active particle is one group
         auto find = [&](int a) {
             while (parent[a] != a) {
                 parent[a] = parent[parent[a]];
@@ -794,10 +812,10 @@ __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
         const int ne = nedge;
         if (ne > kPlanEdges) {
             int r = -1;
-            for (int k = 0; k < np; k++)
-                if (act[k]) {
-                    if (r < 0) r = k;
-                    parent[k] = r;
+            for (int m = 0; m < np; m++)
+                if (act[m]) {
+                    if (r < 0) r = m;
+                    parent[m] = r;
                 }
         } else {
             for (int e = 0; e < ne; e++) {
@@ -808,29 +826,58 @@ __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
                 }
             }
         }
-        int nf = 0;
-        for (int k = 0; k < np; k++) {
-            gsz[k] = 0;
-            if (!act[k]) dem_free(P)[nf++] = k;
-        }
-        for (int k = 0; k < np; k++)
-            if (act[k]) gsz[find(k)]++;
-        int o = 0, ns = 0, nl = 0;
-        for (int k = 0; k < np; k++) {  // groups in the order of their smallest member
-            if (!act[k] || find(k) != k) continue;
-            gfill[k] = o;
-            int *g = dem_groups(P, gsz[k] > kSmallContactGroup);
-            const int slot = gsz[k] > kSmallContactGroup ? nl++ : ns++;
-            g[2 * slot] = o;
-            g[2 * slot + 1] = gsz[k];
-            o += gsz[k];
-        }
-        for (int k = 0; k < np; k++)
-            if (act[k]) dem_active(P)[gfill[find(k)]++] = k;
-        P.dem_list[0] = nf;
-        P.dem_list[1] = o;
-        P.dem_list[2] = ns;
-        P.dem_list[3] = nl;
+    }
+    __syncthreads();
+    const bool on = k < np && act[k];
+    int rk = -1;
+    if (on) {
+        rk = k;
+        while (parent[rk] != rk) rk = parent[rk];
+        root[k] = rk;
+        atomicAdd(&gsz[rk], 1);
+    }
+    __syncthreads();
+    // exclusive block scan of four 16-bit counters: free particles, group
+    // members, small groups, large groups (groups in the order of their
+    // smallest member, the free list and each group in ascending index)
+    const int g = on && rk == k ? gsz[k] : 0;
+    const bool large = g > kSmallContactGroup;
+    const unsigned long long mine = (unsigned long long)(k < np && !on) |
+                                    (unsigned long long)g << 16 |
+                                    (unsigned long long)(g > 0 && !large) << 32 |
+                                    (unsigned long long)(large) << 48;
+    unsigned long long inc = mine;
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += t;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    unsigned long long ex = inc - mine, tot = 0;
+    for (int w = 0; w < nwarp; w++) {
+        if (w < warp) ex += wsum[w];
+        tot += wsum[w];
+    }
+    const int exf = (int)(ex & 0xFFFF), exg = (int)(ex >> 16 & 0xFFFF);
+    if (k < np && !on) dem_free(P)[exf] = k;
+    if (g > 0) {
+        const int slot = large ? (int)(ex >> 48 & 0xFFFF) : (int)(ex >> 32 & 0xFFFF);
+        int *gl = dem_groups(P, large);
+        gl[2 * slot] = exg;
+        gl[2 * slot + 1] = g;
+        gsz[k] = exg;   // the group's first slot in the active list
+    }
+    __syncthreads();
+    if (on) {
+        int rank = 0;
+        for (int m = rk; m < k; m++) rank += act[m] && root[m] == rk;
+        dem_active(P)[gsz[rk] + rank] = k;
+    }
+    if (threadIdx.x == 0) {
+        P.dem_list[0] = (int)(tot & 0xFFFF);
+        P.dem_list[1] = (int)(tot >> 16 & 0xFFFF);
+        P.dem_list[2] = (int)(tot >> 32 & 0xFFFF);
+        P.dem_list[3] = (int)(tot >> 48 & 0xFFFF);
     }
 }
 

@@ -34,6 +34,12 @@ enum StatusSlot { ST_ERR = 0, ST_SLOTS = 16 };
 enum StepCounter { CNT_NREFILL = 0, CNT_NLINKS = 1, CNT_LISTED = 2, CNT_NEAR = 3 };
 enum ErrBits { ERRB_BRICK_OVERFLOW = 1, ERRB_DIVERGED = 2, ERRB_TIMEOUT = 4, ERRB_DEM_CAPACITY = 8,
                ERRB_STATIC_CAPACITY = 16, ERRB_DEM_REACH = 32 };
+// contact history flags (Params::pair_on per pair, wall_on per particle and
+// wall): in contact at the last evaluation (the tangential spring carries
+// over), and warm: the last evaluation of this potential collision (bounding
+// spheres overlapping, or the plane within the bounding sphere) found a valid
+// Newton solution, x_m or x_cw, which starts the next solve (§2.1.4)
+enum ContactFlags { CONTACT_ON = 1, CONTACT_WARM = 2 };
 // DEM kernels (lbm_config.dem_mode): the FP64 rigid-body integrator with the
 // contact geometry in FP32 (k_dem64_plan + k_dem64_free + k_dem64c, lattices
 // below FP64), the compensated-FP32 integrator (k_dem32), and everything in
