@@ -27,9 +27,10 @@ __global__ void __launch_bounds__(BRICK, kNearCtasPerSm) k_sweep_near_batch(Batc
     __shared__ double red[BRICK / 32][6];
     __shared__ int s_links;
     __shared__ LinkScratch ls;
-    const int c = blockIdx.x / B.g_chain, lb = blockIdx.x % B.g_chain;
+    __shared__ int s_next[2];
+    const int c = blockIdx.x / B.g_chain;
     load_case_params(B, c, B.ctr, sP);
-    near_work<S, Q, kForce>(sP, sp, red, s_links, ls, lb, B.g_chain);
+    near_work<S, Q, kForce>(sP, sp, red, s_links, ls, s_next);
     advance_step_when_last(B.ctr + 2, B.ctr);
 }
 

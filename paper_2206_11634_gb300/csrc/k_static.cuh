@@ -228,7 +228,7 @@ __device__ __noinline__ float static_link(const Params &P, StaticScratch &ss, in
         }
     }
     C u_f[3];
-    const C inv_rho_f = C(1) / (rho0 + drho_f);
+    const C inv_rho_f = rcp_w<C>(rho0 + drho_f);  // as the near sweep's link_coop
     for (int a = 0; a < 3; a++) u_f[a] = (m_f[a] - C(0.5) * Prm<C>::F(P, a)) * inv_rho_f;
     LinkGeom<C> g;
     g.q = (C)rec.q;

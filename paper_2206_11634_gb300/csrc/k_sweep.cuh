@@ -80,6 +80,38 @@ __device__ __forceinline__ C m_value(const Params &P, const SmemParticles &sp, i
 
 template <typename C> __device__ __forceinline__ C c0_of(const Params &P) { return sizeof(C) == 4 ? (C)P.c0_f : (C)P.c0; }
 
+// 1 / x in the working precision: the approximate FP32 reciprocal (a link's
+// arithmetic is FP32 throughout below FP64), the IEEE quotient in FP64.
+template <typename C> __device__ __forceinline__ C rcp_w(C x) {
+    if (sizeof(C) == 4) return (C)__fdividef(1.0f, (float)x);
+    return C(1) / x;
+}
+
+// FP32 M of listed particle s at the brick-local fluid node (lx,ly,lz) and at
+// the solid node one link d further, in one pass over the control points
+// (minimum image taken at the fluid node; a particle spans far less than half
+// the box), for the link fraction of Eq. (27), which needs no exact M.
+__device__ __forceinline__ void m_link_f(const Params &P, const SmemParticles &sp, int s, int lx, int ly, int lz,
+                                         int dx, int dy, int dz, float &Mf, float &Ms) {
+    const float Lx = (float)P.nx, Ly = (float)P.ny, Lz = (float)P.nz;
+    float a = 0.f, b = 0.f;
+    const int nc = sp.ncp[s];
+    for (int k = 0; k < nc; k++) {
+        float ox = (float)lx - sp.crel[s][k][0];
+        float oy = (float)ly - sp.crel[s][k][1];
+        float oz = (float)lz - sp.crel[s][k][2];
+        if (P.per[0]) { if (ox > 0.5f * Lx) ox -= Lx; else if (ox < -0.5f * Lx) ox += Lx; }
+        if (P.per[1]) { if (oy > 0.5f * Ly) oy -= Ly; else if (oy < -0.5f * Ly) oy += Ly; }
+        if (P.per[2]) { if (oz > 0.5f * Lz) oz -= Lz; else if (oz < -0.5f * Lz) oz += Lz; }
+        const float sx = ox + (float)dx, sy = oy + (float)dy, sz = oz + (float)dz;
+        const float K = sp.K[s][k];
+        a += K * __fdividef(1.0f, ox * ox + oy * oy + oz * oz);
+        b += K * __fdividef(1.0f, sx * sx + sy * sy + sz * sz);
+    }
+    Mf = a;
+    Ms = b;
+}
+
 // M of listed particle s and its derivative along d at x_b + q d, x_b the
 // brick-local node (lx,ly,lz): M = sum K/r^2, dM/dq = -2 sum K (r.d)/r^4.
 // FP32 works on brick-relative offsets, minimum image taken at the node.
@@ -190,10 +222,18 @@ __device__ __forceinline__ void particle_velocity(const Params &P, const SmemPar
 // FP32 value is kept exactly down to that unit) and add it to the warp's
 // totals in shared memory with integer atomics: exact, so the result does
 // not depend on the order, and no per-thread array lives in local memory.
+// One link's force and torque terms in fixed point, handed back to the
+// warp's link round, which sums them over the warp with integer reductions
+// (exact, like the atomics) before one lane adds them to the warp's totals.
+struct LinkTerms {
+    int s;            // listed slot, -1: none
+    long long t[6];
+};
 template <typename C>
 struct ForceSink {
     C (*acc)[6];
     unsigned long long (*fix)[6];
+    LinkTerms *defer;  // set: the terms go to *defer instead
 };
 
 // Force and torque (r x dP) of one term, and the same in 64-bit fixed point.
@@ -218,10 +258,37 @@ __device__ __forceinline__ void add_term(ForceSink<C> sink, int s, const C dP[3]
     if (sizeof(C) == 8) {
 #pragma unroll
         for (int c = 0; c < 6; c++) sink.acc[s][c] += t[c];
+    } else if (sink.defer) {
+        sink.defer->s = s;
+#pragma unroll
+        for (int c = 0; c < 6; c++) sink.defer->t[c] = (long long)to_fixed<C>(t[c]);
     } else {
 #pragma unroll
         for (int c = 0; c < 6; c++)
             if (t[c] != C(0)) atomicAdd(&sink.fix[s][c], to_fixed<C>(t[c]));
+    }
+}
+
+// The warp's link terms of one round added to its totals per listed slot:
+// each 64-bit term split into 21 + 21 + 22 bits, summed over the warp with
+// 32-bit reductions and put back together, which is the exact 64-bit sum
+// (modulo 2^64, as the atomics).
+__device__ __forceinline__ void warp_add_terms(unsigned long long (*fix)[6], int cnt, const LinkTerms &lt,
+                                               int lane) {
+    for (int s = 0; s < cnt; s++) {
+        const bool mine = lt.s == s;
+        if (!__any_sync(0xffffffffu, mine)) continue;
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            const long long v = mine ? lt.t[c] : 0ll;
+            const unsigned lo = (unsigned)v & 0x1FFFFFu, mid = (unsigned)(v >> 21) & 0x1FFFFFu;
+            const int hi = (int)(v >> 42);
+            const unsigned long long sum =
+                (unsigned long long)__reduce_add_sync(0xffffffffu, lo) +
+                ((unsigned long long)__reduce_add_sync(0xffffffffu, mid) << 21) +
+                ((unsigned long long)(long long)__reduce_add_sync(0xffffffffu, hi) << 42);
+            if (lane == 0) fix[s][c] += sum;
+        }
     }
 }
 
@@ -289,15 +356,23 @@ __device__ __forceinline__ LinkGeom<typename Codec<S>::C> link_geometry(const Pa
     using C = typename Codec<S>::C;
     const int io = L::opp(i);
     const int dx = lat_e<Q>(io, 0), dy = lat_e<Q>(io, 1), dz = lat_e<Q>(io, 2);  // d, into the solid
-    if (*Mf_slot != s) {
-        *Mf_cache = m_value<C>(P, sp, s, lx, ly, lz, bx0, by0, bz0);
-        *Mf_slot = s;
+    C Mf, Ms;
+    if (sizeof(C) == 4) {
+        float mf, ms;
+        m_link_f(P, sp, s, lx, ly, lz, dx, dy, dz, mf, ms);
+        Mf = (C)mf;
+        Ms = (C)ms;
+    } else {
+        if (*Mf_slot != s) {
+            *Mf_cache = m_value<C>(P, sp, s, lx, ly, lz, bx0, by0, bz0);
+            *Mf_slot = s;
+        }
+        Mf = *Mf_cache;
+        Ms = m_value<C>(P, sp, s, lx + dx, ly + dy, lz + dz, bx0, by0, bz0);
     }
-    const C Mf = *Mf_cache;
-    const C Ms = m_value<C>(P, sp, s, lx + dx, ly + dy, lz + dz, bx0, by0, bz0);
     LinkGeom<C> g;
-    C q = (c0_of<C>(P) - Mf) / (Ms - Mf);
-    q = q < C(0) ? C(0) : (q > C(1) ? C(1) : q);
+    C q = sizeof(C) == 4 ? (c0_of<C>(P) - Mf) * rcp_w<C>(Ms - Mf) : (c0_of<C>(P) - Mf) / (Ms - Mf);
+    q = q > C(0) ? (q < C(1) ? q : C(1)) : C(0);  // (a NaN from Ms == Mf becomes 0)
     if (P.q_exact) q = q_root<C>(P, sp, s, lx, ly, lz, dx, dy, dz, bx0, by0, bz0, q);
     g.q = q;
     lever<C>(P, sp, s, bx0, by0, bz0, (C)lx + q * dx, (C)ly + q * dy, (C)lz + q * dz, g.r);
@@ -343,7 +418,7 @@ __device__ __forceinline__ typename Codec<S>::C link_update(const Params &P, int
     } else {
         C u_ff[3];
         const C rho_ff = rho0 + drho_ff;
-        const C inv_rho_ff = C(1) / rho_ff;
+        const C inv_rho_ff = rcp_w<C>(rho_ff);
         for (int a = 0; a < 3; a++) u_ff[a] = (m_ff[a] - C(0.5) * Prm<C>::F(P, a)) * inv_rho_ff;
         const C feq_f = geq_i<C>(dx, dy, dz, w_io, drho_f, rho_f, u_f[0], u_f[1], u_f[2]);
         const C feq_ff = geq_i<C>(dx, dy, dz, w_io, drho_ff, rho_ff, u_ff[0], u_ff[1], u_ff[2]);
@@ -356,11 +431,11 @@ __device__ __forceinline__ typename Codec<S>::C link_update(const Params &P, int
             for (int a = 0; a < 3; a++) us[a] = C(2) * q * u_f[a] + (C(1) - C(2) * q) * u_ff[a];
         } else {            // second branches
             drho_d = drho_f;
-            const C inv_q = C(1) / q;
+            const C inv_q = rcp_w<C>(q);
             const C a_f = (C(1) - q) * inv_q, a_w = (C(2) * q - C(1)) * inv_q;
             for (int a = 0; a < 3; a++) us[a] = a_f * u_f[a] + a_w * uw[a];
         }
-        const C inv_1q = C(1) / (C(1) + q);
+        const C inv_1q = rcp_w<C>(C(1) + q);
         const C b_ff = (C(1) - q) * inv_1q, b_w = C(2) * q * inv_1q;
         for (int a = 0; a < 3; a++) uss[a] = b_ff * u_ff[a] + b_w * uw[a];                 // (24)
         for (int a = 0; a < 3; a++) ud[a] = (us[a] + C(2) * uss[a]) * C(1.0 / 3.0);        // (25)
@@ -490,7 +565,7 @@ __device__ __noinline__ typename Codec<S>::C link_coop(const Params &P, const Sm
         if (k == io) fown_io = fk;
     }
     C u_f[3];
-    const C inv_rho_f = C(1) / (rho0 + drho_f);
+    const C inv_rho_f = rcp_w<C>(rho0 + drho_f);
     for (int a = 0; a < 3; a++) u_f[a] = (m_f[a] - C(0.5) * Prm<C>::F(P, a)) * inv_rho_f;
     C Mf_cache = 0;
     int Mf_slot = -1;
@@ -681,13 +756,23 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
             }
         }
         __syncwarp();
-        for (int e = lane; e < total; e += 32) {
-            const int ent = ls->entry[warp][e];
-            const int L_ = ent >> 5, i = ent & 31;
-            const int t = warp * 32 + L_;  // the node's thread index in the brick
-            ls->result[warp][e] = (float)link_coop<S, Q>(P, sp, i, t % BX, (t / BX) % BY, t / (BX * BY), bx0, by0,
-                                                         bz0, sink);
-            nlinks++;
+        // rounds of 32 links; each round's force terms are summed over the
+        // warp (no per-link atomics on the warp's totals)
+        for (int r = 0; r < total; r += 32) {
+            const int e = r + lane;
+            LinkTerms lt;
+            lt.s = -1;
+            if (e < total) {
+                const int ent = ls->entry[warp][e];
+                const int L_ = ent >> 5, i = ent & 31;
+                const int t = warp * 32 + L_;  // the node's thread index in the brick
+                ForceSink<C> ds = sink;
+                ds.defer = &lt;
+                ls->result[warp][e] = (float)link_coop<S, Q>(P, sp, i, t % BX, (t / BX) % BY, t / (BX * BY), bx0,
+                                                             by0, bz0, ds);
+                nlinks++;
+            }
+            warp_add_terms(ls->fix[warp], cnt, lt, lane);
         }
         __syncwarp();
         if (fluid) {
@@ -751,16 +836,30 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
 
 // The sweep of the bricks listed this step (exactly those some particle's
 // grown search box meets) and of the predicted-near bricks that are not
-// listed (plain path): every brick k_sweep_plain leaves.  Persistent grid.
+// listed (plain path): every brick k_sweep_plain leaves.  Persistent grid;
+// the CTAs take the bricks one at a time from a per-step counter (a brick
+// with particle links costs about ten times one on the plain path, and a
+// fixed split left the busiest CTA near 1.45 times the mean).  Thread 0
+// fetches the next entry while the current brick runs; s_next holds it,
+// alternating between two slots so that a slot is rewritten only after
+// every thread has passed the barrier that follows its last read.
 template <typename S, int Q, bool kForce>
 __device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, double (*red)[6], int &s_links,
-                                          LinkScratch &ls, int blk, int nblk) {
+                                          LinkScratch &ls, int *s_next) {
     const int tid = threadIdx.x;
     const int t = P.step;
     const int c_exact = P.counters[CNT_LISTED];
     const int c_pred = P.pred_stamp_cur ? P.pred_count[t % 3] : 0;
+    const int total = c_exact + c_pred;
     int done = 0;
-    for (int w = blk; w < c_exact + c_pred; w += nblk) {
+    int nxt = 0;
+    if (tid == 0) nxt = atomicAdd(&P.counters[CNT_NEAR_NEXT], 1);
+    for (int k = 0;; k ^= 1) {
+        if (tid == 0) s_next[k] = nxt;
+        __syncthreads();  // the previous brick is done with the shared state
+        const int w = s_next[k];
+        if (w >= total) break;
+        if (tid == 0) nxt = atomicAdd(&P.counters[CNT_NEAR_NEXT], 1);
         int b;
         if (w < c_exact) {
             b = P.wl_list[(t % 3) * P.nbricks + w];
@@ -773,7 +872,6 @@ __device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, do
         brick_coords(P, b, bxi, byi, bzi);
         const int bx0 = bxi * BX, by0 = byi * BY, bz0 = bzi * BZ;
         int cnt = min(P.bcount[b], MAXPB);
-        __syncthreads();  // the previous brick is done with the shared state
         // the brick's particle ids, staged with the neighbourhood check below
         // (made visible by its barrier)
         if (tid >= 32 && tid < 32 + cnt) sp.id[tid - 32] = P.blist[b * MAXPB + (tid - 32)];
@@ -820,7 +918,8 @@ __global__ void __launch_bounds__(BRICK, kNearCtasPerSm) k_sweep_near(Params P) 
     __shared__ double red[BRICK / 32][6];
     __shared__ int s_links;
     __shared__ LinkScratch ls;
-    near_work<S, Q, kForce>(P, sp, red, s_links, ls, blockIdx.x, gridDim.x);
+    __shared__ int s_next[2];
+    near_work<S, Q, kForce>(P, sp, red, s_links, ls, s_next);
 }
 
 }  // namespace lbmmb

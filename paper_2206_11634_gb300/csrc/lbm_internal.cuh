@@ -31,7 +31,8 @@ constexpr int ROT_ITERS = 2;  // fixed-point sweeps of the implicit rotational h
 
 // Status words in the workspace.
 enum StatusSlot { ST_ERR = 0, ST_SLOTS = 16 };
-enum StepCounter { CNT_NREFILL = 0, CNT_NLINKS = 1, CNT_LISTED = 2, CNT_NEAR = 3 };
+// CNT_NEAR_NEXT: the near sweep's brick queue (next entry to hand out)
+enum StepCounter { CNT_NREFILL = 0, CNT_NLINKS = 1, CNT_LISTED = 2, CNT_NEAR = 3, CNT_NEAR_NEXT = 4 };
 enum ErrBits { ERRB_BRICK_OVERFLOW = 1, ERRB_DIVERGED = 2, ERRB_TIMEOUT = 4, ERRB_DEM_CAPACITY = 8,
                ERRB_STATIC_CAPACITY = 16, ERRB_DEM_REACH = 32 };
 // contact history flags (Params::pair_on per pair, wall_on per particle and
