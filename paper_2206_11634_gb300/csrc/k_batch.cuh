@@ -13,9 +13,10 @@ template <typename S, int Q>
 __global__ void __launch_bounds__(BRICK) k_flags_batch(BatchArgs B) {
     __shared__ Params sP;
     __shared__ SmemParticles sp;
+    __shared__ int s_next[2];
     const int c = blockIdx.x / B.g_chain, lb = blockIdx.x % B.g_chain;
     load_case_params(B, c, B.ctr, sP);
-    flags_work<S, Q>(sP, sp, lb, B.g_chain);
+    flags_work<S, Q>(sP, sp, s_next, lb);
 }
 
 // g_chain CTAs per case over its near bricks; the last CTA of the launch

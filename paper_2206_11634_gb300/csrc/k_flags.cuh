@@ -183,8 +183,11 @@ __device__ __forceinline__ void flags_brick(const Params &P, SmemParticles &sp, 
 // Persistent grid over the bricks listed this step and in the two steps
 // before; a brick listed in several of these lists is visited once (its most
 // recent listing).
+// The bricks are handed out one at a time from a per-step counter, as in the
+// near sweep (thread 0 fetches the next entry while the current brick runs;
+// s_next alternates between two slots).
 template <typename S, int Q>
-__device__ __forceinline__ void flags_work(const Params &P, SmemParticles &sp, int blk, int nblk) {
+__device__ __forceinline__ void flags_work(const Params &P, SmemParticles &sp, int *s_next, int blk) {
     const int t = P.step;
     const int r0 = t % 3, r1 = (t + 2) % 3, r2 = (t + 1) % 3;
     const int c0 = P.counters[CNT_LISTED];
@@ -192,7 +195,14 @@ __device__ __forceinline__ void flags_work(const Params &P, SmemParticles &sp, i
     const int c2 = t >= 2 ? P.wl_count[r2] : 0;
     if (blk == 0 && threadIdx.x == 0) P.wl_count[r0] = c0;  // read by the next two steps
     const int total = c0 + c1 + c2;
-    for (int w = blk; w < total; w += nblk) {
+    int nxt = 0;
+    if (threadIdx.x == 0) nxt = atomicAdd(&P.counters[CNT_FLAGS_NEXT], 1);
+    for (int k = 0;; k ^= 1) {
+        if (threadIdx.x == 0) s_next[k] = nxt;
+        __syncthreads();
+        const int w = s_next[k];
+        if (w >= total) break;
+        if (threadIdx.x == 0) nxt = atomicAdd(&P.counters[CNT_FLAGS_NEXT], 1);
         int b;
         if (w < c0) {
             b = P.wl_list[r0 * P.nbricks + w];
@@ -209,7 +219,8 @@ __device__ __forceinline__ void flags_work(const Params &P, SmemParticles &sp, i
 template <typename S, int Q>
 __global__ void __launch_bounds__(BRICK) k_flags(Params P) {
     __shared__ SmemParticles sp;
-    flags_work<S, Q>(P, sp, blockIdx.x, gridDim.x);
+    __shared__ int s_next[2];
+    flags_work<S, Q>(P, sp, s_next, blockIdx.x);
 }
 
 // Every node to f^eq(rho0, u0).

@@ -36,6 +36,9 @@ __device__ void bin_particle(const Params &P, int j) {
         const float hi = (float)p.x[a];
         p.x_hl[a][0] = hi;
         p.x_hl[a][1] = (float)(p.x[a] - (double)hi);
+    } else if (t >= 64 && t < 70) {
+        const int a = t - 64;
+        p.vw_f[a] = (float)(a < 3 ? p.v[a] : p.w[a - 3]);
     }
     __syncthreads();
     if (t == 0) {

@@ -47,7 +47,6 @@ struct Layout {
     int nbx, nby, nbz, nbricks;
 };
 
-constexpr int kStepCounters = 8;  // nrefill, nlinks, listed, near bricks, near-sweep queue, 3 spare
 // Steps with the flag pass after the particles were set, before a geometry of
 // fixed particles counts as static: the pass visits the bricks listed in the
 // last three steps, so three passes leave both flag buffers and the per-brick

@@ -31,8 +31,10 @@ constexpr int ROT_ITERS = 2;  // fixed-point sweeps of the implicit rotational h
 
 // Status words in the workspace.
 enum StatusSlot { ST_ERR = 0, ST_SLOTS = 16 };
-// CNT_NEAR_NEXT: the near sweep's brick queue (next entry to hand out)
-enum StepCounter { CNT_NREFILL = 0, CNT_NLINKS = 1, CNT_LISTED = 2, CNT_NEAR = 3, CNT_NEAR_NEXT = 4 };
+// CNT_NEAR_NEXT, CNT_FLAGS_NEXT: the brick queues of the near sweep and of
+// the flag pass (next entry to hand out)
+enum StepCounter { CNT_NREFILL = 0, CNT_NLINKS = 1, CNT_LISTED = 2, CNT_NEAR = 3, CNT_NEAR_NEXT = 4, CNT_FLAGS_NEXT = 5 };
+constexpr int kStepCounters = 8;  // the slots above, rounded up (zeroed with the brick counts)
 enum ErrBits { ERRB_BRICK_OVERFLOW = 1, ERRB_DIVERGED = 2, ERRB_TIMEOUT = 4, ERRB_DEM_CAPACITY = 8,
                ERRB_STATIC_CAPACITY = 16, ERRB_DEM_REACH = 32 };
 // contact history flags (Params::pair_on per pair, wall_on per particle and
@@ -302,6 +304,7 @@ struct DevParticle {
     // that brick-relative FP32 positions are formed without FP64 arithmetic
     float cpw_hl[MAXCP][3][2];
     float x_hl[3][2];
+    float vw_f[6];         // v and w in FP32, for the sweeps' wall velocities (binning)
 };
 
 // Everything a kernel needs, passed by value.
@@ -605,6 +608,8 @@ __device__ inline void load_particle_records(const Params &P, SmemParticles &sp,
                                              int bz0) {
     const float org[3] = {(float)bx0, (float)by0, (float)bz0};
     const float half[3] = {0.5f * BX, 0.5f * BY, 0.5f * BZ};
+    // every control-point slot is read (slots past ncp hold zeros, unused),
+    // so no load waits for ncp; FP32 copies only (no FP64 conversions)
     for (int t = threadIdx.x; t < cnt * MAXCP; t += blockDim.x) {
         int s = t / MAXCP, k = t % MAXCP;
         const DevParticle &p = P.parts[sp.id[s]];
@@ -612,15 +617,13 @@ __device__ inline void load_particle_records(const Params &P, SmemParticles &sp,
             sp.ncp[s] = p.ncp;
             for (int a = 0; a < 3; a++) {
                 sp.prel[s][a] = minimg_rel_f(P, a, df_minus_int(p.x_hl[a], org[a]), half[a]);
-                sp.v[s][a] = (float)p.v[a];
-                sp.w[s][a] = (float)p.w[a];
+                sp.v[s][a] = p.vw_f[a];
+                sp.w[s][a] = p.vw_f[3 + a];
             }
         }
-        if (k < p.ncp) {
-            for (int a = 0; a < 3; a++)
-                sp.crel[s][k][a] = minimg_rel_f(P, a, df_minus_int(p.cpw_hl[k][a], org[a]), half[a]);
-            sp.K[s][k] = (float)p.K[k];
-        }
+        for (int a = 0; a < 3; a++)
+            sp.crel[s][k][a] = minimg_rel_f(P, a, df_minus_int(p.cpw_hl[k][a], org[a]), half[a]);
+        sp.K[s][k] = p.K_f[k];
     }
     __syncthreads();
 }

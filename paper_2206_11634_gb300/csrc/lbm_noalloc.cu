@@ -30,8 +30,8 @@ constexpr int kMaxParticles = 256;
 constexpr int kMaxDevices = 64;
 
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
-constexpr size_t kOffBin = 0;                                                    // bcount + 4 counters
-constexpr size_t kOffList = align256(kOffBin + (size_t)(kMaxBricks + 4) * 4);    // brick lists
+constexpr size_t kOffBin = 0;                                                    // bcount + step counters
+constexpr size_t kOffList = align256(kOffBin + (size_t)(kMaxBricks + kStepCounters) * 4);  // brick lists
 constexpr size_t kOffWork = align256(kOffList + (size_t)kMaxBricks * MAXPB * 4);  // work list ring, counts, stamps
 constexpr size_t kWorkBytes = (size_t)kMaxBricks * 4 * 4 + 3 * 4;
 constexpr size_t kOffStatus = align256(kOffWork + kWorkBytes);
@@ -87,6 +87,7 @@ extern "C" int lbm_flags_noalloc(const lbm_config *cfg, const lbm_particle *host
             if (!(p.K[k] >= 0.0)) return LBM_ERR_BAD_ARG;
             for (int a = 0; a < 3; a++) d.cpb[k][a] = p.cp[k][a];
             d.K[k] = p.K[k];
+            d.K_f[k] = (float)p.K[k];  // the sweeps' and flag pass's FP32 copy
             Ks += p.K[k];
         }
         d.sumK = Ks;
@@ -98,7 +99,7 @@ extern "C" int lbm_flags_noalloc(const lbm_config *cfg, const lbm_particle *host
     // what must start at zero: brick counts and counters, work lists and
     // stamps, status, and the output (bricks without particles are never
     // written)
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffBin, 0, (size_t)(nbricks + 4) * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffBin, 0, (size_t)(nbricks + kStepCounters) * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffWork, 0, kWorkBytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffStatus, 0, ST_SLOTS * 4, st);
     const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
