@@ -103,8 +103,10 @@ __device__ __forceinline__ void exp_half(float hh, float qh2, const float w[3], 
 // launch (the contact state is loaded from global memory once and written
 // back once), so the sub-step chain never waits on an L2 round trip
 // ---------------------------------------------------------------------------
-template <int CAP, int ITEMS, int CPS>
+template <int CAP, int ITEMS, int CPS, bool kCpb, bool kWarpGroup>
 struct SharedT {
+    static constexpr bool kCacheCpb = kCpb;         // body-frame control points kept in shared memory
+    static constexpr bool kWarp = kWarpGroup;       // one warp per table (else the whole CTA)
     static constexpr int kCap = CAP;                // particles in the tables
     static constexpr int kItems = ITEMS;            // candidate pairs resident in shared memory
     static constexpr int kWordsT = (CAP + 31) / 32;
@@ -116,6 +118,7 @@ struct SharedT {
     float Fc[CAP][3], Tc[CAP][3];   // contact force / torque of the last evaluation
     float brad[CAP], Rs[CAP], reach[CAP];
     float4 rc[CPS];                 // control points R(q) cpb relative to x, and K
+    float4 cpb[kCpb ? CPS : 1];     // control points in the body frame, and K (put_rc's input)
     int cpo[CAP + 1];               // offsets into rc
     unsigned bits[CAP][(CAP + 31) / 32];  // candidate pairs (i < j)
     unsigned short up[CAP][kMaxAdj];      // partners j > i, ascending
@@ -133,9 +136,24 @@ struct SharedT {
     float w_xcw[CAP][NWALL][3], w_xi[CAP][NWALL][3];
 };
 // every particle in one CTA (k_dem32, and k_dem64c for a large contact group)
-using Shared = SharedT<kMaxP, kMaxItems, kDem32MaxCp>;
+using Shared = SharedT<kMaxP, kMaxItems, kDem32MaxCp, false, false>;
 // a contact group of up to 32 particles (k_dem64c, one CTA per group)
-using SharedSmall = SharedT<kSmallContactGroup, 256, kSmallContactGroup * MAXCP>;
+using SharedSmall = SharedT<kSmallContactGroup, 256, kSmallContactGroup * MAXCP, true, false>;
+// a contact group of up to kTinyContactGroup particles (one warp each,
+// kTinyGroupsPerCta tables per CTA; at most 6 candidate pairs)
+using SharedTiny = SharedT<kTinyContactGroup, 8, kTinyContactGroup * MAXCP, true, true>;
+
+// The threads that share one table: the CTA, or for warp tables the warp.
+template <class SH> __device__ __forceinline__ int gtid() { return SH::kWarp ? (int)(threadIdx.x & 31) : (int)threadIdx.x; }
+template <class SH> __device__ __forceinline__ int gdim() { return SH::kWarp ? 32 : (int)blockDim.x; }
+template <class SH> __device__ __forceinline__ void gsync() {
+    if constexpr (SH::kWarp) __syncwarp();
+    else __syncthreads();
+}
+template <class SH> __device__ __forceinline__ int gsync_or(int v) {
+    if constexpr (SH::kWarp) return __any_sync(0xffffffffu, v);
+    else return __syncthreads_or(v);
+}
 
 template <class SH>
 __device__ __forceinline__ void rel_vec(const SH &S, const Params &P, int i, int j, float d[3]) {
@@ -294,12 +312,13 @@ __device__ bool pair_geom_f(const Params &P, const SH &S, int i, int j, const fl
 
 // Wall geometry, Eqs. (10)-(13), frame centred on the particle; prel: the
 // wall plane's coordinate relative to x along its axis.
-template <class SH>
-__device__ bool wall_geom_f(const Params &P, const SH &S, int k, int wall, float prel, bool warm, float xcw[3],
+// The wall's axis is a template parameter, so that every index into x, g
+// and H is a constant and they stay in registers.
+template <int AX, class SH>
+__device__ __forceinline__ bool wall_geom_f(const Params &P, const SH &S, int k, int side, float prel, bool warm, float xcw[3],
                             float &delta, float nv[3], float xcp[3], bool &valid) {
-    const int ax = wall / 2, side = wall % 2;
+    constexpr int ax = AX, t1 = (AX + 1) % 3, t2 = (AX + 2) % 3;
     const float m_ax = side ? 1.0f : -1.0f;
-    const int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
     const float4 *rc = S.rc + S.cpo[k];
     const int nc = S.cpo[k + 1] - S.cpo[k];
     const float zero[3] = {0.f, 0.f, 0.f};
@@ -318,8 +337,7 @@ __device__ bool wall_geom_f(const Params &P, const SH &S, int k, int wall, float
     }
     x[ax] = prel;
     // H index of (a, b)
-    auto hidx = [](int a, int b) { return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5)); };
-    const int i11 = hidx(t1, t1), i12 = hidx(t1, t2), i22 = hidx(t2, t2);
+    constexpr int i11 = t1, i22 = t2, i12 = t1 + t2 == 1 ? 3 : (t1 + t2 == 2 ? 4 : 5);
     float M, g[3], H[6], xe[3];  // the last evaluation, at xe (as for pairs)
     float prev = 3.4e38f;
     bool converged = false;
@@ -363,7 +381,7 @@ __device__ bool wall_geom_f(const Params &P, const SH &S, int k, int wall, float
 template <class SH>
 __device__ void store_items(const Params &P, SH &S) {
     const int np = S.n;
-    for (int i = threadIdx.x; i < np; i += blockDim.x)
+    for (int i = gtid<SH>(); i < np; i += gdim<SH>())
         for (int s = 0; s < S.nup[i]; s++) {
             const int it = S.ioff[i] + s;
             if (it >= SH::kItems) break;
@@ -382,9 +400,9 @@ __device__ void store_items(const Params &P, SH &S) {
 // Loads the candidates' contact history into shared memory.
 template <class SH>
 __device__ void build_lists(const Params &P, SH &S, int *possible) {
-    const int np = S.n, tid = threadIdx.x;
+    const int np = S.n, tid = gtid<SH>(), nth = gdim<SH>();
     const int nw = (np + 31) / 32;
-    for (int idx = tid; idx < np * nw; idx += blockDim.x) {
+    for (int idx = tid; idx < np * nw; idx += nth) {
         const int i = idx / nw, wd = idx % nw;
         unsigned m = 0;
         const float bri = S.brad[i], ri = S.reach[i];
@@ -410,9 +428,9 @@ __device__ void build_lists(const Params &P, SH &S, int *possible) {
         }
         S.bits[i][wd] = m;
     }
-    for (int k = tid; k < np; k += blockDim.x) S.ndn[k] = 0;
-    __syncthreads();
-    for (int i = tid; i < np; i += blockDim.x) {
+    for (int k = tid; k < np; k += nth) S.ndn[k] = 0;
+    gsync<SH>();
+    for (int i = tid; i < np; i += nth) {
         int n = 0;
         for (int wd = 0; wd < nw; wd++) {
             unsigned m = S.bits[i][wd];
@@ -433,8 +451,8 @@ __device__ void build_lists(const Params &P, SH &S, int *possible) {
         }
         S.nup[i] = n;
     }
-    __syncthreads();
-    for (int k = tid; k < np; k += blockDim.x) {
+    gsync<SH>();
+    for (int k = tid; k < np; k += nth) {
         const int n = min(S.ndn[k], kMaxAdj);
         S.ndn[k] = n;
         for (int a = 1; a < n; a++) {  // ascending m
@@ -451,8 +469,8 @@ __device__ void build_lists(const Params &P, SH &S, int *possible) {
         S.ioff[np] = o;
         if (o > SH::kItems) atomicOr(&P.status[ST_ERR], ERRB_DEM_CAPACITY);
     }
-    __syncthreads();
-    for (int i = tid; i < np; i += blockDim.x)
+    gsync<SH>();
+    for (int i = tid; i < np; i += nth)
         for (int s = 0; s < S.nup[i]; s++) {
             const int it = S.ioff[i] + s;
             if (it >= SH::kItems) break;
@@ -463,7 +481,7 @@ __device__ void build_lists(const Params &P, SH &S, int *possible) {
                 S.it_xi[it][a] = P.pair_xi_f[3 * pidx + a];
             }
         }
-    __syncthreads();
+    gsync<SH>();
 }
 
 // Pair contacts of the candidate list (one item per thread); results into
@@ -472,7 +490,7 @@ template <class SH>
 __device__ void pair_contacts(const Params &P, SH &S, float h) {
     const int np = S.n;
     const int total = min(S.ioff[np], SH::kItems);
-    for (int it = threadIdx.x; it < total; it += blockDim.x) {
+    for (int it = gtid<SH>(); it < total; it += gdim<SH>()) {
         int lo = 0, hi = np - 1;  // item -> (i, slot): last i with ioff[i] <= it
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -538,7 +556,10 @@ __device__ void gather_contacts(const Params &P, SH &S, int k, float h, float F[
         const int was = S.w_on[k][wall];
         float xcw[3] = {S.w_xcw[k][wall][0], S.w_xcw[k][wall][1], S.w_xcw[k][wall][2]}, delta, nv[3], xcp[3];
         bool valid;
-        const bool hit = wall_geom_f(P, S, k, wall, prel, (was & CONTACT_WARM) != 0, xcw, delta, nv, xcp, valid);
+        const bool start = (was & CONTACT_WARM) != 0;
+        const bool hit = ax == 0   ? wall_geom_f<0>(P, S, k, side, prel, start, xcw, delta, nv, xcp, valid)
+                         : ax == 1 ? wall_geom_f<1>(P, S, k, side, prel, start, xcw, delta, nv, xcp, valid)
+                                   : wall_geom_f<2>(P, S, k, side, prel, start, xcw, delta, nv, xcp, valid);
         for (int a = 0; a < 3; a++) S.w_xcw[k][wall][a] = xcw[a];
         const int warm = valid ? CONTACT_WARM : 0;
         if (!hit) { S.w_on[k][wall] = warm; continue; }
@@ -555,14 +576,29 @@ __device__ void gather_contacts(const Params &P, SH &S, int k, float h, float F[
     }
 }
 
+// Body-frame control points of particle k into the shared table (once per
+// launch, by the thread that rotates them), where the tables have room.
+template <class SH>
+__device__ __forceinline__ void load_cpb(const Params &P, SH &S, int k) {
+    if constexpr (SH::kCacheCpb) {
+        const DevParticle &p = P.parts[S.gid[k]];
+        const int o = S.cpo[k], nc = S.cpo[k + 1] - o;
+        for (int c = 0; c < nc; c++) S.cpb[o + c] = make_float4(p.cpb_f[c][0], p.cpb_f[c][1], p.cpb_f[c][2], p.K_f[c]);
+    }
+}
+
 // Rotated control points of particle k into the shared table.
 template <class SH>
 __device__ __forceinline__ void put_rc(const Params &P, SH &S, int k, const float q[4]) {
+    const int o = S.cpo[k], nc = S.cpo[k + 1] - o;
     const DevParticle &p = P.parts[S.gid[k]];
-    for (int c = 0; c < p.ncp; c++) {
+    for (int c = 0; c < nc; c++) {
+        const float4 b = SH::kCacheCpb ? S.cpb[o + c]
+                                       : make_float4(p.cpb_f[c][0], p.cpb_f[c][1], p.cpb_f[c][2], p.K_f[c]);
+        const float v[3] = {b.x, b.y, b.z};
         float r[3];
-        qrot_f(q, p.cpb_f[c], r, true);
-        S.rc[S.cpo[k] + c] = make_float4(r[0], r[1], r[2], p.K_f[c]);
+        qrot_f(q, v, r, true);
+        S.rc[o + c] = make_float4(r[0], r[1], r[2], b.w);
     }
 }
 
@@ -624,6 +660,7 @@ __global__ void __launch_bounds__(kThreads) k_dem32(Params P) {
         S.brad[tid] = pp->brad_f;
         S.Rs[tid] = pp->Rs_f;
         if (reach > 0.4f * kSkin) possible = 1;
+        load_cpb(P, S, tid);
         put_rc(P, S, tid, qf);
         for (int wall = 0; wall < NWALL; wall++) {
             const int ax = wall / 2, side = wall % 2;
@@ -893,16 +930,22 @@ struct Delta {
 __device__ __forceinline__ void dl_set(Delta &a, double v) { a.bf = (float)v; a.d = {0.f, 0.f}; }
 __device__ __forceinline__ void dl_add(Delta &a, float b) { a.d = df_add(a.d, b); }
 
-// One CTA per contact group (k_dem64_plan): groups of up to 32 particles
-// with tables sized for them (kLarge = false, 32 threads), larger ones with
-// the full tables (kLarge, 512 threads).
-template <class SH, bool kLarge>
-__global__ void __launch_bounds__(kLarge ? kThreads : kSmallContactGroup, 1) k_dem64c(Params P) {
+// The contact groups of k_dem64_plan by class: groups of up to 4 particles
+// one warp each with tables sized for them (8 groups per CTA, the barriers
+// warp-wide), up to 32 one 32-thread CTA each, larger ones one 512-thread
+// CTA each with the full tables.
+template <class SH, int kClass>
+__global__ void __launch_bounds__(kClass == DEM_GROUP_LARGE   ? kThreads
+                                  : kClass == DEM_GROUP_SMALL ? kSmallContactGroup
+                                                              : 32 * kTinyGroupsPerCta,
+                                  1) k_dem64c(Params P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SH &S = *reinterpret_cast<SH *>(smem_raw);
-    const int tid = threadIdx.x;
-    if ((int)blockIdx.x >= P.dem_list[kLarge ? 3 : 2]) return;
-    const int *grp = dem_groups(P, kLarge) + 2 * blockIdx.x;
+    const int wt = SH::kWarp ? (int)(threadIdx.x >> 5) : 0;  // the warp's table (warp tables)
+    SH &S = reinterpret_cast<SH *>(smem_raw)[wt];
+    const int tid = gtid<SH>();
+    const int slot = SH::kWarp ? (int)blockIdx.x * kTinyGroupsPerCta + wt : (int)blockIdx.x;
+    if (slot >= P.dem_list[2 + kClass]) return;  // (a whole warp, or the whole CTA)
+    const int *grp = dem_groups(P, kClass) + 2 * slot;
     const int na = grp[1];
     const int *act = dem_active(P) + grp[0];
     const float h = P.h_f, hh = 0.5f * h, qh2 = 0.25f * h * h;
@@ -941,8 +984,8 @@ __global__ void __launch_bounds__(kLarge ? kThreads : kSmallContactGroup, 1) k_d
         S.n = na;
         if (o > SH::kCps) atomicOr(&P.status[ST_ERR], ERRB_DEM_CAPACITY);
     }
-    for (int k = tid; k < na; k += blockDim.x) S.gid[k] = act[k];
-    __syncthreads();
+    for (int k = tid; k < na; k += gdim<SH>()) S.gid[k] = act[k];
+    gsync<SH>();
     if (S.cpo[na] > SH::kCps) return;
 
     // FP32 tables: position (hi + lo of the FP64 value), velocity, world
@@ -963,6 +1006,7 @@ __global__ void __launch_bounds__(kLarge ? kThreads : kSmallContactGroup, 1) k_d
         S.reach[tid] = reach;
         S.brad[tid] = pp->brad_f;
         S.Rs[tid] = pp->Rs_f;
+        load_cpb(P, S, tid);
         put_rc(P, S, tid, qf);
         for (int wall = 0; wall < NWALL; wall++) {
             const int wj = g * NWALL + wall;
@@ -973,19 +1017,19 @@ __global__ void __launch_bounds__(kLarge ? kThreads : kSmallContactGroup, 1) k_d
             }
         }
     }
-    __syncthreads();
+    gsync<SH>();
     int dummy = 0;
     if (na > 1) build_lists(P, S, &dummy);
     else if (tid == 0) {
         S.nup[0] = 0; S.ndn[0] = 0; S.ioff[0] = 0; S.ioff[1] = 0;
         for (int a = 0; a < 3; a++) S.xref[0][a] = S.xh[0][a] + S.xl[0][a];
     }
-    __syncthreads();
+    gsync<SH>();
     // contact load at the start: left by the previous step's DEM (same
     // state), unless the particles were set since
     if (!P.fc_valid) {
         pair_contacts(P, S, 0.f);
-        __syncthreads();
+        gsync<SH>();
         if (own) {
             float F[3], T[3];
             gather_contacts(P, S, tid, 0.f, F, T);
@@ -997,7 +1041,7 @@ __global__ void __launch_bounds__(kLarge ? kThreads : kSmallContactGroup, 1) k_d
             S.Tc[tid][a] = (float)P.Tc[3 * g + a];
         }
     }
-    __syncthreads();
+    gsync<SH>();
     for (int sub = 0; sub < P.n_sub; sub++) {
         Delta wh[3] = {wb[0], wb[1], wb[2]};
         int moved = 0;
@@ -1038,14 +1082,14 @@ __global__ void __launch_bounds__(kLarge ? kThreads : kSmallContactGroup, 1) k_d
             if (mov) put_rc(P, S, tid, qf);
             moved = dr2 > 0.25f * kSkin * kSkin;
         }
-        moved = __syncthreads_or(moved);
+        moved = gsync_or<SH>(moved);
         if (moved && na > 1) {
             store_items(P, S);
-            __syncthreads();
+            gsync<SH>();
             build_lists(P, S, &dummy);
         }
         pair_contacts(P, S, h);
-        __syncthreads();
+        gsync<SH>();
         if (own) {
             float F[3], T[3];
             gather_contacts(P, S, tid, h, F, T);
@@ -1068,7 +1112,7 @@ __global__ void __launch_bounds__(kLarge ? kThreads : kSmallContactGroup, 1) k_d
                 }
             }
         }
-        __syncthreads();
+        gsync<SH>();
     }
     // the step's changes added to the FP64 state (still in the record)
     double qd[4] = {1, 0, 0, 0}, wbd[3] = {0, 0, 0}, xd[3] = {0, 0, 0}, vd[3] = {0, 0, 0};
@@ -1091,9 +1135,9 @@ __global__ void __launch_bounds__(kLarge ? kThreads : kSmallContactGroup, 1) k_d
         publish(wf, qf);
         if (mov) put_rc(P, S, tid, qf);
     }
-    __syncthreads();
+    gsync<SH>();
     pair_contacts(P, S, 0.f);
-    __syncthreads();
+    gsync<SH>();
     if (own) {
         float F[3], T[3];
         gather_contacts(P, S, tid, 0.f, F, T);
@@ -1132,14 +1176,20 @@ void launch_dem64c(const Params &P, cudaStream_t st) {
     // the dynamic shared memory limits are raised once per device
     static bool attr_set[64] = {};
     static_assert(sizeof(SharedSmall) <= 48 * 1024, "small contact-group tables exceed 48 KB");
+    static_assert(kTinyGroupsPerCta * sizeof(SharedTiny) <= 48 * 1024, "tiny contact-group tables exceed 48 KB");
     const int big = (int)sizeof(Shared);
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev])
-        attr_set[dev] =
-            cudaFuncSetAttribute(k_dem64c<Shared, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) == cudaSuccess;
-    // every group could be small (grid np); at most np / 33 are large
-    k_dem64c<SharedSmall, false><<<P.np, kSmallContactGroup, sizeof(SharedSmall), st>>>(P);
-    k_dem64c<Shared, true><<<P.np / (kSmallContactGroup + 1) + 1, kThreads, big, st>>>(P);
+        attr_set[dev] = cudaFuncSetAttribute(k_dem64c<Shared, DEM_GROUP_LARGE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, big) == cudaSuccess;
+    // grids for the worst case (every group tiny, or small); at most np / 33
+    // groups are large.  A tiny-group CTA of 8 warps holds most of an SM's
+    // registers, so few other CTAs share the SM with its latency-bound chains.
+    k_dem64c<SharedTiny, DEM_GROUP_TINY><<<(P.np + kTinyGroupsPerCta - 1) / kTinyGroupsPerCta,
+                                           32 * kTinyGroupsPerCta, kTinyGroupsPerCta * sizeof(SharedTiny), st>>>(P);
+    k_dem64c<SharedSmall, DEM_GROUP_SMALL><<<P.np / (kTinyContactGroup + 1) + 1, kSmallContactGroup,
+                                             sizeof(SharedSmall), st>>>(P);
+    k_dem64c<Shared, DEM_GROUP_LARGE><<<P.np / (kSmallContactGroup + 1) + 1, kThreads, big, st>>>(P);
 }
 
 // One CTA: a single warp for a few particles (the barriers between the

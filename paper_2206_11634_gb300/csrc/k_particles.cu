@@ -740,6 +740,7 @@ __device__ void rotate_free_quad(unsigned mk, const DevParticle &p, const double
 // it is active again: the contact history of inactive particles is empty.
 constexpr int kPlanEdges = 4096;
 static_assert(kDem32MaxParticles <= kFastMaxParticles, "one plan thread per particle");
+static_assert(kFastMaxParticles < 4096, "the plan's block scan packs 12-bit counts");
 __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
     // one thread per particle below (np <= kFastMaxParticles = blockDim.x)
     __shared__ float xs[kFastMaxParticles][3], reach[kFastMaxParticles], br[kFastMaxParticles];
@@ -840,15 +841,15 @@ __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
         atomicAdd(&gsz[rk], 1);
     }
     __syncthreads();
-    // exclusive block scan of four 16-bit counters: free particles, group
-    // members, small groups, large groups (groups in the order of their
-    // smallest member, the free list and each group in ascending index)
+    // exclusive block scan of five 12-bit counters (np <= 256): free
+    // particles, group members, and groups of each class (groups in the
+    // order of their smallest member, the free list and each group in
+    // ascending index)
     const int g = on && rk == k ? gsz[k] : 0;
-    const bool large = g > kSmallContactGroup;
+    const int cls = g > kSmallContactGroup ? DEM_GROUP_LARGE : (g > kTinyContactGroup ? DEM_GROUP_SMALL : DEM_GROUP_TINY);
     const unsigned long long mine = (unsigned long long)(k < np && !on) |
-                                    (unsigned long long)g << 16 |
-                                    (unsigned long long)(g > 0 && !large) << 32 |
-                                    (unsigned long long)(large) << 48;
+                                    (unsigned long long)g << 12 |
+                                    (unsigned long long)(g > 0) << (24 + 12 * cls);
     unsigned long long inc = mine;
     for (int d = 1; d < 32; d <<= 1) {
         const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, d);
@@ -861,11 +862,11 @@ __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
         if (w < warp) ex += wsum[w];
         tot += wsum[w];
     }
-    const int exf = (int)(ex & 0xFFFF), exg = (int)(ex >> 16 & 0xFFFF);
+    const int exf = (int)(ex & 0xFFF), exg = (int)(ex >> 12 & 0xFFF);
     if (k < np && !on) dem_free(P)[exf] = k;
     if (g > 0) {
-        const int slot = large ? (int)(ex >> 48 & 0xFFFF) : (int)(ex >> 32 & 0xFFFF);
-        int *gl = dem_groups(P, large);
+        const int slot = (int)(ex >> (24 + 12 * cls) & 0xFFF);
+        int *gl = dem_groups(P, cls);
         gl[2 * slot] = exg;
         gl[2 * slot + 1] = g;
         gsz[k] = exg;   // the group's first slot in the active list
@@ -877,10 +878,7 @@ __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
         dem_active(P)[gsz[rk] + rank] = k;
     }
     if (threadIdx.x == 0) {
-        P.dem_list[0] = (int)(tot & 0xFFFF);
-        P.dem_list[1] = (int)(tot >> 16 & 0xFFFF);
-        P.dem_list[2] = (int)(tot >> 32 & 0xFFFF);
-        P.dem_list[3] = (int)(tot >> 48 & 0xFFFF);
+        for (int f = 0; f < 5; f++) P.dem_list[f] = (int)(tot >> (12 * f) & 0xFFF);
     }
 }
 

@@ -39,7 +39,7 @@ struct Layout {
     size_t pairF, pair_on, pair_xi, pair_xm, wall_on, wall_xi, wall_xcw;
     size_t pair_xi_f, pair_xm_f, wall_xi_f, wall_xcw_f;
     size_t sskip, snodes, slinks, scount, smf;  // fixed-geometry sweep (below FP64)
-    size_t dem_list;   // k_dem64_plan's split of the particles [4 + 6P]
+    size_t dem_list;   // k_dem64_plan's split of the particles [kDemListHead + 8P]
     int snode_cap, slink_cap;
     size_t status;
     size_t total;
@@ -139,7 +139,7 @@ void make_layout(const lbm_config *c, Layout *L) {
     L->slinks = take((size_t)L->slink_cap * sizeof(StaticLink));
     L->scount = take(fixed_sweep ? 8 : 0);
     L->smf = take(fixed_sweep ? P * 48 : 0);
-    L->dem_list = take((4 + 6 * P) * 4);
+    L->dem_list = take((kDemListHead + 8 * P) * 4);
     L->status = take(ST_SLOTS * 4);
     L->total = o;
 }
@@ -941,8 +941,9 @@ int lbm_kernels_per_step(const lbm_handle *h) {
     // DEM (particles, n_sub > 0)
     // once the fixed-geometry sweep runs: its link and plain kernels
     const bool geom_static = h->all_fixed && h->static_steps >= kStaticFlagSteps;
-    // the FP64-integrator DEM is three kernels (split, inactive, active)
-    const int dem = h->np > 0 && h->cfg.n_sub > 0 ? (h->dem_mode == DEM_FP64_INTEGRATOR ? 3 : 1) : 0;
+    // the FP64-integrator DEM is five kernels (split, inactive particles,
+    // tiny, small and large contact groups)
+    const int dem = h->np > 0 && h->cfg.n_sub > 0 ? (h->dem_mode == DEM_FP64_INTEGRATOR ? 5 : 1) : 0;
     if (geom_static && h->static_state == 1) return 2 + dem;
     const int flags = geom_static ? 0 : 1;
     if (h->np == 0) return 3 + flags;

@@ -87,6 +87,10 @@ constexpr int kDem32MaxParticles = 256;
 constexpr int kDem32MaxCp = 2048;     // control points of all particles
 constexpr int kDemMaxAdj = 16;        // candidate contact partners per particle and direction
 constexpr int kSmallContactGroup = 32;  // contact groups up to this size run one 32-thread CTA each
+constexpr int kTinyContactGroup = 4;    // ... up to this size one warp each, kTinyGroupsPerCta per CTA
+constexpr int kTinyGroupsPerCta = 8;
+// k_dem64_plan's group classes (dem_groups)
+enum DemGroupClass { DEM_GROUP_TINY = 0, DEM_GROUP_SMALL = 1, DEM_GROUP_LARGE = 2 };
 
 // ---------------------------------------------------------------------------
 // Lattices.  D3Q19 (rest 1/3, axes 1/18, face diagonals 1/36) and the D3Q15
@@ -378,7 +382,7 @@ struct Params {
     float *wall_xi_f, *wall_xcw_f;  // [np*6][3], FP32 DEM: spring, warm start (relative to x_k)
     void *bin_next;    // batched lattices: the other parity's per-step region (cleared by the binning)
     long long bin_next_bytes;
-    int *dem_list;     // [4 + 6 np], k_dem64_plan's split of the particles (dem_free() and below)
+    int *dem_list;     // [8 + 8 np], k_dem64_plan's split of the particles (dem_free() and below)
     int *status;       // [ST_SLOTS], sticky error bits
     int *counters;     // per-step counters, zeroed with the brick lists
     // fixed-geometry sweep (every particle fixed, lattices below FP64): built
@@ -394,13 +398,14 @@ struct Params {
 };
 
 // k_dem64_plan's split of the particles (P.dem_list): [0] inactive count,
-// [1] active count, [2] small contact groups, [3] large ones; then the
-// inactive particles, the active ones group by group, and per small and per
-// large group its (start in the active list, size) pair.
-__host__ __device__ __forceinline__ int *dem_free(const Params &P) { return P.dem_list + 4; }
-__host__ __device__ __forceinline__ int *dem_active(const Params &P) { return P.dem_list + 4 + P.np; }
-__host__ __device__ __forceinline__ int *dem_groups(const Params &P, bool large) {
-    return P.dem_list + 4 + (large ? 4 : 2) * P.np;
+// [1] active count, [2 + c] groups of class c (DemGroupClass), [5..7]
+// unused; then the inactive particles, the active ones group by group, and
+// per group of each class its (start in the active list, size) pair.
+constexpr int kDemListHead = 8;
+__host__ __device__ __forceinline__ int *dem_free(const Params &P) { return P.dem_list + kDemListHead; }
+__host__ __device__ __forceinline__ int *dem_active(const Params &P) { return P.dem_list + kDemListHead + P.np; }
+__host__ __device__ __forceinline__ int *dem_groups(const Params &P, int cls) {
+    return P.dem_list + kDemListHead + (2 + 2 * cls) * P.np;
 }
 
 __host__ __device__ __forceinline__ int dim_of(const Params &P, int a) { return a == 0 ? P.nx : (a == 1 ? P.ny : P.nz); }
