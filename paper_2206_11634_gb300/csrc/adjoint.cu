@@ -17,7 +17,12 @@
 //       plus the drag's direct dependence on the pulled link values;
 //   A2  per fluid node y: dJ/dg+(t)_k(y) = lambda_in_k(y + e_k) (the pull,
 //       transposed) plus the halfway links' and the drag's dependence on the
-//       node's own populations;
+//       node's own populations.  A1 and A2 run as one kernel in push form:
+//       node n stores lambda_in_j(n) straight into dJ/dg+(t)_j(n - e_j) when
+//       n - e_j is a fluid node, and writes dJ/dg+(t) itself in the
+//       directions whose neighbour is solid (its links); every entry of a
+//       fluid node has exactly one writer, and lambda_in is kept only per
+//       link (for A3), so lambda is read and written once per step;
 //   A3  per VIBB link: the link value depends on the node's and x_ff's
 //       populations through their density, momentum and one population each,
 //       and on q: those 11 partial derivatives come from forward-mode dual
@@ -203,6 +208,7 @@ struct AdjDev {
     float *l_q;               // [L]
     double *l_dqdMf, *l_dqdMs;  // [L] dq/dM at x_f and x_s (0 where q was clamped)
     double *l_dJdq;           // [L]
+    float *l_lam;             // [L] lambda_in of the link's direction at its node (this step)
     int nlinks;
     const double *cp;         // [ncp][3] world
     const double *K;          // [ncp]
@@ -366,10 +372,16 @@ __global__ void __launch_bounds__(256) k_adj_step(AdjDev D, const float *__restr
     }
 }
 
-// A1: lambda_in from lambda' = dJ/dg+(t+1) through the collision, plus the
-// drag's dependence on the pulled link values.
-__global__ void __launch_bounds__(256, 3) k_adj_bgk(AdjDev D, const float *__restrict__ S, const float *__restrict__ lamN,
-                                                  float *__restrict__ lamIn, int window) {
+// A1 + A2 in push form (see the top of the file): lambda_in of fluid node n
+// through the collision (with the drag's dependence on the pulled link
+// values), pushed along the pull it came from; on a link direction i the
+// node writes dJ/dg+(t) of its own opposite direction (no fluid neighbour
+// pushes it): the halfway link's value and the drag's dependence on the
+// node's own populations, and keeps lambda_in_i(n) for A3.  The arithmetic
+// and its order are those of the two-kernel form.
+__global__ void __launch_bounds__(256, 3) k_adj_back(AdjDev D, const float *__restrict__ S,
+                                                    const float *__restrict__ lamN, float *__restrict__ lamT,
+                                                    int window) {
     const AdjConst &A = D.c;
     int x, y, z;
     long long n;
@@ -387,61 +399,63 @@ __global__ void __launch_bounds__(256, 3) k_adj_bgk(AdjDev D, const float *__res
         my += gin[i] * L19::e(i, 1);
         mz += gin[i] * L19::e(i, 2);
     }
-    const Dual<4> Dr = dvar<4>(drho, 0), Dmx = dvar<4>(mx, 1), Dmy = dvar<4>(my, 2), Dmz = dvar<4>(mz, 3);
-    float lam[Q], a = 0.f, b[3] = {0.f, 0.f, 0.f};
+    // a = sum_i lambda_i dh_i/d(drho), b = sum_i lambda_i dh_i/dm for
+    // collide_h (h_i = omega g^eq_i + Guo's term, u = (m + F/2) / rho),
+    // differentiated by hand: with P_i = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u,
+    //   dh_i/d(drho) at fixed u = omega w_i (1 + P_i),
+    //   dh_i/du = omega w_i rho (3 e_i + 9 (e_i.u) e_i - 3 u)
+    //             + gfac w_i (9 (e_i.F) e_i - 3 F),
+    // and du/dm = I / rho, du/d(drho) = -u / rho.
+    const float rho = drho + A.rho0, ir = 1.0f / rho;
+    const float ux = (mx + 0.5f * A.F[0]) * ir, uy = (my + 0.5f * A.F[1]) * ir, uz = (mz + 0.5f * A.F[2]) * ir;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    float lam[Q], sp = 0.f, sl = 0.f, v3[3] = {0.f, 0.f, 0.f}, f3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         lam[i] = lamN[(long long)i * A.N + n];
-        const Dual<4> h = collide_h<Dual<4>>(A, i, Dr, Dmx, Dmy, Dmz);
-        a += lam[i] * h.d[0];
-        b[0] += lam[i] * h.d[1];
-        b[1] += lam[i] * h.d[2];
-        b[2] += lam[i] * h.d[3];
+        const int ex = L19::e(i, 0), ey = L19::e(i, 1), ez = L19::e(i, 2);
+        const float lw = lam[i] * (float)L19::w(i);
+        const float eu = ux * (float)ex + uy * (float)ey + uz * (float)ez;
+        sp += lw * (1.0f + (eu * 3.0f + eu * eu * 4.5f - uu * 1.5f));
+        sl += lw;
+        const float c = lw * (3.0f + 9.0f * eu);
+        const float cf = lw * (9.0f * (ex * A.F[0] + ey * A.F[1] + ez * A.F[2]));
+        v3[0] += c * ex; v3[1] += c * ey; v3[2] += c * ez;
+        f3[0] += cf * ex; f3[1] += cf * ey; f3[2] += cf * ez;
     }
+    const float u3[3] = {ux, uy, uz};
+    float b[3], gu = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float g = A.omega * rho * (v3[c] - 3.0f * u3[c] * sl) + A.gfac * (f3[c] - 3.0f * A.F[c] * sl);
+        b[c] = g * ir;
+        gu += g * u3[c];
+    }
+    const float a = A.omega * sp - gu * ir;
 #pragma unroll
     for (int j = 0; j < Q; j++) {
         float v = (1.0f - A.omega) * lam[j] + a + b[0] * L19::e(j, 0) + b[1] * L19::e(j, 1) + b[2] * L19::e(j, 2);
-        if (window && ((lm >> j) & 1u)) v += D.inv_W * (float)L19::e(L19::opp(j), 0);
-        lamIn[(long long)j * A.N + n] = v;
-    }
-}
-
-// A2: dJ/dg+(t) at fluid node y: the pull transposed, the halfway links and
-// the drag's dependence on the node's own populations.
-__global__ void __launch_bounds__(256) k_adj_pull(AdjDev D, const float *__restrict__ lamIn, float *__restrict__ lamT,
-                                                   int window) {
-    const AdjConst &A = D.c;
-    int x, y, z;
-    long long n;
-    if (!node_of(A, x, y, z, n) || D.solid[n]) return;
-    float acc[Q];
-#pragma unroll
-    for (int k = 0; k < Q; k++) {
-        const int tx = wrapi(x + L19::e(k, 0), A.nx), ty = wrapi(y + L19::e(k, 1), A.ny), tz = wrapi(z + L19::e(k, 2), A.nz);
-        const int t = tx + A.nx * (ty + A.ny * tz);
-        // the neighbour's value and its solid mark in one round
-        const float v = lamIn[(long long)k * A.N + t];
-        acc[k] = D.solid[t] ? 0.f : v;
-    }
-    const uint32_t lm = D.lmask[n];
-    if (lm) {
-#pragma unroll
-        for (int io = 1; io < Q; io++) {
-            const int i = L19::opp(io);  // the link's unknown direction
-            if (!((lm >> i) & 1u)) continue;
-            const int L = D.linkid[(long long)i * A.N + n];
-            if (D.l_nff[L] < 0) acc[io] += lamIn[(long long)i * A.N + n];
-            if (window) acc[io] += D.inv_W * (float)L19::e(io, 0);
+        if ((lm >> j) & 1u) {
+            // link j: x - e_j is solid; lamT_{opp j}(n) has no other writer
+            if (window) v += D.inv_W * (float)L19::e(L19::opp(j), 0);
+            const int L = D.linkid[(long long)j * A.N + n];
+            D.l_lam[L] = v;
+            const int io = L19::opp(j);
+            float acc = 0.f;
+            if (D.l_nff[L] < 0) acc += v;
+            if (window) acc += D.inv_W * (float)L19::e(io, 0);
+            lamT[(long long)io * A.N + n] = acc;
+        } else {
+            const int tx = wrapi(x - L19::e(j, 0), A.nx), ty = wrapi(y - L19::e(j, 1), A.ny),
+                      tz = wrapi(z - L19::e(j, 2), A.nz);
+            lamT[(long long)j * A.N + (tx + A.nx * (ty + (long long)A.ny * tz))] = v;
         }
     }
-#pragma unroll
-    for (int k = 0; k < Q; k++) lamT[(long long)k * A.N + n] = acc[k];
 }
 
 // A3: the VIBB links (x_ff fluid): 11 partial derivatives by dual numbers,
 // scattered into dJ/dg+(t) at x_f and x_ff, and dJ/dq of the link.
-__global__ void __launch_bounds__(128) k_adj_vibb(AdjDev D, const float *__restrict__ S,
-                                                   const float *__restrict__ lamIn, float *__restrict__ lamT) {
+__global__ void __launch_bounds__(128) k_adj_vibb(AdjDev D, const float *__restrict__ S, float *__restrict__ lamT) {
     const AdjConst &A = D.c;
     const long long N = A.N;
     for (int L = blockIdx.x * blockDim.x + threadIdx.x; L < D.nlinks; L += gridDim.x * blockDim.x) {
@@ -449,7 +463,7 @@ __global__ void __launch_bounds__(128) k_adj_vibb(AdjDev D, const float *__restr
         if (nff < 0) continue;
         const long long nf = D.l_nf[L];
         const int i = D.l_dir[L], io = L19::opp(i);
-        const float lam = lamIn[(long long)i * N + nf];
+        const float lam = D.l_lam[L];
         if (lam == 0.f) continue;
         float drf = 0.f, mf[3] = {0.f, 0.f, 0.f}, gf = 0.f, drff = 0.f, mff[3] = {0.f, 0.f, 0.f}, gff = 0.f;
 #pragma unroll
@@ -529,7 +543,7 @@ struct lbm_adj {
     size_t S;                // bytes of one state (19 N floats)
     char *ws;
     cudaStream_t stream;
-    size_t o_state[2], o_ckpt, o_seg, o_lam[2], o_lamin, o_solid, o_lmask, o_linkid, o_lnf, o_ldir, o_lnff, o_lq,
+    size_t o_state[2], o_ckpt, o_seg, o_lam[2], o_llam, o_solid, o_lmask, o_linkid, o_lnf, o_ldir, o_lnff, o_lq,
         o_dqf, o_dqs, o_dJdq, o_cp, o_K, o_J, o_grad, total;
     bool have_forward;
     char err[256];
@@ -644,7 +658,7 @@ void adj_layout(lbm_adj *a) {
     a->o_seg = take(a->S * (size_t)std::max(1, a->K - 1));
     a->o_lam[0] = take(a->S);
     a->o_lam[1] = take(a->S);
-    a->o_lamin = take(a->S);
+    a->o_llam = take(L * 4);
     a->o_solid = take(N);
     a->o_lmask = take(N * 4);
     a->o_linkid = take(N * Q * 4);
@@ -693,6 +707,7 @@ AdjDev adj_dev(lbm_adj *a) {
     D.l_dqdMf = reinterpret_cast<double *>(w + a->o_dqf);
     D.l_dqdMs = reinterpret_cast<double *>(w + a->o_dqs);
     D.l_dJdq = reinterpret_cast<double *>(w + a->o_dJdq);
+    D.l_lam = reinterpret_cast<float *>(w + a->o_llam);
     D.nlinks = a->nlinks;
     D.cp = reinterpret_cast<const double *>(w + a->o_cp);
     D.K = reinterpret_cast<const double *>(w + a->o_K);
@@ -821,7 +836,7 @@ int lbm_adj_backward(lbm_adj *a, double *dJ_dcp, double *dJ_dK) {
     if (rc == LBM_OK) rc = acheck(a, cudaMemsetAsync(a->ws + a->o_lam[0], 0, a->S, a->stream), "cudaMemsetAsync");
     if (rc == LBM_OK) rc = acheck(a, cudaMemsetAsync(a->ws + a->o_grad, 0, (size_t)a->ncp * 32, a->stream), "cudaMemsetAsync");
     if (rc != LBM_OK) return rc;
-    float *lamN = state(a, a->o_lam[0]), *lamT = state(a, a->o_lam[1]), *lamIn = state(a, a->o_lamin);
+    float *lamN = state(a, a->o_lam[0]), *lamT = state(a, a->o_lam[1]);
     const dim3 grid = node_grid(a);
     const int lgrid = std::max(1, std::min(1024, (a->nlinks + 127) / 128));
     for (int c = a->C - 1; c >= 0; c--) {
@@ -836,9 +851,8 @@ int lbm_adj_backward(lbm_adj *a, double *dJ_dcp, double *dJ_dK) {
         for (int t = t1 - 1; t >= t0; t--) {
             const int window = t >= a->T - a->W ? 1 : 0;
             const float *S = seg[(size_t)(t - t0)];
-            k_adj_bgk<<<grid, 256, 0, a->stream>>>(D, S, lamN, lamIn, window);
-            k_adj_pull<<<grid, 256, 0, a->stream>>>(D, lamIn, lamT, window);
-            if (a->nlinks > 0) k_adj_vibb<<<lgrid, 128, 0, a->stream>>>(D, S, lamIn, lamT);
+            k_adj_back<<<grid, 256, 0, a->stream>>>(D, S, lamN, lamT, window);
+            if (a->nlinks > 0) k_adj_vibb<<<lgrid, 128, 0, a->stream>>>(D, S, lamT);
             std::swap(lamN, lamT);
         }
     }
