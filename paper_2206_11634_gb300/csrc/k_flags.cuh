@@ -89,6 +89,7 @@ __device__ __forceinline__ void flags_brick(const Params &P, SmemParticles &sp, 
         int own_s = -1;
         double own_M = -1.0;  // FP64 M of the current owner, < 0 until computed
         for (int s = 0; s < cnt; s++) {
+            if (!in_bound(P, sp, s, lx, ly, lz)) continue;  // outside s: M < c0 there
             bool unsure;
             const float M = metaball32(P, sp, s, (float)lx, (float)ly, (float)lz, unsure);
             bool inside;

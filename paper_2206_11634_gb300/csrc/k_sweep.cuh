@@ -718,6 +718,9 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
         const int owner = (int)nf[0] - 1;
         for (int s = 0; s < sp.n; s++) {
             const int j = sp.id[s];
+            // a node outside another particle's bounding sphere is not inside
+            // it: solid_links would find nothing
+            if (j != owner && !in_bound(P, sp, s, lx, ly, lz)) continue;
             uint32_t cand = 0;
 #pragma unroll
             for (int i = 1; i < Q; i++) {

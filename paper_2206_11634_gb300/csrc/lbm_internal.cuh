@@ -547,7 +547,23 @@ struct SmemParticles {
     float K[MAXPB][MAXCP];
     float prel[MAXPB][3];  // centroid relative to the brick origin
     float v[MAXPB][3], w[MAXPB][3];
+    float brad2[MAXPB];    // (bounding radius + 1)^2: no node farther from the centroid lies inside
 };
+
+// Whether brick-local node (lx,ly,lz) may lie inside listed particle s: within
+// its bounding sphere (M >= c0 forces min_k |x - x_k|^2 <= sum K / c0, so a
+// solid node lies within max_k |x_k - x_c| + sqrt(sum K / c0) of the
+// centroid; the radius carries R_s and one node more, which covers the FP32
+// rounding).  A node outside needs no evaluation of M for s.
+__device__ __forceinline__ bool in_bound(const Params &P, const SmemParticles &sp, int s, int lx, int ly, int lz) {
+    float dx = (float)lx - sp.prel[s][0], dy = (float)ly - sp.prel[s][1], dz = (float)lz - sp.prel[s][2];
+    // nearest periodic image, as metaball32 takes it per control point
+    const float Lx = (float)P.nx, Ly = (float)P.ny, Lz = (float)P.nz;
+    if (P.per[0]) { if (dx > 0.5f * Lx) dx -= Lx; else if (dx < -0.5f * Lx) dx += Lx; }
+    if (P.per[1]) { if (dy > 0.5f * Ly) dy -= Ly; else if (dy < -0.5f * Ly) dy += Ly; }
+    if (P.per[2]) { if (dz > 0.5f * Lz) dz -= Lz; else if (dz < -0.5f * Lz) dz += Lz; }
+    return dx * dx + dy * dy + dz * dz <= sp.brad2[s];
+}
 
 // FP32 M of listed particle s at brick-local integer offset (lx,ly,lz) plus a
 // fractional offset; `unsure` is set when the FP32 value cannot decide
@@ -625,6 +641,7 @@ __device__ inline void load_particle_records(const Params &P, SmemParticles &sp,
                 sp.v[s][a] = p.vw_f[a];
                 sp.w[s][a] = p.vw_f[3 + a];
             }
+            sp.brad2[s] = (p.brad_f + 1.0f) * (p.brad_f + 1.0f);
         }
         for (int a = 0; a < 3; a++)
             sp.crel[s][k][a] = minimg_rel_f(P, a, df_minus_int(p.cpw_hl[k][a], org[a]), half[a]);

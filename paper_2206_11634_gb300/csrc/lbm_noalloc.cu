@@ -82,15 +82,19 @@ extern "C" int lbm_flags_noalloc(const lbm_config *cfg, const lbm_particle *host
         for (int a = 0; a < 4; a++) d.q[a] = p.q[a] / qn;
         for (int a = 0; a < 3; a++) { d.x[a] = p.x[a]; d.v[a] = p.v[a]; d.w[a] = p.w[a]; }
         d.ncp = p.n_cp;
-        double Ks = 0.0;
+        double Ks = 0.0, rmax = 0.0;
         for (int k = 0; k < p.n_cp; k++) {
             if (!(p.K[k] >= 0.0)) return LBM_ERR_BAD_ARG;
             for (int a = 0; a < 3; a++) d.cpb[k][a] = p.cp[k][a];
             d.K[k] = p.K[k];
             d.K_f[k] = (float)p.K[k];  // the sweeps' and flag pass's FP32 copy
             Ks += p.K[k];
+            rmax = std::fmax(rmax, std::sqrt(p.cp[k][0] * p.cp[k][0] + p.cp[k][1] * p.cp[k][1] + p.cp[k][2] * p.cp[k][2]));
         }
         d.sumK = Ks;
+        // bounding radius about x (the flag pass skips nodes outside it)
+        d.brad = rmax + std::sqrt(Ks / cfg->c0) + p.Rs;
+        d.brad_f = (float)d.brad;
     }
 
     cudaError_t e = cudaSuccess;
