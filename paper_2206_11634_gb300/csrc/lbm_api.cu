@@ -151,8 +151,18 @@ thread_local char g_init_error[256] = "no error";
 constexpr int kProfKernels = 6;
 constexpr int kProfCap = 65536;
 
+// Principal axes of a particle's inertia tensor, kept per particle slot so
+// that lbm_set_particles with an unchanged tensor (every call of a run that
+// feeds back the state) skips the eigen-decomposition.
+struct InertiaCache {
+    double key[9];            // the tensor decomposed
+    double Ip[3], U[9], qU[4];
+    bool valid;
+};
+
 struct lbm_handle {
     lbm_config cfg;
+    std::vector<InertiaCache> icache;  // [max_particles]
     // Each lbm_step() call forks two library streams from `stream` and joins
     // them back: `hi` (highest priority) runs the latency-bound chain (binning,
     // flags, near sweep, force reduction, DEM), `aux` (lowest priority) the
@@ -636,7 +646,14 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
     if (n < 0 || (n > 0 && !host)) return fail(h, LBM_ERR_BAD_ARG, "bad particle array");
     if (n > h->cfg.max_particles)
         return fail(h, LBM_ERR_CAPACITY, "%d particles, capacity %d", n, h->cfg.max_particles);
-    std::vector<DevParticle> dev((size_t)(n > 0 ? n : 1));
+    // the table is built in place in the page-locked buffer, once its
+    // previous upload is done, and goes up from there
+    if (n > 0 && h->pin_busy) {
+        const int rc0 = cuda_check(h, cudaEventSynchronize(h->ev_pin), "cudaEventSynchronize");
+        if (rc0 != LBM_OK) return rc0;
+        h->pin_busy = false;
+    }
+    DevParticle *dev = reinterpret_cast<DevParticle *>(h->pin + ST_SLOTS * 4 + (size_t)h->cfg.max_particles * 96);
     int nc_total = 0;
     for (int j = 0; j < n; j++) {
         lbm_particle p = host[j];
@@ -668,8 +685,21 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
         d.Rs = p.Rs;
         // principal frame: I_user = U diag(Ip) U^T, q_principal = q_user (x) q(U)
         double Ip[3], U[9], qU[4];
-        jacobi3(p.inertia, Ip, U);
-        matrix_quat(U, qU);
+        if (h->icache.size() != (size_t)h->cfg.max_particles) h->icache.assign((size_t)h->cfg.max_particles, InertiaCache{});
+        InertiaCache &ic = h->icache[(size_t)j];
+        if (ic.valid && std::memcmp(ic.key, p.inertia, sizeof(ic.key)) == 0) {
+            std::memcpy(Ip, ic.Ip, sizeof(Ip));
+            std::memcpy(U, ic.U, sizeof(U));
+            std::memcpy(qU, ic.qU, sizeof(qU));
+        } else {
+            jacobi3(p.inertia, Ip, U);
+            matrix_quat(U, qU);
+            std::memcpy(ic.key, p.inertia, sizeof(ic.key));
+            std::memcpy(ic.Ip, Ip, sizeof(Ip));
+            std::memcpy(ic.U, U, sizeof(U));
+            std::memcpy(ic.qU, qU, sizeof(qU));
+            ic.valid = true;
+        }
         for (int a = 0; a < 9; a++) d.Iu[a] = p.inertia[a];
         for (int a = 0; a < 4; a++) d.qU[a] = qU[a];
         quat_mul(p.q, qU, d.q);
@@ -731,15 +761,10 @@ int lbm_set_particles(lbm_handle *h, const lbm_particle *host, int n) {
     else h->dem_mode = DEM_FP64_INTEGRATOR;
     int rc = LBM_OK;
     if (n > 0) {
-        // through the page-locked buffer (once its previous upload is done),
-        // so the call returns without waiting for the stream
-        if (h->pin_busy) rc = cuda_check(h, cudaEventSynchronize(h->ev_pin), "cudaEventSynchronize");
-        DevParticle *staged = reinterpret_cast<DevParticle *>(h->pin + ST_SLOTS * 4 + (size_t)h->cfg.max_particles * 96);
-        if (rc == LBM_OK) {
-            std::memcpy(staged, dev.data(), sizeof(DevParticle) * (size_t)n);
-            rc = cuda_check(h, cudaMemcpyAsync(h->ws + h->L.parts, staged, sizeof(DevParticle) * (size_t)n,
-                                               cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(particles)");
-        }
+        // asynchronous upload from the page-locked buffer: the call returns
+        // without waiting for the stream
+        rc = cuda_check(h, cudaMemcpyAsync(h->ws + h->L.parts, dev, sizeof(DevParticle) * (size_t)n,
+                                           cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(particles)");
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventRecord(h->ev_pin, h->stream), "cudaEventRecord");
         h->pin_busy = rc == LBM_OK;
     }
