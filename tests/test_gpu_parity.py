@@ -465,6 +465,39 @@ def test_free_rotation(pkg, oracle_mod, W, storage, n_sub, w0, dem_mode):
     assert np.abs(so["w"] - np.array([w0, -0.6 * w0, 0.3 * w0])).max() > 1e-3 * w0
 
 
+def test_set_particles_new_inertia(pkg, oracle_mod, W):
+    """lbm_set_particles keeps each slot's principal-axes decomposition while
+    its inertia tensor stays the same; a new tensor in the same slot is
+    decomposed again.  After a first set of particles and two steps, the slot
+    gets another tensor (same shape and pose): the torque-free rotation that
+    follows agrees with the oracle's for that tensor to rounding (FP64
+    integrator), which a reused decomposition would not."""
+    I1 = np.array([[40.0, 3.0, -2.0], [3.0, 25.0, 1.5], [-2.0, 1.5, 12.0]])
+    I2 = np.array([[18.0, -4.0, 1.0], [-4.0, 33.0, 2.5], [1.0, 2.5, 27.0]])
+    wl = W.empty_box(16, "f32", (1, 1, 1))
+    wl.update(n_sub=100, gravity=(0.0, 0.0, -1e-4))
+
+    def parts(inertia):
+        return [W._particle([[0.0, 0.0, 0.0], [1.0, 0.5, 0.0]], [4e4, 1e4], (8.3, 7.9, 8.1),
+                            q=(0.9, 0.1, -0.3, 0.2), v=(0.01, 0.0, 0.0), w=(0.02, -0.012, 0.006),
+                            density=2.0, mass=500.0, inertia=inertia)]
+    wl["particles"] = parts(I1)
+    gpu = H.make_gpu(pkg, wl, dem_mode=0)
+    gpu.set_particles(H.gpu_particles(pkg, wl))
+    gpu.step(2)
+    wl["particles"] = parts(I2)
+    gpu.set_particles(H.gpu_particles(pkg, wl))
+    orc = H.make_oracle(oracle_mod, wl)
+    orc.set_particles(H.oracle_particles(oracle_mod, wl))
+    for _ in range(5):
+        gpu.step(1)
+        orc.step(1)
+    sg, so = gpu.particles()[0], orc.get_particles()[0]
+    qg = sg["q"] * np.sign(np.dot(sg["q"], so["q"]))
+    assert np.abs(qg - so["q"]).max() < 1e-12
+    assert np.abs(sg["w"] - so["w"]).max() < 1e-12 * 0.02
+
+
 def test_full_size_settling_metaball_one_step(pkg, oracle_mod, W):
     """Workload 2 at its full 128x128x256 size in the benchmark's launch
     configuration: one step from a perturbed state, every fluid node and the
