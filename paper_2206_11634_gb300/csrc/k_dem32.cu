@@ -118,6 +118,7 @@ struct SharedT {
     float Fc[CAP][3], Tc[CAP][3];   // contact force / torque of the last evaluation
     float brad[CAP], Rs[CAP], reach[CAP];
     float4 rc[CPS];                 // control points R(q) cpb relative to x, and K
+    float4 rc_pad[kWarpGroup ? 32 : 1];  // warp tables: where lanes without a control point store theirs
     float4 cpb[kCpb ? CPS : 1];     // control points in the body frame, and K (put_rc's input)
     int cpo[CAP + 1];               // offsets into rc
     unsigned bits[CAP][(CAP + 31) / 32];  // candidate pairs (i < j)
@@ -141,7 +142,7 @@ using Shared = SharedT<kMaxP, kMaxItems, kDem32MaxCp, false, false>;
 using SharedSmall = SharedT<kSmallContactGroup, 256, kSmallContactGroup * MAXCP, true, false>;
 // a contact group of up to kTinyContactGroup particles (one warp each,
 // kTinyGroupsPerCta tables per CTA; at most 6 candidate pairs)
-using SharedTiny = SharedT<kTinyContactGroup, 8, kTinyContactGroup * MAXCP, true, true>;
+using SharedTiny = SharedT<kTinyContactGroup, 8, kTinyContactGroup * MAXCP, false, true>;
 
 // The threads that share one table: the CTA, or for warp tables the warp.
 template <class SH> __device__ __forceinline__ int gtid() { return SH::kWarp ? (int)(threadIdx.x & 31) : (int)threadIdx.x; }
@@ -168,8 +169,9 @@ __device__ __forceinline__ void rel_vec(const SH &S, const Params &P, int i, int
 struct MbSum {
     float M, g0, g1, g2, h0, h1, h2, h3, h4, h5;
 };
-__device__ __forceinline__ void mb_acc(const float4 cp, const float off[3], const float y[3], MbSum &A) {
-    const float r0 = y[0] - (cp.x + off[0]), r1 = y[1] - (cp.y + off[1]), r2_ = y[2] - (cp.z + off[2]);
+// the terms of one control point (position cp.xyz, weight cp.w) at y
+__device__ __forceinline__ void mb_acc0(const float4 cp, const float y[3], MbSum &A) {
+    const float r0 = y[0] - cp.x, r1 = y[1] - cp.y, r2_ = y[2] - cp.z;
     const float r2 = r0 * r0 + r1 * r1 + r2_ * r2_;
     const float ir = __fdividef(1.0f, r2);
     const float Kr = cp.w * ir;            // K / r^2
@@ -185,6 +187,10 @@ __device__ __forceinline__ void mb_acc(const float4 cp, const float off[3], cons
     A.h3 = fmaf(a2 * r0, r1, A.h3);
     A.h4 = fmaf(a2 * r0, r2_, A.h4);
     A.h5 = fmaf(a2 * r1, r2_, A.h5);
+}
+// ... of a control point at cp.xyz + off
+__device__ __forceinline__ void mb_acc(const float4 cp, const float off[3], const float y[3], MbSum &A) {
+    mb_acc0(make_float4(cp.x + off[0], cp.y + off[1], cp.z + off[2], cp.w), y, A);
 }
 __device__ __forceinline__ void mb_dd_f(const float4 *rc, int ncp, const float off[3], const float y[3], float &M,
                                         float g[3], float H[6]) {
@@ -532,9 +538,9 @@ __device__ void pair_contacts(const Params &P, SH &S, float h) {
     }
 }
 
-// Per particle: pair terms in index order, then the walls.
+// Per particle: its pair terms, in index order.
 template <class SH>
-__device__ void gather_contacts(const Params &P, SH &S, int k, float h, float F[3], float T[3]) {
+__device__ __forceinline__ void gather_pairs(const SH &S, int k, float F[3], float T[3]) {
     for (int a = 0; a < 3; a++) { F[a] = 0.f; T[a] = 0.f; }
     for (int e = 0; e < S.ndn[k]; e++) {
         const int m = S.dn[k][e] >> 8, s = S.dn[k][e] & 255;
@@ -547,6 +553,12 @@ __device__ void gather_contacts(const Params &P, SH &S, int k, float h, float F[
         if (it >= SH::kItems) break;
         for (int a = 0; a < 3; a++) { F[a] += S.it_res[it][a]; T[a] += S.it_res[it][3 + a]; }
     }
+}
+
+// Per particle: pair terms in index order, then the walls.
+template <class SH>
+__device__ void gather_contacts(const Params &P, SH &S, int k, float h, float F[3], float T[3]) {
+    gather_pairs(S, k, F, T);
     for (int wall = 0; wall < NWALL; wall++) {
         const int ax = wall / 2, side = wall % 2;
         if (P.per[ax]) { S.w_on[k][wall] = 0; continue; }
@@ -930,21 +942,18 @@ struct Delta {
 __device__ __forceinline__ void dl_set(Delta &a, double v) { a.bf = (float)v; a.d = {0.f, 0.f}; }
 __device__ __forceinline__ void dl_add(Delta &a, float b) { a.d = df_add(a.d, b); }
 
-// The contact groups of k_dem64_plan by class: groups of up to 4 particles
-// one warp each with tables sized for them (8 groups per CTA, the barriers
-// warp-wide), up to 32 one 32-thread CTA each, larger ones one 512-thread
-// CTA each with the full tables.
+// The contact groups of k_dem64_plan with more than kTinyContactGroup
+// particles (the smaller ones: k_dem64t below): up to 32 one 32-thread CTA
+// each, larger ones one 512-thread CTA each with the full tables; a thread
+// per particle.
 template <class SH, int kClass>
-__global__ void __launch_bounds__(kClass == DEM_GROUP_LARGE   ? kThreads
-                                  : kClass == DEM_GROUP_SMALL ? kSmallContactGroup
-                                                              : 32 * kTinyGroupsPerCta,
-                                  1) k_dem64c(Params P) {
+__global__ void __launch_bounds__(kClass == DEM_GROUP_LARGE ? kThreads : kSmallContactGroup, 1) k_dem64c(Params P) {
+    static_assert(kClass != DEM_GROUP_TINY && !SH::kWarp, "groups of up to kTinyContactGroup: k_dem64t");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int wt = SH::kWarp ? (int)(threadIdx.x >> 5) : 0;  // the warp's table (warp tables)
-    SH &S = reinterpret_cast<SH *>(smem_raw)[wt];
-    const int tid = gtid<SH>();
-    const int slot = SH::kWarp ? (int)blockIdx.x * kTinyGroupsPerCta + wt : (int)blockIdx.x;
-    if (slot >= P.dem_list[2 + kClass]) return;  // (a whole warp, or the whole CTA)
+    SH &S = *reinterpret_cast<SH *>(smem_raw);
+    const int tid = (int)threadIdx.x;
+    const int slot = (int)blockIdx.x;
+    if (slot >= P.dem_list[2 + kClass]) return;  // the whole CTA
     const int *grp = dem_groups(P, kClass) + 2 * slot;
     const int na = grp[1];
     const int *act = dem_active(P) + grp[0];
@@ -1172,6 +1181,588 @@ __global__ void __launch_bounds__(kClass == DEM_GROUP_LARGE   ? kThreads
     if (na > 1) store_items(P, S);
 }
 
+// ---------------------------------------------------------------------------
+// Contact groups of up to four particles, one warp each (k_dem64t).  Lane
+// kSegLanes * k + c works for particle k of the group (for k past the group's
+// size: particle k mod size, as a mirror): the particle's lanes all hold its
+// state (they integrate it from the same inputs in the same order, so they
+// hold the same bits) and lane c holds its control points c and
+// c + kSegLanes (a lane without one holds a point far away with weight zero,
+// whose terms are exact zeros).  The metaball sums of a wall contact run over
+// the particle's lanes and those of a pair contact over the whole warp
+// (sixteen lanes per metaball), each reduced by an xor butterfly, after which
+// every lane of the group holds the same sums; the Newton steps' decisions
+// are still taken from the group's first lane, so that the lanes of a group
+// stay together through every exchange.  Since every lane that writes a
+// table entry writes the same bits there, the stores need no lane test (and
+// the warp no branch around them); only the particles' own lanes write to
+// global memory.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kSegLanes = 32 / kTinyContactGroup;  // lanes per particle
+static_assert(2 * kSegLanes >= MAXCP, "two control points per lane of a particle");
+static_assert(16 >= MAXCP, "one control point per lane in a pair solve");
+constexpr unsigned kFullWarp = 0xffffffffu;
+// stand-in for a missing control point: its terms vanish (K = 0) and r^2 stays
+// far from zero
+__device__ __forceinline__ float4 far_cp() { return make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f); }
+
+// Butterfly sum of the metaball terms over groups of W lanes.
+template <int W>
+__device__ __forceinline__ void mb_bfly(MbSum &A, unsigned mask) {
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) {
+        A.M += __shfl_xor_sync(mask, A.M, o, W);
+        A.g0 += __shfl_xor_sync(mask, A.g0, o, W);
+        A.g1 += __shfl_xor_sync(mask, A.g1, o, W);
+        A.g2 += __shfl_xor_sync(mask, A.g2, o, W);
+        A.h0 += __shfl_xor_sync(mask, A.h0, o, W);
+        A.h1 += __shfl_xor_sync(mask, A.h1, o, W);
+        A.h2 += __shfl_xor_sync(mask, A.h2, o, W);
+        A.h3 += __shfl_xor_sync(mask, A.h3, o, W);
+        A.h4 += __shfl_xor_sync(mask, A.h4, o, W);
+        A.h5 += __shfl_xor_sync(mask, A.h5, o, W);
+    }
+}
+__device__ __forceinline__ void mb_unpack(const MbSum &A, float &M, float g[3], float H[6]) {
+    M = A.M;
+    g[0] = A.g0; g[1] = A.g1; g[2] = A.g2;
+    H[0] = A.h0; H[1] = A.h1; H[2] = A.h2; H[3] = A.h3; H[4] = A.h4; H[5] = A.h5;
+}
+
+// Newton decision of one step, the same in every lane of a group: 1 singular
+// Jacobian (stop before the step), 2 converged, 3 no longer shrinking, 0 go on.
+__device__ __forceinline__ int newton_code(bool bad, float s2, float prev, int it) {
+    return bad ? 1 : (s2 < kNewtonTol2 ? 2 : ((it >= 3 && s2 >= prev) ? 3 : 0));
+}
+
+// Wall geometry of Eqs. (10)-(13), the steps of wall_geom_f, run by the
+// particle's lanes (mask); ca, cb: this lane's rotated control points.
+template <int AX, class SH>
+__device__ __forceinline__ bool wall_geom_seg(const Params &P, const SH &S, int k, int side, float prel, bool warm,
+                                              float xcw[3], float &delta, float nv[3], float xcp[3], bool &valid,
+                                              unsigned mask, const float4 ca, const float4 cb) {
+    constexpr int ax = AX, t1 = (AX + 1) % 3, t2 = (AX + 2) % 3;
+    const float m_ax = side ? 1.0f : -1.0f;
+    float x[3];
+    if (warm) {
+        for (int a = 0; a < 3; a++) x[a] = xcw[a];
+    } else {  // the control point nearest the plane (every lane scans the table)
+        const float4 *rc = S.rc + S.cpo[k];
+        const int nc = S.cpo[k + 1] - S.cpo[k];
+        int kb = 0;
+        float best = 3.4e38f;
+        for (int c = 0; c < nc; c++) {
+            const float pc = ax == 0 ? rc[c].x : (ax == 1 ? rc[c].y : rc[c].z);
+            const float dd = fabsf(prel - pc);
+            if (dd < best) { best = dd; kb = c; }
+        }
+        x[0] = rc[kb].x; x[1] = rc[kb].y; x[2] = rc[kb].z;
+    }
+    x[ax] = prel;
+    constexpr int i11 = t1, i22 = t2, i12 = t1 + t2 == 1 ? 3 : (t1 + t2 == 2 ? 4 : 5);
+    float M, g[3], H[6], xe[3];
+    float prev = 3.4e38f;
+    bool converged = false;
+    valid = false;
+    for (int it = 0;; it++) {
+        MbSum A = {};
+        mb_acc0(ca, x, A);
+        mb_acc0(cb, x, A);
+        mb_bfly<kSegLanes>(A, mask);
+        mb_unpack(A, M, g, H);
+        for (int a = 0; a < 3; a++) xe[a] = x[a];
+        if (it == kNewtonMax) break;
+        const float J00 = H[i11], J01 = H[i12], J11 = H[i22];
+        const float det = J00 * J11 - J01 * J01;
+        const float id = __frcp_rn(det);
+        const float r0 = -g[t1], r1 = -g[t2];
+        const float d0 = (J11 * r0 - J01 * r1) * id, d1 = (-J01 * r0 + J00 * r1) * id;
+        const float s2 = d0 * d0 + d1 * d1;
+        const int code = __shfl_sync(mask, newton_code(det == 0.f || !isfinite(det), s2, prev, it), 0, kSegLanes);
+        if (code == 1) break;
+        x[t1] += d0;
+        x[t2] += d1;
+        if (code == 2) { converged = true; break; }
+        if (code == 3) break;
+        prev = s2;
+    }
+    for (int a = 0; a < 3; a++) xcw[a] = x[a];
+    if (!(g[ax] * m_ax < 0.f)) return false;
+    valid = converged;
+    const float qR = (1.0f - M) * __frcp_rn(dot3f(g, g));
+    float dc[3];
+    for (int a = 0; a < 3; a++) dc[a] = qR * g[a];
+    const float dist = sqrtf(dot3f(dc, dc));
+    delta = S.Rs[k] - dist;
+    if (!(delta > 0.f) || dist == 0.f) return false;
+    const float idist = __frcp_rn(dist);
+    for (int a = 0; a < 3; a++) {
+        nv[a] = dc[a] * idist;
+        xcp[a] = xe[a] - 0.5f * delta * nv[a];
+    }
+    return true;
+}
+
+// The walls' terms of particle k added to F, T (after its pair terms), run by
+// the particle's lanes (mask), which all write the contact history.
+template <class SH>
+__device__ void walls_seg(const Params &P, SH &S, int k, unsigned mask, float h, const float4 ca, const float4 cb,
+                          float F[3], float T[3]) {
+    for (int wall = 0; wall < NWALL; wall++) {
+        const int ax = wall / 2, side = wall % 2;
+        if (P.per[ax]) {
+            S.w_on[k][wall] = 0;
+            continue;
+        }
+        const float plane = side ? P.dim_f[ax] - 0.5f : -0.5f;
+        const float prel = (plane - S.xh[k][ax]) - S.xl[k][ax];
+        const int was = S.w_on[k][wall];
+        float xcw[3], xi[3];
+        for (int a = 0; a < 3; a++) {
+            xcw[a] = S.w_xcw[k][wall][a];
+            xi[a] = (was & CONTACT_ON) ? S.w_xi[k][wall][a] : 0.f;
+        }
+        const int go = __shfl_sync(mask, fabsf(prel) > S.brad[k] ? 0 : 1, 0, kSegLanes);
+        if (!go) {
+            __syncwarp(mask);
+            S.w_on[k][wall] = 0;
+            continue;
+        }
+        float delta, nv[3], xcp[3];
+        bool valid;
+        const bool start = (was & CONTACT_WARM) != 0;
+        const bool hit =
+            ax == 0   ? wall_geom_seg<0>(P, S, k, side, prel, start, xcw, delta, nv, xcp, valid, mask, ca, cb)
+            : ax == 1 ? wall_geom_seg<1>(P, S, k, side, prel, start, xcw, delta, nv, xcp, valid, mask, ca, cb)
+                      : wall_geom_seg<2>(P, S, k, side, prel, start, xcw, delta, nv, xcp, valid, mask, ca, cb);
+        const int warm = valid ? CONTACT_WARM : 0;
+        if (hit) {
+            float wr[3], vi[3], Fi[3], ti[3];
+            cross3f(S.w[k], xcp, wr);
+            for (int a = 0; a < 3; a++) vi[a] = S.v[k][a] + wr[a];
+            contact_law_f(P, delta, nv, vi, xi, h, Fi);
+            cross3f(xcp, Fi, ti);
+            for (int a = 0; a < 3; a++) { F[a] += Fi[a]; T[a] += ti[a]; }
+        }
+        __syncwarp(mask);
+        for (int a = 0; a < 3; a++) S.w_xcw[k][wall][a] = xcw[a];
+        S.w_on[k][wall] = hit ? (warm | CONTACT_ON) : warm;
+        if (hit)
+            for (int a = 0; a < 3; a++) S.w_xi[k][wall][a] = xi[a];
+    }
+}
+
+// Pair geometry of Eqs. (5)-(9), the steps of pair_geom_f, run by the whole
+// warp: lanes 0-15 hold the control points of particle i, lanes 16-31 those
+// of particle j.
+template <class SH>
+__device__ bool pair_geom_w(const Params &P, const SH &S, int i, int j, const float d[3], bool warm, float xm[3],
+                            float &delta, float nv[3], float xcp[3], bool &valid) {
+    const int lane = threadIdx.x & 31, half = lane >> 4, cc = lane & 15;
+    const int m = half ? j : i;
+    const int ncm = S.cpo[m + 1] - S.cpo[m];
+    const float4 cp = cc < ncm ? S.rc[S.cpo[m] + cc] : far_cp();
+    const float off[3] = {half ? d[0] : 0.f, half ? d[1] : 0.f, half ? d[2] : 0.f};
+    float x[3];
+    if (warm) {
+        for (int a = 0; a < 3; a++) x[a] = xm[a];
+    } else {  // midpoint of the closest pair of control points (every lane scans the tables)
+        const float4 *rci = S.rc + S.cpo[i];
+        const float4 *rcj = S.rc + S.cpo[j];
+        const int nci = S.cpo[i + 1] - S.cpo[i], ncj = S.cpo[j + 1] - S.cpo[j];
+        float best = 3.4e38f;
+        x[0] = x[1] = x[2] = 0.f;
+        for (int a = 0; a < nci; a++)
+            for (int b = 0; b < ncj; b++) {
+                const float dd[3] = {(d[0] + rcj[b].x) - rci[a].x, (d[1] + rcj[b].y) - rci[a].y,
+                                     (d[2] + rcj[b].z) - rci[a].z};
+                const float d2 = dot3f(dd, dd);
+                if (d2 < best) {
+                    best = d2;
+                    x[0] = rci[a].x + 0.5f * dd[0];
+                    x[1] = rci[a].y + 0.5f * dd[1];
+                    x[2] = rci[a].z + 0.5f * dd[2];
+                }
+            }
+    }
+    float M0, g0[3], H0[6], M1, g1[3], H1[6], xe[3];
+    float prev = 3.4e38f;
+    bool converged = false;
+    valid = false;
+    for (int it = 0;; it++) {
+        MbSum A = {};
+        mb_acc(cp, off, x, A);
+        mb_bfly<16>(A, kFullWarp);
+        MbSum B;  // the other particle's sums
+        B.M = __shfl_xor_sync(kFullWarp, A.M, 16);
+        B.g0 = __shfl_xor_sync(kFullWarp, A.g0, 16);
+        B.g1 = __shfl_xor_sync(kFullWarp, A.g1, 16);
+        B.g2 = __shfl_xor_sync(kFullWarp, A.g2, 16);
+        B.h0 = __shfl_xor_sync(kFullWarp, A.h0, 16);
+        B.h1 = __shfl_xor_sync(kFullWarp, A.h1, 16);
+        B.h2 = __shfl_xor_sync(kFullWarp, A.h2, 16);
+        B.h3 = __shfl_xor_sync(kFullWarp, A.h3, 16);
+        B.h4 = __shfl_xor_sync(kFullWarp, A.h4, 16);
+        B.h5 = __shfl_xor_sync(kFullWarp, A.h5, 16);
+        mb_unpack(half ? B : A, M0, g0, H0);
+        mb_unpack(half ? A : B, M1, g1, H1);
+        for (int a = 0; a < 3; a++) xe[a] = x[a];
+        if (it == kNewtonMax) break;
+        float H[6], g[3];
+        for (int a = 0; a < 6; a++) H[a] = H0[a] + H1[a];
+        for (int a = 0; a < 3; a++) g[a] = -(g0[a] + g1[a]);
+        const float c0 = H[1] * H[2] - H[5] * H[5];
+        const float c1 = H[5] * H[4] - H[3] * H[2];
+        const float c2 = H[3] * H[5] - H[1] * H[4];
+        const float det = H[0] * c0 + H[3] * c1 + H[4] * c2;
+        const float id = __frcp_rn(det);
+        const float b11 = H[0] * H[2] - H[4] * H[4], b12 = H[4] * H[3] - H[0] * H[5];
+        const float b22 = H[0] * H[1] - H[3] * H[3];
+        float dx[3];
+        dx[0] = (c0 * g[0] + c1 * g[1] + c2 * g[2]) * id;
+        dx[1] = (c1 * g[0] + b11 * g[1] + b12 * g[2]) * id;
+        dx[2] = (c2 * g[0] + b12 * g[1] + b22 * g[2]) * id;
+        const float s2 = dot3f(dx, dx);
+        const int code = __shfl_sync(kFullWarp, newton_code(det == 0.f || !isfinite(det), s2, prev, it), 0);
+        if (code == 1) break;
+        for (int a = 0; a < 3; a++) x[a] += dx[a];
+        if (code == 2) { converged = true; break; }
+        if (code == 3) break;
+        prev = s2;
+    }
+    for (int a = 0; a < 3; a++) xm[a] = x[a];
+    if (!(M0 > P.c_tol_f && M0 < 1.0f && M1 > P.c_tol_f && M1 < 1.0f)) return false;
+    valid = converged;
+    const float q0 = (1.0f - M0) * __frcp_rn(dot3f(g0, g0)), q1 = (1.0f - M1) * __frcp_rn(dot3f(g1, g1));
+    float dc[3];
+    for (int a = 0; a < 3; a++) dc[a] = q0 * g0[a] - q1 * g1[a];
+    const float dist = sqrtf(dot3f(dc, dc));
+    delta = S.Rs[i] + S.Rs[j] - dist;
+    if (!(delta > 0.f) || dist == 0.f) return false;
+    const float idist = __frcp_rn(dist);
+    for (int a = 0; a < 3; a++) {
+        nv[a] = dc[a] * idist;
+        xcp[a] = (xe[a] + q0 * g0[a]) - (S.Rs[i] - 0.5f * delta) * nv[a];
+    }
+    return true;
+}
+
+// Pair contacts of the candidate list, one item after the other, each by the
+// whole warp (every lane writes the results); results into it_res (zeros
+// when not in contact), as pair_contacts.
+template <class SH>
+__device__ void pair_contacts_w(const Params &P, SH &S, float h) {
+    const int np = S.n;
+    const int total = min(S.ioff[np], SH::kItems);
+    for (int it = 0; it < total; it++) {
+        int i = 0;  // last i with ioff[i] <= it
+        while (i + 1 < np && S.ioff[i + 1] <= it) i++;
+        const int j = S.up[i][it - S.ioff[i]];
+        float d[3];
+        rel_vec(S, P, i, j, d);
+        const float brs = S.brad[i] + S.brad[j];
+        const int was = S.it_on[it];
+        float xm[3], xi[3];
+        for (int a = 0; a < 3; a++) {
+            xm[a] = S.it_xm[it][a];
+            xi[a] = (was & CONTACT_ON) ? S.it_xi[it][a] : 0.f;
+        }
+        const int near = __shfl_sync(kFullWarp, dot3f(d, d) > brs * brs ? 0 : 1, 0);
+        float Fi[3] = {0.f, 0.f, 0.f}, ti[3] = {0.f, 0.f, 0.f}, tj[3] = {0.f, 0.f, 0.f};
+        int on = 0;
+        bool hit = false;
+        if (near) {
+            float delta, nv[3], xcp[3];
+            bool valid;
+            hit = pair_geom_w(P, S, i, j, d, (was & CONTACT_WARM) != 0, xm, delta, nv, xcp, valid);
+            on = valid ? CONTACT_WARM : 0;
+            if (hit) {
+                on |= CONTACT_ON;
+                float rj[3], wri[3], wrj[3], vij[3];
+                for (int a = 0; a < 3; a++) rj[a] = xcp[a] - d[a];
+                cross3f(S.w[i], xcp, wri);
+                cross3f(S.w[j], rj, wrj);
+                for (int a = 0; a < 3; a++) vij[a] = (S.v[i][a] + wri[a]) - (S.v[j][a] + wrj[a]);
+                contact_law_f(P, delta, nv, vij, xi, h, Fi);
+                const float Fj[3] = {-Fi[0], -Fi[1], -Fi[2]};
+                cross3f(xcp, Fi, ti);
+                cross3f(rj, Fj, tj);
+            }
+        }
+        __syncwarp();
+        S.it_on[it] = on;
+        if (near)
+            for (int a = 0; a < 3; a++) S.it_xm[it][a] = xm[a];
+        if (hit)
+            for (int a = 0; a < 3; a++) S.it_xi[it][a] = xi[a];
+        for (int a = 0; a < 3; a++) { S.it_res[it][a] = Fi[a]; S.it_res[it][3 + a] = ti[a]; S.it_res[it][6 + a] = tj[a]; }
+    }
+}
+}  // namespace
+
+// A contact group of up to kTinyContactGroup particles per warp,
+// kTinyGroupsPerCta warps per CTA: the sub-steps of k_dem64c with the lanes
+// split by particle (above).
+__global__ void __launch_bounds__(32 * kTinyGroupsPerCta, 1) k_dem64t(Params P) {
+    using SH = SharedTiny;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int wt = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+    SH &S = reinterpret_cast<SH *>(smem_raw)[wt];
+    const int slot = (int)blockIdx.x * kTinyGroupsPerCta + wt;
+    if (slot >= P.dem_list[2 + DEM_GROUP_TINY]) return;  // the whole warp
+    const int *grp = dem_groups(P, DEM_GROUP_TINY) + 2 * slot;
+    const int na = grp[1];
+    const int *act = dem_active(P) + grp[0];
+    const float h = P.h_f, hh = 0.5f * h, qh2 = 0.25f * h * h;
+    const int c = lane % kSegLanes;
+    const unsigned seg = ((1u << kSegLanes) - 1u) << (lane - c);  // this lane's particle lanes
+    const bool own = lane / kSegLanes < na;
+    const int k = own ? lane / kSegLanes : lane / kSegLanes % na;  // the particle (a mirror past the group)
+    const int g = act[k];
+    DevParticle *pp = &P.parts[g];
+
+    Delta x[3], v[3], q[4], wb[3];
+    float xlo[3], Fh[3], Th[3], iI[3], cI[3], bg[3];
+    float Fc[3] = {0.f, 0.f, 0.f}, Tc[3] = {0.f, 0.f, 0.f};  // contact load of the last evaluation
+    {
+        double wbd[3];
+        rot_body(pp->q, pp->w, wbd);
+        for (int a = 0; a < 3; a++) {
+            dl_set(x[a], pp->x[a]);
+            xlo[a] = (float)(pp->x[a] - (double)x[a].bf);  // FP32 rounding error of the start position
+            dl_set(v[a], pp->v[a]);
+            dl_set(wb[a], wbd[a]);
+            Fh[a] = (float)P.Fh[3 * g + a];
+            Th[a] = (float)P.Th[3 * g + a];
+            iI[a] = pp->iI_f[a];
+            cI[a] = pp->cI_f[a];
+            bg[a] = pp->bg_f[a];
+        }
+        for (int a = 0; a < 4; a++) dl_set(q[a], pp->q[a]);
+    }
+    const float inv_m = pp->inv_mass_f;
+    const bool mov = !pp->fixed;
+    const float reach = dem_reach(P, *pp, g);
+    const int ncp = pp->ncp;
+    // this lane's control points (body frame, weight); stand-ins past ncp
+    const float4 cpa = c < ncp ? make_float4(pp->cpb_f[c][0], pp->cpb_f[c][1], pp->cpb_f[c][2], pp->K_f[c]) : far_cp();
+    const float4 cpb = c + kSegLanes < ncp ? make_float4(pp->cpb_f[c + kSegLanes][0], pp->cpb_f[c + kSegLanes][1],
+                                                         pp->cpb_f[c + kSegLanes][2], pp->K_f[c + kSegLanes])
+                                           : far_cp();
+    float4 rca = cpa, rcb = cpb;  // rotated
+    if (lane == 0) {
+        int o = 0;
+        for (int m = 0; m < na; m++) { S.cpo[m] = o; o += P.parts[act[m]].ncp; }
+        S.cpo[na] = o;
+        S.n = na;
+        if (o > SH::kCps) atomicOr(&P.status[ST_ERR], ERRB_DEM_CAPACITY);
+    }
+    if (lane < na) S.gid[lane] = act[lane];
+    __syncwarp();
+    if (S.cpo[na] > SH::kCps) return;
+
+    // FP32 tables: position (hi + lo of the FP64 value), velocity, world
+    // angular velocity from the body rate wf
+    auto publish = [&](const float wf[3], const float qf[4]) {
+        float ww[3];
+        qrot_f(qf, wf, ww, true);
+        for (int a = 0; a < 3; a++) {
+            S.xh[k][a] = x[a].bf;
+            S.xl[k][a] = xlo[a] + (x[a].d.hi + x[a].d.lo);
+            S.v[k][a] = v[a].f();
+            S.w[k][a] = ww[a];
+        }
+    };
+    // this lane's control points rotated by qf, into registers and the table
+    // (stand-ins into the scratch row)
+    const int oc = S.cpo[k];
+    float4 *const dsta = c < ncp ? &S.rc[oc + c] : &S.rc_pad[lane];
+    float4 *const dstb = c + kSegLanes < ncp ? &S.rc[oc + c + kSegLanes] : &S.rc_pad[lane];
+    auto rotate_cps = [&](const float qf[4]) {
+        float r[3];
+        const float ba[3] = {cpa.x, cpa.y, cpa.z}, bb[3] = {cpb.x, cpb.y, cpb.z};
+        qrot_f(qf, ba, r, true);
+        rca = make_float4(r[0], r[1], r[2], cpa.w);
+        qrot_f(qf, bb, r, true);
+        rcb = make_float4(r[0], r[1], r[2], cpb.w);
+        *dsta = rca;
+        *dstb = rcb;
+    };
+    {
+        const float qf[4] = {q[0].f(), q[1].f(), q[2].f(), q[3].f()}, wf[3] = {wb[0].f(), wb[1].f(), wb[2].f()};
+        publish(wf, qf);
+        S.reach[k] = reach;
+        S.brad[k] = pp->brad_f;
+        S.Rs[k] = pp->Rs_f;
+        rotate_cps(qf);
+        if (c < NWALL) {  // lane c: the history of wall c
+            const int wj = g * NWALL + c;
+            S.w_on[k][c] = P.wall_on[wj];
+            for (int a = 0; a < 3; a++) {
+                S.w_xcw[k][c][a] = P.wall_xcw_f[3 * wj + a];
+                S.w_xi[k][c][a] = P.wall_xi_f[3 * wj + a];
+            }
+        }
+    }
+    __syncwarp();
+    int dummy = 0;
+    if (na > 1) build_lists(P, S, &dummy);
+    else if (lane == 0) {
+        S.nup[0] = 0; S.ndn[0] = 0; S.ioff[0] = 0; S.ioff[1] = 0;
+        for (int a = 0; a < 3; a++) S.xref[0][a] = S.xh[0][a] + S.xl[0][a];
+    }
+    __syncwarp();
+    // contact load at the start: left by the previous step's DEM (same
+    // state), unless the particles were set since
+    if (!P.fc_valid) {
+        pair_contacts_w(P, S, 0.f);
+        __syncwarp();
+        gather_pairs(S, k, Fc, Tc);
+        walls_seg(P, S, k, seg, 0.f, rca, rcb, Fc, Tc);
+    } else {
+        for (int a = 0; a < 3; a++) {
+            Fc[a] = (float)P.Fc[3 * g + a];
+            Tc[a] = (float)P.Tc[3 * g + a];
+        }
+    }
+    __syncwarp();
+    for (int sub = 0; sub < P.n_sub; sub++) {
+        Delta wh[3] = {wb[0], wb[1], wb[2]};
+        int moved = 0;
+        {
+            float qf[4] = {q[0].f(), q[1].f(), q[2].f(), q[3].f()};
+            if (mov) {
+                // first half-kick and drift
+                for (int a = 0; a < 3; a++) {
+                    dl_add(v[a], hh * (bg[a] + (Fh[a] + Fc[a]) * inv_m));
+                    dl_add(x[a], h * v[a].f());
+                }
+                // rotation: half-kick, q <- q (x) exp(h wh / 2)
+                float Tw[3], Tb[3], wf[3] = {wb[0].f(), wb[1].f(), wb[2].f()}, dw[3], whf[3];
+                for (int a = 0; a < 3; a++) Tw[a] = Th[a] + Tc[a];
+                qrot_f(qf, Tw, Tb, false);
+                euler_f(iI, cI, wf, Tb, dw);
+                for (int a = 0; a < 3; a++) {
+                    dl_add(wh[a], hh * dw[a]);
+                    whf[a] = wh[a].f();
+                }
+                float cm1, sc;
+                exp_half(hh, qh2, whf, cm1, sc);
+                const float d1 = sc * whf[0], d2 = sc * whf[1], d3 = sc * whf[2];
+                const float q0 = qf[0], q1 = qf[1], q2 = qf[2], q3 = qf[3];
+                dl_add(q[0], q0 * cm1 - (q1 * d1 + q2 * d2 + q3 * d3));
+                dl_add(q[1], q0 * d1 + q1 * cm1 + (q2 * d3 - q3 * d2));
+                dl_add(q[2], q0 * d2 + q2 * cm1 + (q3 * d1 - q1 * d3));
+                dl_add(q[3], q0 * d3 + q3 * cm1 + (q1 * d2 - q2 * d1));
+                for (int a = 0; a < 4; a++) qf[a] = q[a].f();
+            }
+            const float whf[3] = {wh[0].f(), wh[1].f(), wh[2].f()};
+            publish(whf, qf);
+            float dr2 = 0.f;
+            for (int a = 0; a < 3; a++) {
+                const float dd = (x[a].bf - S.xref[k][a]) + (xlo[a] + (x[a].d.hi + x[a].d.lo));
+                dr2 += dd * dd;
+            }
+            if (mov) rotate_cps(qf);
+            moved = dr2 > 0.25f * kSkin * kSkin;
+        }
+        moved = __any_sync(kFullWarp, moved);
+        __syncwarp();
+        if (moved && na > 1) {
+            store_items(P, S);
+            __syncwarp();
+            build_lists(P, S, &dummy);
+        }
+        pair_contacts_w(P, S, h);
+        __syncwarp();
+        {
+            float F[3], T[3];
+            gather_pairs(S, k, F, T);
+            walls_seg(P, S, k, seg, h, rca, rcb, F, T);
+            for (int a = 0; a < 3; a++) { Fc[a] = F[a]; Tc[a] = T[a]; }
+            if (mov) {
+                // closing half-kick with the new contact load
+                for (int a = 0; a < 3; a++) dl_add(v[a], hh * (bg[a] + (Fh[a] + F[a]) * inv_m));
+                const float qf[4] = {q[0].f(), q[1].f(), q[2].f(), q[3].f()};
+                float Tw[3], Tb[3], dw[3], whf[3] = {wh[0].f(), wh[1].f(), wh[2].f()}, w1[3];
+                for (int a = 0; a < 3; a++) { Tw[a] = Th[a] + T[a]; w1[a] = whf[a]; }
+                qrot_f(qf, Tw, Tb, false);
+                for (int it = 0; it + 1 < ROT_ITERS; it++) {
+                    euler_f(iI, cI, w1, Tb, dw);
+                    for (int a = 0; a < 3; a++) w1[a] = whf[a] + hh * dw[a];
+                }
+                euler_f(iI, cI, w1, Tb, dw);
+                for (int a = 0; a < 3; a++) {
+                    wb[a] = wh[a];
+                    dl_add(wb[a], hh * dw[a]);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // the step's changes added to the FP64 state (still in the record)
+    double qd[4] = {1, 0, 0, 0}, wbd[3] = {0, 0, 0}, xd[3] = {0, 0, 0}, vd[3] = {0, 0, 0};
+    if (mov) {
+        double wb0[3];
+        rot_body(pp->q, pp->w, wb0);
+        for (int a = 0; a < 4; a++) qd[a] = q[a].fin(pp->q[a]);
+        for (int a = 0; a < 3; a++) {
+            wbd[a] = wb[a].fin(wb0[a]);
+            xd[a] = x[a].fin(pp->x[a]);
+            vd[a] = v[a].fin(pp->v[a]);
+        }
+        quat_normalize(qd);
+        for (int a = 0; a < 4; a++) dl_set(q[a], qd[a]);
+    }
+    // contact load of the end state (springs not advanced): reported by
+    // lbm_get_contact_forces and the start load of the next step
+    {
+        const float qf[4] = {q[0].f(), q[1].f(), q[2].f(), q[3].f()}, wf[3] = {wb[0].f(), wb[1].f(), wb[2].f()};
+        publish(wf, qf);
+        if (mov) rotate_cps(qf);
+    }
+    __syncwarp();
+    pair_contacts_w(P, S, 0.f);
+    __syncwarp();
+    float F[3], T[3];
+    gather_pairs(S, k, F, T);
+    walls_seg(P, S, k, seg, 0.f, rca, rcb, F, T);
+    __syncwarp();  // every lane has read the particle records (the end state is written below)
+    if (own) {
+        if (c < NWALL) {  // lane c: the history of wall c
+            const int wj = g * NWALL + c;
+            P.wall_on[wj] = S.w_on[k][c];
+            for (int a = 0; a < 3; a++) {
+                P.wall_xcw_f[3 * wj + a] = S.w_xcw[k][c][a];
+                P.wall_xi_f[3 * wj + a] = S.w_xi[k][c][a];
+            }
+        }
+        if (c == 0) {
+            for (int a = 0; a < 3; a++) {
+                P.Fc[3 * g + a] = (double)F[a];
+                P.Tc[3 * g + a] = (double)T[a];
+            }
+            if (mov) {
+                double ww[3];
+                rot_world(qd, wbd, ww);
+                for (int a = 0; a < 3; a++) {
+                    pp->x[a] = xd[a];
+                    pp->v[a] = vd[a];
+                    pp->w[a] = ww[a];
+                }
+                for (int a = 0; a < 4; a++) pp->q[a] = qd[a];
+            }
+            // the planning assumed no larger displacement (contacts with
+            // inactive particles would have been missed otherwise)
+            float d2 = 0.f;
+            for (int a = 0; a < 3; a++) d2 += x[a].d.hi * x[a].d.hi;
+            if (d2 > reach * reach) atomicOr(&P.status[ST_ERR], ERRB_DEM_REACH);
+        }
+    }
+    if (na > 1) store_items(P, S);
+}
+
 void launch_dem64c(const Params &P, cudaStream_t st) {
     // the dynamic shared memory limits are raised once per device
     static bool attr_set[64] = {};
@@ -1185,8 +1776,8 @@ void launch_dem64c(const Params &P, cudaStream_t st) {
     // grids for the worst case (every group tiny, or small); at most np / 33
     // groups are large.  A tiny-group CTA of 8 warps holds most of an SM's
     // registers, so few other CTAs share the SM with its latency-bound chains.
-    k_dem64c<SharedTiny, DEM_GROUP_TINY><<<(P.np + kTinyGroupsPerCta - 1) / kTinyGroupsPerCta,
-                                           32 * kTinyGroupsPerCta, kTinyGroupsPerCta * sizeof(SharedTiny), st>>>(P);
+    k_dem64t<<<(P.np + kTinyGroupsPerCta - 1) / kTinyGroupsPerCta, 32 * kTinyGroupsPerCta,
+               kTinyGroupsPerCta * sizeof(SharedTiny), st>>>(P);
     k_dem64c<SharedSmall, DEM_GROUP_SMALL><<<P.np / (kTinyContactGroup + 1) + 1, kSmallContactGroup,
                                              sizeof(SharedSmall), st>>>(P);
     k_dem64c<Shared, DEM_GROUP_LARGE><<<P.np / (kSmallContactGroup + 1) + 1, kThreads, big, st>>>(P);
