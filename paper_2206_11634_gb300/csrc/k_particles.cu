@@ -757,6 +757,7 @@ __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
         if (c < 3) P.Fh[3 * k + c] = v;
         else P.Th[3 * k + c - 3] = v;
     }
+    __syncthreads();  // dem_reach below reads the load that other threads converted
     const int k = threadIdx.x;
     if (k < np) {
         const DevParticle &p = P.parts[k];
