@@ -253,7 +253,8 @@ int lbm_kernels_per_step(const lbm_handle *h);
  * event pair around each of its kernels on the stream the kernel runs on (up
  * to 65536 launches per kernel; later ones are not recorded).
  * lbm_profile_read() synchronises and returns, for kernel k (0 bin, 1 flags,
- * 2 plain sweep, 3 near sweep, 4 force reduce, 5 DEM), the summed device time
+ * 2 plain sweep, 3 near sweep, 4 force reduce, 5 DEM, 6 the near set's bricks
+ * without particle links), the summed device time
  * in milliseconds and the number of launches recorded since profiling was
  * enabled; enable = 0 stops recording and releases the events.  The events
  * are created on the host side of the CUDA runtime (no device memory is

@@ -837,16 +837,48 @@ __device__ __noinline__ void near_brick(const Params &P, SmemParticles &sp, doub
     }
 }
 
+// Whether a brick of the near set can hold a particle link or a missing
+// force point: it needs a solid node in the brick or a solid neighbour of one
+// of its nodes -- the brick's own mark, and for each of the 26 bricks around
+// it the faces turned towards it (all of them, for an edge or corner brick).
+// Called by every thread of the CTA (a barrier); the same answer in all.
+__device__ __forceinline__ bool brick_near_solid(const Params &P, int bxi, int byi, int bzi) {
+    const int tid = threadIdx.x;
+    bool near_solid = false;
+    if (tid < 27) {
+        const int o[3] = {tid % 3 - 1, (tid / 3) % 3 - 1, tid / 9 - 1};
+        int q[3] = {bxi + o[0], byi + o[1], bzi + o[2]};
+        const int nbs[3] = {P.nbx, P.nby, P.nbz};
+        bool in = true;
+        for (int a = 0; a < 3; a++) {
+            if (q[a] < 0 || q[a] >= nbs[a]) {
+                if (P.per[a]) q[a] = (q[a] + nbs[a]) % nbs[a];
+                else in = false;
+            }
+        }
+        const uint32_t m = in ? (uint32_t)P.brick_solid[q[0] + P.nbx * (q[1] + P.nby * q[2])] : 0u;
+        near_solid = (m & kSolidAny) != 0;
+        for (int a = 0; a < 3; a++)  // a brick below faces us with its high face, and so on
+            if (o[a] != 0) near_solid = near_solid && (m & (1u << (2 * a + (o[a] < 0 ? 1 : 0)))) != 0;
+    }
+    return __syncthreads_or(near_solid) != 0;
+}
+
 // The sweep of the bricks listed this step (exactly those some particle's
 // grown search box meets) and of the predicted-near bricks that are not
-// listed (plain path): every brick k_sweep_plain leaves.  Persistent grid;
+// listed: every brick k_sweep_plain leaves.  A brick of this set that can
+// hold no particle link (no particle listed, or no solid node next to it)
+// takes the plain path, here (kSplit false: the batched sweep) or in
+// k_sweep_near_plain (kSplit true), which runs beside on the plain sweep's
+// stream at the plain sweep's occupancy while this kernel keeps its CTAs
+// for the link bricks.  Persistent grid;
 // the CTAs take the bricks one at a time from a per-step counter (a brick
 // with particle links costs about ten times one on the plain path, and a
 // fixed split left the busiest CTA near 1.45 times the mean).  Thread 0
 // fetches the next entry while the current brick runs; s_next holds it,
 // alternating between two slots so that a slot is rewritten only after
 // every thread has passed the barrier that follows its last read.
-template <typename S, int Q, bool kForce>
+template <typename S, int Q, bool kForce, bool kSplit = false>
 __device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, double (*red)[6], int &s_links,
                                           LinkScratch &ls, int *s_next) {
     const int tid = threadIdx.x;
@@ -870,7 +902,6 @@ __device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, do
             b = P.pred_list_cur[w - c_exact];
             if (P.stamp[b] == t) continue;  // listed: taken above
         }
-        done++;
         int bxi, byi, bzi;
         brick_coords(P, b, bxi, byi, bzi);
         const int bx0 = bxi * BX, by0 = byi * BY, bz0 = bzi * BZ;
@@ -880,36 +911,18 @@ __device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, do
         if (tid >= 32 && tid < 32 + cnt) sp.id[tid - 32] = P.blist[b * MAXPB + (tid - 32)];
         if (tid == 0) sp.n = cnt;
         if (cnt > 0 && P.brick_solid) {
-            // particle links and missing force points need a solid node in
-            // the brick or a solid neighbour of one of its nodes: the brick's
-            // own mark, and for each of the 26 bricks around it the faces
-            // turned towards it (all of them, for an edge or corner brick)
-            bool near_solid = false;
-            if (tid < 27) {
-                const int o[3] = {tid % 3 - 1, (tid / 3) % 3 - 1, tid / 9 - 1};
-                int q[3] = {bxi + o[0], byi + o[1], bzi + o[2]};
-                const int nbs[3] = {P.nbx, P.nby, P.nbz};
-                bool in = true;
-                for (int a = 0; a < 3; a++) {
-                    if (q[a] < 0 || q[a] >= nbs[a]) {
-                        if (P.per[a]) q[a] = (q[a] + nbs[a]) % nbs[a];
-                        else in = false;
-                    }
-                }
-                const uint32_t m = in ? (uint32_t)P.brick_solid[q[0] + P.nbx * (q[1] + P.nby * q[2])] : 0u;
-                near_solid = (m & kSolidAny) != 0;
-                for (int a = 0; a < 3; a++)  // a brick below faces us with its high face, and so on
-                    if (o[a] != 0) near_solid = near_solid && (m & (1u << (2 * a + (o[a] < 0 ? 1 : 0)))) != 0;
-            }
-            if (!__syncthreads_or(near_solid)) cnt = 0;
+            if (!brick_near_solid(P, bxi, byi, bzi)) cnt = 0;
         } else {
             __syncthreads();
         }
         if (cnt == 0) {
+            if (kSplit) continue;  // k_sweep_near_plain takes it
+            done++;
             const int x = bx0 + tid % BX, y = by0 + (tid / BX) % BY, z = bz0 + tid / (BX * BY);
             if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce>(P, x, y, z, x + P.nx * (y + P.ny * z));
             continue;
         }
+        done++;
         if (tid == 0) s_links = 0;
         near_brick<S, Q, kForce>(P, sp, red, &s_links, &ls, b, bx0, by0, bz0, cnt);
     }
@@ -922,7 +935,37 @@ __global__ void __launch_bounds__(BRICK, kNearCtasPerSm) k_sweep_near(Params P) 
     __shared__ int s_links;
     __shared__ LinkScratch ls;
     __shared__ int s_next[2];
-    near_work<S, Q, kForce>(P, sp, red, s_links, ls, s_next);
+    near_work<S, Q, kForce, true>(P, sp, red, s_links, ls, s_next);
+}
+
+// The bricks of the near set that hold no particle link (near_work's test,
+// the same answer): the plain path, a brick per CTA at a time over a
+// persistent grid, on the plain sweep's stream after the flag pass.
+template <typename S, int Q, bool kForce>
+__global__ void __launch_bounds__(BRICK, 4) k_sweep_near_plain(Params P) {
+    const int tid = threadIdx.x;
+    const int t = P.step;
+    const int c_exact = P.counters[CNT_LISTED];
+    const int c_pred = P.pred_stamp_cur ? P.pred_count[t % 3] : 0;
+    const int total = c_exact + c_pred;
+    int done = 0;
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        int b;
+        if (w < c_exact) {
+            b = P.wl_list[(t % 3) * P.nbricks + w];
+        } else {
+            b = P.pred_list_cur[w - c_exact];
+            if (P.stamp[b] == t) continue;  // listed: taken above
+        }
+        int bxi, byi, bzi;
+        brick_coords(P, b, bxi, byi, bzi);
+        const int cnt = min(P.bcount[b], MAXPB);
+        if (cnt > 0 && (!P.brick_solid || brick_near_solid(P, bxi, byi, bzi))) continue;  // the near sweep's
+        done++;
+        const int x = bxi * BX + tid % BX, y = byi * BY + (tid / BX) % BY, z = bzi * BZ + tid / (BX * BY);
+        if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce>(P, x, y, z, x + P.nx * (y + P.ny * z));
+    }
+    if (tid == 0 && done) atomicAdd(&P.counters[CNT_NEAR], done);
 }
 
 }  // namespace lbmmb

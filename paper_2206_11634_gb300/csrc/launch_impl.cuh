@@ -60,6 +60,20 @@ void launch_sweep_near_t(const Params &P, cudaStream_t st) {
         else k_sweep_near<S, 15, false><<<grid, BRICK, 0, st>>>(P);
     }
 }
+// persistent, at the plain sweep's occupancy (4 CTAs per SM)
+template <typename S>
+void launch_sweep_near_plain_t(const Params &P, cudaStream_t st) {
+    const bool force = P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0;
+    const int cap = 4 * sm_count();
+    const int grid = P.nbricks < cap ? P.nbricks : cap;
+    if (P.Q == 19) {
+        if (force) k_sweep_near_plain<S, 19, true><<<grid, BRICK, 0, st>>>(P);
+        else k_sweep_near_plain<S, 19, false><<<grid, BRICK, 0, st>>>(P);
+    } else {
+        if (force) k_sweep_near_plain<S, 15, true><<<grid, BRICK, 0, st>>>(P);
+        else k_sweep_near_plain<S, 15, false><<<grid, BRICK, 0, st>>>(P);
+    }
+}
 template <typename S>
 void launch_fields_t(const Params &P, const void *f, const uint16_t *flags, double *rho, double *u, uint16_t *fl,
                      cudaStream_t st) {
@@ -172,6 +186,7 @@ void launch_static_links_batch_t(const BatchArgs &B, int Q, bool force, int warp
     template void launch_flags_t<S>(const Params &, cudaStream_t);                                               \
     template void launch_sweep_plain_t<S>(const Params &, cudaStream_t);                                         \
     template void launch_sweep_near_t<S>(const Params &, cudaStream_t);                                          \
+    template void launch_sweep_near_plain_t<S>(const Params &, cudaStream_t);                                    \
     template void launch_fields_t<S>(const Params &, const void *, const uint16_t *, double *, double *,         \
                                      uint16_t *, cudaStream_t);                                                  \
     template void launch_get_pop_t<S>(const Params &, const void *, double *, cudaStream_t);                     \

@@ -148,7 +148,7 @@ thread_local char g_init_error[256] = "no error";
 
 }  // namespace
 
-constexpr int kProfKernels = 6;
+constexpr int kProfKernels = 7;
 constexpr int kProfCap = 65536;
 
 // Principal axes of a particle's inertia tensor, kept per particle slot so
@@ -173,6 +173,7 @@ struct lbm_handle {
     // sweep of t+1 waits for it (it reads its halo).
     cudaStream_t aux, hi;
     cudaEvent_t ev_fork, ev_bin, ev_plain, ev_near, ev_join;
+    cudaEvent_t ev_flags;  // after the flag pass (the near set's plain bricks wait for it)
     // FP64-integrator DEM: the particles that cannot touch anything during a
     // step move on dem2 (high priority), forked from hi after the split
     cudaStream_t dem2;
@@ -328,6 +329,7 @@ template <typename S> struct DoInit { static void run(const Params &P, void *f, 
 template <typename S> struct DoFlags { static void run(const Params &P, cudaStream_t st) { launch_flags_t<S>(P, st); } };
 template <typename S> struct DoPlain { static void run(const Params &P, cudaStream_t st) { launch_sweep_plain_t<S>(P, st); } };
 template <typename S> struct DoNear { static void run(const Params &P, cudaStream_t st) { launch_sweep_near_t<S>(P, st); } };
+template <typename S> struct DoNearPlain { static void run(const Params &P, cudaStream_t st) { launch_sweep_near_plain_t<S>(P, st); } };
 template <typename S> struct DoFields {
     static void run(const Params &P, double *rho, double *u, uint16_t *fl, cudaStream_t st) {
         launch_fields_t<S>(P, P.fA, P.flag_new, rho, u, fl, st);
@@ -522,7 +524,7 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
     // bricks occupied, no contacts, no errors
     const size_t zero_from = L.flags[0];
     h->aux = h->hi = h->dem2 = nullptr;
-    h->ev_fork = h->ev_bin = h->ev_plain = h->ev_near = h->ev_join = nullptr;
+    h->ev_fork = h->ev_bin = h->ev_plain = h->ev_near = h->ev_join = h->ev_flags = nullptr;
     h->ev_dsplit = h->ev_dfree = nullptr;
     h->dem_mode = DEM_FP64_ALL;
     h->pin = nullptr;
@@ -555,6 +557,7 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_bin, cudaEventDisableTiming), "cudaEventCreate");
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_plain, cudaEventDisableTiming), "cudaEventCreate");
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_near, cudaEventDisableTiming), "cudaEventCreate");
+        if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_flags, cudaEventDisableTiming), "cudaEventCreate");
         if (rc == LBM_OK)
             rc = cuda_check(h, cudaStreamCreateWithPriority(&h->dem2, cudaStreamNonBlocking, prio_high), "cudaStreamCreateWithPriority");
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_dsplit, cudaEventDisableTiming), "cudaEventCreate");
@@ -580,6 +583,7 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
         if (h->ev_bin) cudaEventDestroy(h->ev_bin);
         if (h->ev_plain) cudaEventDestroy(h->ev_plain);
         if (h->ev_near) cudaEventDestroy(h->ev_near);
+        if (h->ev_flags) cudaEventDestroy(h->ev_flags);
         if (h->ev_join) cudaEventDestroy(h->ev_join);
         if (h->ev_pin) cudaEventDestroy(h->ev_pin);
         if (h->ev_dsplit) cudaEventDestroy(h->ev_dsplit);
@@ -908,6 +912,8 @@ int lbm_step(lbm_handle *h, int nsteps) {
             e = cudaEventRecord(h->ev_bin, hs);
             if (e != cudaSuccess) return cuda_check(h, e, "event record");
             { ProfScope s(h, 1, !geom_static, hs); if (!geom_static) by_storage<DoFlags>(h->cfg.storage, P, hs); }
+            e = cudaEventRecord(h->ev_flags, hs);
+            if (e != cudaSuccess) return cuda_check(h, e, "event record");
             // the near sweep reads the halo the previous plain sweep wrote (this
             // wait is issued before ev_plain is recorded again below; the plain
             // sweep of the call before was joined into `stream` before the fork,
@@ -925,6 +931,7 @@ int lbm_step(lbm_handle *h, int nsteps) {
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_near, 0);
                 if (e != cudaSuccess) return cuda_check(h, e, "stream fork");
                 { ProfScope s(h, 2, true, h->aux); by_storage<DoPlain>(h->cfg.storage, P, h->aux); }
+                { ProfScope s(h, 6, true, h->aux); by_storage<DoNearPlain>(h->cfg.storage, P, h->aux); }
                 e = cudaEventRecord(h->ev_plain, h->aux);
                 if (e != cudaSuccess) return cuda_check(h, e, "event record");
             } else {
@@ -932,6 +939,11 @@ int lbm_step(lbm_handle *h, int nsteps) {
                 e = cudaStreamWaitEvent(h->aux, h->ev_bin, 0);
                 if (e != cudaSuccess) return cuda_check(h, e, "stream wait");
                 { ProfScope s(h, 2, true, h->aux); by_storage<DoPlain>(h->cfg.storage, P, h->aux); }
+                // then the near set's bricks without particle links (the
+                // flag pass decides which), beside the near sweep
+                e = cudaStreamWaitEvent(h->aux, h->ev_flags, 0);
+                if (e != cudaSuccess) return cuda_check(h, e, "stream wait");
+                { ProfScope s(h, 6, true, h->aux); by_storage<DoNearPlain>(h->cfg.storage, P, h->aux); }
                 e = cudaEventRecord(h->ev_plain, h->aux);
                 if (e != cudaSuccess) return cuda_check(h, e, "event record");
                 { ProfScope s(h, 3, true, hs); by_storage<DoNear>(h->cfg.storage, P, hs); }
@@ -962,17 +974,18 @@ int lbm_step(lbm_handle *h, int nsteps) {
 int lbm_kernels_per_step(const lbm_handle *h) {
     if (!h) return 0;
     // binning (every step), flags (left out once the geometry is static),
-    // plain and near sweeps; force reduction (FP64 lattices with particles);
-    // DEM (particles, n_sub > 0)
-    // once the fixed-geometry sweep runs: its link and plain kernels
+    // the plain sweep, the near sweep and the near set's bricks without
+    // particle links; force reduction (FP64 lattices with particles); DEM
+    // (particles, n_sub > 0); once the fixed-geometry sweep runs: its link and
+    // plain kernels
     const bool geom_static = h->all_fixed && h->static_steps >= kStaticFlagSteps;
     // the FP64-integrator DEM is five kernels (split, inactive particles,
     // tiny, small and large contact groups)
     const int dem = h->np > 0 && h->cfg.n_sub > 0 ? (h->dem_mode == DEM_FP64_INTEGRATOR ? 5 : 1) : 0;
     if (geom_static && h->static_state == 1) return 2 + dem;
     const int flags = geom_static ? 0 : 1;
-    if (h->np == 0) return 3 + flags;
-    return 3 + flags + (h->cfg.storage == LBM_STORE_F64 ? 1 : 0) + dem;
+    if (h->np == 0) return 4 + flags;
+    return 4 + flags + (h->cfg.storage == LBM_STORE_F64 ? 1 : 0) + dem;
 }
 
 static int read_status(lbm_handle *h, int *st) {

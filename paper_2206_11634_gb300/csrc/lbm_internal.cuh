@@ -744,6 +744,7 @@ template <typename S> void launch_init_t(const Params &P, void *f, cudaStream_t 
 template <typename S> void launch_flags_t(const Params &P, cudaStream_t st);
 template <typename S> void launch_sweep_plain_t(const Params &P, cudaStream_t st);
 template <typename S> void launch_sweep_near_t(const Params &P, cudaStream_t st);
+template <typename S> void launch_sweep_near_plain_t(const Params &P, cudaStream_t st);
 template <typename S>
 void launch_fields_t(const Params &P, const void *f, const uint16_t *flags, double *rho, double *u, uint16_t *fl,
                      cudaStream_t st);

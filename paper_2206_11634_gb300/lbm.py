@@ -300,7 +300,7 @@ class Lattice:
     def check(self) -> None:
         self._ok(self.L.lbm_check(self.h), self.h)
 
-    KERNELS = ("k_bin", "k_flags", "k_sweep_plain", "k_sweep_near", "k_force_reduce", "k_dem")
+    KERNELS = ("k_bin", "k_flags", "k_sweep_plain", "k_sweep_near", "k_force_reduce", "k_dem", "k_sweep_near_plain")
 
     def profile(self, enable: bool = True, kernels=None, every: int = 1) -> None:
         """Record event pairs around every kernel (enable), or only around the
