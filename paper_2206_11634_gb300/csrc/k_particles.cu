@@ -643,16 +643,23 @@ __device__ __forceinline__ double dneg_if(double v, bool neg) {
     return __longlong_as_double(__double_as_longlong(v) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
 }
 
-__device__ void rotate_free_quad(unsigned mk, const DevParticle &p, const double *Th_world, double h, int n_sub,
-                                 DevParticle &out) {
+// Tw_lane: this lane's component of the world-frame torque (lane 0: not
+// used); the new attitude and world angular velocity go to q_out[4] and
+// w_out[3] (which may be p's own).
+__device__ void rotate_free_quad(unsigned mk, const DevParticle &p, double Tw_lane, double h, int n_sub,
+                                 double *q_out, double *w_out) {
     const QuadLanes L = quad_lanes();
     const int lane = L.lane;
     const int m = lane == 0 ? 0 : lane - 1;
     double q = p.q[lane];
-    const double Tw = lane == 0 ? 0.0 : Th_world[m];
+    const double Tw = lane == 0 ? 0.0 : Tw_lane;
     double wb = qrotate(mk, L, q, lane == 0 ? 0.0 : p.w[m], false);
     double Tb = qrotate(mk, L, q, Tw, false);
-    if (__all_sync(mk, wb == 0.0 && Tb == 0.0)) return;  // nothing turns
+    if (__all_sync(mk, wb == 0.0 && Tb == 0.0)) {  // nothing turns
+        q_out[lane] = q;
+        if (lane > 0) w_out[m] = p.w[m];
+        return;
+    }
     const double hh = 0.5 * h, qh2 = 0.25 * h * h;
     // per-lane constants (lane 0 holds the quaternion's scalar part only)
     const double cIhh = lane == 0 ? 0.0 : hh * p.cI[m];
@@ -717,15 +724,17 @@ __device__ void rotate_free_quad(unsigned mk, const DevParticle &p, const double
     n2 += __shfl_xor_sync(mk, n2, 2, 4);
     q *= rsqrt(n2);
     const double ww = qrotate(mk, L, q, wb, true);
-    out.q[lane] = q;
-    if (lane > 0) out.w[m] = ww;
+    q_out[lane] = q;
+    if (lane > 0) w_out[m] = ww;
 }
 
 // ---------------------------------------------------------------------------
 // FP64 rigid-body integration on lattices stored below FP64 (the default):
-// k_dem64_plan splits the particles of the step, then k_dem64_free moves the
-// ones that cannot touch anything during the step and k_dem64c (k_dem32.cu)
-// the others, on two streams at once.
+// k_dem64_free moves every particle as if it could touch nothing during the
+// step, into the records' step results, while k_dem64_plan splits the
+// particles on the other stream and k_dem64t / k_dem64c (k_dem32.cu) move the
+// ones that can touch something; k_dem64_commit then gives the others their
+// step results.
 // ---------------------------------------------------------------------------
 
 // One CTA.  The hydrodynamic load as FP64 totals (from the sweep's
@@ -883,33 +892,52 @@ __global__ void __launch_bounds__(256) k_dem64_plan(Params P) {
     }
 }
 
-// Four lanes per particle, 32 particles per CTA: the inactive particles of
-// the plan.  Translation in closed form over the unit step (x += v + a/2, v
-// += a: what the n_s kick-drift-kick sub-steps give under the constant
-// force), rotation sub-stepped by rotate_free_quad, all FP64; no contact load.
+// Four lanes per particle, 32 particles per CTA, every particle (the plan
+// runs beside it): the step of a particle that touches nothing, into its
+// record's step results (nx, nv, nq, nw).  Translation in closed form over
+// the unit step (x += v + a/2, v += a: what the n_s kick-drift-kick
+// sub-steps give under the constant force), rotation sub-stepped by
+// rotate_free_quad, all FP64.  The hydrodynamic load comes from the sweep's
+// fixed-point totals by the plan's conversion (the same bits as its Fh, Th).
 __global__ void __launch_bounds__(128) k_dem64_free(Params P) {
-    const int nf = P.dem_list[0];
+    const int np = P.np;
     const int slot = blockIdx.x * 32 + (int)(threadIdx.x >> 2);
-    if (blockIdx.x * 32 + (int)((threadIdx.x & ~31u) >> 2) >= nf) return;  // the whole warp is idle
-    const bool has = slot < nf;
-    const int k = has ? dem_free(P)[slot] : 0;
-    const int lane = threadIdx.x & 3;
-    if (has) {
-        DevParticle &p = P.parts[k];
-        if (lane > 0) {
-            const int m = lane - 1;
-            if (!p.fixed) {
-                const double acc = p.buoy * P.g[m] + P.Fh[3 * k + m] * p.inv_mass;
-                p.x[m] += p.v[m] + 0.5 * acc;
-                p.v[m] += acc;
-            }
-            P.Fc[3 * k + m] = 0.0;
-            P.Tc[3 * k + m] = 0.0;
-        }
+    if (blockIdx.x * 32 + (int)((threadIdx.x & ~31u) >> 2) >= np) return;  // the whole warp is idle
+    const bool has = slot < np;
+    const int k = has ? slot : 0;
+    const int lane = threadIdx.x & 3, m = lane == 0 ? 0 : lane - 1;
+    constexpr double kFix = 1.0 / (double)(1ull << kForceFixBits);
+    DevParticle &p = P.parts[k];
+    const bool moving = has && !p.fixed;
+    if (moving && lane > 0) {
+        const double acc = p.buoy * P.g[m] + ((double)(long long)P.Ffix[6 * k + m] * kFix) * p.inv_mass;
+        p.nx[m] = p.x[m] + (p.v[m] + 0.5 * acc);
+        p.nv[m] = p.v[m] + acc;
     }
-    const bool moving = has && !P.parts[k].fixed;
     const unsigned mk = __ballot_sync(0xffffffffu, moving);
-    if (moving) rotate_free_quad(mk, P.parts[k], P.Th + 3 * k, 1.0 / P.n_sub, P.n_sub, P.parts[k]);
+    if (moving)
+        rotate_free_quad(mk, p, (double)(long long)P.Ffix[6 * k + 3 + m] * kFix, 1.0 / P.n_sub, P.n_sub, p.nq, p.nw);
+}
+
+// The plan's inactive particles take k_dem64_free's step results; their
+// contact load is zero.  One thread per inactive particle.
+__global__ void __launch_bounds__(128) k_dem64_commit(Params P) {
+    const int s = blockIdx.x * blockDim.x + (int)threadIdx.x;
+    if (s >= P.dem_list[0]) return;
+    const int k = dem_free(P)[s];
+    DevParticle &p = P.parts[k];
+    if (!p.fixed) {
+        for (int a = 0; a < 3; a++) {
+            p.x[a] = p.nx[a];
+            p.v[a] = p.nv[a];
+            p.w[a] = p.nw[a];
+        }
+        for (int a = 0; a < 4; a++) p.q[a] = p.nq[a];
+    }
+    for (int a = 0; a < 3; a++) {
+        P.Fc[3 * k + a] = 0.0;
+        P.Tc[3 * k + a] = 0.0;
+    }
 }
 
 // One CTA.  Kick-drift-kick velocity Verlet with the hydrodynamic load frozen
@@ -949,7 +977,10 @@ __global__ void __launch_bounds__(256) k_dem(Params P) {
             const int k = base + (int)(threadIdx.x >> 2);
             const bool moving = k < P.np && !P.parts[k].fixed;
             const unsigned mk = __ballot_sync(0xffffffffu, moving);
-            if (moving) rotate_free_quad(mk, P.parts[k], P.Th + 3 * k, h, P.n_sub, P.parts[k]);
+            const int ql = threadIdx.x & 3;
+            if (moving)
+                rotate_free_quad(mk, P.parts[k], ql == 0 ? 0.0 : P.Th[3 * k + ql - 1], h, P.n_sub, P.parts[k].q,
+                                 P.parts[k].w);
         }
         return;
     }
@@ -1020,14 +1051,16 @@ void launch_dem(const Params &P, cudaStream_t st, cudaStream_t st2, cudaEvent_t 
     if (P.dem_mode == DEM_FP32) {
         launch_dem32(P, st);
     } else if (P.dem_mode == DEM_FP64_INTEGRATOR) {
-        // plan, then the inactive particles on st2 beside the active ones on st
-        k_dem64_plan<<<1, 256, 0, st>>>(P);
+        // every particle's free step on st2 beside the plan and the contact
+        // groups on st; then the plan's inactive particles take theirs
         cudaEventRecord(ev_split, st);
         cudaStreamWaitEvent(st2, ev_split, 0);
         k_dem64_free<<<(P.np + 31) / 32, 128, 0, st2>>>(P);
         cudaEventRecord(ev_free, st2);
+        k_dem64_plan<<<1, 256, 0, st>>>(P);
         launch_dem64c(P, st);
         cudaStreamWaitEvent(st, ev_free, 0);
+        k_dem64_commit<<<(P.np + 127) / 128, 128, 0, st>>>(P);
     } else {
         k_dem<<<1, 256, 0, st>>>(P);
     }

@@ -979,9 +979,9 @@ int lbm_kernels_per_step(const lbm_handle *h) {
     // (particles, n_sub > 0); once the fixed-geometry sweep runs: its link and
     // plain kernels
     const bool geom_static = h->all_fixed && h->static_steps >= kStaticFlagSteps;
-    // the FP64-integrator DEM is five kernels (split, inactive particles,
-    // tiny, small and large contact groups)
-    const int dem = h->np > 0 && h->cfg.n_sub > 0 ? (h->dem_mode == DEM_FP64_INTEGRATOR ? 5 : 1) : 0;
+    // the FP64-integrator DEM is six kernels (every particle's free step, the
+    // split, tiny, small and large contact groups, the free steps taken)
+    const int dem = h->np > 0 && h->cfg.n_sub > 0 ? (h->dem_mode == DEM_FP64_INTEGRATOR ? 6 : 1) : 0;
     if (geom_static && h->static_state == 1) return 2 + dem;
     const int flags = geom_static ? 0 : 1;
     if (h->np == 0) return 4 + flags;

@@ -309,6 +309,10 @@ struct DevParticle {
     float cpw_hl[MAXCP][3][2];
     float x_hl[3][2];
     float vw_f[6];         // v and w in FP32, for the sweeps' wall velocities (binning)
+    // the particle's step if it touches nothing (FP64 integrator below FP64
+    // storage: k_dem64_free, taken by k_dem64_commit when the plan leaves the
+    // particle inactive)
+    double nx[3], nv[3], nq[4], nw[3];
 };
 
 // Everything a kernel needs, passed by value.
