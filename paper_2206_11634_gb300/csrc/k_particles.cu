@@ -100,6 +100,9 @@ __global__ void __launch_bounds__(256) k_bin(Params P) {
     // the binning; slot step+2 (consumed by the near sweep of step-1) is
     // cleared for the next binning
     if (blockIdx.x == 0 && threadIdx.x == 0 && P.pred_count) P.pred_count[(P.step + 2) % 3] = 0;
+    // this step's list of the near set's link-free bricks, filled by the near
+    // sweep (its reader two steps back finished before the last near sweep)
+    if (blockIdx.x == 0 && threadIdx.x == 0 && P.np_count) *P.np_count = 0;
     if (P.bin_next && blockIdx.x == gridDim.x - 1) {
         // the region of step + 1 (that of step - 1, whose readers are done:
         // they ran before this kernel on the same stream)

@@ -868,10 +868,11 @@ __device__ __forceinline__ bool brick_near_solid(const Params &P, int bxi, int b
 // grown search box meets) and of the predicted-near bricks that are not
 // listed: every brick k_sweep_plain leaves.  A brick of this set that can
 // hold no particle link (no particle listed, or no solid node next to it)
-// takes the plain path, here (kSplit false: the batched sweep) or in
-// k_sweep_near_plain (kSplit true), which runs beside on the plain sweep's
-// stream at the plain sweep's occupancy while this kernel keeps its CTAs
-// for the link bricks.  Persistent grid;
+// takes the plain path, here (kSplit false: the batched sweep), or (kSplit
+// true) it is appended to the step's list for k_sweep_near_plain, which runs
+// after this kernel on the plain sweep's stream at the plain sweep's
+// occupancy, while this kernel keeps its CTAs for the link bricks.
+// Persistent grid;
 // the CTAs take the bricks one at a time from a per-step counter (a brick
 // with particle links costs about ten times one on the plain path, and a
 // fixed split left the busiest CTA near 1.45 times the mean).  Thread 0
@@ -915,14 +916,16 @@ __device__ __forceinline__ void near_work(const Params &P, SmemParticles &sp, do
         } else {
             __syncthreads();
         }
+        done++;
         if (cnt == 0) {
-            if (kSplit) continue;  // k_sweep_near_plain takes it
-            done++;
+            if (kSplit) {  // k_sweep_near_plain takes it (each brick is listed once a step)
+                if (tid == 0) P.np_list[atomicAdd(P.np_count, 1)] = b;
+                continue;
+            }
             const int x = bx0 + tid % BX, y = by0 + (tid / BX) % BY, z = bz0 + tid / (BX * BY);
             if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce>(P, x, y, z, x + P.nx * (y + P.ny * z));
             continue;
         }
-        done++;
         if (tid == 0) s_links = 0;
         near_brick<S, Q, kForce>(P, sp, red, &s_links, &ls, b, bx0, by0, bz0, cnt);
     }
@@ -938,34 +941,22 @@ __global__ void __launch_bounds__(BRICK, kNearCtasPerSm) k_sweep_near(Params P) 
     near_work<S, Q, kForce, true>(P, sp, red, s_links, ls, s_next);
 }
 
-// The bricks of the near set that hold no particle link (near_work's test,
-// the same answer): the plain path, a brick per CTA at a time over a
-// persistent grid, on the plain sweep's stream after the flag pass.
+// The bricks of the near set that hold no particle link, as the near sweep
+// listed them (np_list, np_count: this step's parity): the plain path, one
+// brick per CTA at a time over a persistent grid, on the plain sweep's stream
+// after the near sweep.  It reads nothing else of the step's lists, so the
+// next step's binning and flag pass (which rewrite them) may run beside it.
 template <typename S, int Q, bool kForce>
 __global__ void __launch_bounds__(BRICK, 4) k_sweep_near_plain(Params P) {
     const int tid = threadIdx.x;
-    const int t = P.step;
-    const int c_exact = P.counters[CNT_LISTED];
-    const int c_pred = P.pred_stamp_cur ? P.pred_count[t % 3] : 0;
-    const int total = c_exact + c_pred;
-    int done = 0;
+    const int total = *P.np_count;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
-        int b;
-        if (w < c_exact) {
-            b = P.wl_list[(t % 3) * P.nbricks + w];
-        } else {
-            b = P.pred_list_cur[w - c_exact];
-            if (P.stamp[b] == t) continue;  // listed: taken above
-        }
+        const int b = P.np_list[w];
         int bxi, byi, bzi;
         brick_coords(P, b, bxi, byi, bzi);
-        const int cnt = min(P.bcount[b], MAXPB);
-        if (cnt > 0 && (!P.brick_solid || brick_near_solid(P, bxi, byi, bzi))) continue;  // the near sweep's
-        done++;
         const int x = bxi * BX + tid % BX, y = byi * BY + (tid / BX) % BY, z = bzi * BZ + tid / (BX * BY);
         if (x < P.nx && y < P.ny && z < P.nz) plain_node<S, Q, kForce>(P, x, y, z, x + P.nx * (y + P.ny * z));
     }
-    if (tid == 0 && done) atomicAdd(&P.counters[CNT_NEAR], done);
 }
 
 }  // namespace lbmmb

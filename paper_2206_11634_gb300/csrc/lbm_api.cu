@@ -30,7 +30,7 @@ void split_pair(double v, float out[2]) {
 struct Layout {
     size_t f[2], flags[2];
     size_t wl_list, wl_count, stamp;
-    size_t pred_stamp, pred_list, pred_count, skip, brick_solid;
+    size_t pred_stamp, pred_list, pred_count, skip, brick_solid, np_list, np_count;
     size_t bin;        // bcount[nbricks] followed by the per-step counters
     size_t bin_bytes;
     size_t bin_alt;    // second per-step region: step t uses bin (t even) or bin_alt (t odd)
@@ -101,6 +101,8 @@ void make_layout(const lbm_config *c, Layout *L) {
     L->pred_count = take(3 * 4);
     L->skip = take(3 * nb * 4);
     L->brick_solid = take(nb);
+    L->np_list = take(2 * nb * 4);  // by step parity
+    L->np_count = take(2 * 4);
     // per-step regions, one per step parity, clear when a step starts: brick
     // counts, counters, and (FP32 and below) the fixed-point force/torque
     // totals; the binning of step t clears the region of step t + 1
@@ -173,7 +175,6 @@ struct lbm_handle {
     // sweep of t+1 waits for it (it reads its halo).
     cudaStream_t aux, hi;
     cudaEvent_t ev_fork, ev_bin, ev_plain, ev_near, ev_join;
-    cudaEvent_t ev_flags;  // after the flag pass (the near set's plain bricks wait for it)
     // FP64-integrator DEM: the particles that cannot touch anything during a
     // step move on dem2 (high priority), forked from hi after the split
     cudaStream_t dem2;
@@ -261,6 +262,8 @@ Params make_params(lbm_handle *h) {
     P.pred_list_next = at<int>(h, h->L.pred_list + (size_t)(1 - cur) * h->L.nbricks * 4);
     P.pred_count = at<int>(h, h->L.pred_count);
     P.skip = at<int>(h, h->L.skip);
+    P.np_list = at<int>(h, h->L.np_list + (size_t)cur * h->L.nbricks * 4);
+    P.np_count = at<int>(h, h->L.np_count + (size_t)cur * 4);
     P.brick_solid = at<uint8_t>(h, h->L.brick_solid);
     if (h->L.snode_cap > 0) {
         P.sskip = at<uint8_t>(h, h->L.sskip);
@@ -524,7 +527,7 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
     // bricks occupied, no contacts, no errors
     const size_t zero_from = L.flags[0];
     h->aux = h->hi = h->dem2 = nullptr;
-    h->ev_fork = h->ev_bin = h->ev_plain = h->ev_near = h->ev_join = h->ev_flags = nullptr;
+    h->ev_fork = h->ev_bin = h->ev_plain = h->ev_near = h->ev_join = nullptr;
     h->ev_dsplit = h->ev_dfree = nullptr;
     h->dem_mode = DEM_FP64_ALL;
     h->pin = nullptr;
@@ -557,7 +560,6 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_bin, cudaEventDisableTiming), "cudaEventCreate");
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_plain, cudaEventDisableTiming), "cudaEventCreate");
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_near, cudaEventDisableTiming), "cudaEventCreate");
-        if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_flags, cudaEventDisableTiming), "cudaEventCreate");
         if (rc == LBM_OK)
             rc = cuda_check(h, cudaStreamCreateWithPriority(&h->dem2, cudaStreamNonBlocking, prio_high), "cudaStreamCreateWithPriority");
         if (rc == LBM_OK) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_dsplit, cudaEventDisableTiming), "cudaEventCreate");
@@ -583,7 +585,6 @@ int init_handle(const lbm_config *cfg, void *dev_ws, size_t ws_bytes, void *cuda
         if (h->ev_bin) cudaEventDestroy(h->ev_bin);
         if (h->ev_plain) cudaEventDestroy(h->ev_plain);
         if (h->ev_near) cudaEventDestroy(h->ev_near);
-        if (h->ev_flags) cudaEventDestroy(h->ev_flags);
         if (h->ev_join) cudaEventDestroy(h->ev_join);
         if (h->ev_pin) cudaEventDestroy(h->ev_pin);
         if (h->ev_dsplit) cudaEventDestroy(h->ev_dsplit);
@@ -912,8 +913,6 @@ int lbm_step(lbm_handle *h, int nsteps) {
             e = cudaEventRecord(h->ev_bin, hs);
             if (e != cudaSuccess) return cuda_check(h, e, "event record");
             { ProfScope s(h, 1, !geom_static, hs); if (!geom_static) by_storage<DoFlags>(h->cfg.storage, P, hs); }
-            e = cudaEventRecord(h->ev_flags, hs);
-            if (e != cudaSuccess) return cuda_check(h, e, "event record");
             // the near sweep reads the halo the previous plain sweep wrote (this
             // wait is issued before ev_plain is recorded again below; the plain
             // sweep of the call before was joined into `stream` before the fork,
@@ -939,17 +938,15 @@ int lbm_step(lbm_handle *h, int nsteps) {
                 e = cudaStreamWaitEvent(h->aux, h->ev_bin, 0);
                 if (e != cudaSuccess) return cuda_check(h, e, "stream wait");
                 { ProfScope s(h, 2, true, h->aux); by_storage<DoPlain>(h->cfg.storage, P, h->aux); }
-                // then the near set's bricks without particle links (the
-                // flag pass decides which), beside the near sweep
-                e = cudaStreamWaitEvent(h->aux, h->ev_flags, 0);
-                if (e != cudaSuccess) return cuda_check(h, e, "stream wait");
-                { ProfScope s(h, 6, true, h->aux); by_storage<DoNearPlain>(h->cfg.storage, P, h->aux); }
-                e = cudaEventRecord(h->ev_plain, h->aux);
-                if (e != cudaSuccess) return cuda_check(h, e, "event record");
                 { ProfScope s(h, 3, true, hs); by_storage<DoNear>(h->cfg.storage, P, hs); }
                 e = cudaEventRecord(h->ev_near, hs);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_near, 0);
                 if (e != cudaSuccess) return cuda_check(h, e, "stream fork");
+                // then the near set's bricks without particle links, as the
+                // near sweep listed them
+                { ProfScope s(h, 6, true, h->aux); by_storage<DoNearPlain>(h->cfg.storage, P, h->aux); }
+                e = cudaEventRecord(h->ev_plain, h->aux);
+                if (e != cudaSuccess) return cuda_check(h, e, "event record");
             }
         }
         if (!P.force_fixed) { ProfScope s(h, 4, P.np > 0, hs); launch_force_reduce(P, hs); }

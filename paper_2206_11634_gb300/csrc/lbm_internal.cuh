@@ -363,6 +363,10 @@ struct Params {
     int *pred_list_cur;    // [nbricks]
     int *pred_list_next;   // [nbricks]
     int *pred_count;       // [3], ring by step
+    // the near set's bricks without particle links, listed by the near sweep
+    // for k_sweep_near_plain (this step's parity; NULL: not split)
+    int *np_list;          // [nbricks]
+    int *np_count;         // [1]
     // Bricks the plain sweep of a step leaves alone, ring of three by step
     // (== step: binned or predicted near).  The plain sweep of step t runs
     // while the chain of t and the binning of t+1 run; the binning of t+1
